@@ -1,0 +1,236 @@
+/*
+ * ngb.h -- C ABI of the GB300 spiking-network simulator core.
+ *
+ * The library simulates networks of spiking point neurons on one GPU with the
+ * method of Golosio et al., "Fast simulations of highly-connected spiking
+ * cortical models using GPUs" (NeuronGPU, 2020):
+ *   - LIF neurons with exponential post-synaptic currents (Eqs. 1-2), updated
+ *     by exact integration on the dt grid (Sec. 2.1);
+ *   - AdEx neurons with exponential conductance synapses (Eqs. 3-5), updated by
+ *     an embedded fifth-order Runge-Kutta method with adaptive step size
+ *     (Sec. 2.1);
+ *   - Poisson generators as external drive (Sec. 2.1, devices);
+ *   - connections by the fixed-indegree and fixed-total-number rules (Sec. 2.1)
+ *     stored per source, grouped by delay (Sec. 2.2);
+ *   - spike delivery: every spike of step t adds each outgoing synapse weight to
+ *     the target's input of step t + delay (Sec. 2.2).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value 0 (NGB_OK) on success, a negative NGB_ERR_* code on failure;
+ *     ngb_last_error() then returns a message (thread-local, valid until the
+ *     next call on the same thread).
+ *   - All pointers in this header are HOST pointers; the library owns all
+ *     device memory it allocates and frees it in ngb_destroy().  Output arrays
+ *     are caller-owned and must hold the stated number of elements.
+ *   - A handle is not thread-safe: use one handle per thread.
+ *   - Units: ms, mV, pF, pA, nS, Hz.
+ *   - A spike reported at step s crossed threshold during step s, i.e. in the
+ *     interval [s*dt, (s+1)*dt); its time is (s+1)*dt.
+ *   - Neuron ids are global (creation order over all populations) unless a call
+ *     says population-local.
+ */
+#ifndef NGB_H
+#define NGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- errors */
+#define NGB_OK 0
+#define NGB_ERR_INVALID_ARG (-1) /* an argument is out of range or inconsistent */
+#define NGB_ERR_STATE (-2)       /* call not allowed now (e.g. connect after the first simulate) */
+#define NGB_ERR_OOM (-3)         /* a device or host allocation failed */
+#define NGB_ERR_CUDA (-4)        /* a CUDA call failed; the message names it */
+#define NGB_ERR_TIMEOUT (-5)     /* a bounded device wait gave up */
+#define NGB_ERR_OVERFLOW (-6)    /* spike record full, delay beyond the ring, or RK sub-step cap hit */
+
+/* ----------------------------------------------------------------- enums */
+typedef enum { NGB_WEIGHT_FP32 = 0, NGB_WEIGHT_BF16 = 1, NGB_WEIGHT_FP16 = 2 } ngb_weight_dtype;
+typedef enum { NGB_LIF_PSC_EXP = 0, NGB_AEIF_COND_EXP = 1 } ngb_model;
+typedef enum { NGB_RULE_FIXED_INDEGREE = 0, NGB_RULE_FIXED_TOTAL_NUMBER = 1 } ngb_rule;
+typedef enum { NGB_DIST_CONST = 0, NGB_DIST_NORMAL = 1, NGB_DIST_UNIFORM = 2 } ngb_dist;
+typedef enum {
+  NGB_VAR_V_M = 0,     /* membrane potential, mV (both models) */
+  NGB_VAR_I_SYN = 1,   /* LIF: synaptic current, pA.  AdEx: adaptation current w, pA */
+  NGB_VAR_G_EX = 2,    /* AdEx: excitatory conductance, nS */
+  NGB_VAR_G_IN = 3,    /* AdEx: inhibitory conductance, nS */
+  NGB_VAR_REFRACT = 4, /* LIF: refractory steps left */
+  NGB_VAR_H = 5        /* AdEx: carried Runge-Kutta step proposal, ms */
+} ngb_state_var;
+
+/* ------------------------------------------------------------ structures */
+/* Simulation-wide settings (ngb_create). */
+typedef struct {
+  double dt_ms;            /* time step, > 0 */
+  uint64_t seed;           /* key of instance 0's random streams */
+  int32_t weight_dtype;    /* ngb_weight_dtype: storage of synapse weights; accumulation is FP32 */
+  int32_t device;          /* CUDA device ordinal */
+  void* stream;            /* cudaStream_t to run on, or NULL for a library-owned stream */
+  int32_t deterministic;   /* 1: accumulate inputs in 64-bit fixed point (2^-32 units), so the
+                              result does not depend on the order of the atomic additions */
+  int32_t record_spikes;   /* 1: keep every spike for ngb_get_spikes */
+  int64_t record_capacity; /* device spike-record entries between drains; 0 = default */
+  int32_t steps_per_graph; /* steps captured in one CUDA graph; 0 = default, <0 = no graph */
+  int32_t drain_steps;     /* steps between spike-record drains; 0 = default */
+} ngb_sim_config;
+
+/* External Poisson drive of a population (Sec. 2.1, Poisson generator device):
+ * every neuron independently receives k ~ Poisson(n_inputs * rate_hz * dt)
+ * input spikes per step, each of weight `weight` (pA for LIF, nS for AdEx),
+ * on receptor `receptor` (AdEx: 0 excitatory, 1 inhibitory). */
+typedef struct {
+  double n_inputs;
+  double rate_hz;
+  double weight;
+  int32_t receptor;
+  int32_t pad_;
+} ngb_poisson_drive;
+
+/* LIF with exponential PSC (Eqs. 1-2).  Initial V ~ Normal(V_init_mean, V_init_sd). */
+typedef struct {
+  double tau_m_ms, C_m_pF, E_L_mV, V_reset_mV, V_th_mV, t_ref_ms, tau_syn_ms, I_e_pA;
+  double V_init_mean_mV, V_init_sd_mV;
+  ngb_poisson_drive poisson;
+} ngb_lif_params;
+
+/* AdEx with exponential conductances (Eqs. 3-5).  No refractory period.
+ * rk_tol: relative tolerance of the adaptive Runge-Kutta step; with FP32 state
+ * the effective tolerance is max(rk_tol, 8 * 2^-24). */
+typedef struct {
+  double C_m_pF, g_L_nS, E_L_mV, V_T_mV, Delta_T_mV, a_nS, b_pA, tau_w_ms, V_peak_mV, V_reset_mV;
+  double E_ex_mV, E_in_mV, tau_ex_ms, tau_in_ms, I_e_pA;
+  double V_init_mean_mV, V_init_sd_mV, w_init_pA;
+  double rk_tol, rk_h_min_ms, rk_h_init_ms;
+  int64_t rk_max_substeps;
+  ngb_poisson_drive poisson;
+} ngb_aeif_params;
+
+/* Connection rule (Sec. 2.1).  FIXED_INDEGREE: every target draws K sources
+ * uniformly with replacement.  FIXED_TOTAL_NUMBER: K (source, target) pairs
+ * drawn uniformly with replacement.  Multapses are allowed; autapses only
+ * when allow_autapses is set (and only matter when source == target pop). */
+typedef struct {
+  int32_t rule;
+  int32_t allow_autapses;
+  int64_t K;
+} ngb_conn_spec;
+
+/* Distribution of a synapse parameter.  CONST: p0.  NORMAL(mean p0, sd p1):
+ * for weights re-drawn until the sign equals the sign of the mean; for delays
+ * re-drawn until >= dt.  UNIFORM on (p0, p1]. */
+typedef struct {
+  int32_t dist;
+  int32_t pad_;
+  double p0, p1;
+} ngb_dist_spec;
+
+/* Synapse parameters: weight (pA for LIF targets, nS for AdEx targets; an
+ * inhibitory AdEx synapse has a positive weight on receptor 1), delay in ms
+ * (rounded to the nearest step, ties to even, at least one step). */
+typedef struct {
+  ngb_dist_spec weight;
+  ngb_dist_spec delay_ms;
+  int32_t receptor;
+  int32_t pad_;
+} ngb_syn_spec;
+
+/* Counters accumulated since ngb_create. */
+typedef struct {
+  int64_t steps;        /* steps simulated */
+  int64_t spikes;       /* spikes emitted (with multiplicity) */
+  int64_t events;       /* synaptic events delivered (spikes x out-degree) */
+  int64_t rk_substeps;  /* accepted + rejected Runge-Kutta sub-steps of all AdEx neurons */
+  int64_t num_neurons;
+  int64_t num_synapses;
+  int64_t num_groups;   /* (source, delay) connection groups */
+  int64_t ring_slots;   /* L, a power of two > max delay in steps */
+  int64_t max_delay_steps;
+  int64_t device_bytes; /* device memory held by the handle */
+} ngb_stats;
+
+typedef struct ngb_sim ngb_sim;
+
+/* ------------------------------------------------------------ lifecycle */
+/* Create an empty simulation on cfg->device.  *out receives the handle. */
+int ngb_create(ngb_sim** out, const ngb_sim_config* cfg);
+
+/* Free every resource of the handle; NULL is a no-op. */
+int ngb_destroy(ngb_sim* sim);
+
+/* Message of the last failed call on this thread ("" if none).  `sim` may be NULL. */
+const char* ngb_last_error(const ngb_sim* sim);
+
+/* -------------------------------------------------------- construction */
+/* Add a network instance with its own random key (batched execution: several
+ * independent networks advance in the same kernels; instance 0 exists from
+ * ngb_create with cfg->seed).  Random streams use instance-local neuron ids
+ * and connect-call indices, so an instance's result does not depend on what
+ * else is batched with it.  NGB_ERR_STATE after the first simulate. */
+int ngb_add_instance(ngb_sim* sim, uint64_t seed, int32_t* instance_out);
+
+/* Add n neurons of `model` (params: ngb_lif_params* or ngb_aeif_params*) to
+ * instance 0.  Population ids count from 0 over the whole handle. */
+int ngb_add_population(ngb_sim* sim, int32_t model, int64_t n, const void* params, int32_t* pop_id_out);
+
+/* As ngb_add_population, into the given instance. */
+int ngb_add_population_in(ngb_sim* sim, int32_t instance, int32_t model, int64_t n, const void* params,
+                          int32_t* pop_id_out);
+
+/* Connect src_pop -> tgt_pop (same instance) with rule `conn` and synapse
+ * parameters `syn` (Sec. 2.1).  Synapses are drawn on the device when the
+ * network is finalised (first ngb_simulate or ngb_finalize). */
+int ngb_connect(ngb_sim* sim, int32_t src_pop, int32_t tgt_pop, const ngb_conn_spec* conn,
+                const ngb_syn_spec* syn);
+
+/* Build the delay-grouped CSR on the device (Sec. 2.2 connection groups),
+ * allocate state, ring buffer and spike lists, and capture the step graph.
+ * Called implicitly by the first ngb_simulate. */
+int ngb_finalize(ngb_sim* sim);
+
+/* ----------------------------------------------------------- simulation */
+/* Advance every instance by `steps` steps; returns when done (blocking). */
+int ngb_simulate(ngb_sim* sim, int64_t steps);
+
+/* As ngb_simulate, without CUDA graphs, with CUDA events around every kernel
+ * launch.  kernel_ms[3] receives the summed device time of the LIF update,
+ * AdEx update and delivery kernels; launches[3] their launch counts. */
+int ngb_simulate_profiled(ngb_sim* sim, int64_t steps, double* kernel_ms, int64_t* launches);
+
+/* Spikes recorded in steps [t0_step, t1_step) of population `pop` (-1 = all,
+ * then ids are global; else population-local), sorted by (step, id).  With
+ * ids == NULL only *n_out is set.  Otherwise up to `capacity` entries are
+ * written and *n_out is the number available. */
+int ngb_get_spikes(ngb_sim* sim, int32_t pop, int64_t t0_step, int64_t t1_step, int32_t* ids,
+                   int64_t* steps, int64_t capacity, int64_t* n_out);
+
+/* --------------------------------------------------------- introspection */
+int ngb_get_stats(ngb_sim* sim, ngb_stats* out);
+
+/* Global id of the first neuron of `pop` and its size. */
+int ngb_population_range(ngb_sim* sim, int32_t pop, int64_t* offset_out, int64_t* n_out);
+
+/* Copy state variable `var` (ngb_state_var) of neurons [first, first+n) into out[n]. */
+int ngb_get_state(ngb_sim* sim, int32_t var, int64_t first, int64_t n, float* out);
+
+/* Copy the input accumulated so far for step (current step + step_offset),
+ * receptor `receptor`, neurons [first, first+n), as FP32 (offset 0 is the
+ * complete synaptic input the next update consumes; the Poisson drive is not
+ * included).  0 <= step_offset < ring slots. */
+int ngb_get_input(ngb_sim* sim, int32_t receptor, int64_t step_offset, int64_t first, int64_t n, float* out);
+
+/* Number of synapses of sources [0, N) before each source: src_ptr[N+1]. */
+int ngb_get_src_ptr(ngb_sim* sim, uint64_t* src_ptr);
+
+/* Synapses [first, first+n) of the CSR in storage order (source, delay,
+ * connect call, draw index): global target id, receptor, weight widened to
+ * FP32, delay in steps. Any output pointer may be NULL. */
+int ngb_get_synapses(ngb_sim* sim, int64_t first, int64_t n, uint32_t* tgt, uint8_t* receptor, float* weight,
+                     uint16_t* delay);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NGB_H */

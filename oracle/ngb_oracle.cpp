@@ -1,0 +1,849 @@
+// ngb_oracle.cpp -- plain, slow CPU oracle of the spiking-network hot path.
+//
+// TEST INFRASTRUCTURE ONLY: only tests/, the smoke check and the benchmark's
+// CPU-baseline leg may load this file's library.  It shares no code with the
+// GPU library; every step below is written from the method's definition:
+//
+//   * LIF with exponential PSCs (Eqs. 1-2), integrated by exact integration
+//     on the dt grid (Sec. 2.1, "The NeuronGPU library", after Rotter &
+//     Diesmann 1999).
+//   * AdEx with conductance synapses (Eqs. 3-5), integrated by an embedded
+//     fifth-order Runge-Kutta method with adaptive step size (Sec. 2.1);
+//     the tableau is the published Cash-Karp (1990) one.
+//   * Poisson generators as the external drive (Sec. 2.1, devices).
+//   * Connections by the fixed-indegree and fixed-total-number rules
+//     (Sec. 2.1), grouped per source by delay (Sec. 2.2).
+//   * Spike delivery: a spike of neuron s at step t adds each synapse weight
+//     to its target's input at step t + delay, once (Sec. 2.2).
+//
+// Readings where the paper is silent or garbled (summation index of Eq. 2,
+// sign of Eq. 4, step order, RNG layout, delay rounding, ...) are the ones
+// listed in the design notes; each is restated next to the code using it.
+// Parity status: see ngb_oracle.h.
+//
+// Build with -ffp-contract=off: FP32 expressions are evaluated op by op with
+// round-to-nearest, in the order written.
+
+#include "ngb_oracle.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_err;
+
+int32_t fail(const std::string& m) {
+  g_err = m;
+  return -1;
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+// as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies whose high
+// halves are xored into the other two words together with the round key; the
+// key is bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+void philox(const uint32_t in[4], uint32_t k0, uint32_t k1, uint32_t out[4]) {
+  const uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
+  const uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
+  uint32_t x0 = in[0], x1 = in[1], x2 = in[2], x3 = in[3];
+  for (int round = 0; round < 10; ++round) {
+    const uint64_t prod0 = (uint64_t)kMul0 * (uint64_t)x0;
+    const uint64_t prod1 = (uint64_t)kMul1 * (uint64_t)x2;
+    const uint32_t y0 = (uint32_t)(prod1 >> 32) ^ x1 ^ k0;
+    const uint32_t y1 = (uint32_t)prod1;
+    const uint32_t y2 = (uint32_t)(prod0 >> 32) ^ x3 ^ k1;
+    const uint32_t y3 = (uint32_t)prod0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    k0 += kWeyl0;
+    k1 += kWeyl1;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+// Counter layout (design reading "RNG layout"): key = (seed low, seed high);
+// counter = (index low, index high, purpose | attempt << 8, stream).
+enum Purpose : uint32_t { kSrc = 1, kWeight = 2, kDelay = 3, kPoisson = 4, kVinit = 5 };
+
+void draw(uint64_t seed, uint64_t index, uint32_t purpose, uint32_t attempt, uint32_t stream,
+          uint32_t out[4]) {
+  const uint32_t ctr[4] = {(uint32_t)index, (uint32_t)(index >> 32), purpose | (attempt << 8), stream};
+  philox(ctr, (uint32_t)seed, (uint32_t)(seed >> 32), out);
+}
+
+// Uniform integer in [0, n): high half of the 64-bit product x * n.
+uint32_t uniform_index(uint32_t x, uint32_t n) { return (uint32_t)(((uint64_t)x * n) >> 32); }
+
+// Uniform double in (0, 1] from two words: the top 53 bits, plus one, times 2^-53.
+double uniform53(uint32_t hi, uint32_t lo) {
+  const uint64_t bits = (((uint64_t)hi << 32) | lo) >> 11;
+  return (double)(bits + 1) * 0x1p-53;
+}
+
+// Standard normal by the Box-Muller transform (cosine branch).
+double normal_from(const uint32_t w[4]) {
+  const double two_pi = 6.283185307179586;
+  const double u1 = uniform53(w[0], w[1]);
+  const double u2 = uniform53(w[2], w[3]);
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(two_pi * u2);
+}
+
+// Poisson(lambda) by inversion: the smallest k with u < F(k), u = x * 2^-32,
+// F accumulated term by term from p0 = exp(-lambda), p_k = p_{k-1} * lambda / k.
+const int kPoissonKmax = 255;
+int poisson_inversion(double lambda, uint32_t x) {
+  const double u = (double)x * 0x1p-32;
+  double p = std::exp(-lambda);
+  double F = p;
+  int k = 0;
+  while (u >= F && k < kPoissonKmax) {
+    k += 1;
+    p = p * lambda / (double)k;
+    F = F + p;
+  }
+  return k;
+}
+
+// Exact-integration propagators of Eqs. 1-2 over one step h (y = V - E_L):
+//   y(t+h) = P22 y + P21 I + P20 I_e,  I(t+h) = P11 I.
+void lif_propagators(double tau_m, double C, double tau_s, double h, double P[4]) {
+  const double P11 = std::exp(-h / tau_s);
+  const double P22 = std::exp(-h / tau_m);
+  double P21;
+  if (tau_m == tau_s) {
+    P21 = h / C * P22;
+  } else {
+    P21 = tau_m * tau_s / (C * (tau_m - tau_s)) * (std::expm1(-h / tau_m) - std::expm1(-h / tau_s));
+  }
+  const double P20 = -tau_m / C * std::expm1(-h / tau_m);
+  P[0] = P11; P[1] = P21; P[2] = P22; P[3] = P20;
+}
+
+// Cash & Karp (1990) embedded 4(5) Runge-Kutta tableau.
+struct Tableau {
+  double c[6];
+  double a[6][6];
+  double b5[6];
+  double b4[6];
+};
+Tableau cash_karp() {
+  Tableau t;
+  std::memset(&t, 0, sizeof(t));
+  const double c[6] = {0.0, 1.0 / 5.0, 3.0 / 10.0, 3.0 / 5.0, 1.0, 7.0 / 8.0};
+  for (int i = 0; i < 6; ++i) t.c[i] = c[i];
+  t.a[1][0] = 1.0 / 5.0;
+  t.a[2][0] = 3.0 / 40.0;        t.a[2][1] = 9.0 / 40.0;
+  t.a[3][0] = 3.0 / 10.0;        t.a[3][1] = -9.0 / 10.0;   t.a[3][2] = 6.0 / 5.0;
+  t.a[4][0] = -11.0 / 54.0;      t.a[4][1] = 5.0 / 2.0;     t.a[4][2] = -70.0 / 27.0;
+  t.a[4][3] = 35.0 / 27.0;
+  t.a[5][0] = 1631.0 / 55296.0;  t.a[5][1] = 175.0 / 512.0; t.a[5][2] = 575.0 / 13824.0;
+  t.a[5][3] = 44275.0 / 110592.0; t.a[5][4] = 253.0 / 4096.0;
+  const double b5[6] = {37.0 / 378.0, 0.0, 250.0 / 621.0, 125.0 / 594.0, 0.0, 512.0 / 1771.0};
+  const double b4[6] = {2825.0 / 27648.0, 0.0, 18575.0 / 48384.0, 13525.0 / 55296.0,
+                        277.0 / 14336.0, 1.0 / 4.0};
+  for (int i = 0; i < 6; ++i) { t.b5[i] = b5[i]; t.b4[i] = b4[i]; }
+  return t;
+}
+
+// Round an FP32 weight to the storage precision and back (round to nearest,
+// ties to even).  prec 1 = bfloat16 (8-bit exponent, 7 stored mantissa bits),
+// prec 2 = IEEE binary16 (5-bit exponent, 10 mantissa bits, subnormals).
+float round_weight(float w, int prec) {
+  if (prec == 0) return w;
+  if (prec == 1) {
+    uint32_t bits;
+    std::memcpy(&bits, &w, 4);
+    const uint32_t lsb = (bits >> 16) & 1u;
+    bits += 0x7FFFu + lsb;
+    bits &= 0xFFFF0000u;
+    float r;
+    std::memcpy(&r, &bits, 4);
+    return r;
+  }
+  // binary16: quantum of the binade of |w| (never below the subnormal quantum 2^-24)
+  const double v = (double)w;
+  if (v == 0.0) return w;
+  int e2;
+  std::frexp(std::fabs(v), &e2);        // |v| = m * 2^e2, m in [0.5, 1)
+  int exponent = e2 - 1;                // floor(log2 |v|)
+  if (exponent < -14) exponent = -14;   // subnormal range shares the 2^-24 quantum
+  const double quantum = std::ldexp(1.0, exponent - 10);
+  double r = std::nearbyint(v / quantum) * quantum;
+  if (std::fabs(r) >= 65520.0) r = std::copysign(INFINITY, v);
+  return (float)r;
+}
+
+// ---------------------------------------------------------------------------
+// Network description
+// ---------------------------------------------------------------------------
+struct LifPar {
+  double tau_m, C_m, E_L, V_reset, V_th, t_ref, tau_syn, I_e, V0_mean, V0_sd;
+  double pn, prate, pw;
+  int precv;
+};
+struct AeifPar {
+  double C_m, g_L, E_L, V_T, Delta_T, a, b, tau_w, V_peak, V_reset, E_ex, E_in, tau_ex, tau_in, I_e;
+  double V0_mean, V0_sd, w0, tol, h_min, h_init;
+  int64_t max_sub;
+  double pn, prate, pw;
+  int prec_rcpt;
+  int fp64;
+};
+
+struct Population {
+  int model;          // 0 LIF, 1 AdEx
+  int instance;
+  int64_t n;
+  int64_t offset;     // first global neuron id
+  int64_t local_off;  // first instance-local neuron id
+  LifPar lif;
+  AeifPar aeif;
+  // derived
+  double lambda;      // Poisson mean per step
+  float P11, P21, P22, P20Ie, theta, y_reset, w_ext;
+  int ref_steps;
+};
+
+struct Instance {
+  uint64_t seed;
+  int64_t n;
+  uint32_t n_calls;
+};
+
+struct Call {
+  int src_pop, tgt_pop, rule, autapses, wdist, ddist, receptor;
+  int64_t K;
+  double w0, w1, d0, d1;
+  uint32_t stream;  // connect-call index within the instance
+};
+
+struct Synapse {
+  uint32_t src, tgt;
+  float w;
+  uint16_t delay;
+  uint8_t receptor;
+};
+
+}  // namespace
+
+struct ora_net {
+  double dt;
+  int prec;
+  int deterministic;
+  int track_abs;
+  std::vector<Instance> inst;
+  std::vector<Population> pops;
+  std::vector<Call> calls;
+  bool finalized = false;
+  int64_t N = 0;
+  // canonical CSR, source-major, ordered by (source, delay, call, draw index)
+  std::vector<uint64_t> src_ptr;
+  std::vector<uint32_t> tgt;
+  std::vector<uint8_t> rcpt;
+  std::vector<float> w;
+  std::vector<uint16_t> delay;
+  int max_delay = 1;
+  int64_t L = 2;
+  int R = 1;
+  // per-neuron state (double arrays; FP32 models keep float-representable values)
+  std::vector<double> s0, s1, s2, s3, s4;  // LIF: y, I, ref | AdEx: V, w, gex, gin, h
+  std::vector<int> pop_of;
+  // ring[(slot * R + r) * N + i]
+  std::vector<float> ring;
+  std::vector<int64_t> ring_fx;
+  std::vector<double> ring_abs, ring_exact;
+  int64_t t = 0;
+  int64_t events = 0;
+  int64_t rk_substeps = 0;
+  int64_t rk_cap_hits = 0;  // steps whose sub-step count reached the cap
+  std::vector<int64_t> spk_id, spk_step;
+};
+
+namespace {
+
+const double kFixScale = 4294967296.0;  // 2^32: fixed-point ring of the deterministic mode
+
+uint16_t delay_steps(double d_ms, double dt) {
+  double s = std::nearbyint(d_ms / dt);  // round half to even
+  if (s < 1.0) s = 1.0;
+  if (s > 4095.0) s = 4095.0;
+  return (uint16_t)s;
+}
+
+// Draw the weight of one synapse (draw index q of call c), re-drawing a
+// normal sample until its sign equals the sign of the mean.
+double draw_weight(const ora_net* net, const Call& c, uint64_t seed, uint64_t q) {
+  (void)net;
+  if (c.wdist == 0) return c.w0;
+  for (uint32_t attempt = 0;; ++attempt) {
+    uint32_t r[4];
+    draw(seed, q, kWeight, attempt, c.stream, r);
+    if (c.wdist == 1) {
+      const double v = c.w0 + c.w1 * normal_from(r);
+      if (c.w0 > 0.0 && !(v > 0.0)) continue;
+      if (c.w0 < 0.0 && !(v < 0.0)) continue;
+      return v;
+    }
+    return c.w0 + (c.w1 - c.w0) * uniform53(r[0], r[1]);
+  }
+}
+
+// Draw the delay (ms) of one synapse; a normal delay is re-drawn until >= dt.
+double draw_delay(const ora_net* net, const Call& c, uint64_t seed, uint64_t q) {
+  if (c.ddist == 0) return c.d0;
+  for (uint32_t attempt = 0;; ++attempt) {
+    uint32_t r[4];
+    draw(seed, q, kDelay, attempt, c.stream, r);
+    if (c.ddist == 1) {
+      const double v = c.d0 + c.d1 * normal_from(r);
+      if (v < net->dt) continue;
+      return v;
+    }
+    return c.d0 + (c.d1 - c.d0) * uniform53(r[0], r[1]);
+  }
+}
+
+void generate(const ora_net* net, const Call& c, std::vector<Synapse>& out) {
+  const Population& ps = net->pops[c.src_pop];
+  const Population& pt = net->pops[c.tgt_pop];
+  const uint64_t seed = net->inst[ps.instance].seed;
+  const bool same = (c.src_pop == c.tgt_pop);
+  const uint64_t nsyn = (c.rule == 0) ? (uint64_t)c.K * (uint64_t)pt.n : (uint64_t)c.K;
+  for (uint64_t q = 0; q < nsyn; ++q) {
+    uint32_t src = 0, tgt = 0;
+    for (uint32_t attempt = 0;; ++attempt) {
+      uint32_t r[4];
+      draw(seed, q, kSrc, attempt, c.stream, r);
+      if (c.rule == 0) {
+        tgt = (uint32_t)(q / (uint64_t)c.K);
+        src = uniform_index(r[0], (uint32_t)ps.n);
+      } else {
+        src = uniform_index(r[0], (uint32_t)ps.n);
+        tgt = uniform_index(r[1], (uint32_t)pt.n);
+      }
+      if (same && !c.autapses && src == tgt) continue;
+      break;
+    }
+    Synapse s;
+    s.src = (uint32_t)(ps.offset + src);
+    s.tgt = (uint32_t)(pt.offset + tgt);
+    s.w = round_weight((float)draw_weight(net, c, seed, q), net->prec);
+    s.delay = delay_steps(draw_delay(net, c, seed, q), net->dt);
+    s.receptor = (uint8_t)c.receptor;
+    out.push_back(s);
+  }
+}
+
+// One embedded Cash-Karp step of the AdEx system (Eqs. 3-5 with the
+// conductances of Eq. 4 as state) from y over h; returns the fifth-order
+// solution in y5 and the difference to the fourth-order one in err.
+template <typename T>
+struct AdexSystem {
+  T g_L, E_L, V_T, Delta_T, inv_Delta_T, a, inv_tau_w, V_peak, E_ex, E_in, inv_tau_ex, inv_tau_in, I_e,
+      inv_C;
+  void deriv(const T y[4], T f[4]) const {
+    const T V = std::min(y[0], V_peak);  // the exponential is evaluated at most at V_peak
+    const T I_spike = (Delta_T > T(0)) ? g_L * Delta_T * std::exp((V - V_T) * inv_Delta_T) : T(0);
+    // reading of Eq. 4: I_syn = sum_i g_i (E_rev,i - V), so excitation depolarises
+    const T I_syn = y[2] * (E_ex - V) + y[3] * (E_in - V);
+    f[0] = (-g_L * (V - E_L) + I_spike + I_syn - y[1] + I_e) * inv_C;
+    f[1] = (a * (V - E_L) - y[1]) * inv_tau_w;
+    f[2] = -y[2] * inv_tau_ex;
+    f[3] = -y[3] * inv_tau_in;
+  }
+};
+
+template <typename T>
+void ck_step(const AdexSystem<T>& sys, const Tableau& tab, const T y[4], const T f0[4], double h, T y5[4],
+             T err[4]) {
+  T k[6][4];
+  for (int i = 0; i < 4; ++i) k[0][i] = f0[i];
+  for (int s = 1; s < 6; ++s) {
+    T ys[4];
+    for (int i = 0; i < 4; ++i) {
+      T acc = T(0);
+      for (int j = 0; j < s; ++j) acc += T(tab.a[s][j]) * k[j][i];
+      ys[i] = y[i] + T(h) * acc;
+    }
+    sys.deriv(ys, k[s]);
+  }
+  for (int i = 0; i < 4; ++i) {
+    T acc5 = T(0), accd = T(0);
+    for (int s = 0; s < 6; ++s) {
+      acc5 += T(tab.b5[s]) * k[s][i];
+      accd += T(tab.b5[s] - tab.b4[s]) * k[s][i];
+    }
+    y5[i] = y[i] + T(h) * acc5;
+    err[i] = T(h) * accd;
+  }
+}
+
+// Integrate one AdEx neuron over one step dt (adaptive step size, error
+// relative to |y| + |h f| + floor, safety factor 0.9, growth exponent -1/5,
+// shrink exponent -1/4, growth at most 5x, shrink at most 10x), resetting
+// V -> V_reset and w -> w + b after every accepted sub-step that ends with
+// V >= V_peak.  Returns the number of spikes; h carries the proposed step.
+template <typename T>
+int adex_advance(const AdexSystem<T>& sys, const Tableau& tab, const AeifPar& p, double dt, double tol,
+                 T y[4], double& h, int64_t& substeps, int64_t& cap_hits) {
+  const T floor_[4] = {T(1.0), T(1.0), T(1e-3), T(1e-3)};
+  int spikes = 0;
+  double t_in = 0.0;
+  int64_t n = 0;
+  if (!(h > 0.0)) h = p.h_init;
+  for (;;) {
+    const double rem = dt - t_in;
+    bool last = false;
+    if (h >= rem) {
+      h = rem;
+      last = true;
+    }
+    T f0[4], y5[4], err[4];
+    sys.deriv(y, f0);
+    ck_step(sys, tab, y, f0, h, y5, err);
+    T emax = T(0);
+    for (int i = 0; i < 4; ++i) {
+      const T scale = std::fabs(y[i]) + std::fabs(T(h) * f0[i]) + floor_[i];
+      const T r = std::fabs(err[i]) / scale;
+      if (r > emax) emax = r;
+    }
+    const double ratio = (double)emax / tol;
+    ++n;
+    if (ratio <= 1.0 || h <= p.h_min || n >= p.max_sub) {
+      for (int i = 0; i < 4; ++i) y[i] = y5[i];
+      if (y[0] >= T(p.V_peak)) {
+        y[0] = T(p.V_reset);
+        y[1] = y[1] + T(p.b);
+        ++spikes;
+      }
+      double grow = 5.0;
+      if (ratio > 0.0) grow = std::min(5.0, 0.9 * std::pow(ratio, -0.2));
+      const double h_used = h;
+      h = std::max(h * grow, p.h_min);
+      if (n >= p.max_sub && !last) cap_hits += 1;
+      if (last || n >= p.max_sub) break;
+      t_in += h_used;
+    } else {
+      const double shrink = std::max(0.1, 0.9 * std::pow(ratio, -0.25));
+      h = std::max(h * shrink, p.h_min);
+    }
+  }
+  substeps += n;
+  return spikes;
+}
+
+float fx_to_float(int64_t v) { return (float)((double)v / kFixScale); }
+
+int64_t ring_index(const ora_net* net, int64_t step, int r, int64_t i) {
+  return ((step % net->L) * net->R + r) * net->N + i;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C interface
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* ora_last_error(void) { return g_err.c_str(); }
+
+ora_net* ora_create(double dt_ms, uint64_t seed, int32_t weight_prec, int32_t deterministic,
+                    int32_t track_abs) {
+  if (!(dt_ms > 0.0) || weight_prec < 0 || weight_prec > 2) {
+    fail("ora_create: invalid dt or weight precision");
+    return nullptr;
+  }
+  ora_net* net = new ora_net();
+  net->dt = dt_ms;
+  net->prec = weight_prec;
+  net->deterministic = deterministic ? 1 : 0;
+  net->track_abs = track_abs ? 1 : 0;
+  net->inst.push_back(Instance{seed, 0, 0});
+  return net;
+}
+
+void ora_destroy(ora_net* net) { delete net; }
+
+int32_t ora_add_instance(ora_net* net, uint64_t seed) {
+  if (!net || net->finalized) return fail("ora_add_instance: bad state");
+  net->inst.push_back(Instance{seed, 0, 0});
+  return (int32_t)net->inst.size() - 1;
+}
+
+int32_t ora_add_population(ora_net* net, int32_t instance, int32_t model, int64_t n, const double* p) {
+  if (!net || net->finalized) return fail("ora_add_population: bad state");
+  if (instance < 0 || instance >= (int32_t)net->inst.size()) return fail("ora_add_population: instance");
+  if (n <= 0 || n > 0x7FFFFFFF || (model != 0 && model != 1)) return fail("ora_add_population: n/model");
+  Population P;
+  std::memset(&P, 0, sizeof(P));
+  P.model = model;
+  P.instance = instance;
+  P.n = n;
+  P.offset = net->N;
+  P.local_off = net->inst[instance].n;
+  const double dt = net->dt;
+  if (model == 0) {
+    LifPar& q = P.lif;
+    q.tau_m = p[0]; q.C_m = p[1]; q.E_L = p[2]; q.V_reset = p[3]; q.V_th = p[4]; q.t_ref = p[5];
+    q.tau_syn = p[6]; q.I_e = p[7]; q.V0_mean = p[8]; q.V0_sd = p[9];
+    q.pn = p[10]; q.prate = p[11]; q.pw = p[12]; q.precv = (int)p[13];
+    if (!(q.tau_m > 0 && q.C_m > 0 && q.tau_syn > 0 && q.t_ref >= 0)) return fail("ora: LIF params");
+    double Pv[4];
+    lif_propagators(q.tau_m, q.C_m, q.tau_syn, dt, Pv);
+    P.P11 = (float)Pv[0];
+    P.P21 = (float)Pv[1];
+    P.P22 = (float)Pv[2];
+    P.P20Ie = (float)(Pv[3] * q.I_e);
+    P.theta = (float)(q.V_th - q.E_L);
+    P.y_reset = (float)(q.V_reset - q.E_L);
+    P.ref_steps = (int)std::nearbyint(q.t_ref / dt);
+    P.lambda = q.pn * q.prate * dt * 1e-3;
+    P.w_ext = (float)q.pw;
+  } else {
+    AeifPar& q = P.aeif;
+    q.C_m = p[0]; q.g_L = p[1]; q.E_L = p[2]; q.V_T = p[3]; q.Delta_T = p[4]; q.a = p[5]; q.b = p[6];
+    q.tau_w = p[7]; q.V_peak = p[8]; q.V_reset = p[9]; q.E_ex = p[10]; q.E_in = p[11];
+    q.tau_ex = p[12]; q.tau_in = p[13]; q.I_e = p[14]; q.V0_mean = p[15]; q.V0_sd = p[16];
+    q.w0 = p[17]; q.tol = p[18]; q.h_min = p[19]; q.h_init = p[20]; q.max_sub = (int64_t)p[21];
+    q.pn = p[22]; q.prate = p[23]; q.pw = p[24]; q.prec_rcpt = (int)p[25]; q.fp64 = (int)p[26];
+    if (!(q.C_m > 0 && q.tau_w > 0 && q.tau_ex > 0 && q.tau_in > 0 && q.tol > 0 && q.h_min > 0 &&
+          q.h_init > 0 && q.max_sub > 0))
+      return fail("ora: AdEx params");
+    P.lambda = q.pn * q.prate * dt * 1e-3;
+    P.w_ext = (float)q.pw;
+    net->R = 2;
+  }
+  if (!(P.lambda >= 0.0 && P.lambda <= 100.0)) return fail("ora: Poisson mean per step must be in [0,100]");
+  net->pops.push_back(P);
+  net->N += n;
+  net->inst[instance].n += n;
+  return (int32_t)net->pops.size() - 1;
+}
+
+int32_t ora_connect(ora_net* net, int32_t src_pop, int32_t tgt_pop, int32_t rule, int64_t K,
+                    int32_t allow_autapses, int32_t wdist, double w0, double w1, int32_t ddist, double d0,
+                    double d1, int32_t receptor) {
+  if (!net || net->finalized) return fail("ora_connect: bad state");
+  const int32_t np = (int32_t)net->pops.size();
+  if (src_pop < 0 || src_pop >= np || tgt_pop < 0 || tgt_pop >= np) return fail("ora_connect: pop");
+  if (net->pops[src_pop].instance != net->pops[tgt_pop].instance) return fail("ora_connect: instances");
+  if (K < 0 || (rule != 0 && rule != 1)) return fail("ora_connect: rule/K");
+  if (receptor < 0 || receptor > 1) return fail("ora_connect: receptor");
+  if (receptor == 1 && net->pops[tgt_pop].model == 0) return fail("ora_connect: LIF has one receptor");
+  if (src_pop == tgt_pop && !allow_autapses && net->pops[src_pop].n < 2 && K > 0)
+    return fail("ora_connect: no admissible source without autapses");
+  Instance& I = net->inst[net->pops[src_pop].instance];
+  Call c{src_pop, tgt_pop, rule, allow_autapses ? 1 : 0, wdist, ddist, receptor, K, w0, w1, d0, d1, I.n_calls};
+  I.n_calls += 1;
+  net->calls.push_back(c);
+  return 0;
+}
+
+int32_t ora_finalize(ora_net* net) {
+  if (!net) return fail("ora_finalize: null");
+  if (net->finalized) return 0;
+  const int64_t N = net->N;
+  // 1. all synapses in (call, draw index) order
+  std::vector<Synapse> syn;
+  uint64_t total = 0;
+  for (const Call& c : net->calls)
+    total += (c.rule == 0) ? (uint64_t)c.K * (uint64_t)net->pops[c.tgt_pop].n : (uint64_t)c.K;
+  syn.reserve((size_t)total);
+  for (const Call& c : net->calls) generate(net, c, syn);
+  // 2. stable counting sort by (source, delay): canonical CSR order
+  int maxd = 1;
+  for (const Synapse& s : syn) maxd = std::max<int>(maxd, s.delay);
+  const int64_t D = maxd + 1;
+  std::vector<uint64_t> bucket((size_t)(N * D + 1), 0);
+  for (const Synapse& s : syn) bucket[(size_t)(s.src * D + s.delay) + 1] += 1;
+  for (size_t b = 1; b < bucket.size(); ++b) bucket[b] += bucket[b - 1];
+  const size_t K = syn.size();
+  net->tgt.assign(K, 0);
+  net->rcpt.assign(K, 0);
+  net->w.assign(K, 0.0f);
+  net->delay.assign(K, 0);
+  for (const Synapse& s : syn) {
+    const size_t pos = (size_t)bucket[(size_t)(s.src * D + s.delay)]++;
+    net->tgt[pos] = s.tgt;
+    net->rcpt[pos] = s.receptor;
+    net->w[pos] = s.w;
+    net->delay[pos] = s.delay;
+  }
+  net->src_ptr.assign((size_t)N + 1, 0);
+  for (const Synapse& s : syn) net->src_ptr[(size_t)s.src + 1] += 1;
+  for (int64_t i = 0; i < N; ++i) net->src_ptr[(size_t)i + 1] += net->src_ptr[(size_t)i];
+  std::vector<Synapse>().swap(syn);
+  net->max_delay = maxd;
+  net->L = maxd + 1;
+  // 3. state
+  net->s0.assign((size_t)N, 0.0); net->s1.assign((size_t)N, 0.0); net->s2.assign((size_t)N, 0.0);
+  net->s3.assign((size_t)N, 0.0); net->s4.assign((size_t)N, 0.0);
+  net->pop_of.assign((size_t)N, 0);
+  for (size_t pi = 0; pi < net->pops.size(); ++pi) {
+    const Population& P = net->pops[pi];
+    const uint64_t seed = net->inst[P.instance].seed;
+    for (int64_t k = 0; k < P.n; ++k) {
+      const int64_t i = P.offset + k;
+      net->pop_of[(size_t)i] = (int)pi;
+      const double mean = P.model == 0 ? P.lif.V0_mean : P.aeif.V0_mean;
+      const double sd = P.model == 0 ? P.lif.V0_sd : P.aeif.V0_sd;
+      double V0 = mean;
+      if (sd != 0.0) {
+        uint32_t r[4];
+        draw(seed, (uint64_t)(P.local_off + k), kVinit, 0, 0, r);
+        V0 = mean + sd * normal_from(r);
+      }
+      if (P.model == 0) {
+        net->s0[(size_t)i] = (double)(float)(V0 - P.lif.E_L);
+      } else {
+        const bool f64 = P.aeif.fp64 != 0;
+        net->s0[(size_t)i] = f64 ? V0 : (double)(float)V0;
+        net->s1[(size_t)i] = f64 ? P.aeif.w0 : (double)(float)P.aeif.w0;
+        net->s4[(size_t)i] = P.aeif.h_init;
+      }
+    }
+  }
+  const size_t ring_sz = (size_t)(net->L * net->R * N);
+  if (net->deterministic) net->ring_fx.assign(ring_sz, 0);
+  else net->ring.assign(ring_sz, 0.0f);
+  if (net->track_abs) {
+    net->ring_abs.assign(ring_sz, 0.0);
+    net->ring_exact.assign(ring_sz, 0.0);
+  }
+  net->finalized = true;
+  return 0;
+}
+
+int32_t ora_simulate(ora_net* net, int64_t steps) {
+  if (!net) return fail("ora_simulate: null");
+  if (!net->finalized) {
+    const int32_t rc = ora_finalize(net);
+    if (rc < 0) return rc;
+  }
+  const Tableau tab = cash_karp();
+  const int64_t N = net->N;
+  std::vector<int64_t> fired;
+  std::vector<int> mult;
+  for (int64_t s = 0; s < steps; ++s) {
+    const int64_t t = net->t;
+    fired.clear();
+    mult.clear();
+    // --- update of every neuron with the input of step t (Eqs. 1-5)
+    for (size_t pi = 0; pi < net->pops.size(); ++pi) {
+      const Population& P = net->pops[pi];
+      const uint64_t seed = net->inst[P.instance].seed;
+      for (int64_t k = 0; k < P.n; ++k) {
+        const int64_t i = P.offset + k;
+        float in[2] = {0.0f, 0.0f};
+        for (int r = 0; r < net->R; ++r) {
+          const int64_t idx = ring_index(net, t, r, i);
+          if (net->deterministic) {
+            in[r] = fx_to_float(net->ring_fx[(size_t)idx]);
+            net->ring_fx[(size_t)idx] = 0;
+          } else {
+            in[r] = net->ring[(size_t)idx];
+            net->ring[(size_t)idx] = 0.0f;
+          }
+          if (net->track_abs) {
+            net->ring_abs[(size_t)idx] = 0.0;
+            net->ring_exact[(size_t)idx] = 0.0;
+          }
+        }
+        // Poisson drive of step t: k ~ Poisson(lambda), adds k * w_ext
+        if (P.lambda > 0.0) {
+          uint32_t r[4];
+          draw(seed, (uint64_t)t, kPoisson, 0, (uint32_t)(P.local_off + k), r);
+          const int kp = poisson_inversion(P.lambda, r[0]);
+          const int rc = P.model == 0 ? 0 : P.aeif.prec_rcpt;
+          const float add = (float)kp * P.w_ext;
+          in[rc] = in[rc] + add;
+        }
+        int nspk = 0;
+        if (P.model == 0) {
+          float y = (float)net->s0[(size_t)i];
+          float I = (float)net->s1[(size_t)i];
+          int ref = (int)net->s2[(size_t)i];
+          if (ref > 0) {
+            ref -= 1;  // absolute refractory: V is held at V_reset
+          } else {
+            y = P.P22 * y + P.P21 * I + P.P20Ie;  // propagate V with the current of the previous grid point
+          }
+          I = P.P11 * I + in[0];                  // input of step t enters after the V propagation
+          if (y >= P.theta) {
+            y = P.y_reset;
+            ref = P.ref_steps;
+            nspk = 1;
+          }
+          net->s0[(size_t)i] = y;
+          net->s1[(size_t)i] = I;
+          net->s2[(size_t)i] = ref;
+        } else {
+          const AeifPar& q = P.aeif;
+          double h = net->s4[(size_t)i];
+          if (q.fp64) {
+            AdexSystem<double> sys{q.g_L, q.E_L, q.V_T, q.Delta_T, 1.0 / q.Delta_T, q.a, 1.0 / q.tau_w,
+                                   q.V_peak, q.E_ex, q.E_in, 1.0 / q.tau_ex, 1.0 / q.tau_in, q.I_e,
+                                   1.0 / q.C_m};
+            double y[4] = {net->s0[(size_t)i], net->s1[(size_t)i], net->s2[(size_t)i], net->s3[(size_t)i]};
+            nspk = adex_advance<double>(sys, tab, q, net->dt, q.tol, y, h, net->rk_substeps, net->rk_cap_hits);
+            y[2] += (double)in[0];
+            y[3] += (double)in[1];
+            net->s0[(size_t)i] = y[0]; net->s1[(size_t)i] = y[1];
+            net->s2[(size_t)i] = y[2]; net->s3[(size_t)i] = y[3];
+          } else {
+            AdexSystem<float> sys{(float)q.g_L, (float)q.E_L, (float)q.V_T, (float)q.Delta_T,
+                                  (float)(1.0 / q.Delta_T), (float)q.a, (float)(1.0 / q.tau_w),
+                                  (float)q.V_peak, (float)q.E_ex, (float)q.E_in, (float)(1.0 / q.tau_ex),
+                                  (float)(1.0 / q.tau_in), (float)q.I_e, (float)(1.0 / q.C_m)};
+            float y[4] = {(float)net->s0[(size_t)i], (float)net->s1[(size_t)i], (float)net->s2[(size_t)i],
+                          (float)net->s3[(size_t)i]};
+            const double tol_eff = std::max(q.tol, 8.0 * 0x1p-24);
+            nspk = adex_advance<float>(sys, tab, q, net->dt, tol_eff, y, h, net->rk_substeps, net->rk_cap_hits);
+            y[2] = y[2] + in[0];
+            y[3] = y[3] + in[1];
+            net->s0[(size_t)i] = y[0]; net->s1[(size_t)i] = y[1];
+            net->s2[(size_t)i] = y[2]; net->s3[(size_t)i] = y[3];
+            h = (double)(float)h;  // the step-size proposal is carried in FP32 between steps
+          }
+          net->s4[(size_t)i] = h;
+        }
+        if (nspk > 0) {
+          fired.push_back(i);
+          mult.push_back(nspk);
+        }
+      }
+    }
+    // --- delivery of the spikes of step t to the inputs of step t + delay (Sec. 2.2)
+    for (size_t f = 0; f < fired.size(); ++f) {
+      const int64_t src = fired[f];
+      for (int m = 0; m < mult[f]; ++m) {
+        net->spk_id.push_back(src);
+        net->spk_step.push_back(t);
+        for (uint64_t j = net->src_ptr[(size_t)src]; j < net->src_ptr[(size_t)src + 1]; ++j) {
+          const int64_t idx = ring_index(net, t + net->delay[j], net->rcpt[j], net->tgt[j]);
+          if (net->deterministic)
+            net->ring_fx[(size_t)idx] += (int64_t)std::llrint((double)net->w[j] * kFixScale);
+          else
+            net->ring[(size_t)idx] = net->ring[(size_t)idx] + net->w[j];
+          if (net->track_abs) {
+            net->ring_abs[(size_t)idx] += std::fabs((double)net->w[j]);
+            net->ring_exact[(size_t)idx] += (double)net->w[j];
+          }
+        }
+        net->events += (int64_t)(net->src_ptr[(size_t)src + 1] - net->src_ptr[(size_t)src]);
+      }
+    }
+    net->t += 1;
+  }
+  (void)N;
+  return 0;
+}
+
+int32_t ora_inject(ora_net* net, int64_t neuron, int32_t receptor, int64_t step_offset, double value) {
+  if (!net || !net->finalized) return fail("ora_inject: finalize first");
+  if (neuron < 0 || neuron >= net->N || receptor < 0 || receptor >= net->R || step_offset < 0 ||
+      step_offset >= net->L)
+    return fail("ora_inject: range");
+  const int64_t idx = ring_index(net, net->t + step_offset, receptor, neuron);
+  if (net->deterministic) net->ring_fx[(size_t)idx] += (int64_t)std::llrint(value * kFixScale);
+  else net->ring[(size_t)idx] = net->ring[(size_t)idx] + (float)value;
+  if (net->track_abs) {
+    net->ring_abs[(size_t)idx] += std::fabs(value);
+    net->ring_exact[(size_t)idx] += value;
+  }
+  return 0;
+}
+
+int64_t ora_num_neurons(const ora_net* net) { return net ? net->N : -1; }
+int64_t ora_pop_offset(const ora_net* net, int32_t pop) {
+  if (!net || pop < 0 || pop >= (int32_t)net->pops.size()) return -1;
+  return net->pops[pop].offset;
+}
+int64_t ora_num_synapses(const ora_net* net) { return net ? (int64_t)net->tgt.size() : -1; }
+int64_t ora_ring_length(const ora_net* net) { return net ? net->L : -1; }
+int64_t ora_steps_done(const ora_net* net) { return net ? net->t : -1; }
+int64_t ora_events(const ora_net* net) { return net ? net->events : -1; }
+int64_t ora_num_spikes(const ora_net* net) { return net ? (int64_t)net->spk_id.size() : -1; }
+int64_t ora_rk_substeps(const ora_net* net) { return net ? net->rk_substeps : -1; }
+int64_t ora_rk_cap_hits(const ora_net* net) { return net ? net->rk_cap_hits : -1; }
+
+int32_t ora_get_csr(const ora_net* net, uint64_t* src_ptr, uint32_t* tgt, uint8_t* receptor, float* weight,
+                    uint16_t* delay) {
+  if (!net || !net->finalized) return fail("ora_get_csr: finalize first");
+  const size_t K = net->tgt.size();
+  if (src_ptr) std::memcpy(src_ptr, net->src_ptr.data(), net->src_ptr.size() * sizeof(uint64_t));
+  if (tgt) std::memcpy(tgt, net->tgt.data(), K * sizeof(uint32_t));
+  if (receptor) std::memcpy(receptor, net->rcpt.data(), K);
+  if (weight) std::memcpy(weight, net->w.data(), K * sizeof(float));
+  if (delay) std::memcpy(delay, net->delay.data(), K * sizeof(uint16_t));
+  return 0;
+}
+
+int32_t ora_get_state(const ora_net* net, int32_t var, double* out) {
+  if (!net || !net->finalized) return fail("ora_get_state: finalize first");
+  for (int64_t i = 0; i < net->N; ++i) {
+    const Population& P = net->pops[(size_t)net->pop_of[(size_t)i]];
+    double v = 0.0;
+    if (P.model == 0) {
+      if (var == 0) v = net->s0[(size_t)i] + P.lif.E_L;
+      else if (var == 1) v = net->s1[(size_t)i];
+      else if (var == 4) v = net->s2[(size_t)i];
+    } else {
+      if (var == 0) v = net->s0[(size_t)i];
+      else if (var == 1) v = net->s1[(size_t)i];
+      else if (var == 2) v = net->s2[(size_t)i];
+      else if (var == 3) v = net->s3[(size_t)i];
+      else if (var == 5) v = net->s4[(size_t)i];
+    }
+    out[i] = v;
+  }
+  return 0;
+}
+
+int32_t ora_get_input(const ora_net* net, int32_t receptor, int64_t step_offset, float* out, double* abs_out,
+                      double* exact_out) {
+  if (!net || !net->finalized) return fail("ora_get_input: finalize first");
+  if (receptor < 0 || receptor >= net->R || step_offset < 0 || step_offset >= net->L)
+    return fail("ora_get_input: range");
+  for (int64_t i = 0; i < net->N; ++i) {
+    const int64_t idx = ring_index(net, net->t + step_offset, receptor, i);
+    if (out) out[i] = net->deterministic ? fx_to_float(net->ring_fx[(size_t)idx]) : net->ring[(size_t)idx];
+    if (abs_out) abs_out[i] = net->track_abs ? net->ring_abs[(size_t)idx] : 0.0;
+    if (exact_out) exact_out[i] = net->track_abs ? net->ring_exact[(size_t)idx] : 0.0;
+  }
+  return 0;
+}
+
+int32_t ora_get_spikes(const ora_net* net, int64_t* ids, int64_t* steps) {
+  if (!net) return fail("ora_get_spikes: null");
+  const size_t n = net->spk_id.size();
+  if (ids) std::memcpy(ids, net->spk_id.data(), n * sizeof(int64_t));
+  if (steps) std::memcpy(steps, net->spk_step.data(), n * sizeof(int64_t));
+  return 0;
+}
+
+void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  philox(ctr, key[0], key[1], out);
+}
+int32_t ora_poisson_inversion(double lambda, uint32_t x) { return poisson_inversion(lambda, x); }
+void ora_lif_propagators(double tau_m, double C_m, double tau_syn, double h, double out[4]) {
+  lif_propagators(tau_m, C_m, tau_syn, h, out);
+}
+void ora_cash_karp_tableau(double c[6], double a[36], double b5[6], double b4[6]) {
+  const Tableau t = cash_karp();
+  for (int i = 0; i < 6; ++i) {
+    c[i] = t.c[i];
+    b5[i] = t.b5[i];
+    b4[i] = t.b4[i];
+    for (int j = 0; j < 6; ++j) a[i * 6 + j] = t.a[i][j];
+  }
+}
+float ora_round_weight(float w, int32_t prec) { return round_weight(w, prec); }
+double ora_normal_from_words(const uint32_t w[4]) { return normal_from(w); }
+
+}  // extern "C"
