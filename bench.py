@@ -1,0 +1,364 @@
+"""Benchmark: full-scale cortical microcircuit on one GB300 (real-time factor
+and synaptic events/s), printed as one JSON line.
+
+A bench step is one second of biological time (10,000 simulation steps of
+dt = 0.1 ms) of the 8-population microcircuit (77,169 LIF neurons,
+298,880,968 synapses, Poisson background), run through the C ABI
+(ngb_simulate): per simulation step the fused LIF update (Poisson drive,
+exact integration, threshold/reset, spike compaction) and the spike delivery
+into the ring buffer, replayed from CUDA graphs.  The network is built on the
+device before the timed region.  The CSR (2.4 GB) is larger than L2 and is
+streamed per spike; the state and ring (~21 MB) stay resident by design.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (plain C++, one core) on the same
+workload: it builds the same network and simulates a bounded sample of
+simulation steps per bench step.  Under torchrun (N > 1) every rank runs an
+independent replica with its own seed (the path has no exchange step), and
+value is the sum over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "real-time factor & synaptic events/s; batched/served vs plain at stated tol"
+UNIT = "synaptic events/s"
+SIM_STEPS_PER_BENCH_STEP = 10_000  # 1 s of biological time at dt = 0.1 ms
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--weights", choices=["fp32", "bf16", "fp16"], default="fp32")
+    ap.add_argument("--sim-steps", type=int, default=SIM_STEPS_PER_BENCH_STEP,
+                    help="simulation steps per bench step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=2000,
+                    help="oracle simulation steps timed for the CPU baseline")
+    ap.add_argument("--profile-steps", type=int, default=2000)
+    ap.add_argument("--no-variant", action="store_true", help="skip the BF16-weight variant")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", gpu_index, "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, ValueError):
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.2)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _spec(weights: str, seed: int):
+    from paper_2007_14236_gb300 import workloads as W
+    return W.microcircuit(scale=1.0, seed=seed, weight_dtype=weights)
+
+
+def _cpu_info():
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    import platform
+    return "%s %s" % (platform.machine(), model)
+
+
+def cpu_baseline(weights: str, sample_steps: int, seed: int = 1):
+    """The oracle (one core) on the full-scale microcircuit: build (untimed), a
+    short untimed warm-up past the onset transient, then `sample_steps` timed
+    simulation steps; events/s of that sample."""
+    import oracle
+    spec = _spec(weights, seed)
+    t0 = time.perf_counter()
+    net = oracle.OracleNet(spec)
+    net.finalize()
+    build_s = time.perf_counter() - t0
+    net.simulate(500)
+    e0 = net.events
+    t1 = time.perf_counter()
+    net.simulate(sample_steps)
+    dt_s = time.perf_counter() - t1
+    ev = net.events - e0
+    bio_s = sample_steps * spec.dt * 1e-3
+    return {"value": ev / dt_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "full-scale microcircuit, %d simulation steps (%.0f ms biological) after a 500-step "
+                      "warm-up; single-threaded C++ oracle on %s; build %.1f s untimed"
+                      % (sample_steps, bio_s * 1e3, _cpu_info(), build_s),
+            "real_time_factor": dt_s / bio_s}
+
+
+def run_reference(a):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    spec = _spec(a.weights, 1)
+    net = oracle.OracleNet(spec)
+    net.finalize()
+    per_step = 100  # simulation steps (10 ms biological) per bench step
+    net.simulate(500)
+    for _ in range(a.warmup):
+        net.simulate(per_step)
+    e0 = net.events
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        net.simulate(per_step)
+    wall = time.perf_counter() - t0
+    ev = net.events - e0
+    bio_s = a.steps * per_step * spec.dt * 1e-3
+    value = ev / wall
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": wall * 1e3 / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "potjans_diesmann_microcircuit_full_scale", "neurons": 77169,
+                       "synapses": 298880968, "dt_ms": 0.1, "bio_ms_per_step": per_step * 0.1,
+                       "weights": a.weights},
+            "real_time_factor": wall / bio_s,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "full-scale microcircuit, %d x %d simulation steps after a 500-step "
+                                       "warm-up, single-threaded C++ oracle on %s"
+                                       % (a.steps, per_step, _cpu_info())},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    ws, rank, local = _dist()
+    import numpy as np
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+
+    from paper_2007_14236_gb300 import ngb
+    ngb.load()
+    stream = torch.cuda.Stream()
+    spec = _spec(a.weights, 1 + rank)
+    t0 = time.perf_counter()
+    sim = ngb.from_spec(spec, device=local, stream=stream.cuda_stream, steps_per_graph=100, drain_steps=10_000,
+                        record_capacity=4_000_000)
+    sim.finalize()
+    build_s = time.perf_counter() - t0
+    st0 = sim.stats()
+
+    for _ in range(a.warmup):
+        sim.simulate(a.sim_steps)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------------------------------------------------------- timed region (device clock)
+    gpu_idx = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if ws > 1 else 0]
+    barrier()
+    sampler = ClockSampler(gpu_idx)
+    ev_before = sim.stats()["events"]
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
+    e_start.record(stream)
+    for _ in range(a.steps):
+        sim.simulate(a.sim_steps)
+    e_end.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = e_start.elapsed_time(e_end)
+    events = sim.stats()["events"] - ev_before
+    if pg is not None:
+        t = torch.tensor([ms, float(events)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+        pg.all_reduce(t, op=pg.ReduceOp.SUM)
+        ms, events = float(tmax[0]), float(t[1])
+    bio_s_rank = a.steps * a.sim_steps * spec.dt * 1e-3
+    value = events / (ms * 1e-3)
+    rtf = (ms * 1e-3) / bio_s_rank
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    barrier()
+    ev_b = sim.stats()["events"]
+    t_now = sim.stats()["steps"]
+    d2h = 0
+    h0 = time.perf_counter()
+    for _ in range(a.steps):
+        sim.simulate(a.sim_steps)
+        ids, stp = sim.spikes(t0=t_now, t1=t_now + a.sim_steps)  # spike record read back into host buffers
+        d2h += ids.size * (4 + 8)
+        t_now += a.sim_steps
+    barrier()
+    e2e_s = time.perf_counter() - h0
+    e2e_events = sim.stats()["events"] - ev_b
+    if pg is not None:
+        t = torch.tensor([e2e_s, float(e2e_events)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+        pg.all_reduce(t, op=pg.ReduceOp.SUM)
+        e2e_s, e2e_events = float(tmax[0]), float(t[1])
+
+    # ---------------------------------------------------------------- per-kernel times (CUDA events)
+    ev_p0 = sim.stats()["events"]
+    kms, nlaunch = sim.simulate_profiled(a.profile_steps)
+    ev_p = sim.stats()["events"] - ev_p0
+    N = st0["num_neurons"]
+    lif_bytes = N * 32  # y, I, refractory read+write (24 B) + ring slot read and zero (8 B)
+    wbytes = 4 if a.weights == "fp32" else 2
+    spikes_per_step = None
+    ev_per_launch = ev_p / max(1, nlaunch[2])
+    deliver_bytes = ev_per_launch * (4 + wbytes + 4)
+    kern = {
+        "k_update_lif": {"launches": int(nlaunch[0]), "ms_total": float(kms[0]),
+                         "us_per_launch": 1e3 * float(kms[0]) / max(1, nlaunch[0]),
+                         "algorithmic_bytes_per_launch": lif_bytes},
+        "k_deliver": {"launches": int(nlaunch[2]), "ms_total": float(kms[2]),
+                      "us_per_launch": 1e3 * float(kms[2]) / max(1, nlaunch[2]),
+                      "algorithmic_bytes_per_launch": deliver_bytes,
+                      "events_per_launch": ev_per_launch},
+    }
+    dom = max(kern, key=lambda k: kern[k]["ms_total"])
+    peak, peak_kind = _peaks()
+    ach = kern[dom]["algorithmic_bytes_per_launch"] / (kern[dom]["us_per_launch"] * 1e-6) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_source": peak_kind, "traffic": None}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded Philox network and Poisson drive)",
+        "config": {"workload": "potjans_diesmann_microcircuit_full_scale", "neurons": N,
+                   "synapses": st0["num_synapses"], "dt_ms": spec.dt, "bio_s_per_step": a.sim_steps * spec.dt * 1e-3,
+                   "weights": a.weights, "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "CSR (%.1f GB) larger than L2 and streamed per spike; state and ring stay resident"
+                         % (st0["num_synapses"] * (4 + wbytes) / 1e9)},
+        "real_time_factor": rtf,
+        "build_s": build_s,
+        "gpu_launches": int(a.steps * a.sim_steps * 2),
+        "e2e": {"value": e2e_events / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": int(d2h / a.steps), "real_time_factor": e2e_s / bio_s_rank},
+        "roofline": roofline,
+        "kernels": kern,
+        "clocks": clocks,
+    }
+    sim.close()
+    torch.cuda.synchronize()
+
+    if rank == 0 and ws == 1 and not a.no_variant and a.weights == "fp32":
+        v = ngb.from_spec(_spec("bf16", 1), device=local, stream=stream.cuda_stream, steps_per_graph=100,
+                          drain_steps=10_000, record_capacity=4_000_000)
+        v.finalize()
+        v.simulate(a.sim_steps)
+        e0 = v.stats()["events"]
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(max(1, a.steps // 2)):
+            v.simulate(a.sim_steps)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        vms = s0.elapsed_time(s1)
+        vb = max(1, a.steps // 2) * a.sim_steps * spec.dt * 1e-3
+        line["variants"] = {"bf16_weights": {"value": (v.stats()["events"] - e0) / (vms * 1e-3),
+                                             "real_time_factor": vms * 1e-3 / vb}}
+        v.close()
+
+    if rank == 0 and ws == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a.weights, a.cpu_sample_steps)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -34,6 +34,12 @@
 
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define NGB_API __attribute__((visibility("default")))
+#else
+#define NGB_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -155,13 +161,13 @@ typedef struct ngb_sim ngb_sim;
 
 /* ------------------------------------------------------------ lifecycle */
 /* Create an empty simulation on cfg->device.  *out receives the handle. */
-int ngb_create(ngb_sim** out, const ngb_sim_config* cfg);
+NGB_API int ngb_create(ngb_sim** out, const ngb_sim_config* cfg);
 
 /* Free every resource of the handle; NULL is a no-op. */
-int ngb_destroy(ngb_sim* sim);
+NGB_API int ngb_destroy(ngb_sim* sim);
 
 /* Message of the last failed call on this thread ("" if none).  `sim` may be NULL. */
-const char* ngb_last_error(const ngb_sim* sim);
+NGB_API const char* ngb_last_error(const ngb_sim* sim);
 
 /* -------------------------------------------------------- construction */
 /* Add a network instance with its own random key (batched execution: several
@@ -169,65 +175,65 @@ const char* ngb_last_error(const ngb_sim* sim);
  * ngb_create with cfg->seed).  Random streams use instance-local neuron ids
  * and connect-call indices, so an instance's result does not depend on what
  * else is batched with it.  NGB_ERR_STATE after the first simulate. */
-int ngb_add_instance(ngb_sim* sim, uint64_t seed, int32_t* instance_out);
+NGB_API int ngb_add_instance(ngb_sim* sim, uint64_t seed, int32_t* instance_out);
 
 /* Add n neurons of `model` (params: ngb_lif_params* or ngb_aeif_params*) to
  * instance 0.  Population ids count from 0 over the whole handle. */
-int ngb_add_population(ngb_sim* sim, int32_t model, int64_t n, const void* params, int32_t* pop_id_out);
+NGB_API int ngb_add_population(ngb_sim* sim, int32_t model, int64_t n, const void* params, int32_t* pop_id_out);
 
 /* As ngb_add_population, into the given instance. */
-int ngb_add_population_in(ngb_sim* sim, int32_t instance, int32_t model, int64_t n, const void* params,
+NGB_API int ngb_add_population_in(ngb_sim* sim, int32_t instance, int32_t model, int64_t n, const void* params,
                           int32_t* pop_id_out);
 
 /* Connect src_pop -> tgt_pop (same instance) with rule `conn` and synapse
  * parameters `syn` (Sec. 2.1).  Synapses are drawn on the device when the
  * network is finalised (first ngb_simulate or ngb_finalize). */
-int ngb_connect(ngb_sim* sim, int32_t src_pop, int32_t tgt_pop, const ngb_conn_spec* conn,
+NGB_API int ngb_connect(ngb_sim* sim, int32_t src_pop, int32_t tgt_pop, const ngb_conn_spec* conn,
                 const ngb_syn_spec* syn);
 
 /* Build the delay-grouped CSR on the device (Sec. 2.2 connection groups),
  * allocate state, ring buffer and spike lists, and capture the step graph.
  * Called implicitly by the first ngb_simulate. */
-int ngb_finalize(ngb_sim* sim);
+NGB_API int ngb_finalize(ngb_sim* sim);
 
 /* ----------------------------------------------------------- simulation */
 /* Advance every instance by `steps` steps; returns when done (blocking). */
-int ngb_simulate(ngb_sim* sim, int64_t steps);
+NGB_API int ngb_simulate(ngb_sim* sim, int64_t steps);
 
 /* As ngb_simulate, without CUDA graphs, with CUDA events around every kernel
  * launch.  kernel_ms[3] receives the summed device time of the LIF update,
  * AdEx update and delivery kernels; launches[3] their launch counts. */
-int ngb_simulate_profiled(ngb_sim* sim, int64_t steps, double* kernel_ms, int64_t* launches);
+NGB_API int ngb_simulate_profiled(ngb_sim* sim, int64_t steps, double* kernel_ms, int64_t* launches);
 
 /* Spikes recorded in steps [t0_step, t1_step) of population `pop` (-1 = all,
  * then ids are global; else population-local), sorted by (step, id).  With
  * ids == NULL only *n_out is set.  Otherwise up to `capacity` entries are
  * written and *n_out is the number available. */
-int ngb_get_spikes(ngb_sim* sim, int32_t pop, int64_t t0_step, int64_t t1_step, int32_t* ids,
+NGB_API int ngb_get_spikes(ngb_sim* sim, int32_t pop, int64_t t0_step, int64_t t1_step, int32_t* ids,
                    int64_t* steps, int64_t capacity, int64_t* n_out);
 
 /* --------------------------------------------------------- introspection */
-int ngb_get_stats(ngb_sim* sim, ngb_stats* out);
+NGB_API int ngb_get_stats(ngb_sim* sim, ngb_stats* out);
 
 /* Global id of the first neuron of `pop` and its size. */
-int ngb_population_range(ngb_sim* sim, int32_t pop, int64_t* offset_out, int64_t* n_out);
+NGB_API int ngb_population_range(ngb_sim* sim, int32_t pop, int64_t* offset_out, int64_t* n_out);
 
 /* Copy state variable `var` (ngb_state_var) of neurons [first, first+n) into out[n]. */
-int ngb_get_state(ngb_sim* sim, int32_t var, int64_t first, int64_t n, float* out);
+NGB_API int ngb_get_state(ngb_sim* sim, int32_t var, int64_t first, int64_t n, float* out);
 
 /* Copy the input accumulated so far for step (current step + step_offset),
  * receptor `receptor`, neurons [first, first+n), as FP32 (offset 0 is the
  * complete synaptic input the next update consumes; the Poisson drive is not
  * included).  0 <= step_offset < ring slots. */
-int ngb_get_input(ngb_sim* sim, int32_t receptor, int64_t step_offset, int64_t first, int64_t n, float* out);
+NGB_API int ngb_get_input(ngb_sim* sim, int32_t receptor, int64_t step_offset, int64_t first, int64_t n, float* out);
 
 /* Number of synapses of sources [0, N) before each source: src_ptr[N+1]. */
-int ngb_get_src_ptr(ngb_sim* sim, uint64_t* src_ptr);
+NGB_API int ngb_get_src_ptr(ngb_sim* sim, uint64_t* src_ptr);
 
 /* Synapses [first, first+n) of the CSR in storage order (source, delay,
  * connect call, draw index): global target id, receptor, weight widened to
  * FP32, delay in steps. Any output pointer may be NULL. */
-int ngb_get_synapses(ngb_sim* sim, int64_t first, int64_t n, uint32_t* tgt, uint8_t* receptor, float* weight,
+NGB_API int ngb_get_synapses(ngb_sim* sim, int64_t first, int64_t n, uint32_t* tgt, uint8_t* receptor, float* weight,
                      uint16_t* delay);
 
 #ifdef __cplusplus

@@ -48,6 +48,8 @@ def lib():
     L.ora_get_state.argtypes = [P, C.c_int32, P]
     L.ora_get_input.argtypes = [P, C.c_int32, C.c_int64, P, P, P]
     L.ora_get_spikes.argtypes = [P, P, P]
+    L.ora_rows_for_sources.restype = C.c_int64
+    L.ora_rows_for_sources.argtypes = [P, C.c_int64, P, C.c_int64, P, P, P, P, P]
     L.ora_philox4x32_10.argtypes = [P, P, P]
     L.ora_poisson_inversion.restype = C.c_int32
     L.ora_poisson_inversion.argtypes = [C.c_double, C.c_uint32]
@@ -215,6 +217,18 @@ class OracleNet:
         ex = np.zeros(self.N, dtype=np.float64)
         _check(lib().ora_get_input(self.h, receptor, step_offset, _ptr(out), _ptr(ab), _ptr(ex)))
         return out, ab, ex
+
+    def rows_for_sources(self, srcs):
+        """Canonical CSR rows of the given global sources, drawn one by one."""
+        srcs = np.ascontiguousarray(np.asarray(srcs, dtype=np.int64))
+        n = int(lib().ora_rows_for_sources(self.h, len(srcs), _ptr(srcs), 0, None, None, None, None, None))
+        _check(n)
+        out = dict(src=np.zeros(n, dtype=np.uint32), tgt=np.zeros(n, dtype=np.uint32),
+                   receptor=np.zeros(n, dtype=np.uint8), weight=np.zeros(n, dtype=np.float32),
+                   delay=np.zeros(n, dtype=np.uint16))
+        lib().ora_rows_for_sources(self.h, len(srcs), _ptr(srcs), n, _ptr(out["src"]), _ptr(out["tgt"]),
+                                   _ptr(out["receptor"]), _ptr(out["weight"]), _ptr(out["delay"]))
+        return out
 
     def spikes(self):
         n = int(lib().ora_num_spikes(self.h))

@@ -267,6 +267,7 @@ struct ora_net {
 namespace {
 
 const double kFixScale = 4294967296.0;  // 2^32: fixed-point ring of the deterministic mode
+const uint32_t kMaxAttempts = 10000;    // cap of every re-draw loop
 
 uint16_t delay_steps(double d_ms, double dt) {
   double s = std::nearbyint(d_ms / dt);  // round half to even
@@ -281,6 +282,7 @@ double draw_weight(const ora_net* net, const Call& c, uint64_t seed, uint64_t q)
   (void)net;
   if (c.wdist == 0) return c.w0;
   for (uint32_t attempt = 0;; ++attempt) {
+    if (attempt == kMaxAttempts) return c.w0;  // re-draws exhausted: the mean
     uint32_t r[4];
     draw(seed, q, kWeight, attempt, c.stream, r);
     if (c.wdist == 1) {
@@ -297,6 +299,7 @@ double draw_weight(const ora_net* net, const Call& c, uint64_t seed, uint64_t q)
 double draw_delay(const ora_net* net, const Call& c, uint64_t seed, uint64_t q) {
   if (c.ddist == 0) return c.d0;
   for (uint32_t attempt = 0;; ++attempt) {
+    if (attempt == kMaxAttempts) return std::max(c.d0, net->dt);  // re-draws exhausted
     uint32_t r[4];
     draw(seed, q, kDelay, attempt, c.stream, r);
     if (c.ddist == 1) {
@@ -308,35 +311,43 @@ double draw_delay(const ora_net* net, const Call& c, uint64_t seed, uint64_t q) 
   }
 }
 
-void generate(const ora_net* net, const Call& c, std::vector<Synapse>& out) {
+// Synapse of draw index q of connect call c (Sec. 2.1 connection rules).
+Synapse draw_synapse(const ora_net* net, const Call& c, uint64_t q) {
   const Population& ps = net->pops[c.src_pop];
   const Population& pt = net->pops[c.tgt_pop];
   const uint64_t seed = net->inst[ps.instance].seed;
   const bool same = (c.src_pop == c.tgt_pop);
-  const uint64_t nsyn = (c.rule == 0) ? (uint64_t)c.K * (uint64_t)pt.n : (uint64_t)c.K;
-  for (uint64_t q = 0; q < nsyn; ++q) {
-    uint32_t src = 0, tgt = 0;
-    for (uint32_t attempt = 0;; ++attempt) {
-      uint32_t r[4];
-      draw(seed, q, kSrc, attempt, c.stream, r);
-      if (c.rule == 0) {
-        tgt = (uint32_t)(q / (uint64_t)c.K);
-        src = uniform_index(r[0], (uint32_t)ps.n);
-      } else {
-        src = uniform_index(r[0], (uint32_t)ps.n);
-        tgt = uniform_index(r[1], (uint32_t)pt.n);
-      }
-      if (same && !c.autapses && src == tgt) continue;
-      break;
+  uint32_t src = 0, tgt = 0;
+  for (uint32_t attempt = 0;; ++attempt) {
+    uint32_t r[4];
+    draw(seed, q, kSrc, attempt, c.stream, r);
+    if (attempt == kMaxAttempts) break;  // keep the last draw (needs a population of one)
+    if (c.rule == 0) {
+      tgt = (uint32_t)(q / (uint64_t)c.K);
+      src = uniform_index(r[0], (uint32_t)ps.n);
+    } else {
+      src = uniform_index(r[0], (uint32_t)ps.n);
+      tgt = uniform_index(r[1], (uint32_t)pt.n);
     }
-    Synapse s;
-    s.src = (uint32_t)(ps.offset + src);
-    s.tgt = (uint32_t)(pt.offset + tgt);
-    s.w = round_weight((float)draw_weight(net, c, seed, q), net->prec);
-    s.delay = delay_steps(draw_delay(net, c, seed, q), net->dt);
-    s.receptor = (uint8_t)c.receptor;
-    out.push_back(s);
+    if (same && !c.autapses && src == tgt) continue;
+    break;
   }
+  Synapse s;
+  s.src = (uint32_t)(ps.offset + src);
+  s.tgt = (uint32_t)(pt.offset + tgt);
+  s.w = round_weight((float)draw_weight(net, c, seed, q), net->prec);
+  s.delay = delay_steps(draw_delay(net, c, seed, q), net->dt);
+  s.receptor = (uint8_t)c.receptor;
+  return s;
+}
+
+uint64_t call_size(const ora_net* net, const Call& c) {
+  return (c.rule == 0) ? (uint64_t)c.K * (uint64_t)net->pops[c.tgt_pop].n : (uint64_t)c.K;
+}
+
+void generate(const ora_net* net, const Call& c, std::vector<Synapse>& out) {
+  const uint64_t nsyn = call_size(net, c);
+  for (uint64_t q = 0; q < nsyn; ++q) out.push_back(draw_synapse(net, c, q));
 }
 
 // One embedded Cash-Karp step of the AdEx system (Eqs. 3-5 with the
@@ -825,6 +836,45 @@ int32_t ora_get_spikes(const ora_net* net, int64_t* ids, int64_t* steps) {
   if (ids) std::memcpy(ids, net->spk_id.data(), n * sizeof(int64_t));
   if (steps) std::memcpy(steps, net->spk_step.data(), n * sizeof(int64_t));
   return 0;
+}
+
+int64_t ora_rows_for_sources(const ora_net* net, int64_t n_src, const int64_t* srcs, int64_t cap,
+                             uint32_t* src_out, uint32_t* tgt, uint8_t* receptor, float* weight, uint16_t* delay) {
+  if (!net) return fail("ora_rows_for_sources: null");
+  std::vector<int64_t> want(srcs, srcs + n_src);
+  std::sort(want.begin(), want.end());
+  std::vector<Synapse> rows;
+  for (const Call& c : net->calls) {
+    const Population& ps = net->pops[c.src_pop];
+    const auto lo = std::lower_bound(want.begin(), want.end(), ps.offset);
+    const auto hi = std::lower_bound(want.begin(), want.end(), ps.offset + ps.n);
+    if (lo == hi) continue;
+    const uint64_t nsyn = call_size(net, c);
+    const uint64_t seed = net->inst[ps.instance].seed;
+    for (uint64_t q = 0; q < nsyn; ++q) {
+      // cheap pre-test on the first source draw; the full draw decides
+      uint32_t r[4];
+      draw(seed, q, kSrc, 0, c.stream, r);
+      const int64_t s0 = ps.offset + uniform_index(r[0], (uint32_t)ps.n);
+      const bool maybe = std::binary_search(lo, hi, s0) || (c.src_pop == c.tgt_pop && !c.autapses);
+      if (!maybe) continue;
+      const Synapse syn = draw_synapse(net, c, q);
+      if (std::binary_search(lo, hi, (int64_t)syn.src)) rows.push_back(syn);
+    }
+  }
+  std::stable_sort(rows.begin(), rows.end(), [](const Synapse& a, const Synapse& b) {
+    if (a.src != b.src) return a.src < b.src;
+    return a.delay < b.delay;
+  });
+  const int64_t n = (int64_t)rows.size();
+  for (int64_t i = 0; i < n && i < cap; ++i) {
+    if (src_out) src_out[i] = rows[(size_t)i].src;
+    if (tgt) tgt[i] = rows[(size_t)i].tgt;
+    if (receptor) receptor[i] = rows[(size_t)i].receptor;
+    if (weight) weight[i] = rows[(size_t)i].w;
+    if (delay) delay[i] = rows[(size_t)i].delay;
+  }
+  return n;
 }
 
 void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {

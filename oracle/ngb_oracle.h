@@ -76,6 +76,13 @@ int32_t ora_get_spikes(const ora_net* net, int64_t* ids, int64_t* steps);
 int64_t ora_rk_substeps(const ora_net* net);
 int64_t ora_rk_cap_hits(const ora_net* net);
 
+/* Synapses of the given global source ids in canonical order (source, delay,
+ * call, draw index), computed draw by draw without building the network (the
+ * network need not be finalised).  Returns the number of synapses; at most cap
+ * are written. */
+int64_t ora_rows_for_sources(const ora_net* net, int64_t n_src, const int64_t* srcs, int64_t cap,
+                             uint32_t* src_out, uint32_t* tgt, uint8_t* receptor, float* weight, uint16_t* delay);
+
 /* Building blocks exposed for the pins. */
 void ora_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 int32_t ora_poisson_inversion(double lambda, uint32_t x);

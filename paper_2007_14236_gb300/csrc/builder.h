@@ -1,0 +1,58 @@
+// builder.h -- host interface of the device connection builder (builder.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace ngb {
+
+// One connect call, as the draw kernel sees it.
+struct CallDev {
+  uint64_t seed;       // instance key
+  uint64_t nsyn;       // draws: K * n_tgt (fixed indegree) or K (fixed total)
+  int64_t K;
+  double w0, w1, d0, d1, dt;
+  uint32_t stream;     // connect-call index within the instance
+  int32_t rule;        // 0 fixed indegree, 1 fixed total number
+  int32_t no_autapse;  // source == target population and autapses excluded
+  int32_t wdist, ddist, receptor, prec;
+  uint32_t n_src, n_tgt;
+  uint32_t src_off, tgt_off;  // global id of the first source / target neuron
+};
+
+// Device scratch sized for the largest source population.
+struct BuildScratch {
+  unsigned long long* keys = nullptr;
+  unsigned long long* keys_alt = nullptr;
+  uint32_t* vals = nullptr;
+  uint32_t* vals_alt = nullptr;
+  uint32_t* st_tgt = nullptr;
+  float* st_w = nullptr;
+  uint32_t* flag = nullptr;
+  uint32_t* gidx = nullptr;
+  void* sort_tmp = nullptr;
+  size_t sort_bytes = 0;
+  void* scan_tmp = nullptr;
+  size_t scan_bytes = 0;
+};
+
+cudaError_t sort_scratch_bytes(uint64_t n, int key_bits, size_t* sort_bytes, size_t* scan_bytes);
+cudaError_t scan_scratch_bytes_u64(uint64_t n, size_t* bytes);
+
+// Draw, sort and gather every synapse whose source is in one population; the
+// CSR slice starts at tgt_out / w_out (already offset).  Returns the
+// population's group starts (global synapse index) and delays in new device
+// arrays owned by the caller.
+cudaError_t build_source_population(const std::vector<CallDev>& calls, uint64_t n_total, int src_bits,
+                                    uint64_t csr_off, int wdtype, BuildScratch& s, uint32_t* tgt_out, void* w_out,
+                                    unsigned long long* src_cnt, unsigned long long* src_ngrp, int* max_delay,
+                                    uint64_t** gstart_out, uint16_t** gdelay_out, uint64_t* ngroups_out,
+                                    cudaStream_t st, std::string& err);
+
+cudaError_t exclusive_scan_u64(const unsigned long long* in, unsigned long long* out, uint64_t n, void* tmp,
+                               size_t tmp_bytes, cudaStream_t st);
+cudaError_t narrow_u64_to_u32(const unsigned long long* in, uint32_t* out, uint64_t n, cudaStream_t st);
+
+}  // namespace ngb

@@ -1,0 +1,270 @@
+"""GPU path vs the CPU oracle, through the C ABI (needs a GB300).
+
+* Connectivity (tgt, receptor, delay, row pointers) bit-exact; weights equal
+  up to one FP32 ulp where the FP64 Box-Muller draw's last bit differs between
+  CUDA's and the C library's log/cos (counted, must be rare).
+* Deterministic mode (64-bit fixed-point ring): spike trains and state
+  bit-exact for whole runs.
+* FP32 mode: per-step input currents within 1e-5 x sum|w|; spike trains
+  identical up to the first step decided by FP32 summation order, where every
+  differing neuron must sit at threshold; long-run rates within 2 % and CV ISI
+  within 0.05.
+* AdEx: FP32-state GPU integration against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2007_14236_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ngb():
+    from paper_2007_14236_gb300 import ngb as m
+    m.load()
+    return m
+
+
+def _pair(ngb, spec, deterministic=False, **kw):
+    g = ngb.from_spec(spec, deterministic=deterministic, **kw)
+    g.finalize()
+    o = oracle.OracleNet(spec, deterministic=deterministic, track_abs=True)
+    o.finalize()
+    return g, o
+
+
+def _ulp_diff(a, b):
+    ai = a.astype(np.float32).view(np.int32).astype(np.int64)
+    bi = b.astype(np.float32).view(np.int32).astype(np.int64)
+    return np.abs(ai - bi)
+
+
+def _assert_same_csr(g, o):
+    oc = o.csr()
+    assert np.array_equal(g.src_ptr(), oc["src_ptr"])
+    gs = g.synapses()
+    assert np.array_equal(gs["tgt"], oc["tgt"])
+    assert np.array_equal(gs["receptor"], oc["receptor"])
+    assert np.array_equal(gs["delay"], oc["delay"])
+    du = _ulp_diff(gs["weight"], oc["weight"])
+    assert du.max(initial=0) <= 1
+    assert np.count_nonzero(du) <= max(2, 1e-5 * len(du))
+    st = g.stats()
+    assert st["num_synapses"] == o.num_synapses
+    assert st["max_delay_steps"] == int(oc["delay"].max(initial=0))
+    return gs, oc
+
+
+SPECS = {
+    "balanced_lif_1000": lambda: W.balanced_lif(n=1000, indegree=100, seed=1),
+    "microcircuit_0.02_total": lambda: W.microcircuit(scale=0.02, seed=3, keep_indegree=False),
+    "balanced_adex_2000": lambda: W.balanced_adex(n=2000, indegree=100, seed=2, weight_dtype="fp32"),
+    "microcircuit_bf16": lambda: W.microcircuit(scale=0.02, seed=4, keep_indegree=False, weight_dtype="bf16"),
+    "microcircuit_fp16": lambda: W.microcircuit(scale=0.02, seed=5, keep_indegree=False, weight_dtype="fp16"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(SPECS))
+def test_connectivity_matches_oracle(ngb, name):
+    spec = SPECS[name]()
+    g, o = _pair(ngb, spec)
+    _assert_same_csr(g, o)
+
+
+def test_connectivity_without_autapses_and_ragged_sizes(ngb):
+    spec = W.balanced_lif(n=333, indegree=37, seed=17)
+    for c in spec.conns:
+        c.allow_autapses = False
+    spec.pops[0].n = 267  # ragged, not a multiple of any block size
+    g, o = _pair(ngb, spec)
+    gs, oc = _assert_same_csr(g, o)
+    src = np.repeat(np.arange(g.stats()["num_neurons"]), np.diff(g.src_ptr().astype(np.int64)))
+    assert not np.any(src == gs["tgt"])
+
+
+def test_deterministic_balanced_lif_bit_exact(ngb):
+    spec = W.balanced_lif(n=1000, indegree=100, seed=1)  # the 1,000-neuron network, 100 ms
+    g, o = _pair(ngb, spec, deterministic=True)
+    for chunk in (1, 9, 90, 400, 500):
+        g.simulate(chunk)
+        o.simulate(chunk)
+        assert np.array_equal(g.state("V_m"), o.state("V_m").astype(np.float32))
+        assert np.array_equal(g.state("I_syn"), o.state("I_syn").astype(np.float32))
+        assert np.array_equal(g.state("refractory"), o.state("refractory").astype(np.float32))
+        assert np.array_equal(g.input(0, 0), o.input(0, 0)[0])
+    gi, gt = g.spikes()
+    oi, ot = o.spikes()
+    assert len(oi) > 1000
+    assert np.array_equal(gt, ot) and np.array_equal(gi, oi)
+    assert g.stats()["events"] == o.events
+
+
+def test_deterministic_microcircuit_small_bit_exact(ngb):
+    spec = W.microcircuit(scale=0.03, seed=7, keep_indegree=False)
+    g, o = _pair(ngb, spec, deterministic=True)
+    g.simulate(600)
+    o.simulate(600)
+    gi, gt = g.spikes()
+    oi, ot = o.spikes()
+    assert len(oi) > 200
+    assert np.array_equal(gt, ot) and np.array_equal(gi, oi)
+    assert np.array_equal(g.state("V_m"), o.state("V_m").astype(np.float32))
+    for off in range(0, 8):
+        assert np.array_equal(g.input(0, off), o.input(0, off)[0])
+
+
+def test_deterministic_bf16_weights_bit_exact(ngb):
+    spec = W.microcircuit(scale=0.03, seed=8, keep_indegree=False, weight_dtype="bf16")
+    g, o = _pair(ngb, spec, deterministic=True)
+    g.simulate(400)
+    o.simulate(400)
+    gi, gt = g.spikes()
+    oi, ot = o.spikes()
+    assert np.array_equal(gt, ot) and np.array_equal(gi, oi)
+
+
+def test_fp32_inputs_and_spikes_until_summation_order_decides(ngb):
+    spec = W.balanced_lif(n=1000, indegree=100, seed=1)
+    g, o = _pair(ngb, spec)
+    lif = spec.pops[0].params
+    P = oracle.lif_propagators(lif.tau_m, lif.C_m, lif.tau_syn, spec.dt)
+    theta = lif.V_th - lif.E_L
+    steps_same = 0
+    for step in range(1000):
+        gin = g.input(0, 0)
+        oin, oabs, oex = o.input(0, 0)
+        # per-step input: within 1e-5 of the summed magnitudes of the contributing weights
+        assert np.all(np.abs(gin.astype(np.float64) - oex) <= 1e-5 * oabs + 1e-6), step
+        yg, Ig, rg = g.state("V_m") - lif.E_L, g.state("I_syn"), g.state("refractory")
+        g.simulate(1)
+        o.simulate(1)
+        gi, gt = g.spikes(t0=step, t1=step + 1)
+        oi, ot = o.spikes()
+        oi = oi[ot == step]
+        if not np.array_equal(np.sort(gi), np.sort(oi)):
+            # first divergence: every differing neuron crossed within rounding of threshold
+            diff = np.setxor1d(gi, oi)
+            y_pre = P["P22"] * yg.astype(np.float64) + P["P21"] * Ig.astype(np.float64) + P["P20"] * lif.I_e
+            near = np.abs(y_pre[diff] - theta)
+            assert np.all(rg[diff] == 0) and np.all(near < 1e-3), (step, diff, near)
+            break
+        steps_same += 1
+    assert steps_same >= 50
+
+
+def _rates_cv(ids, steps, n, t_lo, t_hi, dt):
+    m = (steps >= t_lo) & (steps < t_hi)
+    ids, steps = ids[m], steps[m]
+    rate = len(ids) / n / ((t_hi - t_lo) * dt * 1e-3)
+    cvs = []
+    order = np.lexsort((steps, ids))
+    ids, steps = ids[order], steps[order]
+    bounds = np.flatnonzero(np.diff(ids)) + 1
+    for a, b in zip(np.r_[0, bounds], np.r_[bounds, len(ids)]):
+        if b - a >= 4:
+            isi = np.diff(steps[a:b]).astype(np.float64)
+            cvs.append(isi.std() / isi.mean())
+    return rate, float(np.mean(cvs)) if cvs else float("nan")
+
+
+def test_fp32_long_run_rates_and_cv(ngb):
+    steps = 10_000  # 1 s
+    rg, ro, cg, co = [], [], [], []
+    for seed in (1, 2, 3):
+        spec = W.balanced_lif(n=1000, indegree=100, seed=seed)
+        g, o = _pair(ngb, spec)
+        g.simulate(steps)
+        o.simulate(steps)
+        a = _rates_cv(*g.spikes(), 1000, 1000, steps, spec.dt)
+        b = _rates_cv(*o.spikes(), 1000, 1000, steps, spec.dt)
+        rg.append(a[0]); cg.append(a[1]); ro.append(b[0]); co.append(b[1])
+    assert abs(np.mean(rg) - np.mean(ro)) <= 0.02 * np.mean(ro), (rg, ro)
+    assert abs(np.mean(cg) - np.mean(co)) <= 0.05, (cg, co)
+
+
+def _adex_single(I_e):
+    par = W.AeifParams(V_reset=-60.0, tau_ex=1.0, tau_in=1.0, I_e=I_e, rk_h_min=1e-9, rk_max_substeps=100000)
+    return W.NetSpec(name="adex1", seeds=[1], pops=[W.Population("n", W.AEIF, 1, par)])
+
+
+def test_adex_single_neuron_700pA_vs_fp64_oracle(ngb):
+    spec = _adex_single(700.0)
+    g = ngb.from_spec(spec)
+    g.finalize()
+    o = oracle.OracleNet(spec, adex_fp64=True)
+    o.finalize()
+    steps = 1500
+    Vg = np.zeros(steps)
+    Vo = np.zeros(steps)
+    for k in range(steps):
+        g.simulate(1)
+        o.simulate(1)
+        Vg[k] = g.state("V_m")[0]
+        Vo[k] = o.state("V_m")[0]
+    sg = g.spikes()[1]
+    so = o.spikes()[1]
+    assert len(so) >= 3 and len(sg) == len(so)
+    assert np.all(np.abs(sg - so) <= 1)
+    mask = np.ones(steps, dtype=bool)
+    for s in so:
+        mask[max(0, s - 20):s + 2] = False
+    assert np.abs(Vg - Vo)[mask].max() <= 5e-3
+
+
+def test_adex_network_matches_fp32_oracle_statistics(ngb):
+    spec = W.balanced_adex(n=2000, indegree=100, seed=2, weight_dtype="fp32", poisson_weight=4.0, w_ex=2.0,
+                           w_in=4.0)
+    g, o = _pair(ngb, spec)
+    g.simulate(2000)
+    o.simulate(2000)
+    ng, no = len(g.spikes()[0]), len(o.spikes()[0])
+    assert no > 200
+    assert abs(ng - no) <= 0.05 * no + 10, (ng, no)
+    # identical for the first steps, before any order-dependent rounding
+    gi, gt = g.spikes(t0=0, t1=50)
+    oi, ot = o.spikes()
+    assert np.array_equal(np.sort(gi), np.sort(oi[ot < 50]))
+    st = g.stats()
+    assert st["rk_substeps"] > 2000 * 2000
+
+
+def test_graph_and_eager_paths_identical(ngb):
+    spec = W.microcircuit(scale=0.02, seed=9, keep_indegree=False)
+    a = ngb.from_spec(spec, deterministic=True)  # default: 100-step graphs
+    b = ngb.from_spec(spec, deterministic=True, steps_per_graph=-1)
+    c = ngb.from_spec(spec, deterministic=True, steps_per_graph=7, drain_steps=50)
+    a.simulate(350)
+    b.simulate(350)
+    ms, n = c.simulate_profiled(350)
+    for x in (b, c):
+        assert np.array_equal(a.spikes()[0], x.spikes()[0])
+        assert np.array_equal(a.spikes()[1], x.spikes()[1])
+    assert n[0] == 350 and n[2] == 350 and ms[0] > 0 and ms[2] > 0
+
+
+def test_record_overflow_is_reported(ngb):
+    spec = W.balanced_lif(n=1000, indegree=100, seed=1)
+    g = ngb.from_spec(spec, record_capacity=16, drain_steps=500)
+    with pytest.raises(ngb.NgbError) as e:
+        g.simulate(1000)
+    assert e.value.code == -6
+    # the simulation itself carried on; the counters still count every spike
+    assert g.stats()["steps"] == 1000 and g.stats()["spikes"] > 16
+
+
+def test_edge_cases_empty_and_single(ngb):
+    # a population with no connections and no drive, and a one-neuron population
+    spec = W.NetSpec(name="edge", seeds=[5])
+    spec.pops = [W.Population("a", W.LIF, 1, W.LifParams(I_e=500.0)),
+                 W.Population("b", W.LIF, 70, W.LifParams())]
+    spec.conns = [W.Connection(0, 1, W.TOTAL, 0, W.Dist("const", 10.0), W.Dist("const", 1.0))]
+    g, o = _pair(ngb, spec, deterministic=True)
+    g.simulate(300)
+    o.simulate(300)
+    assert np.array_equal(g.spikes()[1], o.spikes()[1])
+    assert g.stats()["num_synapses"] == 0 and len(g.spikes()[0]) > 5
+    assert np.all(g.state("V_m")[1:] == -65.0)
+    with pytest.raises(ngb.NgbError):
+        g.connect(0, 1, W.TOTAL, 1, W.Dist("const", 1.0), W.Dist("const", 1.0))  # after finalise

@@ -205,3 +205,18 @@ def test_events_count_and_spike_order():
     assert np.array_equal(order, np.arange(len(ids)))  # (step, id) order
     outdeg = np.diff(net.csr()["src_ptr"].astype(np.int64))
     assert net.events == int(outdeg[ids].sum())
+
+
+def test_rows_for_sources_equal_the_built_csr():
+    spec = W.microcircuit(scale=0.02, seed=11, keep_indegree=False)
+    for c in spec.conns[:6]:
+        c.allow_autapses = False
+    built = _net(spec)
+    csr = built.csr()
+    lazy = oracle.OracleNet(spec)  # never finalised: rows are drawn one by one
+    srcs = [0, 5, 17, 400, int(built.N) - 1]
+    rows = lazy.rows_for_sources(srcs)
+    sp = csr["src_ptr"].astype(np.int64)
+    sel = np.concatenate([np.arange(sp[s], sp[s + 1]) for s in sorted(srcs)])
+    for k in ("tgt", "receptor", "weight", "delay"):
+        assert np.array_equal(rows[k], csr[k][sel]), k
