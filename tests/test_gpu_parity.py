@@ -261,10 +261,11 @@ def test_edge_cases_empty_and_single(ngb):
                  W.Population("b", W.LIF, 70, W.LifParams())]
     spec.conns = [W.Connection(0, 1, W.TOTAL, 0, W.Dist("const", 10.0), W.Dist("const", 1.0))]
     g, o = _pair(ngb, spec, deterministic=True)
-    g.simulate(300)
-    o.simulate(300)
+    g.simulate(1000)
+    o.simulate(1000)
     assert np.array_equal(g.spikes()[1], o.spikes()[1])
-    assert g.stats()["num_synapses"] == 0 and len(g.spikes()[0]) > 5
+    # constant 500 pA: one spike every 20 + 139 steps
+    assert g.stats()["num_synapses"] == 0 and len(g.spikes()[0]) == 6
     assert np.all(g.state("V_m")[1:] == -65.0)
     with pytest.raises(ngb.NgbError):
         g.connect(0, 1, W.TOTAL, 1, W.Dist("const", 1.0), W.Dist("const", 1.0))  # after finalise
