@@ -52,6 +52,8 @@ def _args():
                     help="oracle simulation steps timed for the CPU baseline")
     ap.add_argument("--profile-steps", type=int, default=2000)
     ap.add_argument("--no-variant", action="store_true", help="skip the BF16-weight variant")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="microcircuit scale (population sizes and per-pathway counts); 1.0 is the benchmark")
     return ap.parse_args()
 
 
@@ -123,9 +125,9 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def _spec(weights: str, seed: int):
+def _spec(weights: str, seed: int, scale: float = 1.0):
     from paper_2007_14236_gb300 import workloads as W
-    return W.microcircuit(scale=1.0, seed=seed, weight_dtype=weights)
+    return W.microcircuit(scale=scale, seed=seed, weight_dtype=weights)
 
 
 def _cpu_info():
@@ -222,7 +224,7 @@ def main():
     from paper_2007_14236_gb300 import ngb
     ngb.load()
     stream = torch.cuda.Stream()
-    spec = _spec(a.weights, 1 + rank)
+    spec = _spec(a.weights, 1 + rank, a.scale)
     t0 = time.perf_counter()
     sim = ngb.from_spec(spec, device=local, stream=stream.cuda_stream, steps_per_graph=100, drain_steps=10_000,
                         record_capacity=4_000_000)
@@ -314,7 +316,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic (seeded Philox network and Poisson drive)",
-        "config": {"workload": "potjans_diesmann_microcircuit_full_scale", "neurons": N,
+        "config": {"workload": "potjans_diesmann_microcircuit_full_scale" if a.scale == 1.0 else
+                   "potjans_diesmann_microcircuit_scale_%g" % a.scale, "neurons": N,
                    "synapses": st0["num_synapses"], "dt_ms": spec.dt, "bio_s_per_step": a.sim_steps * spec.dt * 1e-3,
                    "weights": a.weights, "parallelism": "replicas" if ws > 1 else "single",
                    "l2": "CSR (%.1f GB) larger than L2 and streamed per spike; state and ring stay resident"

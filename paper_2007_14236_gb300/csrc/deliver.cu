@@ -9,15 +9,18 @@
 // contributes ceil((end - align4(begin)) / 128) work items of 128 consecutive
 // synapses, aligned to 16 bytes; the compaction already assigned each spike
 // the index of its first work item, so a warp maps a work item to its spike
-// by binary search over the (monotone) work-item offsets.  Each lane then
-// loads 4 target words (one 16-byte load) and 4 weights (16 or 8 bytes) with
-// non-caching loads, finds each synapse's delay group by advancing from the
-// work item's first group, and issues one red.global.add per synapse:
-// FP32 (or int64 fixed point in deterministic mode).
+// by binary search over the (monotone) work-item offsets, staged in shared
+// memory.  The spike's list entry carries the source's row and group range.
+// Each lane loads 4 target words (one 16-byte load) and 4 weights (16 or 8
+// bytes); the warp holds the source's delay groups (up to 64) in registers,
+// two per lane, and finds each synapse's group with ballots over the group
+// starts; then one red.global.add per synapse: FP32 (or int64 fixed point in
+// deterministic mode).  Per work item the warp waits on two dependent memory
+// round trips (spike entry, then synapses + groups).
 //
-// Reading a spike's delay groups costs two loads per work item; reading the
-// synapses costs 8 (FP32) or 6 (BF16/FP16) bytes per synapse; the
-// accumulation costs one 4-byte (8-byte) L2 atomic per synapse.
+// Bytes: 8 (FP32) or 6 (BF16/FP16) per synapse read, one 4-byte (8-byte)
+// L2 atomic per synapse, plus 32 bytes of spike entry and 10 bytes per delay
+// group of the source per work item.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -59,72 +62,137 @@ struct W4<__half> {
 
 }  // namespace
 
+constexpr int kStageSpikes = 2048;  // work-item offsets staged in shared memory (8 KB)
+constexpr uint32_t kWindow = 64;     // delay groups a warp holds in registers
+
 template <typename WT, bool kFixed>
 __global__ void __launch_bounds__(kDeliverBlock) k_deliver(SpikeBuf sb, Csr csr, Ring ring, int64_t* clk) {
+  __shared__ uint32_t s_choff[kStageSpikes];
+  const unsigned full = 0xffffffffu;
+  // both parities' counters are read together with the step counter (one round trip)
+  const unsigned long long c0 = sb.ctr[0], c1 = sb.ctr[1];
   const int64_t t = clk[1];
   const int buf = (int)(t & 1);
-  const unsigned long long c = sb.ctr[buf];  // written by the update kernels of step t
+  const unsigned long long c = buf ? c1 : c0;
   const uint32_t nspk = (uint32_t)(c >> kSpkShift);
   const uint32_t nch = (uint32_t)(c & kChunkMask);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     clk[0] = t + 1;        // next step for the update kernels
     sb.ctr[buf ^ 1] = 0;   // the next step's list starts empty
   }
-  const int lane = threadIdx.x & 31;
+  const uint32_t* __restrict__ co = buf ? sb.choff[1] : sb.choff[0];
+  const uint4* __restrict__ info = buf ? sb.info[1] : sb.info[0];
   const uint32_t warp = (blockIdx.x * (uint32_t)kDeliverBlock + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * (uint32_t)kDeliverBlock) >> 5;
-  const uint32_t* __restrict__ sl = buf ? sb.src[1] : sb.src[0];
-  const uint32_t* __restrict__ co = buf ? sb.choff[1] : sb.choff[0];
+  const uint32_t first_ch = blockIdx.x * (uint32_t)(kDeliverBlock / 32);
+  if (first_ch >= nch) return;  // whole block idle this step (uniform per block)
+  const bool staged = nspk <= (uint32_t)kStageSpikes;
+  if (staged) {
+    for (uint32_t i = threadIdx.x; i < nspk; i += kDeliverBlock) s_choff[i] = co[i];
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31;
   for (uint32_t ch = warp; ch < nch; ch += nwarps) {
-    // the spike owning work item ch: last i with co[i] <= ch
+    // the spike owning work item ch: last i with choff[i] <= ch
     uint32_t lo = 0, hi = nspk;
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (co[mid] <= ch) lo = mid;
-      else hi = mid;
+    if (staged) {
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_choff[mid] <= ch) lo = mid;
+        else hi = mid;
+      }
+    } else {
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (co[mid] <= ch) lo = mid;
+        else hi = mid;
+      }
     }
-    const uint32_t word = sl[lo];
-    const uint32_t src = word & kIdMask;
-    const uint32_t mult = word >> kIdBits;
-    const uint32_t local = ch - co[lo];
-    const uint64_t b = __ldg(csr.src_syn + src), e = __ldg(csr.src_syn + src + 1);
+    const uint4 a = info[2 * lo], m2 = info[2 * lo + 1];
+    const uint32_t mult = a.x >> kIdBits;
+    const uint32_t local = ch - a.y;
+    const uint64_t b = (uint64_t)a.z | ((uint64_t)(a.w & 0xFFFFu) << 32);
+    const uint64_t e = b + m2.x;
+    const uint32_t ngrp = a.w >> 16;
+    const uint32_t glo = m2.y;
     const uint64_t cbase = (b & ~3ull) + (uint64_t)local * kChunk;
     const uint64_t j0 = cbase + (uint64_t)lane * 4;
+    const bool any = j0 < e && j0 + 4 > b;
     uint4 tv = make_uint4(0, 0, 0, 0);
     float wv[4] = {0.f, 0.f, 0.f, 0.f};
-    const bool any = j0 < e && j0 + 4 > b;
     if (any) {
       tv = __ldg(reinterpret_cast<const uint4*>(csr.tgt + j0));
       W4<WT>::load(csr.w, j0, wv);
     }
-    // group of the work item's first synapse (uniform across the warp)
-    const uint64_t jf = cbase > b ? cbase : b;
-    uint32_t glo = __ldg(csr.src_grp + src), ghi = __ldg(csr.src_grp + src + 1);
-    while (ghi - glo > 1) {
-      const uint32_t mid = (glo + ghi) >> 1;
-      if (__ldg(csr.grp_start + mid) <= jf) glo = mid;
-      else ghi = mid;
-    }
-    const uint32_t gend = __ldg(csr.src_grp + src + 1);
-    uint32_t g = glo;
-    if (any) {
-  #pragma unroll
+    uint32_t g[4];
+    uint32_t dA = 0, dB = 0;
+    if (ngrp <= kWindow) {
+      // the source's delay groups, two per lane: starts and delays in registers
+      uint64_t sA = ~0ull, sB = ~0ull;
+      if ((uint32_t)lane < ngrp) {
+        sA = __ldg(csr.grp_start + glo + lane);
+        dA = __ldg(csr.grp_delay + glo + lane);
+      }
+      if ((uint32_t)lane + 32 < ngrp) {
+        sB = __ldg(csr.grp_start + glo + 32 + lane);
+        dB = __ldg(csr.grp_delay + glo + 32 + lane);
+      }
+      const uint64_t jf = cbase > b ? cbase : b;             // first synapse of the work item
+      const uint64_t jl = cbase + kChunk < e ? cbase + kChunk : e;
+      // group of jf = (starts <= jf) - 1; the starts are sorted
+      const uint32_t gf = __popc(__ballot_sync(full, sA <= jf)) + __popc(__ballot_sync(full, sB <= jf)) - 1;
+      g[0] = g[1] = g[2] = g[3] = gf;
+      // group boundaries strictly inside the work item
+      for (unsigned mA = __ballot_sync(full, sA > jf && sA < jl); mA; mA &= mA - 1) {
+        const uint64_t bk = __shfl_sync(full, sA, __ffs(mA) - 1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) g[q] += (j0 + q >= bk) ? 1u : 0u;
+      }
+      for (unsigned mB = __ballot_sync(full, sB > jf && sB < jl); mB; mB &= mB - 1) {
+        const uint64_t bk = __shfl_sync(full, sB, __ffs(mB) - 1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) g[q] += (j0 + q >= bk) ? 1u : 0u;
+      }
+    } else {
+      // many delay groups: search the group table in memory
+      const uint64_t jf = cbase > b ? cbase : b;
+      uint32_t l = glo, h = glo + ngrp;
+      while (h - l > 1) {
+        const uint32_t mid = (l + h) >> 1;
+        if (__ldg(csr.grp_start + mid) <= jf) l = mid;
+        else h = mid;
+      }
+      uint32_t gg = l;
+#pragma unroll
       for (int q = 0; q < 4; ++q) {
         const uint64_t j = j0 + q;
-        const uint32_t twq = q == 0 ? tv.x : q == 1 ? tv.y : q == 2 ? tv.z : tv.w;
-        if (j < b || j >= e) continue;
-        while (g + 1 < gend && __ldg(csr.grp_start + g + 1) <= j) ++g;
-        const uint32_t d = __ldg(csr.grp_delay + g);
-        const uint64_t slot = (uint64_t)((t + d) & ring.L_mask);
-        const uint32_t r = twq >> 31;
-        const uint64_t idx = (slot * (uint64_t)ring.R + r) * (uint64_t)ring.N + (twq & 0x7FFFFFFFu);
-        if (kFixed) {
-          const long long qv = __float2ll_rn(wv[q] * 4294967296.0f) * (long long)mult;
-          atomicAdd(reinterpret_cast<unsigned long long*>(ring.p) + idx, (unsigned long long)qv);
-        } else {
-          const float v = mult == 1u ? wv[q] : wv[q] * (float)mult;
-          atomicAdd(reinterpret_cast<float*>(ring.p) + idx, v);
-        }
+        if (any && j >= jf && j < e)
+          while (gg + 1 < glo + ngrp && __ldg(csr.grp_start + gg + 1) <= j) ++gg;
+        g[q] = gg - glo;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t d;
+      if (ngrp <= kWindow) {
+        const uint32_t xa = __shfl_sync(full, dA, g[q] & 31u);
+        const uint32_t xb = __shfl_sync(full, dB, g[q] & 31u);
+        d = g[q] < 32u ? xa : xb;
+      } else {
+        d = __ldg(csr.grp_delay + glo + g[q]);
+      }
+      const uint64_t j = j0 + q;
+      if (!any || j < b || j >= e) continue;
+      const uint32_t twq = q == 0 ? tv.x : q == 1 ? tv.y : q == 2 ? tv.z : tv.w;
+      const uint64_t slot = (uint64_t)((t + d) & ring.L_mask);
+      const uint32_t r = twq >> 31;
+      const uint64_t idx = (slot * (uint64_t)ring.R + r) * (uint64_t)ring.N + (twq & 0x7FFFFFFFu);
+      if (kFixed) {
+        const long long qv = __float2ll_rn(wv[q] * 4294967296.0f) * (long long)mult;
+        atomicAdd(reinterpret_cast<unsigned long long*>(ring.p) + idx, (unsigned long long)qv);
+      } else {
+        const float v = mult == 1u ? wv[q] : wv[q] * (float)mult;
+        atomicAdd(reinterpret_cast<float*>(ring.p) + idx, v);
       }
     }
   }

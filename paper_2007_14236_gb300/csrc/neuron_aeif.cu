@@ -63,17 +63,19 @@ __device__ __forceinline__ float ratio_of(float err, float y, float hf, float fl
 }  // namespace
 
 template <bool kFixed>
-__global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const AeifSeg* __restrict__ segs, int nseg,
+__global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constant__ SegTable<AeifSeg> T,
                                                             const uint32_t* __restrict__ thr,
                                                             float* __restrict__ V_, float* __restrict__ w_,
                                                             float* __restrict__ ge_, float* __restrict__ gi_,
                                                             float* __restrict__ h_, Ring ring, int64_t* clk,
-                                                            const uint64_t* __restrict__ src_syn, SpikeBuf sb) {
-  const int s = find_segment(segs, nseg, (int64_t)blockIdx.x);
-  const AeifSeg& p = segs[s];
+                                                            const uint4* __restrict__ src_meta, SpikeBuf sb) {
+  __shared__ uint32_t s_thr[kMaxThr];
+  const AeifSeg p = segment_of(T, (int64_t)blockIdx.x);
   const int64_t k = ((int64_t)blockIdx.x - p.blk_begin) * kAeifBlock + threadIdx.x;
   const int64_t t = clk[0];
+  for (uint32_t i = threadIdx.x; i < p.n_thr; i += kAeifBlock) s_thr[i] = __ldg(thr + p.thr_off + i);
   if (blockIdx.x == 0 && threadIdx.x == 0) clk[1] = t;
+  __syncthreads();
   const bool valid = k < p.n;
   const uint32_t gid = (uint32_t)(p.offset + k);
   uint32_t nspk = 0;
@@ -100,9 +102,8 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const AeifSeg* __res
     if (p.n_thr > 0) {
       const int64_t tl = t - p.t0;
       const U4 r = draw4(p.seed, (uint64_t)tl, kPurPoisson, 0u, p.local_off + (uint32_t)k);
-      const uint32_t* th = thr + p.thr_off;
       uint32_t kp = 0;
-      while (kp < p.n_thr && r.x >= __ldg(th + kp)) ++kp;
+      while (kp < p.n_thr && r.x >= s_thr[kp]) ++kp;
       const float add = __fmul_rn((float)kp, p.w_ext);
       if (p.prec_rcpt == 0) in0 = __fadd_rn(in0, add);
       else in1 = __fadd_rn(in1, add);
@@ -187,19 +188,19 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const AeifSeg* __res
   for (int o = 16; o > 0; o >>= 1) nsub += __shfl_xor_sync(0xffffffffu, nsub, o);
   if ((threadIdx.x & 31) == 0 && nsub) atomicAdd(sb.substeps, nsub);
   const uint32_t mult = nspk > 63u ? 63u : nspk;
-  emit_spikes(nspk > 0, gid, mult, t, src_syn, sb);
+  emit_spikes(nspk > 0, gid, mult, t, src_meta, sb);
 }
 
-cudaError_t launch_update_aeif(const AeifSeg* segs, int nseg, int64_t blocks, const uint32_t* thr, float* V,
+cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V,
                                float* w, float* gex, float* gin, float* h, Ring ring, bool fixed, int64_t* clk,
-                               const uint64_t* src_syn, SpikeBuf sb, cudaStream_t st) {
+                               const uint4* src_meta, SpikeBuf sb, cudaStream_t st) {
   if (blocks <= 0) return cudaSuccess;
   if (fixed)
-    k_update_aeif<true><<<(unsigned)blocks, kAeifBlock, 0, st>>>(segs, nseg, thr, V, w, gex, gin, h, ring, clk,
-                                                                 src_syn, sb);
+    k_update_aeif<true><<<(unsigned)blocks, kAeifBlock, 0, st>>>(segs, thr, V, w, gex, gin, h, ring, clk,
+                                                                 src_meta, sb);
   else
-    k_update_aeif<false><<<(unsigned)blocks, kAeifBlock, 0, st>>>(segs, nseg, thr, V, w, gex, gin, h, ring, clk,
-                                                                  src_syn, sb);
+    k_update_aeif<false><<<(unsigned)blocks, kAeifBlock, 0, st>>>(segs, thr, V, w, gex, gin, h, ring, clk,
+                                                                  src_meta, sb);
   return cudaGetLastError();
 }
 

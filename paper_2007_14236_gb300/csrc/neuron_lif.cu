@@ -2,7 +2,11 @@
 //
 // One thread per neuron per step, for LIF neurons with exponential PSCs
 // (Eqs. 1-2), integrated exactly on the dt grid (Sec. 2.1, exact integration
-// after Rotter & Diesmann 1999).  In one pass each thread
+// after Rotter & Diesmann 1999).  The population's constants come from the
+// kernel parameters, its Poisson table is staged in shared memory, and all
+// independent loads are issued before the step counter is needed, so a
+// thread waits on two dependent memory round trips (counter, ring slot) plus
+// one more when it spikes.  In one pass each thread
 //   1. reads its ring-buffer slot for step t and zeroes it in place,
 //   2. adds the Poisson drive of step t (Sec. 2.1 Poisson generator): the
 //      count is the inverse CDF of a Philox word, evaluated as the number of
@@ -19,19 +23,29 @@
 namespace ngb {
 
 template <bool kFixed>
-__global__ void __launch_bounds__(kLifBlock) k_update_lif(const LifSeg* __restrict__ segs, int nseg,
+__global__ void __launch_bounds__(kLifBlock) k_update_lif(const __grid_constant__ SegTable<LifSeg> T,
                                                           const uint32_t* __restrict__ thr, float* __restrict__ y_,
                                                           float* __restrict__ I_, int32_t* __restrict__ ref_,
                                                           Ring ring, int64_t* clk,
-                                                          const uint64_t* __restrict__ src_syn, SpikeBuf sb) {
-  const int s = find_segment(segs, nseg, (int64_t)blockIdx.x);
-  const LifSeg& sg = segs[s];
+                                                          const uint4* __restrict__ src_meta, SpikeBuf sb) {
+  __shared__ uint32_t s_thr[kMaxThr];
+  const LifSeg sg = segment_of(T, (int64_t)blockIdx.x);
   const int64_t k = ((int64_t)blockIdx.x - sg.blk_begin) * kLifBlock + threadIdx.x;
-  const int64_t t = clk[0];
-  if (blockIdx.x == 0 && threadIdx.x == 0) clk[1] = t;
   const bool valid = k < sg.n;
-  bool spk = false;
   const uint32_t gid = (uint32_t)(sg.offset + k);
+  // independent loads first: step counter, state, Poisson table (to shared memory)
+  const int64_t t = *(volatile int64_t*)clk;
+  float y = 0.0f, I = 0.0f;
+  int32_t ref = 0;
+  if (valid) {
+    y = y_[gid];
+    I = I_[gid];
+    ref = ref_[gid];
+  }
+  for (uint32_t i = threadIdx.x; i < sg.n_thr; i += kLifBlock) s_thr[i] = __ldg(thr + sg.thr_off + i);
+  if (blockIdx.x == 0 && threadIdx.x == 0) clk[1] = t;
+  __syncthreads();
+  bool spk = false;
   if (valid) {
     const uint64_t slot = (uint64_t)(t & ring.L_mask);
     const uint64_t idx = slot * (uint64_t)ring.R * (uint64_t)ring.N + gid;
@@ -49,14 +63,10 @@ __global__ void __launch_bounds__(kLifBlock) k_update_lif(const LifSeg* __restri
     if (sg.n_thr > 0) {
       const int64_t tl = t - sg.t0;
       const U4 r = draw4(sg.seed, (uint64_t)tl, kPurPoisson, 0u, sg.local_off + (uint32_t)k);
-      const uint32_t* th = thr + sg.thr_off;
       uint32_t kp = 0;
-      while (kp < sg.n_thr && r.x >= __ldg(th + kp)) ++kp;
+      while (kp < sg.n_thr && r.x >= s_thr[kp]) ++kp;
       in = __fadd_rn(in, __fmul_rn((float)kp, sg.w_ext));
     }
-    float y = y_[gid];
-    float I = I_[gid];
-    int32_t ref = ref_[gid];
     if (ref > 0) {
       ref -= 1;
     } else {
@@ -72,17 +82,34 @@ __global__ void __launch_bounds__(kLifBlock) k_update_lif(const LifSeg* __restri
     I_[gid] = I;
     ref_[gid] = ref;
   }
-  emit_spikes(spk, gid, 1u, t, src_syn, sb);
+  emit_spikes(spk, gid, 1u, t, src_meta, sb);
 }
 
-cudaError_t launch_update_lif(const LifSeg* segs, int nseg, int64_t blocks, const uint32_t* thr, float* y, float* I,
-                              int32_t* ref, Ring ring, bool fixed, int64_t* clk, const uint64_t* src_syn,
+cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, const uint32_t* thr, float* y,
+                              float* I, int32_t* ref, Ring ring, bool fixed, int64_t* clk, const uint4* src_meta,
                               SpikeBuf sb, cudaStream_t st) {
   if (blocks <= 0) return cudaSuccess;
   if (fixed)
-    k_update_lif<true><<<(unsigned)blocks, kLifBlock, 0, st>>>(segs, nseg, thr, y, I, ref, ring, clk, src_syn, sb);
+    k_update_lif<true><<<(unsigned)blocks, kLifBlock, 0, st>>>(segs, thr, y, I, ref, ring, clk, src_meta, sb);
   else
-    k_update_lif<false><<<(unsigned)blocks, kLifBlock, 0, st>>>(segs, nseg, thr, y, I, ref, ring, clk, src_syn, sb);
+    k_update_lif<false><<<(unsigned)blocks, kLifBlock, 0, st>>>(segs, thr, y, I, ref, ring, clk, src_meta, sb);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ source metadata
+__global__ void k_build_meta(int64_t N, const uint64_t* __restrict__ src_syn, const uint32_t* __restrict__ src_grp,
+                             uint4* __restrict__ meta) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const uint64_t b = src_syn[i], e = src_syn[i + 1];
+  const uint32_t g0 = src_grp[i], g1 = src_grp[i + 1];
+  meta[i] = make_uint4((uint32_t)b, (uint32_t)((b >> 32) & 0xFFFFu) | ((g1 - g0) << 16), (uint32_t)(e - b), g0);
+}
+
+cudaError_t launch_build_meta(int64_t N, const uint64_t* src_syn, const uint32_t* src_grp, uint4* meta,
+                              cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  k_build_meta<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, src_syn, src_grp, meta);
   return cudaGetLastError();
 }
 

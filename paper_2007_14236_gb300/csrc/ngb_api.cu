@@ -126,12 +126,13 @@ struct ngb_sim {
   uint16_t* grp_delay = nullptr;
   uint32_t* tgt = nullptr;
   void* w = nullptr;
+  uint4* src_meta = nullptr;
   SpikeBuf sb{};
   int64_t* clk = nullptr;
-  LifSeg* lif_segs = nullptr;
+  SegTable<LifSeg> lif_tab{};
   int n_lif = 0;
   int64_t lif_blocks = 0;
-  AeifSeg* aeif_segs = nullptr;
+  SegTable<AeifSeg> aeif_tab{};
   int n_aeif = 0;
   int64_t aeif_blocks = 0;
   uint32_t* thr = nullptr;
@@ -164,23 +165,35 @@ namespace {
 Ring ring_of(const ngb_sim* s) { return Ring{s->ring, s->N, (uint32_t)(s->L - 1), s->R}; }
 
 Csr csr_of(const ngb_sim* s) {
-  return Csr{s->src_syn, s->src_grp, s->grp_start, s->grp_delay, s->tgt, s->w};
+  return Csr{s->src_meta, s->src_syn, s->src_grp, s->grp_start, s->grp_delay, s->tgt, s->w};
+}
+
+cudaError_t launch_lif(ngb_sim* s) {
+  return launch_update_lif(s->lif_tab, s->lif_blocks, s->thr, s->st0, s->st1, s->ref, ring_of(s),
+                           s->cfg.deterministic != 0, s->clk, s->src_meta, s->sb, s->stream);
+}
+
+cudaError_t launch_aeif(ngb_sim* s) {
+  return launch_update_aeif(s->aeif_tab, s->aeif_blocks, s->thr, s->st0, s->st1, s->st2, s->st3, s->st4,
+                            ring_of(s), s->cfg.deterministic != 0, s->clk, s->src_meta, s->sb, s->stream);
+}
+
+cudaError_t launch_del(ngb_sim* s) {
+  return launch_deliver(s->sb, csr_of(s), s->cfg.weight_dtype, ring_of(s), s->cfg.deterministic != 0, s->clk,
+                        s->deliver_grid, s->stream);
 }
 
 cudaError_t launch_step(ngb_sim* s) {
   cudaError_t e;
   if (s->n_lif) {
-    e = launch_update_lif(s->lif_segs, s->n_lif, s->lif_blocks, s->thr, s->st0, s->st1, s->ref, ring_of(s),
-                          s->cfg.deterministic != 0, s->clk, s->src_syn, s->sb, s->stream);
+    e = launch_lif(s);
     if (e != cudaSuccess) return e;
   }
   if (s->n_aeif) {
-    e = launch_update_aeif(s->aeif_segs, s->n_aeif, s->aeif_blocks, s->thr, s->st0, s->st1, s->st2, s->st3,
-                           s->st4, ring_of(s), s->cfg.deterministic != 0, s->clk, s->src_syn, s->sb, s->stream);
+    e = launch_aeif(s);
     if (e != cudaSuccess) return e;
   }
-  return launch_deliver(s->sb, csr_of(s), s->cfg.weight_dtype, ring_of(s), s->cfg.deterministic != 0, s->clk,
-                        s->deliver_grid, s->stream);
+  return launch_del(s);
 }
 
 // Collect the device spike record and error flags; resets the record.
@@ -352,6 +365,8 @@ int finalize_impl(ngb_sim* s) {
     CK(exclusive_scan_u64(src_ngrp, scan_out, (uint64_t)N + 1, tmp, tmp_bytes, st));
     CK(s->dalloc(&s->src_grp, N + 1));
     CK(narrow_u64_to_u32(scan_out, s->src_grp, (uint64_t)N + 1, st));
+    CK(s->dalloc(&s->src_meta, N));
+    CK(launch_build_meta(N, s->src_syn, s->src_grp, s->src_meta, st));
     int md = 0;
     CK(cudaMemcpyAsync(&md, dmax, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -464,20 +479,28 @@ int finalize_impl(ngb_sim* s) {
   s->n_lif = (int)lsegs.size();
   s->n_aeif = (int)asegs.size();
   if (s->n_lif) {
-    CK(s->dalloc(&s->lif_segs, lsegs.size()));
-    CK(cudaMemcpyAsync(s->lif_segs, lsegs.data(), lsegs.size() * sizeof(LifSeg), cudaMemcpyHostToDevice, st));
+    LifSeg* d = nullptr;
+    CK(s->dalloc(&d, lsegs.size()));
+    CK(cudaMemcpyAsync(d, lsegs.data(), lsegs.size() * sizeof(LifSeg), cudaMemcpyHostToDevice, st));
+    s->lif_tab.dev = d;
+    s->lif_tab.n = s->n_lif;
+    for (int i = 0; i < std::min(s->n_lif, kInlineSegs); ++i) s->lif_tab.s[i] = lsegs[i];
   }
   if (s->n_aeif) {
-    CK(s->dalloc(&s->aeif_segs, asegs.size()));
-    CK(cudaMemcpyAsync(s->aeif_segs, asegs.data(), asegs.size() * sizeof(AeifSeg), cudaMemcpyHostToDevice, st));
+    AeifSeg* d = nullptr;
+    CK(s->dalloc(&d, asegs.size()));
+    CK(cudaMemcpyAsync(d, asegs.data(), asegs.size() * sizeof(AeifSeg), cudaMemcpyHostToDevice, st));
+    s->aeif_tab.dev = d;
+    s->aeif_tab.n = s->n_aeif;
+    for (int i = 0; i < std::min(s->n_aeif, kInlineSegs); ++i) s->aeif_tab.s[i] = asegs[i];
   }
   CK(s->dalloc(&s->thr, thr_all.size() + 1));
   if (!thr_all.empty())
     CK(cudaMemcpyAsync(s->thr, thr_all.data(), thr_all.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
 
   // ---------------------------------------------------------------- spike lists and record
-  CK(s->dalloc(&s->sb.src[0], N));
-  CK(s->dalloc(&s->sb.src[1], N));
+  CK(s->dalloc(&s->sb.info[0], 2 * N));
+  CK(s->dalloc(&s->sb.info[1], 2 * N));
   CK(s->dalloc(&s->sb.choff[0], N));
   CK(s->dalloc(&s->sb.choff[1], N));
   unsigned long long* ctrs = nullptr;
@@ -504,7 +527,7 @@ int finalize_impl(ngb_sim* s) {
   int dev = 0, sms = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  s->deliver_grid = std::max(1, sms) * (2048 / kDeliverBlock);
+  s->deliver_grid = std::max(1, sms) * 2;
   CK(cudaStreamSynchronize(st));
 
   // ---------------------------------------------------------------- step graph
@@ -576,17 +599,11 @@ int simulate_impl(ngb_sim* s, int64_t steps, bool profiled, double* kernel_ms, i
     for (int64_t i = 0; i < chunk; ++i) {
       cudaEvent_t* e = &ev[4 * i];
       CK(cudaEventRecord(e[0], s->stream));
-      if (s->n_lif)
-        CK(launch_update_lif(s->lif_segs, s->n_lif, s->lif_blocks, s->thr, s->st0, s->st1, s->ref, ring_of(s),
-                             s->cfg.deterministic != 0, s->clk, s->src_syn, s->sb, s->stream));
+      if (s->n_lif) CK(launch_lif(s));
       CK(cudaEventRecord(e[1], s->stream));
-      if (s->n_aeif)
-        CK(launch_update_aeif(s->aeif_segs, s->n_aeif, s->aeif_blocks, s->thr, s->st0, s->st1, s->st2, s->st3,
-                              s->st4, ring_of(s), s->cfg.deterministic != 0, s->clk, s->src_syn, s->sb,
-                              s->stream));
+      if (s->n_aeif) CK(launch_aeif(s));
       CK(cudaEventRecord(e[2], s->stream));
-      CK(launch_deliver(s->sb, csr_of(s), s->cfg.weight_dtype, ring_of(s), s->cfg.deterministic != 0, s->clk,
-                        s->deliver_grid, s->stream));
+      CK(launch_del(s));
       CK(cudaEventRecord(e[3], s->stream));
     }
     CK(cudaStreamSynchronize(s->stream));

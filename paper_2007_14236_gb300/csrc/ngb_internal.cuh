@@ -13,9 +13,13 @@
 //              groups: a source's synapses with equal delay, in delay order),
 //              tgt[K] u32 (bit 31 = receptor, bits 0-30 = global target),
 //              w[K] FP32 / BF16 / FP16
-//   spikes     per step (double-buffered by step parity): src[] u32 (bits
-//              0-25 neuron, 26-31 multiplicity), choff[] u32 (first delivery
-//              work item of the spike) and one packed u64 counter
+//   src_meta   uint4 per source {row start lo, row start hi (16 bits) | groups
+//              << 16, synapses, first group}: everything delivery needs about
+//              a spiking source, read once by the update kernel
+//   spikes     per step (double-buffered by step parity): choff[] u32 (first
+//              delivery work item of the spike), info[] 2 x uint4 per spike
+//              ({neuron | multiplicity << 26, choff, meta.x, meta.y},
+//              {meta.z, meta.w, 0, 0}) and one packed u64 counter
 //              (spikes << 38 | work items)
 #pragma once
 
@@ -66,7 +70,7 @@ struct AeifSeg {
 };
 
 struct SpikeBuf {
-  uint32_t* src[2];
+  uint4* info[2];                   // 2 entries per spike
   uint32_t* choff[2];
   unsigned long long* ctr;          // [2] packed per-step counters
   unsigned long long* events;       // synaptic events delivered (cumulative)
@@ -79,6 +83,7 @@ struct SpikeBuf {
 };
 
 struct Csr {
+  const uint4* src_meta;
   const uint64_t* src_syn;
   const uint32_t* src_grp;
   const uint64_t* grp_start;
@@ -98,19 +103,24 @@ struct Ring {
 // list (Sec. 2.2 spike array, at most N entries), with one atomic per warp
 // reserving both list positions and delivery work items, plus the spike
 // record.  Every lane of the warp must call it (no early exit before it).
+// A spiking lane reads its source's metadata once and passes it on, so the
+// delivery kernel needs no further per-source lookups.
 __device__ __forceinline__ void emit_spikes(bool spk, uint32_t gid, uint32_t mult, int64_t t,
-                                            const uint64_t* __restrict__ src_syn, const SpikeBuf& sb) {
+                                            const uint4* __restrict__ src_meta, const SpikeBuf& sb) {
   const unsigned full = 0xffffffffu;
   const unsigned ball = __ballot_sync(full, spk);
   if (ball == 0) return;
   const int lane = threadIdx.x & 31;
   uint32_t nch = 0, m = 0;
   unsigned long long nev = 0;
+  uint4 meta = make_uint4(0, 0, 0, 0);
   if (spk) {
-    const uint64_t b = src_syn[gid], e = src_syn[gid + 1];
+    meta = __ldg(src_meta + gid);
+    const uint64_t b = (uint64_t)meta.x | ((uint64_t)(meta.y & 0xFFFFu) << 32);
+    const uint64_t e = b + meta.z;
     if (e > b) nch = (uint32_t)((e - (b & ~3ull) + kChunk - 1) / kChunk);
     m = mult;
-    nev = (unsigned long long)(e - b) * mult;
+    nev = (unsigned long long)meta.z * mult;
   }
   uint32_t inc_ch = nch, inc_m = m;
 #pragma unroll
@@ -138,10 +148,12 @@ __device__ __forceinline__ void emit_spikes(bool spk, uint32_t gid, uint32_t mul
   if (spk) {
     const uint32_t rank = __popc(ball & ((1u << lane) - 1u));
     const unsigned long long pos = (base >> kSpkShift) + rank;
-    uint32_t* const src_list = buf ? sb.src[1] : sb.src[0];
+    uint4* const info = buf ? sb.info[1] : sb.info[0];
     uint32_t* const choff_list = buf ? sb.choff[1] : sb.choff[0];
-    src_list[pos] = gid | (mult << kIdBits);
-    choff_list[pos] = (uint32_t)(base & kChunkMask) + inc_ch - nch;
+    const uint32_t choff = (uint32_t)(base & kChunkMask) + inc_ch - nch;
+    choff_list[pos] = choff;
+    info[2 * pos] = make_uint4(gid | (mult << kIdBits), choff, meta.x, meta.y);
+    info[2 * pos + 1] = make_uint4(meta.z, meta.w, 0u, 0u);
     if (sb.rec_cap > 0) {
       const unsigned long long r0 = rbase + inc_m - m;
       for (uint32_t k = 0; k < m; ++k) {
@@ -156,26 +168,48 @@ __device__ __forceinline__ void emit_spikes(bool spk, uint32_t gid, uint32_t mul
   }
 }
 
-// Binary search of the segment that owns block `blk` (segments sorted by blk_begin).
+// Segment tables passed by value in the kernel parameters (constant bank)
+// when they are small; otherwise the kernels read the device copy.
+constexpr int kInlineSegs = 12;
 template <typename Seg>
-__device__ __forceinline__ int find_segment(const Seg* __restrict__ segs, int nseg, int64_t blk) {
-  int lo = 0, hi = nseg;
+struct SegTable {
+  Seg s[kInlineSegs];
+  const Seg* dev;  // device copy of all segments (always valid)
+  int n;
+};
+
+// The segment owning block `blk`: binary search over blk_begin in the inline
+// copy (constant bank) or, for long tables, in the device copy.
+template <typename Seg>
+__device__ __forceinline__ Seg segment_of(const SegTable<Seg>& T, int64_t blk) {
+  int lo = 0, hi = T.n;
+  if (T.n <= kInlineSegs) {
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (T.s[mid].blk_begin <= blk) lo = mid;
+      else hi = mid;
+    }
+    return T.s[lo];
+  }
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
-    if (segs[mid].blk_begin <= blk) lo = mid;
+    if (T.dev[mid].blk_begin <= blk) lo = mid;
     else hi = mid;
   }
-  return lo;
+  return T.dev[lo];
 }
 
 // ------------------------------------------------------------------ host side
 // Kernel launchers (one translation unit each).
-cudaError_t launch_update_lif(const LifSeg* segs, int nseg, int64_t blocks, const uint32_t* thr, float* y, float* I,
-                              int32_t* ref, Ring ring, bool fixed, int64_t* clk, const uint64_t* src_syn,
+cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, const uint32_t* thr, float* y,
+                              float* I, int32_t* ref, Ring ring, bool fixed, int64_t* clk, const uint4* src_meta,
                               SpikeBuf sb, cudaStream_t st);
-cudaError_t launch_update_aeif(const AeifSeg* segs, int nseg, int64_t blocks, const uint32_t* thr, float* V,
+cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V,
                                float* w, float* gex, float* gin, float* h, Ring ring, bool fixed, int64_t* clk,
-                               const uint64_t* src_syn, SpikeBuf sb, cudaStream_t st);
+                               const uint4* src_meta, SpikeBuf sb, cudaStream_t st);
+// Per-source metadata for the update kernels' spike lists.
+cudaError_t launch_build_meta(int64_t N, const uint64_t* src_syn, const uint32_t* src_grp, uint4* meta,
+                              cudaStream_t st);
 cudaError_t launch_deliver(SpikeBuf sb, Csr csr, int wdtype, Ring ring, bool fixed, int64_t* clk, int grid,
                            cudaStream_t st);
 // Initial state of one population: V0 = mean + sd * z (z standard normal from
