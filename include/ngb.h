@@ -197,13 +197,24 @@ NGB_API int ngb_connect(ngb_sim* sim, int32_t src_pop, int32_t tgt_pop, const ng
 NGB_API int ngb_finalize(ngb_sim* sim);
 
 /* ----------------------------------------------------------- simulation */
-/* Advance every instance by `steps` steps; returns when done (blocking). */
+/* Advance every instance by `steps` steps; returns when done (blocking).
+ * The step's kernels are chained with programmatic dependent launch unless
+ * the environment variable NGB_PDL is "0" when the network is finalised. */
 NGB_API int ngb_simulate(ngb_sim* sim, int64_t steps);
 
 /* As ngb_simulate, without CUDA graphs, with CUDA events around every kernel
  * launch.  kernel_ms[3] receives the summed device time of the LIF update,
  * AdEx update and delivery kernels; launches[3] their launch counts. */
 NGB_API int ngb_simulate_profiled(ngb_sim* sim, int64_t steps, double* kernel_ms, int64_t* launches);
+
+/* Autotune the delivery launch (blocks per SM in {1, 2, 4, 8}) by timing
+ * trial_steps steps (0 = 500) of graph replays per candidate on this network;
+ * the simulation state is saved before and restored after the trials, so the
+ * simulation does not advance.  With the environment variable
+ * NGB_AUTOTUNE_CACHE naming a file, results are looked up and appended there
+ * per (GPU, network shape) key.  *deliver_grid_out (may be NULL) receives the
+ * chosen grid. */
+NGB_API int ngb_autotune(ngb_sim* sim, int64_t trial_steps, int32_t* deliver_grid_out);
 
 /* Spikes recorded in steps [t0_step, t1_step) of population `pop` (-1 = all,
  * then ids are global; else population-local), sorted by (step, id).  With

@@ -256,6 +256,42 @@ cudaError_t scan_scratch_bytes_u64(uint64_t n, size_t* bytes) {
                                        (unsigned long long*)nullptr, (int64_t)n);
 }
 
+// Synapses [first, first + n) decoded for introspection: target, receptor,
+// weight widened to FP32 and the delay of the group containing each synapse
+// (binary search over the group starts).
+__global__ void k_expand(uint64_t first, uint64_t n, const uint32_t* __restrict__ tgt, const void* __restrict__ w,
+                         int wdtype, const uint64_t* __restrict__ gstart, uint64_t G,
+                         const uint16_t* __restrict__ gdelay, uint32_t* __restrict__ o_tgt,
+                         uint8_t* __restrict__ o_rc, float* __restrict__ o_w, uint16_t* __restrict__ o_d) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t j = first + i;
+    const uint32_t tw = tgt[j];
+    o_tgt[i] = tw & 0x7FFFFFFFu;
+    o_rc[i] = (uint8_t)(tw >> 31);
+    float v;
+    if (wdtype == 0) v = reinterpret_cast<const float*>(w)[j];
+    else if (wdtype == 1) v = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(w)[j]);
+    else v = __half2float(reinterpret_cast<const __half*>(w)[j]);
+    o_w[i] = v;
+    uint64_t lo = 0, hi = G;  // last g with gstart[g] <= j
+    while (hi - lo > 1) {
+      const uint64_t mid = (lo + hi) >> 1;
+      if (gstart[mid] <= j) lo = mid;
+      else hi = mid;
+    }
+    o_d[i] = gdelay[lo];
+  }
+}
+
+cudaError_t expand_synapses(uint64_t first, uint64_t n, const uint32_t* tgt, const void* w, int wdtype,
+                            const uint64_t* gstart, uint64_t G, const uint16_t* gdelay, uint32_t* o_tgt,
+                            uint8_t* o_rc, float* o_w, uint16_t* o_d, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_expand<<<grid_for(n), 256, 0, st>>>(first, n, tgt, w, wdtype, gstart, G, gdelay, o_tgt, o_rc, o_w, o_d);
+  return cudaGetLastError();
+}
+
 cudaError_t narrow_u64_to_u32(const unsigned long long* in, uint32_t* out, uint64_t n, cudaStream_t st) {
   k_to_u32<<<grid_for(n), 256, 0, st>>>(n, in, out);
   return cudaGetLastError();

@@ -53,6 +53,9 @@ cudaError_t build_source_population(const std::vector<CallDev>& calls, uint64_t 
 
 cudaError_t exclusive_scan_u64(const unsigned long long* in, unsigned long long* out, uint64_t n, void* tmp,
                                size_t tmp_bytes, cudaStream_t st);
+cudaError_t expand_synapses(uint64_t first, uint64_t n, const uint32_t* tgt, const void* w, int wdtype,
+                            const uint64_t* gstart, uint64_t G, const uint16_t* gdelay, uint32_t* o_tgt,
+                            uint8_t* o_rc, float* o_w, uint16_t* o_d, cudaStream_t st);
 cudaError_t narrow_u64_to_u32(const unsigned long long* in, uint32_t* out, uint64_t n, cudaStream_t st);
 
 }  // namespace ngb

@@ -7,20 +7,19 @@
 //
 // Work decomposition (load-balanced, synapse-parallel): every spiking source
 // contributes ceil((end - align4(begin)) / 128) work items of 128 consecutive
-// synapses, aligned to 16 bytes; the compaction already assigned each spike
-// the index of its first work item, so a warp maps a work item to its spike
-// by binary search over the (monotone) work-item offsets, staged in shared
-// memory.  The spike's list entry carries the source's row and group range.
-// Each lane loads 4 target words (one 16-byte load) and 4 weights (16 or 8
-// bytes); the warp holds the source's delay groups (up to 64) in registers,
-// two per lane, and finds each synapse's group with ballots over the group
-// starts; then one red.global.add per synapse: FP32 (or int64 fixed point in
-// deterministic mode).  Per work item the warp waits on two dependent memory
-// round trips (spike entry, then synapses + groups).
+// synapses, aligned to 16 bytes.  The compaction in the update kernels wrote
+// one 32-byte entry per work item (source, index within the source, row and
+// group range), so a warp reads its work item with one load.  Each lane
+// loads 4 target words (one 16-byte load) and 4 weights (16 or 8 bytes); the
+// warp holds the source's delay groups (up to 64) in registers, two per lane,
+// and finds each synapse's group with ballots over the group starts; then one
+// red.global.add per synapse: FP32 (or int64 fixed point in deterministic
+// mode).  Per work item the warp waits on two dependent memory round trips
+// (work-item entry, then synapses + groups).
 //
 // Bytes: 8 (FP32) or 6 (BF16/FP16) per synapse read, one 4-byte (8-byte)
-// L2 atomic per synapse, plus 32 bytes of spike entry and 10 bytes per delay
-// group of the source per work item.
+// L2 atomic per synapse, plus 32 bytes of work-item entry and 10 bytes per
+// delay group of the source per work item.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -62,55 +61,31 @@ struct W4<__half> {
 
 }  // namespace
 
-constexpr int kStageSpikes = 2048;  // work-item offsets staged in shared memory (8 KB)
-constexpr uint32_t kWindow = 64;     // delay groups a warp holds in registers
+constexpr uint32_t kWindow = 64;  // delay groups a warp holds in registers
 
 template <typename WT, bool kFixed>
 __global__ void __launch_bounds__(kDeliverBlock) k_deliver(SpikeBuf sb, Csr csr, Ring ring, int64_t* clk) {
-  __shared__ uint32_t s_choff[kStageSpikes];
   const unsigned full = 0xffffffffu;
+  griddep_wait();    // the step's update kernels have completed
+  griddep_launch();  // the next step's update may start its prologue
   // both parities' counters are read together with the step counter (one round trip)
   const unsigned long long c0 = sb.ctr[0], c1 = sb.ctr[1];
   const int64_t t = clk[1];
   const int buf = (int)(t & 1);
   const unsigned long long c = buf ? c1 : c0;
-  const uint32_t nspk = (uint32_t)(c >> kSpkShift);
   const uint32_t nch = (uint32_t)(c & kChunkMask);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     clk[0] = t + 1;        // next step for the update kernels
     sb.ctr[buf ^ 1] = 0;   // the next step's list starts empty
   }
-  const uint32_t* __restrict__ co = buf ? sb.choff[1] : sb.choff[0];
-  const uint4* __restrict__ info = buf ? sb.info[1] : sb.info[0];
+  const uint4* __restrict__ wi = buf ? sb.wi[1] : sb.wi[0];
   const uint32_t warp = (blockIdx.x * (uint32_t)kDeliverBlock + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * (uint32_t)kDeliverBlock) >> 5;
-  const uint32_t first_ch = blockIdx.x * (uint32_t)(kDeliverBlock / 32);
-  if (first_ch >= nch) return;  // whole block idle this step (uniform per block)
-  const bool staged = nspk <= (uint32_t)kStageSpikes;
-  if (staged) {
-    for (uint32_t i = threadIdx.x; i < nspk; i += kDeliverBlock) s_choff[i] = co[i];
-    __syncthreads();
-  }
   const int lane = threadIdx.x & 31;
   for (uint32_t ch = warp; ch < nch; ch += nwarps) {
-    // the spike owning work item ch: last i with choff[i] <= ch
-    uint32_t lo = 0, hi = nspk;
-    if (staged) {
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (s_choff[mid] <= ch) lo = mid;
-        else hi = mid;
-      }
-    } else {
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (co[mid] <= ch) lo = mid;
-        else hi = mid;
-      }
-    }
-    const uint4 a = info[2 * lo], m2 = info[2 * lo + 1];
+    const uint4 a = wi[2 * (uint64_t)ch], m2 = wi[2 * (uint64_t)ch + 1];
     const uint32_t mult = a.x >> kIdBits;
-    const uint32_t local = ch - a.y;
+    const uint32_t local = a.y;
     const uint64_t b = (uint64_t)a.z | ((uint64_t)(a.w & 0xFFFFu) << 32);
     const uint64_t e = b + m2.x;
     const uint32_t ngrp = a.w >> 16;
@@ -199,17 +174,16 @@ __global__ void __launch_bounds__(kDeliverBlock) k_deliver(SpikeBuf sb, Csr csr,
 }
 
 cudaError_t launch_deliver(SpikeBuf sb, Csr csr, int wdtype, Ring ring, bool fixed, int64_t* clk, int grid,
-                           cudaStream_t st) {
+                           bool pdl, cudaStream_t st) {
+  const dim3 g((unsigned)grid), b(kDeliverBlock);
   if (fixed) {
-    if (wdtype == 0) k_deliver<float, true><<<grid, kDeliverBlock, 0, st>>>(sb, csr, ring, clk);
-    else if (wdtype == 1) k_deliver<__nv_bfloat16, true><<<grid, kDeliverBlock, 0, st>>>(sb, csr, ring, clk);
-    else k_deliver<__half, true><<<grid, kDeliverBlock, 0, st>>>(sb, csr, ring, clk);
-  } else {
-    if (wdtype == 0) k_deliver<float, false><<<grid, kDeliverBlock, 0, st>>>(sb, csr, ring, clk);
-    else if (wdtype == 1) k_deliver<__nv_bfloat16, false><<<grid, kDeliverBlock, 0, st>>>(sb, csr, ring, clk);
-    else k_deliver<__half, false><<<grid, kDeliverBlock, 0, st>>>(sb, csr, ring, clk);
+    if (wdtype == 0) return launch_k(k_deliver<float, true>, g, b, pdl, st, sb, csr, ring, clk);
+    if (wdtype == 1) return launch_k(k_deliver<__nv_bfloat16, true>, g, b, pdl, st, sb, csr, ring, clk);
+    return launch_k(k_deliver<__half, true>, g, b, pdl, st, sb, csr, ring, clk);
   }
-  return cudaGetLastError();
+  if (wdtype == 0) return launch_k(k_deliver<float, false>, g, b, pdl, st, sb, csr, ring, clk);
+  if (wdtype == 1) return launch_k(k_deliver<__nv_bfloat16, false>, g, b, pdl, st, sb, csr, ring, clk);
+  return launch_k(k_deliver<__half, false>, g, b, pdl, st, sb, csr, ring, clk);
 }
 
 }  // namespace ngb

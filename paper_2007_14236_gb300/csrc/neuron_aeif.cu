@@ -72,12 +72,23 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
   __shared__ uint32_t s_thr[kMaxThr];
   const AeifSeg p = segment_of(T, (int64_t)blockIdx.x);
   const int64_t k = ((int64_t)blockIdx.x - p.blk_begin) * kAeifBlock + threadIdx.x;
-  const int64_t t = clk[0];
-  for (uint32_t i = threadIdx.x; i < p.n_thr; i += kAeifBlock) s_thr[i] = __ldg(thr + p.thr_off + i);
-  if (blockIdx.x == 0 && threadIdx.x == 0) clk[1] = t;
-  __syncthreads();
   const bool valid = k < p.n;
   const uint32_t gid = (uint32_t)(p.offset + k);
+  // prologue (overlaps the previous kernel): state, source metadata, Poisson table
+  St y{0.f, 0.f, 0.f, 0.f};
+  float h0 = 0.f;
+  uint4 meta = make_uint4(0, 0, 0, 0);
+  if (valid) {
+    y = St{V_[gid], w_[gid], ge_[gid], gi_[gid]};
+    h0 = h_[gid];
+    meta = __ldg(src_meta + gid);
+  }
+  for (uint32_t i = threadIdx.x; i < p.n_thr; i += kAeifBlock) s_thr[i] = __ldg(thr + p.thr_off + i);
+  __syncthreads();
+  griddep_wait();
+  griddep_launch();
+  const int64_t t = clk[0];
+  if (blockIdx.x == 0 && threadIdx.x == 0) clk[1] = t;
   uint32_t nspk = 0;
   unsigned long long nsub = 0;
   if (valid) {
@@ -108,8 +119,7 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
       if (p.prec_rcpt == 0) in0 = __fadd_rn(in0, add);
       else in1 = __fadd_rn(in1, add);
     }
-    St y{V_[gid], w_[gid], ge_[gid], gi_[gid]};
-    double h = (double)h_[gid];
+    double h = (double)h0;
     if (!(h > 0.0)) h = p.dt;
     double t_in = 0.0;
     for (;;) {
@@ -188,20 +198,17 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
   for (int o = 16; o > 0; o >>= 1) nsub += __shfl_xor_sync(0xffffffffu, nsub, o);
   if ((threadIdx.x & 31) == 0 && nsub) atomicAdd(sb.substeps, nsub);
   const uint32_t mult = nspk > 63u ? 63u : nspk;
-  emit_spikes(nspk > 0, gid, mult, t, src_meta, sb);
+  emit_spikes(nspk > 0, gid, mult, t, meta, sb);
 }
 
 cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V,
                                float* w, float* gex, float* gin, float* h, Ring ring, bool fixed, int64_t* clk,
-                               const uint4* src_meta, SpikeBuf sb, cudaStream_t st) {
+                               const uint4* src_meta, SpikeBuf sb, bool pdl, cudaStream_t st) {
   if (blocks <= 0) return cudaSuccess;
+  const dim3 g((unsigned)blocks), b(kAeifBlock);
   if (fixed)
-    k_update_aeif<true><<<(unsigned)blocks, kAeifBlock, 0, st>>>(segs, thr, V, w, gex, gin, h, ring, clk,
-                                                                 src_meta, sb);
-  else
-    k_update_aeif<false><<<(unsigned)blocks, kAeifBlock, 0, st>>>(segs, thr, V, w, gex, gin, h, ring, clk,
-                                                                  src_meta, sb);
-  return cudaGetLastError();
+    return launch_k(k_update_aeif<true>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, ring, clk, src_meta, sb);
+  return launch_k(k_update_aeif<false>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, ring, clk, src_meta, sb);
 }
 
 }  // namespace ngb

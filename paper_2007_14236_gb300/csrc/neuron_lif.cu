@@ -6,7 +6,9 @@
 // kernel parameters, its Poisson table is staged in shared memory, and all
 // independent loads are issued before the step counter is needed, so a
 // thread waits on two dependent memory round trips (counter, ring slot) plus
-// one more when it spikes.  In one pass each thread
+// one more when it spikes.  Loads that do not depend on the previous kernel
+// are issued before griddep_wait(), so with programmatic dependent launch
+// they overlap the previous step's delivery.  In one pass each thread
 //   1. reads its ring-buffer slot for step t and zeroes it in place,
 //   2. adds the Poisson drive of step t (Sec. 2.1 Poisson generator): the
 //      count is the inverse CDF of a Philox word, evaluated as the number of
@@ -33,18 +35,24 @@ __global__ void __launch_bounds__(kLifBlock) k_update_lif(const __grid_constant_
   const int64_t k = ((int64_t)blockIdx.x - sg.blk_begin) * kLifBlock + threadIdx.x;
   const bool valid = k < sg.n;
   const uint32_t gid = (uint32_t)(sg.offset + k);
-  // independent loads first: step counter, state, Poisson table (to shared memory)
-  const int64_t t = *(volatile int64_t*)clk;
+  // Prologue, overlapping the previous kernel (programmatic dependent launch):
+  // state written two launches ago, static source metadata, Poisson table.
   float y = 0.0f, I = 0.0f;
   int32_t ref = 0;
+  uint4 meta = make_uint4(0, 0, 0, 0);
   if (valid) {
     y = y_[gid];
     I = I_[gid];
     ref = ref_[gid];
+    meta = __ldg(src_meta + gid);
   }
   for (uint32_t i = threadIdx.x; i < sg.n_thr; i += kLifBlock) s_thr[i] = __ldg(thr + sg.thr_off + i);
-  if (blockIdx.x == 0 && threadIdx.x == 0) clk[1] = t;
   __syncthreads();
+  // the previous step's delivery has completed: ring slot t and the counters are final
+  griddep_wait();
+  griddep_launch();
+  const int64_t t = clk[0];
+  if (blockIdx.x == 0 && threadIdx.x == 0) clk[1] = t;
   bool spk = false;
   if (valid) {
     const uint64_t slot = (uint64_t)(t & ring.L_mask);
@@ -82,34 +90,33 @@ __global__ void __launch_bounds__(kLifBlock) k_update_lif(const __grid_constant_
     I_[gid] = I;
     ref_[gid] = ref;
   }
-  emit_spikes(spk, gid, 1u, t, src_meta, sb);
+  emit_spikes(spk, gid, 1u, t, meta, sb);
 }
 
 cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, const uint32_t* thr, float* y,
                               float* I, int32_t* ref, Ring ring, bool fixed, int64_t* clk, const uint4* src_meta,
-                              SpikeBuf sb, cudaStream_t st) {
+                              SpikeBuf sb, bool pdl, cudaStream_t st) {
   if (blocks <= 0) return cudaSuccess;
-  if (fixed)
-    k_update_lif<true><<<(unsigned)blocks, kLifBlock, 0, st>>>(segs, thr, y, I, ref, ring, clk, src_meta, sb);
-  else
-    k_update_lif<false><<<(unsigned)blocks, kLifBlock, 0, st>>>(segs, thr, y, I, ref, ring, clk, src_meta, sb);
-  return cudaGetLastError();
+  const dim3 g((unsigned)blocks), b(kLifBlock);
+  if (fixed) return launch_k(k_update_lif<true>, g, b, pdl, st, segs, thr, y, I, ref, ring, clk, src_meta, sb);
+  return launch_k(k_update_lif<false>, g, b, pdl, st, segs, thr, y, I, ref, ring, clk, src_meta, sb);
 }
 
 // ------------------------------------------------------------------ source metadata
 __global__ void k_build_meta(int64_t N, const uint64_t* __restrict__ src_syn, const uint32_t* __restrict__ src_grp,
-                             uint4* __restrict__ meta) {
+                             uint4* __restrict__ meta, unsigned long long* __restrict__ total_items) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const uint64_t b = src_syn[i], e = src_syn[i + 1];
   const uint32_t g0 = src_grp[i], g1 = src_grp[i + 1];
   meta[i] = make_uint4((uint32_t)b, (uint32_t)((b >> 32) & 0xFFFFu) | ((g1 - g0) << 16), (uint32_t)(e - b), g0);
+  if (e > b) atomicAdd(total_items, (unsigned long long)((e - (b & ~3ull) + kChunk - 1) / kChunk));
 }
 
 cudaError_t launch_build_meta(int64_t N, const uint64_t* src_syn, const uint32_t* src_grp, uint4* meta,
-                              cudaStream_t st) {
+                              unsigned long long* total_items, cudaStream_t st) {
   if (N <= 0) return cudaSuccess;
-  k_build_meta<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, src_syn, src_grp, meta);
+  k_build_meta<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, src_syn, src_grp, meta, total_items);
   return cudaGetLastError();
 }
 

@@ -14,7 +14,10 @@
 // ngb_simulate) to collect the spike record and error flags.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
 #include <string>
 #include <vector>
 
@@ -137,6 +140,8 @@ struct ngb_sim {
   int64_t aeif_blocks = 0;
   uint32_t* thr = nullptr;
   int deliver_grid = 0;
+  bool pdl = true;  // programmatic dependent launch between the step's kernels
+  uint64_t work_items = 0;  // delivery work items of all sources (map capacity)
   cudaGraphExec_t gexec = nullptr;
   int graph_steps = 0;
   int drain_steps = 1000;
@@ -170,17 +175,18 @@ Csr csr_of(const ngb_sim* s) {
 
 cudaError_t launch_lif(ngb_sim* s) {
   return launch_update_lif(s->lif_tab, s->lif_blocks, s->thr, s->st0, s->st1, s->ref, ring_of(s),
-                           s->cfg.deterministic != 0, s->clk, s->src_meta, s->sb, s->stream);
+                           s->cfg.deterministic != 0, s->clk, s->src_meta, s->sb, s->pdl, s->stream);
 }
 
 cudaError_t launch_aeif(ngb_sim* s) {
   return launch_update_aeif(s->aeif_tab, s->aeif_blocks, s->thr, s->st0, s->st1, s->st2, s->st3, s->st4,
-                            ring_of(s), s->cfg.deterministic != 0, s->clk, s->src_meta, s->sb, s->stream);
+                            ring_of(s), s->cfg.deterministic != 0, s->clk, s->src_meta, s->sb, s->pdl,
+                            s->stream);
 }
 
 cudaError_t launch_del(ngb_sim* s) {
   return launch_deliver(s->sb, csr_of(s), s->cfg.weight_dtype, ring_of(s), s->cfg.deterministic != 0, s->clk,
-                        s->deliver_grid, s->stream);
+                        s->deliver_grid, s->pdl, s->stream);
 }
 
 cudaError_t launch_step(ngb_sim* s) {
@@ -221,6 +227,27 @@ int drain(ngb_sim* s) {
     return fail(NGB_ERR_OVERFLOW, "spike record overflow: raise record_capacity or lower drain_steps");
   if (err & kErrSubstepCap)
     return fail(NGB_ERR_OVERFLOW, "AdEx Runge-Kutta sub-step cap reached (rk_max_substeps)");
+  return NGB_OK;
+}
+
+// (Re)capture the CUDA graph of graph_steps steps with the current launch
+// configuration.
+int capture_graph(ngb_sim* s) {
+  if (s->gexec) {
+    cudaGraphExecDestroy(s->gexec);
+    s->gexec = nullptr;
+  }
+  if (s->graph_steps <= 0) return NGB_OK;
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < s->graph_steps && e == cudaSuccess; ++i) e = launch_step(s);
+  cudaError_t e2 = cudaStreamEndCapture(s->stream, &graph);
+  if (e != cudaSuccess) return cuda_fail(e, "graph capture (kernel launch)");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&s->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
   return NGB_OK;
 }
 
@@ -366,7 +393,17 @@ int finalize_impl(ngb_sim* s) {
     CK(s->dalloc(&s->src_grp, N + 1));
     CK(narrow_u64_to_u32(scan_out, s->src_grp, (uint64_t)N + 1, st));
     CK(s->dalloc(&s->src_meta, N));
-    CK(launch_build_meta(N, s->src_syn, s->src_grp, s->src_meta, st));
+    unsigned long long* items = nullptr;
+    CK(cudaMalloc(&items, sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(items, 0, sizeof(unsigned long long), st));
+    CK(launch_build_meta(N, s->src_syn, s->src_grp, s->src_meta, items, st));
+    unsigned long long items_h = 0;
+    CK(cudaMemcpyAsync(&items_h, items, sizeof(items_h), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    cudaFree(items);
+    s->work_items = items_h;
+    if (items_h >= (1ull << 32))
+      return fail(NGB_ERR_INVALID_ARG, "ngb_finalize: more than 2^32 delivery work items per step");
     int md = 0;
     CK(cudaMemcpyAsync(&md, dmax, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -485,6 +522,15 @@ int finalize_impl(ngb_sim* s) {
     s->lif_tab.dev = d;
     s->lif_tab.n = s->n_lif;
     for (int i = 0; i < std::min(s->n_lif, kInlineSegs); ++i) s->lif_tab.s[i] = lsegs[i];
+    std::vector<uint32_t> bs((size_t)s->lif_blocks);
+    for (size_t i = 0; i < lsegs.size(); ++i) {
+      const int64_t nb = (lsegs[i].n + kLifBlock - 1) / kLifBlock;
+      for (int64_t b = 0; b < nb; ++b) bs[(size_t)(lsegs[i].blk_begin + b)] = (uint32_t)i;
+    }
+    uint32_t* db = nullptr;
+    CK(s->dalloc(&db, bs.size()));
+    CK(cudaMemcpyAsync(db, bs.data(), bs.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    s->lif_tab.blk_seg = db;
   }
   if (s->n_aeif) {
     AeifSeg* d = nullptr;
@@ -493,16 +539,27 @@ int finalize_impl(ngb_sim* s) {
     s->aeif_tab.dev = d;
     s->aeif_tab.n = s->n_aeif;
     for (int i = 0; i < std::min(s->n_aeif, kInlineSegs); ++i) s->aeif_tab.s[i] = asegs[i];
+    std::vector<uint32_t> bs((size_t)s->aeif_blocks);
+    for (size_t i = 0; i < asegs.size(); ++i) {
+      const int64_t nb = (asegs[i].n + kAeifBlock - 1) / kAeifBlock;
+      for (int64_t b = 0; b < nb; ++b) bs[(size_t)(asegs[i].blk_begin + b)] = (uint32_t)i;
+    }
+    uint32_t* db = nullptr;
+    CK(s->dalloc(&db, bs.size()));
+    CK(cudaMemcpyAsync(db, bs.data(), bs.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    s->aeif_tab.blk_seg = db;
   }
   CK(s->dalloc(&s->thr, thr_all.size() + 1));
   if (!thr_all.empty())
     CK(cudaMemcpyAsync(s->thr, thr_all.data(), thr_all.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
 
   // ---------------------------------------------------------------- spike lists and record
-  CK(s->dalloc(&s->sb.info[0], 2 * N));
-  CK(s->dalloc(&s->sb.info[1], 2 * N));
-  CK(s->dalloc(&s->sb.choff[0], N));
-  CK(s->dalloc(&s->sb.choff[1], N));
+  CK(s->dalloc(&s->sb.wi[0], 2 * s->work_items + 2));
+  CK(s->dalloc(&s->sb.wi[1], 2 * s->work_items + 2));
+  {
+    const char* env = std::getenv("NGB_PDL");
+    s->pdl = !(env && env[0] == '0');
+  }
   unsigned long long* ctrs = nullptr;
   CK(s->dalloc(&ctrs, 6));  // ctr[2], events, substeps, rec_count, spare
   CK(cudaMemsetAsync(ctrs, 0, 6 * sizeof(unsigned long long), st));
@@ -532,17 +589,9 @@ int finalize_impl(ngb_sim* s) {
 
   // ---------------------------------------------------------------- step graph
   s->graph_steps = s->cfg.steps_per_graph == 0 ? 100 : std::max(0, s->cfg.steps_per_graph);
-  if (s->graph_steps > 0) {
-    cudaGraph_t graph = nullptr;
-    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
-    for (int i = 0; i < s->graph_steps && e == cudaSuccess; ++i) e = launch_step(s);
-    cudaError_t e2 = cudaStreamEndCapture(st, &graph);
-    if (e != cudaSuccess) return cuda_fail(e, "graph capture (kernel launch)");
-    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&s->gexec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  {
+    const int rc = capture_graph(s);
+    if (rc != NGB_OK) return rc;
   }
   s->finalized = true;
   return NGB_OK;
@@ -632,6 +681,57 @@ int simulate_impl(ngb_sim* s, int64_t steps, bool profiled, double* kernel_ms, i
 }
 
 bool valid_dist(const ngb_dist_spec& d) { return d.dist >= NGB_DIST_CONST && d.dist <= NGB_DIST_UNIFORM; }
+
+// Device state that a simulated step changes: neuron state, ring buffer,
+// counters and the step clock.  Saved and restored around autotuning trials.
+struct Snapshot {
+  std::vector<std::pair<void*, size_t>> parts;
+  std::vector<void*> copies;
+};
+
+int snapshot_take(ngb_sim* s, Snapshot& sn) {
+  const int64_t N = s->N;
+  const size_t ring_bytes = (size_t)s->L * s->R * N * (s->cfg.deterministic ? 8 : 4);
+  sn.parts = {{s->st0, N * 4}, {s->st1, N * 4}, {s->ref, N * 4}, {s->ring, ring_bytes},
+              {s->sb.ctr, 6 * sizeof(unsigned long long)}, {s->clk, 2 * sizeof(int64_t)},
+              {s->sb.err, sizeof(uint32_t)}};
+  if (s->st2) {
+    sn.parts.push_back({s->st2, N * 4});
+    sn.parts.push_back({s->st3, N * 4});
+    sn.parts.push_back({s->st4, N * 4});
+  }
+  for (auto& p : sn.parts) {
+    void* c = nullptr;
+    CK(cudaMalloc(&c, p.second));
+    sn.copies.push_back(c);
+    CK(cudaMemcpyAsync(c, p.first, p.second, cudaMemcpyDeviceToDevice, s->stream));
+  }
+  return NGB_OK;
+}
+
+int snapshot_restore(ngb_sim* s, const Snapshot& sn) {
+  for (size_t i = 0; i < sn.parts.size(); ++i)
+    CK(cudaMemcpyAsync(sn.parts[i].first, sn.copies[i], sn.parts[i].second, cudaMemcpyDeviceToDevice, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return NGB_OK;
+}
+
+void snapshot_free(Snapshot& sn) {
+  for (void* c : sn.copies) cudaFree(c);
+  sn.copies.clear();
+}
+
+std::string tune_key(ngb_sim* s) {
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, s->cfg.device);
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), "%s|sm%d|N%lld|K%llu|G%llu|L%lld|R%d|w%d|det%d|lif%d|aeif%d", prop.name,
+                prop.multiProcessorCount, (long long)s->N, (unsigned long long)s->K, (unsigned long long)s->G,
+                (long long)s->L, s->R, s->cfg.weight_dtype, s->cfg.deterministic, s->n_lif, s->n_aeif);
+  for (char* c = buf; *c; ++c)
+    if (*c == ' ') *c = '_';
+  return buf;
+}
 
 }  // namespace
 
@@ -793,6 +893,84 @@ int ngb_simulate_profiled(ngb_sim* s, int64_t steps, double* kernel_ms, int64_t*
   return simulate_impl(s, steps, true, kernel_ms, launches);
 }
 
+int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
+  int rc = check_handle(s);
+  if (rc != NGB_OK) return rc;
+  if (trial_steps < 0) return fail(NGB_ERR_INVALID_ARG, "ngb_autotune: trial_steps < 0");
+  if (!s->finalized) {
+    rc = finalize_impl(s);
+    if (rc != NGB_OK) {
+      s->failed = true;
+      return rc;
+    }
+  }
+  if (trial_steps == 0) trial_steps = 500;
+  int dev = 0, sms = 1;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const std::string key = tune_key(s);
+  const char* cache = std::getenv("NGB_AUTOTUNE_CACHE");
+  if (cache && *cache) {
+    std::ifstream in(cache);
+    std::string k;
+    int g = 0;
+    while (in >> k >> g) {
+      if (k == key && g > 0) {
+        s->deliver_grid = g;
+        rc = capture_graph(s);
+        if (rc == NGB_OK && deliver_grid_out) *deliver_grid_out = g;
+        return rc;
+      }
+    }
+  }
+  Snapshot sn;
+  rc = snapshot_take(s, sn);
+  if (rc != NGB_OK) {
+    snapshot_free(sn);
+    return rc;
+  }
+  const int per_sm[] = {1, 2, 4, 8};
+  const int saved_graph_steps = s->graph_steps;
+  if (s->graph_steps <= 0) s->graph_steps = 100;
+  int best = s->deliver_grid;
+  float best_ms = 1e30f;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int b : per_sm) {
+    s->deliver_grid = b * sms;
+    rc = capture_graph(s);
+    if (rc == NGB_OK) rc = snapshot_restore(s, sn);
+    if (rc != NGB_OK) break;
+    const int64_t reps = std::max<int64_t>(1, trial_steps / s->graph_steps);
+    CK(cudaGraphLaunch(s->gexec, s->stream));  // warm-up replay
+    CK(cudaEventRecord(e0, s->stream));
+    for (int64_t r = 0; r < reps; ++r) CK(cudaGraphLaunch(s->gexec, s->stream));
+    CK(cudaEventRecord(e1, s->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = s->deliver_grid;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == NGB_OK) rc = snapshot_restore(s, sn);
+  snapshot_free(sn);
+  s->graph_steps = saved_graph_steps;
+  s->deliver_grid = best;
+  if (rc == NGB_OK) rc = capture_graph(s);
+  if (rc != NGB_OK) return rc;
+  if (cache && *cache) {
+    std::ofstream out(cache, std::ios::app);
+    out << key << " " << best << "\n";
+  }
+  if (deliver_grid_out) *deliver_grid_out = best;
+  return NGB_OK;
+}
+
 int ngb_get_spikes(ngb_sim* s, int32_t pop, int64_t t0_step, int64_t t1_step, int32_t* ids, int64_t* steps,
                    int64_t capacity, int64_t* n_out) {
   if (!s || !n_out) return fail(NGB_ERR_INVALID_ARG, "ngb_get_spikes: NULL argument");
@@ -946,62 +1124,23 @@ int ngb_get_synapses(ngb_sim* s, int64_t first, int64_t n, uint32_t* tgt, uint8_
   if (!s->finalized) return fail(NGB_ERR_STATE, "ngb_get_synapses: not finalised");
   if (first < 0 || n < 0 || (uint64_t)(first + n) > s->K) return fail(NGB_ERR_INVALID_ARG, "ngb_get_synapses: range");
   if (n == 0) return NGB_OK;
-  std::vector<uint32_t> tw((size_t)n);
-  CK(cudaMemcpyAsync(tw.data(), s->tgt + first, n * sizeof(uint32_t), cudaMemcpyDeviceToHost, s->stream));
-  std::vector<uint16_t> wraw;
-  if (weight) {
-    if (s->cfg.weight_dtype == NGB_WEIGHT_FP32) {
-      CK(cudaMemcpyAsync(weight, (float*)s->w + first, n * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
-    } else {
-      wraw.resize((size_t)n);
-      CK(cudaMemcpyAsync(wraw.data(), (uint16_t*)s->w + first, n * sizeof(uint16_t), cudaMemcpyDeviceToHost,
-                         s->stream));
-    }
-  }
-  std::vector<uint64_t> gs;
-  std::vector<uint16_t> gd;
-  if (delay) {
-    gs.resize(s->G + 1);
-    gd.resize(s->G + 1);
-    CK(cudaMemcpyAsync(gs.data(), s->grp_start, (s->G + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaMemcpyAsync(gd.data(), s->grp_delay, (s->G + 1) * sizeof(uint16_t), cudaMemcpyDeviceToHost, s->stream));
-  }
-  CK(cudaStreamSynchronize(s->stream));
-  for (int64_t i = 0; i < n; ++i) {
-    if (tgt) tgt[i] = tw[(size_t)i] & 0x7FFFFFFFu;
-    if (receptor) receptor[i] = (uint8_t)(tw[(size_t)i] >> 31);
-  }
-  if (weight && s->cfg.weight_dtype != NGB_WEIGHT_FP32) {
-    for (int64_t i = 0; i < n; ++i) {
-      const uint16_t hbits = wraw[(size_t)i];
-      float f;
-      if (s->cfg.weight_dtype == NGB_WEIGHT_BF16) {
-        const uint32_t bits = (uint32_t)hbits << 16;
-        std::memcpy(&f, &bits, 4);
-      } else {  // binary16 -> binary32
-        const uint32_t sign = (uint32_t)(hbits >> 15) << 31;
-        const int ex = (hbits >> 10) & 0x1F;
-        const uint32_t man = hbits & 0x3FF;
-        double v;
-        if (ex == 0) v = std::ldexp((double)man, -24);
-        else if (ex == 31) v = man ? NAN : INFINITY;
-        else v = std::ldexp((double)(man | 0x400), ex - 25);
-        f = (float)v;
-        uint32_t bits;
-        std::memcpy(&bits, &f, 4);
-        bits |= sign;
-        std::memcpy(&f, &bits, 4);
-      }
-      weight[i] = f;
-    }
-  }
-  if (delay) {
-    for (int64_t i = 0; i < n; ++i) {
-      const uint64_t j = (uint64_t)(first + i);
-      const size_t g = (size_t)(std::upper_bound(gs.begin(), gs.begin() + s->G, j) - gs.begin()) - 1;
-      delay[i] = gd[g];
-    }
-  }
+  // decode on the device into a temporary buffer, then one copy per field
+  const size_t bytes = (size_t)n * (4 + 1 + 4 + 2) + 64;
+  uint8_t* tmp = nullptr;
+  CK(cudaMalloc(&tmp, bytes));
+  uint32_t* d_t = reinterpret_cast<uint32_t*>(tmp);
+  float* d_w = reinterpret_cast<float*>(tmp + (size_t)n * 4);
+  uint16_t* d_d = reinterpret_cast<uint16_t*>(tmp + (size_t)n * 8);
+  uint8_t* d_r = tmp + (size_t)n * 10;
+  cudaError_t e = expand_synapses((uint64_t)first, (uint64_t)n, s->tgt, s->w, s->cfg.weight_dtype, s->grp_start,
+                                  s->G, s->grp_delay, d_t, d_r, d_w, d_d, s->stream);
+  if (e == cudaSuccess && tgt) e = cudaMemcpyAsync(tgt, d_t, n * 4, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess && weight) e = cudaMemcpyAsync(weight, d_w, n * 4, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess && delay) e = cudaMemcpyAsync(delay, d_d, n * 2, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess && receptor) e = cudaMemcpyAsync(receptor, d_r, n, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "ngb_get_synapses");
   return NGB_OK;
 }
 

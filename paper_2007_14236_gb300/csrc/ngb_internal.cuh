@@ -16,11 +16,11 @@
 //   src_meta   uint4 per source {row start lo, row start hi (16 bits) | groups
 //              << 16, synapses, first group}: everything delivery needs about
 //              a spiking source, read once by the update kernel
-//   spikes     per step (double-buffered by step parity): choff[] u32 (first
-//              delivery work item of the spike), info[] 2 x uint4 per spike
-//              ({neuron | multiplicity << 26, choff, meta.x, meta.y},
-//              {meta.z, meta.w, 0, 0}) and one packed u64 counter
-//              (spikes << 38 | work items)
+//   work items per step (double-buffered by step parity): 2 x uint4 per
+//              work item of 128 synapses ({neuron | multiplicity << 26, index
+//              of the item within its source, meta.x, meta.y}, {meta.z,
+//              meta.w, 0, 0}) and one packed u64 counter (spikes << 38 |
+//              work items); capacity = the work items of all sources
 #pragma once
 
 #include <cuda_runtime.h>
@@ -70,8 +70,7 @@ struct AeifSeg {
 };
 
 struct SpikeBuf {
-  uint4* info[2];                   // 2 entries per spike
-  uint32_t* choff[2];
+  uint4* wi[2];                     // 2 entries per delivery work item
   unsigned long long* ctr;          // [2] packed per-step counters
   unsigned long long* events;       // synaptic events delivered (cumulative)
   unsigned long long* substeps;     // RK sub-steps (cumulative)
@@ -103,19 +102,18 @@ struct Ring {
 // list (Sec. 2.2 spike array, at most N entries), with one atomic per warp
 // reserving both list positions and delivery work items, plus the spike
 // record.  Every lane of the warp must call it (no early exit before it).
-// A spiking lane reads its source's metadata once and passes it on, so the
-// delivery kernel needs no further per-source lookups.
-__device__ __forceinline__ void emit_spikes(bool spk, uint32_t gid, uint32_t mult, int64_t t,
-                                            const uint4* __restrict__ src_meta, const SpikeBuf& sb) {
+// A spiking lane writes one entry per delivery work item of its source,
+// carrying the source's row and group range, so the delivery kernel maps a
+// work item to its synapses with a single load.
+__device__ __forceinline__ void emit_spikes(bool spk, uint32_t gid, uint32_t mult, int64_t t, uint4 meta,
+                                            const SpikeBuf& sb) {
   const unsigned full = 0xffffffffu;
   const unsigned ball = __ballot_sync(full, spk);
   if (ball == 0) return;
   const int lane = threadIdx.x & 31;
   uint32_t nch = 0, m = 0;
   unsigned long long nev = 0;
-  uint4 meta = make_uint4(0, 0, 0, 0);
   if (spk) {
-    meta = __ldg(src_meta + gid);
     const uint64_t b = (uint64_t)meta.x | ((uint64_t)(meta.y & 0xFFFFu) << 32);
     const uint64_t e = b + meta.z;
     if (e > b) nch = (uint32_t)((e - (b & ~3ull) + kChunk - 1) / kChunk);
@@ -148,12 +146,14 @@ __device__ __forceinline__ void emit_spikes(bool spk, uint32_t gid, uint32_t mul
   if (spk) {
     const uint32_t rank = __popc(ball & ((1u << lane) - 1u));
     const unsigned long long pos = (base >> kSpkShift) + rank;
-    uint4* const info = buf ? sb.info[1] : sb.info[0];
-    uint32_t* const choff_list = buf ? sb.choff[1] : sb.choff[0];
-    const uint32_t choff = (uint32_t)(base & kChunkMask) + inc_ch - nch;
-    choff_list[pos] = choff;
-    info[2 * pos] = make_uint4(gid | (mult << kIdBits), choff, meta.x, meta.y);
-    info[2 * pos + 1] = make_uint4(meta.z, meta.w, 0u, 0u);
+    (void)pos;
+    uint4* const wi = buf ? sb.wi[1] : sb.wi[0];
+    const uint64_t first = (base & kChunkMask) + inc_ch - nch;
+    const uint32_t word = gid | (mult << kIdBits);
+    for (uint32_t c = 0; c < nch; ++c) {
+      wi[2 * (first + c)] = make_uint4(word, c, meta.x, meta.y);
+      wi[2 * (first + c) + 1] = make_uint4(meta.z, meta.w, 0u, 0u);
+    }
     if (sb.rec_cap > 0) {
       const unsigned long long r0 = rbase + inc_m - m;
       for (uint32_t k = 0; k < m; ++k) {
@@ -168,18 +168,28 @@ __device__ __forceinline__ void emit_spikes(bool spk, uint32_t gid, uint32_t mul
   }
 }
 
+// Programmatic dependent launch (sm_90+): a kernel launched with the
+// programmatic-serialisation attribute may start while its predecessor in
+// the stream finishes; griddep_wait() blocks until the predecessor grid has
+// completed and its memory is visible, griddep_launch() lets the successor
+// start.  Without the attribute both are no-ops.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Segment tables passed by value in the kernel parameters (constant bank)
 // when they are small; otherwise the kernels read the device copy.
 constexpr int kInlineSegs = 12;
 template <typename Seg>
 struct SegTable {
   Seg s[kInlineSegs];
-  const Seg* dev;  // device copy of all segments (always valid)
+  const Seg* dev;           // device copy of all segments (always valid)
+  const uint32_t* blk_seg;  // segment of every block (used when n > kInlineSegs)
   int n;
 };
 
 // The segment owning block `blk`: binary search over blk_begin in the inline
-// copy (constant bank) or, for long tables, in the device copy.
+// copy (constant bank) or, for long tables (batched instances), the block's
+// entry of the per-block segment table.
 template <typename Seg>
 __device__ __forceinline__ Seg segment_of(const SegTable<Seg>& T, int64_t blk) {
   int lo = 0, hi = T.n;
@@ -191,27 +201,40 @@ __device__ __forceinline__ Seg segment_of(const SegTable<Seg>& T, int64_t blk) {
     }
     return T.s[lo];
   }
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (T.dev[mid].blk_begin <= blk) lo = mid;
-    else hi = mid;
-  }
-  return T.dev[lo];
+  (void)hi;
+  return T.dev[__ldg(T.blk_seg + blk)];
 }
 
 // ------------------------------------------------------------------ host side
 // Kernel launchers (one translation unit each).
 cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, const uint32_t* thr, float* y,
                               float* I, int32_t* ref, Ring ring, bool fixed, int64_t* clk, const uint4* src_meta,
-                              SpikeBuf sb, cudaStream_t st);
+                              SpikeBuf sb, bool pdl, cudaStream_t st);
 cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V,
                                float* w, float* gex, float* gin, float* h, Ring ring, bool fixed, int64_t* clk,
-                               const uint4* src_meta, SpikeBuf sb, cudaStream_t st);
-// Per-source metadata for the update kernels' spike lists.
+                               const uint4* src_meta, SpikeBuf sb, bool pdl, cudaStream_t st);
+// Per-source metadata for the update kernels' spike lists; *total_items
+// (device) receives the delivery work items of all sources together.
 cudaError_t launch_build_meta(int64_t N, const uint64_t* src_syn, const uint32_t* src_grp, uint4* meta,
-                              cudaStream_t st);
+                              unsigned long long* total_items, cudaStream_t st);
+
+// Launch `kernel` with the programmatic-serialisation attribute when pdl.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, bool pdl, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 cudaError_t launch_deliver(SpikeBuf sb, Csr csr, int wdtype, Ring ring, bool fixed, int64_t* clk, int grid,
-                           cudaStream_t st);
+                           bool pdl, cudaStream_t st);
 // Initial state of one population: V0 = mean + sd * z (z standard normal from
 // the instance's stream, purpose kPurVinit, index = instance-local id).
 // LIF (model 0): a = y = V0 - E_L.  AdEx (model 1): a = V0, b = w0, h = h0.

@@ -75,7 +75,7 @@ _lib = None
 EXPORTS = ["ngb_create", "ngb_destroy", "ngb_last_error", "ngb_add_instance", "ngb_add_population",
            "ngb_add_population_in", "ngb_connect", "ngb_finalize", "ngb_simulate", "ngb_simulate_profiled",
            "ngb_get_spikes", "ngb_get_stats", "ngb_population_range", "ngb_get_state", "ngb_get_input",
-           "ngb_get_src_ptr", "ngb_get_synapses"]
+           "ngb_get_src_ptr", "ngb_get_synapses", "ngb_autotune"]
 
 
 def lib_path() -> str:
@@ -112,6 +112,7 @@ def load(build_if_missing: bool = True):
     L.ngb_get_input.argtypes = [P, C.c_int32, C.c_int64, C.c_int64, C.c_int64, P]
     L.ngb_get_src_ptr.argtypes = [P, P]
     L.ngb_get_synapses.argtypes = [P, C.c_int64, C.c_int64, P, P, P, P]
+    L.ngb_autotune.argtypes = [P, C.c_int64, C.POINTER(C.c_int32)]
     for name in EXPORTS:
         if name not in ("ngb_last_error",):
             getattr(L, name).restype = C.c_int
@@ -210,6 +211,12 @@ class Simulator:
         n = np.zeros(3, dtype=np.int64)
         self._c(load().ngb_simulate_profiled(self.h, steps, _ptr(ms), _ptr(n)))
         return ms, n
+
+    def autotune(self, trial_steps: int = 0) -> int:
+        """Pick the delivery grid by timing graph replays; the state is restored."""
+        g = C.c_int32()
+        self._c(load().ngb_autotune(self.h, trial_steps, C.byref(g)))
+        return g.value
 
     # ---- results / introspection
     def spikes(self, pop: int = -1, t0: int = 0, t1: int = 2**62):

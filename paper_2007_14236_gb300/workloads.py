@@ -300,3 +300,15 @@ def request_net(req: Request, spec: Optional[NetSpec] = None, instance: int = 0)
         spec.conns.append(replace(c, src=c.src + base, tgt=c.tgt + base))
     spec.seeds.append(req.seed)
     return spec
+
+
+def instance_spec(spec: NetSpec, instance: int) -> NetSpec:
+    """The populations and connections of one instance of a batched spec, as a
+    standalone network with that instance's seed (same random streams)."""
+    pops = spec.instance_pops(instance)
+    remap = {p: i for i, p in enumerate(pops)}
+    one = NetSpec(name="%s_instance%d" % (spec.name, instance), dt=spec.dt, seeds=[spec.seeds[instance]],
+                  weight_dtype=spec.weight_dtype)
+    one.pops = [replace(spec.pops[p], instance=0) for p in pops]
+    one.conns = [replace(c, src=remap[c.src], tgt=remap[c.tgt]) for c in spec.conns if c.src in remap]
+    return one

@@ -1,0 +1,92 @@
+"""Full-size parity: the 77,169-neuron, 298,880,968-synapse microcircuit in the
+launch configuration bench.py times (100-step CUDA graphs, FP32 weights).
+
+* Sampled connectivity: the CSR rows of sampled sources equal the oracle's
+  rows, which it computes draw by draw without building the network.
+* Delivery at full size: after a run, the input pending in every ring slot
+  equals the FP64 sum of the weights of the recorded spikes' synapses whose
+  delay lands on that slot, within 1e-5 of the summed magnitudes (a property
+  that holds at any size).
+* Whole-network counts: per-pathway synapse totals are exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2007_14236_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mc():
+    from paper_2007_14236_gb300 import ngb
+    spec = W.microcircuit(scale=1.0, seed=1)
+    sim = ngb.from_spec(spec, steps_per_graph=100, drain_steps=10_000, record_capacity=4_000_000)
+    sim.finalize()
+    yield spec, sim
+    sim.close()
+
+
+def test_fullsize_counts(mc):
+    spec, sim = mc
+    st = sim.stats()
+    assert st["num_neurons"] == 77_169
+    assert st["num_synapses"] == 298_880_968 == spec.num_synapses()
+    sp = sim.src_ptr().astype(np.int64)
+    assert sp[-1] == st["num_synapses"] and np.all(np.diff(sp) >= 0)
+    offs = np.cumsum([0] + [p.n for p in spec.pops])
+    # out-degree of each source population = sum of its pathway counts
+    for s in range(8):
+        want = sum(c.K for c in spec.conns if c.src == s)
+        assert sp[offs[s + 1]] - sp[offs[s]] == want
+
+
+def test_fullsize_sampled_rows_match_oracle(mc):
+    spec, sim = mc
+    rng = np.random.default_rng(123)
+    srcs = np.sort(rng.choice(spec.num_neurons(), size=6, replace=False))
+    lazy = oracle.OracleNet(spec)  # not finalised: rows drawn one by one
+    rows = lazy.rows_for_sources(srcs)
+    sp = sim.src_ptr().astype(np.int64)
+    got = {k: [] for k in ("tgt", "receptor", "weight", "delay")}
+    for s in srcs:
+        g = sim.synapses(int(sp[s]), int(sp[s + 1] - sp[s]))
+        for k in got:
+            got[k].append(g[k])
+    for k in ("tgt", "receptor", "delay"):
+        assert np.array_equal(np.concatenate(got[k]), rows[k]), k
+    w = np.concatenate(got["weight"])
+    du = np.abs(w.view(np.int32).astype(np.int64) - rows["weight"].view(np.int32).astype(np.int64))
+    assert du.max(initial=0) <= 1 and np.count_nonzero(du) <= 2
+
+
+def test_fullsize_pending_inputs_equal_delivered_weights(mc):
+    spec, sim = mc
+    sim.simulate(1200)  # past the onset transient, then one full graph chunk more
+    st = sim.stats()
+    L = st["ring_slots"]
+    D = st["max_delay_steps"]
+    t_now = st["steps"]
+    ids, steps = sim.spikes(t0=t_now - D, t1=t_now)
+    assert len(ids) > 100
+    sp = sim.src_ptr().astype(np.int64)
+    N = st["num_neurons"]
+    expect = np.zeros((L, N))
+    absw = np.zeros((L, N))
+    for s in np.unique(ids):
+        n_s = int(np.count_nonzero(ids == s))
+        fired = steps[ids == s]
+        g = sim.synapses(int(sp[s]), int(sp[s + 1] - sp[s]))
+        for ts in fired:
+            arrive = ts + g["delay"].astype(np.int64)
+            keep = arrive >= t_now  # still pending
+            if not np.any(keep):
+                continue
+            off = arrive[keep] - t_now
+            np.add.at(expect, (off, g["tgt"][keep].astype(np.int64)), g["weight"][keep].astype(np.float64))
+            np.add.at(absw, (off, g["tgt"][keep].astype(np.int64)), np.abs(g["weight"][keep].astype(np.float64)))
+        del n_s
+    for off in range(0, D + 1):
+        got = sim.input(0, off).astype(np.float64)
+        assert np.all(np.abs(got - expect[off]) <= 1e-5 * absw[off] + 1e-4), off
