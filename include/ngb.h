@@ -247,6 +247,51 @@ NGB_API int ngb_get_src_ptr(ngb_sim* sim, uint64_t* src_ptr);
 NGB_API int ngb_get_synapses(ngb_sim* sim, int64_t first, int64_t n, uint32_t* tgt, uint8_t* receptor, float* weight,
                      uint16_t* delay);
 
+/* --------------------------------------------------- allocation-free entry */
+/* Device-resident CSR described by caller-owned DEVICE pointers (the layout
+ * ngb_finalize builds): src_syn[N+1] first synapse of each source,
+ * src_grp[N+1] first delay group of each source, grp_start[G+1] first synapse
+ * of each group, grp_delay[G] its delay in steps, tgt[K] target id with the
+ * receptor in bit 31, weight[K] in weight_dtype. */
+typedef struct {
+  const uint64_t* src_syn;
+  const uint32_t* src_grp;
+  const uint64_t* grp_start;
+  const uint16_t* grp_delay;
+  const uint32_t* tgt;
+  const void* weight;
+  int64_t num_neurons, num_synapses, num_groups;
+  int32_t weight_dtype;
+  int32_t pad_;
+} ngb_csr_device;
+
+/* Largest spike count one ngb_deliver_spikes_noalloc call accepts. */
+#define NGB_NOALLOC_MAX_SPIKES 4096
+
+/* Deliver the spikes of step t -- spikes[n_spikes], global source ids, a
+ * DEVICE array -- through the CSR into the DEVICE ring buffer
+ * ring[ring_slots][receptors][num_neurons] (FP32, or int64 in units of 2^-32
+ * when fixed_point is 1), adding each synapse's weight at slot
+ * (t + delay) & (ring_slots - 1), on `stream` (a cudaStream_t, NULL = the
+ * legacy default stream).  Asynchronous: returns after enqueueing.
+ *
+ * Counterpart in the paper: none -- this is a library convenience.  It exists
+ * for callers that cannot allocate device memory (a host application that
+ * owns all GPU memory through its own allocator, a plugin that is not allowed
+ * to call cudaMalloc, a latency-critical loop that must never block in the
+ * allocator): it calls no cudaMalloc, cudaFree or allocating library routine.
+ * Its working memory is a fixed array of about 150 KB compiled into the
+ * library, which every GPU that loads the library holds until the process
+ * exits; it limits a call to NGB_NOALLOC_MAX_SPIKES spikes (more is
+ * NGB_ERR_INVALID_ARG).  The first call on each device looks up that array's
+ * device address (with that device current); make that first call before any
+ * stream capture.  All calls share the array: calls whose work overlaps on
+ * the GPU (different streams, or devices sharing it) race, so serialise them.
+ * Spike ids >= num_neurons and targets outside the ring are skipped. */
+NGB_API int ngb_deliver_spikes_noalloc(const ngb_csr_device* csr, const uint32_t* spikes, int64_t n_spikes,
+                                       void* ring, int64_t ring_slots, int32_t receptors, int32_t fixed_point,
+                                       int64_t t, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -103,6 +103,11 @@ int bits_for(uint64_t n) {  // bits to represent values 0 .. n-1
 
 }  // namespace
 
+namespace ngb {
+// Error message for ngb_last_error() from other translation units.
+int set_last_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace ngb
+
 struct ngb_sim {
   ngb_sim_config cfg{};
   cudaStream_t stream = nullptr;

@@ -75,7 +75,7 @@ _lib = None
 EXPORTS = ["ngb_create", "ngb_destroy", "ngb_last_error", "ngb_add_instance", "ngb_add_population",
            "ngb_add_population_in", "ngb_connect", "ngb_finalize", "ngb_simulate", "ngb_simulate_profiled",
            "ngb_get_spikes", "ngb_get_stats", "ngb_population_range", "ngb_get_state", "ngb_get_input",
-           "ngb_get_src_ptr", "ngb_get_synapses", "ngb_autotune"]
+           "ngb_get_src_ptr", "ngb_get_synapses", "ngb_autotune", "ngb_deliver_spikes_noalloc"]
 
 
 def lib_path() -> str:
