@@ -155,6 +155,8 @@ typedef struct {
   int64_t ring_slots;   /* L, a power of two > max delay in steps */
   int64_t max_delay_steps;
   int64_t device_bytes; /* device memory held by the handle */
+  int64_t mode;         /* step loop: 0 per-step kernels in CUDA graphs, 1 persistent step kernel */
+  int64_t launch_grid;  /* blocks of the delivery kernel (mode 0) or of the persistent kernel (mode 1) */
 } ngb_stats;
 
 typedef struct ngb_sim ngb_sim;
@@ -207,13 +209,17 @@ NGB_API int ngb_simulate(ngb_sim* sim, int64_t steps);
  * AdEx update and delivery kernels; launches[3] their launch counts. */
 NGB_API int ngb_simulate_profiled(ngb_sim* sim, int64_t steps, double* kernel_ms, int64_t* launches);
 
-/* Autotune the delivery launch (blocks per SM in {1, 2, 4, 8}) by timing
- * trial_steps steps (0 = 500) of graph replays per candidate on this network;
- * the simulation state is saved before and restored after the trials, so the
- * simulation does not advance.  With the environment variable
- * NGB_AUTOTUNE_CACHE naming a file, results are looked up and appended there
- * per (GPU, network shape) key.  *deliver_grid_out (may be NULL) receives the
- * chosen grid. */
+/* Autotune the step loop on this network: the per-step kernels in CUDA
+ * graphs with the delivery kernel at 1, 2, 4 or 8 blocks per SM, and the
+ * persistent step kernel (one cooperative launch for many steps, grid
+ * barriers between its phases) at 1, 2 or 4 blocks per SM.  Each candidate is
+ * timed over trial_steps steps (0 = 500); the simulation state is saved
+ * before and restored after the trials, so the simulation does not advance.
+ * The fastest candidate is kept (see ngb_stats.mode / launch_grid).  With the
+ * environment variable NGB_AUTOTUNE_CACHE naming a file, results are looked up
+ * and appended there per (GPU, network shape) key.  *deliver_grid_out (may be
+ * NULL) receives the chosen grid.  The environment variable NGB_MODE=persistent
+ * selects the persistent kernel at finalisation without tuning. */
 NGB_API int ngb_autotune(ngb_sim* sim, int64_t trial_steps, int32_t* deliver_grid_out);
 
 /* Spikes recorded in steps [t0_step, t1_step) of population `pop` (-1 = all,

@@ -1,0 +1,147 @@
+// deliver_item.cuh -- delivery of one work item (128 consecutive synapses of
+// one spiking source) into the ring buffer; shared by the per-step delivery
+// kernel and the persistent step kernel.
+//
+// The warp reads 4 target words (one 16-byte load) and 4 weights (16 or 8
+// bytes) per lane, holds the source's delay groups (up to 64) in registers,
+// two per lane, finds each synapse's group with ballots over the group starts
+// (a table search for sources with more groups), and issues one
+// red.global.add per synapse at ring slot (t + d) & (L - 1): FP32, or int64
+// fixed point (units of 2^-32) in deterministic mode.  Every lane of the warp
+// must call it with the same work item.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "ngb_internal.cuh"
+
+namespace ngb {
+
+template <typename WT>
+struct W4;
+template <>
+struct W4<float> {
+  static __device__ __forceinline__ void load(const void* w, uint64_t j, float out[4]) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(reinterpret_cast<const float*>(w) + j));
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+  }
+};
+template <>
+struct W4<__nv_bfloat16> {
+  static __device__ __forceinline__ void load(const void* w, uint64_t j, float out[4]) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const __nv_bfloat16*>(w) + j));
+    out[0] = __uint_as_float(v.x << 16);
+    out[1] = __uint_as_float(v.x & 0xFFFF0000u);
+    out[2] = __uint_as_float(v.y << 16);
+    out[3] = __uint_as_float(v.y & 0xFFFF0000u);
+  }
+};
+template <>
+struct W4<__half> {
+  static __device__ __forceinline__ void load(const void* w, uint64_t j, float out[4]) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(reinterpret_cast<const __half*>(w) + j));
+    const __half2 a = *reinterpret_cast<const __half2*>(&v.x);
+    const __half2 b = *reinterpret_cast<const __half2*>(&v.y);
+    const float2 fa = __half22float2(a), fb = __half22float2(b);
+    out[0] = fa.x; out[1] = fa.y; out[2] = fb.x; out[3] = fb.y;
+  }
+};
+
+constexpr uint32_t kWindow = 64;  // delay groups a warp holds in registers
+
+// a, m2: the work item's two entries ({source | multiplicity << 26, index of
+// the item within the source, row start lo, row start hi | groups << 16},
+// {synapses, first group, -, -}).
+template <typename WT, bool kFixed>
+__device__ __forceinline__ void deliver_work_item(const uint4 a, const uint4 m2, const int64_t t, const Csr& csr,
+                                                  const Ring& ring, const int lane) {
+  const unsigned full = 0xffffffffu;
+  const uint32_t mult = a.x >> kIdBits;
+  const uint32_t local = a.y;
+  const uint64_t b = (uint64_t)a.z | ((uint64_t)(a.w & 0xFFFFu) << 32);
+  const uint64_t e = b + m2.x;
+  const uint32_t ngrp = a.w >> 16;
+  const uint32_t glo = m2.y;
+  const uint64_t cbase = (b & ~3ull) + (uint64_t)local * kChunk;
+  const uint64_t j0 = cbase + (uint64_t)lane * 4;
+  const bool any = j0 < e && j0 + 4 > b;
+  uint4 tv = make_uint4(0, 0, 0, 0);
+  float wv[4] = {0.f, 0.f, 0.f, 0.f};
+  if (any) {
+    tv = __ldg(reinterpret_cast<const uint4*>(csr.tgt + j0));
+    W4<WT>::load(csr.w, j0, wv);
+  }
+  uint32_t g[4];
+  uint32_t dA = 0, dB = 0;
+  if (ngrp <= kWindow) {
+    // the source's delay groups, two per lane: starts and delays in registers
+    uint64_t sA = ~0ull, sB = ~0ull;
+    if ((uint32_t)lane < ngrp) {
+      sA = __ldg(csr.grp_start + glo + lane);
+      dA = __ldg(csr.grp_delay + glo + lane);
+    }
+    if ((uint32_t)lane + 32 < ngrp) {
+      sB = __ldg(csr.grp_start + glo + 32 + lane);
+      dB = __ldg(csr.grp_delay + glo + 32 + lane);
+    }
+    const uint64_t jf = cbase > b ? cbase : b;             // first synapse of the work item
+    const uint64_t jl = cbase + kChunk < e ? cbase + kChunk : e;
+    // group of jf = (starts <= jf) - 1; the starts are sorted
+    const uint32_t gf = __popc(__ballot_sync(full, sA <= jf)) + __popc(__ballot_sync(full, sB <= jf)) - 1;
+    g[0] = g[1] = g[2] = g[3] = gf;
+    // group boundaries strictly inside the work item
+    for (unsigned mA = __ballot_sync(full, sA > jf && sA < jl); mA; mA &= mA - 1) {
+      const uint64_t bk = __shfl_sync(full, sA, __ffs(mA) - 1);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) g[q] += (j0 + q >= bk) ? 1u : 0u;
+    }
+    for (unsigned mB = __ballot_sync(full, sB > jf && sB < jl); mB; mB &= mB - 1) {
+      const uint64_t bk = __shfl_sync(full, sB, __ffs(mB) - 1);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) g[q] += (j0 + q >= bk) ? 1u : 0u;
+    }
+  } else {
+    // many delay groups: search the group table in memory
+    const uint64_t jf = cbase > b ? cbase : b;
+    uint32_t l = glo, h = glo + ngrp;
+    while (h - l > 1) {
+      const uint32_t mid = (l + h) >> 1;
+      if (__ldg(csr.grp_start + mid) <= jf) l = mid;
+      else h = mid;
+    }
+    uint32_t gg = l;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint64_t j = j0 + q;
+      if (any && j >= jf && j < e)
+        while (gg + 1 < glo + ngrp && __ldg(csr.grp_start + gg + 1) <= j) ++gg;
+      g[q] = gg - glo;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    uint32_t d;
+    if (ngrp <= kWindow) {
+      const uint32_t xa = __shfl_sync(full, dA, g[q] & 31u);
+      const uint32_t xb = __shfl_sync(full, dB, g[q] & 31u);
+      d = g[q] < 32u ? xa : xb;
+    } else {
+      d = __ldg(csr.grp_delay + glo + g[q]);
+    }
+    const uint64_t j = j0 + q;
+    if (!any || j < b || j >= e) continue;
+    const uint32_t twq = q == 0 ? tv.x : q == 1 ? tv.y : q == 2 ? tv.z : tv.w;
+    const uint64_t slot = (uint64_t)((t + d) & ring.L_mask);
+    const uint32_t r = twq >> 31;
+    const uint64_t idx = (slot * (uint64_t)ring.R + r) * (uint64_t)ring.N + (twq & 0x7FFFFFFFu);
+    if (kFixed) {
+      const long long qv = __float2ll_rn(wv[q] * 4294967296.0f) * (long long)mult;
+      atomicAdd(reinterpret_cast<unsigned long long*>(ring.p) + idx, (unsigned long long)qv);
+    } else {
+      const float v = mult == 1u ? wv[q] : wv[q] * (float)mult;
+      atomicAdd(reinterpret_cast<float*>(ring.p) + idx, v);
+    }
+  }
+}
+
+}  // namespace ngb

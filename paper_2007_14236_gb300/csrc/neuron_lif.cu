@@ -19,8 +19,7 @@
 //   5. joins the warp-ballot compaction of the new spikes.
 // All FP32 arithmetic uses explicit round-to-nearest intrinsics, so no FMA
 // contraction changes the result: V and I are a fixed function of the input.
-#include "ngb_internal.cuh"
-#include "philox.cuh"
+#include "neuron_step.cuh"
 
 namespace ngb {
 
@@ -56,36 +55,12 @@ __global__ void __launch_bounds__(kLifBlock) k_update_lif(const __grid_constant_
   bool spk = false;
   if (valid) {
     const uint64_t slot = (uint64_t)(t & ring.L_mask);
-    const uint64_t idx = slot * (uint64_t)ring.R * (uint64_t)ring.N + gid;
-    float in;
-    if (kFixed) {
-      long long* rp = reinterpret_cast<long long*>(ring.p) + idx;
-      const long long v = *rp;
-      *rp = 0;
-      in = __double2float_rn(__dmul_rn(__ll2double_rn(v), 2.3283064365386963e-10));  // x 2^-32
-    } else {
-      float* rp = reinterpret_cast<float*>(ring.p) + idx;
-      in = *rp;
-      *rp = 0.0f;
-    }
+    float in = ring_take<kFixed, false>(ring.p, slot * (uint64_t)ring.R * (uint64_t)ring.N + gid);
     if (sg.n_thr > 0) {
-      const int64_t tl = t - sg.t0;
-      const U4 r = draw4(sg.seed, (uint64_t)tl, kPurPoisson, 0u, sg.local_off + (uint32_t)k);
-      uint32_t kp = 0;
-      while (kp < sg.n_thr && r.x >= s_thr[kp]) ++kp;
+      const uint32_t kp = poisson_count(sg.seed, t - sg.t0, sg.local_off + (uint32_t)k, s_thr, sg.n_thr);
       in = __fadd_rn(in, __fmul_rn((float)kp, sg.w_ext));
     }
-    if (ref > 0) {
-      ref -= 1;
-    } else {
-      y = __fadd_rn(__fadd_rn(__fmul_rn(sg.P22, y), __fmul_rn(sg.P21, I)), sg.P20Ie);
-    }
-    I = __fadd_rn(__fmul_rn(sg.P11, I), in);
-    if (y >= sg.theta) {
-      y = sg.y_reset;
-      ref = sg.ref_steps;
-      spk = true;
-    }
+    spk = lif_step(sg, y, I, ref, in);
     y_[gid] = y;
     I_[gid] = I;
     ref_[gid] = ref;

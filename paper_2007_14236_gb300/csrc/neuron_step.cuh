@@ -1,0 +1,62 @@
+// neuron_step.cuh -- per-neuron arithmetic of one simulation step, shared by
+// the per-step update kernels and the persistent step kernel.
+//
+//  * ring_take: read the input of the step from the ring buffer and zero it
+//    (FP32, or int64 fixed point in units of 2^-32 converted once to FP32).
+//  * poisson_count: the Poisson drive of the step (Sec. 2.1 Poisson
+//    generator): the number of inverse-CDF thresholds ceil(F(k) * 2^32) not
+//    above one Philox word (key = instance seed, counter = (instance-local
+//    step, -, purpose 4, instance-local neuron)).
+//  * lif_step: exact integration of Eqs. 1-2 over one step (Sec. 2.1),
+//    threshold, reset and refractory count, with round-to-nearest intrinsics
+//    so that no FMA contraction changes the result.
+//  * aeif_integrate: Cash-Karp embedded RK45 with adaptive step over one step
+//    for Eqs. 3-5 (Sec. 2.1).
+#pragma once
+#include "ngb_internal.cuh"
+#include "philox.cuh"
+
+namespace ngb {
+
+// kCoherent: the slot may have been written by other SMs during the same
+// kernel (persistent kernel), so the load bypasses L1.
+template <bool kFixed, bool kCoherent>
+__device__ __forceinline__ float ring_take(void* ring, uint64_t idx) {
+  if (kFixed) {
+    long long* rp = reinterpret_cast<long long*>(ring) + idx;
+    const long long v = kCoherent ? __ldcg(rp) : *rp;
+    *rp = 0;
+    return __double2float_rn(__dmul_rn(__ll2double_rn(v), 2.3283064365386963e-10));  // x 2^-32
+  }
+  float* rp = reinterpret_cast<float*>(ring) + idx;
+  const float v = kCoherent ? __ldcg(rp) : *rp;
+  *rp = 0.0f;
+  return v;
+}
+
+__device__ __forceinline__ uint32_t poisson_count(uint64_t seed, int64_t tl, uint32_t sid, const uint32_t* thr,
+                                                  uint32_t n_thr) {
+  const U4 r = draw4(seed, (uint64_t)tl, kPurPoisson, 0u, sid);
+  uint32_t kp = 0;
+  while (kp < n_thr && r.x >= thr[kp]) ++kp;
+  return kp;
+}
+
+// One exact-integration step of a LIF neuron with input `in` (ring + Poisson);
+// returns whether it spiked.
+__device__ __forceinline__ bool lif_step(const LifSeg& sg, float& y, float& I, int32_t& ref, float in) {
+  if (ref > 0) {
+    ref -= 1;  // absolute refractory period: V held at V_reset
+  } else {
+    y = __fadd_rn(__fadd_rn(__fmul_rn(sg.P22, y), __fmul_rn(sg.P21, I)), sg.P20Ie);
+  }
+  I = __fadd_rn(__fmul_rn(sg.P11, I), in);
+  if (y >= sg.theta) {
+    y = sg.y_reset;
+    ref = sg.ref_steps;
+    return true;
+  }
+  return false;
+}
+
+}  // namespace ngb

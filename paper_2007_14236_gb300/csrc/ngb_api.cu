@@ -146,6 +146,14 @@ struct ngb_sim {
   uint32_t* thr = nullptr;
   int deliver_grid = 0;
   bool pdl = true;  // programmatic dependent launch between the step's kernels
+  int mode = 0;     // 0: per-step kernels in CUDA graphs, 1: persistent step kernel
+  bool persist_ok = false;
+  int persist_grid = 0;
+  int persist_max_bpsm = 0;
+  size_t persist_smem = 0;
+  PersistArgs pa{};
+  unsigned* bar = nullptr;
+  uint32_t n_thr_total = 0;
   uint64_t work_items = 0;  // delivery work items of all sources (map capacity)
   cudaGraphExec_t gexec = nullptr;
   int graph_steps = 0;
@@ -207,6 +215,16 @@ cudaError_t launch_step(ngb_sim* s) {
   return launch_del(s);
 }
 
+// One persistent launch of `steps` steps.
+cudaError_t launch_persistent_chunk(ngb_sim* s, int64_t steps) {
+  cudaError_t e = cudaMemsetAsync(s->bar, 0, 4 * sizeof(unsigned), s->stream);
+  if (e != cudaSuccess) return e;
+  s->pa.steps = steps;
+  s->pa.sb = s->sb;
+  return launch_persistent(s->pa, s->cfg.deterministic != 0, s->cfg.weight_dtype, s->n_lif > 0, s->n_aeif > 0,
+                           s->persist_grid, s->persist_smem, s->stream);
+}
+
 // Collect the device spike record and error flags; resets the record.
 int drain(ngb_sim* s) {
   unsigned long long cnt = 0;
@@ -228,6 +246,10 @@ int drain(ngb_sim* s) {
   CK(cudaMemsetAsync(s->sb.rec_count, 0, sizeof(unsigned long long), s->stream));
   CK(cudaMemsetAsync(s->sb.err, 0, sizeof(uint32_t), s->stream));
   CK(cudaStreamSynchronize(s->stream));
+  if (err & kErrBarrierTimeout) {
+    s->failed = true;
+    return fail(NGB_ERR_TIMEOUT, "persistent step kernel: a grid barrier wait gave up (handle unusable)");
+  }
   if (err & kErrRecordOverflow)
     return fail(NGB_ERR_OVERFLOW, "spike record overflow: raise record_capacity or lower drain_steps");
   if (err & kErrSubstepCap)
@@ -592,6 +614,61 @@ int finalize_impl(ngb_sim* s) {
   s->deliver_grid = std::max(1, sms) * 2;
   CK(cudaStreamSynchronize(st));
 
+  // ---------------------------------------------------------------- persistent kernel set-up
+  {
+    std::vector<int64_t> lv(1, 0), av(1, 0);
+    for (const LifSeg& g : lsegs) lv.push_back(lv.back() + g.n);
+    for (const AeifSeg& g : asegs) av.push_back(av.back() + g.n);
+    int64_t *dlv = nullptr, *dav = nullptr;
+    CK(s->dalloc(&dlv, lv.size()));
+    CK(s->dalloc(&dav, av.size()));
+    CK(cudaMemcpyAsync(dlv, lv.data(), lv.size() * 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dav, av.data(), av.size() * 8, cudaMemcpyHostToDevice, st));
+    CK(s->dalloc(&s->bar, 4));
+    auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    PersistArgs& a = s->pa;
+    a.lseg = s->lif_tab.dev;
+    a.aseg = s->aeif_tab.dev;
+    a.lvoff = dlv;
+    a.avoff = dav;
+    a.thr = s->thr;
+    a.st0 = s->st0; a.st1 = s->st1; a.st2 = s->st2; a.st3 = s->st3; a.st4 = s->st4;
+    a.ref = s->ref;
+    a.src_meta = s->src_meta;
+    a.ring = ring_of(s);
+    a.csr = csr_of(s);
+    a.sb = s->sb;
+    a.clk = s->clk;
+    a.bar = s->bar;
+    a.n_lif = lv.back();
+    a.n_aeif = av.back();
+    a.n_thr = (uint32_t)thr_all.size();
+    a.n_lseg = (int32_t)lsegs.size();
+    a.n_aseg = (int32_t)asegs.size();
+    const char* env_spin = std::getenv("NGB_BARRIER_SPIN_LIMIT");
+    a.spin_limit = env_spin ? std::strtoull(env_spin, nullptr, 10) : (1ull << 24);
+    const char* env_wh = std::getenv("NGB_TEST_WITHHOLD_BLOCK");
+    a.withhold_block = env_wh ? std::atoi(env_wh) : -1;
+    a.off_aseg = (uint32_t)a16(lsegs.size() * sizeof(LifSeg));
+    a.off_lvoff = a.off_aseg + (uint32_t)a16(asegs.size() * sizeof(AeifSeg));
+    a.off_avoff = a.off_lvoff + (uint32_t)a16(lv.size() * 8);
+    a.off_thr = a.off_avoff + (uint32_t)a16(av.size() * 8);
+    s->persist_smem = a.off_thr + a16(thr_all.size() * 4);
+    s->persist_ok = false;
+    if (s->persist_smem <= 200 * 1024) {
+      int bpsm = 0;
+      if (persistent_max_blocks_per_sm(s->cfg.deterministic != 0, s->cfg.weight_dtype, s->n_lif > 0,
+                                       s->n_aeif > 0, s->persist_smem, &bpsm) == cudaSuccess && bpsm > 0) {
+        s->persist_ok = true;
+        s->persist_max_bpsm = bpsm;
+        s->persist_grid = sms * std::min(bpsm, 2);
+      }
+      cudaGetLastError();
+    }
+    const char* env_mode = std::getenv("NGB_MODE");
+    s->mode = (env_mode && std::string(env_mode) == "persistent" && s->persist_ok) ? 1 : 0;
+  }
+
   // ---------------------------------------------------------------- step graph
   s->graph_steps = s->cfg.steps_per_graph == 0 ? 100 : std::max(0, s->cfg.steps_per_graph);
   {
@@ -625,6 +702,10 @@ int simulate_impl(ngb_sim* s, int64_t steps, bool profiled, double* kernel_ms, i
     while (left > 0) {
       const int64_t chunk = std::min<int64_t>(left, s->drain_steps);
       int64_t done = 0;
+      if (s->mode == 1) {
+        CK(launch_persistent_chunk(s, chunk));
+        done = chunk;
+      }
       if (s->gexec) {
         while (chunk - done >= s->graph_steps) {
           CK(cudaGraphLaunch(s->gexec, s->stream));
@@ -918,12 +999,14 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
   if (cache && *cache) {
     std::ifstream in(cache);
     std::string k;
-    int g = 0;
-    while (in >> k >> g) {
-      if (k == key && g > 0) {
+    int m = 0, g = 0, pg = 0;
+    while (in >> k >> m >> g >> pg) {
+      if (k == key && g > 0 && (m == 0 || (s->persist_ok && pg > 0))) {
+        s->mode = m;
         s->deliver_grid = g;
+        if (pg > 0) s->persist_grid = pg;
         rc = capture_graph(s);
-        if (rc == NGB_OK && deliver_grid_out) *deliver_grid_out = g;
+        if (rc == NGB_OK && deliver_grid_out) *deliver_grid_out = m == 1 ? s->persist_grid : g;
         return rc;
       }
     }
@@ -934,15 +1017,15 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
     snapshot_free(sn);
     return rc;
   }
-  const int per_sm[] = {1, 2, 4, 8};
   const int saved_graph_steps = s->graph_steps;
   if (s->graph_steps <= 0) s->graph_steps = 100;
-  int best = s->deliver_grid;
-  float best_ms = 1e30f;
+  int best_mode = 0, best_grid = s->deliver_grid, best_pgrid = s->persist_grid;
+  double best_ms = 1e30;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  for (int b : per_sm) {
+  // per-step kernels in graphs: delivery blocks per SM
+  for (int b : {1, 2, 4, 8}) {
     s->deliver_grid = b * sms;
     rc = capture_graph(s);
     if (rc == NGB_OK) rc = snapshot_restore(s, sn);
@@ -955,9 +1038,36 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
     CK(cudaEventSynchronize(e1));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best_ms) {
-      best_ms = ms;
-      best = s->deliver_grid;
+    const double per_step = ms / (double)(reps * s->graph_steps);
+    if (per_step < best_ms) {
+      best_ms = per_step;
+      best_mode = 0;
+      best_grid = s->deliver_grid;
+    }
+  }
+  // persistent step kernel: blocks per SM
+  if (rc == NGB_OK && s->persist_ok) {
+    for (int b : {1, 2, 4}) {
+      if (b > s->persist_max_bpsm) break;
+      s->persist_grid = b * sms;
+      rc = snapshot_restore(s, sn);
+      if (rc != NGB_OK) break;
+      CK(launch_persistent_chunk(s, 100));  // warm-up
+      CK(cudaEventRecord(e0, s->stream));
+      CK(launch_persistent_chunk(s, trial_steps));
+      CK(cudaEventRecord(e1, s->stream));
+      CK(cudaEventSynchronize(e1));
+      uint32_t err = 0;
+      CK(cudaMemcpy(&err, s->sb.err, sizeof(err), cudaMemcpyDeviceToHost));
+      if (err & kErrBarrierTimeout) continue;  // never chosen; the snapshot restores the flags
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      const double per_step = ms / (double)trial_steps;
+      if (per_step < best_ms) {
+        best_ms = per_step;
+        best_mode = 1;
+        best_pgrid = s->persist_grid;
+      }
     }
   }
   cudaEventDestroy(e0);
@@ -965,14 +1075,16 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
   if (rc == NGB_OK) rc = snapshot_restore(s, sn);
   snapshot_free(sn);
   s->graph_steps = saved_graph_steps;
-  s->deliver_grid = best;
+  s->deliver_grid = best_grid;
+  s->persist_grid = best_pgrid;
+  s->mode = best_mode;
   if (rc == NGB_OK) rc = capture_graph(s);
   if (rc != NGB_OK) return rc;
   if (cache && *cache) {
     std::ofstream out(cache, std::ios::app);
-    out << key << " " << best << "\n";
+    out << key << " " << best_mode << " " << best_grid << " " << (s->persist_ok ? best_pgrid : 0) << "\n";
   }
-  if (deliver_grid_out) *deliver_grid_out = best;
+  if (deliver_grid_out) *deliver_grid_out = best_mode == 1 ? best_pgrid : best_grid;
   return NGB_OK;
 }
 
@@ -1039,6 +1151,8 @@ int ngb_get_stats(ngb_sim* s, ngb_stats* out) {
     out->ring_slots = s->L;
     out->max_delay_steps = s->max_delay;
     out->device_bytes = (int64_t)s->dev_bytes;
+    out->mode = s->mode;
+    out->launch_grid = s->mode == 1 ? s->persist_grid : s->deliver_grid;
   }
   return NGB_OK;
 }

@@ -41,6 +41,7 @@ constexpr uint32_t kRcptBit = 0x80000000u;
 // error flags (device word)
 constexpr uint32_t kErrRecordOverflow = 1u;
 constexpr uint32_t kErrSubstepCap = 2u;
+constexpr uint32_t kErrBarrierTimeout = 4u;
 
 // random-stream purposes: counter word 2 = purpose | attempt << 8
 enum : uint32_t { kPurSrc = 1, kPurWeight = 2, kPurDelay = 3, kPurPoisson = 4, kPurVinit = 5 };
@@ -205,6 +206,29 @@ __device__ __forceinline__ Seg segment_of(const SegTable<Seg>& T, int64_t blk) {
   return T.dev[__ldg(T.blk_seg + blk)];
 }
 
+// Arguments of the persistent step kernel (persistent.cu).
+struct PersistArgs {
+  const LifSeg* lseg;
+  const AeifSeg* aseg;
+  const int64_t* lvoff;  // [n_lseg + 1] first LIF-only index of each LIF segment
+  const int64_t* avoff;  // [n_aseg + 1]
+  const uint32_t* thr;
+  float *st0, *st1, *st2, *st3, *st4;
+  int32_t* ref;
+  const uint4* src_meta;
+  Ring ring;
+  Csr csr;
+  SpikeBuf sb;
+  int64_t* clk;
+  unsigned* bar;  // [0] arrivals, [1] generation, [2] abort
+  int64_t n_lif, n_aeif, steps;
+  unsigned long long spin_limit;
+  uint32_t n_thr;
+  int32_t n_lseg, n_aseg;
+  int32_t withhold_block;  // test hook: this block never arrives at the first barrier (-1: none)
+  uint32_t off_aseg, off_lvoff, off_avoff, off_thr;  // dynamic shared memory layout
+};
+
 // ------------------------------------------------------------------ host side
 // Kernel launchers (one translation unit each).
 cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, const uint32_t* thr, float* y,
@@ -213,6 +237,10 @@ cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, cons
 cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V,
                                float* w, float* gex, float* gin, float* h, Ring ring, bool fixed, int64_t* clk,
                                const uint4* src_meta, SpikeBuf sb, bool pdl, cudaStream_t st);
+cudaError_t persistent_max_blocks_per_sm(bool fixed, int wdtype, bool lif, bool aeif, size_t smem, int* out);
+cudaError_t launch_persistent(const PersistArgs& a, bool fixed, int wdtype, bool lif, bool aeif, int grid,
+                              size_t smem, cudaStream_t st);
+
 // Per-source metadata for the update kernels' spike lists; *total_items
 // (device) receives the delivery work items of all sources together.
 cudaError_t launch_build_meta(int64_t N, const uint64_t* src_syn, const uint32_t* src_grp, uint4* meta,

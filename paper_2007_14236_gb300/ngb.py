@@ -66,7 +66,8 @@ class SynSpec(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("steps", "spikes", "events", "rk_substeps", "num_neurons", "num_synapses",
-                                         "num_groups", "ring_slots", "max_delay_steps", "device_bytes")]
+                                         "num_groups", "ring_slots", "max_delay_steps", "device_bytes", "mode",
+                                         "launch_grid")]
 
 
 _lib = None

@@ -1,0 +1,119 @@
+"""Persistent step kernel (many steps per cooperative launch, grid barriers
+between the update and delivery phases) against the per-step kernels, and
+the bounded barrier wait.
+
+* Deterministic mode: the persistent kernel gives bit-identical spike trains
+  and state to the per-step path (LIF, AdEx, batched instances), and to the
+  oracle.
+* Autotuning (which times both step loops on a snapshot) leaves the
+  simulation where it was.
+* A block that never arrives at a barrier (test hook) makes every wait give
+  up after its poll limit: ngb_simulate returns NGB_ERR_TIMEOUT instead of
+  hanging, and the GPU stays usable.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2007_14236_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ngb():
+    from paper_2007_14236_gb300 import ngb as m
+    m.load()
+    return m
+
+
+class _env:
+    def __init__(self, **kv):
+        self.kv = kv
+
+    def __enter__(self):
+        self.old = {k: os.environ.get(k) for k in self.kv}
+        os.environ.update({k: str(v) for k, v in self.kv.items()})
+
+    def __exit__(self, *a):
+        for k, v in self.old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def _persistent(ngb, spec, **kw):
+    with _env(NGB_MODE="persistent"):
+        sim = ngb.from_spec(spec, **kw)
+        sim.finalize()
+    assert sim.stats()["mode"] == 1
+    return sim
+
+
+@pytest.mark.parametrize("name", ["balanced_lif", "microcircuit", "adex", "batched"])
+def test_persistent_equals_per_step_kernels(ngb, name):
+    spec = {"balanced_lif": lambda: W.balanced_lif(n=1000, indegree=100, seed=1),
+            "microcircuit": lambda: W.microcircuit(scale=0.03, seed=7, keep_indegree=False),
+            "adex": lambda: W.balanced_adex(n=2000, indegree=100, seed=2, weight_dtype="fp32", poisson_weight=4.0,
+                                            w_ex=2.0, w_in=4.0),
+            "batched": lambda: W.batched_microcircuits(n_instances=3, scale_lo=0.02, scale_hi=0.04, seed=7)}[name]()
+    a = ngb.from_spec(spec, deterministic=True)
+    b = _persistent(ngb, spec, deterministic=True, drain_steps=250)
+    a.simulate(700)
+    b.simulate(300)
+    b.simulate(400)
+    ai, at = a.spikes()
+    bi, bt = b.spikes()
+    assert len(ai) > 50
+    assert np.array_equal(at, bt) and np.array_equal(ai, bi)
+    assert np.array_equal(a.state("V_m"), b.state("V_m"))
+    assert a.stats()["events"] == b.stats()["events"]
+    if name == "adex":
+        assert a.stats()["rk_substeps"] == b.stats()["rk_substeps"]
+    if name == "balanced_lif":
+        o = oracle.OracleNet(spec, deterministic=True)
+        o.simulate(700)
+        oi, ot = o.spikes()
+        assert np.array_equal(ot, bt) and np.array_equal(oi, bi)
+
+
+def test_persistent_fp32_rates(ngb):
+    spec = W.microcircuit(scale=0.05, seed=5, keep_indegree=False)
+    a = ngb.from_spec(spec)
+    b = _persistent(ngb, spec)
+    a.simulate(3000)
+    b.simulate(3000)
+    na, nb = len(a.spikes()[0]), len(b.spikes()[0])
+    assert abs(na - nb) <= 0.05 * na + 20
+
+
+def test_autotune_does_not_advance_the_simulation(ngb):
+    spec = W.microcircuit(scale=0.03, seed=3, keep_indegree=False)
+    a = ngb.from_spec(spec, deterministic=True)
+    b = ngb.from_spec(spec, deterministic=True)
+    a.simulate(200)
+    b.simulate(200)
+    grid = b.autotune(300)
+    st = b.stats()
+    assert grid > 0 and st["steps"] == 200 and st["mode"] in (0, 1)
+    a.simulate(500)
+    b.simulate(500)
+    assert np.array_equal(a.spikes()[0], b.spikes()[0]) and np.array_equal(a.spikes()[1], b.spikes()[1])
+    assert a.stats()["events"] == b.stats()["events"]
+
+
+def test_barrier_wait_is_bounded(ngb):
+    spec = W.balanced_lif(n=1000, indegree=100, seed=1)
+    with _env(NGB_TEST_WITHHOLD_BLOCK=0, NGB_BARRIER_SPIN_LIMIT=20000):
+        sim = _persistent(ngb, spec)
+    with pytest.raises(ngb.NgbError) as e:
+        sim.simulate(50)
+    assert e.value.code == -5  # NGB_ERR_TIMEOUT
+    sim.close()
+    # the GPU is still usable
+    ok = _persistent(ngb, spec, deterministic=True)
+    ok.simulate(100)
+    assert ok.stats()["steps"] == 100
