@@ -193,6 +193,34 @@ NGB_API int ngb_add_population_in(ngb_sim* sim, int32_t instance, int32_t model,
 NGB_API int ngb_connect(ngb_sim* sim, int32_t src_pop, int32_t tgt_pop, const ngb_conn_spec* conn,
                 const ngb_syn_spec* syn);
 
+/* ----------------------------------------------------- continuous batching */
+/* Make the handle a serving handle: reserve pools for max_neurons neurons,
+ * max_synapses synapses and max_groups (source, delay) connection groups, a
+ * ring of ring_slots (power of two, > every delay in steps) slots and
+ * `receptors` receptors (2 if any AdEx instance will come).  Call before the
+ * handle is finalised.  Afterwards instances may be added (ngb_add_instance,
+ * ngb_add_population_in, ngb_connect) and committed or retired between
+ * simulate calls, while the other instances keep running in the same kernels.
+ * Population ids and global neuron ids then refer to pool positions, valid
+ * once the instance is committed. */
+NGB_API int ngb_reserve(ngb_sim* sim, int64_t max_neurons, int64_t max_synapses, int64_t max_groups,
+                        int32_t ring_slots, int32_t receptors);
+
+/* Serving handles: build a pending instance's connections on the device
+ * into the pools (Sec. 2.1 rules, Sec. 2.2 groups) and make it active from
+ * the current step on (its instance-local step 0).  NGB_ERR_OOM when a pool
+ * lacks room (nothing is changed then); NGB_ERR_OVERFLOW when a delay does
+ * not fit the reserved ring. */
+NGB_API int ngb_commit_instance(ngb_sim* sim, int32_t instance);
+
+/* Serving handles: stop an active instance and return its pool ranges.  Its
+ * recorded spikes stay readable until another instance reuses the neurons. */
+NGB_API int ngb_retire_instance(ngb_sim* sim, int32_t instance);
+
+/* The step at which an instance became active and its state (0 pending,
+ * 1 active, 2 retired). */
+NGB_API int ngb_instance_info(ngb_sim* sim, int32_t instance, int64_t* t0_out, int32_t* state_out);
+
 /* Build the delay-grouped CSR on the device (Sec. 2.2 connection groups),
  * allocate state, ring buffer and spike lists, and capture the step graph.
  * Called implicitly by the first ngb_simulate. */

@@ -60,6 +60,7 @@ __device__ __forceinline__ void aeif_integrate(const AeifSeg& p, St& y, double& 
                                                unsigned long long& nsub, bool& cap_hit) {
   if (!(h > 0.0)) h = p.dt;
   double t_in = 0.0;
+  int64_t n = 0;  // sub-steps of this step (the cap applies per neuron and step)
   for (;;) {
     const double rem = p.dt - t_in;
     bool last = false;
@@ -102,7 +103,8 @@ __device__ __forceinline__ void aeif_integrate(const AeifSeg& p, St& y, double& 
     emax = fmaxf(emax, ratio_of(er.gi, y.gi, hf * k1.gi, 1e-3f));
     const double ratio = (double)emax * p.inv_tol;
     ++nsub;
-    const bool cap = nsub >= (unsigned long long)p.max_sub;
+    ++n;
+    const bool cap = n >= p.max_sub;
     if (ratio <= 1.0 || h <= p.h_min || cap) {
       y = y5;
       if (y.V >= p.V_peak) {

@@ -292,6 +292,37 @@ cudaError_t expand_synapses(uint64_t first, uint64_t n, const uint32_t* tgt, con
   return cudaGetLastError();
 }
 
+// Per-source metadata of one population placed at neurons [off, off + n):
+// cnt_scan / grp_scan are the exclusive scans (n + 1 entries) of the
+// population's per-source synapse and group counts; k_off / g_off are the
+// population's ranges in the synapse and group pools.
+__global__ void k_fill_meta(uint64_t n, uint64_t off, uint64_t k_off, uint64_t g_off,
+                            const unsigned long long* __restrict__ cnt_scan,
+                            const unsigned long long* __restrict__ grp_scan, uint4* __restrict__ meta,
+                            uint64_t* __restrict__ src_syn, uint32_t* __restrict__ src_grp,
+                            unsigned long long* __restrict__ items) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t b = k_off + cnt_scan[i];
+  const uint64_t nsyn = cnt_scan[i + 1] - cnt_scan[i];
+  const uint64_t g0 = g_off + grp_scan[i];
+  const uint64_t ng = grp_scan[i + 1] - grp_scan[i];
+  meta[off + i] = make_uint4((uint32_t)b, (uint32_t)((b >> 32) & 0xFFFFu) | ((uint32_t)ng << 16), (uint32_t)nsyn,
+                             (uint32_t)g0);
+  src_syn[off + i] = b;
+  src_grp[off + i] = (uint32_t)g0;
+  if (nsyn) atomicAdd(items, (unsigned long long)((b + nsyn - (b & ~3ull) + kChunk - 1) / kChunk));
+}
+
+cudaError_t fill_meta(uint64_t n, uint64_t off, uint64_t k_off, uint64_t g_off, const unsigned long long* cnt_scan,
+                      const unsigned long long* grp_scan, uint4* meta, uint64_t* src_syn, uint32_t* src_grp,
+                      unsigned long long* items, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_fill_meta<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, off, k_off, g_off, cnt_scan, grp_scan, meta, src_syn,
+                                                           src_grp, items);
+  return cudaGetLastError();
+}
+
 cudaError_t narrow_u64_to_u32(const unsigned long long* in, uint32_t* out, uint64_t n, cudaStream_t st) {
   k_to_u32<<<grid_for(n), 256, 0, st>>>(n, in, out);
   return cudaGetLastError();

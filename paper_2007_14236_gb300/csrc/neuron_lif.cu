@@ -77,6 +77,18 @@ cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, cons
   return launch_k(k_update_lif<false>, g, b, pdl, st, segs, thr, y, I, ref, ring, clk, src_meta, sb);
 }
 
+// Step counter hand-over when no update kernel runs (a network with no
+// active neurons): the delivery kernel reads clk[1].
+__global__ void k_tick(int64_t* clk) {
+  griddep_wait();
+  griddep_launch();
+  clk[1] = clk[0];
+}
+
+cudaError_t launch_tick(int64_t* clk, bool pdl, cudaStream_t st) {
+  return launch_k(k_tick, dim3(1), dim3(32), pdl, st, clk);
+}
+
 // ------------------------------------------------------------------ source metadata
 __global__ void k_build_meta(int64_t N, const uint64_t* __restrict__ src_syn, const uint32_t* __restrict__ src_grp,
                              uint4* __restrict__ meta, unsigned long long* __restrict__ total_items) {

@@ -47,14 +47,63 @@ int cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #expr);    \
   } while (0)
 
+// First-fit allocator of ranges in a pool (neurons, synapses, groups).
+struct RangeAlloc {
+  uint64_t cap = 0;
+  std::vector<std::pair<uint64_t, uint64_t>> free_;  // (offset, length), sorted by offset
+  void init(uint64_t c) {
+    cap = c;
+    free_.clear();
+    if (c) free_.push_back({0, c});
+  }
+  bool alloc(uint64_t n, uint64_t* off) {
+    if (n == 0) {
+      *off = 0;
+      return true;
+    }
+    for (size_t i = 0; i < free_.size(); ++i) {
+      if (free_[i].second >= n) {
+        *off = free_[i].first;
+        free_[i].first += n;
+        free_[i].second -= n;
+        if (free_[i].second == 0) free_.erase(free_.begin() + i);
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(uint64_t off, uint64_t n) {
+    if (n == 0) return;
+    auto it = std::lower_bound(free_.begin(), free_.end(), std::make_pair(off, (uint64_t)0));
+    it = free_.insert(it, {off, n});
+    size_t i = (size_t)(it - free_.begin());
+    if (i + 1 < free_.size() && free_[i].first + free_[i].second == free_[i + 1].first) {
+      free_[i].second += free_[i + 1].second;
+      free_.erase(free_.begin() + i + 1);
+    }
+    if (i > 0 && free_[i - 1].first + free_[i - 1].second == free_[i].first) {
+      free_[i - 1].second += free_[i].second;
+      free_.erase(free_.begin() + i);
+    }
+  }
+  uint64_t largest() const {
+    uint64_t m = 0;
+    for (const auto& r : free_) m = std::max(m, r.second);
+    return m;
+  }
+};
+
 struct PopHost {
   int model;
   int instance;
   int64_t n;
-  int64_t offset;      // global id of the first neuron
+  int64_t offset;      // global id of the first neuron (pool position once placed)
   uint32_t local_off;  // instance-local id of the first neuron
   ngb_lif_params lif;
   ngb_aeif_params aeif;
+  bool placed = false;           // neuron range allocated and initialised
+  uint64_t k_off = 0, k_len = 0;  // outgoing synapses in the synapse pool
+  uint64_t g_off = 0, g_len = 0;  // their delay groups in the group pool
 };
 
 struct InstHost {
@@ -62,6 +111,7 @@ struct InstHost {
   int64_t n;
   uint32_t n_calls;
   int64_t t0;
+  int state = 0;  // 0 pending, 1 active, 2 retired
 };
 
 struct CallHost {
@@ -154,6 +204,14 @@ struct ngb_sim {
   PersistArgs pa{};
   unsigned* bar = nullptr;
   uint32_t n_thr_total = 0;
+  bool serving = false;   // pools reserved by ngb_reserve; instances committed and retired while running
+  int64_t N_cap = 0;
+  uint64_t K_cap = 0, G_cap = 0;
+  RangeAlloc nalloc, kalloc, galloc;
+  bool tables_dirty = true;
+  std::vector<void*> table_allocs;  // segment and Poisson tables, rebuilt when instances change
+  int64_t n_active = 0;
+  int sms = 0;
   uint64_t work_items = 0;  // delivery work items of all sources (map capacity)
   cudaGraphExec_t gexec = nullptr;
   int graph_steps = 0;
@@ -180,7 +238,7 @@ struct ngb_sim {
 
 namespace {
 
-Ring ring_of(const ngb_sim* s) { return Ring{s->ring, s->N, (uint32_t)(s->L - 1), s->R}; }
+Ring ring_of(const ngb_sim* s) { return Ring{s->ring, s->N_cap, (uint32_t)(s->L - 1), s->R}; }
 
 Csr csr_of(const ngb_sim* s) {
   return Csr{s->src_meta, s->src_syn, s->src_grp, s->grp_start, s->grp_delay, s->tgt, s->w};
@@ -204,6 +262,10 @@ cudaError_t launch_del(ngb_sim* s) {
 
 cudaError_t launch_step(ngb_sim* s) {
   cudaError_t e;
+  if (!s->n_lif && !s->n_aeif) {
+    e = launch_tick(s->clk, s->pdl, s->stream);
+    if (e != cudaSuccess) return e;
+  }
   if (s->n_lif) {
     e = launch_lif(s);
     if (e != cudaSuccess) return e;
@@ -278,197 +340,283 @@ int capture_graph(ngb_sim* s) {
   return NGB_OK;
 }
 
-int finalize_impl(ngb_sim* s) {
-  if (s->finalized) return NGB_OK;
-  if (s->N <= 0) return fail(NGB_ERR_STATE, "ngb_finalize: no neurons");
-  if (s->N >= (int64_t)kIdMask) return fail(NGB_ERR_INVALID_ARG, "ngb_finalize: more than 2^26 neurons");
+// ---------------------------------------------------------------------------
+// Network construction into pools.  A population is placed at a neuron range
+// of the pool; its outgoing synapses occupy a range of the synapse pool and
+// their delay groups a range of the group pool.  A static network places all
+// populations in creation order at ngb_finalize (so the pools are exactly
+// full and contiguous); a serving handle (ngb_reserve) places each instance
+// when it is committed and frees its ranges when it is retired.
+// ---------------------------------------------------------------------------
+struct PopParts {
+  int pop;
+  uint64_t* gs;
+  uint16_t* gd;
+  uint64_t G;
+  unsigned long long* cnt_scan;  // n + 1
+  unsigned long long* grp_scan;  // n + 1
+};
+
+void free_parts(std::vector<PopParts>& parts) {
+  for (PopParts& q : parts) {
+    cudaFree(q.gs);
+    cudaFree(q.gd);
+    cudaFree(q.cnt_scan);
+    cudaFree(q.grp_scan);
+  }
+  parts.clear();
+}
+
+// Place the population's neurons (serving handles allocate the range) and
+// initialise their state; in a serving handle also clear their ring columns.
+int place_population(ngb_sim* s, int pi) {
+  PopHost& p = s->pops[(size_t)pi];
   cudaStream_t st = s->stream;
-  const int64_t N = s->N;
-  s->R = 1;
-  for (const PopHost& p : s->pops)
-    if (p.model == NGB_AEIF_COND_EXP) s->R = 2;
+  uint64_t off = 0;
+  if (!s->nalloc.alloc((uint64_t)p.n, &off))
+    return fail(NGB_ERR_OOM, "neuron pool full (ngb_reserve max_neurons)");
+  if (!s->serving && (int64_t)off != p.offset) return fail(NGB_ERR_STATE, "internal: population placement");
+  p.offset = (int64_t)off;
+  const uint64_t seed = s->inst[(size_t)p.instance].seed;
+  CK(cudaMemsetAsync(s->st1 + off, 0, p.n * sizeof(float), st));
+  CK(cudaMemsetAsync(s->ref + off, 0, p.n * sizeof(int32_t), st));
+  if (p.model == NGB_LIF_PSC_EXP) {
+    const ngb_lif_params& q = p.lif;
+    CK(launch_init_state(0, p.n, q.V_init_mean_mV, q.V_init_sd_mV, q.E_L_mV, 0.0, 0.0, seed, p.local_off,
+                         s->st0 + off, nullptr, nullptr, st));
+  } else {
+    const ngb_aeif_params& q = p.aeif;
+    CK(cudaMemsetAsync(s->st2 + off, 0, p.n * sizeof(float), st));
+    CK(cudaMemsetAsync(s->st3 + off, 0, p.n * sizeof(float), st));
+    CK(launch_init_state(1, p.n, q.V_init_mean_mV, q.V_init_sd_mV, q.E_L_mV, q.w_init_pA, q.rk_h_init_ms, seed,
+                         p.local_off, s->st0 + off, s->st1 + off, s->st4 + off, st));
+  }
+  if (s->serving && s->ring) {
+    const size_t es = s->cfg.deterministic ? 8 : 4;
+    CK(cudaMemset2DAsync((uint8_t*)s->ring + off * es, (size_t)s->N_cap * es, 0, (size_t)p.n * es,
+                         (size_t)(s->L * s->R), st));
+  }
+  p.placed = true;
+  return NGB_OK;
+}
+
+// Draw, sort and gather the outgoing synapses of every population of
+// `instance` (Sec. 2.1 rules, Sec. 2.2 delay groups) into the synapse pool.
+int build_instance(ngb_sim* s, int instance, std::vector<PopParts>& parts, int* max_delay_out,
+                   uint64_t* running_k) {
+  cudaStream_t st = s->stream;
   const double dt = s->cfg.dt_ms;
   const int prec = s->cfg.weight_dtype;
   const size_t wsize = prec == NGB_WEIGHT_FP32 ? 4 : 2;
-
-  // ---------------------------------------------------------------- connections
-  unsigned long long *src_cnt = nullptr, *src_ngrp = nullptr, *scan_out = nullptr;
+  std::vector<int> srcs;
+  for (size_t p = 0; p < s->pops.size(); ++p)
+    if (s->pops[p].instance == instance) srcs.push_back((int)p);
+  std::vector<std::vector<CallDev>> by_src(srcs.size());
+  std::vector<uint64_t> n_by_src(srcs.size(), 0);
+  uint64_t kmax = 0;
+  int max_bits = 1;
+  for (size_t i = 0; i < srcs.size(); ++i) {
+    const PopHost& ps = s->pops[(size_t)srcs[i]];
+    for (const CallHost& c : s->calls) {
+      if (c.src_pop != srcs[i]) continue;
+      const PopHost& pt = s->pops[(size_t)c.tgt_pop];
+      CallDev d{};
+      d.seed = s->inst[(size_t)ps.instance].seed;
+      d.K = c.conn.K;
+      d.nsyn = c.conn.rule == NGB_RULE_FIXED_INDEGREE ? (uint64_t)c.conn.K * (uint64_t)pt.n : (uint64_t)c.conn.K;
+      d.w0 = c.syn.weight.p0;
+      d.w1 = c.syn.weight.p1;
+      d.d0 = c.syn.delay_ms.p0;
+      d.d1 = c.syn.delay_ms.p1;
+      d.dt = dt;
+      d.stream = c.stream;
+      d.rule = c.conn.rule;
+      d.no_autapse = (c.src_pop == c.tgt_pop && !c.conn.allow_autapses) ? 1 : 0;
+      d.wdist = c.syn.weight.dist;
+      d.ddist = c.syn.delay_ms.dist;
+      d.receptor = c.syn.receptor;
+      d.prec = prec;
+      d.n_src = (uint32_t)ps.n;
+      d.n_tgt = (uint32_t)pt.n;
+      d.src_off = 0;  // per-population count arrays
+      d.tgt_off = (uint32_t)pt.offset;
+      by_src[i].push_back(d);
+      n_by_src[i] += d.nsyn;
+    }
+    if (n_by_src[i] >= (1ull << 32))
+      return fail(NGB_ERR_INVALID_ARG, "more than 2^32 synapses from one population");
+    kmax = std::max(kmax, n_by_src[i]);
+    max_bits = std::max(max_bits, bits_for((uint64_t)ps.n));
+  }
   int* dmax = nullptr;
-  CK(cudaMalloc(&src_cnt, (N + 1) * sizeof(unsigned long long)));
-  CK(cudaMalloc(&src_ngrp, (N + 1) * sizeof(unsigned long long)));
-  CK(cudaMalloc(&scan_out, (N + 1) * sizeof(unsigned long long)));
   CK(cudaMalloc(&dmax, sizeof(int)));
-  CK(cudaMemsetAsync(src_cnt, 0, (N + 1) * sizeof(unsigned long long), st));
-  CK(cudaMemsetAsync(src_ngrp, 0, (N + 1) * sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(dmax, 0, sizeof(int), st));
-
-  std::vector<std::vector<CallDev>> by_src(s->pops.size());
-  std::vector<uint64_t> n_by_src(s->pops.size(), 0);
-  uint64_t Kmax_pop = 0;
-  for (const CallHost& c : s->calls) {
-    const PopHost& ps = s->pops[c.src_pop];
-    const PopHost& pt = s->pops[c.tgt_pop];
-    CallDev d{};
-    d.seed = s->inst[ps.instance].seed;
-    d.K = c.conn.K;
-    d.nsyn = c.conn.rule == NGB_RULE_FIXED_INDEGREE ? (uint64_t)c.conn.K * (uint64_t)pt.n : (uint64_t)c.conn.K;
-    d.w0 = c.syn.weight.p0;
-    d.w1 = c.syn.weight.p1;
-    d.d0 = c.syn.delay_ms.p0;
-    d.d1 = c.syn.delay_ms.p1;
-    d.dt = dt;
-    d.stream = c.stream;
-    d.rule = c.conn.rule;
-    d.no_autapse = (c.src_pop == c.tgt_pop && !c.conn.allow_autapses) ? 1 : 0;
-    d.wdist = c.syn.weight.dist;
-    d.ddist = c.syn.delay_ms.dist;
-    d.receptor = c.syn.receptor;
-    d.prec = prec;
-    d.n_src = (uint32_t)ps.n;
-    d.n_tgt = (uint32_t)pt.n;
-    d.src_off = (uint32_t)ps.offset;
-    d.tgt_off = (uint32_t)pt.offset;
-    by_src[c.src_pop].push_back(d);
-    n_by_src[c.src_pop] += d.nsyn;
-  }
-  uint64_t K = 0;
-  for (size_t p = 0; p < s->pops.size(); ++p) {
-    K += n_by_src[p];
-    Kmax_pop = std::max(Kmax_pop, n_by_src[p]);
-    if (n_by_src[p] >= (1ull << 32))
-      return fail(NGB_ERR_INVALID_ARG, "ngb_finalize: more than 2^32 synapses from one population");
-  }
-  s->K = K;
-  const uint64_t Kpad = ((K + 3) & ~3ull) + kChunk;
-  CK(s->dalloc(&s->tgt, Kpad));
-  CK(s->dalloc((uint8_t**)&s->w, Kpad * wsize));
-  CK(cudaMemsetAsync(s->tgt, 0, Kpad * sizeof(uint32_t), st));
-  CK(cudaMemsetAsync(s->w, 0, Kpad * wsize, st));
-
-  std::vector<uint64_t*> gs_parts;
-  std::vector<uint16_t*> gd_parts;
-  std::vector<uint64_t> g_counts;
-  if (Kmax_pop > 0) {
-    BuildScratch sc;
-    int max_bits = 1;
-    for (size_t p = 0; p < s->pops.size(); ++p) max_bits = std::max(max_bits, bits_for((uint64_t)s->pops[p].n));
-    CK(sort_scratch_bytes(Kmax_pop, max_bits + kDelayBits, &sc.sort_bytes, &sc.scan_bytes));
-    CK(cudaMalloc(&sc.keys, Kmax_pop * sizeof(unsigned long long)));
-    CK(cudaMalloc(&sc.keys_alt, Kmax_pop * sizeof(unsigned long long)));
-    CK(cudaMalloc(&sc.vals, Kmax_pop * sizeof(uint32_t)));
-    CK(cudaMalloc(&sc.vals_alt, Kmax_pop * sizeof(uint32_t)));
-    CK(cudaMalloc(&sc.st_tgt, Kmax_pop * sizeof(uint32_t)));
-    CK(cudaMalloc(&sc.st_w, Kmax_pop * sizeof(float)));
-    CK(cudaMalloc(&sc.flag, Kmax_pop * sizeof(uint32_t)));
-    CK(cudaMalloc(&sc.gidx, Kmax_pop * sizeof(uint32_t)));
+  BuildScratch sc;
+  size_t scan_u64_bytes = 0;
+  void* scan_u64_tmp = nullptr;
+  int64_t nmax = 1;
+  for (int p : srcs) nmax = std::max<int64_t>(nmax, s->pops[(size_t)p].n);
+  CK(scan_scratch_bytes_u64((uint64_t)nmax + 1, &scan_u64_bytes));
+  CK(cudaMalloc(&scan_u64_tmp, std::max<size_t>(scan_u64_bytes, 16)));
+  if (kmax > 0) {
+    CK(sort_scratch_bytes(kmax, max_bits + kDelayBits, &sc.sort_bytes, &sc.scan_bytes));
+    CK(cudaMalloc(&sc.keys, kmax * sizeof(unsigned long long)));
+    CK(cudaMalloc(&sc.keys_alt, kmax * sizeof(unsigned long long)));
+    CK(cudaMalloc(&sc.vals, kmax * sizeof(uint32_t)));
+    CK(cudaMalloc(&sc.vals_alt, kmax * sizeof(uint32_t)));
+    CK(cudaMalloc(&sc.st_tgt, kmax * sizeof(uint32_t)));
+    CK(cudaMalloc(&sc.st_w, kmax * sizeof(float)));
+    CK(cudaMalloc(&sc.flag, kmax * sizeof(uint32_t)));
+    CK(cudaMalloc(&sc.gidx, kmax * sizeof(uint32_t)));
     CK(cudaMalloc(&sc.sort_tmp, std::max<size_t>(sc.sort_bytes, 16)));
     CK(cudaMalloc(&sc.scan_tmp, std::max<size_t>(sc.scan_bytes, 16)));
-    uint64_t csr_off = 0;
-    for (size_t p = 0; p < s->pops.size(); ++p) {
-      if (n_by_src[p] == 0) continue;
+  }
+  int rc = NGB_OK;
+  for (size_t i = 0; i < srcs.size() && rc == NGB_OK; ++i) {
+    PopHost& ps = s->pops[(size_t)srcs[i]];
+    const uint64_t n = (uint64_t)ps.n;
+    uint64_t k_off = 0;
+    if (!s->kalloc.alloc(n_by_src[i], &k_off)) {
+      rc = fail(NGB_ERR_OOM, "synapse pool full (ngb_reserve max_synapses)");
+      break;
+    }
+    if (!s->serving) k_off = *running_k;  // static pools are filled in order
+    *running_k += n_by_src[i];
+    ps.k_off = k_off;
+    ps.k_len = n_by_src[i];
+    PopParts q{srcs[i], nullptr, nullptr, 0, nullptr, nullptr};
+    unsigned long long *cnt = nullptr, *ngrp = nullptr;
+    CK(cudaMalloc(&cnt, (n + 1) * sizeof(unsigned long long)));
+    CK(cudaMalloc(&ngrp, (n + 1) * sizeof(unsigned long long)));
+    CK(cudaMalloc(&q.cnt_scan, (n + 1) * sizeof(unsigned long long)));
+    CK(cudaMalloc(&q.grp_scan, (n + 1) * sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(cnt, 0, (n + 1) * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(ngrp, 0, (n + 1) * sizeof(unsigned long long), st));
+    if (n_by_src[i] > 0) {
       std::string err;
-      uint64_t* gs = nullptr;
-      uint16_t* gd = nullptr;
-      uint64_t gcount = 0;
-      cudaError_t e = build_source_population(by_src[p], n_by_src[p], bits_for((uint64_t)s->pops[p].n), csr_off,
-                                              prec, sc, s->tgt + csr_off, (uint8_t*)s->w + csr_off * wsize, src_cnt,
-                                              src_ngrp, dmax, &gs, &gd, &gcount, st, err);
-      if (e != cudaSuccess) return cuda_fail(e, ("connection builder: " + err).c_str());
-      gs_parts.push_back(gs);
-      gd_parts.push_back(gd);
-      g_counts.push_back(gcount);
-      csr_off += n_by_src[p];
+      cudaError_t e = build_source_population(by_src[i], n_by_src[i], bits_for(n), k_off, prec, sc, s->tgt + k_off,
+                                              (uint8_t*)s->w + k_off * wsize, cnt, ngrp, dmax, &q.gs, &q.gd, &q.G,
+                                              st, err);
+      if (e != cudaSuccess) rc = cuda_fail(e, ("connection builder: " + err).c_str());
+    }
+    if (rc == NGB_OK) {
+      cudaError_t e = exclusive_scan_u64(cnt, q.cnt_scan, n + 1, scan_u64_tmp, scan_u64_bytes, st);
+      if (e == cudaSuccess) e = exclusive_scan_u64(ngrp, q.grp_scan, n + 1, scan_u64_tmp, scan_u64_bytes, st);
+      if (e != cudaSuccess) rc = cuda_fail(e, "population scans");
     }
     CK(cudaStreamSynchronize(st));
-    cudaFree(sc.keys); cudaFree(sc.keys_alt); cudaFree(sc.vals); cudaFree(sc.vals_alt);
-    cudaFree(sc.st_tgt); cudaFree(sc.st_w); cudaFree(sc.flag); cudaFree(sc.gidx);
-    cudaFree(sc.sort_tmp); cudaFree(sc.scan_tmp);
+    cudaFree(cnt);
+    cudaFree(ngrp);
+    parts.push_back(q);
   }
-  uint64_t G = 0;
-  for (uint64_t g : g_counts) G += g;
-  if (G >= (1ull << 32)) return fail(NGB_ERR_INVALID_ARG, "ngb_finalize: more than 2^32 connection groups");
-  s->G = G;
-  CK(s->dalloc(&s->grp_start, G + 1));
-  CK(s->dalloc(&s->grp_delay, G + 1));
-  {
-    uint64_t off = 0;
-    for (size_t i = 0; i < gs_parts.size(); ++i) {
-      if (g_counts[i]) {
-        CK(cudaMemcpyAsync(s->grp_start + off, gs_parts[i], g_counts[i] * sizeof(uint64_t),
-                           cudaMemcpyDeviceToDevice, st));
-        CK(cudaMemcpyAsync(s->grp_delay + off, gd_parts[i], g_counts[i] * sizeof(uint16_t),
-                           cudaMemcpyDeviceToDevice, st));
-      }
-      off += g_counts[i];
-    }
-    const uint64_t Kend = K;
-    CK(cudaMemcpyAsync(s->grp_start + G, &Kend, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-    CK(cudaStreamSynchronize(st));
-    for (size_t i = 0; i < gs_parts.size(); ++i) {
-      cudaFree(gs_parts[i]);
-      cudaFree(gd_parts[i]);
-    }
-  }
-  {
-    size_t tmp_bytes = 0;
-    CK(scan_scratch_bytes_u64((uint64_t)N + 1, &tmp_bytes));
-    void* tmp = nullptr;
-    CK(cudaMalloc(&tmp, std::max<size_t>(tmp_bytes, 16)));
-    CK(s->dalloc(&s->src_syn, N + 1));
-    CK(exclusive_scan_u64(src_cnt, (unsigned long long*)s->src_syn, (uint64_t)N + 1, tmp, tmp_bytes, st));
-    CK(exclusive_scan_u64(src_ngrp, scan_out, (uint64_t)N + 1, tmp, tmp_bytes, st));
-    CK(s->dalloc(&s->src_grp, N + 1));
-    CK(narrow_u64_to_u32(scan_out, s->src_grp, (uint64_t)N + 1, st));
-    CK(s->dalloc(&s->src_meta, N));
-    unsigned long long* items = nullptr;
-    CK(cudaMalloc(&items, sizeof(unsigned long long)));
-    CK(cudaMemsetAsync(items, 0, sizeof(unsigned long long), st));
-    CK(launch_build_meta(N, s->src_syn, s->src_grp, s->src_meta, items, st));
-    unsigned long long items_h = 0;
-    CK(cudaMemcpyAsync(&items_h, items, sizeof(items_h), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    cudaFree(items);
-    s->work_items = items_h;
-    if (items_h >= (1ull << 32))
-      return fail(NGB_ERR_INVALID_ARG, "ngb_finalize: more than 2^32 delivery work items per step");
-    int md = 0;
-    CK(cudaMemcpyAsync(&md, dmax, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    cudaFree(tmp);
-    s->max_delay = md;
-  }
-  cudaFree(src_cnt);
-  cudaFree(src_ngrp);
-  cudaFree(scan_out);
+  CK(cudaStreamSynchronize(st));
+  cudaFree(sc.keys); cudaFree(sc.keys_alt); cudaFree(sc.vals); cudaFree(sc.vals_alt);
+  cudaFree(sc.st_tgt); cudaFree(sc.st_w); cudaFree(sc.flag); cudaFree(sc.gidx);
+  cudaFree(sc.sort_tmp); cudaFree(sc.scan_tmp); cudaFree(scan_u64_tmp);
+  int md = 0;
+  CK(cudaMemcpy(&md, dmax, sizeof(int), cudaMemcpyDeviceToHost));
   cudaFree(dmax);
-  s->L = (int64_t)std::max<uint64_t>(2, next_pow2((uint64_t)s->max_delay + 1));
+  *max_delay_out = md;
+  return rc;
+}
 
-  // ---------------------------------------------------------------- state and ring
-  const size_t ring_elems = (size_t)s->L * s->R * N;
-  const size_t ring_esize = s->cfg.deterministic ? 8 : 4;
-  CK(s->dalloc((uint8_t**)&s->ring, ring_elems * ring_esize));
-  CK(cudaMemsetAsync(s->ring, 0, ring_elems * ring_esize, st));
-  CK(s->dalloc(&s->st0, N));
-  CK(s->dalloc(&s->st1, N));
-  CK(s->dalloc(&s->ref, N));
-  CK(cudaMemsetAsync(s->st1, 0, N * sizeof(float), st));
-  CK(cudaMemsetAsync(s->ref, 0, N * sizeof(int32_t), st));
-  if (s->R == 2) {
-    CK(s->dalloc(&s->st2, N));
-    CK(s->dalloc(&s->st3, N));
-    CK(s->dalloc(&s->st4, N));
-    CK(cudaMemsetAsync(s->st2, 0, N * sizeof(float), st));
-    CK(cudaMemsetAsync(s->st3, 0, N * sizeof(float), st));
+// Groups of the built populations into the group pool, and their per-source
+// metadata (row, synapse count, group range).
+int place_parts(ngb_sim* s, std::vector<PopParts>& parts, uint64_t* running_g, uint64_t* items_out) {
+  cudaStream_t st = s->stream;
+  unsigned long long* items = nullptr;
+  CK(cudaMalloc(&items, sizeof(unsigned long long)));
+  CK(cudaMemsetAsync(items, 0, sizeof(unsigned long long), st));
+  int rc = NGB_OK;
+  for (PopParts& q : parts) {
+    PopHost& p = s->pops[(size_t)q.pop];
+    uint64_t g_off = 0;
+    if (!s->galloc.alloc(q.G, &g_off)) {
+      rc = fail(NGB_ERR_OOM, "group pool full (ngb_reserve max_groups)");
+      break;
+    }
+    if (!s->serving) g_off = *running_g;
+    *running_g += q.G;
+    p.g_off = g_off;
+    p.g_len = q.G;
+    if (q.G) {
+      CK(cudaMemcpyAsync(s->grp_start + g_off, q.gs, q.G * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
+      CK(cudaMemcpyAsync(s->grp_delay + g_off, q.gd, q.G * sizeof(uint16_t), cudaMemcpyDeviceToDevice, st));
+    }
+    CK(fill_meta((uint64_t)p.n, (uint64_t)p.offset, p.k_off, g_off, q.cnt_scan, q.grp_scan, s->src_meta, s->src_syn,
+                 s->src_grp, items, st));
   }
+  unsigned long long ih = 0;
+  CK(cudaMemcpyAsync(&ih, items, sizeof(ih), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  cudaFree(items);
+  free_parts(parts);
+  if (items_out) *items_out = ih;
+  return rc;
+}
+
+void release_instance_ranges(ngb_sim* s, int instance) {
+  for (PopHost& p : s->pops) {
+    if (p.instance != instance) continue;
+    if (p.placed) s->nalloc.release((uint64_t)p.offset, (uint64_t)p.n);
+    s->kalloc.release(p.k_off, p.k_len);
+    s->galloc.release(p.g_off, p.g_len);
+    p.placed = false;
+    p.k_len = p.g_len = 0;
+  }
+}
+
+// Serving handles: place, build and activate one pending instance at the
+// current step.
+int commit_impl(ngb_sim* s, int instance) {
+  InstHost& I = s->inst[(size_t)instance];
+  if (I.state != 0) return fail(NGB_ERR_STATE, "ngb_commit_instance: instance not pending");
+  int rc = NGB_OK;
+  for (size_t p = 0; p < s->pops.size() && rc == NGB_OK; ++p)
+    if (s->pops[p].instance == instance) rc = place_population(s, (int)p);
+  std::vector<PopParts> parts;
+  int md = 0;
+  uint64_t rk = 0, rg = 0, items = 0;
+  if (rc == NGB_OK) rc = build_instance(s, instance, parts, &md, &rk);
+  if (rc == NGB_OK && md > s->L - 1) rc = fail(NGB_ERR_OVERFLOW, "a delay is beyond the reserved ring slots");
+  if (rc == NGB_OK) rc = place_parts(s, parts, &rg, &items);
+  if (rc != NGB_OK) {
+    free_parts(parts);
+    release_instance_ranges(s, instance);
+    return rc;
+  }
+  s->max_delay = std::max(s->max_delay, md);
+  I.t0 = s->t;
+  I.state = 1;
+  s->tables_dirty = true;
+  return NGB_OK;
+}
+
+// Segment tables, Poisson tables, persistent-kernel arguments and the step
+// graph for the active populations.
+int rebuild_tables(ngb_sim* s) {
+  cudaStream_t st = s->stream;
+  CK(cudaStreamSynchronize(st));
+  for (void* p : s->table_allocs) cudaFree(p);
+  s->table_allocs.clear();
+  auto talloc = [&](void** p, size_t bytes) -> cudaError_t {
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess) s->table_allocs.push_back(*p);
+    return e;
+  };
+  const double dt = s->cfg.dt_ms;
   std::vector<LifSeg> lsegs;
   std::vector<AeifSeg> asegs;
   std::vector<uint32_t> thr_all;
+  s->lif_blocks = 0;
+  s->aeif_blocks = 0;
+  s->n_active = 0;
   for (const PopHost& p : s->pops) {
-    const uint64_t seed = s->inst[p.instance].seed;
+    if (!p.placed || s->inst[(size_t)p.instance].state != 1) continue;
+    s->n_active += p.n;
+    const InstHost& I = s->inst[(size_t)p.instance];
     if (p.model == NGB_LIF_PSC_EXP) {
       const ngb_lif_params& q = p.lif;
-      CK(launch_init_state(0, p.n, q.V_init_mean_mV, q.V_init_sd_mV, q.E_L_mV, 0.0, 0.0, seed, p.local_off,
-                           s->st0 + p.offset, nullptr, nullptr, st));
       // exact-integration propagators over one step (Eqs. 1-2), y = V - E_L
       const double h = dt, tm = q.tau_m_ms, ts = q.tau_syn_ms, C = q.C_m_pF;
       const double P11 = std::exp(-h / ts);
@@ -481,8 +629,8 @@ int finalize_impl(ngb_sim* s) {
       g.offset = p.offset;
       g.n = p.n;
       g.blk_begin = s->lif_blocks;
-      g.t0 = s->inst[p.instance].t0;
-      g.seed = seed;
+      g.t0 = I.t0;
+      g.seed = I.seed;
       g.local_off = p.local_off;
       const std::vector<uint32_t> th = poisson_thresholds(q.poisson.n_inputs * q.poisson.rate_hz * dt * 1e-3);
       g.n_thr = (uint32_t)th.size();
@@ -500,14 +648,12 @@ int finalize_impl(ngb_sim* s) {
       s->lif_blocks += (p.n + kLifBlock - 1) / kLifBlock;
     } else {
       const ngb_aeif_params& q = p.aeif;
-      CK(launch_init_state(1, p.n, q.V_init_mean_mV, q.V_init_sd_mV, q.E_L_mV, q.w_init_pA, q.rk_h_init_ms, seed,
-                           p.local_off, s->st0 + p.offset, s->st1 + p.offset, s->st4 + p.offset, st));
       AeifSeg g{};
       g.offset = p.offset;
       g.n = p.n;
       g.blk_begin = s->aeif_blocks;
-      g.t0 = s->inst[p.instance].t0;
-      g.seed = seed;
+      g.t0 = I.t0;
+      g.seed = I.seed;
       g.local_off = p.local_off;
       const std::vector<uint32_t> th = poisson_thresholds(q.poisson.n_inputs * q.poisson.rate_hz * dt * 1e-3);
       g.n_thr = (uint32_t)th.size();
@@ -542,89 +688,56 @@ int finalize_impl(ngb_sim* s) {
   }
   s->n_lif = (int)lsegs.size();
   s->n_aeif = (int)asegs.size();
+  s->lif_tab = SegTable<LifSeg>{};
+  s->aeif_tab = SegTable<AeifSeg>{};
   if (s->n_lif) {
     LifSeg* d = nullptr;
-    CK(s->dalloc(&d, lsegs.size()));
+    CK(talloc((void**)&d, lsegs.size() * sizeof(LifSeg)));
     CK(cudaMemcpyAsync(d, lsegs.data(), lsegs.size() * sizeof(LifSeg), cudaMemcpyHostToDevice, st));
     s->lif_tab.dev = d;
     s->lif_tab.n = s->n_lif;
-    for (int i = 0; i < std::min(s->n_lif, kInlineSegs); ++i) s->lif_tab.s[i] = lsegs[i];
+    for (int i = 0; i < std::min(s->n_lif, kInlineSegs); ++i) s->lif_tab.s[i] = lsegs[(size_t)i];
     std::vector<uint32_t> bs((size_t)s->lif_blocks);
     for (size_t i = 0; i < lsegs.size(); ++i) {
       const int64_t nb = (lsegs[i].n + kLifBlock - 1) / kLifBlock;
       for (int64_t b = 0; b < nb; ++b) bs[(size_t)(lsegs[i].blk_begin + b)] = (uint32_t)i;
     }
     uint32_t* db = nullptr;
-    CK(s->dalloc(&db, bs.size()));
+    CK(talloc((void**)&db, bs.size() * sizeof(uint32_t)));
     CK(cudaMemcpyAsync(db, bs.data(), bs.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     s->lif_tab.blk_seg = db;
   }
   if (s->n_aeif) {
     AeifSeg* d = nullptr;
-    CK(s->dalloc(&d, asegs.size()));
+    CK(talloc((void**)&d, asegs.size() * sizeof(AeifSeg)));
     CK(cudaMemcpyAsync(d, asegs.data(), asegs.size() * sizeof(AeifSeg), cudaMemcpyHostToDevice, st));
     s->aeif_tab.dev = d;
     s->aeif_tab.n = s->n_aeif;
-    for (int i = 0; i < std::min(s->n_aeif, kInlineSegs); ++i) s->aeif_tab.s[i] = asegs[i];
+    for (int i = 0; i < std::min(s->n_aeif, kInlineSegs); ++i) s->aeif_tab.s[i] = asegs[(size_t)i];
     std::vector<uint32_t> bs((size_t)s->aeif_blocks);
     for (size_t i = 0; i < asegs.size(); ++i) {
       const int64_t nb = (asegs[i].n + kAeifBlock - 1) / kAeifBlock;
       for (int64_t b = 0; b < nb; ++b) bs[(size_t)(asegs[i].blk_begin + b)] = (uint32_t)i;
     }
     uint32_t* db = nullptr;
-    CK(s->dalloc(&db, bs.size()));
+    CK(talloc((void**)&db, bs.size() * sizeof(uint32_t)));
     CK(cudaMemcpyAsync(db, bs.data(), bs.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     s->aeif_tab.blk_seg = db;
   }
-  CK(s->dalloc(&s->thr, thr_all.size() + 1));
+  CK(talloc((void**)&s->thr, (thr_all.size() + 1) * sizeof(uint32_t)));
   if (!thr_all.empty())
     CK(cudaMemcpyAsync(s->thr, thr_all.data(), thr_all.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
 
-  // ---------------------------------------------------------------- spike lists and record
-  CK(s->dalloc(&s->sb.wi[0], 2 * s->work_items + 2));
-  CK(s->dalloc(&s->sb.wi[1], 2 * s->work_items + 2));
-  {
-    const char* env = std::getenv("NGB_PDL");
-    s->pdl = !(env && env[0] == '0');
-  }
-  unsigned long long* ctrs = nullptr;
-  CK(s->dalloc(&ctrs, 6));  // ctr[2], events, substeps, rec_count, spare
-  CK(cudaMemsetAsync(ctrs, 0, 6 * sizeof(unsigned long long), st));
-  s->sb.ctr = ctrs;
-  s->sb.events = ctrs + 2;
-  s->sb.substeps = ctrs + 3;
-  s->sb.rec_count = ctrs + 4;
-  CK(s->dalloc(&s->sb.err, 1));
-  CK(cudaMemsetAsync(s->sb.err, 0, sizeof(uint32_t), st));
-  CK(s->dalloc(&s->clk, 2));
-  CK(cudaMemsetAsync(s->clk, 0, 2 * sizeof(int64_t), st));
-  s->drain_steps = s->cfg.drain_steps > 0 ? s->cfg.drain_steps : 1000;
-  int64_t cap = 0;
-  if (s->cfg.record_spikes) {
-    cap = s->cfg.record_capacity > 0 ? s->cfg.record_capacity
-                                     : std::max<int64_t>(1 << 20, N * (int64_t)s->drain_steps / 100);
-    CK(s->dalloc(&s->sb.rec_id, cap));
-    CK(s->dalloc(&s->sb.rec_step, cap));
-  }
-  s->sb.rec_cap = cap;
-
-  int dev = 0, sms = 0;
-  CK(cudaGetDevice(&dev));
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  s->deliver_grid = std::max(1, sms) * 2;
-  CK(cudaStreamSynchronize(st));
-
-  // ---------------------------------------------------------------- persistent kernel set-up
+  // persistent kernel arguments
   {
     std::vector<int64_t> lv(1, 0), av(1, 0);
     for (const LifSeg& g : lsegs) lv.push_back(lv.back() + g.n);
     for (const AeifSeg& g : asegs) av.push_back(av.back() + g.n);
     int64_t *dlv = nullptr, *dav = nullptr;
-    CK(s->dalloc(&dlv, lv.size()));
-    CK(s->dalloc(&dav, av.size()));
+    CK(talloc((void**)&dlv, lv.size() * 8));
+    CK(talloc((void**)&dav, av.size() * 8));
     CK(cudaMemcpyAsync(dlv, lv.data(), lv.size() * 8, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(dav, av.data(), av.size() * 8, cudaMemcpyHostToDevice, st));
-    CK(s->dalloc(&s->bar, 4));
     auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
     PersistArgs& a = s->pa;
     a.lseg = s->lif_tab.dev;
@@ -654,6 +767,7 @@ int finalize_impl(ngb_sim* s) {
     a.off_avoff = a.off_lvoff + (uint32_t)a16(lv.size() * 8);
     a.off_thr = a.off_avoff + (uint32_t)a16(av.size() * 8);
     s->persist_smem = a.off_thr + a16(thr_all.size() * 4);
+    const bool was_ok = s->persist_ok;
     s->persist_ok = false;
     if (s->persist_smem <= 200 * 1024) {
       int bpsm = 0;
@@ -661,22 +775,172 @@ int finalize_impl(ngb_sim* s) {
                                        s->n_aeif > 0, s->persist_smem, &bpsm) == cudaSuccess && bpsm > 0) {
         s->persist_ok = true;
         s->persist_max_bpsm = bpsm;
-        s->persist_grid = sms * std::min(bpsm, 2);
+        if (!was_ok || s->persist_grid <= 0 || s->persist_grid > s->sms * bpsm)
+          s->persist_grid = s->sms * std::min(bpsm, 2);
       }
       cudaGetLastError();
     }
-    const char* env_mode = std::getenv("NGB_MODE");
-    s->mode = (env_mode && std::string(env_mode) == "persistent" && s->persist_ok) ? 1 : 0;
+    if (!s->persist_ok) s->mode = 0;
   }
+  s->tables_dirty = false;
+  return capture_graph(s);
+}
 
-  // ---------------------------------------------------------------- step graph
-  s->graph_steps = s->cfg.steps_per_graph == 0 ? 100 : std::max(0, s->cfg.steps_per_graph);
-  {
-    const int rc = capture_graph(s);
-    if (rc != NGB_OK) return rc;
+int finalize_impl(ngb_sim* s) {
+  if (s->finalized) return NGB_OK;
+  cudaStream_t st = s->stream;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev));
+  if (!s->serving) {
+    if (s->N <= 0) return fail(NGB_ERR_STATE, "ngb_finalize: no neurons");
+    s->R = 1;
+    for (const PopHost& p : s->pops)
+      if (p.model == NGB_AEIF_COND_EXP) s->R = 2;
+    s->N_cap = s->N;
+    uint64_t K = 0;
+    for (const CallHost& c : s->calls) {
+      const PopHost& pt = s->pops[(size_t)c.tgt_pop];
+      K += c.conn.rule == NGB_RULE_FIXED_INDEGREE ? (uint64_t)c.conn.K * (uint64_t)pt.n : (uint64_t)c.conn.K;
+    }
+    s->K_cap = K;
   }
+  if (s->N_cap >= (int64_t)kIdMask) return fail(NGB_ERR_INVALID_ARG, "ngb_finalize: more than 2^26 neurons");
+  const int64_t N = s->N_cap;
+  const size_t wsize = s->cfg.weight_dtype == NGB_WEIGHT_FP32 ? 4 : 2;
+
+  // neuron-indexed arrays
+  CK(s->dalloc(&s->st0, N));
+  CK(s->dalloc(&s->st1, N));
+  CK(s->dalloc(&s->ref, N));
+  CK(cudaMemsetAsync(s->st0, 0, N * sizeof(float), st));
+  CK(cudaMemsetAsync(s->st1, 0, N * sizeof(float), st));
+  CK(cudaMemsetAsync(s->ref, 0, N * sizeof(int32_t), st));
+  if (s->R == 2) {
+    CK(s->dalloc(&s->st2, N));
+    CK(s->dalloc(&s->st3, N));
+    CK(s->dalloc(&s->st4, N));
+    CK(cudaMemsetAsync(s->st2, 0, N * sizeof(float), st));
+    CK(cudaMemsetAsync(s->st3, 0, N * sizeof(float), st));
+    CK(cudaMemsetAsync(s->st4, 0, N * sizeof(float), st));
+  }
+  CK(s->dalloc(&s->src_syn, N + 1));
+  CK(s->dalloc(&s->src_grp, N + 1));
+  CK(s->dalloc(&s->src_meta, N));
+  CK(cudaMemsetAsync(s->src_syn, 0, (N + 1) * sizeof(uint64_t), st));
+  CK(cudaMemsetAsync(s->src_grp, 0, (N + 1) * sizeof(uint32_t), st));
+  CK(cudaMemsetAsync(s->src_meta, 0, N * sizeof(uint4), st));
+  // synapse pool (padded for the 16-byte vector loads)
+  const uint64_t Kpad = ((s->K_cap + 3) & ~3ull) + kChunk;
+  CK(s->dalloc(&s->tgt, Kpad));
+  CK(s->dalloc((uint8_t**)&s->w, Kpad * wsize));
+  CK(cudaMemsetAsync(s->tgt, 0, Kpad * sizeof(uint32_t), st));
+  CK(cudaMemsetAsync(s->w, 0, Kpad * wsize, st));
+  s->nalloc.init((uint64_t)N);
+  s->kalloc.init(s->K_cap);
+
+  // counters, clock, spike record, barrier
+  unsigned long long* ctrs = nullptr;
+  CK(s->dalloc(&ctrs, 6));  // ctr[2], events, substeps, rec_count, spare
+  CK(cudaMemsetAsync(ctrs, 0, 6 * sizeof(unsigned long long), st));
+  s->sb.ctr = ctrs;
+  s->sb.events = ctrs + 2;
+  s->sb.substeps = ctrs + 3;
+  s->sb.rec_count = ctrs + 4;
+  CK(s->dalloc(&s->sb.err, 1));
+  CK(cudaMemsetAsync(s->sb.err, 0, sizeof(uint32_t), st));
+  CK(s->dalloc(&s->clk, 2));
+  CK(cudaMemsetAsync(s->clk, 0, 2 * sizeof(int64_t), st));
+  CK(s->dalloc(&s->bar, 4));
+  s->drain_steps = s->cfg.drain_steps > 0 ? s->cfg.drain_steps : 1000;
+  int64_t cap = 0;
+  if (s->cfg.record_spikes) {
+    cap = s->cfg.record_capacity > 0 ? s->cfg.record_capacity
+                                     : std::max<int64_t>(1 << 20, N * (int64_t)s->drain_steps / 100);
+    CK(s->dalloc(&s->sb.rec_id, cap));
+    CK(s->dalloc(&s->sb.rec_step, cap));
+  }
+  s->sb.rec_cap = cap;
+  {
+    const char* env = std::getenv("NGB_PDL");
+    s->pdl = !(env && env[0] == '0');
+  }
+  s->deliver_grid = std::max(1, s->sms) * 2;
+
+  uint64_t items = 0;
+  if (!s->serving) {
+    // every population in creation order; groups sized after the build
+    for (size_t p = 0; p < s->pops.size(); ++p) {
+      const int rc = place_population(s, (int)p);
+      if (rc != NGB_OK) return rc;
+    }
+    std::vector<PopParts> parts;
+    uint64_t rk = 0;
+    int md_all = 0;
+    for (size_t i = 0; i < s->inst.size(); ++i) {
+      int md = 0;
+      const int rc = build_instance(s, (int)i, parts, &md, &rk);
+      if (rc != NGB_OK) {
+        free_parts(parts);
+        return rc;
+      }
+      md_all = std::max(md_all, md);
+    }
+    uint64_t G = 0;
+    for (const PopParts& q : parts) G += q.G;
+    if (G >= (1ull << 32)) {
+      free_parts(parts);
+      return fail(NGB_ERR_INVALID_ARG, "ngb_finalize: more than 2^32 connection groups");
+    }
+    s->G_cap = G;
+    CK(s->dalloc(&s->grp_start, G + 1));
+    CK(s->dalloc(&s->grp_delay, G + 1));
+    s->galloc.init(G);
+    uint64_t rg = 0;
+    int rc = place_parts(s, parts, &rg, &items);
+    if (rc != NGB_OK) return rc;
+    const uint64_t Kend = s->K_cap;
+    CK(cudaMemcpyAsync(s->grp_start + G, &Kend, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(s->src_syn + N, &Kend, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    const uint32_t Gend = (uint32_t)G;
+    CK(cudaMemcpyAsync(s->src_grp + N, &Gend, sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    s->max_delay = md_all;
+    s->L = (int64_t)std::max<uint64_t>(2, next_pow2((uint64_t)s->max_delay + 1));
+    for (InstHost& I : s->inst) I.state = 1;
+  } else {
+    CK(s->dalloc(&s->grp_start, s->G_cap + 1));
+    CK(s->dalloc(&s->grp_delay, s->G_cap + 1));
+    CK(cudaMemsetAsync(s->grp_start, 0, (s->G_cap + 1) * sizeof(uint64_t), st));
+    s->galloc.init(s->G_cap);
+    items = s->K_cap / kChunk + 2 * (uint64_t)N + 2;
+  }
+  s->K = s->K_cap;
+  s->G = s->G_cap;
+  if (items >= (1ull << 32)) return fail(NGB_ERR_INVALID_ARG, "ngb_finalize: more than 2^32 delivery work items");
+  s->work_items = items;
+  CK(s->dalloc(&s->sb.wi[0], 2 * s->work_items + 2));
+  CK(s->dalloc(&s->sb.wi[1], 2 * s->work_items + 2));
+  // ring buffer
+  const size_t ring_bytes = (size_t)s->L * s->R * N * (s->cfg.deterministic ? 8 : 4);
+  CK(s->dalloc((uint8_t**)&s->ring, ring_bytes));
+  CK(cudaMemsetAsync(s->ring, 0, ring_bytes, st));
+  CK(cudaStreamSynchronize(st));
   s->finalized = true;
-  return NGB_OK;
+  if (s->serving) {
+    for (size_t i = 0; i < s->inst.size(); ++i) {
+      if (s->inst[i].state != 0) continue;
+      bool has_pop = false;
+      for (const PopHost& p : s->pops) has_pop = has_pop || p.instance == (int)i;
+      if (!has_pop) continue;
+      const int rc = commit_impl(s, (int)i);
+      if (rc != NGB_OK) return rc;
+    }
+  }
+  const char* env_mode = std::getenv("NGB_MODE");
+  s->mode = (env_mode && std::string(env_mode) == "persistent") ? 1 : 0;
+  s->graph_steps = s->cfg.steps_per_graph == 0 ? 100 : std::max(0, s->cfg.steps_per_graph);
+  return rebuild_tables(s);
 }
 
 int check_handle(ngb_sim* s) {
@@ -695,6 +959,10 @@ int simulate_impl(ngb_sim* s, int64_t steps, bool profiled, double* kernel_ms, i
       s->failed = true;
       return rc;
     }
+  }
+  if (s->tables_dirty) {
+    const int rc = rebuild_tables(s);
+    if (rc != NGB_OK) return rc;
   }
   int rc_overflow = NGB_OK;
   if (!profiled) {
@@ -776,7 +1044,7 @@ struct Snapshot {
 };
 
 int snapshot_take(ngb_sim* s, Snapshot& sn) {
-  const int64_t N = s->N;
+  const int64_t N = s->N_cap;
   const size_t ring_bytes = (size_t)s->L * s->R * N * (s->cfg.deterministic ? 8 : 4);
   sn.parts = {{s->st0, N * 4}, {s->st1, N * 4}, {s->ref, N * 4}, {s->ring, ring_bytes},
               {s->sb.ctr, 6 * sizeof(unsigned long long)}, {s->clk, 2 * sizeof(int64_t)},
@@ -864,6 +1132,7 @@ int ngb_destroy(ngb_sim* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   for (void* p : s->allocs) cudaFree(p);
+  for (void* p : s->table_allocs) cudaFree(p);
   if (s->own_stream) cudaStreamDestroy(s->stream);
   delete s;
   return NGB_OK;
@@ -871,7 +1140,7 @@ int ngb_destroy(ngb_sim* s) {
 
 int ngb_add_instance(ngb_sim* s, uint64_t seed, int32_t* instance_out) {
   if (!s) return fail(NGB_ERR_INVALID_ARG, "NULL handle");
-  if (s->finalized) return fail(NGB_ERR_STATE, "ngb_add_instance: network already finalised");
+  if (s->finalized && !s->serving) return fail(NGB_ERR_STATE, "ngb_add_instance: network already finalised");
   s->inst.push_back(InstHost{seed, 0, 0, 0});
   if (instance_out) *instance_out = (int32_t)s->inst.size() - 1;
   return NGB_OK;
@@ -880,15 +1149,16 @@ int ngb_add_instance(ngb_sim* s, uint64_t seed, int32_t* instance_out) {
 int ngb_add_population_in(ngb_sim* s, int32_t instance, int32_t model, int64_t n, const void* params,
                           int32_t* pop_id_out) {
   if (!s || !params) return fail(NGB_ERR_INVALID_ARG, "ngb_add_population: NULL argument");
-  if (s->finalized) return fail(NGB_ERR_STATE, "ngb_add_population: network already finalised");
   if (instance < 0 || instance >= (int32_t)s->inst.size())
     return fail(NGB_ERR_INVALID_ARG, "ngb_add_population: unknown instance");
+  if ((s->finalized && !s->serving) || s->inst[(size_t)instance].state != 0)
+    return fail(NGB_ERR_STATE, "ngb_add_population: network (instance) already built");
   if (n <= 0 || s->N + n >= (int64_t)kIdMask) return fail(NGB_ERR_INVALID_ARG, "ngb_add_population: n");
   PopHost p{};
   p.model = model;
   p.instance = instance;
   p.n = n;
-  p.offset = s->N;
+  p.offset = s->serving ? -1 : s->N;  // serving handles place populations when the instance is committed
   p.local_off = (uint32_t)s->inst[instance].n;
   const double dt = s->cfg.dt_ms;
   double lambda = 0.0;
@@ -926,12 +1196,13 @@ int ngb_add_population(ngb_sim* s, int32_t model, int64_t n, const void* params,
 
 int ngb_connect(ngb_sim* s, int32_t src_pop, int32_t tgt_pop, const ngb_conn_spec* conn, const ngb_syn_spec* syn) {
   if (!s || !conn || !syn) return fail(NGB_ERR_INVALID_ARG, "ngb_connect: NULL argument");
-  if (s->finalized) return fail(NGB_ERR_STATE, "ngb_connect: network already finalised");
   const int32_t np = (int32_t)s->pops.size();
   if (src_pop < 0 || src_pop >= np || tgt_pop < 0 || tgt_pop >= np)
     return fail(NGB_ERR_INVALID_ARG, "ngb_connect: population id");
   const PopHost& ps = s->pops[src_pop];
   const PopHost& pt = s->pops[tgt_pop];
+  if ((s->finalized && !s->serving) || s->inst[(size_t)ps.instance].state != 0)
+    return fail(NGB_ERR_STATE, "ngb_connect: network (instance) already built");
   if (ps.instance != pt.instance) return fail(NGB_ERR_INVALID_ARG, "ngb_connect: populations of different instances");
   if (conn->rule != NGB_RULE_FIXED_INDEGREE && conn->rule != NGB_RULE_FIXED_TOTAL_NUMBER)
     return fail(NGB_ERR_INVALID_ARG, "ngb_connect: rule");
@@ -1088,6 +1359,69 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
   return NGB_OK;
 }
 
+int ngb_reserve(ngb_sim* s, int64_t max_neurons, int64_t max_synapses, int64_t max_groups, int32_t ring_slots,
+                int32_t receptors) {
+  if (!s) return fail(NGB_ERR_INVALID_ARG, "NULL handle");
+  if (s->finalized) return fail(NGB_ERR_STATE, "ngb_reserve: network already finalised");
+  if (max_neurons <= 0 || max_neurons >= (int64_t)kIdMask || max_synapses < 0 || max_groups < 0 ||
+      ring_slots < 2 || ring_slots > 4096 || (ring_slots & (ring_slots - 1)) != 0 || receptors < 1 ||
+      receptors > 2)
+    return fail(NGB_ERR_INVALID_ARG, "ngb_reserve: capacities");
+  if (max_neurons < s->N) return fail(NGB_ERR_INVALID_ARG, "ngb_reserve: fewer neurons than already added");
+  for (const PopHost& p : s->pops)
+    if (p.model == NGB_AEIF_COND_EXP && receptors < 2)
+      return fail(NGB_ERR_INVALID_ARG, "ngb_reserve: AdEx populations need two receptors");
+  s->serving = true;
+  s->N_cap = max_neurons;
+  s->K_cap = (uint64_t)max_synapses;
+  s->G_cap = (uint64_t)max_groups;
+  s->L = ring_slots;
+  s->R = receptors;
+  for (PopHost& p : s->pops) p.offset = -1;
+  return NGB_OK;
+}
+
+int ngb_commit_instance(ngb_sim* s, int32_t instance) {
+  int rc = check_handle(s);
+  if (rc != NGB_OK) return rc;
+  if (!s->serving) return fail(NGB_ERR_STATE, "ngb_commit_instance: needs ngb_reserve before finalising");
+  if (instance < 0 || instance >= (int32_t)s->inst.size())
+    return fail(NGB_ERR_INVALID_ARG, "ngb_commit_instance: instance");
+  for (const PopHost& p : s->pops)
+    if (p.instance == instance && p.model == NGB_AEIF_COND_EXP && s->R < 2)
+      return fail(NGB_ERR_INVALID_ARG, "ngb_commit_instance: AdEx needs two receptors");
+  if (!s->finalized) {
+    rc = finalize_impl(s);
+    if (rc != NGB_OK) {
+      s->failed = true;
+      return rc;
+    }
+    return s->inst[(size_t)instance].state == 1 ? NGB_OK : commit_impl(s, instance);
+  }
+  return commit_impl(s, instance);
+}
+
+int ngb_retire_instance(ngb_sim* s, int32_t instance) {
+  int rc = check_handle(s);
+  if (rc != NGB_OK) return rc;
+  if (!s->serving) return fail(NGB_ERR_STATE, "ngb_retire_instance: not a serving handle");
+  if (instance < 0 || instance >= (int32_t)s->inst.size() || s->inst[(size_t)instance].state != 1)
+    return fail(NGB_ERR_INVALID_ARG, "ngb_retire_instance: instance is not active");
+  CK(cudaStreamSynchronize(s->stream));
+  release_instance_ranges(s, instance);
+  s->inst[(size_t)instance].state = 2;
+  s->tables_dirty = true;
+  return NGB_OK;
+}
+
+int ngb_instance_info(ngb_sim* s, int32_t instance, int64_t* t0_out, int32_t* state_out) {
+  if (!s || instance < 0 || instance >= (int32_t)s->inst.size())
+    return fail(NGB_ERR_INVALID_ARG, "ngb_instance_info: instance");
+  if (t0_out) *t0_out = s->inst[(size_t)instance].t0;
+  if (state_out) *state_out = s->inst[(size_t)instance].state;
+  return NGB_OK;
+}
+
 int ngb_get_spikes(ngb_sim* s, int32_t pop, int64_t t0_step, int64_t t1_step, int32_t* ids, int64_t* steps,
                    int64_t capacity, int64_t* n_out) {
   if (!s || !n_out) return fail(NGB_ERR_INVALID_ARG, "ngb_get_spikes: NULL argument");
@@ -1114,7 +1448,7 @@ int ngb_get_spikes(ngb_sim* s, int32_t pop, int64_t t0_step, int64_t t1_step, in
     s->rec_sorted_upto = s->rec_ids.size();
   }
   const int64_t lo = pop >= 0 ? s->pops[pop].offset : 0;
-  const int64_t hi = pop >= 0 ? s->pops[pop].offset + s->pops[pop].n : s->N;
+  const int64_t hi = pop >= 0 ? s->pops[pop].offset + s->pops[pop].n : std::max<int64_t>(s->N, s->N_cap);
   const auto first = std::lower_bound(s->rec_steps.begin(), s->rec_steps.end(), t0_step);
   const auto last = std::lower_bound(s->rec_steps.begin(), s->rec_steps.end(), t1_step);
   int64_t n = 0;
@@ -1136,7 +1470,7 @@ int ngb_get_stats(ngb_sim* s, ngb_stats* out) {
   if (!s || !out) return fail(NGB_ERR_INVALID_ARG, "ngb_get_stats: NULL argument");
   std::memset(out, 0, sizeof(*out));
   out->steps = s->t;
-  out->num_neurons = s->N;
+  out->num_neurons = s->finalized ? s->N_cap : s->N;
   out->spikes = s->spikes_total;
   if (s->finalized) {
     const int rc = check_handle(s);
@@ -1160,6 +1494,7 @@ int ngb_get_stats(ngb_sim* s, ngb_stats* out) {
 int ngb_population_range(ngb_sim* s, int32_t pop, int64_t* offset_out, int64_t* n_out) {
   if (!s || pop < 0 || pop >= (int32_t)s->pops.size())
     return fail(NGB_ERR_INVALID_ARG, "ngb_population_range: pop");
+  if (s->pops[pop].offset < 0) return fail(NGB_ERR_STATE, "ngb_population_range: population not placed yet");
   if (offset_out) *offset_out = s->pops[pop].offset;
   if (n_out) *n_out = s->pops[pop].n;
   return NGB_OK;
@@ -1169,7 +1504,7 @@ int ngb_get_state(ngb_sim* s, int32_t var, int64_t first, int64_t n, float* out)
   int rc = check_handle(s);
   if (rc != NGB_OK) return rc;
   if (!s->finalized) return fail(NGB_ERR_STATE, "ngb_get_state: not finalised");
-  if (!out || first < 0 || n < 0 || first + n > s->N) return fail(NGB_ERR_INVALID_ARG, "ngb_get_state: range");
+  if (!out || first < 0 || n < 0 || first + n > s->N_cap) return fail(NGB_ERR_INVALID_ARG, "ngb_get_state: range");
   const float* src = nullptr;
   bool is_ref = false;
   switch (var) {
@@ -1208,11 +1543,11 @@ int ngb_get_input(ngb_sim* s, int32_t receptor, int64_t step_offset, int64_t fir
   if (rc != NGB_OK) return rc;
   if (!s->finalized) return fail(NGB_ERR_STATE, "ngb_get_input: not finalised");
   if (!out || receptor < 0 || receptor >= s->R || step_offset < 0 || step_offset >= s->L || first < 0 || n < 0 ||
-      first + n > s->N)
+      first + n > s->N_cap)
     return fail(NGB_ERR_INVALID_ARG, "ngb_get_input: range");
   if (n == 0) return NGB_OK;
   const uint64_t slot = (uint64_t)((s->t + step_offset) & (s->L - 1));
-  const uint64_t off = (slot * (uint64_t)s->R + (uint64_t)receptor) * (uint64_t)s->N + (uint64_t)first;
+  const uint64_t off = (slot * (uint64_t)s->R + (uint64_t)receptor) * (uint64_t)s->N_cap + (uint64_t)first;
   if (s->cfg.deterministic) {
     std::vector<long long> tmp((size_t)n);
     CK(cudaMemcpyAsync(tmp.data(), (long long*)s->ring + off, n * sizeof(long long), cudaMemcpyDeviceToHost,
@@ -1231,7 +1566,7 @@ int ngb_get_src_ptr(ngb_sim* s, uint64_t* src_ptr) {
   if (rc != NGB_OK) return rc;
   if (!s->finalized) return fail(NGB_ERR_STATE, "ngb_get_src_ptr: not finalised");
   if (!src_ptr) return fail(NGB_ERR_INVALID_ARG, "ngb_get_src_ptr: NULL");
-  CK(cudaMemcpyAsync(src_ptr, s->src_syn, (s->N + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(src_ptr, s->src_syn, (s->N_cap + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   return NGB_OK;
 }

@@ -237,6 +237,7 @@ cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, cons
 cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V,
                                float* w, float* gex, float* gin, float* h, Ring ring, bool fixed, int64_t* clk,
                                const uint4* src_meta, SpikeBuf sb, bool pdl, cudaStream_t st);
+cudaError_t launch_tick(int64_t* clk, bool pdl, cudaStream_t st);
 cudaError_t persistent_max_blocks_per_sm(bool fixed, int wdtype, bool lif, bool aeif, size_t smem, int* out);
 cudaError_t launch_persistent(const PersistArgs& a, bool fixed, int wdtype, bool lif, bool aeif, int grid,
                               size_t smem, cudaStream_t st);

@@ -76,7 +76,8 @@ _lib = None
 EXPORTS = ["ngb_create", "ngb_destroy", "ngb_last_error", "ngb_add_instance", "ngb_add_population",
            "ngb_add_population_in", "ngb_connect", "ngb_finalize", "ngb_simulate", "ngb_simulate_profiled",
            "ngb_get_spikes", "ngb_get_stats", "ngb_population_range", "ngb_get_state", "ngb_get_input",
-           "ngb_get_src_ptr", "ngb_get_synapses", "ngb_autotune", "ngb_deliver_spikes_noalloc"]
+           "ngb_get_src_ptr", "ngb_get_synapses", "ngb_autotune", "ngb_deliver_spikes_noalloc",
+           "ngb_reserve", "ngb_commit_instance", "ngb_retire_instance", "ngb_instance_info"]
 
 
 def lib_path() -> str:
@@ -114,6 +115,10 @@ def load(build_if_missing: bool = True):
     L.ngb_get_src_ptr.argtypes = [P, P]
     L.ngb_get_synapses.argtypes = [P, C.c_int64, C.c_int64, P, P, P, P]
     L.ngb_autotune.argtypes = [P, C.c_int64, C.POINTER(C.c_int32)]
+    L.ngb_reserve.argtypes = [P, C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_int32]
+    L.ngb_commit_instance.argtypes = [P, C.c_int32]
+    L.ngb_retire_instance.argtypes = [P, C.c_int32]
+    L.ngb_instance_info.argtypes = [P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
     for name in EXPORTS:
         if name not in ("ngb_last_error",):
             getattr(L, name).restype = C.c_int
@@ -212,6 +217,32 @@ class Simulator:
         n = np.zeros(3, dtype=np.int64)
         self._c(load().ngb_simulate_profiled(self.h, steps, _ptr(ms), _ptr(n)))
         return ms, n
+
+    # ---- continuous batching (serving handles)
+    def reserve(self, max_neurons: int, max_synapses: int, max_groups: int, ring_slots: int = 64,
+                receptors: int = 1):
+        self._c(load().ngb_reserve(self.h, max_neurons, max_synapses, max_groups, ring_slots, receptors))
+
+    def commit(self, instance: int):
+        self._c(load().ngb_commit_instance(self.h, instance))
+
+    def retire(self, instance: int):
+        self._c(load().ngb_retire_instance(self.h, instance))
+
+    def instance_info(self, instance: int):
+        t0 = C.c_int64()
+        st = C.c_int32()
+        self._c(load().ngb_instance_info(self.h, instance, C.byref(t0), C.byref(st)))
+        return t0.value, st.value
+
+    def add_spec_instance(self, spec: W.NetSpec) -> Tuple[int, list]:
+        """Add the single-instance network `spec` as a new pending instance;
+        returns (instance id, population ids)."""
+        inst = self.add_instance(spec.seeds[0])
+        pops = [self.add_population(p.model, p.n, p.params, instance=inst) for p in spec.pops]
+        for c in spec.conns:
+            self.connect(pops[c.src], pops[c.tgt], c.rule, c.K, c.weight, c.delay, c.receptor, c.allow_autapses)
+        return inst, pops
 
     def autotune(self, trial_steps: int = 0) -> int:
         """Pick the delivery grid by timing graph replays; the state is restored."""
