@@ -54,6 +54,11 @@ def _args():
     ap.add_argument("--no-variant", action="store_true", help="skip the BF16-weight variant")
     ap.add_argument("--mode", choices=["auto", "graph", "persistent"], default="auto",
                     help="step loop: autotuned (default), per-step kernels in CUDA graphs, or the persistent kernel")
+    ap.add_argument("--workload", choices=["microcircuit", "batched", "adex", "serve"], default="microcircuit",
+                    help="microcircuit: the benchmark line; batched: 64 microcircuit instances vs the plain path; "
+                         "adex: the 1e6-neuron AdEx network; serve: the served request stream")
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--serve-duration", type=float, default=60.0)
     ap.add_argument("--scale", type=float, default=1.0,
                     help="microcircuit scale (population sizes and per-pathway counts); 1.0 is the benchmark")
     return ap.parse_args()
@@ -207,10 +212,110 @@ def run_reference(a):
     return 0
 
 
+def run_batched(a):
+    """Config 3: independent microcircuit instances of random scale advanced in
+    the same kernels, against the plain path (each instance alone)."""
+    import torch
+    from paper_2007_14236_gb300 import ngb, workloads as W
+    spec = W.batched_microcircuits(n_instances=a.instances, weight_dtype=a.weights)
+    t0 = time.perf_counter()
+    sim = ngb.from_spec(spec, drain_steps=a.sim_steps, record_capacity=16_000_000)
+    sim.finalize()
+    build_s = time.perf_counter() - t0
+    if a.mode == "auto":
+        sim.autotune(500)
+    st = sim.stats()
+    sim.simulate(1000)
+    e0 = sim.stats()["events"]
+    t1 = time.perf_counter()
+    for _ in range(a.steps):
+        sim.simulate(a.sim_steps)
+    wall = time.perf_counter() - t1
+    ev = sim.stats()["events"] - e0
+    batched = ev / wall
+    mode = "persistent" if sim.stats()["mode"] == 1 else "graph"
+    sim.close()
+    # plain path: a sample of instances, each alone
+    rng = np.random.default_rng(0)
+    sample = sorted(rng.choice(a.instances, size=min(8, a.instances), replace=False).tolist())
+    pw, pe = 0.0, 0
+    for i in sample:
+        one = ngb.from_spec(W.instance_spec(spec, i), drain_steps=a.sim_steps)
+        one.finalize()
+        one.simulate(1000)
+        e1 = one.stats()["events"]
+        t2 = time.perf_counter()
+        for _ in range(a.steps):
+            one.simulate(a.sim_steps)
+        pw += time.perf_counter() - t2
+        pe += one.stats()["events"] - e1
+        one.close()
+    plain = pe / pw
+    print(json.dumps({"workload": "batched_microcircuits", "instances": a.instances, "neurons": st["num_neurons"],
+                      "synapses": st["num_synapses"], "build_s": build_s, "step_loop": mode,
+                      "batched_events_per_s": batched, "plain_events_per_s": plain, "batched_vs_plain": batched / plain,
+                      "bio_s": a.steps * a.sim_steps * 1e-4, "plain_sample": sample}), flush=True)
+    return 0
+
+
+def run_adex(a):
+    """Config 2: 1e6 AdEx neurons, in-degree 1000, BF16 weights."""
+    from paper_2007_14236_gb300 import ngb, workloads as W
+    spec = W.balanced_adex(n=1_000_000, indegree=1000, seed=1, weight_dtype="bf16")
+    t0 = time.perf_counter()
+    sim = ngb.from_spec(spec, drain_steps=a.sim_steps)
+    sim.finalize()
+    build_s = time.perf_counter() - t0
+    if a.mode == "auto":
+        sim.autotune(200)
+    sim.simulate(1000)
+    s0 = sim.stats()
+    t1 = time.perf_counter()
+    for _ in range(a.steps):
+        sim.simulate(a.sim_steps)
+    wall = time.perf_counter() - t1
+    s1 = sim.stats()
+    bio = a.steps * a.sim_steps * 1e-4
+    ms, nl = sim.simulate_profiled(200)
+    print(json.dumps({"workload": "balanced_adex_1e6", "neurons": s1["num_neurons"], "synapses": s1["num_synapses"],
+                      "build_s": build_s, "real_time_factor": wall / bio, "bio_s": bio,
+                      "spikes": s1["spikes"] - s0["spikes"], "events": s1["events"] - s0["events"],
+                      "rate_hz": (s1["spikes"] - s0["spikes"]) / 1e6 / bio,
+                      "rk_substeps_per_neuron_step": (s1["rk_substeps"] - s0["rk_substeps"]) / 1e6 / (bio * 1e4),
+                      "us_per_launch": {"k_update_aeif": 1e3 * ms[1] / max(1, nl[1]),
+                                        "k_deliver": 1e3 * ms[2] / max(1, nl[2])},
+                      "step_loop": "persistent" if s1["mode"] == 1 else "graph"}), flush=True)
+    return 0
+
+
+def run_serve(a):
+    from paper_2007_14236_gb300 import serve, workloads as W
+    reqs = W.served_requests(duration_s=a.serve_duration)
+    srv = serve.Server(8_000_000, 4_000_000_000, 8_000_000, ring_slots=32)
+    done, summary = srv.run(reqs)
+    srv.close()
+    rng = np.random.default_rng(0)
+    sample = rng.choice(len(reqs), size=min(30, len(reqs)), replace=False)
+    pw, pe = 0.0, 0
+    for i in sample:
+        w, ev, _, _ = serve.run_alone(reqs[int(i)])
+        pw += w
+        pe += ev
+    summary.update({"workload": "served_requests", "arrival_rate_per_s": 20.0, "window_s": a.serve_duration,
+                    "plain_events_per_s": pe / pw, "served_vs_plain": summary["events_per_s"] / (pe / pw),
+                    "plain_sample": len(sample)})
+    print(json.dumps(summary), flush=True)
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload != "microcircuit":
+        global np
+        import numpy as np
+        return {"batched": run_batched, "adex": run_adex, "serve": run_serve}[a.workload](a)
     ws, rank, local = _dist()
     import numpy as np
     import torch

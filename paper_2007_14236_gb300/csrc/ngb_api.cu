@@ -86,11 +86,6 @@ struct RangeAlloc {
       free_.erase(free_.begin() + i);
     }
   }
-  uint64_t largest() const {
-    uint64_t m = 0;
-    for (const auto& r : free_) m = std::max(m, r.second);
-    return m;
-  }
 };
 
 struct PopHost {
@@ -400,17 +395,14 @@ int place_population(ngb_sim* s, int pi) {
   return NGB_OK;
 }
 
-// Draw, sort and gather the outgoing synapses of every population of
-// `instance` (Sec. 2.1 rules, Sec. 2.2 delay groups) into the synapse pool.
-int build_instance(ngb_sim* s, int instance, std::vector<PopParts>& parts, int* max_delay_out,
-                   uint64_t* running_k) {
+// Draw, sort and gather the outgoing synapses of the source populations
+// `srcs` (Sec. 2.1 rules, Sec. 2.2 delay groups) into the synapse pool.
+int build_populations(ngb_sim* s, const std::vector<int>& srcs, std::vector<PopParts>& parts, int* max_delay_out,
+                      uint64_t* running_k) {
   cudaStream_t st = s->stream;
   const double dt = s->cfg.dt_ms;
   const int prec = s->cfg.weight_dtype;
   const size_t wsize = prec == NGB_WEIGHT_FP32 ? 4 : 2;
-  std::vector<int> srcs;
-  for (size_t p = 0; p < s->pops.size(); ++p)
-    if (s->pops[p].instance == instance) srcs.push_back((int)p);
   std::vector<std::vector<CallDev>> by_src(srcs.size());
   std::vector<uint64_t> n_by_src(srcs.size(), 0);
   uint64_t kmax = 0;
@@ -577,7 +569,10 @@ int commit_impl(ngb_sim* s, int instance) {
   std::vector<PopParts> parts;
   int md = 0;
   uint64_t rk = 0, rg = 0, items = 0;
-  if (rc == NGB_OK) rc = build_instance(s, instance, parts, &md, &rk);
+  std::vector<int> srcs;
+  for (size_t p = 0; p < s->pops.size(); ++p)
+    if (s->pops[p].instance == instance) srcs.push_back((int)p);
+  if (rc == NGB_OK) rc = build_populations(s, srcs, parts, &md, &rk);
   if (rc == NGB_OK && md > s->L - 1) rc = fail(NGB_ERR_OVERFLOW, "a delay is beyond the reserved ring slots");
   if (rc == NGB_OK) rc = place_parts(s, parts, &rg, &items);
   if (rc != NGB_OK) {
@@ -874,17 +869,18 @@ int finalize_impl(ngb_sim* s) {
       const int rc = place_population(s, (int)p);
       if (rc != NGB_OK) return rc;
     }
+    // sources in global id order, so the CSR is ordered by source across instances
     std::vector<PopParts> parts;
     uint64_t rk = 0;
     int md_all = 0;
-    for (size_t i = 0; i < s->inst.size(); ++i) {
-      int md = 0;
-      const int rc = build_instance(s, (int)i, parts, &md, &rk);
+    std::vector<int> srcs;
+    for (size_t p = 0; p < s->pops.size(); ++p) srcs.push_back((int)p);
+    {
+      const int rc = build_populations(s, srcs, parts, &md_all, &rk);
       if (rc != NGB_OK) {
         free_parts(parts);
         return rc;
       }
-      md_all = std::max(md_all, md);
     }
     uint64_t G = 0;
     for (const PopParts& q : parts) G += q.G;

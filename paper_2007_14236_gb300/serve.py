@@ -92,6 +92,7 @@ class Server:
         queue = deque(order)
         waiting: deque = deque()
         active: Dict[int, dict] = {}
+        built: Dict[int, tuple] = {}  # requests added as pending instances, waiting for room
         done: List[Done] = []
         ev0 = self.sim.stats()["events"]
         wall0 = time.perf_counter()
@@ -117,13 +118,16 @@ class Server:
                 fp = footprint(spec)
                 if not self._fits(fp):
                     break
-                inst, pops = self.sim.add_spec_instance(spec)
+                if i not in built:
+                    built[i] = self.sim.add_spec_instance(spec)
+                inst, pops = built[i]
                 try:
                     self.sim.commit(inst)
                 except _ngb.NgbError as e:
                     if e.code == -3:  # pool fragmentation: retry after the next retirements
                         break
                     raise
+                del built[i]
                 waiting.popleft()
                 for k in fp:
                     self.used[k] += fp[k]
