@@ -215,7 +215,7 @@ def run_reference(a):
 def run_batched(a):
     """Config 3: independent microcircuit instances of random scale advanced in
     the same kernels, against the plain path (each instance alone)."""
-    import torch
+    import numpy as np
     from paper_2007_14236_gb300 import ngb, workloads as W
     spec = W.batched_microcircuits(n_instances=a.instances, weight_dtype=a.weights)
     t0 = time.perf_counter()
@@ -289,6 +289,7 @@ def run_adex(a):
 
 
 def run_serve(a):
+    import numpy as np
     from paper_2007_14236_gb300 import serve, workloads as W
     reqs = W.served_requests(duration_s=a.serve_duration)
     srv = serve.Server(8_000_000, 4_000_000_000, 8_000_000, ring_slots=32)
@@ -313,8 +314,6 @@ def main():
     if a.impl == "reference":
         return run_reference(a)
     if a.workload != "microcircuit":
-        global np
-        import numpy as np
         return {"batched": run_batched, "adex": run_adex, "serve": run_serve}[a.workload](a)
     ws, rank, local = _dist()
     import numpy as np
