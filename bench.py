@@ -234,6 +234,19 @@ def run_batched(a):
     ev = sim.stats()["events"] - e0
     batched = ev / wall
     mode = "persistent" if sim.stats()["mode"] == 1 else "graph"
+    # per-kernel CUDA-event times of the per-step kernels on the batch
+    ep0 = sim.stats()["events"]
+    kms, nl = sim.simulate_profiled(300)
+    evl = (sim.stats()["events"] - ep0) / max(1, nl[2])
+    wbytes = 4 if a.weights == "fp32" else 2
+    peak, _ = _peaks()
+    us_d = 1e3 * kms[2] / max(1, nl[2])
+    us_u = 1e3 * kms[0] / max(1, nl[0])
+    kern = {"k_deliver": {"us_per_launch": us_d, "events_per_launch": evl,
+                          "achieved_gbs": evl * (8 + wbytes) / (us_d * 1e-6) / 1e9,
+                          "frac_of_measured_hbm": evl * (8 + wbytes) / (us_d * 1e-6) / 1e9 / peak},
+            "k_update_lif": {"us_per_launch": us_u, "achieved_gbs": st["num_neurons"] * 32 / (us_u * 1e-6) / 1e9,
+                             "frac_of_measured_hbm": st["num_neurons"] * 32 / (us_u * 1e-6) / 1e9 / peak}}
     sim.close()
     # plain path: a sample of instances, each alone
     rng = np.random.default_rng(0)
@@ -254,7 +267,7 @@ def run_batched(a):
     print(json.dumps({"workload": "batched_microcircuits", "instances": a.instances, "neurons": st["num_neurons"],
                       "synapses": st["num_synapses"], "build_s": build_s, "step_loop": mode,
                       "batched_events_per_s": batched, "plain_events_per_s": plain, "batched_vs_plain": batched / plain,
-                      "bio_s": a.steps * a.sim_steps * 1e-4, "plain_sample": sample}), flush=True)
+                      "bio_s": a.steps * a.sim_steps * 1e-4, "plain_sample": sample, "kernels": kern}), flush=True)
     return 0
 
 
