@@ -72,9 +72,10 @@ class Server:
     def __init__(self, max_neurons: int, max_synapses: int, max_groups: int, ring_slots: int = 32,
                  chunk_steps: int = 1000, deterministic: bool = False, keep_spikes: bool = False,
                  weight_dtype: str = "fp32", device: int = 0):
+        # spikes are recorded only when the caller keeps them; the counters count them either way
         self.sim = _ngb.Simulator(dt_ms=0.1, seed=0, weight_dtype=weight_dtype, device=device,
-                                  deterministic=deterministic, record_spikes=True, drain_steps=chunk_steps,
-                                  record_capacity=max(1 << 22, max_neurons * chunk_steps // 50))
+                                  deterministic=deterministic, record_spikes=keep_spikes, drain_steps=chunk_steps,
+                                  record_capacity=max(1 << 22, max_neurons * chunk_steps // 20))
         self.sim.reserve(max_neurons, max_synapses, max_groups, ring_slots, 1)
         self.sim.finalize()
         self.cap = {"neurons": max_neurons, "synapses": max_synapses, "groups": max_groups}
@@ -153,9 +154,9 @@ class Server:
                 local = 0  # network-local id of the population's first neuron
                 for p in a["pops"]:
                     off, n = self.sim.population_range(p)
-                    ids, st = self.sim.spikes(pop=p, t0=a["t0"], t1=a["end"])
-                    n_spk += len(ids)
                     if self.keep:
+                        ids, st = self.sim.spikes(pop=p, t0=a["t0"], t1=a["end"])
+                        n_spk += len(ids)
                         ids_all.append(ids + local)
                         st_all.append(st - a["t0"])
                     local += n
@@ -190,7 +191,8 @@ def run_alone(req: W.Request, spec: Optional[W.NetSpec] = None, deterministic: b
     simulate, read spikes).  Returns (wall seconds, events, ids, steps)."""
     spec = spec or W.request_net(req)
     t0 = time.perf_counter()
-    sim = _ngb.from_spec(spec, deterministic=deterministic, drain_steps=1000)
+    sim = _ngb.from_spec(spec, deterministic=deterministic, drain_steps=1000, record_spikes=keep_spikes,
+                         record_capacity=max(1 << 22, spec.num_neurons() * 50))
     steps = int(round(req.bio_time_ms / 0.1))
     sim.simulate(steps)
     ids, st = sim.spikes(t0=0, t1=steps)

@@ -23,12 +23,13 @@ def mods():
     return ngb, serve
 
 
-def _requests(n, seed, n_lo=2000, n_hi=6000, k_lo=50, k_hi=120, t_lo=20.0, t_hi=80.0):
+def _requests(n, seed, n_lo=2000, n_hi=6000, k_lo=50, k_hi=120, t_lo=20.0, t_hi=80.0, burst=True):
     rng = np.random.default_rng(seed)
     out = []
     t = 0.0
     for i in range(n):
-        t += rng.exponential(0.01)
+        if not burst:
+            t += rng.exponential(0.01)
         out.append(W.Request(arrival_s=t, n=int(rng.integers(n_lo, n_hi)), indegree=int(rng.integers(k_lo, k_hi)),
                              bio_time_ms=float(round(rng.uniform(t_lo, t_hi), 1)), seed=500 + i))
     return out
