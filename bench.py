@@ -58,6 +58,7 @@ def _args():
                     help="microcircuit: the benchmark line; batched: 64 microcircuit instances vs the plain path; "
                          "adex: the 1e6-neuron AdEx network; serve: the served request stream")
     ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--adex-n", type=int, default=1_000_000, help="neurons of the AdEx workload")
     ap.add_argument("--serve-duration", type=float, default=60.0)
     ap.add_argument("--scale", type=float, default=1.0,
                     help="microcircuit scale (population sizes and per-pathway counts); 1.0 is the benchmark")
@@ -274,7 +275,7 @@ def run_batched(a):
 def run_adex(a):
     """Config 2: 1e6 AdEx neurons, in-degree 1000, BF16 weights."""
     from paper_2007_14236_gb300 import ngb, workloads as W
-    spec = W.balanced_adex(n=1_000_000, indegree=1000, seed=1, weight_dtype="bf16")
+    spec = W.balanced_adex(n=a.adex_n, indegree=1000, seed=1, weight_dtype="bf16")
     t0 = time.perf_counter()
     sim = ngb.from_spec(spec, drain_steps=a.sim_steps)
     sim.finalize()
@@ -290,11 +291,11 @@ def run_adex(a):
     s1 = sim.stats()
     bio = a.steps * a.sim_steps * 1e-4
     ms, nl = sim.simulate_profiled(200)
-    print(json.dumps({"workload": "balanced_adex_1e6", "neurons": s1["num_neurons"], "synapses": s1["num_synapses"],
+    print(json.dumps({"workload": "balanced_adex_%d" % a.adex_n, "neurons": s1["num_neurons"], "synapses": s1["num_synapses"],
                       "build_s": build_s, "real_time_factor": wall / bio, "bio_s": bio,
                       "spikes": s1["spikes"] - s0["spikes"], "events": s1["events"] - s0["events"],
-                      "rate_hz": (s1["spikes"] - s0["spikes"]) / 1e6 / bio,
-                      "rk_substeps_per_neuron_step": (s1["rk_substeps"] - s0["rk_substeps"]) / 1e6 / (bio * 1e4),
+                      "rate_hz": (s1["spikes"] - s0["spikes"]) / a.adex_n / bio,
+                      "rk_substeps_per_neuron_step": (s1["rk_substeps"] - s0["rk_substeps"]) / a.adex_n / (bio * 1e4),
                       "us_per_launch": {"k_update_aeif": 1e3 * ms[1] / max(1, nl[1]),
                                         "k_deliver": 1e3 * ms[2] / max(1, nl[2])},
                       "step_loop": "persistent" if s1["mode"] == 1 else "graph"}), flush=True)

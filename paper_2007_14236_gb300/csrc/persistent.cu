@@ -42,9 +42,29 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   return v;
 }
 
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed_u32(unsigned* p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Grid-wide barrier with a bounded wait.  Returns false when the launch must
 // stop (this block or another one gave up waiting).  withhold: this block does
 // not arrive (test hook for the timeout path).
+//
+// The block's threads meet at __syncthreads; thread 0 then arrives with an
+// acquire-release atomic on the arrival counter (making the block's writes,
+// ordered before it by the CTA barrier, visible at GPU scope).  The last
+// arriver resets the counter and publishes the next generation with a
+// release store; the others poll the generation with acquire loads.
 __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned long long spin_limit, uint32_t* err,
                                           bool withhold) {
   __shared__ int s_ok;
@@ -52,20 +72,18 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned long long spin
   if (threadIdx.x == 0) {
     int ok = 1;
     const unsigned gen = ld_acquire_u32(bar + 1);
-    __threadfence();
     bool released = false;
     if (!withhold) {
-      if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-        atomicExch(bar, 0u);
-        __threadfence();
-        atomicAdd(bar + 1, 1u);  // new generation: everyone may go
+      if (atom_add_acq_rel_u32(bar, 1u) == gridDim.x - 1) {
+        st_relaxed_u32(bar, 0u);
+        st_release_u32(bar + 1, gen + 1u);  // new generation: everyone may go
         released = true;
       }
     }
     if (!released) {
       unsigned long long spins = 0;
       while (ld_acquire_u32(bar + 1) == gen) {
-        if (ld_acquire_u32(bar + 2) != 0u) {  // another block gave up
+        if ((spins & 63u) == 63u && ld_acquire_u32(bar + 2) != 0u) {  // another block gave up
           ok = 0;
           break;
         }
@@ -75,10 +93,8 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned long long spin
           ok = 0;
           break;
         }
-        __nanosleep(64);
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
