@@ -59,6 +59,7 @@ def _args():
                          "adex: the 1e6-neuron AdEx network; serve: the served request stream")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--adex-n", type=int, default=1_000_000, help="neurons of the AdEx workload")
+    ap.add_argument("--adex-ctl32", action="store_true", help="AdEx step-size control in FP32")
     ap.add_argument("--serve-duration", type=float, default=60.0)
     ap.add_argument("--scale", type=float, default=1.0,
                     help="microcircuit scale (population sizes and per-pathway counts); 1.0 is the benchmark")
@@ -276,6 +277,8 @@ def run_adex(a):
     """Config 2: 1e6 AdEx neurons, in-degree 1000, BF16 weights."""
     from paper_2007_14236_gb300 import ngb, workloads as W
     spec = W.balanced_adex(n=a.adex_n, indegree=1000, seed=1, weight_dtype="bf16")
+    for p in spec.pops:
+        p.params.rk_control_fp32 = a.adex_ctl32
     t0 = time.perf_counter()
     sim = ngb.from_spec(spec, drain_steps=a.sim_steps)
     sim.finalize()
@@ -298,7 +301,8 @@ def run_adex(a):
                       "rk_substeps_per_neuron_step": (s1["rk_substeps"] - s0["rk_substeps"]) / a.adex_n / (bio * 1e4),
                       "us_per_launch": {"k_update_aeif": 1e3 * ms[1] / max(1, nl[1]),
                                         "k_deliver": 1e3 * ms[2] / max(1, nl[2])},
-                      "step_loop": "persistent" if s1["mode"] == 1 else "graph"}), flush=True)
+                      "step_loop": "persistent" if s1["mode"] == 1 else "graph",
+                      "rk_control": "fp32" if a.adex_ctl32 else "fp64"}), flush=True)
     return 0
 
 

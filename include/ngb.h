@@ -104,13 +104,17 @@ typedef struct {
 
 /* AdEx with exponential conductances (Eqs. 3-5).  No refractory period.
  * rk_tol: relative tolerance of the adaptive Runge-Kutta step; with FP32 state
- * the effective tolerance is max(rk_tol, 8 * 2^-24). */
+ * the effective tolerance is max(rk_tol, 8 * 2^-24).  The step size, the time
+ * inside the step and the error-ratio test are FP64 unless rk_control_fp32 is
+ * 1 (then FP32: faster on parts with few FP64 units, same state precision). */
 typedef struct {
   double C_m_pF, g_L_nS, E_L_mV, V_T_mV, Delta_T_mV, a_nS, b_pA, tau_w_ms, V_peak_mV, V_reset_mV;
   double E_ex_mV, E_in_mV, tau_ex_ms, tau_in_ms, I_e_pA;
   double V_init_mean_mV, V_init_sd_mV, w_init_pA;
   double rk_tol, rk_h_min_ms, rk_h_init_ms;
   int64_t rk_max_substeps;
+  int32_t rk_control_fp32;
+  int32_t pad_;
   ngb_poisson_drive poisson;
 } ngb_aeif_params;
 

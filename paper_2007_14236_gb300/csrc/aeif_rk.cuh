@@ -55,14 +55,17 @@ __device__ __forceinline__ float ratio_of(float err, float y, float hf, float fl
 
 // Integrate y over one step of p.dt; h carries the step-size proposal in
 // and out.  Adds the sub-steps to nsub and the spikes to nspk; cap_hit is set
-// when the sub-step cap ended the step early.
-__device__ __forceinline__ void aeif_integrate(const AeifSeg& p, St& y, double& h, uint32_t& nspk,
-                                               unsigned long long& nsub, bool& cap_hit) {
-  if (!(h > 0.0)) h = p.dt;
-  double t_in = 0.0;
+// when the sub-step cap ended the step early.  CT is the precision of the
+// step-size control (h, time inside the step, error-ratio test).
+template <typename CT>
+__device__ __forceinline__ void aeif_integrate_t(const AeifSeg& p, St& y, CT& h, uint32_t& nspk,
+                                                 unsigned long long& nsub, bool& cap_hit) {
+  const CT dt = (CT)p.dt, h_min = (CT)p.h_min;
+  if (!(h > (CT)0)) h = dt;
+  CT t_in = (CT)0;
   int64_t n = 0;  // sub-steps of this step (the cap applies per neuron and step)
   for (;;) {
-    const double rem = p.dt - t_in;
+    const CT rem = dt - t_in;
     bool last = false;
     if (h >= rem) {
       h = rem;
@@ -101,29 +104,43 @@ __device__ __forceinline__ void aeif_integrate(const AeifSeg& p, St& y, double& 
     emax = fmaxf(emax, ratio_of(er.w, y.w, hf * k1.w, 1.0f));
     emax = fmaxf(emax, ratio_of(er.ge, y.ge, hf * k1.ge, 1e-3f));
     emax = fmaxf(emax, ratio_of(er.gi, y.gi, hf * k1.gi, 1e-3f));
-    const double ratio = (double)emax * p.inv_tol;
+    const CT ratio = (CT)emax * (CT)p.inv_tol;
     ++nsub;
     ++n;
     const bool cap = n >= p.max_sub;
-    if (ratio <= 1.0 || h <= p.h_min || cap) {
+    if (ratio <= (CT)1 || h <= h_min || cap) {
       y = y5;
       if (y.V >= p.V_peak) {
         y.V = p.V_reset;
         y.w = y.w + p.b;
         ++nspk;
       }
-      const float rf = (float)ratio;
+      const float rf = emax * (float)p.inv_tol;
       float grow = 5.0f;
       if (rf > 0.0f) grow = fminf(5.0f, 0.9f * exp2f(-0.2f * __log2f(rf)));
-      const double h_used = h;
-      h = fmax(h * (double)grow, p.h_min);
+      const CT h_used = h;
+      h = h * (CT)grow;
+      if (h < h_min) h = h_min;
       if (cap && !last) cap_hit = true;
       if (last || cap) break;
       t_in += h_used;
     } else {
-      const float shrink = fmaxf(0.1f, 0.9f * exp2f(-0.25f * __log2f((float)ratio)));
-      h = fmax(h * (double)shrink, p.h_min);
+      const float shrink = fmaxf(0.1f, 0.9f * exp2f(-0.25f * __log2f(emax * (float)p.inv_tol)));
+      h = h * (CT)shrink;
+      if (h < h_min) h = h_min;
     }
+  }
+}
+
+// FP64 step-size control by default, FP32 when the population asks for it.
+__device__ __forceinline__ void aeif_integrate(const AeifSeg& p, St& y, double& h, uint32_t& nspk,
+                                               unsigned long long& nsub, bool& cap_hit) {
+  if (p.ctl32) {
+    float hf = (float)h;
+    aeif_integrate_t<float>(p, y, hf, nspk, nsub, cap_hit);
+    h = (double)hf;
+  } else {
+    aeif_integrate_t<double>(p, y, h, nspk, nsub, cap_hit);
   }
 }
 

@@ -655,6 +655,7 @@ int rebuild_tables(ngb_sim* s) {
       g.thr_off = (uint32_t)thr_all.size();
       thr_all.insert(thr_all.end(), th.begin(), th.end());
       g.prec_rcpt = q.poisson.receptor;
+      g.ctl32 = q.rk_control_fp32 ? 1 : 0;
       g.g_L = (float)q.g_L_nS;
       g.E_L = (float)q.E_L_mV;
       g.V_T = (float)q.V_T_mV;

@@ -64,6 +64,8 @@ struct AeifSeg {
   uint64_t seed;
   uint32_t local_off, n_thr, thr_off;
   int32_t prec_rcpt;   // receptor of the Poisson drive
+  int32_t ctl32;       // step-size control in FP32 instead of FP64
+  int32_t pad2_;
   float g_L, E_L, V_T, Delta_T, inv_Delta_T, a, inv_tau_w, V_peak, V_reset, b;
   float E_ex, E_in, inv_tau_ex, inv_tau_in, I_e, inv_C, w_ext, pad_;
   double inv_tol, h_min, dt;

@@ -49,7 +49,8 @@ class AeifParams(C.Structure):
                                           "tau_ex_ms", "tau_in_ms", "I_e_pA", "V_init_mean_mV",
                                           "V_init_sd_mV", "w_init_pA", "rk_tol", "rk_h_min_ms",
                                           "rk_h_init_ms")] + \
-               [("rk_max_substeps", C.c_int64), ("poisson", PoissonDrive)]
+               [("rk_max_substeps", C.c_int64), ("rk_control_fp32", C.c_int32), ("pad_", C.c_int32),
+                ("poisson", PoissonDrive)]
 
 
 class ConnSpec(C.Structure):
@@ -154,7 +155,7 @@ def lif_params(p: W.LifParams) -> LifParams:
 def aeif_params(p: W.AeifParams) -> AeifParams:
     return AeifParams(p.C_m, p.g_L, p.E_L, p.V_T, p.Delta_T, p.a, p.b, p.tau_w, p.V_peak, p.V_reset, p.E_ex, p.E_in,
                       p.tau_ex, p.tau_in, p.I_e, p.V_init_mean, p.V_init_sd, p.w_init, p.rk_tol, p.rk_h_min,
-                      p.rk_h_init, int(p.rk_max_substeps), _poisson(p.poisson))
+                      p.rk_h_init, int(p.rk_max_substeps), int(p.rk_control_fp32), 0, _poisson(p.poisson))
 
 
 class Simulator:

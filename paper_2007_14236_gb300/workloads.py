@@ -77,6 +77,7 @@ class AeifParams:
     rk_h_min: float = 1e-6
     rk_h_init: float = 0.1
     rk_max_substeps: int = 10000
+    rk_control_fp32: bool = False
     poisson: Poisson = field(default_factory=Poisson)
 
 

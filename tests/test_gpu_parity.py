@@ -184,13 +184,15 @@ def test_fp32_long_run_rates_and_cv(ngb):
     assert abs(np.mean(cg) - np.mean(co)) <= 0.05, (cg, co)
 
 
-def _adex_single(I_e):
-    par = W.AeifParams(V_reset=-60.0, tau_ex=1.0, tau_in=1.0, I_e=I_e, rk_h_min=1e-9, rk_max_substeps=100000)
+def _adex_single(I_e, ctl32=False):
+    par = W.AeifParams(V_reset=-60.0, tau_ex=1.0, tau_in=1.0, I_e=I_e, rk_h_min=1e-9, rk_max_substeps=100000,
+                       rk_control_fp32=ctl32)
     return W.NetSpec(name="adex1", seeds=[1], pops=[W.Population("n", W.AEIF, 1, par)])
 
 
-def test_adex_single_neuron_700pA_vs_fp64_oracle(ngb):
-    spec = _adex_single(700.0)
+@pytest.mark.parametrize("ctl32", [False, True])
+def test_adex_single_neuron_700pA_vs_fp64_oracle(ngb, ctl32):
+    spec = _adex_single(700.0, ctl32)
     g = ngb.from_spec(spec)
     g.finalize()
     o = oracle.OracleNet(spec, adex_fp64=True)
@@ -213,9 +215,12 @@ def test_adex_single_neuron_700pA_vs_fp64_oracle(ngb):
     assert np.abs(Vg - Vo)[mask].max() <= 5e-3
 
 
-def test_adex_network_matches_fp32_oracle_statistics(ngb):
+@pytest.mark.parametrize("ctl32", [False, True])
+def test_adex_network_matches_fp32_oracle_statistics(ngb, ctl32):
     spec = W.balanced_adex(n=2000, indegree=100, seed=2, weight_dtype="fp32", poisson_weight=4.0, w_ex=2.0,
                            w_in=4.0)
+    for p in spec.pops:
+        p.params.rk_control_fp32 = ctl32
     g, o = _pair(ngb, spec)
     g.simulate(2000)
     o.simulate(2000)

@@ -55,7 +55,7 @@ def test_served_fp32_counts_close_to_alone(mods):
     ngb, serve = mods
     reqs = _requests(6, seed=2, t_lo=100.0, t_hi=150.0)
     srv = serve.Server(max_neurons=40000, max_synapses=4_000_000, max_groups=40000, ring_slots=16,
-                       chunk_steps=250)
+                       chunk_steps=250, keep_spikes=True)
     done, _ = srv.run(reqs)
     srv.close()
     for d in done:
