@@ -54,10 +54,13 @@ def _args():
     ap.add_argument("--no-variant", action="store_true", help="skip the BF16-weight variant")
     ap.add_argument("--mode", choices=["auto", "graph", "persistent"], default="auto",
                     help="step loop: autotuned (default), per-step kernels in CUDA graphs, or the persistent kernel")
-    ap.add_argument("--workload", choices=["microcircuit", "batched", "adex", "serve"], default="microcircuit",
+    ap.add_argument("--workload", choices=["microcircuit", "batched", "adex", "serve", "request"],
+                    default="microcircuit",
                     help="microcircuit: the benchmark line; batched: 64 microcircuit instances vs the plain path; "
                          "adex: the 1e6-neuron AdEx network; serve: the served request stream")
     ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--req-n", type=int, default=200_000, help="neurons of the single-request workload")
+    ap.add_argument("--req-k", type=int, default=1000, help="in-degree of the single-request workload")
     ap.add_argument("--adex-n", type=int, default=1_000_000, help="neurons of the AdEx workload")
     ap.add_argument("--adex-ctl32", action="store_true", help="AdEx step-size control in FP32")
     ap.add_argument("--serve-duration", type=float, default=60.0)
@@ -306,6 +309,39 @@ def run_adex(a):
     return 0
 
 
+def run_request(a):
+    """One served-request network alone (balanced LIF, config-0 neurons and
+    weights) at a given size and in-degree: the high-load delivery case."""
+    from paper_2007_14236_gb300 import ngb, workloads as W
+    spec = W.balanced_lif(n=a.req_n, indegree=a.req_k, seed=7)
+    sim = ngb.from_spec(spec, drain_steps=a.sim_steps, record_spikes=False)
+    sim.finalize()
+    if a.mode == "auto":
+        sim.autotune(300)
+    sim.simulate(1000)
+    s0 = sim.stats()
+    t1 = time.perf_counter()
+    for _ in range(a.steps):
+        sim.simulate(a.sim_steps)
+    wall = time.perf_counter() - t1
+    s1 = sim.stats()
+    ep0 = s1["events"]
+    kms, nl = sim.simulate_profiled(200)
+    evl = (sim.stats()["events"] - ep0) / max(1, nl[2])
+    peak, _ = _peaks()
+    us_d = 1e3 * kms[2] / max(1, nl[2])
+    bio = a.steps * a.sim_steps * 1e-4
+    print(json.dumps({"workload": "request_n%d_k%d" % (a.req_n, a.req_k), "synapses": s1["num_synapses"],
+                      "events_per_s": (s1["events"] - s0["events"]) / wall, "real_time_factor": wall / bio,
+                      "rate_hz": (s1["spikes"] - s0["spikes"]) / a.req_n / bio,
+                      "k_deliver": {"us_per_launch": us_d, "events_per_launch": evl,
+                                    "achieved_gbs": evl * 12 / (us_d * 1e-6) / 1e9,
+                                    "frac_of_measured_hbm": evl * 12 / (us_d * 1e-6) / 1e9 / peak},
+                      "k_update_lif_us": 1e3 * kms[0] / max(1, nl[0]),
+                      "step_loop": "persistent" if s1["mode"] == 1 else "graph"}), flush=True)
+    return 0
+
+
 def run_serve(a):
     import numpy as np
     from paper_2007_14236_gb300 import serve, workloads as W
@@ -332,7 +368,7 @@ def main():
     if a.impl == "reference":
         return run_reference(a)
     if a.workload != "microcircuit":
-        return {"batched": run_batched, "adex": run_adex, "serve": run_serve}[a.workload](a)
+        return {"batched": run_batched, "adex": run_adex, "serve": run_serve, "request": run_request}[a.workload](a)
     ws, rank, local = _dist()
     import numpy as np
     import torch
