@@ -35,6 +35,8 @@ if ROOT not in sys.path:
 
 METRIC = "real-time factor & synaptic events/s; batched/served vs plain at stated tol"
 UNIT = "synaptic events/s"
+DELIVERY = {1: "ring", 2: "spike_buffer"}
+LOOPS = {0: "graph", 1: "persistent", 2: "fused"}
 SIM_STEPS_PER_BENCH_STEP = 10_000  # 1 s of biological time at dt = 0.1 ms
 
 
@@ -52,9 +54,12 @@ def _args():
                     help="oracle simulation steps timed for the CPU baseline")
     ap.add_argument("--profile-steps", type=int, default=2000)
     ap.add_argument("--no-variant", action="store_true", help="skip the BF16-weight variant")
-    ap.add_argument("--mode", choices=["auto", "graph", "persistent"], default="auto",
-                    help="step loop: autotuned (default), per-step kernels in CUDA graphs, or the persistent kernel")
-    ap.add_argument("--workload", choices=["microcircuit", "batched", "adex", "serve", "request"],
+    ap.add_argument("--delivery", choices=["auto", "ring", "spike_buffer"], default="auto",
+                    help="spike delivery scheme (auto: chosen at finalisation, and by the autotuner at step 0)")
+    ap.add_argument("--mode", choices=["auto", "graph", "persistent", "fused"], default="auto",
+                    help="step loop: autotuned (default), per-step kernels in CUDA graphs, the persistent kernel, "
+                         "or the fused update + delivery kernels in CUDA graphs")
+    ap.add_argument("--workload", choices=["microcircuit", "small", "batched", "adex", "serve", "request"],
                     default="microcircuit",
                     help="microcircuit: the benchmark line; batched: 64 microcircuit instances vs the plain path; "
                          "adex: the 1e6-neuron AdEx network; serve: the served request stream")
@@ -224,7 +229,7 @@ def run_batched(a):
     from paper_2007_14236_gb300 import ngb, workloads as W
     spec = W.batched_microcircuits(n_instances=a.instances, weight_dtype=a.weights)
     t0 = time.perf_counter()
-    sim = ngb.from_spec(spec, drain_steps=a.sim_steps, record_capacity=16_000_000)
+    sim = ngb.from_spec(spec, drain_steps=a.sim_steps, record_capacity=16_000_000, delivery=a.delivery)
     sim.finalize()
     build_s = time.perf_counter() - t0
     if a.mode == "auto":
@@ -238,7 +243,8 @@ def run_batched(a):
     wall = time.perf_counter() - t1
     ev = sim.stats()["events"] - e0
     batched = ev / wall
-    mode = "persistent" if sim.stats()["mode"] == 1 else "graph"
+    mode = LOOPS[sim.stats()["mode"]]
+    sim_delivery = sim.stats()["delivery"]
     # per-kernel CUDA-event times of the per-step kernels on the batch
     ep0 = sim.stats()["events"]
     kms, nl = sim.simulate_profiled(300)
@@ -258,7 +264,7 @@ def run_batched(a):
     sample = sorted(rng.choice(a.instances, size=min(8, a.instances), replace=False).tolist())
     pw, pe = 0.0, 0
     for i in sample:
-        one = ngb.from_spec(W.instance_spec(spec, i), drain_steps=a.sim_steps)
+        one = ngb.from_spec(W.instance_spec(spec, i), drain_steps=a.sim_steps)  # the library's default choices
         one.finalize()
         one.simulate(1000)
         e1 = one.stats()["events"]
@@ -271,6 +277,7 @@ def run_batched(a):
     plain = pe / pw
     print(json.dumps({"workload": "batched_microcircuits", "instances": a.instances, "neurons": st["num_neurons"],
                       "synapses": st["num_synapses"], "build_s": build_s, "step_loop": mode,
+                      "delivery": DELIVERY[sim_delivery],
                       "batched_events_per_s": batched, "plain_events_per_s": plain, "batched_vs_plain": batched / plain,
                       "bio_s": a.steps * a.sim_steps * 1e-4, "plain_sample": sample, "kernels": kern}), flush=True)
     return 0
@@ -283,7 +290,7 @@ def run_adex(a):
     for p in spec.pops:
         p.params.rk_control_fp32 = a.adex_ctl32
     t0 = time.perf_counter()
-    sim = ngb.from_spec(spec, drain_steps=a.sim_steps)
+    sim = ngb.from_spec(spec, drain_steps=a.sim_steps, delivery=a.delivery)
     sim.finalize()
     build_s = time.perf_counter() - t0
     if a.mode == "auto":
@@ -297,6 +304,25 @@ def run_adex(a):
     s1 = sim.stats()
     bio = a.steps * a.sim_steps * 1e-4
     ms, nl = sim.simulate_profiled(200)
+    sim.close()
+    cpu = None
+    if not a.no_cpu_baseline:
+        # the oracle (FP32-state replica at the same tolerance) on a bounded sample: 20,000 neurons of the
+        # same network for 100 steps after 20; scaled per neuron-step to the full network
+        import oracle
+        n_s = 20_000
+        small = W.balanced_adex(n=n_s, indegree=1000, seed=1, weight_dtype="bf16")
+        for p in small.pops:
+            p.params.rk_control_fp32 = a.adex_ctl32
+        o = oracle.OracleNet(small)
+        o.finalize()
+        o.simulate(20)
+        c0 = time.perf_counter()
+        o.simulate(100)
+        cw = time.perf_counter() - c0
+        cpu = {"real_time_factor": cw / 100 / n_s * a.adex_n / 1e-4, "cores": 1, "kind": "oracle",
+               "sample": "%d neurons of the same network (in-degree 1000), 100 steps after 20, single-threaded "
+                         "C++ oracle on %s; scaled per neuron-step to %d neurons" % (n_s, _cpu_info(), a.adex_n)}
     print(json.dumps({"workload": "balanced_adex_%d" % a.adex_n, "neurons": s1["num_neurons"], "synapses": s1["num_synapses"],
                       "build_s": build_s, "real_time_factor": wall / bio, "bio_s": bio,
                       "spikes": s1["spikes"] - s0["spikes"], "events": s1["events"] - s0["events"],
@@ -304,8 +330,45 @@ def run_adex(a):
                       "rk_substeps_per_neuron_step": (s1["rk_substeps"] - s0["rk_substeps"]) / a.adex_n / (bio * 1e4),
                       "us_per_launch": {"k_update_aeif": 1e3 * ms[1] / max(1, nl[1]),
                                         "k_deliver": 1e3 * ms[2] / max(1, nl[2])},
-                      "step_loop": "persistent" if s1["mode"] == 1 else "graph",
-                      "rk_control": "fp32" if a.adex_ctl32 else "fp64"}), flush=True)
+                      "step_loop": LOOPS[s1["mode"]],
+                      "delivery": DELIVERY[s1["delivery"]],
+                      "rk_control": "fp32" if a.adex_ctl32 else "fp64", "cpu_baseline": cpu}), flush=True)
+    return 0
+
+
+def run_small(a):
+    """Config 0: the 1,000-neuron balanced LIF network, 100 ms of biological
+    time per bench step, beside the oracle on the host for the same 100 ms."""
+    from paper_2007_14236_gb300 import ngb, workloads as W
+    spec = W.balanced_lif(n=1000, indegree=100, seed=1)
+    sim = ngb.from_spec(spec, drain_steps=1000, delivery=a.delivery)
+    sim.finalize()
+    if a.mode == "auto":
+        sim.autotune(500)
+    sim.simulate(1000)
+    s0 = sim.stats()
+    t1 = time.perf_counter()
+    for _ in range(a.steps):
+        sim.simulate(1000)
+    wall = time.perf_counter() - t1
+    s1 = sim.stats()
+    sim.close()
+    bio = a.steps * 0.1
+    out = {"workload": "balanced_lif_1000", "neurons": 1000, "synapses": s1["num_synapses"],
+           "real_time_factor": wall / bio, "events_per_s": (s1["events"] - s0["events"]) / wall,
+           "rate_hz": (s1["spikes"] - s0["spikes"]) / 1000 / bio, "step_loop": LOOPS[s1["mode"]],
+           "delivery": DELIVERY[s1["delivery"]]}
+    if not a.no_cpu_baseline:
+        import oracle
+        o = oracle.OracleNet(spec)
+        o.finalize()
+        c0 = time.perf_counter()
+        o.simulate(1000)
+        cw = time.perf_counter() - c0
+        out["cpu_baseline"] = {"real_time_factor": cw / 0.1, "events_per_s": o.events / cw, "cores": 1,
+                               "kind": "oracle", "sample": "the whole 100 ms run, single-threaded C++ oracle on %s"
+                                                           % _cpu_info()}
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -314,7 +377,7 @@ def run_request(a):
     weights) at a given size and in-degree: the high-load delivery case."""
     from paper_2007_14236_gb300 import ngb, workloads as W
     spec = W.balanced_lif(n=a.req_n, indegree=a.req_k, seed=7)
-    sim = ngb.from_spec(spec, drain_steps=a.sim_steps, record_spikes=False)
+    sim = ngb.from_spec(spec, drain_steps=a.sim_steps, record_spikes=False, delivery=a.delivery)
     sim.finalize()
     if a.mode == "auto":
         sim.autotune(300)
@@ -338,7 +401,8 @@ def run_request(a):
                                     "achieved_gbs": evl * 12 / (us_d * 1e-6) / 1e9,
                                     "frac_of_measured_hbm": evl * 12 / (us_d * 1e-6) / 1e9 / peak},
                       "k_update_lif_us": 1e3 * kms[0] / max(1, nl[0]),
-                      "step_loop": "persistent" if s1["mode"] == 1 else "graph"}), flush=True)
+                      "step_loop": LOOPS[s1["mode"]],
+                      "delivery": DELIVERY[s1["delivery"]]}), flush=True)
     return 0
 
 
@@ -346,9 +410,11 @@ def run_serve(a):
     import numpy as np
     from paper_2007_14236_gb300 import serve, workloads as W
     reqs = W.served_requests(duration_s=a.serve_duration)
-    srv = serve.Server(8_000_000, 4_000_000_000, 8_000_000, ring_slots=32)
+    srv = serve.Server(8_000_000, 4_000_000_000, 8_000_000, ring_slots=32, delivery=a.delivery)
+    delivery = DELIVERY[srv.sim.stats()["delivery"]]
     done, summary = srv.run(reqs)
     srv.close()
+    summary["delivery"] = delivery
     rng = np.random.default_rng(0)
     sample = rng.choice(len(reqs), size=min(30, len(reqs)), replace=False)
     pw, pe = 0.0, 0
@@ -367,8 +433,11 @@ def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
+    if a.mode in ("persistent", "fused"):
+        os.environ["NGB_MODE"] = a.mode  # read by the library when a network is finalised
     if a.workload != "microcircuit":
-        return {"batched": run_batched, "adex": run_adex, "serve": run_serve, "request": run_request}[a.workload](a)
+        return {"small": run_small, "batched": run_batched, "adex": run_adex, "serve": run_serve,
+                "request": run_request}[a.workload](a)
     ws, rank, local = _dist()
     import numpy as np
     import torch
@@ -385,11 +454,9 @@ def main():
     ngb.load()
     stream = torch.cuda.Stream()
     spec = _spec(a.weights, 1 + rank, a.scale)
-    if a.mode == "persistent":
-        os.environ["NGB_MODE"] = "persistent"
     t0 = time.perf_counter()
     sim = ngb.from_spec(spec, device=local, stream=stream.cuda_stream, steps_per_graph=100,
-                        drain_steps=a.sim_steps, record_capacity=4_000_000)
+                        drain_steps=a.sim_steps, record_capacity=4_000_000, delivery=a.delivery)
     sim.finalize()
     build_s = time.perf_counter() - t0
     tune_s = 0.0
@@ -398,7 +465,7 @@ def main():
         sim.autotune(1000)
         tune_s = time.perf_counter() - t1
     st0 = sim.stats()
-    mode = "persistent" if st0["mode"] == 1 else "graph"
+    mode = {0: "graph", 1: "persistent", 2: "fused"}[st0["mode"]]
 
     for _ in range(a.warmup):
         sim.simulate(a.sim_steps)
@@ -465,15 +532,27 @@ def main():
     spikes_per_step = None
     ev_per_launch = ev_p / max(1, nlaunch[2])
     deliver_bytes = ev_per_launch * (4 + wbytes + 4)
-    kern = {
-        "k_update_lif": {"launches": int(nlaunch[0]), "ms_total": float(kms[0]),
-                         "us_per_launch": 1e3 * float(kms[0]) / max(1, nlaunch[0]),
-                         "algorithmic_bytes_per_launch": lif_bytes},
-        "k_deliver": {"launches": int(nlaunch[2]), "ms_total": float(kms[2]),
-                      "us_per_launch": 1e3 * float(kms[2]) / max(1, nlaunch[2]),
-                      "algorithmic_bytes_per_launch": deliver_bytes,
-                      "events_per_launch": ev_per_launch},
-    }
+    if mode == "fused":
+        # one launch per step updates the neurons and delivers their spikes; entry 2 is the step-counter tick
+        kern = {
+            "k_step_lif": {"launches": int(nlaunch[0]), "ms_total": float(kms[0]),
+                           "us_per_launch": 1e3 * float(kms[0]) / max(1, nlaunch[0]),
+                           "algorithmic_bytes_per_launch": lif_bytes + deliver_bytes,
+                           "events_per_launch": ev_per_launch},
+            "k_tick_add": {"launches": int(nlaunch[2]), "ms_total": float(kms[2]),
+                           "us_per_launch": 1e3 * float(kms[2]) / max(1, nlaunch[2]),
+                           "algorithmic_bytes_per_launch": 16},
+        }
+    else:
+        kern = {
+            "k_update_lif": {"launches": int(nlaunch[0]), "ms_total": float(kms[0]),
+                             "us_per_launch": 1e3 * float(kms[0]) / max(1, nlaunch[0]),
+                             "algorithmic_bytes_per_launch": lif_bytes},
+            "k_deliver": {"launches": int(nlaunch[2]), "ms_total": float(kms[2]),
+                          "us_per_launch": 1e3 * float(kms[2]) / max(1, nlaunch[2]),
+                          "algorithmic_bytes_per_launch": deliver_bytes,
+                          "events_per_launch": ev_per_launch},
+        }
     peak, peak_kind = _peaks()
     if mode == "persistent":
         # one launch per bench step (sim_steps steps); its duration from the timed region's events
@@ -498,13 +577,16 @@ def main():
                    "potjans_diesmann_microcircuit_scale_%g" % a.scale, "neurons": N,
                    "synapses": st0["num_synapses"], "dt_ms": spec.dt, "bio_s_per_step": a.sim_steps * spec.dt * 1e-3,
                    "weights": a.weights, "parallelism": "replicas" if ws > 1 else "single",
-                   "step_loop": mode, "launch_grid": st0["launch_grid"],
-                   "l2": "CSR (%.1f GB) larger than L2 and streamed per spike; state and ring stay resident"
-                         % (st0["num_synapses"] * (4 + wbytes) / 1e9)},
+                   "step_loop": mode, "launch_grid": st0["launch_grid"], "delivery": DELIVERY[st0["delivery"]],
+                   "l2": "CSR (%.1f GB) larger than L2 and streamed per spike; state and %s stay resident"
+                         % (st0["num_synapses"] * (4 + wbytes) / 1e9,
+                            "ring" if st0["delivery"] == 1 else "input slot and pending spikes")},
         "real_time_factor": rtf,
         "build_s": build_s,
         "autotune_s": tune_s,
-        "gpu_launches": int(a.steps if mode == "persistent" else a.steps * a.sim_steps * 2),
+        "gpu_launches": int(a.steps if mode == "persistent" else
+                            a.steps * (a.sim_steps + (a.sim_steps + 99) // 100) if mode == "fused" else
+                            a.steps * a.sim_steps * 2),
         "e2e": {"value": e2e_events / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(d2h / a.steps), "real_time_factor": e2e_s / bio_s_rank},
         "roofline": roofline,
@@ -516,7 +598,7 @@ def main():
 
     if rank == 0 and ws == 1 and not a.no_variant and a.weights == "fp32":
         v = ngb.from_spec(_spec("bf16", 1), device=local, stream=stream.cuda_stream, steps_per_graph=100,
-                          drain_steps=10_000, record_capacity=4_000_000)
+                          drain_steps=10_000, record_capacity=4_000_000, delivery=a.delivery)
         v.finalize()
         if a.mode == "auto":
             v.autotune(1000)
@@ -533,7 +615,7 @@ def main():
         vb = max(1, a.steps // 2) * a.sim_steps * spec.dt * 1e-3
         line["variants"] = {"bf16_weights": {"value": (v.stats()["events"] - e0) / (vms * 1e-3),
                                              "real_time_factor": vms * 1e-3 / vb,
-                                             "step_loop": "persistent" if v.stats()["mode"] == 1 else "graph"}}
+                                             "step_loop": LOOPS[v.stats()["mode"]]}}
         v.close()
 
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:

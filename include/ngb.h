@@ -13,7 +13,11 @@
  *   - connections by the fixed-indegree and fixed-total-number rules (Sec. 2.1)
  *     stored per source, grouped by delay (Sec. 2.2);
  *   - spike delivery: every spike of step t adds each outgoing synapse weight to
- *     the target's input of step t + delay (Sec. 2.2).
+ *     the target's input of step t + delay (Sec. 2.2), either scattered at
+ *     once into a ring of future inputs, or by the paper's spike buffer (a
+ *     spike waits until its age reaches the delay of its next connection
+ *     group, which is then scattered into the next step's input); both give
+ *     the same sums.
  *
  * Conventions shared by every entry point:
  *   - Return value 0 (NGB_OK) on success, a negative NGB_ERR_* code on failure;
@@ -58,6 +62,18 @@ typedef enum { NGB_WEIGHT_FP32 = 0, NGB_WEIGHT_BF16 = 1, NGB_WEIGHT_FP16 = 2 } n
 typedef enum { NGB_LIF_PSC_EXP = 0, NGB_AEIF_COND_EXP = 1 } ngb_model;
 typedef enum { NGB_RULE_FIXED_INDEGREE = 0, NGB_RULE_FIXED_TOTAL_NUMBER = 1 } ngb_rule;
 typedef enum { NGB_DIST_CONST = 0, NGB_DIST_NORMAL = 1, NGB_DIST_UNIFORM = 2 } ngb_dist;
+/* Spike delivery scheme (results are the same; memory traffic differs):
+ *   RING          every spike is scattered at once into ring slots t + delay
+ *                 (L slots of N x receptors words);
+ *   SPIKE_BUFFER  Sec. 2.2: a spike waits in a pending list until its age
+ *                 equals the delay of its next connection group, which is
+ *                 then scattered into the next step's input (one slot), so
+ *                 the scattered-to array stays in L2 on large networks.
+ *                 With it, at most (refractory steps + 1)-spaced spikes per
+ *                 source can be in flight; an overflow is NGB_ERR_OVERFLOW.
+ *   AUTO          spike buffer when the L-slot ring would exceed half of the
+ *                 L2 cache, else ring; ngb_autotune at step 0 times both. */
+typedef enum { NGB_DELIVERY_AUTO = 0, NGB_DELIVERY_RING = 1, NGB_DELIVERY_SPIKE_BUFFER = 2 } ngb_delivery;
 typedef enum {
   NGB_VAR_V_M = 0,     /* membrane potential, mV (both models) */
   NGB_VAR_I_SYN = 1,   /* LIF: synaptic current, pA.  AdEx: adaptation current w, pA */
@@ -81,6 +97,8 @@ typedef struct {
   int64_t record_capacity; /* device spike-record entries between drains; 0 = default */
   int32_t steps_per_graph; /* steps captured in one CUDA graph; 0 = default, <0 = no graph */
   int32_t drain_steps;     /* steps between spike-record drains; 0 = default */
+  int32_t delivery;        /* ngb_delivery: 0 automatic, 1 ring, 2 spike buffer */
+  int32_t pad_;
 } ngb_sim_config;
 
 /* External Poisson drive of a population (Sec. 2.1, Poisson generator device):
@@ -159,8 +177,9 @@ typedef struct {
   int64_t ring_slots;   /* L, a power of two > max delay in steps */
   int64_t max_delay_steps;
   int64_t device_bytes; /* device memory held by the handle */
-  int64_t mode;         /* step loop: 0 per-step kernels in CUDA graphs, 1 persistent step kernel */
+  int64_t mode;         /* step loop: 0 per-step kernels in CUDA graphs, 1 persistent step kernel, 2 fused update + delivery */
   int64_t launch_grid;  /* blocks of the delivery kernel (mode 0) or of the persistent kernel (mode 1) */
+  int64_t delivery;     /* delivery scheme in use: 1 ring, 2 spike buffer */
 } ngb_stats;
 
 typedef struct ngb_sim ngb_sim;
@@ -238,20 +257,26 @@ NGB_API int ngb_simulate(ngb_sim* sim, int64_t steps);
 
 /* As ngb_simulate, without CUDA graphs, with CUDA events around every kernel
  * launch.  kernel_ms[3] receives the summed device time of the LIF update,
- * AdEx update and delivery kernels; launches[3] their launch counts. */
+ * AdEx update and delivery kernels; launches[3] their launch counts.  In the
+ * fused step loop (ngb_stats.mode 2) the update kernels include the delivery
+ * of their own spikes and entry 2 is the step-counter launch. */
 NGB_API int ngb_simulate_profiled(ngb_sim* sim, int64_t steps, double* kernel_ms, int64_t* launches);
 
 /* Autotune the step loop on this network: the per-step kernels in CUDA
- * graphs with the delivery kernel at 1, 2, 4 or 8 blocks per SM, and the
- * persistent step kernel (one cooperative launch for many steps, grid
- * barriers between its phases) at 1, 2 or 4 blocks per SM.  Each candidate is
+ * graphs with the delivery kernel at 1, 2, 4 or 8 blocks per SM; the fused
+ * loop (ring scheme: each update block delivers its own spikes, one launch
+ * per step and model, in CUDA graphs); and the persistent step kernel (one
+ * cooperative launch for many steps, grid barriers between its phases) at
+ * 1, 2 or 4 blocks per SM; at step 0 with delivery AUTO, under both delivery
+ * schemes (ngb_stats.delivery).  Each candidate is
  * timed over trial_steps steps (0 = 500); the simulation state is saved
  * before and restored after the trials, so the simulation does not advance.
  * The fastest candidate is kept (see ngb_stats.mode / launch_grid).  With the
  * environment variable NGB_AUTOTUNE_CACHE naming a file, results are looked up
  * and appended there per (GPU, network shape) key.  *deliver_grid_out (may be
- * NULL) receives the chosen grid.  The environment variable NGB_MODE=persistent
- * selects the persistent kernel at finalisation without tuning. */
+ * NULL) receives the chosen grid.  The environment variable NGB_MODE
+ * ("persistent" or "fused") selects that step loop at finalisation without
+ * tuning. */
 NGB_API int ngb_autotune(ngb_sim* sim, int64_t trial_steps, int32_t* deliver_grid_out);
 
 /* Spikes recorded in steps [t0_step, t1_step) of population `pop` (-1 = all,
@@ -273,7 +298,8 @@ NGB_API int ngb_get_state(ngb_sim* sim, int32_t var, int64_t first, int64_t n, f
 /* Copy the input accumulated so far for step (current step + step_offset),
  * receptor `receptor`, neurons [first, first+n), as FP32 (offset 0 is the
  * complete synaptic input the next update consumes; the Poisson drive is not
- * included).  0 <= step_offset < ring slots. */
+ * included).  0 <= step_offset < ring slots; with the spike-buffer delivery
+ * scheme only step_offset 0 exists (NGB_ERR_INVALID_ARG otherwise). */
 NGB_API int ngb_get_input(ngb_sim* sim, int32_t receptor, int64_t step_offset, int64_t first, int64_t n, float* out);
 
 /* Number of synapses of sources [0, N) before each source: src_ptr[N+1]. */

@@ -296,11 +296,14 @@ cudaError_t expand_synapses(uint64_t first, uint64_t n, const uint32_t* tgt, con
 // cnt_scan / grp_scan are the exclusive scans (n + 1 entries) of the
 // population's per-source synapse and group counts; k_off / g_off are the
 // population's ranges in the synapse and group pools.
+// Per-source tables of one placed population.  The population's group
+// starts and delays are already in the pool (grp_start, grp_delay).
 __global__ void k_fill_meta(uint64_t n, uint64_t off, uint64_t k_off, uint64_t g_off,
                             const unsigned long long* __restrict__ cnt_scan,
-                            const unsigned long long* __restrict__ grp_scan, uint4* __restrict__ meta,
+                            const unsigned long long* __restrict__ grp_scan, const uint64_t* __restrict__ grp_start,
+                            const uint16_t* __restrict__ grp_delay, uint4* __restrict__ meta,
                             uint64_t* __restrict__ src_syn, uint32_t* __restrict__ src_grp,
-                            unsigned long long* __restrict__ items) {
+                            uint2* __restrict__ src_age, unsigned long long* __restrict__ items) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint64_t b = k_off + cnt_scan[i];
@@ -311,15 +314,24 @@ __global__ void k_fill_meta(uint64_t n, uint64_t off, uint64_t k_off, uint64_t g
                              (uint32_t)g0);
   src_syn[off + i] = b;
   src_grp[off + i] = (uint32_t)g0;
+  // first connection group: synapses, delay, and the delay of the second group
+  uint2 ag = make_uint2(0, 0);
+  if (ng > 0) {
+    const uint64_t size0 = ng > 1 ? grp_start[g0 + 1] - grp_start[g0] : nsyn;
+    const uint32_t d0 = grp_delay[g0], d1 = ng > 1 ? grp_delay[g0 + 1] : 0u;
+    ag = make_uint2((uint32_t)size0, d0 | (d1 << 16));
+  }
+  src_age[off + i] = ag;
   if (nsyn) atomicAdd(items, (unsigned long long)((b + nsyn - (b & ~3ull) + kChunk - 1) / kChunk));
 }
 
 cudaError_t fill_meta(uint64_t n, uint64_t off, uint64_t k_off, uint64_t g_off, const unsigned long long* cnt_scan,
-                      const unsigned long long* grp_scan, uint4* meta, uint64_t* src_syn, uint32_t* src_grp,
-                      unsigned long long* items, cudaStream_t st) {
+                      const unsigned long long* grp_scan, const uint64_t* grp_start, const uint16_t* grp_delay,
+                      uint4* meta, uint64_t* src_syn, uint32_t* src_grp, uint2* src_age, unsigned long long* items,
+                      cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_fill_meta<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, off, k_off, g_off, cnt_scan, grp_scan, meta, src_syn,
-                                                           src_grp, items);
+  k_fill_meta<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, off, k_off, g_off, cnt_scan, grp_scan, grp_start,
+                                                           grp_delay, meta, src_syn, src_grp, src_age, items);
   return cudaGetLastError();
 }
 

@@ -56,9 +56,13 @@ cudaError_t exclusive_scan_u64(const unsigned long long* in, unsigned long long*
 cudaError_t expand_synapses(uint64_t first, uint64_t n, const uint32_t* tgt, const void* w, int wdtype,
                             const uint64_t* gstart, uint64_t G, const uint16_t* gdelay, uint32_t* o_tgt,
                             uint8_t* o_rc, float* o_w, uint16_t* o_d, cudaStream_t st);
+// Source tables of a placed population (meta, first synapse, first group,
+// first-group data for spike-buffer delivery); *items (device) accumulates
+// the ring scheme's delivery work items.
 cudaError_t fill_meta(uint64_t n, uint64_t off, uint64_t k_off, uint64_t g_off, const unsigned long long* cnt_scan,
-                      const unsigned long long* grp_scan, uint4* meta, uint64_t* src_syn, uint32_t* src_grp,
-                      unsigned long long* items, cudaStream_t st);
+                      const unsigned long long* grp_scan, const uint64_t* grp_start, const uint16_t* grp_delay,
+                      uint4* meta, uint64_t* src_syn, uint32_t* src_grp, uint2* src_age, unsigned long long* items,
+                      cudaStream_t st);
 cudaError_t narrow_u64_to_u32(const unsigned long long* in, uint32_t* out, uint64_t n, cudaStream_t st);
 
 }  // namespace ngb

@@ -144,4 +144,121 @@ __device__ __forceinline__ void deliver_work_item(const uint4 a, const uint4 m2,
   }
 }
 
+// The spikes of one thread block, delivered by that block (fused step loop).
+template <int kBlock>
+struct BlockSpikes {
+  uint4 meta[kBlock];         // source metadata of each spike
+  uint32_t word[kBlock];      // neuron | multiplicity << 26
+  uint32_t pre[kBlock + 1];   // first work item of each spike (prefix sum)
+  int n;
+};
+
+// Compact the block's spikes into S and scatter them into the ring (slots
+// t + d, ring scheme): the block's warps share the spikes' 128-synapse work
+// items.  S.n must be 0 and visible to the block before the call; every
+// thread of the block must call it.  Deliveries of step t land in slots
+// t + 1 ... t + L - 1, never in slot t that other blocks are still reading.
+template <typename WT, bool kFixed, int kBlock>
+__device__ __forceinline__ void deliver_block_spikes(bool spk, uint32_t gid, uint32_t mult, uint4 meta, int64_t t,
+                                                     const Csr& csr, const Ring& ring, BlockSpikes<kBlock>& S) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned ball = __ballot_sync(full, spk);
+  if (ball) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&S.n, __popc(ball));
+    base = __shfl_sync(full, base, 0);
+    if (spk) {
+      const int pos = base + __popc(ball & ((1u << lane) - 1u));
+      S.meta[pos] = meta;
+      S.word[pos] = gid | (mult << kIdBits);
+    }
+  }
+  __syncthreads();
+  const int n = S.n;
+  if (n == 0) return;
+  if (warp == 0) {
+    uint32_t carry = 0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+      const int i = i0 + lane;
+      uint32_t nch = 0;
+      if (i < n) {
+        const uint4 m = S.meta[i];
+        const uint64_t b = (uint64_t)m.x | ((uint64_t)(m.y & 0xFFFFu) << 32);
+        if (m.z) nch = (uint32_t)((b + m.z - (b & ~3ull) + kChunk - 1) / kChunk);
+      }
+      uint32_t inc = nch;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t a = __shfl_up_sync(full, inc, o);
+        if (lane >= o) inc += a;
+      }
+      if (i < n) S.pre[i + 1] = carry + inc;
+      carry += __shfl_sync(full, inc, 31);
+    }
+    if (lane == 0) S.pre[0] = 0;
+  }
+  __syncthreads();
+  const uint32_t total = S.pre[n];
+  for (uint32_t c = warp; c < total; c += kBlock / 32) {
+    int lo = 0, hi = n;  // spike owning item c: the last with pre <= c
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (S.pre[mid] <= c) lo = mid;
+      else hi = mid;
+    }
+    const uint4 m = S.meta[lo];
+    deliver_work_item<WT, kFixed>(make_uint4(S.word[lo], c - S.pre[lo], m.x, m.y), make_uint4(m.z, m.w, 0u, 0u), t,
+                                  csr, ring, lane);
+  }
+}
+
+// Spike-buffer scheme (Sec. 2.2): one due item is up to 1024 consecutive
+// synapses of one connection group (equal delay), all of which go to the
+// single ring slot (the input of the next step).  it = {first synapse lo, hi
+// | multiplicity << 16, synapses, -}.  The warp walks the item in aligned
+// chunks of 128 synapses, two chunks per pass so that both chunks' loads are
+// in flight together.
+template <typename WT, bool kFixed>
+__device__ __forceinline__ void deliver_due_item(const uint4 it, const Csr& csr, const Ring& ring, const int lane) {
+  const uint64_t b = (uint64_t)it.x | ((uint64_t)(it.y & 0xFFFFu) << 32);
+  const uint32_t mult = it.y >> 16;
+  const uint64_t e = b + it.z;
+  for (uint64_t c = b & ~3ull; c < e; c += 2 * kChunk) {
+    uint4 tv[2];
+    float wv[2][4];
+    bool any[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const uint64_t j0 = c + (uint64_t)u * kChunk + (uint64_t)lane * 4;
+      any[u] = j0 < e && j0 + 4 > b;
+      tv[u] = make_uint4(0, 0, 0, 0);
+      wv[u][0] = wv[u][1] = wv[u][2] = wv[u][3] = 0.f;
+      if (any[u]) {
+        tv[u] = __ldg(reinterpret_cast<const uint4*>(csr.tgt + j0));
+        W4<WT>::load(csr.w, j0, wv[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (!any[u]) continue;
+      const uint64_t j0 = c + (uint64_t)u * kChunk + (uint64_t)lane * 4;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint64_t j = j0 + q;
+        if (j < b || j >= e) continue;
+        const uint32_t twq = q == 0 ? tv[u].x : q == 1 ? tv[u].y : q == 2 ? tv[u].z : tv[u].w;
+        const uint64_t idx = (uint64_t)(twq >> 31) * (uint64_t)ring.N + (twq & 0x7FFFFFFFu);
+        if (kFixed) {
+          const long long qv = __float2ll_rn(wv[u][q] * 4294967296.0f) * (long long)mult;
+          atomicAdd(reinterpret_cast<unsigned long long*>(ring.p) + idx, (unsigned long long)qv);
+        } else {
+          const float v = mult == 1u ? wv[u][q] : wv[u][q] * (float)mult;
+          atomicAdd(reinterpret_cast<float*>(ring.p) + idx, v);
+        }
+      }
+    }
+  }
+}
+
 }  // namespace ngb

@@ -13,19 +13,21 @@
 // 5x, shrink exponent -1/4 capped at 10x), reset V -> V_reset, w -> w + b
 // after every accepted sub-step ending at V >= V_peak (the exponential term
 // is evaluated at min(V, V_peak)), then add the step's conductance input and
-// join the warp-ballot spike compaction with the spike multiplicity.
+// join the warp-ballot spike compaction with the spike multiplicity.  In the
+// spike-buffer delivery scheme the kernel that runs first in the step also
+// scans the pending spikes (as the LIF kernel).
 #include "aeif_rk.cuh"
 #include "neuron_step.cuh"
 
 namespace ngb {
 
-template <bool kFixed>
+template <bool kFixed, bool kAge>
 __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constant__ SegTable<AeifSeg> T,
                                                             const uint32_t* __restrict__ thr,
                                                             float* __restrict__ V_, float* __restrict__ w_,
                                                             float* __restrict__ ge_, float* __restrict__ gi_,
                                                             float* __restrict__ h_, Ring ring, int64_t* clk,
-                                                            const uint4* __restrict__ src_meta, SpikeBuf sb) {
+                                                            const Csr csr, SpikeBuf sb, int scan) {
   __shared__ uint32_t s_thr[kMaxThr];
   const AeifSeg p = segment_of(T, (int64_t)blockIdx.x);
   const int64_t k = ((int64_t)blockIdx.x - p.blk_begin) * kAeifBlock + threadIdx.x;
@@ -38,7 +40,7 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
   if (valid) {
     y = St{V_[gid], w_[gid], ge_[gid], gi_[gid]};
     h0 = h_[gid];
-    meta = __ldg(src_meta + gid);
+    if (!kAge) meta = __ldg(csr.src_meta + gid);
   }
   for (uint32_t i = threadIdx.x; i < p.n_thr; i += kAeifBlock) s_thr[i] = __ldg(thr + p.thr_off + i);
   __syncthreads();
@@ -46,6 +48,9 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
   griddep_launch();
   const int64_t t = clk[0];
   if (blockIdx.x == 0 && threadIdx.x == 0) clk[1] = t;
+  if (kAge && scan)
+    scan_pending<false>(t, csr, sb, ((int64_t)blockIdx.x * kAeifBlock + threadIdx.x) >> 5,
+                        ((int64_t)gridDim.x * kAeifBlock) >> 5);
   uint32_t nspk = 0;
   unsigned long long nsub = 0;
   if (valid) {
@@ -76,17 +81,24 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
   for (int o = 16; o > 0; o >>= 1) nsub += __shfl_xor_sync(0xffffffffu, nsub, o);
   if ((threadIdx.x & 31) == 0 && nsub) atomicAdd(sb.substeps, nsub);
   const uint32_t mult = nspk > 63u ? 63u : nspk;
-  emit_spikes(nspk > 0, gid, mult, t, meta, sb);
+  if (kAge) emit_spikes_age(nspk > 0, gid, mult, t, csr, sb);
+  else emit_spikes(nspk > 0, gid, mult, t, meta, sb);
 }
 
 cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V,
                                float* w, float* gex, float* gin, float* h, Ring ring, bool fixed, int64_t* clk,
-                               const uint4* src_meta, SpikeBuf sb, bool pdl, cudaStream_t st) {
+                               const Csr& csr, SpikeBuf sb, bool age, bool scan, bool pdl, cudaStream_t st) {
   if (blocks <= 0) return cudaSuccess;
   const dim3 g((unsigned)blocks), b(kAeifBlock);
-  if (fixed)
-    return launch_k(k_update_aeif<true>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, ring, clk, src_meta, sb);
-  return launch_k(k_update_aeif<false>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, ring, clk, src_meta, sb);
+  const int sc = scan ? 1 : 0;
+  if (fixed) {
+    if (age)
+      return launch_k(k_update_aeif<true, true>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, ring, clk, csr, sb, sc);
+    return launch_k(k_update_aeif<true, false>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, ring, clk, csr, sb, sc);
+  }
+  if (age)
+    return launch_k(k_update_aeif<false, true>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, ring, clk, csr, sb, sc);
+  return launch_k(k_update_aeif<false, false>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, ring, clk, csr, sb, sc);
 }
 
 }  // namespace ngb

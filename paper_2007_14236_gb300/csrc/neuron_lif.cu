@@ -17,33 +17,47 @@
 //      refractory, then decays the current and adds the step's input,
 //   4. tests the threshold (V >= V_th -> V = V_reset, refractory counter),
 //   5. joins the warp-ballot compaction of the new spikes.
+// In the spike-buffer delivery scheme (Sec. 2.2) the kernel that runs first in
+// the step also moves the pending spikes whose next connection group is due
+// to the step's due-item list, and a new spike reads its source's group data
+// only when it fires (no per-neuron metadata prefetch).
 // All FP32 arithmetic uses explicit round-to-nearest intrinsics, so no FMA
 // contraction changes the result: V and I are a fixed function of the input.
 #include "neuron_step.cuh"
 
 namespace ngb {
 
-template <bool kFixed>
-__global__ void __launch_bounds__(kLifBlock) k_update_lif(const __grid_constant__ SegTable<LifSeg> T,
-                                                          const uint32_t* __restrict__ thr, float* __restrict__ y_,
-                                                          float* __restrict__ I_, int32_t* __restrict__ ref_,
-                                                          Ring ring, int64_t* clk,
-                                                          const uint4* __restrict__ src_meta, SpikeBuf sb) {
+// kNpt neurons per thread (1, or 4 for networks that fill the GPU several
+// times over): a block covers 256 * kNpt consecutive neurons of one segment,
+// and each thread issues the loads of all its neurons before the first use,
+// so that enough bytes are in flight to cover the memory latency.
+template <bool kFixed, bool kAge, int kNpt>
+__global__ void __launch_bounds__(kLifBlock, kNpt > 1 ? 3 : (kAge ? 6 : 8))
+    k_update_lif(const __grid_constant__ SegTable<LifSeg> T, const uint32_t* __restrict__ thr,
+                 float* __restrict__ y_, float* __restrict__ I_, int32_t* __restrict__ ref_, Ring ring, int64_t* clk,
+                 const Csr csr, SpikeBuf sb, int scan) {
   __shared__ uint32_t s_thr[kMaxThr];
   const LifSeg sg = segment_of(T, (int64_t)blockIdx.x);
-  const int64_t k = ((int64_t)blockIdx.x - sg.blk_begin) * kLifBlock + threadIdx.x;
-  const bool valid = k < sg.n;
-  const uint32_t gid = (uint32_t)(sg.offset + k);
+  const int64_t k0 = ((int64_t)blockIdx.x - sg.blk_begin) * (kLifBlock * kNpt) + threadIdx.x;
   // Prologue, overlapping the previous kernel (programmatic dependent launch):
   // state written two launches ago, static source metadata, Poisson table.
-  float y = 0.0f, I = 0.0f;
-  int32_t ref = 0;
-  uint4 meta = make_uint4(0, 0, 0, 0);
-  if (valid) {
-    y = y_[gid];
-    I = I_[gid];
-    ref = ref_[gid];
-    meta = __ldg(src_meta + gid);
+  float y[kNpt], I[kNpt];
+  int32_t ref[kNpt];
+  uint4 meta[kNpt];
+#pragma unroll
+  for (int j = 0; j < kNpt; ++j) {
+    const int64_t k = k0 + j * kLifBlock;
+    const uint32_t gid = (uint32_t)(sg.offset + k);
+    y[j] = 0.0f;
+    I[j] = 0.0f;
+    ref[j] = 0;
+    meta[j] = make_uint4(0, 0, 0, 0);
+    if (k < sg.n) {
+      y[j] = y_[gid];
+      I[j] = I_[gid];
+      ref[j] = ref_[gid];
+      if (!kAge) meta[j] = __ldg(csr.src_meta + gid);
+    }
   }
   for (uint32_t i = threadIdx.x; i < sg.n_thr; i += kLifBlock) s_thr[i] = __ldg(thr + sg.thr_off + i);
   __syncthreads();
@@ -52,29 +66,60 @@ __global__ void __launch_bounds__(kLifBlock) k_update_lif(const __grid_constant_
   griddep_launch();
   const int64_t t = clk[0];
   if (blockIdx.x == 0 && threadIdx.x == 0) clk[1] = t;
-  bool spk = false;
-  if (valid) {
-    const uint64_t slot = (uint64_t)(t & ring.L_mask);
-    float in = ring_take<kFixed, false>(ring.p, slot * (uint64_t)ring.R * (uint64_t)ring.N + gid);
-    if (sg.n_thr > 0) {
-      const uint32_t kp = poisson_count(sg.seed, t - sg.t0, sg.local_off + (uint32_t)k, s_thr, sg.n_thr);
-      in = __fadd_rn(in, __fmul_rn((float)kp, sg.w_ext));
-    }
-    spk = lif_step(sg, y, I, ref, in);
-    y_[gid] = y;
-    I_[gid] = I;
-    ref_[gid] = ref;
+  if (kAge && scan)
+    scan_pending<false>(t, csr, sb, ((int64_t)blockIdx.x * kLifBlock + threadIdx.x) >> 5,
+                        ((int64_t)gridDim.x * kLifBlock) >> 5);
+  const uint64_t slot_base = (uint64_t)(t & ring.L_mask) * (uint64_t)ring.R * (uint64_t)ring.N;
+  float in[kNpt];
+#pragma unroll
+  for (int j = 0; j < kNpt; ++j) {
+    const int64_t k = k0 + j * kLifBlock;
+    in[j] = k < sg.n ? ring_read<kFixed, false>(ring.p, slot_base + (uint32_t)(sg.offset + k)) : 0.0f;
   }
-  emit_spikes(spk, gid, 1u, t, meta, sb);
+#pragma unroll
+  for (int j = 0; j < kNpt; ++j) {
+    const int64_t k = k0 + j * kLifBlock;
+    const uint32_t gid = (uint32_t)(sg.offset + k);
+    bool spk = false;
+    if (k < sg.n) {
+      ring_clear<kFixed>(ring.p, slot_base + gid);
+      float x = in[j];
+      if (sg.n_thr > 0) {
+        const uint32_t kp = poisson_count(sg.seed, t - sg.t0, sg.local_off + (uint32_t)k, s_thr, sg.n_thr);
+        x = __fadd_rn(x, __fmul_rn((float)kp, sg.w_ext));
+      }
+      spk = lif_step(sg, y[j], I[j], ref[j], x);
+      y_[gid] = y[j];
+      I_[gid] = I[j];
+      ref_[gid] = ref[j];
+    }
+    if (kAge) emit_spikes_age(spk, gid, 1u, t, csr, sb);
+    else emit_spikes(spk, gid, 1u, t, meta[j], sb);
+  }
 }
 
-cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, const uint32_t* thr, float* y,
-                              float* I, int32_t* ref, Ring ring, bool fixed, int64_t* clk, const uint4* src_meta,
-                              SpikeBuf sb, bool pdl, cudaStream_t st) {
+cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, int npt, const uint32_t* thr, float* y,
+                              float* I, int32_t* ref, Ring ring, bool fixed, int64_t* clk, const Csr& csr,
+                              SpikeBuf sb, bool age, bool scan, bool pdl, cudaStream_t st) {
   if (blocks <= 0) return cudaSuccess;
   const dim3 g((unsigned)blocks), b(kLifBlock);
-  if (fixed) return launch_k(k_update_lif<true>, g, b, pdl, st, segs, thr, y, I, ref, ring, clk, src_meta, sb);
-  return launch_k(k_update_lif<false>, g, b, pdl, st, segs, thr, y, I, ref, ring, clk, src_meta, sb);
+  const int sc = scan ? 1 : 0;
+#define NGB_LIF(F, A, P) return launch_k(k_update_lif<F, A, P>, g, b, pdl, st, segs, thr, y, I, ref, ring, clk, csr, sb, sc)
+  if (npt == 4) {
+    if (fixed) {
+      if (age) NGB_LIF(true, true, 4);
+      NGB_LIF(true, false, 4);
+    }
+    if (age) NGB_LIF(false, true, 4);
+    NGB_LIF(false, false, 4);
+  }
+  if (fixed) {
+    if (age) NGB_LIF(true, true, 1);
+    NGB_LIF(true, false, 1);
+  }
+  if (age) NGB_LIF(false, true, 1);
+  NGB_LIF(false, false, 1);
+#undef NGB_LIF
 }
 
 // Step counter hand-over when no update kernel runs (a network with no

@@ -34,6 +34,25 @@ __device__ __forceinline__ float ring_take(void* ring, uint64_t idx) {
   return v;
 }
 
+// The same as ring_take in two parts, so that several neurons' reads can be
+// issued before any slot is cleared.
+template <bool kFixed, bool kCoherent>
+__device__ __forceinline__ float ring_read(const void* ring, uint64_t idx) {
+  if (kFixed) {
+    const long long* rp = reinterpret_cast<const long long*>(ring) + idx;
+    const long long v = kCoherent ? __ldcg(rp) : *rp;
+    return __double2float_rn(__dmul_rn(__ll2double_rn(v), 2.3283064365386963e-10));  // x 2^-32
+  }
+  const float* rp = reinterpret_cast<const float*>(ring) + idx;
+  return kCoherent ? __ldcg(rp) : *rp;
+}
+
+template <bool kFixed>
+__device__ __forceinline__ void ring_clear(void* ring, uint64_t idx) {
+  if (kFixed) reinterpret_cast<long long*>(ring)[idx] = 0;
+  else reinterpret_cast<float*>(ring)[idx] = 0.0f;
+}
+
 __device__ __forceinline__ uint32_t poisson_count(uint64_t seed, int64_t tl, uint32_t sid, const uint32_t* thr,
                                                   uint32_t n_thr) {
   const U4 r = draw4(seed, (uint64_t)tl, kPurPoisson, 0u, sid);

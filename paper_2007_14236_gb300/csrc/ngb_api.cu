@@ -12,6 +12,13 @@
 // (clk), so a captured graph of S steps can be replayed unchanged; host and
 // device meet only at drain points (every drain_steps steps and at the end of
 // ngb_simulate) to collect the spike record and error flags.
+//
+// Delivery scheme (ngb_sim_config.delivery): the ring scheme scatters each
+// spike at once into ring slots t + d (L slots); the spike-buffer scheme of
+// Sec. 2.2 keeps spikes pending until their next connection group is due and
+// scatters into one slot (the next step's input).  Automatic choice: the
+// spike buffer when the L-slot ring would not fit in half the L2 cache;
+// ngb_autotune may also time both while the simulation is at step 0.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -134,6 +141,8 @@ std::vector<uint32_t> poisson_thresholds(double lambda) {
   return out;
 }
 
+constexpr int kCounters = 8;  // device counter words: ctr[2], events, substeps, rec_count, spare, pcnt[2]
+
 uint64_t next_pow2(uint64_t x) {
   uint64_t p = 1;
   while (p < x) p <<= 1;
@@ -182,16 +191,19 @@ struct ngb_sim {
   uint4* src_meta = nullptr;
   SpikeBuf sb{};
   int64_t* clk = nullptr;
+  uint2* src_age = nullptr;  // first-group data per source (spike-buffer scheme)
+  int scheme = 1;            // 1 ring, 2 spike buffer
   SegTable<LifSeg> lif_tab{};
   int n_lif = 0;
   int64_t lif_blocks = 0;
+  int lif_npt = 1;  // LIF neurons per thread of the per-step update kernel (1 or 4)
   SegTable<AeifSeg> aeif_tab{};
   int n_aeif = 0;
   int64_t aeif_blocks = 0;
   uint32_t* thr = nullptr;
   int deliver_grid = 0;
   bool pdl = true;  // programmatic dependent launch between the step's kernels
-  int mode = 0;     // 0: per-step kernels in CUDA graphs, 1: persistent step kernel
+  int mode = 0;     // 0: per-step kernels in CUDA graphs, 1: persistent step kernel, 2: fused update + delivery
   bool persist_ok = false;
   int persist_grid = 0;
   int persist_max_bpsm = 0;
@@ -233,30 +245,62 @@ struct ngb_sim {
 
 namespace {
 
-Ring ring_of(const ngb_sim* s) { return Ring{s->ring, s->N_cap, (uint32_t)(s->L - 1), s->R}; }
-
-Csr csr_of(const ngb_sim* s) {
-  return Csr{s->src_meta, s->src_syn, s->src_grp, s->grp_start, s->grp_delay, s->tgt, s->w};
+// The spike-buffer scheme uses one ring slot (L_mask 0).
+Ring ring_of(const ngb_sim* s) {
+  return Ring{s->ring, s->N_cap, (uint32_t)(s->scheme == 2 ? 0 : s->L - 1), s->R};
 }
 
+Csr csr_of(const ngb_sim* s) {
+  return Csr{s->src_meta, s->src_syn, s->src_grp, s->grp_start, s->grp_delay, s->tgt, s->w, s->src_age};
+}
+
+// The first update kernel of the step scans the pending spikes (spike-buffer scheme).
 cudaError_t launch_lif(ngb_sim* s) {
-  return launch_update_lif(s->lif_tab, s->lif_blocks, s->thr, s->st0, s->st1, s->ref, ring_of(s),
-                           s->cfg.deterministic != 0, s->clk, s->src_meta, s->sb, s->pdl, s->stream);
+  return launch_update_lif(s->lif_tab, s->lif_blocks, s->lif_npt, s->thr, s->st0, s->st1, s->ref, ring_of(s),
+                           s->cfg.deterministic != 0, s->clk, csr_of(s), s->sb, s->scheme == 2, true, s->pdl,
+                           s->stream);
 }
 
 cudaError_t launch_aeif(ngb_sim* s) {
   return launch_update_aeif(s->aeif_tab, s->aeif_blocks, s->thr, s->st0, s->st1, s->st2, s->st3, s->st4,
-                            ring_of(s), s->cfg.deterministic != 0, s->clk, s->src_meta, s->sb, s->pdl,
-                            s->stream);
+                            ring_of(s), s->cfg.deterministic != 0, s->clk, csr_of(s), s->sb, s->scheme == 2,
+                            s->n_lif == 0, s->pdl, s->stream);
 }
 
 cudaError_t launch_del(ngb_sim* s) {
-  return launch_deliver(s->sb, csr_of(s), s->cfg.weight_dtype, ring_of(s), s->cfg.deterministic != 0, s->clk,
-                        s->deliver_grid, s->pdl, s->stream);
+  return launch_deliver(s->sb, csr_of(s), s->cfg.weight_dtype, ring_of(s), s->cfg.deterministic != 0,
+                        s->scheme == 2, s->clk, s->deliver_grid, s->pdl, s->stream);
+}
+
+// Switch the delivery scheme (only while no spike is in flight: step 0).
+void set_scheme(ngb_sim* s, int scheme) {
+  s->scheme = scheme;
+  s->pa.ring = ring_of(s);
+  s->pa.csr = csr_of(s);
+  s->pa.age = scheme == 2 ? 1 : 0;
+}
+
+// Fused step loop (mode 2, ring scheme): update kernels that deliver their
+// blocks' spikes; the step is clk[0] + step_off.
+cudaError_t launch_fused(ngb_sim* s, int64_t step_off) {
+  cudaError_t e = cudaSuccess;
+  const bool det = s->cfg.deterministic != 0;
+  if (s->n_lif)
+    e = launch_step_lif(s->lif_tab, s->lif_blocks, s->thr, s->st0, s->st1, s->ref, ring_of(s), det,
+                        s->cfg.weight_dtype, s->clk, step_off, csr_of(s), s->sb, s->pdl, s->stream);
+  if (e == cudaSuccess && s->n_aeif)
+    e = launch_step_aeif(s->aeif_tab, s->aeif_blocks, s->thr, s->st0, s->st1, s->st2, s->st3, s->st4, ring_of(s),
+                         det, s->cfg.weight_dtype, s->clk, step_off, csr_of(s), s->sb, s->pdl, s->stream);
+  return e;
 }
 
 cudaError_t launch_step(ngb_sim* s) {
   cudaError_t e;
+  if (s->mode == 2) {
+    e = launch_fused(s, 0);
+    if (e != cudaSuccess) return e;
+    return launch_tick_add(s->clk, 1, s->sb.ctr, s->pdl, s->stream);
+  }
   if (!s->n_lif && !s->n_aeif) {
     e = launch_tick(s->clk, s->pdl, s->stream);
     if (e != cudaSuccess) return e;
@@ -307,6 +351,9 @@ int drain(ngb_sim* s) {
     s->failed = true;
     return fail(NGB_ERR_TIMEOUT, "persistent step kernel: a grid barrier wait gave up (handle unusable)");
   }
+  if (err & kErrPendingOverflow)
+    return fail(NGB_ERR_OVERFLOW,
+                "spike-buffer delivery: more spikes in flight than the pending list holds (use the ring scheme)");
   if (err & kErrRecordOverflow)
     return fail(NGB_ERR_OVERFLOW, "spike record overflow: raise record_capacity or lower drain_steps");
   if (err & kErrSubstepCap)
@@ -325,7 +372,12 @@ int capture_graph(ngb_sim* s) {
   cudaGraph_t graph = nullptr;
   CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
-  for (int i = 0; i < s->graph_steps && e == cudaSuccess; ++i) e = launch_step(s);
+  if (s->mode == 2) {
+    for (int i = 0; i < s->graph_steps && e == cudaSuccess; ++i) e = launch_fused(s, i);
+    if (e == cudaSuccess) e = launch_tick_add(s->clk, s->graph_steps, s->sb.ctr, s->pdl, s->stream);
+  } else {
+    for (int i = 0; i < s->graph_steps && e == cudaSuccess; ++i) e = launch_step(s);
+  }
   cudaError_t e2 = cudaStreamEndCapture(s->stream, &graph);
   if (e != cudaSuccess) return cuda_fail(e, "graph capture (kernel launch)");
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
@@ -535,8 +587,8 @@ int place_parts(ngb_sim* s, std::vector<PopParts>& parts, uint64_t* running_g, u
       CK(cudaMemcpyAsync(s->grp_start + g_off, q.gs, q.G * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st));
       CK(cudaMemcpyAsync(s->grp_delay + g_off, q.gd, q.G * sizeof(uint16_t), cudaMemcpyDeviceToDevice, st));
     }
-    CK(fill_meta((uint64_t)p.n, (uint64_t)p.offset, p.k_off, g_off, q.cnt_scan, q.grp_scan, s->src_meta, s->src_syn,
-                 s->src_grp, items, st));
+    CK(fill_meta((uint64_t)p.n, (uint64_t)p.offset, p.k_off, g_off, q.cnt_scan, q.grp_scan, s->grp_start,
+                 s->grp_delay, s->src_meta, s->src_syn, s->src_grp, s->src_age, items, st));
   }
   unsigned long long ih = 0;
   CK(cudaMemcpyAsync(&ih, items, sizeof(ih), cudaMemcpyDeviceToHost, st));
@@ -606,6 +658,17 @@ int rebuild_tables(ngb_sim* s) {
   s->lif_blocks = 0;
   s->aeif_blocks = 0;
   s->n_active = 0;
+  {
+    // several LIF neurons per thread when the update grid would fill the GPU
+    // more than twice over at one neuron per thread
+    int64_t n_lif_total = 0;
+    for (const PopHost& p : s->pops)
+      if (p.placed && s->inst[(size_t)p.instance].state == 1 && p.model == NGB_LIF_PSC_EXP) n_lif_total += p.n;
+    s->lif_npt = n_lif_total > 2 * (int64_t)std::max(1, s->sms) * 2048 ? 4 : 1;
+    const char* env_npt = std::getenv("NGB_LIF_NPT");
+    if (env_npt && (std::atoi(env_npt) == 1 || std::atoi(env_npt) == 4)) s->lif_npt = std::atoi(env_npt);
+  }
+  const int64_t lif_tile = (int64_t)kLifBlock * s->lif_npt;
   for (const PopHost& p : s->pops) {
     if (!p.placed || s->inst[(size_t)p.instance].state != 1) continue;
     s->n_active += p.n;
@@ -640,7 +703,7 @@ int rebuild_tables(ngb_sim* s) {
       g.y_reset = (float)(q.V_reset_mV - q.E_L_mV);
       g.w_ext = (float)q.poisson.weight;
       lsegs.push_back(g);
-      s->lif_blocks += (p.n + kLifBlock - 1) / kLifBlock;
+      s->lif_blocks += (p.n + lif_tile - 1) / lif_tile;
     } else {
       const ngb_aeif_params& q = p.aeif;
       AeifSeg g{};
@@ -695,7 +758,7 @@ int rebuild_tables(ngb_sim* s) {
     for (int i = 0; i < std::min(s->n_lif, kInlineSegs); ++i) s->lif_tab.s[i] = lsegs[(size_t)i];
     std::vector<uint32_t> bs((size_t)s->lif_blocks);
     for (size_t i = 0; i < lsegs.size(); ++i) {
-      const int64_t nb = (lsegs[i].n + kLifBlock - 1) / kLifBlock;
+      const int64_t nb = (lsegs[i].n + lif_tile - 1) / lif_tile;
       for (int64_t b = 0; b < nb; ++b) bs[(size_t)(lsegs[i].blk_begin + b)] = (uint32_t)i;
     }
     uint32_t* db = nullptr;
@@ -758,6 +821,7 @@ int rebuild_tables(ngb_sim* s) {
     a.spin_limit = env_spin ? std::strtoull(env_spin, nullptr, 10) : (1ull << 24);
     const char* env_wh = std::getenv("NGB_TEST_WITHHOLD_BLOCK");
     a.withhold_block = env_wh ? std::atoi(env_wh) : -1;
+    a.age = s->scheme == 2 ? 1 : 0;
     a.off_aseg = (uint32_t)a16(lsegs.size() * sizeof(LifSeg));
     a.off_lvoff = a.off_aseg + (uint32_t)a16(asegs.size() * sizeof(AeifSeg));
     a.off_avoff = a.off_lvoff + (uint32_t)a16(lv.size() * 8);
@@ -776,8 +840,10 @@ int rebuild_tables(ngb_sim* s) {
       }
       cudaGetLastError();
     }
-    if (!s->persist_ok) s->mode = 0;
+    if (!s->persist_ok && s->mode == 1) s->mode = 0;
   }
+  // the fused loop runs one LIF neuron per thread and delivers with the ring scheme
+  if (s->mode == 2 && (s->lif_npt != 1 || s->scheme != 1)) s->mode = 0;
   s->tables_dirty = false;
   return capture_graph(s);
 }
@@ -823,6 +889,8 @@ int finalize_impl(ngb_sim* s) {
   CK(s->dalloc(&s->src_syn, N + 1));
   CK(s->dalloc(&s->src_grp, N + 1));
   CK(s->dalloc(&s->src_meta, N));
+  CK(s->dalloc(&s->src_age, N));
+  CK(cudaMemsetAsync(s->src_age, 0, N * sizeof(uint2), st));
   CK(cudaMemsetAsync(s->src_syn, 0, (N + 1) * sizeof(uint64_t), st));
   CK(cudaMemsetAsync(s->src_grp, 0, (N + 1) * sizeof(uint32_t), st));
   CK(cudaMemsetAsync(s->src_meta, 0, N * sizeof(uint4), st));
@@ -837,12 +905,13 @@ int finalize_impl(ngb_sim* s) {
 
   // counters, clock, spike record, barrier
   unsigned long long* ctrs = nullptr;
-  CK(s->dalloc(&ctrs, 6));  // ctr[2], events, substeps, rec_count, spare
-  CK(cudaMemsetAsync(ctrs, 0, 6 * sizeof(unsigned long long), st));
+  CK(s->dalloc(&ctrs, kCounters));  // ctr[2], events, substeps, rec_count, spare, pcnt[2]
+  CK(cudaMemsetAsync(ctrs, 0, kCounters * sizeof(unsigned long long), st));
   s->sb.ctr = ctrs;
   s->sb.events = ctrs + 2;
   s->sb.substeps = ctrs + 3;
   s->sb.rec_count = ctrs + 4;
+  s->sb.pcnt = ctrs + 6;
   CK(s->dalloc(&s->sb.err, 1));
   CK(cudaMemsetAsync(s->sb.err, 0, sizeof(uint32_t), st));
   CK(s->dalloc(&s->clk, 2));
@@ -916,8 +985,43 @@ int finalize_impl(ngb_sim* s) {
   s->G = s->G_cap;
   if (items >= (1ull << 32)) return fail(NGB_ERR_INVALID_ARG, "ngb_finalize: more than 2^32 delivery work items");
   s->work_items = items;
-  CK(s->dalloc(&s->sb.wi[0], 2 * s->work_items + 2));
-  CK(s->dalloc(&s->sb.wi[1], 2 * s->work_items + 2));
+  // delivery scheme (ngb_sim_config.delivery; automatic: spike buffer when the ring would not stay in L2)
+  {
+    int l2 = 0;
+    CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    const double ring_full = (double)s->L * s->R * (double)N * (s->cfg.deterministic ? 8 : 4);
+    if (s->cfg.delivery == 1) s->scheme = 1;
+    else if (s->cfg.delivery == 2) s->scheme = 2;
+    else s->scheme = ring_full > 0.5 * (double)l2 ? 2 : 1;
+  }
+  // pending-spike lists (spike-buffer scheme): a source has at most one spike
+  // per refractory period + 1 steps in flight, and none older than the
+  // largest delay
+  uint64_t wi_entries = 2 * s->work_items + 2;
+  if (s->cfg.delivery != 1) {
+    uint64_t cap = 1024;
+    if (s->serving) {
+      cap += (uint64_t)N * (uint64_t)std::min<int64_t>(s->L, 8);
+    } else {
+      const int64_t D = std::max(1, s->max_delay);
+      for (const PopHost& p : s->pops) {
+        int64_t ref = 0;
+        if (p.model == NGB_LIF_PSC_EXP) ref = std::max<int64_t>(0, (int64_t)std::nearbyint(p.lif.t_ref_ms / s->cfg.dt_ms));
+        const int64_t per = std::min<int64_t>(D, (D + ref) / (ref + 1) + 1);
+        cap += (uint64_t)p.n * (uint64_t)per;
+      }
+    }
+    const char* env_cap = std::getenv("NGB_TEST_PENDING_CAP");
+    if (env_cap) cap = std::strtoull(env_cap, nullptr, 10);
+    s->sb.pend_cap = (int64_t)cap;
+    CK(s->dalloc(&s->sb.pend[0], cap + 1));
+    CK(s->dalloc(&s->sb.pend[1], cap + 1));
+    // due items per step: at most one per pending or new spike plus one per 1024 synapses
+    wi_entries = std::max<uint64_t>(wi_entries, cap + (uint64_t)N + s->K_cap / kAgeSpan + 2);
+  }
+  s->sb.wi_cap = (int64_t)wi_entries;
+  CK(s->dalloc(&s->sb.wi[0], wi_entries));
+  CK(s->dalloc(&s->sb.wi[1], wi_entries));
   // ring buffer
   const size_t ring_bytes = (size_t)s->L * s->R * N * (s->cfg.deterministic ? 8 : 4);
   CK(s->dalloc((uint8_t**)&s->ring, ring_bytes));
@@ -935,7 +1039,9 @@ int finalize_impl(ngb_sim* s) {
     }
   }
   const char* env_mode = std::getenv("NGB_MODE");
-  s->mode = (env_mode && std::string(env_mode) == "persistent") ? 1 : 0;
+  s->mode = 0;
+  if (env_mode && std::string(env_mode) == "persistent") s->mode = 1;
+  if (env_mode && std::string(env_mode) == "fused" && s->scheme == 1) s->mode = 2;
   s->graph_steps = s->cfg.steps_per_graph == 0 ? 100 : std::max(0, s->cfg.steps_per_graph);
   return rebuild_tables(s);
 }
@@ -996,14 +1102,21 @@ int simulate_impl(ngb_sim* s, int64_t steps, bool profiled, double* kernel_ms, i
   int rc_final = NGB_OK;
   while (left > 0 && rc_final == NGB_OK) {
     const int64_t chunk = std::min<int64_t>(left, std::min<int64_t>(kBatch, s->drain_steps));
+    const bool fused = s->mode == 2;
     for (int64_t i = 0; i < chunk; ++i) {
       cudaEvent_t* e = &ev[4 * i];
       CK(cudaEventRecord(e[0], s->stream));
-      if (s->n_lif) CK(launch_lif(s));
+      if (s->n_lif) CK(fused ? launch_step_lif(s->lif_tab, s->lif_blocks, s->thr, s->st0, s->st1, s->ref, ring_of(s),
+                                               s->cfg.deterministic != 0, s->cfg.weight_dtype, s->clk, 0, csr_of(s),
+                                               s->sb, s->pdl, s->stream)
+                             : launch_lif(s));
       CK(cudaEventRecord(e[1], s->stream));
-      if (s->n_aeif) CK(launch_aeif(s));
+      if (s->n_aeif) CK(fused ? launch_step_aeif(s->aeif_tab, s->aeif_blocks, s->thr, s->st0, s->st1, s->st2, s->st3,
+                                                 s->st4, ring_of(s), s->cfg.deterministic != 0, s->cfg.weight_dtype,
+                                                 s->clk, 0, csr_of(s), s->sb, s->pdl, s->stream)
+                              : launch_aeif(s));
       CK(cudaEventRecord(e[2], s->stream));
-      CK(launch_del(s));
+      CK(fused ? launch_tick_add(s->clk, 1, s->sb.ctr, s->pdl, s->stream) : launch_del(s));
       CK(cudaEventRecord(e[3], s->stream));
     }
     CK(cudaStreamSynchronize(s->stream));
@@ -1044,8 +1157,12 @@ int snapshot_take(ngb_sim* s, Snapshot& sn) {
   const int64_t N = s->N_cap;
   const size_t ring_bytes = (size_t)s->L * s->R * N * (s->cfg.deterministic ? 8 : 4);
   sn.parts = {{s->st0, N * 4}, {s->st1, N * 4}, {s->ref, N * 4}, {s->ring, ring_bytes},
-              {s->sb.ctr, 6 * sizeof(unsigned long long)}, {s->clk, 2 * sizeof(int64_t)},
+              {s->sb.ctr, kCounters * sizeof(unsigned long long)}, {s->clk, 2 * sizeof(int64_t)},
               {s->sb.err, sizeof(uint32_t)}};
+  if (s->sb.pend[0]) {
+    sn.parts.push_back({s->sb.pend[0], (size_t)s->sb.pend_cap * sizeof(uint4)});
+    sn.parts.push_back({s->sb.pend[1], (size_t)s->sb.pend_cap * sizeof(uint4)});
+  }
   if (s->st2) {
     sn.parts.push_back({s->st2, N * 4});
     sn.parts.push_back({s->st3, N * 4});
@@ -1076,9 +1193,10 @@ std::string tune_key(ngb_sim* s) {
   cudaDeviceProp prop{};
   cudaGetDeviceProperties(&prop, s->cfg.device);
   char buf[512];
-  std::snprintf(buf, sizeof(buf), "%s|sm%d|N%lld|K%llu|G%llu|L%lld|R%d|w%d|det%d|lif%d|aeif%d", prop.name,
+  std::snprintf(buf, sizeof(buf), "%s|sm%d|N%lld|K%llu|G%llu|L%lld|R%d|w%d|det%d|lif%d|aeif%d|dl%d", prop.name,
                 prop.multiProcessorCount, (long long)s->N, (unsigned long long)s->K, (unsigned long long)s->G,
-                (long long)s->L, s->R, s->cfg.weight_dtype, s->cfg.deterministic, s->n_lif, s->n_aeif);
+                (long long)s->L, s->R, s->cfg.weight_dtype, s->cfg.deterministic, s->n_lif, s->n_aeif,
+                s->cfg.delivery);
   for (char* c = buf; *c; ++c)
     if (*c == ' ') *c = '_';
   return buf;
@@ -1100,6 +1218,7 @@ int ngb_create(ngb_sim** out, const ngb_sim_config* cfg) {
   if (cfg->weight_dtype < NGB_WEIGHT_FP32 || cfg->weight_dtype > NGB_WEIGHT_FP16)
     return fail(NGB_ERR_INVALID_ARG, "ngb_create: weight_dtype");
   if (cfg->record_capacity < 0 || cfg->drain_steps < 0) return fail(NGB_ERR_INVALID_ARG, "ngb_create: capacities");
+  if (cfg->delivery < 0 || cfg->delivery > 2) return fail(NGB_ERR_INVALID_ARG, "ngb_create: delivery");
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
@@ -1258,18 +1377,27 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
       return rc;
     }
   }
+  if (s->tables_dirty) {
+    rc = rebuild_tables(s);
+    if (rc != NGB_OK) return rc;
+  }
   if (trial_steps == 0) trial_steps = 500;
   int dev = 0, sms = 1;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  // Both delivery schemes are candidates only while no spike is in flight
+  // (step 0) and the configuration leaves the choice open.
+  const bool both = s->cfg.delivery == 0 && s->t == 0 && !s->serving && s->sb.pend[0] != nullptr;
   const std::string key = tune_key(s);
   const char* cache = std::getenv("NGB_AUTOTUNE_CACHE");
   if (cache && *cache) {
     std::ifstream in(cache);
     std::string k;
-    int m = 0, g = 0, pg = 0;
-    while (in >> k >> m >> g >> pg) {
-      if (k == key && g > 0 && (m == 0 || (s->persist_ok && pg > 0))) {
+    int m = 0, g = 0, pg = 0, sc = 0;
+    while (in >> k >> m >> g >> pg >> sc) {
+      if (k == key && g > 0 && (m == 0 || (m == 2 && sc == 1) || (s->persist_ok && pg > 0)) &&
+          (sc == s->scheme || both)) {
+        set_scheme(s, sc);
         s->mode = m;
         s->deliver_grid = g;
         if (pg > 0) s->persist_grid = pg;
@@ -1287,54 +1415,87 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
   }
   const int saved_graph_steps = s->graph_steps;
   if (s->graph_steps <= 0) s->graph_steps = 100;
-  int best_mode = 0, best_grid = s->deliver_grid, best_pgrid = s->persist_grid;
+  int best_mode = 0, best_grid = s->deliver_grid, best_pgrid = s->persist_grid, best_scheme = s->scheme;
   double best_ms = 1e30;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  // per-step kernels in graphs: delivery blocks per SM
-  for (int b : {1, 2, 4, 8}) {
-    s->deliver_grid = b * sms;
-    rc = capture_graph(s);
-    if (rc == NGB_OK) rc = snapshot_restore(s, sn);
+  std::vector<int> schemes;
+  if (both) schemes = {1, 2};
+  else schemes = {s->scheme};
+  for (int scheme : schemes) {
     if (rc != NGB_OK) break;
-    const int64_t reps = std::max<int64_t>(1, trial_steps / s->graph_steps);
-    CK(cudaGraphLaunch(s->gexec, s->stream));  // warm-up replay
-    CK(cudaEventRecord(e0, s->stream));
-    for (int64_t r = 0; r < reps; ++r) CK(cudaGraphLaunch(s->gexec, s->stream));
-    CK(cudaEventRecord(e1, s->stream));
-    CK(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    const double per_step = ms / (double)(reps * s->graph_steps);
-    if (per_step < best_ms) {
-      best_ms = per_step;
-      best_mode = 0;
-      best_grid = s->deliver_grid;
-    }
-  }
-  // persistent step kernel: blocks per SM
-  if (rc == NGB_OK && s->persist_ok) {
-    for (int b : {1, 2, 4}) {
-      if (b > s->persist_max_bpsm) break;
-      s->persist_grid = b * sms;
-      rc = snapshot_restore(s, sn);
+    set_scheme(s, scheme);
+    s->mode = 0;
+    // per-step kernels in graphs: delivery blocks per SM
+    for (int b : {1, 2, 4, 8}) {
+      s->deliver_grid = b * sms;
+      rc = capture_graph(s);
+      if (rc == NGB_OK) rc = snapshot_restore(s, sn);
       if (rc != NGB_OK) break;
-      CK(launch_persistent_chunk(s, 100));  // warm-up
+      const int64_t reps = std::max<int64_t>(1, trial_steps / s->graph_steps);
+      CK(cudaGraphLaunch(s->gexec, s->stream));  // warm-up replay
       CK(cudaEventRecord(e0, s->stream));
-      CK(launch_persistent_chunk(s, trial_steps));
+      for (int64_t r = 0; r < reps; ++r) CK(cudaGraphLaunch(s->gexec, s->stream));
       CK(cudaEventRecord(e1, s->stream));
       CK(cudaEventSynchronize(e1));
-      uint32_t err = 0;
-      CK(cudaMemcpy(&err, s->sb.err, sizeof(err), cudaMemcpyDeviceToHost));
-      if (err & kErrBarrierTimeout) continue;  // never chosen; the snapshot restores the flags
       float ms = 0.f;
       CK(cudaEventElapsedTime(&ms, e0, e1));
-      const double per_step = ms / (double)trial_steps;
+      const double per_step = ms / (double)(reps * s->graph_steps);
       if (per_step < best_ms) {
         best_ms = per_step;
-        best_mode = 1;
-        best_pgrid = s->persist_grid;
+        best_mode = 0;
+        best_grid = s->deliver_grid;
+        best_scheme = scheme;
+      }
+    }
+    // fused update + delivery in graphs (ring scheme)
+    if (rc == NGB_OK && scheme == 1 && s->lif_npt == 1) {
+      s->mode = 2;
+      rc = capture_graph(s);
+      if (rc == NGB_OK) rc = snapshot_restore(s, sn);
+      if (rc == NGB_OK) {
+        const int64_t reps = std::max<int64_t>(1, trial_steps / s->graph_steps);
+        CK(cudaGraphLaunch(s->gexec, s->stream));  // warm-up replay
+        CK(cudaEventRecord(e0, s->stream));
+        for (int64_t r = 0; r < reps; ++r) CK(cudaGraphLaunch(s->gexec, s->stream));
+        CK(cudaEventRecord(e1, s->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        const double per_step = ms / (double)(reps * s->graph_steps);
+        if (per_step < best_ms) {
+          best_ms = per_step;
+          best_mode = 2;
+          best_scheme = scheme;
+        }
+      }
+      s->mode = 0;
+    }
+    // persistent step kernel: blocks per SM
+    if (rc == NGB_OK && s->persist_ok) {
+      for (int b : {1, 2, 4}) {
+        if (b > s->persist_max_bpsm) break;
+        s->persist_grid = b * sms;
+        rc = snapshot_restore(s, sn);
+        if (rc != NGB_OK) break;
+        CK(launch_persistent_chunk(s, 100));  // warm-up
+        CK(cudaEventRecord(e0, s->stream));
+        CK(launch_persistent_chunk(s, trial_steps));
+        CK(cudaEventRecord(e1, s->stream));
+        CK(cudaEventSynchronize(e1));
+        uint32_t err = 0;
+        CK(cudaMemcpy(&err, s->sb.err, sizeof(err), cudaMemcpyDeviceToHost));
+        if (err & kErrBarrierTimeout) continue;  // never chosen; the snapshot restores the flags
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        const double per_step = ms / (double)trial_steps;
+        if (per_step < best_ms) {
+          best_ms = per_step;
+          best_mode = 1;
+          best_pgrid = s->persist_grid;
+          best_scheme = scheme;
+        }
       }
     }
   }
@@ -1343,6 +1504,7 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
   if (rc == NGB_OK) rc = snapshot_restore(s, sn);
   snapshot_free(sn);
   s->graph_steps = saved_graph_steps;
+  set_scheme(s, best_scheme);
   s->deliver_grid = best_grid;
   s->persist_grid = best_pgrid;
   s->mode = best_mode;
@@ -1350,7 +1512,8 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
   if (rc != NGB_OK) return rc;
   if (cache && *cache) {
     std::ofstream out(cache, std::ios::app);
-    out << key << " " << best_mode << " " << best_grid << " " << (s->persist_ok ? best_pgrid : 0) << "\n";
+    out << key << " " << best_mode << " " << best_grid << " " << (s->persist_ok ? best_pgrid : 0) << " "
+        << best_scheme << "\n";
   }
   if (deliver_grid_out) *deliver_grid_out = best_mode == 1 ? best_pgrid : best_grid;
   return NGB_OK;
@@ -1405,6 +1568,16 @@ int ngb_retire_instance(ngb_sim* s, int32_t instance) {
   if (instance < 0 || instance >= (int32_t)s->inst.size() || s->inst[(size_t)instance].state != 1)
     return fail(NGB_ERR_INVALID_ARG, "ngb_retire_instance: instance is not active");
   CK(cudaStreamSynchronize(s->stream));
+  if (s->scheme == 2) {
+    // spikes of the instance still waiting for a connection group are dropped
+    const int pb = (int)(s->t & 1);
+    for (const PopHost& p : s->pops) {
+      if (p.instance != instance || !p.placed) continue;
+      CK(launch_kill_pending(s->sb.pend[pb], s->sb.pcnt + pb, s->sb.pend_cap, (uint32_t)p.offset,
+                             (uint32_t)(p.offset + p.n), s->stream));
+    }
+    CK(cudaStreamSynchronize(s->stream));
+  }
   release_instance_ranges(s, instance);
   s->inst[(size_t)instance].state = 2;
   s->tables_dirty = true;
@@ -1483,7 +1656,8 @@ int ngb_get_stats(ngb_sim* s, ngb_stats* out) {
     out->max_delay_steps = s->max_delay;
     out->device_bytes = (int64_t)s->dev_bytes;
     out->mode = s->mode;
-    out->launch_grid = s->mode == 1 ? s->persist_grid : s->deliver_grid;
+    out->launch_grid = s->mode == 1 ? s->persist_grid : s->mode == 2 ? s->lif_blocks + s->aeif_blocks : s->deliver_grid;
+    out->delivery = s->scheme;
   }
   return NGB_OK;
 }
@@ -1542,8 +1716,11 @@ int ngb_get_input(ngb_sim* s, int32_t receptor, int64_t step_offset, int64_t fir
   if (!out || receptor < 0 || receptor >= s->R || step_offset < 0 || step_offset >= s->L || first < 0 || n < 0 ||
       first + n > s->N_cap)
     return fail(NGB_ERR_INVALID_ARG, "ngb_get_input: range");
+  if (s->scheme == 2 && step_offset != 0)
+    return fail(NGB_ERR_INVALID_ARG,
+                "ngb_get_input: with spike-buffer delivery only the next step's input (step_offset 0) exists");
   if (n == 0) return NGB_OK;
-  const uint64_t slot = (uint64_t)((s->t + step_offset) & (s->L - 1));
+  const uint64_t slot = s->scheme == 2 ? 0 : (uint64_t)((s->t + step_offset) & (s->L - 1));
   const uint64_t off = (slot * (uint64_t)s->R + (uint64_t)receptor) * (uint64_t)s->N_cap + (uint64_t)first;
   if (s->cfg.deterministic) {
     std::vector<long long> tmp((size_t)n);

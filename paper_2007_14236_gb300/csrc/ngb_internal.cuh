@@ -21,6 +21,29 @@
 //              of the item within its source, meta.x, meta.y}, {meta.z,
 //              meta.w, 0, 0}) and one packed u64 counter (spikes << 38 |
 //              work items); capacity = the work items of all sources
+//
+// Two delivery schemes share these arrays:
+//   ring          (push at spike time) every spike of step t is scattered
+//                 at once into ring slots t + d of all its groups; the ring
+//                 has L slots;
+//   spike buffer  (Sec. 2.2: a spike carries an age and the index of its next
+//                 connection group, and reaches a group when its age equals
+//                 the group's delay) the ring has one slot, the input of the
+//                 next step.  Spikes whose groups are not all delivered wait
+//                 in a pending list (double-buffered by step parity, one
+//                 uint4 per spike: {neuron | multiplicity << 26, next group,
+//                 end group, due step (low 32 bits)}).  Every step the update
+//                 kernel moves the spikes whose next group is due (age + 1 =
+//                 delay: delivered after step t into the input of step t+1)
+//                 to the step's due-item list (one uint4 per <= 1024
+//                 synapses of one group: {first synapse lo, hi | multiplicity
+//                 << 16, synapses, 0}), which the delivery kernel scatters
+//                 into the single slot.  The scattered-to array is N x R
+//                 words instead of L x N x R, so it stays in L2 for networks
+//                 whose ring would not.
+//   src_age    uint2 per source {synapses of its first group, delay of the
+//              first group | delay of the second group << 16}: what a new
+//              spike needs to decide whether its first group is due at once
 #pragma once
 
 #include <cuda_runtime.h>
@@ -42,6 +65,11 @@ constexpr uint32_t kRcptBit = 0x80000000u;
 constexpr uint32_t kErrRecordOverflow = 1u;
 constexpr uint32_t kErrSubstepCap = 2u;
 constexpr uint32_t kErrBarrierTimeout = 4u;
+constexpr uint32_t kErrPendingOverflow = 8u;
+
+// spike-buffer delivery
+constexpr uint32_t kAgeSpan = 1024;         // synapses per due item
+constexpr uint32_t kDeadWord = 0xFFFFFFFFu;  // pending entry removed (its instance was retired)
 
 // random-stream purposes: counter word 2 = purpose | attempt << 8
 enum : uint32_t { kPurSrc = 1, kPurWeight = 2, kPurDelay = 3, kPurPoisson = 4, kPurVinit = 5 };
@@ -82,6 +110,11 @@ struct SpikeBuf {
   unsigned long long* rec_count;    // spikes since the last drain (with multiplicity)
   int64_t rec_cap;
   uint32_t* err;
+  // spike-buffer delivery
+  uint4* pend[2];                   // pending spikes, by step parity
+  unsigned long long* pcnt;         // [2] pending-list lengths
+  int64_t pend_cap;                 // entries per pending list
+  int64_t wi_cap;                   // uint4 entries per work-item / due-item list
 };
 
 struct Csr {
@@ -92,6 +125,7 @@ struct Csr {
   const uint16_t* grp_delay;
   const uint32_t* tgt;
   const void* w;
+  const uint2* src_age;
 };
 
 struct Ring {
@@ -171,6 +205,167 @@ __device__ __forceinline__ void emit_spikes(bool spk, uint32_t gid, uint32_t mul
   }
 }
 
+// ------------------------------------------------------------ spike buffer
+// The spike-buffer scheme (Sec. 2.2).  Every lane of the warp must call these
+// (no early exit before them); lists are filled with one atomic per warp.
+
+// Warp-aggregated output of the spike-buffer bookkeeping: lane contributes
+// n_it due items covering the n synapses from b (multiplicity mult) to the
+// due-item list of parity ib, and, if keep, the pending entry ent to the
+// pending list of parity pb.  Positions beyond the lists' capacities are
+// dropped and raise kErrPendingOverflow.
+__device__ __forceinline__ void age_emit(uint32_t n_it, uint64_t b, uint32_t n, uint32_t mult, bool keep, uint4 ent,
+                                         int ib, int pb, const SpikeBuf& sb) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned kb = __ballot_sync(full, keep);
+  uint32_t inc = n_it;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t a = __shfl_up_sync(full, inc, o);
+    if (lane >= o) inc += a;
+  }
+  const uint32_t tot = __shfl_sync(full, inc, 31);
+  if (tot == 0 && kb == 0) return;
+  unsigned long long ibase = 0, pbase = 0;
+  if (lane == 0) {
+    if (tot) ibase = atomicAdd(sb.ctr + ib, (unsigned long long)tot);
+    if (kb) pbase = atomicAdd(sb.pcnt + pb, (unsigned long long)__popc(kb));
+  }
+  ibase = __shfl_sync(full, ibase, 0) & kChunkMask;
+  pbase = __shfl_sync(full, pbase, 0);
+  if (n_it) {
+    uint4* const di = ib ? sb.wi[1] : sb.wi[0];
+    const unsigned long long first = ibase + inc - n_it;
+    for (uint32_t k = 0; k < n_it; ++k) {
+      const uint64_t bk = b + (uint64_t)k * kAgeSpan;
+      const uint32_t nk = n - k * kAgeSpan < kAgeSpan ? n - k * kAgeSpan : kAgeSpan;
+      if (first + k < (unsigned long long)sb.wi_cap)
+        di[first + k] = make_uint4((uint32_t)bk, (uint32_t)((bk >> 32) & 0xFFFFu) | (mult << 16), nk, 0u);
+      else
+        atomicOr(sb.err, kErrPendingOverflow);
+    }
+  }
+  if (keep) {
+    const unsigned long long pos = pbase + __popc(kb & ((1u << lane) - 1u));
+    uint4* const pl = pb ? sb.pend[1] : sb.pend[0];
+    if (pos < (unsigned long long)sb.pend_cap) pl[pos] = ent;
+    else atomicOr(sb.err, kErrPendingOverflow);
+  }
+}
+
+// Spike record and event count of the new spikes of one warp (spike-buffer
+// scheme; the ring scheme does the same inside emit_spikes).
+__device__ __forceinline__ void record_spikes(bool spk, uint32_t gid, uint32_t mult, int64_t t,
+                                              unsigned long long nev, const SpikeBuf& sb) {
+  const unsigned full = 0xffffffffu;
+  if (__ballot_sync(full, spk) == 0) return;
+  const int lane = threadIdx.x & 31;
+  uint32_t m = spk ? mult : 0u, inc = m;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t a = __shfl_up_sync(full, inc, o);
+    if (lane >= o) inc += a;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nev += __shfl_xor_sync(full, nev, o);
+  const uint32_t tot = __shfl_sync(full, inc, 31);
+  unsigned long long rbase = 0;
+  if (lane == 0) {
+    rbase = atomicAdd(sb.rec_count, (unsigned long long)tot);
+    atomicAdd(sb.events, nev);
+  }
+  rbase = __shfl_sync(full, rbase, 0);
+  if (spk && sb.rec_cap > 0) {
+    const unsigned long long r0 = rbase + inc - m;
+    for (uint32_t k = 0; k < m; ++k) {
+      if (r0 + k < (unsigned long long)sb.rec_cap) {
+        sb.rec_id[r0 + k] = gid;
+        sb.rec_step[r0 + k] = t;
+      } else {
+        atomicOr(sb.err, kErrRecordOverflow);
+      }
+    }
+  }
+}
+
+// New spikes of step t in the spike-buffer scheme: a spike whose first group
+// has delay 1 is due at once (its synapses go to the due-item list of step
+// t); otherwise, and while groups remain, it joins the pending list of step
+// t + 1.  Synaptic events are counted at spike time, as in the ring scheme.
+__device__ __forceinline__ void emit_spikes_age(bool spk, uint32_t gid, uint32_t mult, int64_t t, const Csr& csr,
+                                                const SpikeBuf& sb) {
+  const unsigned ball = __ballot_sync(0xffffffffu, spk);
+  if (ball == 0) return;
+  uint4 meta = make_uint4(0, 0, 0, 0);
+  uint2 ag = make_uint2(0, 0);
+  if (spk) {
+    meta = __ldg(csr.src_meta + gid);
+    ag = __ldg(csr.src_age + gid);
+  }
+  const uint32_t ngrp = meta.y >> 16;
+  const uint64_t bsrc = (uint64_t)meta.x | ((uint64_t)(meta.y & 0xFFFFu) << 32);
+  const uint32_t d0 = ag.y & 0xFFFFu, d1 = ag.y >> 16;
+  const bool has = spk && ngrp > 0;
+  const bool now = has && d0 == 1u;
+  const uint32_t n_it = now ? (ag.x + kAgeSpan - 1) / kAgeSpan : 0u;
+  const bool keep = has && (!now || ngrp > 1u);
+  const uint32_t word = gid | (mult << kIdBits);
+  const uint4 ent = now ? make_uint4(word, meta.w + 1u, meta.w + ngrp, (uint32_t)(t + d1))
+                        : make_uint4(word, meta.w, meta.w + ngrp, (uint32_t)(t + d0));
+  record_spikes(spk, gid, mult, t, spk ? (unsigned long long)meta.z * mult : 0ull, sb);
+  age_emit(n_it, bsrc, ag.x, mult, keep, ent, (int)(t & 1), (int)((t + 1) & 1), sb);
+}
+
+// Pending spikes at the update of step t (spike-buffer scheme): a spike whose
+// next group is due (due step == t + 1) sends that group to the due-item list
+// of step t and advances to its next group; a spike with groups left stays
+// in the pending list of step t + 1.  The warps [warp0, warp0 + nwarps) of
+// the grid share the list, 32 entries per warp and pass.  kCoherent: the list
+// was written by other SMs in the same launch.
+template <bool kCoherent>
+__device__ __forceinline__ void scan_pending(int64_t t, const Csr& csr, const SpikeBuf& sb, int64_t warp0,
+                                             int64_t nwarps) {
+  const int lane = threadIdx.x & 31;
+  const int pb = (int)(t & 1);
+  unsigned long long n = kCoherent ? __ldcg(sb.pcnt + pb) : sb.pcnt[pb];
+  if (n > (unsigned long long)sb.pend_cap) n = (unsigned long long)sb.pend_cap;
+  const uint4* const pl = pb ? sb.pend[1] : sb.pend[0];
+  const uint32_t due_now = (uint32_t)(t + 1);
+  for (unsigned long long base = (unsigned long long)warp0 * 32; base < n;
+       base += (unsigned long long)nwarps * 32) {
+    const unsigned long long i = base + lane;
+    uint4 e = make_uint4(kDeadWord, 0, 0, 0);
+    if (i < n) e = kCoherent ? __ldcg(pl + i) : pl[i];
+    const bool live = e.x != kDeadWord;
+    const bool due = live && e.w == due_now;
+    uint32_t n_it = 0, sz = 0;
+    uint64_t b = 0;
+    bool keep = live;
+    uint4 ent = e;
+    if (due) {
+      const uint32_t ig = e.y;
+      const bool more = ig + 1u < e.z;
+      b = __ldg(csr.grp_start + ig);
+      const uint32_t dcur = __ldg(csr.grp_delay + ig);
+      uint64_t end;
+      uint32_t dnext = 0;
+      if (more) {
+        end = __ldg(csr.grp_start + ig + 1);
+        dnext = __ldg(csr.grp_delay + ig + 1);
+      } else {
+        const uint4 m = __ldg(csr.src_meta + (e.x & kIdMask));
+        end = ((uint64_t)m.x | ((uint64_t)(m.y & 0xFFFFu) << 32)) + m.z;
+      }
+      sz = (uint32_t)(end - b);
+      n_it = (sz + kAgeSpan - 1) / kAgeSpan;
+      keep = more;
+      ent = make_uint4(e.x, ig + 1u, e.z, e.w - dcur + dnext);
+    }
+    age_emit(n_it, b, sz, e.x >> kIdBits, keep, ent, pb, pb ^ 1, sb);
+  }
+}
+
 // Programmatic dependent launch (sm_90+): a kernel launched with the
 // programmatic-serialisation attribute may start while its predecessor in
 // the stream finishes; griddep_wait() blocks until the predecessor grid has
@@ -228,17 +423,21 @@ struct PersistArgs {
   uint32_t n_thr;
   int32_t n_lseg, n_aseg;
   int32_t withhold_block;  // test hook: this block never arrives at the first barrier (-1: none)
+  int32_t age;             // spike-buffer delivery scheme
   uint32_t off_aseg, off_lvoff, off_avoff, off_thr;  // dynamic shared memory layout
 };
 
 // ------------------------------------------------------------------ host side
 // Kernel launchers (one translation unit each).
-cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, const uint32_t* thr, float* y,
-                              float* I, int32_t* ref, Ring ring, bool fixed, int64_t* clk, const uint4* src_meta,
-                              SpikeBuf sb, bool pdl, cudaStream_t st);
+// age: spike-buffer scheme; scan: this kernel also scans the pending list
+// (the first update kernel of the step).
+// npt: LIF neurons per thread (1 or 4); a block covers kLifBlock * npt neurons.
+cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, int npt, const uint32_t* thr, float* y,
+                              float* I, int32_t* ref, Ring ring, bool fixed, int64_t* clk, const Csr& csr,
+                              SpikeBuf sb, bool age, bool scan, bool pdl, cudaStream_t st);
 cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V,
                                float* w, float* gex, float* gin, float* h, Ring ring, bool fixed, int64_t* clk,
-                               const uint4* src_meta, SpikeBuf sb, bool pdl, cudaStream_t st);
+                               const Csr& csr, SpikeBuf sb, bool age, bool scan, bool pdl, cudaStream_t st);
 cudaError_t launch_tick(int64_t* clk, bool pdl, cudaStream_t st);
 cudaError_t persistent_max_blocks_per_sm(bool fixed, int wdtype, bool lif, bool aeif, size_t smem, int* out);
 cudaError_t launch_persistent(const PersistArgs& a, bool fixed, int wdtype, bool lif, bool aeif, int grid,
@@ -248,6 +447,18 @@ cudaError_t launch_persistent(const PersistArgs& a, bool fixed, int wdtype, bool
 // (device) receives the delivery work items of all sources together.
 cudaError_t launch_build_meta(int64_t N, const uint64_t* src_syn, const uint32_t* src_grp, uint4* meta,
                               unsigned long long* total_items, cudaStream_t st);
+
+// Fused step loop (ring scheme, one launch per step and model): the update
+// kernel delivers its block's own spikes.  t = clk[0] + step_off; clk[0]
+// advances by a tick launch after each graph (or eager step).
+cudaError_t launch_step_lif(const SegTable<LifSeg>& segs, int64_t blocks, const uint32_t* thr, float* y, float* I,
+                            int32_t* ref, Ring ring, bool fixed, int wdtype, const int64_t* clk, int64_t step_off,
+                            const Csr& csr, SpikeBuf sb, bool pdl, cudaStream_t st);
+cudaError_t launch_step_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V, float* w,
+                             float* gex, float* gin, float* h, Ring ring, bool fixed, int wdtype, const int64_t* clk,
+                             int64_t step_off, const Csr& csr, SpikeBuf sb, bool pdl, cudaStream_t st);
+// clk[0] += n (clk[1] = clk[0] - 1); the ring scheme's step counters are cleared.
+cudaError_t launch_tick_add(int64_t* clk, int64_t n, unsigned long long* ctr, bool pdl, cudaStream_t st);
 
 // Launch `kernel` with the programmatic-serialisation attribute when pdl.
 template <typename... KArgs, typename... Args>
@@ -264,8 +475,12 @@ cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, bool pdl, 
   cfg.numAttrs = pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
-cudaError_t launch_deliver(SpikeBuf sb, Csr csr, int wdtype, Ring ring, bool fixed, int64_t* clk, int grid,
-                           bool pdl, cudaStream_t st);
+cudaError_t launch_deliver(SpikeBuf sb, Csr csr, int wdtype, Ring ring, bool fixed, bool age, int64_t* clk,
+                           int grid, bool pdl, cudaStream_t st);
+// Spike-buffer scheme, serving handles: mark the pending entries of sources
+// in [lo, hi) dead (their instance was retired).
+cudaError_t launch_kill_pending(uint4* list, const unsigned long long* count, int64_t cap, uint32_t lo, uint32_t hi,
+                                cudaStream_t st);
 // Initial state of one population: V0 = mean + sd * z (z standard normal from
 // the instance's stream, purpose kPurVinit, index = instance-local id).
 // LIF (model 0): a = y = V0 - E_L.  AdEx (model 1): a = V0, b = w0, h = h0.

@@ -15,6 +15,11 @@
 //                    them into ring slots t + d (as the per-step kernel)
 //     grid barrier   slot t + 1 is complete
 //
+// In the spike-buffer delivery scheme (a.age) the update phase first moves
+// the pending spikes whose next group is due to the step's due-item list, new
+// spikes join that list or the pending list, and the delivery phase scatters
+// the due items into the single ring slot.
+//
 // The step counter lives in registers.  The arithmetic is the same device
 // code as the per-step kernels (neuron_step.cuh, aeif_rk.cuh,
 // deliver_item.cuh), so both paths give identical results.  Data written by
@@ -141,6 +146,7 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(PersistArgs a) {
   for (int64_t step = 0; step < a.steps; ++step) {
     const uint64_t slot = (uint64_t)(t & ring.L_mask);
     // ------------------------------------------------------------ update phase
+    if (a.age) scan_pending<true>(t, a.csr, a.sb, warp, nwarps);
     if (kLif) {
       for (int64_t vb = warp * 32; vb < a.n_lif; vb += nwarps * 32) {
         const int64_t v = vb + lane;
@@ -154,7 +160,7 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(PersistArgs a) {
         if (valid) {
           float y = a.st0[gid], I = a.st1[gid];
           int32_t ref = a.ref[gid];
-          meta = __ldg(a.src_meta + gid);
+          if (!a.age) meta = __ldg(a.src_meta + gid);
           float in = ring_take<kFixed, true>(ring.p, slot * plane + gid);
           if (sg.n_thr > 0) {
             const uint32_t kp = poisson_count(sg.seed, t - sg.t0, sg.local_off + (uint32_t)k, s_thr + sg.thr_off,
@@ -166,7 +172,8 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(PersistArgs a) {
           a.st1[gid] = I;
           a.ref[gid] = ref;
         }
-        emit_spikes(spk, gid, 1u, t, meta, a.sb);
+        if (a.age) emit_spikes_age(spk, gid, 1u, t, a.csr, a.sb);
+        else emit_spikes(spk, gid, 1u, t, meta, a.sb);
       }
     }
     if (kAeif) {
@@ -182,7 +189,7 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(PersistArgs a) {
         if (valid) {
           St y{a.st0[gid], a.st1[gid], a.st2[gid], a.st3[gid]};
           double h = (double)a.st4[gid];
-          meta = __ldg(a.src_meta + gid);
+          if (!a.age) meta = __ldg(a.src_meta + gid);
           const uint64_t i0 = slot * plane + gid;
           float in0 = ring_take<kFixed, true>(ring.p, i0);
           float in1 = ring_take<kFixed, true>(ring.p, i0 + (uint64_t)ring.N);
@@ -203,7 +210,8 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(PersistArgs a) {
           a.st4[gid] = (float)h;
         }
         const uint32_t mult = nspk > 63u ? 63u : nspk;
-        emit_spikes(nspk > 0, gid, mult, t, meta, a.sb);
+        if (a.age) emit_spikes_age(nspk > 0, gid, mult, t, a.csr, a.sb);
+        else emit_spikes(nspk > 0, gid, mult, t, meta, a.sb);
       }
     }
     if (!grid_sync(a.bar, a.spin_limit, a.sb.err, first_barrier && (int)blockIdx.x == a.withhold_block)) break;
@@ -211,12 +219,21 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(PersistArgs a) {
     // ------------------------------------------------------------ delivery phase
     const int buf = (int)(t & 1);
     const unsigned long long c = __ldcg(a.sb.ctr + buf);
-    const uint32_t nch = (uint32_t)(c & kChunkMask);
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.sb.ctr[buf ^ 1] = 0;  // the next step's list starts empty
+    uint32_t nch = (uint32_t)(c & kChunkMask);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      a.sb.ctr[buf ^ 1] = 0;           // the next step's list starts empty
+      if (a.age) a.sb.pcnt[buf] = 0;   // consumed by this step's scan
+    }
     const uint4* wi = buf ? a.sb.wi[1] : a.sb.wi[0];
-    for (int64_t ch = warp; ch < (int64_t)nch; ch += nwarps) {
-      const uint4 e0 = __ldcg(wi + 2 * ch), e1 = __ldcg(wi + 2 * ch + 1);
-      deliver_work_item<WT, kFixed>(e0, e1, t, a.csr, ring, lane);
+    if (a.age) {
+      if ((unsigned long long)nch > (unsigned long long)a.sb.wi_cap) nch = (uint32_t)a.sb.wi_cap;
+      for (int64_t it = warp; it < (int64_t)nch; it += nwarps)
+        deliver_due_item<WT, kFixed>(__ldcg(wi + it), a.csr, ring, lane);
+    } else {
+      for (int64_t ch = warp; ch < (int64_t)nch; ch += nwarps) {
+        const uint4 e0 = __ldcg(wi + 2 * ch), e1 = __ldcg(wi + 2 * ch + 1);
+        deliver_work_item<WT, kFixed>(e0, e1, t, a.csr, ring, lane);
+      }
     }
     if (!grid_sync(a.bar, a.spin_limit, a.sb.err, false)) break;
     ++t;

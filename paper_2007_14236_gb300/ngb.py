@@ -23,13 +23,15 @@ WEIGHT_DTYPES = {"fp32": 0, "bf16": 1, "fp16": 2}
 MODELS = {W.LIF: 0, W.AEIF: 1}
 RULES = {W.INDEGREE: 0, W.TOTAL: 1}
 DISTS = {"const": 0, "normal": 1, "uniform": 2}
+DELIVERY = {"auto": 0, "ring": 1, "spike_buffer": 2}
 VARS = {"V_m": 0, "I_syn": 1, "w": 1, "g_ex": 2, "g_in": 3, "refractory": 4, "h": 5}
 
 
 class SimConfig(C.Structure):
     _fields_ = [("dt_ms", C.c_double), ("seed", C.c_uint64), ("weight_dtype", C.c_int32), ("device", C.c_int32),
                 ("stream", C.c_void_p), ("deterministic", C.c_int32), ("record_spikes", C.c_int32),
-                ("record_capacity", C.c_int64), ("steps_per_graph", C.c_int32), ("drain_steps", C.c_int32)]
+                ("record_capacity", C.c_int64), ("steps_per_graph", C.c_int32), ("drain_steps", C.c_int32),
+                ("delivery", C.c_int32), ("pad_", C.c_int32)]
 
 
 class PoissonDrive(C.Structure):
@@ -68,7 +70,7 @@ class SynSpec(C.Structure):
 class Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("steps", "spikes", "events", "rk_substeps", "num_neurons", "num_synapses",
                                          "num_groups", "ring_slots", "max_delay_steps", "device_bytes", "mode",
-                                         "launch_grid")]
+                                         "launch_grid", "delivery")]
 
 
 _lib = None
@@ -163,10 +165,11 @@ class Simulator:
 
     def __init__(self, dt_ms: float = 0.1, seed: int = 1, weight_dtype: str = "fp32", device: int = 0,
                  stream: Optional[int] = None, deterministic: bool = False, record_spikes: bool = True,
-                 record_capacity: int = 0, steps_per_graph: int = 0, drain_steps: int = 0):
+                 record_capacity: int = 0, steps_per_graph: int = 0, drain_steps: int = 0,
+                 delivery: str = "auto"):
         L = load()
         cfg = SimConfig(dt_ms, seed, WEIGHT_DTYPES[weight_dtype], device, stream, int(deterministic),
-                        int(record_spikes), record_capacity, steps_per_graph, drain_steps)
+                        int(record_spikes), record_capacity, steps_per_graph, drain_steps, DELIVERY[delivery], 0)
         h = C.c_void_p()
         _check(L.ngb_create(C.byref(h), C.byref(cfg)))
         self.h = h
@@ -246,7 +249,8 @@ class Simulator:
         return inst, pops
 
     def autotune(self, trial_steps: int = 0) -> int:
-        """Pick the delivery grid by timing graph replays; the state is restored."""
+        """Pick the step loop, delivery grid and (at step 0) delivery scheme by
+        timing them; the state is restored."""
         g = C.c_int32()
         self._c(load().ngb_autotune(self.h, trial_steps, C.byref(g)))
         return g.value

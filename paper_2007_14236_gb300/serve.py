@@ -71,11 +71,11 @@ def footprint(spec: W.NetSpec) -> Dict[str, int]:
 class Server:
     def __init__(self, max_neurons: int, max_synapses: int, max_groups: int, ring_slots: int = 32,
                  chunk_steps: int = 1000, deterministic: bool = False, keep_spikes: bool = False,
-                 weight_dtype: str = "fp32", device: int = 0):
+                 weight_dtype: str = "fp32", device: int = 0, delivery: str = "auto"):
         # spikes are recorded only when the caller keeps them; the counters count them either way
         self.sim = _ngb.Simulator(dt_ms=0.1, seed=0, weight_dtype=weight_dtype, device=device,
                                   deterministic=deterministic, record_spikes=keep_spikes, drain_steps=chunk_steps,
-                                  record_capacity=max(1 << 22, max_neurons * chunk_steps // 20))
+                                  record_capacity=max(1 << 22, max_neurons * chunk_steps // 20), delivery=delivery)
         self.sim.reserve(max_neurons, max_synapses, max_groups, ring_slots, 1)
         self.sim.finalize()
         self.cap = {"neurons": max_neurons, "synapses": max_synapses, "groups": max_groups}

@@ -8,6 +8,8 @@ launch configuration bench.py times (100-step CUDA graphs, FP32 weights).
   delay lands on that slot, within 1e-5 of the summed magnitudes (a property
   that holds at any size).
 * Whole-network counts: per-pathway synapse totals are exact.
+* The same delivery property for the spike-buffer scheme, whose only input
+  slot is the next step's.
 """
 import numpy as np
 import pytest
@@ -22,7 +24,7 @@ pytestmark = pytest.mark.gpu
 def mc():
     from paper_2007_14236_gb300 import ngb
     spec = W.microcircuit(scale=1.0, seed=1)
-    sim = ngb.from_spec(spec, steps_per_graph=100, drain_steps=10_000, record_capacity=4_000_000)
+    sim = ngb.from_spec(spec, steps_per_graph=100, drain_steps=10_000, record_capacity=4_000_000, delivery="ring")
     sim.finalize()
     yield spec, sim
     sim.close()
@@ -59,6 +61,46 @@ def test_fullsize_sampled_rows_match_oracle(mc):
     w = np.concatenate(got["weight"])
     du = np.abs(w.view(np.int32).astype(np.int64) - rows["weight"].view(np.int32).astype(np.int64))
     assert du.max(initial=0) <= 1 and np.count_nonzero(du) <= 2
+
+
+def _expected_inputs(sim, L):
+    """FP64 sums of the weights of the recorded spikes' synapses that land on
+    each of the next L steps (and their magnitudes)."""
+    st = sim.stats()
+    D = st["max_delay_steps"]
+    t_now = st["steps"]
+    ids, steps = sim.spikes(t0=t_now - D, t1=t_now)
+    assert len(ids) > 100
+    sp = sim.src_ptr().astype(np.int64)
+    N = st["num_neurons"]
+    expect = np.zeros((L, N))
+    absw = np.zeros((L, N))
+    for s in np.unique(ids):
+        fired = steps[ids == s]
+        g = sim.synapses(int(sp[s]), int(sp[s + 1] - sp[s]))
+        for ts in fired:
+            arrive = ts + g["delay"].astype(np.int64)
+            keep = (arrive >= t_now) & (arrive < t_now + L)
+            if not np.any(keep):
+                continue
+            off = arrive[keep] - t_now
+            np.add.at(expect, (off, g["tgt"][keep].astype(np.int64)), g["weight"][keep].astype(np.float64))
+            np.add.at(absw, (off, g["tgt"][keep].astype(np.int64)), np.abs(g["weight"][keep].astype(np.float64)))
+    return expect, absw
+
+
+def test_fullsize_spike_buffer_next_input_equals_delivered_weights():
+    from paper_2007_14236_gb300 import ngb
+    spec = W.microcircuit(scale=1.0, seed=1)
+    sim = ngb.from_spec(spec, steps_per_graph=100, drain_steps=10_000, record_capacity=4_000_000,
+                        delivery="spike_buffer")
+    sim.finalize()
+    assert sim.stats()["delivery"] == 2
+    sim.simulate(1200)
+    expect, absw = _expected_inputs(sim, 1)
+    got = sim.input(0, 0).astype(np.float64)
+    assert np.all(np.abs(got - expect[0]) <= 1e-5 * absw[0] + 1e-4)
+    sim.close()
 
 
 def test_fullsize_pending_inputs_equal_delivered_weights(mc):

@@ -103,7 +103,7 @@ def test_deterministic_balanced_lif_bit_exact(ngb):
 
 def test_deterministic_microcircuit_small_bit_exact(ngb):
     spec = W.microcircuit(scale=0.03, seed=7, keep_indegree=False)
-    g, o = _pair(ngb, spec, deterministic=True)
+    g, o = _pair(ngb, spec, deterministic=True, delivery="ring")  # reads future ring slots
     g.simulate(600)
     o.simulate(600)
     gi, gt = g.spikes()

@@ -1,6 +1,8 @@
-"""Persistent step kernel (many steps per cooperative launch, grid barriers
-between the update and delivery phases) against the per-step kernels, and
-the bounded barrier wait.
+"""Step loops against each other: the persistent step kernel (many steps per
+cooperative launch, grid barriers between the update and delivery phases),
+the fused loop (each update block delivers its own spikes, one launch per
+step) and the update kernel at four neurons per thread, against the per-step
+kernels; and the bounded barrier wait.
 
 * Deterministic mode: the persistent kernel gives bit-identical spike trains
   and state to the per-step path (LIF, AdEx, batched instances), and to the
@@ -98,7 +100,7 @@ def test_autotune_does_not_advance_the_simulation(ngb):
     b.simulate(200)
     grid = b.autotune(300)
     st = b.stats()
-    assert grid > 0 and st["steps"] == 200 and st["mode"] in (0, 1)
+    assert grid > 0 and st["steps"] == 200 and st["mode"] in (0, 1, 2)
     a.simulate(500)
     b.simulate(500)
     assert np.array_equal(a.spikes()[0], b.spikes()[0]) and np.array_equal(a.spikes()[1], b.spikes()[1])
@@ -117,3 +119,50 @@ def test_barrier_wait_is_bounded(ngb):
     ok = _persistent(ngb, spec, deterministic=True)
     ok.simulate(100)
     assert ok.stats()["steps"] == 100
+
+
+@pytest.mark.parametrize("name", ["balanced_lif", "microcircuit", "adex", "batched", "mc_bf16"])
+def test_fused_equals_per_step_kernels(ngb, name):
+    spec = {"balanced_lif": lambda: W.balanced_lif(n=1000, indegree=100, seed=1),
+            "microcircuit": lambda: W.microcircuit(scale=0.03, seed=7, keep_indegree=False),
+            "adex": lambda: W.balanced_adex(n=2000, indegree=100, seed=2, weight_dtype="fp32", poisson_weight=4.0,
+                                            w_ex=2.0, w_in=4.0),
+            "batched": lambda: W.batched_microcircuits(n_instances=3, scale_lo=0.02, scale_hi=0.04, seed=7),
+            "mc_bf16": lambda: W.microcircuit(scale=0.03, seed=8, keep_indegree=False, weight_dtype="bf16")}[name]()
+    a = ngb.from_spec(spec, deterministic=True, delivery="ring")
+    with _env(NGB_MODE="fused"):
+        b = ngb.from_spec(spec, deterministic=True, delivery="ring", drain_steps=250)
+        b.finalize()
+    assert b.stats()["mode"] == 2
+    a.simulate(700)
+    b.simulate(250)  # graphs of 100 steps and eager steps, in chunks of 250
+    b.simulate_profiled(50)
+    b.simulate(400)
+    ai, at = a.spikes()
+    bi, bt = b.spikes()
+    assert len(ai) > 50
+    assert np.array_equal(at, bt) and np.array_equal(ai, bi)
+    assert np.array_equal(a.state("V_m"), b.state("V_m"))
+    assert a.stats()["events"] == b.stats()["events"]
+    for off in range(0, 4):
+        assert np.array_equal(a.input(0, off), b.input(0, off))
+
+
+@pytest.mark.parametrize("delivery", ["ring", "spike_buffer"])
+def test_four_neurons_per_thread_equal_one(ngb, delivery):
+    spec = W.microcircuit(scale=0.05, seed=5, keep_indegree=False)  # population sizes not multiples of 1024
+    sims = []
+    for npt in (1, 4):
+        with _env(NGB_LIF_NPT=npt):
+            s = ngb.from_spec(spec, deterministic=True, delivery=delivery)
+            s.finalize()
+        s.simulate(600)
+        sims.append(s)
+    a, b = sims
+    ai, at = a.spikes()
+    bi, bt = b.spikes()
+    assert len(ai) > 50
+    assert np.array_equal(at, bt) and np.array_equal(ai, bi)
+    assert np.array_equal(a.state("V_m"), b.state("V_m"))
+    assert np.array_equal(a.state("I_syn"), b.state("I_syn"))
+    assert a.stats()["events"] == b.stats()["events"]
