@@ -60,7 +60,13 @@ extern "C" {
 /* ----------------------------------------------------------------- enums */
 typedef enum { NGB_WEIGHT_FP32 = 0, NGB_WEIGHT_BF16 = 1, NGB_WEIGHT_FP16 = 2 } ngb_weight_dtype;
 typedef enum { NGB_LIF_PSC_EXP = 0, NGB_AEIF_COND_EXP = 1 } ngb_model;
-typedef enum { NGB_RULE_FIXED_INDEGREE = 0, NGB_RULE_FIXED_TOTAL_NUMBER = 1 } ngb_rule;
+typedef enum {
+  NGB_RULE_FIXED_INDEGREE = 0,
+  NGB_RULE_FIXED_TOTAL_NUMBER = 1,
+  NGB_RULE_FIXED_OUTDEGREE = 2,
+  NGB_RULE_ONE_TO_ONE = 3,
+  NGB_RULE_ALL_TO_ALL = 4
+} ngb_rule;
 typedef enum { NGB_DIST_CONST = 0, NGB_DIST_NORMAL = 1, NGB_DIST_UNIFORM = 2 } ngb_dist;
 /* Spike delivery scheme (results are the same; memory traffic differs):
  *   RING          every spike is scattered at once into ring slots t + delay
@@ -138,8 +144,14 @@ typedef struct {
 
 /* Connection rule (Sec. 2.1).  FIXED_INDEGREE: every target draws K sources
  * uniformly with replacement.  FIXED_TOTAL_NUMBER: K (source, target) pairs
- * drawn uniformly with replacement.  Multapses are allowed; autapses only
- * when allow_autapses is set (and only matter when source == target pop). */
+ * drawn uniformly with replacement.  FIXED_OUTDEGREE: every source draws K
+ * targets uniformly with replacement.  ONE_TO_ONE: source i -> target i
+ * (equal sizes; K unused).  ALL_TO_ALL: every (source, target) pair once
+ * (K unused).  Multapses are allowed; autapses only when allow_autapses is set
+ * (and only matter when source == target pop; ONE_TO_ONE within one
+ * population then needs them).  Draw index q numbers the synapses of a call:
+ * target-major for FIXED_INDEGREE and ALL_TO_ALL, source-major for
+ * FIXED_OUTDEGREE, the source for ONE_TO_ONE. */
 typedef struct {
   int32_t rule;
   int32_t allow_autapses;

@@ -144,7 +144,8 @@ class OracleNet:
                 v = np.array(_aeif_vec(p.params, adex_fp64), dtype=np.float64)
                 _check(L.ora_add_population(self.h, p.instance, 1, p.n, v.ctypes.data_as(C.POINTER(C.c_double))))
         for c in spec.conns:
-            rule = 0 if c.rule == "fixed_indegree" else 1
+            rule = {"fixed_indegree": 0, "fixed_total_number": 1, "fixed_outdegree": 2, "one_to_one": 3,
+                    "all_to_all": 4}[c.rule]
             _check(L.ora_connect(self.h, c.src, c.tgt, rule, c.K, int(c.allow_autapses), _DIST[c.weight.kind],
                                  c.weight.p0, c.weight.p1, _DIST[c.delay.kind], c.delay.p0, c.delay.p1,
                                  c.receptor))

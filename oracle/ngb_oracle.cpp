@@ -11,8 +11,9 @@
 //     fifth-order Runge-Kutta method with adaptive step size (Sec. 2.1);
 //     the tableau is the published Cash-Karp (1990) one.
 //   * Poisson generators as the external drive (Sec. 2.1, devices).
-//   * Connections by the fixed-indegree and fixed-total-number rules
-//     (Sec. 2.1), grouped per source by delay (Sec. 2.2).
+//   * Connections by the rules of Sec. 2.1 (fixed indegree, fixed total
+//     number, fixed outdegree, one-to-one, all-to-all), grouped per source by
+//     delay (Sec. 2.2).
 //   * Spike delivery: a spike of neuron s at step t adds each synapse weight
 //     to its target's input at step t + delay, once (Sec. 2.2).
 //
@@ -318,19 +319,35 @@ Synapse draw_synapse(const ora_net* net, const Call& c, uint64_t q) {
   const uint64_t seed = net->inst[ps.instance].seed;
   const bool same = (c.src_pop == c.tgt_pop);
   uint32_t src = 0, tgt = 0;
-  for (uint32_t attempt = 0;; ++attempt) {
-    uint32_t r[4];
-    draw(seed, q, kSrc, attempt, c.stream, r);
-    if (attempt == kMaxAttempts) break;  // keep the last draw (needs a population of one)
-    if (c.rule == 0) {
-      tgt = (uint32_t)(q / (uint64_t)c.K);
-      src = uniform_index(r[0], (uint32_t)ps.n);
-    } else {
-      src = uniform_index(r[0], (uint32_t)ps.n);
-      tgt = uniform_index(r[1], (uint32_t)pt.n);
+  if (c.rule == 3) {
+    // one-to-one: source i -> target i, no draw
+    src = tgt = (uint32_t)q;
+  } else if (c.rule == 4) {
+    // all-to-all: pairs in target-major order, (i, i) left out without autapses
+    const uint64_t per_target = (same && !c.autapses) ? (uint64_t)ps.n - 1 : (uint64_t)ps.n;
+    tgt = (uint32_t)(q / per_target);
+    src = (uint32_t)(q % per_target);
+    if (same && !c.autapses && src >= tgt) src += 1;
+  } else {
+    for (uint32_t attempt = 0;; ++attempt) {
+      uint32_t r[4];
+      draw(seed, q, kSrc, attempt, c.stream, r);
+      if (attempt == kMaxAttempts) break;  // keep the last draw (needs a population of one)
+      if (c.rule == 0) {
+        // fixed indegree: draw q belongs to target q / K
+        tgt = (uint32_t)(q / (uint64_t)c.K);
+        src = uniform_index(r[0], (uint32_t)ps.n);
+      } else if (c.rule == 2) {
+        // fixed outdegree: draw q belongs to source q / K
+        src = (uint32_t)(q / (uint64_t)c.K);
+        tgt = uniform_index(r[0], (uint32_t)pt.n);
+      } else {
+        src = uniform_index(r[0], (uint32_t)ps.n);
+        tgt = uniform_index(r[1], (uint32_t)pt.n);
+      }
+      if (same && !c.autapses && src == tgt) continue;
+      break;
     }
-    if (same && !c.autapses && src == tgt) continue;
-    break;
   }
   Synapse s;
   s.src = (uint32_t)(ps.offset + src);
@@ -341,8 +358,17 @@ Synapse draw_synapse(const ora_net* net, const Call& c, uint64_t q) {
   return s;
 }
 
+// Synapses of connect call c: K per target, K in all, K per source, one per
+// source, or one per (source, target) pair (Sec. 2.1 connection rules).
 uint64_t call_size(const ora_net* net, const Call& c) {
-  return (c.rule == 0) ? (uint64_t)c.K * (uint64_t)net->pops[c.tgt_pop].n : (uint64_t)c.K;
+  const uint64_t ns = (uint64_t)net->pops[c.src_pop].n, nt = (uint64_t)net->pops[c.tgt_pop].n;
+  switch (c.rule) {
+    case 0: return (uint64_t)c.K * nt;
+    case 2: return (uint64_t)c.K * ns;
+    case 3: return ns;
+    case 4: return (c.src_pop == c.tgt_pop && !c.autapses) ? ns * (ns - 1) : ns * nt;
+    default: return (uint64_t)c.K;
+  }
 }
 
 void generate(const ora_net* net, const Call& c, std::vector<Synapse>& out) {
@@ -543,7 +569,9 @@ int32_t ora_connect(ora_net* net, int32_t src_pop, int32_t tgt_pop, int32_t rule
   const int32_t np = (int32_t)net->pops.size();
   if (src_pop < 0 || src_pop >= np || tgt_pop < 0 || tgt_pop >= np) return fail("ora_connect: pop");
   if (net->pops[src_pop].instance != net->pops[tgt_pop].instance) return fail("ora_connect: instances");
-  if (K < 0 || (rule != 0 && rule != 1)) return fail("ora_connect: rule/K");
+  if (K < 0 || rule < 0 || rule > 4) return fail("ora_connect: rule/K");
+  if (rule == 3 && (net->pops[src_pop].n != net->pops[tgt_pop].n || (src_pop == tgt_pop && !allow_autapses)))
+    return fail("ora_connect: one-to-one sizes");
   if (receptor < 0 || receptor > 1) return fail("ora_connect: receptor");
   if (receptor == 1 && net->pops[tgt_pop].model == 0) return fail("ora_connect: LIF has one receptor");
   if (src_pop == tgt_pop && !allow_autapses && net->pops[src_pop].n < 2 && K > 0)
@@ -562,8 +590,7 @@ int32_t ora_finalize(ora_net* net) {
   // 1. all synapses in (call, draw index) order
   std::vector<Synapse> syn;
   uint64_t total = 0;
-  for (const Call& c : net->calls)
-    total += (c.rule == 0) ? (uint64_t)c.K * (uint64_t)net->pops[c.tgt_pop].n : (uint64_t)c.K;
+  for (const Call& c : net->calls) total += call_size(net, c);
   syn.reserve((size_t)total);
   for (const Call& c : net->calls) generate(net, c, syn);
   // 2. stable counting sort by (source, delay): canonical CSR order
@@ -852,11 +879,16 @@ int64_t ora_rows_for_sources(const ora_net* net, int64_t n_src, const int64_t* s
     const uint64_t nsyn = call_size(net, c);
     const uint64_t seed = net->inst[ps.instance].seed;
     for (uint64_t q = 0; q < nsyn; ++q) {
-      // cheap pre-test on the first source draw; the full draw decides
-      uint32_t r[4];
-      draw(seed, q, kSrc, 0, c.stream, r);
-      const int64_t s0 = ps.offset + uniform_index(r[0], (uint32_t)ps.n);
-      const bool maybe = std::binary_search(lo, hi, s0) || (c.src_pop == c.tgt_pop && !c.autapses);
+      // cheap pre-test on the source (first draw of the random-source rules); the full draw decides
+      bool maybe = true;
+      if (c.rule == 0 || c.rule == 1) {
+        uint32_t r[4];
+        draw(seed, q, kSrc, 0, c.stream, r);
+        const int64_t s0 = ps.offset + uniform_index(r[0], (uint32_t)ps.n);
+        maybe = std::binary_search(lo, hi, s0) || (c.src_pop == c.tgt_pop && !c.autapses);
+      } else if (c.rule == 2) {
+        maybe = std::binary_search(lo, hi, ps.offset + (int64_t)(q / (uint64_t)c.K));
+      }
       if (!maybe) continue;
       const Synapse syn = draw_synapse(net, c, q);
       if (std::binary_search(lo, hi, (int64_t)syn.src)) rows.push_back(syn);

@@ -1,6 +1,7 @@
 // builder.cu -- connection builder on the device.
 //
-// Sec. 2.1 (connection rules fixed indegree and fixed total number, weights
+// Sec. 2.1 (connection rules fixed indegree, fixed total number, fixed
+// outdegree, one-to-one and all-to-all, weights
 // and delays from distributions) and Sec. 2.2 (per-source connection groups
 // ordered by delay).  The paper builds connections in host RAM and copies
 // them before the simulation (Sec. 3.1) and names building on the GPU as the
@@ -81,18 +82,34 @@ __global__ void k_draw(CallDev c, uint64_t base, unsigned long long* __restrict_
   int dmax = 0;
   for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < c.nsyn; q += stride) {
     uint32_t src = 0, tgt = 0;
-    for (uint32_t attempt = 0;; ++attempt) {
-      const U4 r = draw4(c.seed, q, kPurSrc, attempt, c.stream);
-      if (attempt == kMaxAttempts) break;  // keep the last draw (needs a population of one)
-      if (c.rule == 0) {
-        tgt = (uint32_t)(q / (uint64_t)c.K);
-        src = scale_index(r.x, c.n_src);
+    if (c.rule == 3) {  // one-to-one
+      src = tgt = (uint32_t)q;
+    } else if (c.rule == 4) {  // all-to-all, target-major; (i, i) skipped without autapses
+      if (c.no_autapse) {
+        tgt = (uint32_t)(q / (uint64_t)(c.n_src - 1));
+        const uint32_t r = (uint32_t)(q % (uint64_t)(c.n_src - 1));
+        src = r < tgt ? r : r + 1;
       } else {
-        src = scale_index(r.x, c.n_src);
-        tgt = scale_index(r.y, c.n_tgt);
+        tgt = (uint32_t)(q / (uint64_t)c.n_src);
+        src = (uint32_t)(q % (uint64_t)c.n_src);
       }
-      if (c.no_autapse && src == tgt) continue;
-      break;
+    } else {
+      for (uint32_t attempt = 0;; ++attempt) {
+        const U4 r = draw4(c.seed, q, kPurSrc, attempt, c.stream);
+        if (attempt == kMaxAttempts) break;  // keep the last draw (needs a population of one)
+        if (c.rule == 0) {  // fixed indegree
+          tgt = (uint32_t)(q / (uint64_t)c.K);
+          src = scale_index(r.x, c.n_src);
+        } else if (c.rule == 2) {  // fixed outdegree
+          src = (uint32_t)(q / (uint64_t)c.K);
+          tgt = scale_index(r.x, c.n_tgt);
+        } else {  // fixed total number
+          src = scale_index(r.x, c.n_src);
+          tgt = scale_index(r.y, c.n_tgt);
+        }
+        if (c.no_autapse && src == tgt) continue;
+        break;
+      }
     }
     const float w = round_storage(__double2float_rn(draw_weight(c, q)), c.prec);
     double ds = rint(__ddiv_rn(draw_delay(c, q), c.dt));

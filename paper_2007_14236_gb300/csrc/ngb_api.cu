@@ -141,6 +141,18 @@ std::vector<uint32_t> poisson_thresholds(double lambda) {
   return out;
 }
 
+// Synapses of one connect call (Sec. 2.1 connection rules).
+uint64_t call_synapses(const ngb_conn_spec& c, int64_t ns, int64_t nt, bool same) {
+  switch (c.rule) {
+    case NGB_RULE_FIXED_INDEGREE: return (uint64_t)c.K * (uint64_t)nt;
+    case NGB_RULE_FIXED_OUTDEGREE: return (uint64_t)c.K * (uint64_t)ns;
+    case NGB_RULE_ONE_TO_ONE: return (uint64_t)ns;
+    case NGB_RULE_ALL_TO_ALL:
+      return same && !c.allow_autapses ? (uint64_t)ns * (uint64_t)(ns - 1) : (uint64_t)ns * (uint64_t)nt;
+    default: return (uint64_t)c.K;
+  }
+}
+
 constexpr int kCounters = 8;  // device counter words: ctr[2], events, substeps, rec_count, spare, pcnt[2]
 
 uint64_t next_pow2(uint64_t x) {
@@ -467,7 +479,7 @@ int build_populations(ngb_sim* s, const std::vector<int>& srcs, std::vector<PopP
       CallDev d{};
       d.seed = s->inst[(size_t)ps.instance].seed;
       d.K = c.conn.K;
-      d.nsyn = c.conn.rule == NGB_RULE_FIXED_INDEGREE ? (uint64_t)c.conn.K * (uint64_t)pt.n : (uint64_t)c.conn.K;
+      d.nsyn = call_synapses(c.conn, s->pops[(size_t)c.src_pop].n, pt.n, c.src_pop == c.tgt_pop);
       d.w0 = c.syn.weight.p0;
       d.w1 = c.syn.weight.p1;
       d.d0 = c.syn.delay_ms.p0;
@@ -863,7 +875,7 @@ int finalize_impl(ngb_sim* s) {
     uint64_t K = 0;
     for (const CallHost& c : s->calls) {
       const PopHost& pt = s->pops[(size_t)c.tgt_pop];
-      K += c.conn.rule == NGB_RULE_FIXED_INDEGREE ? (uint64_t)c.conn.K * (uint64_t)pt.n : (uint64_t)c.conn.K;
+      K += call_synapses(c.conn, s->pops[(size_t)c.src_pop].n, pt.n, c.src_pop == c.tgt_pop);
     }
     s->K_cap = K;
   }
@@ -1320,8 +1332,10 @@ int ngb_connect(ngb_sim* s, int32_t src_pop, int32_t tgt_pop, const ngb_conn_spe
   if ((s->finalized && !s->serving) || s->inst[(size_t)ps.instance].state != 0)
     return fail(NGB_ERR_STATE, "ngb_connect: network (instance) already built");
   if (ps.instance != pt.instance) return fail(NGB_ERR_INVALID_ARG, "ngb_connect: populations of different instances");
-  if (conn->rule != NGB_RULE_FIXED_INDEGREE && conn->rule != NGB_RULE_FIXED_TOTAL_NUMBER)
+  if (conn->rule < NGB_RULE_FIXED_INDEGREE || conn->rule > NGB_RULE_ALL_TO_ALL)
     return fail(NGB_ERR_INVALID_ARG, "ngb_connect: rule");
+  if (conn->rule == NGB_RULE_ONE_TO_ONE && (ps.n != pt.n || (src_pop == tgt_pop && !conn->allow_autapses)))
+    return fail(NGB_ERR_INVALID_ARG, "ngb_connect: one-to-one needs equal sizes (and autapses within a population)");
   if (conn->K < 0) return fail(NGB_ERR_INVALID_ARG, "ngb_connect: K < 0");
   if (!valid_dist(syn->weight) || !valid_dist(syn->delay_ms))
     return fail(NGB_ERR_INVALID_ARG, "ngb_connect: distribution");

@@ -28,6 +28,9 @@ LIF = "lif_psc_exp"
 AEIF = "aeif_cond_exp"
 INDEGREE = "fixed_indegree"
 TOTAL = "fixed_total_number"
+OUTDEGREE = "fixed_outdegree"
+ONE_TO_ONE = "one_to_one"
+ALL_TO_ALL = "all_to_all"
 
 
 @dataclass
@@ -124,7 +127,9 @@ class NetSpec:
     def num_synapses(self) -> int:
         total = 0
         for c in self.conns:
-            total += c.K * self.pops[c.tgt].n if c.rule == INDEGREE else c.K
+            ns, nt = self.pops[c.src].n, self.pops[c.tgt].n
+            total += {INDEGREE: c.K * nt, TOTAL: c.K, OUTDEGREE: c.K * ns, ONE_TO_ONE: ns,
+                      ALL_TO_ALL: ns * (ns - 1) if (c.src == c.tgt and not c.allow_autapses) else ns * nt}[c.rule]
         return total
 
     def instance_pops(self, instance: int) -> List[int]:
@@ -149,6 +154,25 @@ def balanced_lif(n: int = 1000, indegree: int = 100, seed: int = 1, rate_hz: flo
     for tgt in (0, 1):
         spec.conns.append(Connection(0, tgt, INDEGREE, k_e, Dist("const", j_ex), Dist("const", d_ex)))
         spec.conns.append(Connection(1, tgt, INDEGREE, k_i, Dist("const", -g * j_ex), Dist("const", d_in)))
+    return spec
+
+
+def rules_net(seed: int = 1, weight_dtype: str = "fp32") -> NetSpec:
+    """A small LIF network wired with the rules beyond fixed in-degree / total
+    number (Sec. 2.1): one-to-one A -> B, fixed out-degree B -> C, all-to-all
+    C -> A, all-to-all without autapses A -> A and one-to-one B -> B
+    (autapses).  A is driven by Poisson input."""
+    drive = LifParams(V_init_mean=-65.0, V_init_sd=4.0, poisson=Poisson(n_inputs=1000.0, rate_hz=9.0, weight=87.8))
+    quiet = LifParams(V_init_mean=-65.0, V_init_sd=4.0, poisson=Poisson(n_inputs=1000.0, rate_hz=7.0, weight=87.8))
+    spec = NetSpec(name="rules_net", seeds=[seed], weight_dtype=weight_dtype)
+    spec.pops = [Population("A", LIF, 300, drive), Population("B", LIF, 300, quiet), Population("C", LIF, 200, quiet)]
+    spec.conns = [
+        Connection(0, 1, ONE_TO_ONE, 0, Dist("const", 2500.0), Dist("const", 1.0)),
+        Connection(1, 2, OUTDEGREE, 40, Dist("normal", 60.0, 6.0), Dist("normal", 1.5, 0.5)),
+        Connection(2, 0, ALL_TO_ALL, 0, Dist("const", -8.0), Dist("uniform", 0.5, 2.0)),
+        Connection(0, 0, ALL_TO_ALL, 0, Dist("normal", 1.0, 0.1), Dist("const", 0.8), allow_autapses=False),
+        Connection(1, 1, ONE_TO_ONE, 0, Dist("const", 20.0), Dist("const", 2.0)),
+    ]
     return spec
 
 

@@ -63,6 +63,7 @@ SPECS = {
     "balanced_adex_2000": lambda: W.balanced_adex(n=2000, indegree=100, seed=2, weight_dtype="fp32"),
     "microcircuit_bf16": lambda: W.microcircuit(scale=0.02, seed=4, keep_indegree=False, weight_dtype="bf16"),
     "microcircuit_fp16": lambda: W.microcircuit(scale=0.02, seed=5, keep_indegree=False, weight_dtype="fp16"),
+    "rules_net": lambda: W.rules_net(seed=4),
 }
 
 
@@ -113,6 +114,20 @@ def test_deterministic_microcircuit_small_bit_exact(ngb):
     assert np.array_equal(g.state("V_m"), o.state("V_m").astype(np.float32))
     for off in range(0, 8):
         assert np.array_equal(g.input(0, off), o.input(0, off)[0])
+
+
+def test_deterministic_rules_net_bit_exact(ngb):
+    """One-to-one, fixed out-degree and all-to-all wiring, simulated."""
+    spec = W.rules_net(seed=4)
+    g, o = _pair(ngb, spec, deterministic=True)
+    g.simulate(500)
+    o.simulate(500)
+    gi, gt = g.spikes()
+    oi, ot = o.spikes()
+    assert len(oi) > 100
+    assert np.array_equal(gt, ot) and np.array_equal(gi, oi)
+    assert np.array_equal(g.state("V_m"), o.state("V_m").astype(np.float32))
+    assert g.stats()["events"] == o.events
 
 
 def test_deterministic_bf16_weights_bit_exact(ngb):

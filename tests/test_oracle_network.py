@@ -107,6 +107,57 @@ def test_fixed_total_number_pathway_counts_and_distributions():
     assert d.min() >= 1
 
 
+def test_rules_one_to_one_outdegree_all_to_all():
+    """Sec. 2.1 rules, each checked against its definition."""
+    spec = W.rules_net(seed=4)
+    net = _net(spec)
+    csr = net.csr()
+    src = _src_of(csr)
+    tgt = csr["tgt"].astype(np.int64)
+    offs = np.cumsum([0] + [p.n for p in spec.pops])
+    pop_of = np.searchsorted(offs, np.arange(offs[-1]), side="right") - 1
+    ps, pt = pop_of[src], pop_of[tgt]
+    assert net.num_synapses == spec.num_synapses() == 300 + 300 * 40 + 200 * 300 + 300 * 299 + 300
+    # one-to-one A -> B and B -> B: neuron i to neuron i, exactly once
+    for a, b in ((0, 1), (1, 1)):
+        m = (ps == a) & (pt == b)
+        assert np.count_nonzero(m) == 300
+        assert np.array_equal(np.sort(src[m] - offs[a]), np.arange(300))
+        assert np.all(src[m] - offs[a] == tgt[m] - offs[b])
+    # fixed out-degree B -> C: exactly 40 per source, targets uniform
+    m = (ps == 1) & (pt == 2)
+    assert np.all(np.bincount(src[m] - offs[1], minlength=300) == 40)
+    cnt = np.bincount(tgt[m] - offs[2], minlength=200)
+    chi2 = ((cnt - cnt.mean()) ** 2 / cnt.mean()).sum()
+    assert stats.chi2.sf(chi2, 199) > 1e-4
+    # all-to-all C -> A: every pair once; A -> A without autapses: every pair but (i, i)
+    m = (ps == 2) & (pt == 0)
+    pairs = (src[m] - offs[2]) * 300 + (tgt[m] - offs[0])
+    assert np.array_equal(np.sort(pairs), np.arange(200 * 300))
+    m = (ps == 0) & (pt == 0)
+    a_s, a_t = src[m], tgt[m]
+    assert len(a_s) == 300 * 299 and not np.any(a_s == a_t)
+    assert len(np.unique(a_s * 300 + a_t)) == 300 * 299
+    # delays: constant / uniform (0.5, 2] ms / clipped normal, as specified
+    assert set(np.unique(csr["delay"][(ps == 0) & (pt == 1)])) == {10}
+    d_ca = csr["delay"][(ps == 2) & (pt == 0)].astype(np.int64)
+    assert d_ca.min() == 5 and d_ca.max() == 20
+    assert np.all(csr["delay"] >= 1)
+
+
+def test_rules_rows_for_sources():
+    spec = W.rules_net(seed=4)
+    net = _net(spec)
+    csr = net.csr()
+    sp = csr["src_ptr"].astype(np.int64)
+    lazy = oracle.OracleNet(spec)
+    srcs = np.array([3, 299, 301, 450, 600, 799])
+    rows = lazy.rows_for_sources(srcs)
+    want = np.concatenate([np.arange(sp[s], sp[s + 1]) for s in srcs])
+    for k in ("tgt", "receptor", "weight", "delay"):
+        assert np.array_equal(rows[k], csr[k][want]), k
+
+
 def test_uniform_delay_histogram():
     spec = W.balanced_adex(n=500, indegree=100, seed=2, weight_dtype="fp32")
     net = _net(spec)
