@@ -15,7 +15,7 @@ from . import build as _build
 
 _lib = None
 
-_VAR = {"V_m": 0, "I_syn": 1, "w": 1, "g_ex": 2, "g_in": 3, "refractory": 4, "h": 5}
+_VAR = {"V_m": 0, "I_syn": 1, "w": 1, "g_ex": 2, "g_in": 3, "refractory": 4, "h": 5, "dg_ex": 6, "dg_in": 7}
 
 
 def lib():
@@ -142,7 +142,9 @@ class OracleNet:
                 _check(L.ora_add_population(self.h, p.instance, 0, p.n, v.ctypes.data_as(C.POINTER(C.c_double))))
             else:
                 v = np.array(_aeif_vec(p.params, adex_fp64), dtype=np.float64)
-                _check(L.ora_add_population(self.h, p.instance, 1, p.n, v.ctypes.data_as(C.POINTER(C.c_double))))
+                model = 2 if p.model == "aeif_cond_alpha" else 1
+                _check(L.ora_add_population(self.h, p.instance, model, p.n,
+                                            v.ctypes.data_as(C.POINTER(C.c_double))))
         for c in spec.conns:
             rule = {"fixed_indegree": 0, "fixed_total_number": 1, "fixed_outdegree": 2, "one_to_one": 3,
                     "all_to_all": 4}[c.rule]

@@ -253,6 +253,7 @@ struct ora_net {
   int R = 1;
   // per-neuron state (double arrays; FP32 models keep float-representable values)
   std::vector<double> s0, s1, s2, s3, s4;  // LIF: y, I, ref | AdEx: V, w, gex, gin, h
+  std::vector<double> s5, s6;              // AdEx with alpha conductances: dg_ex, dg_in
   std::vector<int> pop_of;
   // ring[(slot * R + r) * N + i]
   std::vector<float> ring;
@@ -376,40 +377,58 @@ void generate(const ora_net* net, const Call& c, std::vector<Synapse>& out) {
   for (uint64_t q = 0; q < nsyn; ++q) out.push_back(draw_synapse(net, c, q));
 }
 
-// One embedded Cash-Karp step of the AdEx system (Eqs. 3-5 with the
-// conductances of Eq. 4 as state) from y over h; returns the fifth-order
-// solution in y5 and the difference to the fourth-order one in err.
+// The AdEx system (Eqs. 3-5) with the synaptic conductances as state:
+// y = {V, w, g_ex, g_in, dg_ex, dg_in}.  Exponential conductances (alpha =
+// false): dg/dt = -g / tau, the last two components stay 0.  Alpha-function
+// conductances (the paper's balanced network, Sec. 2.3): g(t) = W (t/tau)
+// e^(1 - t/tau) after a spike of weight W, generated by dg/dt = x - g/tau,
+// dx/dt = -x/tau with x jumping by W e / tau at the spike.
+constexpr int kAdexN = 6;
+constexpr double kEuler = 2.718281828459045;  // e
+
 template <typename T>
 struct AdexSystem {
   T g_L, E_L, V_T, Delta_T, inv_Delta_T, a, inv_tau_w, V_peak, E_ex, E_in, inv_tau_ex, inv_tau_in, I_e,
       inv_C;
-  void deriv(const T y[4], T f[4]) const {
+  bool alpha;
+  void deriv(const T y[kAdexN], T f[kAdexN]) const {
     const T V = std::min(y[0], V_peak);  // the exponential is evaluated at most at V_peak
     const T I_spike = (Delta_T > T(0)) ? g_L * Delta_T * std::exp((V - V_T) * inv_Delta_T) : T(0);
     // reading of Eq. 4: I_syn = sum_i g_i (E_rev,i - V), so excitation depolarises
     const T I_syn = y[2] * (E_ex - V) + y[3] * (E_in - V);
     f[0] = (-g_L * (V - E_L) + I_spike + I_syn - y[1] + I_e) * inv_C;
     f[1] = (a * (V - E_L) - y[1]) * inv_tau_w;
-    f[2] = -y[2] * inv_tau_ex;
-    f[3] = -y[3] * inv_tau_in;
+    if (alpha) {
+      f[2] = y[4] - y[2] * inv_tau_ex;
+      f[3] = y[5] - y[3] * inv_tau_in;
+      f[4] = -y[4] * inv_tau_ex;
+      f[5] = -y[5] * inv_tau_in;
+    } else {
+      f[2] = -y[2] * inv_tau_ex;
+      f[3] = -y[3] * inv_tau_in;
+      f[4] = T(0);
+      f[5] = T(0);
+    }
   }
 };
 
+// One embedded Cash-Karp step from y over h: the fifth-order solution in y5
+// and its difference to the fourth-order one in err.
 template <typename T>
-void ck_step(const AdexSystem<T>& sys, const Tableau& tab, const T y[4], const T f0[4], double h, T y5[4],
-             T err[4]) {
-  T k[6][4];
-  for (int i = 0; i < 4; ++i) k[0][i] = f0[i];
+void ck_step(const AdexSystem<T>& sys, const Tableau& tab, const T y[kAdexN], const T f0[kAdexN], double h,
+             T y5[kAdexN], T err[kAdexN]) {
+  T k[6][kAdexN];
+  for (int i = 0; i < kAdexN; ++i) k[0][i] = f0[i];
   for (int s = 1; s < 6; ++s) {
-    T ys[4];
-    for (int i = 0; i < 4; ++i) {
+    T ys[kAdexN];
+    for (int i = 0; i < kAdexN; ++i) {
       T acc = T(0);
       for (int j = 0; j < s; ++j) acc += T(tab.a[s][j]) * k[j][i];
       ys[i] = y[i] + T(h) * acc;
     }
     sys.deriv(ys, k[s]);
   }
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < kAdexN; ++i) {
     T acc5 = T(0), accd = T(0);
     for (int s = 0; s < 6; ++s) {
       acc5 += T(tab.b5[s]) * k[s][i];
@@ -427,8 +446,8 @@ void ck_step(const AdexSystem<T>& sys, const Tableau& tab, const T y[4], const T
 // V >= V_peak.  Returns the number of spikes; h carries the proposed step.
 template <typename T>
 int adex_advance(const AdexSystem<T>& sys, const Tableau& tab, const AeifPar& p, double dt, double tol,
-                 T y[4], double& h, int64_t& substeps, int64_t& cap_hits) {
-  const T floor_[4] = {T(1.0), T(1.0), T(1e-3), T(1e-3)};
+                 T y[kAdexN], double& h, int64_t& substeps, int64_t& cap_hits) {
+  const T floor_[kAdexN] = {T(1.0), T(1.0), T(1e-3), T(1e-3), T(1e-3), T(1e-3)};
   int spikes = 0;
   double t_in = 0.0;
   int64_t n = 0;
@@ -440,11 +459,11 @@ int adex_advance(const AdexSystem<T>& sys, const Tableau& tab, const AeifPar& p,
       h = rem;
       last = true;
     }
-    T f0[4], y5[4], err[4];
+    T f0[kAdexN], y5[kAdexN], err[kAdexN];
     sys.deriv(y, f0);
     ck_step(sys, tab, y, f0, h, y5, err);
     T emax = T(0);
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < kAdexN; ++i) {
       const T scale = std::fabs(y[i]) + std::fabs(T(h) * f0[i]) + floor_[i];
       const T r = std::fabs(err[i]) / scale;
       if (r > emax) emax = r;
@@ -452,7 +471,7 @@ int adex_advance(const AdexSystem<T>& sys, const Tableau& tab, const AeifPar& p,
     const double ratio = (double)emax / tol;
     ++n;
     if (ratio <= 1.0 || h <= p.h_min || n >= p.max_sub) {
-      for (int i = 0; i < 4; ++i) y[i] = y5[i];
+      for (int i = 0; i < kAdexN; ++i) y[i] = y5[i];
       if (y[0] >= T(p.V_peak)) {
         y[0] = T(p.V_reset);
         y[1] = y[1] + T(p.b);
@@ -515,7 +534,7 @@ int32_t ora_add_instance(ora_net* net, uint64_t seed) {
 int32_t ora_add_population(ora_net* net, int32_t instance, int32_t model, int64_t n, const double* p) {
   if (!net || net->finalized) return fail("ora_add_population: bad state");
   if (instance < 0 || instance >= (int32_t)net->inst.size()) return fail("ora_add_population: instance");
-  if (n <= 0 || n > 0x7FFFFFFF || (model != 0 && model != 1)) return fail("ora_add_population: n/model");
+  if (n <= 0 || n > 0x7FFFFFFF || model < 0 || model > 2) return fail("ora_add_population: n/model");
   Population P;
   std::memset(&P, 0, sizeof(P));
   P.model = model;
@@ -621,6 +640,7 @@ int32_t ora_finalize(ora_net* net) {
   // 3. state
   net->s0.assign((size_t)N, 0.0); net->s1.assign((size_t)N, 0.0); net->s2.assign((size_t)N, 0.0);
   net->s3.assign((size_t)N, 0.0); net->s4.assign((size_t)N, 0.0);
+  net->s5.assign((size_t)N, 0.0); net->s6.assign((size_t)N, 0.0);
   net->pop_of.assign((size_t)N, 0);
   for (size_t pi = 0; pi < net->pops.size(); ++pi) {
     const Population& P = net->pops[pi];
@@ -722,30 +742,45 @@ int32_t ora_simulate(ora_net* net, int64_t steps) {
           net->s2[(size_t)i] = ref;
         } else {
           const AeifPar& q = P.aeif;
+          const bool alpha = P.model == 2;
           double h = net->s4[(size_t)i];
           if (q.fp64) {
             AdexSystem<double> sys{q.g_L, q.E_L, q.V_T, q.Delta_T, 1.0 / q.Delta_T, q.a, 1.0 / q.tau_w,
                                    q.V_peak, q.E_ex, q.E_in, 1.0 / q.tau_ex, 1.0 / q.tau_in, q.I_e,
-                                   1.0 / q.C_m};
-            double y[4] = {net->s0[(size_t)i], net->s1[(size_t)i], net->s2[(size_t)i], net->s3[(size_t)i]};
+                                   1.0 / q.C_m, alpha};
+            double y[kAdexN] = {net->s0[(size_t)i], net->s1[(size_t)i], net->s2[(size_t)i], net->s3[(size_t)i],
+                                net->s5[(size_t)i], net->s6[(size_t)i]};
             nspk = adex_advance<double>(sys, tab, q, net->dt, q.tol, y, h, net->rk_substeps, net->rk_cap_hits);
-            y[2] += (double)in[0];
-            y[3] += (double)in[1];
+            // input of step t: a conductance jump (exponential), or a jump of dg/dt by W e / tau (alpha)
+            if (alpha) {
+              y[4] += (double)in[0] * (kEuler / q.tau_ex);
+              y[5] += (double)in[1] * (kEuler / q.tau_in);
+            } else {
+              y[2] += (double)in[0];
+              y[3] += (double)in[1];
+            }
             net->s0[(size_t)i] = y[0]; net->s1[(size_t)i] = y[1];
             net->s2[(size_t)i] = y[2]; net->s3[(size_t)i] = y[3];
+            net->s5[(size_t)i] = y[4]; net->s6[(size_t)i] = y[5];
           } else {
             AdexSystem<float> sys{(float)q.g_L, (float)q.E_L, (float)q.V_T, (float)q.Delta_T,
                                   (float)(1.0 / q.Delta_T), (float)q.a, (float)(1.0 / q.tau_w),
                                   (float)q.V_peak, (float)q.E_ex, (float)q.E_in, (float)(1.0 / q.tau_ex),
-                                  (float)(1.0 / q.tau_in), (float)q.I_e, (float)(1.0 / q.C_m)};
-            float y[4] = {(float)net->s0[(size_t)i], (float)net->s1[(size_t)i], (float)net->s2[(size_t)i],
-                          (float)net->s3[(size_t)i]};
+                                  (float)(1.0 / q.tau_in), (float)q.I_e, (float)(1.0 / q.C_m), alpha};
+            float y[kAdexN] = {(float)net->s0[(size_t)i], (float)net->s1[(size_t)i], (float)net->s2[(size_t)i],
+                               (float)net->s3[(size_t)i], (float)net->s5[(size_t)i], (float)net->s6[(size_t)i]};
             const double tol_eff = std::max(q.tol, 8.0 * 0x1p-24);
             nspk = adex_advance<float>(sys, tab, q, net->dt, tol_eff, y, h, net->rk_substeps, net->rk_cap_hits);
-            y[2] = y[2] + in[0];
-            y[3] = y[3] + in[1];
+            if (alpha) {
+              y[4] = y[4] + in[0] * (float)(kEuler / q.tau_ex);
+              y[5] = y[5] + in[1] * (float)(kEuler / q.tau_in);
+            } else {
+              y[2] = y[2] + in[0];
+              y[3] = y[3] + in[1];
+            }
             net->s0[(size_t)i] = y[0]; net->s1[(size_t)i] = y[1];
             net->s2[(size_t)i] = y[2]; net->s3[(size_t)i] = y[3];
+            net->s5[(size_t)i] = y[4]; net->s6[(size_t)i] = y[5];
             h = (double)(float)h;  // the step-size proposal is carried in FP32 between steps
           }
           net->s4[(size_t)i] = h;
@@ -837,6 +872,8 @@ int32_t ora_get_state(const ora_net* net, int32_t var, double* out) {
       else if (var == 2) v = net->s2[(size_t)i];
       else if (var == 3) v = net->s3[(size_t)i];
       else if (var == 5) v = net->s4[(size_t)i];
+      else if (var == 6) v = net->s5[(size_t)i];
+      else if (var == 7) v = net->s6[(size_t)i];
     }
     out[i] = v;
   }

@@ -51,7 +51,7 @@ ora_net* ora_create(double dt_ms, uint64_t seed, int32_t weight_prec /*0 fp32,1 
                     int32_t deterministic, int32_t track_abs);
 void ora_destroy(ora_net* net);
 int32_t ora_add_instance(ora_net* net, uint64_t seed);
-int32_t ora_add_population(ora_net* net, int32_t instance, int32_t model /*0 LIF, 1 AdEx*/,
+int32_t ora_add_population(ora_net* net, int32_t instance, int32_t model /*0 LIF, 1 AdEx exp, 2 AdEx alpha*/,
                            int64_t n, const double* params);
 int32_t ora_connect(ora_net* net, int32_t src_pop, int32_t tgt_pop, int32_t rule /*0 indeg, 1 total, 2 outdeg, 3 one-to-one, 4 all-to-all*/,
                     int64_t K, int32_t allow_autapses, int32_t wdist, double w0, double w1,

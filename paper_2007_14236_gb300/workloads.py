@@ -26,6 +26,7 @@ import numpy as np
 
 LIF = "lif_psc_exp"
 AEIF = "aeif_cond_exp"
+AEIF_ALPHA = "aeif_cond_alpha"  # AdEx with alpha-function conductances
 INDEGREE = "fixed_indegree"
 TOTAL = "fixed_total_number"
 OUTDEGREE = "fixed_outdegree"

@@ -13,6 +13,11 @@
   two receptors of the exponential-conductance model): |dV| <= 1e-4 mV.
 * The FP32-state specification stays within the FP32 error budget of the
   FP64 reference on the same trace.
+* Alpha-function conductances (the paper's balanced network, Sec. 2.3): the
+  conductance after one input of weight W follows W (t/tau) e^(1 - t/tau)
+  (peak W at t = tau) at every grid point; the subthreshold response to inputs
+  on both receptors and a spiking run match DOP853 on the same six-variable
+  system.
 """
 import math
 
@@ -64,23 +69,26 @@ def _table2(**kw):
     return W.AeifParams(**base)
 
 
-def _oracle_trace(par, steps, fp64=True, injections=()):
-    spec = W.NetSpec(name="adex1", seeds=[1], pops=[W.Population("n", W.AEIF, 1, par)])
+def _oracle_trace(par, steps, fp64=True, injections=(), model=W.AEIF, record=("V_m",)):
+    spec = W.NetSpec(name="adex1", seeds=[1], pops=[W.Population("n", model, 1, par)])
     net = oracle.OracleNet(spec, adex_fp64=fp64)
     net.finalize()
     inj = {}
     for step, rcpt, val in injections:
         inj.setdefault(step, []).append((rcpt, val))
-    V = np.zeros(steps)
+    out = {v: np.zeros(steps) for v in record}
     for k in range(steps):
         for rcpt, val in inj.get(k, []):
             net.inject(0, rcpt, 0, val)
         net.simulate(1)
-        V[k] = net.state("V_m")[0]
-    return V, net.spikes()[1]
+        for v in record:
+            out[v][k] = net.state(v)[0]
+    if record == ("V_m",):
+        return out["V_m"], net.spikes()[1]
+    return out, net.spikes()[1]
 
 
-def _scipy_trace(par, steps, injections=()):
+def _scipy_trace(par, steps, injections=(), alpha=False):
     integ = pytest.importorskip("scipy.integrate")
     p = par
 
@@ -88,8 +96,11 @@ def _scipy_trace(par, steps, injections=()):
         V = min(y[0], p.V_peak)
         I_spk = p.g_L * p.Delta_T * math.exp((V - p.V_T) / p.Delta_T)
         I_syn = y[2] * (p.E_ex - V) + y[3] * (p.E_in - V)
-        return [(-p.g_L * (V - p.E_L) + I_spk + I_syn - y[1] + p.I_e) / p.C_m,
-                (p.a * (V - p.E_L) - y[1]) / p.tau_w, -y[2] / p.tau_ex, -y[3] / p.tau_in]
+        f = [(-p.g_L * (V - p.E_L) + I_spk + I_syn - y[1] + p.I_e) / p.C_m,
+             (p.a * (V - p.E_L) - y[1]) / p.tau_w]
+        if alpha:  # g' = x - g / tau, x' = -x / tau
+            return f + [y[4] - y[2] / p.tau_ex, y[5] - y[3] / p.tau_in, -y[4] / p.tau_ex, -y[5] / p.tau_in]
+        return f + [-y[2] / p.tau_ex, -y[3] / p.tau_in]
 
     # Near V_peak the solution blows up (|dV/dt| ~ 1e10 mV/ms at V = 0), which
     # no fixed-tolerance solver resolves; the crossing of V_peak - 5 mV is
@@ -105,7 +116,7 @@ def _scipy_trace(par, steps, injections=()):
     inj = {}
     for step, rcpt, val in injections:
         inj.setdefault(step, []).append((rcpt, val))
-    y = np.array([p.V_init_mean, p.w_init, 0.0, 0.0])
+    y = np.array([p.V_init_mean, p.w_init, 0.0, 0.0] + ([0.0, 0.0] if alpha else []))
     V = np.zeros(steps)
     spikes = []
     for k in range(steps):
@@ -122,7 +133,12 @@ def _scipy_trace(par, steps, injections=()):
                 continue
             break
         for rcpt, val in inj.get(k, []):
-            y[2 + rcpt] += val  # input of step k enters after step k's integration
+            # input of step k enters after step k's integration: a conductance jump, or (alpha)
+            # a jump of x by W e / tau
+            if alpha:
+                y[4 + rcpt] += val * math.e / (p.tau_ex if rcpt == 0 else p.tau_in)
+            else:
+                y[2 + rcpt] += val
         V[k] = y[0]
     return V, np.array(spikes)
 
@@ -168,3 +184,42 @@ def test_adex_fp32_specification_close_to_fp64_reference():
     assert np.all(np.abs(sp32 - sp64) <= 1)
     m = _away_from_spikes(steps, sp64)
     assert np.abs(V32 - V64)[m].max() <= 2e-3
+
+
+def test_alpha_conductance_closed_form():
+    par = _table2(I_e=0.0, tau_ex=1.0, tau_in=2.5)
+    W_ex, W_in, k0 = 2.0, 3.0, 10
+    out, _ = _oracle_trace(par, 120, fp64=True, injections=[(k0, 0, W_ex), (k0, 1, W_in)],
+                           model=W.AEIF_ALPHA, record=("g_ex", "g_in", "dg_ex"))
+    t = (np.arange(120) - k0) * DT  # time since the input entered (end of step k0)
+    after = t > 0
+    for var, w, tau in (("g_ex", W_ex, 1.0), ("g_in", W_in, 2.5)):
+        ref = w * (t / tau) * np.exp(1.0 - t / tau)
+        assert np.all(out[var][~after] == 0.0)
+        assert np.abs(out[var][after] - ref[after]).max() <= 1e-8 * w, var
+    # the peak, W at t = tau
+    assert abs(out["g_ex"][k0 + 10] - W_ex) <= 1e-8 * W_ex
+    assert abs(out["dg_ex"][k0 + 5] - W_ex * math.e * np.exp(-0.5)) <= 1e-8 * W_ex
+
+
+def test_alpha_subthreshold_three_inputs_match_dop853():
+    par = _table2(I_e=0.0, tau_ex=1.0, tau_in=1.0)
+    inj = [(50, 0, 4.0), (150, 1, 3.0), (250, 0, 6.0)]
+    steps = 450
+    V_o, sp_o = _oracle_trace(par, steps, fp64=True, injections=inj, model=W.AEIF_ALPHA)
+    V_s, sp_s = _scipy_trace(par, steps, injections=inj, alpha=True)
+    assert len(sp_o) == 0 and len(sp_s) == 0
+    assert np.abs(V_o - V_s).max() <= 1e-4
+    assert V_o[70] > V_o[45] + 0.1 and V_o[170] < V_o[145] - 0.1 and V_o[270] > V_o[245] + 0.1
+
+
+def test_alpha_spiking_matches_dop853():
+    par = _table2(I_e=700.0, tau_ex=1.0, tau_in=1.0)
+    inj = [(k, k % 2, 3.0) for k in range(20, 1200, 40)]
+    steps = 1200
+    V_o, sp_o = _oracle_trace(par, steps, fp64=True, injections=inj, model=W.AEIF_ALPHA)
+    V_s, sp_s = _scipy_trace(par, steps, injections=inj, alpha=True)
+    assert len(sp_s) >= 3
+    assert np.array_equal(sp_o, sp_s), (sp_o, sp_s)
+    m = _away_from_spikes(steps, sp_s)
+    assert np.abs(V_o - V_s)[m].max() <= 1e-5
