@@ -37,6 +37,11 @@ METRIC = "real-time factor & synaptic events/s; batched/served vs plain at state
 UNIT = "synaptic events/s"
 DELIVERY = {1: "ring", 2: "spike_buffer"}
 LOOPS = {0: "graph", 1: "persistent", 2: "fused"}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches) from one ncu
+# capture of the full-size microcircuit with FP32 weights in this configuration (delivery scheme, step loop);
+# a kernel or configuration without a capture reports null
+NCU_TRAFFIC = {("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "graph", "k_update_lif"): 2483840,
+               ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "graph", "k_deliver"): 3033728}
 SIM_STEPS_PER_BENCH_STEP = 10_000  # 1 s of biological time at dt = 0.1 ms
 
 
@@ -59,7 +64,10 @@ def _args():
     ap.add_argument("--mode", choices=["auto", "graph", "persistent", "fused"], default="auto",
                     help="step loop: autotuned (default), per-step kernels in CUDA graphs, the persistent kernel, "
                          "or the fused update + delivery kernels in CUDA graphs")
-    ap.add_argument("--workload", choices=["microcircuit", "small", "batched", "adex", "serve", "request"],
+    ap.add_argument("--paper-n", type=str, default="1000000",
+                    help="neurons of the paper's balanced network (comma-separated for a sweep)")
+    ap.add_argument("--paper-ce", type=int, default=800, help="excitatory in-degree of the paper's balanced network")
+    ap.add_argument("--workload", choices=["microcircuit", "small", "batched", "adex", "paper", "serve", "request"],
                     default="microcircuit",
                     help="microcircuit: the benchmark line; batched: 64 microcircuit instances vs the plain path; "
                          "adex: the 1e6-neuron AdEx network; serve: the served request stream")
@@ -336,6 +344,63 @@ def run_adex(a):
     return 0
 
 
+def run_paper(a):
+    """The paper's balanced network (AdEx with alpha-function conductances,
+    in-degree CE + CE/4 = 1000 by default), at one or several sizes: time per
+    biological second, synaptic events/s and the mean rate, beside the paper's
+    figures on one RTX 2080 Ti (about 70 s per biological second at 1e6
+    neurons x 1,000 synapses; 30.7 Hz)."""
+    from paper_2007_14236_gb300 import ngb, workloads as W
+    sizes = [int(x) for x in a.paper_n.split(",")]
+    out = []
+    for n in sizes:
+        n_ex = (n * 4) // 5
+        spec = W.paper_balanced(n_ex=n_ex, ce=a.paper_ce, seed=1, weight_dtype=a.weights)
+        t0 = time.perf_counter()
+        sim = ngb.from_spec(spec, drain_steps=a.sim_steps, record_spikes=False, delivery=a.delivery)
+        sim.finalize()
+        build_s = time.perf_counter() - t0
+        if a.mode == "auto":
+            sim.autotune(200)
+        sim.simulate(1000)  # 100 ms: past the onset transient
+        s0 = sim.stats()
+        t1 = time.perf_counter()
+        for _ in range(a.steps):
+            sim.simulate(a.sim_steps)
+        wall = time.perf_counter() - t1
+        s1 = sim.stats()
+        ms, nl = sim.simulate_profiled(100)
+        nn = s1["num_neurons"]
+        bio = a.steps * a.sim_steps * spec.dt * 1e-3
+        row = {"neurons": nn, "synapses": s1["num_synapses"], "build_s": build_s, "real_time_factor": wall / bio,
+               "events_per_s": (s1["events"] - s0["events"]) / wall,
+               "rate_hz": (s1["spikes"] - s0["spikes"]) / nn / bio,
+               "rk_substeps_per_neuron_step": (s1["rk_substeps"] - s0["rk_substeps"]) / nn / (bio / spec.dt * 1e3),
+               "us_per_launch": {"k_update_aeif": 1e3 * ms[1] / max(1, nl[1]),
+                                 "k_deliver": 1e3 * ms[2] / max(1, nl[2])},
+               "step_loop": LOOPS[s1["mode"]], "delivery": DELIVERY[s1["delivery"]]}
+        sim.close()
+        out.append(row)
+    line = {"workload": "paper_balanced_alpha", "in_degree": a.paper_ce + a.paper_ce // 4, "weights": a.weights,
+            "bio_s_per_size": a.steps * a.sim_steps * 1e-4, "sizes": out,
+            "paper": {"s_per_bio_s_1e6_rtx2080ti": 70.0, "rate_hz": 30.7}}
+    if not a.no_cpu_baseline:
+        # the oracle on 10,000 neurons of the same network (same in-degree), 200 steps after 1,000
+        import oracle
+        small = W.paper_balanced(n_ex=8000, ce=a.paper_ce, seed=1, weight_dtype=a.weights)
+        o = oracle.OracleNet(small)
+        o.finalize()
+        o.simulate(1000)
+        c0 = time.perf_counter()
+        o.simulate(200)
+        cw = time.perf_counter() - c0
+        line["cpu_baseline"] = {"s_per_bio_s_per_1e6_neurons": cw / 0.02 * 100.0, "cores": 1, "kind": "oracle",
+                                "sample": "10,000 neurons of the same network, 200 steps after 1,000, single-threaded "
+                                          "C++ oracle on %s; scaled per neuron to 1e6 neurons" % _cpu_info()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_small(a):
     """Config 0: the 1,000-neuron balanced LIF network, 100 ms of biological
     time per bench step, beside the oracle on the host for the same 100 ms."""
@@ -436,8 +501,8 @@ def main():
     if a.mode in ("persistent", "fused"):
         os.environ["NGB_MODE"] = a.mode  # read by the library when a network is finalised
     if a.workload != "microcircuit":
-        return {"small": run_small, "batched": run_batched, "adex": run_adex, "serve": run_serve,
-                "request": run_request}[a.workload](a)
+        return {"small": run_small, "batched": run_batched, "adex": run_adex, "paper": run_paper,
+                "serve": run_serve, "request": run_request}[a.workload](a)
     ws, rank, local = _dist()
     import numpy as np
     import torch
@@ -566,8 +631,11 @@ def main():
     else:
         dom = max(kern, key=lambda k: kern[k]["ms_total"])
     ach = kern[dom]["algorithmic_bytes_per_launch"] / (kern[dom]["us_per_launch"] * 1e-6) / 1e9
+    workload = ("potjans_diesmann_microcircuit_full_scale" if a.scale == 1.0 else
+                "potjans_diesmann_microcircuit_scale_%g" % a.scale)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_source": peak_kind, "traffic": None}
+                "frac": ach / peak, "peak_source": peak_kind,
+                "traffic": NCU_TRAFFIC.get((workload, a.weights, DELIVERY[st0["delivery"]], mode, dom))}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps, "warmup": a.warmup,

@@ -59,7 +59,11 @@ extern "C" {
 
 /* ----------------------------------------------------------------- enums */
 typedef enum { NGB_WEIGHT_FP32 = 0, NGB_WEIGHT_BF16 = 1, NGB_WEIGHT_FP16 = 2 } ngb_weight_dtype;
-typedef enum { NGB_LIF_PSC_EXP = 0, NGB_AEIF_COND_EXP = 1 } ngb_model;
+/* Neuron models: LIF with exponential PSCs (Eqs. 1-2); AdEx (Eqs. 3-5) with
+ * exponential conductances; AdEx with alpha-function conductances (the
+ * paper's balanced network, Sec. 2.3: an input of weight W gives
+ * g(t) = W (t/tau) e^(1 - t/tau), peak W at t = tau). */
+typedef enum { NGB_LIF_PSC_EXP = 0, NGB_AEIF_COND_EXP = 1, NGB_AEIF_COND_ALPHA = 2 } ngb_model;
 typedef enum {
   NGB_RULE_FIXED_INDEGREE = 0,
   NGB_RULE_FIXED_TOTAL_NUMBER = 1,
@@ -86,7 +90,9 @@ typedef enum {
   NGB_VAR_G_EX = 2,    /* AdEx: excitatory conductance, nS */
   NGB_VAR_G_IN = 3,    /* AdEx: inhibitory conductance, nS */
   NGB_VAR_REFRACT = 4, /* LIF: refractory steps left */
-  NGB_VAR_H = 5        /* AdEx: carried Runge-Kutta step proposal, ms */
+  NGB_VAR_H = 5,       /* AdEx: carried Runge-Kutta step proposal, ms */
+  NGB_VAR_DG_EX = 6,   /* AdEx alpha: x_ex with g_ex' = x_ex - g_ex / tau_ex, nS/ms */
+  NGB_VAR_DG_IN = 7    /* AdEx alpha: x_in, nS/ms */
 } ngb_state_var;
 
 /* ------------------------------------------------------------ structures */
@@ -126,7 +132,9 @@ typedef struct {
   ngb_poisson_drive poisson;
 } ngb_lif_params;
 
-/* AdEx with exponential conductances (Eqs. 3-5).  No refractory period.
+/* AdEx (Eqs. 3-5), for both conductance models (NGB_AEIF_COND_EXP,
+ * NGB_AEIF_COND_ALPHA; tau_ex / tau_in are the decay or alpha time
+ * constants).  No refractory period.
  * rk_tol: relative tolerance of the adaptive Runge-Kutta step; with FP32 state
  * the effective tolerance is max(rk_tol, 8 * 2^-24).  The step size, the time
  * inside the step and the error-ratio test are FP64 unless rk_control_fp32 is

@@ -1,14 +1,20 @@
 // aeif_rk.cuh -- adaptive embedded Runge-Kutta integration of one AdEx neuron
-// with exponential conductances over one step (Sec. 2.1; Eqs. 3-5), shared by
-// the per-step AdEx kernel and the persistent step kernel.
+// over one step (Sec. 2.1; Eqs. 3-5), shared by the per-step AdEx kernel, the
+// fused step kernel and the persistent step kernel.
+//
+// State y = {V, w, g_ex, g_in} for exponential conductances; with
+// alpha-function conductances (the paper's balanced network, Sec. 2.3)
+// also {x_ex, x_in}: g' = x - g/tau, x' = -x/tau, so that an input of weight
+// W (x += W e / tau) gives g(t) = W (t/tau) e^(1 - t/tau).
 //
 // Cash & Karp (1990) 4(5) tableau; FP32 state and stages; the step size h,
-// the time inside the step and the error-ratio test in FP64.  The error of
-// component i is taken relative to |y_i| + |h f_i| + floor_i; accepted
-// steps grow h by min(5, 0.9 r^-1/5), rejected ones shrink it by
-// max(0.1, 0.9 r^-1/4); h >= h_min is always accepted.  After every
-// accepted sub-step ending at V >= V_peak: V -> V_reset, w -> w + b, and
-// the spike is counted (the exponential term uses min(V, V_peak)).
+// the time inside the step and the error-ratio test in FP64 (or FP32 when the
+// population asks for it).  The error of component i is taken relative to
+// |y_i| + |h f_i| + floor_i (floors 1 mV, 1 pA, 1e-3 nS, 1e-3 nS, 1e-3 nS/ms,
+// 1e-3 nS/ms); accepted steps grow h by min(5, 0.9 r^-1/5), rejected ones
+// shrink it by max(0.1, 0.9 r^-1/4); h >= h_min is always accepted.  After
+// every accepted sub-step ending at V >= V_peak: V -> V_reset, w -> w + b,
+// and the spike is counted (the exponential term uses min(V, V_peak)).
 #pragma once
 #include "ngb_internal.cuh"
 
@@ -29,36 +35,40 @@ constexpr float E4 = (float)(125.0 / 594.0 - 13525.0 / 55296.0);
 constexpr float E5 = (float)(-277.0 / 14336.0);
 constexpr float E6 = (float)(512.0 / 1771.0 - 1.0 / 4.0);
 
+// Neuron state in registers: V, w, g_ex, g_in and (alpha conductances) x_ex, x_in.
 struct St {
-  float V, w, ge, gi;
+  float V, w, ge, gi, xe, xi;
 };
 
-__device__ __forceinline__ St deriv(const AeifSeg& p, St y) {
-  const float V = fminf(y.V, p.V_peak);
+template <int NC>
+__device__ __forceinline__ void deriv(const AeifSeg& p, const float y[NC], float f[NC]) {
+  const float V = fminf(y[0], p.V_peak);
   const float I_spk = (p.Delta_T > 0.0f) ? p.g_L * p.Delta_T * expf((V - p.V_T) * p.inv_Delta_T) : 0.0f;
-  const float I_syn = y.ge * (p.E_ex - V) + y.gi * (p.E_in - V);
-  St f;
-  f.V = (-p.g_L * (V - p.E_L) + I_spk + I_syn - y.w + p.I_e) * p.inv_C;
-  f.w = (p.a * (V - p.E_L) - y.w) * p.inv_tau_w;
-  f.ge = -y.ge * p.inv_tau_ex;
-  f.gi = -y.gi * p.inv_tau_in;
-  return f;
-}
-
-__device__ __forceinline__ St axpy(St y, float h, St k) {
-  return St{y.V + h * k.V, y.w + h * k.w, y.ge + h * k.ge, y.gi + h * k.gi};
+  const float I_syn = y[2] * (p.E_ex - V) + y[3] * (p.E_in - V);
+  f[0] = (-p.g_L * (V - p.E_L) + I_spk + I_syn - y[1] + p.I_e) * p.inv_C;
+  f[1] = (p.a * (V - p.E_L) - y[1]) * p.inv_tau_w;
+  if constexpr (NC == 6) {
+    f[2] = y[4] - y[2] * p.inv_tau_ex;
+    f[3] = y[5] - y[3] * p.inv_tau_in;
+    f[4] = -y[4] * p.inv_tau_ex;
+    f[5] = -y[5] * p.inv_tau_in;
+  } else {
+    f[2] = -y[2] * p.inv_tau_ex;
+    f[3] = -y[3] * p.inv_tau_in;
+  }
 }
 
 __device__ __forceinline__ float ratio_of(float err, float y, float hf, float fl) {
   return fabsf(err) / (fabsf(y) + fabsf(hf) + fl);
 }
 
-// Integrate y over one step of p.dt; h carries the step-size proposal in
-// and out.  Adds the sub-steps to nsub and the spikes to nspk; cap_hit is set
-// when the sub-step cap ended the step early.  CT is the precision of the
-// step-size control (h, time inside the step, error-ratio test).
-template <typename CT>
-__device__ __forceinline__ void aeif_integrate_t(const AeifSeg& p, St& y, CT& h, uint32_t& nspk,
+// Integrate y (NC components) over one step of p.dt; h carries the step-size
+// proposal in and out.  Adds the sub-steps to nsub and the spikes to nspk;
+// cap_hit is set when the sub-step cap ended the step early.  CT is the
+// precision of the step-size control (h, time inside the step, error-ratio
+// test).
+template <typename CT, int NC>
+__device__ __forceinline__ void aeif_integrate_t(const AeifSeg& p, float y[NC], CT& h, uint32_t& nspk,
                                                  unsigned long long& nsub, bool& cap_hit) {
   const CT dt = (CT)p.dt, h_min = (CT)p.h_min;
   if (!(h > (CT)0)) h = dt;
@@ -72,47 +82,44 @@ __device__ __forceinline__ void aeif_integrate_t(const AeifSeg& p, St& y, CT& h,
       last = true;
     }
     const float hf = (float)h;
-    const St k1 = deriv(p, y);
-    const St k2 = deriv(p, axpy(y, hf * A21, k1));
-    St ys;
-    ys = St{y.V + hf * (A31 * k1.V + A32 * k2.V), y.w + hf * (A31 * k1.w + A32 * k2.w),
-            y.ge + hf * (A31 * k1.ge + A32 * k2.ge), y.gi + hf * (A31 * k1.gi + A32 * k2.gi)};
-    const St k3 = deriv(p, ys);
-    ys = St{y.V + hf * (A41 * k1.V + A42 * k2.V + A43 * k3.V), y.w + hf * (A41 * k1.w + A42 * k2.w + A43 * k3.w),
-            y.ge + hf * (A41 * k1.ge + A42 * k2.ge + A43 * k3.ge),
-            y.gi + hf * (A41 * k1.gi + A42 * k2.gi + A43 * k3.gi)};
-    const St k4 = deriv(p, ys);
-    ys = St{y.V + hf * (A51 * k1.V + A52 * k2.V + A53 * k3.V + A54 * k4.V),
-            y.w + hf * (A51 * k1.w + A52 * k2.w + A53 * k3.w + A54 * k4.w),
-            y.ge + hf * (A51 * k1.ge + A52 * k2.ge + A53 * k3.ge + A54 * k4.ge),
-            y.gi + hf * (A51 * k1.gi + A52 * k2.gi + A53 * k3.gi + A54 * k4.gi)};
-    const St k5 = deriv(p, ys);
-    ys = St{y.V + hf * (A61 * k1.V + A62 * k2.V + A63 * k3.V + A64 * k4.V + A65 * k5.V),
-            y.w + hf * (A61 * k1.w + A62 * k2.w + A63 * k3.w + A64 * k4.w + A65 * k5.w),
-            y.ge + hf * (A61 * k1.ge + A62 * k2.ge + A63 * k3.ge + A64 * k4.ge + A65 * k5.ge),
-            y.gi + hf * (A61 * k1.gi + A62 * k2.gi + A63 * k3.gi + A64 * k4.gi + A65 * k5.gi)};
-    const St k6 = deriv(p, ys);
-    const St y5{y.V + hf * (B1 * k1.V + B3 * k3.V + B4 * k4.V + B6 * k6.V),
-                y.w + hf * (B1 * k1.w + B3 * k3.w + B4 * k4.w + B6 * k6.w),
-                y.ge + hf * (B1 * k1.ge + B3 * k3.ge + B4 * k4.ge + B6 * k6.ge),
-                y.gi + hf * (B1 * k1.gi + B3 * k3.gi + B4 * k4.gi + B6 * k6.gi)};
-    const St er{hf * (E1 * k1.V + E3 * k3.V + E4 * k4.V + E5 * k5.V + E6 * k6.V),
-                hf * (E1 * k1.w + E3 * k3.w + E4 * k4.w + E5 * k5.w + E6 * k6.w),
-                hf * (E1 * k1.ge + E3 * k3.ge + E4 * k4.ge + E5 * k5.ge + E6 * k6.ge),
-                hf * (E1 * k1.gi + E3 * k3.gi + E4 * k4.gi + E5 * k5.gi + E6 * k6.gi)};
-    float emax = ratio_of(er.V, y.V, hf * k1.V, 1.0f);
-    emax = fmaxf(emax, ratio_of(er.w, y.w, hf * k1.w, 1.0f));
-    emax = fmaxf(emax, ratio_of(er.ge, y.ge, hf * k1.ge, 1e-3f));
-    emax = fmaxf(emax, ratio_of(er.gi, y.gi, hf * k1.gi, 1e-3f));
+    float k1[NC], k2[NC], k3[NC], k4[NC], k5[NC], k6[NC], ys[NC];
+    deriv<NC>(p, y, k1);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) ys[i] = y[i] + hf * A21 * k1[i];
+    deriv<NC>(p, ys, k2);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) ys[i] = y[i] + hf * (A31 * k1[i] + A32 * k2[i]);
+    deriv<NC>(p, ys, k3);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) ys[i] = y[i] + hf * (A41 * k1[i] + A42 * k2[i] + A43 * k3[i]);
+    deriv<NC>(p, ys, k4);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) ys[i] = y[i] + hf * (A51 * k1[i] + A52 * k2[i] + A53 * k3[i] + A54 * k4[i]);
+    deriv<NC>(p, ys, k5);
+#pragma unroll
+    for (int i = 0; i < NC; ++i)
+      ys[i] = y[i] + hf * (A61 * k1[i] + A62 * k2[i] + A63 * k3[i] + A64 * k4[i] + A65 * k5[i]);
+    deriv<NC>(p, ys, k6);
+    float y5[NC], er[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      y5[i] = y[i] + hf * (B1 * k1[i] + B3 * k3[i] + B4 * k4[i] + B6 * k6[i]);
+      er[i] = hf * (E1 * k1[i] + E3 * k3[i] + E4 * k4[i] + E5 * k5[i] + E6 * k6[i]);
+    }
+    float emax = ratio_of(er[0], y[0], hf * k1[0], 1.0f);
+    emax = fmaxf(emax, ratio_of(er[1], y[1], hf * k1[1], 1.0f));
+#pragma unroll
+    for (int i = 2; i < NC; ++i) emax = fmaxf(emax, ratio_of(er[i], y[i], hf * k1[i], 1e-3f));
     const CT ratio = (CT)emax * (CT)p.inv_tol;
     ++nsub;
     ++n;
     const bool cap = n >= p.max_sub;
     if (ratio <= (CT)1 || h <= h_min || cap) {
-      y = y5;
-      if (y.V >= p.V_peak) {
-        y.V = p.V_reset;
-        y.w = y.w + p.b;
+#pragma unroll
+      for (int i = 0; i < NC; ++i) y[i] = y5[i];
+      if (y[0] >= p.V_peak) {
+        y[0] = p.V_reset;
+        y[1] = y[1] + p.b;
         ++nspk;
       }
       const float rf = emax * (float)p.inv_tol;
@@ -132,15 +139,50 @@ __device__ __forceinline__ void aeif_integrate_t(const AeifSeg& p, St& y, CT& h,
   }
 }
 
-// FP64 step-size control by default, FP32 when the population asks for it.
-__device__ __forceinline__ void aeif_integrate(const AeifSeg& p, St& y, double& h, uint32_t& nspk,
-                                               unsigned long long& nsub, bool& cap_hit) {
+template <int NC>
+__device__ __forceinline__ void aeif_integrate_nc(const AeifSeg& p, St& s, double& h, uint32_t& nspk,
+                                                  unsigned long long& nsub, bool& cap_hit) {
+  float y[NC];
+  y[0] = s.V;
+  y[1] = s.w;
+  y[2] = s.ge;
+  y[3] = s.gi;
+  if constexpr (NC == 6) {
+    y[4] = s.xe;
+    y[5] = s.xi;
+  }
   if (p.ctl32) {
     float hf = (float)h;
-    aeif_integrate_t<float>(p, y, hf, nspk, nsub, cap_hit);
+    aeif_integrate_t<float, NC>(p, y, hf, nspk, nsub, cap_hit);
     h = (double)hf;
   } else {
-    aeif_integrate_t<double>(p, y, h, nspk, nsub, cap_hit);
+    aeif_integrate_t<double, NC>(p, y, h, nspk, nsub, cap_hit);
+  }
+  s.V = y[0];
+  s.w = y[1];
+  s.ge = y[2];
+  s.gi = y[3];
+  if constexpr (NC == 6) {
+    s.xe = y[4];
+    s.xi = y[5];
+  }
+}
+
+// One AdEx step of neuron state s: integration (FP64 step-size control by
+// default, FP32 when the population asks for it), then the step's input on
+// the two receptors: a conductance jump (exponential), or x += W e / tau
+// (alpha).  kAlpha selects the conductance model at compile time.
+template <bool kAlpha>
+__device__ __forceinline__ void aeif_step(const AeifSeg& p, St& s, double& h, float in0, float in1, uint32_t& nspk,
+                                          unsigned long long& nsub, bool& cap_hit) {
+  if (kAlpha) {
+    aeif_integrate_nc<6>(p, s, h, nspk, nsub, cap_hit);
+    s.xe = __fadd_rn(s.xe, __fmul_rn(in0, p.e_tau_ex));
+    s.xi = __fadd_rn(s.xi, __fmul_rn(in1, p.e_tau_in));
+  } else {
+    aeif_integrate_nc<4>(p, s, h, nspk, nsub, cap_hit);
+    s.ge = __fadd_rn(s.ge, in0);
+    s.gi = __fadd_rn(s.gi, in1);
   }
 }
 

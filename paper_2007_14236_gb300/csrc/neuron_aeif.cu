@@ -15,18 +15,20 @@
 // is evaluated at min(V, V_peak)), then add the step's conductance input and
 // join the warp-ballot spike compaction with the spike multiplicity.  In the
 // spike-buffer delivery scheme the kernel that runs first in the step also
-// scans the pending spikes (as the LIF kernel).
+// scans the pending spikes (as the LIF kernel).  kAlpha: alpha-function
+// conductances (the paper's balanced network, Sec. 2.3) with state x_ex, x_in.
 #include "aeif_rk.cuh"
 #include "neuron_step.cuh"
 
 namespace ngb {
 
-template <bool kFixed, bool kAge>
+template <bool kFixed, bool kAge, bool kAlpha>
 __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constant__ SegTable<AeifSeg> T,
                                                             const uint32_t* __restrict__ thr,
                                                             float* __restrict__ V_, float* __restrict__ w_,
                                                             float* __restrict__ ge_, float* __restrict__ gi_,
-                                                            float* __restrict__ h_, Ring ring, int64_t* clk,
+                                                            float* __restrict__ h_, float* __restrict__ xe_,
+                                                            float* __restrict__ xi_, Ring ring, int64_t* clk,
                                                             const Csr csr, SpikeBuf sb, int scan) {
   __shared__ uint32_t s_thr[kMaxThr];
   const AeifSeg p = segment_of(T, (int64_t)blockIdx.x);
@@ -34,11 +36,18 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
   const bool valid = k < p.n;
   const uint32_t gid = (uint32_t)(p.offset + k);
   // prologue (overlaps the previous kernel): state, source metadata, Poisson table
-  St y{0.f, 0.f, 0.f, 0.f};
+  St y{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   float h0 = 0.f;
   uint4 meta = make_uint4(0, 0, 0, 0);
   if (valid) {
-    y = St{V_[gid], w_[gid], ge_[gid], gi_[gid]};
+    y.V = V_[gid];
+    y.w = w_[gid];
+    y.ge = ge_[gid];
+    y.gi = gi_[gid];
+    if (kAlpha) {
+      y.xe = xe_[gid];
+      y.xi = xi_[gid];
+    }
     h0 = h_[gid];
     if (!kAge) meta = __ldg(csr.src_meta + gid);
   }
@@ -66,14 +75,16 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
     }
     double h = (double)h0;
     bool cap_hit = false;
-    aeif_integrate(p, y, h, nspk, nsub, cap_hit);
+    aeif_step<kAlpha>(p, y, h, in0, in1, nspk, nsub, cap_hit);
     if (cap_hit) atomicOr(sb.err, kErrSubstepCap);
-    y.ge = __fadd_rn(y.ge, in0);
-    y.gi = __fadd_rn(y.gi, in1);
     V_[gid] = y.V;
     w_[gid] = y.w;
     ge_[gid] = y.ge;
     gi_[gid] = y.gi;
+    if (kAlpha) {
+      xe_[gid] = y.xe;
+      xi_[gid] = y.xi;
+    }
     h_[gid] = (float)h;
   }
   // sub-step statistics: one atomic per warp
@@ -86,19 +97,29 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
 }
 
 cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V,
-                               float* w, float* gex, float* gin, float* h, Ring ring, bool fixed, int64_t* clk,
-                               const Csr& csr, SpikeBuf sb, bool age, bool scan, bool pdl, cudaStream_t st) {
+                               float* w, float* gex, float* gin, float* h, float* xe, float* xi, bool alpha,
+                               Ring ring, bool fixed, int64_t* clk, const Csr& csr, SpikeBuf sb, bool age, bool scan,
+                               bool pdl, cudaStream_t st) {
   if (blocks <= 0) return cudaSuccess;
   const dim3 g((unsigned)blocks), b(kAeifBlock);
   const int sc = scan ? 1 : 0;
-  if (fixed) {
-    if (age)
-      return launch_k(k_update_aeif<true, true>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, ring, clk, csr, sb, sc);
-    return launch_k(k_update_aeif<true, false>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, ring, clk, csr, sb, sc);
+#define NGB_AEIF(F, A, P) \
+  return launch_k(k_update_aeif<F, A, P>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, xe, xi, ring, clk, csr, sb, sc)
+  if (alpha) {
+    if (fixed) {
+      if (age) NGB_AEIF(true, true, true);
+      NGB_AEIF(true, false, true);
+    }
+    if (age) NGB_AEIF(false, true, true);
+    NGB_AEIF(false, false, true);
   }
-  if (age)
-    return launch_k(k_update_aeif<false, true>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, ring, clk, csr, sb, sc);
-  return launch_k(k_update_aeif<false, false>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, ring, clk, csr, sb, sc);
+  if (fixed) {
+    if (age) NGB_AEIF(true, true, false);
+    NGB_AEIF(true, false, false);
+  }
+  if (age) NGB_AEIF(false, true, false);
+  NGB_AEIF(false, false, false);
+#undef NGB_AEIF
 }
 
 }  // namespace ngb

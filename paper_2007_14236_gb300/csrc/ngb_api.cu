@@ -192,6 +192,7 @@ struct ngb_sim {
   std::vector<void*> allocs;
   size_t dev_bytes = 0;
   float *st0 = nullptr, *st1 = nullptr, *st2 = nullptr, *st3 = nullptr, *st4 = nullptr;
+  float *st5 = nullptr, *st6 = nullptr;  // AdEx alpha conductances: x_ex, x_in
   int32_t* ref = nullptr;
   void* ring = nullptr;
   uint64_t* src_syn = nullptr;
@@ -209,9 +210,11 @@ struct ngb_sim {
   int n_lif = 0;
   int64_t lif_blocks = 0;
   int lif_npt = 1;  // LIF neurons per thread of the per-step update kernel (1 or 4)
-  SegTable<AeifSeg> aeif_tab{};
-  int n_aeif = 0;
-  int64_t aeif_blocks = 0;
+  SegTable<AeifSeg> aeif_tab{};   // AdEx segments with exponential conductances
+  SegTable<AeifSeg> aeifa_tab{};  // AdEx segments with alpha-function conductances
+  int n_aeif = 0;                 // AdEx segments of both kinds
+  int n_aeif_exp = 0, n_aeif_alpha = 0;
+  int64_t aeif_blocks = 0, aeifa_blocks = 0;
   uint32_t* thr = nullptr;
   int deliver_grid = 0;
   bool pdl = true;  // programmatic dependent launch between the step's kernels
@@ -273,10 +276,18 @@ cudaError_t launch_lif(ngb_sim* s) {
                            s->stream);
 }
 
+// AdEx update kernels: exponential-conductance segments, then alpha ones.
 cudaError_t launch_aeif(ngb_sim* s) {
-  return launch_update_aeif(s->aeif_tab, s->aeif_blocks, s->thr, s->st0, s->st1, s->st2, s->st3, s->st4,
-                            ring_of(s), s->cfg.deterministic != 0, s->clk, csr_of(s), s->sb, s->scheme == 2,
-                            s->n_lif == 0, s->pdl, s->stream);
+  cudaError_t e = cudaSuccess;
+  if (s->n_aeif_exp)
+    e = launch_update_aeif(s->aeif_tab, s->aeif_blocks, s->thr, s->st0, s->st1, s->st2, s->st3, s->st4, s->st5,
+                           s->st6, false, ring_of(s), s->cfg.deterministic != 0, s->clk, csr_of(s), s->sb,
+                           s->scheme == 2, s->n_lif == 0, s->pdl, s->stream);
+  if (e == cudaSuccess && s->n_aeif_alpha)
+    e = launch_update_aeif(s->aeifa_tab, s->aeifa_blocks, s->thr, s->st0, s->st1, s->st2, s->st3, s->st4, s->st5,
+                           s->st6, true, ring_of(s), s->cfg.deterministic != 0, s->clk, csr_of(s), s->sb,
+                           s->scheme == 2, s->n_lif == 0 && s->n_aeif_exp == 0, s->pdl, s->stream);
+  return e;
 }
 
 cudaError_t launch_del(ngb_sim* s) {
@@ -294,15 +305,30 @@ void set_scheme(ngb_sim* s, int scheme) {
 
 // Fused step loop (mode 2, ring scheme): update kernels that deliver their
 // blocks' spikes; the step is clk[0] + step_off.
-cudaError_t launch_fused(ngb_sim* s, int64_t step_off) {
+cudaError_t launch_fused_lif(ngb_sim* s, int64_t step_off) {
+  if (!s->n_lif) return cudaSuccess;
+  return launch_step_lif(s->lif_tab, s->lif_blocks, s->thr, s->st0, s->st1, s->ref, ring_of(s),
+                         s->cfg.deterministic != 0, s->cfg.weight_dtype, s->clk, step_off, csr_of(s), s->sb, s->pdl,
+                         s->stream);
+}
+
+cudaError_t launch_fused_aeif(ngb_sim* s, int64_t step_off) {
   cudaError_t e = cudaSuccess;
   const bool det = s->cfg.deterministic != 0;
-  if (s->n_lif)
-    e = launch_step_lif(s->lif_tab, s->lif_blocks, s->thr, s->st0, s->st1, s->ref, ring_of(s), det,
-                        s->cfg.weight_dtype, s->clk, step_off, csr_of(s), s->sb, s->pdl, s->stream);
-  if (e == cudaSuccess && s->n_aeif)
-    e = launch_step_aeif(s->aeif_tab, s->aeif_blocks, s->thr, s->st0, s->st1, s->st2, s->st3, s->st4, ring_of(s),
-                         det, s->cfg.weight_dtype, s->clk, step_off, csr_of(s), s->sb, s->pdl, s->stream);
+  if (s->n_aeif_exp)
+    e = launch_step_aeif(s->aeif_tab, s->aeif_blocks, s->thr, s->st0, s->st1, s->st2, s->st3, s->st4, s->st5, s->st6,
+                         false, ring_of(s), det, s->cfg.weight_dtype, s->clk, step_off, csr_of(s), s->sb, s->pdl,
+                         s->stream);
+  if (e == cudaSuccess && s->n_aeif_alpha)
+    e = launch_step_aeif(s->aeifa_tab, s->aeifa_blocks, s->thr, s->st0, s->st1, s->st2, s->st3, s->st4, s->st5,
+                         s->st6, true, ring_of(s), det, s->cfg.weight_dtype, s->clk, step_off, csr_of(s), s->sb,
+                         s->pdl, s->stream);
+  return e;
+}
+
+cudaError_t launch_fused(ngb_sim* s, int64_t step_off) {
+  cudaError_t e = launch_fused_lif(s, step_off);
+  if (e == cudaSuccess) e = launch_fused_aeif(s, step_off);
   return e;
 }
 
@@ -447,6 +473,8 @@ int place_population(ngb_sim* s, int pi) {
     const ngb_aeif_params& q = p.aeif;
     CK(cudaMemsetAsync(s->st2 + off, 0, p.n * sizeof(float), st));
     CK(cudaMemsetAsync(s->st3 + off, 0, p.n * sizeof(float), st));
+    CK(cudaMemsetAsync(s->st5 + off, 0, p.n * sizeof(float), st));
+    CK(cudaMemsetAsync(s->st6 + off, 0, p.n * sizeof(float), st));
     CK(launch_init_state(1, p.n, q.V_init_mean_mV, q.V_init_sd_mV, q.E_L_mV, q.w_init_pA, q.rk_h_init_ms, seed,
                          p.local_off, s->st0 + off, s->st1 + off, s->st4 + off, st));
   }
@@ -665,10 +693,11 @@ int rebuild_tables(ngb_sim* s) {
   };
   const double dt = s->cfg.dt_ms;
   std::vector<LifSeg> lsegs;
-  std::vector<AeifSeg> asegs;
+  std::vector<AeifSeg> asegs_exp, asegs_alpha;
   std::vector<uint32_t> thr_all;
   s->lif_blocks = 0;
   s->aeif_blocks = 0;
+  s->aeifa_blocks = 0;
   s->n_active = 0;
   {
     // several LIF neurons per thread when the update grid would fill the GPU
@@ -721,7 +750,8 @@ int rebuild_tables(ngb_sim* s) {
       AeifSeg g{};
       g.offset = p.offset;
       g.n = p.n;
-      g.blk_begin = s->aeif_blocks;
+      g.alpha = p.model == NGB_AEIF_COND_ALPHA ? 1 : 0;
+      g.blk_begin = g.alpha ? s->aeifa_blocks : s->aeif_blocks;
       g.t0 = I.t0;
       g.seed = I.seed;
       g.local_off = p.local_off;
@@ -753,14 +783,22 @@ int rebuild_tables(ngb_sim* s) {
       g.h_min = q.rk_h_min_ms;
       g.dt = dt;
       g.max_sub = q.rk_max_substeps;
-      asegs.push_back(g);
-      s->aeif_blocks += (p.n + kAeifBlock - 1) / kAeifBlock;
+      constexpr double kEuler = 2.718281828459045;
+      g.e_tau_ex = (float)(kEuler / q.tau_ex_ms);
+      g.e_tau_in = (float)(kEuler / q.tau_in_ms);
+      (g.alpha ? asegs_alpha : asegs_exp).push_back(g);
+      (g.alpha ? s->aeifa_blocks : s->aeif_blocks) += (p.n + kAeifBlock - 1) / kAeifBlock;
     }
   }
   s->n_lif = (int)lsegs.size();
-  s->n_aeif = (int)asegs.size();
+  s->n_aeif_exp = (int)asegs_exp.size();
+  s->n_aeif_alpha = (int)asegs_alpha.size();
+  s->n_aeif = s->n_aeif_exp + s->n_aeif_alpha;
+  std::vector<AeifSeg> asegs(asegs_exp);  // every AdEx segment, for the persistent kernel
+  asegs.insert(asegs.end(), asegs_alpha.begin(), asegs_alpha.end());
   s->lif_tab = SegTable<LifSeg>{};
   s->aeif_tab = SegTable<AeifSeg>{};
+  s->aeifa_tab = SegTable<AeifSeg>{};
   if (s->n_lif) {
     LifSeg* d = nullptr;
     CK(talloc((void**)&d, lsegs.size() * sizeof(LifSeg)));
@@ -778,22 +816,32 @@ int rebuild_tables(ngb_sim* s) {
     CK(cudaMemcpyAsync(db, bs.data(), bs.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
     s->lif_tab.blk_seg = db;
   }
-  if (s->n_aeif) {
+  // per-step tables of the AdEx kernels, one per conductance model
+  auto aeif_table = [&](const std::vector<AeifSeg>& v, int64_t blocks, SegTable<AeifSeg>& tab) -> cudaError_t {
+    if (v.empty()) return cudaSuccess;
     AeifSeg* d = nullptr;
-    CK(talloc((void**)&d, asegs.size() * sizeof(AeifSeg)));
-    CK(cudaMemcpyAsync(d, asegs.data(), asegs.size() * sizeof(AeifSeg), cudaMemcpyHostToDevice, st));
-    s->aeif_tab.dev = d;
-    s->aeif_tab.n = s->n_aeif;
-    for (int i = 0; i < std::min(s->n_aeif, kInlineSegs); ++i) s->aeif_tab.s[i] = asegs[(size_t)i];
-    std::vector<uint32_t> bs((size_t)s->aeif_blocks);
-    for (size_t i = 0; i < asegs.size(); ++i) {
-      const int64_t nb = (asegs[i].n + kAeifBlock - 1) / kAeifBlock;
-      for (int64_t b = 0; b < nb; ++b) bs[(size_t)(asegs[i].blk_begin + b)] = (uint32_t)i;
+    cudaError_t e = talloc((void**)&d, v.size() * sizeof(AeifSeg));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, v.data(), v.size() * sizeof(AeifSeg), cudaMemcpyHostToDevice, st);
+    tab.dev = d;
+    tab.n = (int)v.size();
+    for (int i = 0; i < std::min(tab.n, kInlineSegs); ++i) tab.s[i] = v[(size_t)i];
+    std::vector<uint32_t> bs((size_t)blocks);
+    for (size_t i = 0; i < v.size(); ++i) {
+      const int64_t nb = (v[i].n + kAeifBlock - 1) / kAeifBlock;
+      for (int64_t b = 0; b < nb; ++b) bs[(size_t)(v[i].blk_begin + b)] = (uint32_t)i;
     }
     uint32_t* db = nullptr;
-    CK(talloc((void**)&db, bs.size() * sizeof(uint32_t)));
-    CK(cudaMemcpyAsync(db, bs.data(), bs.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    s->aeif_tab.blk_seg = db;
+    if (e == cudaSuccess) e = talloc((void**)&db, bs.size() * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(db, bs.data(), bs.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+    tab.blk_seg = db;
+    return e;
+  };
+  CK(aeif_table(asegs_exp, s->aeif_blocks, s->aeif_tab));
+  CK(aeif_table(asegs_alpha, s->aeifa_blocks, s->aeifa_tab));
+  AeifSeg* d_asegs = nullptr;
+  if (!asegs.empty()) {
+    CK(talloc((void**)&d_asegs, asegs.size() * sizeof(AeifSeg)));
+    CK(cudaMemcpyAsync(d_asegs, asegs.data(), asegs.size() * sizeof(AeifSeg), cudaMemcpyHostToDevice, st));
   }
   CK(talloc((void**)&s->thr, (thr_all.size() + 1) * sizeof(uint32_t)));
   if (!thr_all.empty())
@@ -812,11 +860,12 @@ int rebuild_tables(ngb_sim* s) {
     auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
     PersistArgs& a = s->pa;
     a.lseg = s->lif_tab.dev;
-    a.aseg = s->aeif_tab.dev;
+    a.aseg = d_asegs;
     a.lvoff = dlv;
     a.avoff = dav;
     a.thr = s->thr;
     a.st0 = s->st0; a.st1 = s->st1; a.st2 = s->st2; a.st3 = s->st3; a.st4 = s->st4;
+    a.st5 = s->st5; a.st6 = s->st6;
     a.ref = s->ref;
     a.src_meta = s->src_meta;
     a.ring = ring_of(s);
@@ -870,7 +919,7 @@ int finalize_impl(ngb_sim* s) {
     if (s->N <= 0) return fail(NGB_ERR_STATE, "ngb_finalize: no neurons");
     s->R = 1;
     for (const PopHost& p : s->pops)
-      if (p.model == NGB_AEIF_COND_EXP) s->R = 2;
+      if (p.model != NGB_LIF_PSC_EXP) s->R = 2;
     s->N_cap = s->N;
     uint64_t K = 0;
     for (const CallHost& c : s->calls) {
@@ -894,6 +943,10 @@ int finalize_impl(ngb_sim* s) {
     CK(s->dalloc(&s->st2, N));
     CK(s->dalloc(&s->st3, N));
     CK(s->dalloc(&s->st4, N));
+    CK(s->dalloc(&s->st5, N));
+    CK(s->dalloc(&s->st6, N));
+    CK(cudaMemsetAsync(s->st5, 0, N * sizeof(float), st));
+    CK(cudaMemsetAsync(s->st6, 0, N * sizeof(float), st));
     CK(cudaMemsetAsync(s->st2, 0, N * sizeof(float), st));
     CK(cudaMemsetAsync(s->st3, 0, N * sizeof(float), st));
     CK(cudaMemsetAsync(s->st4, 0, N * sizeof(float), st));
@@ -1118,15 +1171,9 @@ int simulate_impl(ngb_sim* s, int64_t steps, bool profiled, double* kernel_ms, i
     for (int64_t i = 0; i < chunk; ++i) {
       cudaEvent_t* e = &ev[4 * i];
       CK(cudaEventRecord(e[0], s->stream));
-      if (s->n_lif) CK(fused ? launch_step_lif(s->lif_tab, s->lif_blocks, s->thr, s->st0, s->st1, s->ref, ring_of(s),
-                                               s->cfg.deterministic != 0, s->cfg.weight_dtype, s->clk, 0, csr_of(s),
-                                               s->sb, s->pdl, s->stream)
-                             : launch_lif(s));
+      if (s->n_lif) CK(fused ? launch_fused_lif(s, 0) : launch_lif(s));
       CK(cudaEventRecord(e[1], s->stream));
-      if (s->n_aeif) CK(fused ? launch_step_aeif(s->aeif_tab, s->aeif_blocks, s->thr, s->st0, s->st1, s->st2, s->st3,
-                                                 s->st4, ring_of(s), s->cfg.deterministic != 0, s->cfg.weight_dtype,
-                                                 s->clk, 0, csr_of(s), s->sb, s->pdl, s->stream)
-                              : launch_aeif(s));
+      if (s->n_aeif) CK(fused ? launch_fused_aeif(s, 0) : launch_aeif(s));
       CK(cudaEventRecord(e[2], s->stream));
       CK(fused ? launch_tick_add(s->clk, 1, s->sb.ctr, s->pdl, s->stream) : launch_del(s));
       CK(cudaEventRecord(e[3], s->stream));
@@ -1179,6 +1226,8 @@ int snapshot_take(ngb_sim* s, Snapshot& sn) {
     sn.parts.push_back({s->st2, N * 4});
     sn.parts.push_back({s->st3, N * 4});
     sn.parts.push_back({s->st4, N * 4});
+    sn.parts.push_back({s->st5, N * 4});
+    sn.parts.push_back({s->st6, N * 4});
   }
   for (auto& p : sn.parts) {
     void* c = nullptr;
@@ -1207,7 +1256,7 @@ std::string tune_key(ngb_sim* s) {
   char buf[512];
   std::snprintf(buf, sizeof(buf), "%s|sm%d|N%lld|K%llu|G%llu|L%lld|R%d|w%d|det%d|lif%d|aeif%d|dl%d", prop.name,
                 prop.multiProcessorCount, (long long)s->N, (unsigned long long)s->K, (unsigned long long)s->G,
-                (long long)s->L, s->R, s->cfg.weight_dtype, s->cfg.deterministic, s->n_lif, s->n_aeif,
+                (long long)s->L, s->R, s->cfg.weight_dtype, s->cfg.deterministic, s->n_lif, s->n_aeif * 100 + s->n_aeif_alpha,
                 s->cfg.delivery);
   for (char* c = buf; *c; ++c)
     if (*c == ' ') *c = '_';
@@ -1297,7 +1346,7 @@ int ngb_add_population_in(ngb_sim* s, int32_t instance, int32_t model, int64_t n
       return fail(NGB_ERR_INVALID_ARG, "ngb_add_population: LIF parameters");
     lambda = q.poisson.n_inputs * q.poisson.rate_hz * dt * 1e-3;
     s->pop_E_L.push_back(q.E_L_mV);
-  } else if (model == NGB_AEIF_COND_EXP) {
+  } else if (model == NGB_AEIF_COND_EXP || model == NGB_AEIF_COND_ALPHA) {
     p.aeif = *(const ngb_aeif_params*)params;
     const ngb_aeif_params& q = p.aeif;
     if (!(q.C_m_pF > 0 && q.tau_w_ms > 0 && q.tau_ex_ms > 0 && q.tau_in_ms > 0 && q.rk_tol > 0 &&
@@ -1543,7 +1592,7 @@ int ngb_reserve(ngb_sim* s, int64_t max_neurons, int64_t max_synapses, int64_t m
     return fail(NGB_ERR_INVALID_ARG, "ngb_reserve: capacities");
   if (max_neurons < s->N) return fail(NGB_ERR_INVALID_ARG, "ngb_reserve: fewer neurons than already added");
   for (const PopHost& p : s->pops)
-    if (p.model == NGB_AEIF_COND_EXP && receptors < 2)
+    if (p.model != NGB_LIF_PSC_EXP && receptors < 2)
       return fail(NGB_ERR_INVALID_ARG, "ngb_reserve: AdEx populations need two receptors");
   s->serving = true;
   s->N_cap = max_neurons;
@@ -1562,7 +1611,7 @@ int ngb_commit_instance(ngb_sim* s, int32_t instance) {
   if (instance < 0 || instance >= (int32_t)s->inst.size())
     return fail(NGB_ERR_INVALID_ARG, "ngb_commit_instance: instance");
   for (const PopHost& p : s->pops)
-    if (p.instance == instance && p.model == NGB_AEIF_COND_EXP && s->R < 2)
+    if (p.instance == instance && p.model != NGB_LIF_PSC_EXP && s->R < 2)
       return fail(NGB_ERR_INVALID_ARG, "ngb_commit_instance: AdEx needs two receptors");
   if (!s->finalized) {
     rc = finalize_impl(s);
@@ -1670,7 +1719,9 @@ int ngb_get_stats(ngb_sim* s, ngb_stats* out) {
     out->max_delay_steps = s->max_delay;
     out->device_bytes = (int64_t)s->dev_bytes;
     out->mode = s->mode;
-    out->launch_grid = s->mode == 1 ? s->persist_grid : s->mode == 2 ? s->lif_blocks + s->aeif_blocks : s->deliver_grid;
+    out->launch_grid = s->mode == 1   ? s->persist_grid
+                       : s->mode == 2 ? s->lif_blocks + s->aeif_blocks + s->aeifa_blocks
+                                      : s->deliver_grid;
     out->delivery = s->scheme;
   }
   return NGB_OK;
@@ -1698,6 +1749,8 @@ int ngb_get_state(ngb_sim* s, int32_t var, int64_t first, int64_t n, float* out)
     case NGB_VAR_G_EX: src = s->st2; break;
     case NGB_VAR_G_IN: src = s->st3; break;
     case NGB_VAR_H: src = s->st4; break;
+    case NGB_VAR_DG_EX: src = s->st5; break;
+    case NGB_VAR_DG_IN: src = s->st6; break;
     case NGB_VAR_REFRACT: is_ref = true; break;
     default: return fail(NGB_ERR_INVALID_ARG, "ngb_get_state: var");
   }

@@ -93,9 +93,11 @@ struct AeifSeg {
   uint32_t local_off, n_thr, thr_off;
   int32_t prec_rcpt;   // receptor of the Poisson drive
   int32_t ctl32;       // step-size control in FP32 instead of FP64
-  int32_t pad2_;
+  int32_t alpha;       // alpha-function conductances (state x_ex, x_in)
   float g_L, E_L, V_T, Delta_T, inv_Delta_T, a, inv_tau_w, V_peak, V_reset, b;
-  float E_ex, E_in, inv_tau_ex, inv_tau_in, I_e, inv_C, w_ext, pad_;
+  float E_ex, E_in, inv_tau_ex, inv_tau_in, I_e, inv_C, w_ext;
+  float e_tau_ex, e_tau_in;  // e / tau: the jump of x per unit input weight (alpha)
+  float pad_;
   double inv_tol, h_min, dt;
   int64_t max_sub;
 };
@@ -410,7 +412,7 @@ struct PersistArgs {
   const int64_t* lvoff;  // [n_lseg + 1] first LIF-only index of each LIF segment
   const int64_t* avoff;  // [n_aseg + 1]
   const uint32_t* thr;
-  float *st0, *st1, *st2, *st3, *st4;
+  float *st0, *st1, *st2, *st3, *st4, *st5, *st6;
   int32_t* ref;
   const uint4* src_meta;
   Ring ring;
@@ -435,9 +437,11 @@ struct PersistArgs {
 cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, int npt, const uint32_t* thr, float* y,
                               float* I, int32_t* ref, Ring ring, bool fixed, int64_t* clk, const Csr& csr,
                               SpikeBuf sb, bool age, bool scan, bool pdl, cudaStream_t st);
+// alpha: the segments have alpha-function conductances (x_ex, x_in in xe, xi).
 cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V,
-                               float* w, float* gex, float* gin, float* h, Ring ring, bool fixed, int64_t* clk,
-                               const Csr& csr, SpikeBuf sb, bool age, bool scan, bool pdl, cudaStream_t st);
+                               float* w, float* gex, float* gin, float* h, float* xe, float* xi, bool alpha,
+                               Ring ring, bool fixed, int64_t* clk, const Csr& csr, SpikeBuf sb, bool age, bool scan,
+                               bool pdl, cudaStream_t st);
 cudaError_t launch_tick(int64_t* clk, bool pdl, cudaStream_t st);
 cudaError_t persistent_max_blocks_per_sm(bool fixed, int wdtype, bool lif, bool aeif, size_t smem, int* out);
 cudaError_t launch_persistent(const PersistArgs& a, bool fixed, int wdtype, bool lif, bool aeif, int grid,
@@ -455,8 +459,9 @@ cudaError_t launch_step_lif(const SegTable<LifSeg>& segs, int64_t blocks, const 
                             int32_t* ref, Ring ring, bool fixed, int wdtype, const int64_t* clk, int64_t step_off,
                             const Csr& csr, SpikeBuf sb, bool pdl, cudaStream_t st);
 cudaError_t launch_step_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V, float* w,
-                             float* gex, float* gin, float* h, Ring ring, bool fixed, int wdtype, const int64_t* clk,
-                             int64_t step_off, const Csr& csr, SpikeBuf sb, bool pdl, cudaStream_t st);
+                             float* gex, float* gin, float* h, float* xe, float* xi, bool alpha, Ring ring, bool fixed,
+                             int wdtype, const int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, bool pdl,
+                             cudaStream_t st);
 // clk[0] += n (clk[1] = clk[0] - 1); the ring scheme's step counters are cleared.
 cudaError_t launch_tick_add(int64_t* clk, int64_t n, unsigned long long* ctr, bool pdl, cudaStream_t st);
 

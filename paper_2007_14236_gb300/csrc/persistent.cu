@@ -187,7 +187,11 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(PersistArgs a) {
         uint32_t nspk = 0;
         uint4 meta = make_uint4(0, 0, 0, 0);
         if (valid) {
-          St y{a.st0[gid], a.st1[gid], a.st2[gid], a.st3[gid]};
+          St y{a.st0[gid], a.st1[gid], a.st2[gid], a.st3[gid], 0.f, 0.f};
+          if (p.alpha) {
+            y.xe = a.st5[gid];
+            y.xi = a.st6[gid];
+          }
           double h = (double)a.st4[gid];
           if (!a.age) meta = __ldg(a.src_meta + gid);
           const uint64_t i0 = slot * plane + gid;
@@ -200,13 +204,16 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(PersistArgs a) {
             if (p.prec_rcpt == 0) in0 = __fadd_rn(in0, add);
             else in1 = __fadd_rn(in1, add);
           }
-          aeif_integrate(p, y, h, nspk, nsub, cap_hit);
-          y.ge = __fadd_rn(y.ge, in0);
-          y.gi = __fadd_rn(y.gi, in1);
+          if (p.alpha) aeif_step<true>(p, y, h, in0, in1, nspk, nsub, cap_hit);
+          else aeif_step<false>(p, y, h, in0, in1, nspk, nsub, cap_hit);
           a.st0[gid] = y.V;
           a.st1[gid] = y.w;
           a.st2[gid] = y.ge;
           a.st3[gid] = y.gi;
+          if (p.alpha) {
+            a.st5[gid] = y.xe;
+            a.st6[gid] = y.xi;
+          }
           a.st4[gid] = (float)h;
         }
         const uint32_t mult = nspk > 63u ? 63u : nspk;

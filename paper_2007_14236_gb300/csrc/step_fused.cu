@@ -62,11 +62,12 @@ __global__ void __launch_bounds__(kLifBlock) k_step_lif(const __grid_constant__ 
   deliver_block_spikes<WT, kFixed, kLifBlock>(spk, gid, 1u, meta, t, csr, ring, S);
 }
 
-template <bool kFixed, typename WT>
+template <bool kFixed, typename WT, bool kAlpha>
 __global__ void __launch_bounds__(kAeifBlock) k_step_aeif(const __grid_constant__ SegTable<AeifSeg> T,
                                                           const uint32_t* __restrict__ thr, float* __restrict__ V_,
                                                           float* __restrict__ w_, float* __restrict__ ge_,
-                                                          float* __restrict__ gi_, float* __restrict__ h_, Ring ring,
+                                                          float* __restrict__ gi_, float* __restrict__ h_,
+                                                          float* __restrict__ xe_, float* __restrict__ xi_, Ring ring,
                                                           const int64_t* clk, int64_t step_off, const Csr csr,
                                                           SpikeBuf sb) {
   __shared__ uint32_t s_thr[kMaxThr];
@@ -86,7 +87,11 @@ __global__ void __launch_bounds__(kAeifBlock) k_step_aeif(const __grid_constant_
   uint32_t nspk = 0;
   unsigned long long nsub = 0;
   if (valid) {
-    St y{V_[gid], w_[gid], ge_[gid], gi_[gid]};
+    St y{V_[gid], w_[gid], ge_[gid], gi_[gid], 0.f, 0.f};
+    if (kAlpha) {
+      y.xe = xe_[gid];
+      y.xi = xi_[gid];
+    }
     double h = (double)h_[gid];
     const uint64_t slot = (uint64_t)(t & ring.L_mask);
     const uint64_t i0 = (slot * (uint64_t)ring.R) * (uint64_t)ring.N + gid;
@@ -99,14 +104,16 @@ __global__ void __launch_bounds__(kAeifBlock) k_step_aeif(const __grid_constant_
       else in1 = __fadd_rn(in1, add);
     }
     bool cap_hit = false;
-    aeif_integrate(p, y, h, nspk, nsub, cap_hit);
+    aeif_step<kAlpha>(p, y, h, in0, in1, nspk, nsub, cap_hit);
     if (cap_hit) atomicOr(sb.err, kErrSubstepCap);
-    y.ge = __fadd_rn(y.ge, in0);
-    y.gi = __fadd_rn(y.gi, in1);
     V_[gid] = y.V;
     w_[gid] = y.w;
     ge_[gid] = y.ge;
     gi_[gid] = y.gi;
+    if (kAlpha) {
+      xe_[gid] = y.xe;
+      xi_[gid] = y.xi;
+    }
     h_[gid] = (float)h;
   }
 #pragma unroll
@@ -138,10 +145,13 @@ cudaError_t lif_t(const SegTable<LifSeg>& segs, int64_t blocks, const uint32_t* 
 }
 template <bool kFixed, typename WT>
 cudaError_t aeif_t(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V, float* w, float* gex,
-                   float* gin, float* h, Ring ring, const int64_t* clk, int64_t step_off, const Csr& csr,
-                   SpikeBuf sb, bool pdl, cudaStream_t st) {
-  return launch_k(k_step_aeif<kFixed, WT>, dim3((unsigned)blocks), dim3(kAeifBlock), pdl, st, segs, thr, V, w, gex,
-                  gin, h, ring, clk, step_off, csr, sb);
+                   float* gin, float* h, float* xe, float* xi, bool alpha, Ring ring, const int64_t* clk,
+                   int64_t step_off, const Csr& csr, SpikeBuf sb, bool pdl, cudaStream_t st) {
+  if (alpha)
+    return launch_k(k_step_aeif<kFixed, WT, true>, dim3((unsigned)blocks), dim3(kAeifBlock), pdl, st, segs, thr, V, w,
+                    gex, gin, h, xe, xi, ring, clk, step_off, csr, sb);
+  return launch_k(k_step_aeif<kFixed, WT, false>, dim3((unsigned)blocks), dim3(kAeifBlock), pdl, st, segs, thr, V, w,
+                  gex, gin, h, xe, xi, ring, clk, step_off, csr, sb);
 }
 }  // namespace
 
@@ -162,21 +172,20 @@ cudaError_t launch_step_lif(const SegTable<LifSeg>& segs, int64_t blocks, const 
 }
 
 cudaError_t launch_step_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V, float* w,
-                             float* gex, float* gin, float* h, Ring ring, bool fixed, int wdtype, const int64_t* clk,
-                             int64_t step_off, const Csr& csr, SpikeBuf sb, bool pdl, cudaStream_t st) {
+                             float* gex, float* gin, float* h, float* xe, float* xi, bool alpha, Ring ring, bool fixed,
+                             int wdtype, const int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, bool pdl,
+                             cudaStream_t st) {
   if (blocks <= 0) return cudaSuccess;
+#define NGB_A(F, T) return aeif_t<F, T>(segs, blocks, thr, V, w, gex, gin, h, xe, xi, alpha, ring, clk, step_off, csr, sb, pdl, st)
   if (fixed) {
-    if (wdtype == 0)
-      return aeif_t<true, float>(segs, blocks, thr, V, w, gex, gin, h, ring, clk, step_off, csr, sb, pdl, st);
-    if (wdtype == 1)
-      return aeif_t<true, __nv_bfloat16>(segs, blocks, thr, V, w, gex, gin, h, ring, clk, step_off, csr, sb, pdl, st);
-    return aeif_t<true, __half>(segs, blocks, thr, V, w, gex, gin, h, ring, clk, step_off, csr, sb, pdl, st);
+    if (wdtype == 0) NGB_A(true, float);
+    if (wdtype == 1) NGB_A(true, __nv_bfloat16);
+    NGB_A(true, __half);
   }
-  if (wdtype == 0)
-    return aeif_t<false, float>(segs, blocks, thr, V, w, gex, gin, h, ring, clk, step_off, csr, sb, pdl, st);
-  if (wdtype == 1)
-    return aeif_t<false, __nv_bfloat16>(segs, blocks, thr, V, w, gex, gin, h, ring, clk, step_off, csr, sb, pdl, st);
-  return aeif_t<false, __half>(segs, blocks, thr, V, w, gex, gin, h, ring, clk, step_off, csr, sb, pdl, st);
+  if (wdtype == 0) NGB_A(false, float);
+  if (wdtype == 1) NGB_A(false, __nv_bfloat16);
+  NGB_A(false, __half);
+#undef NGB_A
 }
 
 cudaError_t launch_tick_add(int64_t* clk, int64_t n, unsigned long long* ctr, bool pdl, cudaStream_t st) {

@@ -20,11 +20,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "STATE", -3: "OOM", -4: "CUDA", -5: "TIMEOUT", -6: "OVERFLOW"}
 WEIGHT_DTYPES = {"fp32": 0, "bf16": 1, "fp16": 2}
-MODELS = {W.LIF: 0, W.AEIF: 1}
+MODELS = {W.LIF: 0, W.AEIF: 1, W.AEIF_ALPHA: 2}
 RULES = {W.INDEGREE: 0, W.TOTAL: 1, W.OUTDEGREE: 2, W.ONE_TO_ONE: 3, W.ALL_TO_ALL: 4}
 DISTS = {"const": 0, "normal": 1, "uniform": 2}
 DELIVERY = {"auto": 0, "ring": 1, "spike_buffer": 2}
-VARS = {"V_m": 0, "I_syn": 1, "w": 1, "g_ex": 2, "g_in": 3, "refractory": 4, "h": 5}
+VARS = {"V_m": 0, "I_syn": 1, "w": 1, "g_ex": 2, "g_in": 3, "refractory": 4, "h": 5, "dg_ex": 6, "dg_in": 7}
 
 
 class SimConfig(C.Structure):

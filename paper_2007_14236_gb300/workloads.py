@@ -158,6 +158,45 @@ def balanced_lif(n: int = 1000, indegree: int = 100, seed: int = 1, rate_hz: flo
     return spec
 
 
+def paper_balanced(n_ex: int = 8000, ce: int = 800, seed: int = 1, weight_dtype: str = "fp32",
+                   rk_tol: float = 1e-10, rk_control_fp32: bool = False) -> NetSpec:
+    """The paper's balanced network (Sec. 2.3 with its two parameter tables):
+    N_in = N_ex / 4 and CI = CE / 4 (fixed in-degree), AdEx with alpha-function
+    conductances (tau_syn 1 ms on both receptors), V_r = -60 mV, weights
+    0.05 nS (excitatory) and 0.35 nS (inhibitory, receptor 1), delays
+    Normal(0.5, 0.25) ms re-drawn below dt, Poisson drive 20 kHz x 0.37 nS on
+    both populations.  Initial V = E_L, w = 0 (the paper gives none)."""
+    n_in = n_ex // 4
+    ci = ce // 4
+    par = AeifParams(V_reset=-60.0, tau_ex=1.0, tau_in=1.0, rk_tol=rk_tol, rk_control_fp32=rk_control_fp32,
+                     poisson=Poisson(n_inputs=1.0, rate_hz=20000.0, weight=0.37, receptor=0))
+    spec = NetSpec(name="paper_balanced_%d_%d" % (n_ex + n_in, ce + ci), seeds=[seed], weight_dtype=weight_dtype)
+    spec.pops = [Population("E", AEIF_ALPHA, n_ex, par), Population("I", AEIF_ALPHA, n_in, replace(par))]
+    for tgt in (0, 1):
+        spec.conns.append(Connection(0, tgt, INDEGREE, ce, Dist("const", 0.05), Dist("normal", 0.5, 0.25), 0))
+        spec.conns.append(Connection(1, tgt, INDEGREE, ci, Dist("const", 0.35), Dist("normal", 0.5, 0.25), 1))
+    return spec
+
+
+def mixed_net(seed: int = 1, weight_dtype: str = "fp32") -> NetSpec:
+    """LIF, AdEx (exponential conductances) and AdEx (alpha conductances)
+    populations in one network, connected in a loop with an inhibitory
+    pathway: L -> E -> A -> L and L -| A."""
+    lif = LifParams(V_init_mean=-65.0, V_init_sd=5.0, poisson=Poisson(n_inputs=1000.0, rate_hz=8.5, weight=87.8))
+    ex = AeifParams(V_init_sd=3.0, poisson=Poisson(n_inputs=1.0, rate_hz=20000.0, weight=2.5, receptor=0))
+    al = AeifParams(V_reset=-60.0, tau_ex=1.0, tau_in=1.0, V_init_sd=3.0,
+                    poisson=Poisson(n_inputs=1.0, rate_hz=20000.0, weight=0.3, receptor=0))
+    spec = NetSpec(name="mixed_net", seeds=[seed], weight_dtype=weight_dtype)
+    spec.pops = [Population("L", LIF, 400, lif), Population("E", AEIF, 300, ex), Population("A", AEIF_ALPHA, 300, al)]
+    spec.conns = [
+        Connection(0, 1, INDEGREE, 50, Dist("const", 6.0), Dist("const", 1.0), 0),
+        Connection(1, 2, INDEGREE, 50, Dist("const", 0.5), Dist("uniform", 0.5, 1.5), 0),
+        Connection(2, 0, INDEGREE, 40, Dist("const", 60.0), Dist("const", 2.0)),
+        Connection(0, 2, INDEGREE, 30, Dist("const", 1.0), Dist("const", 0.8), 1),
+    ]
+    return spec
+
+
 def rules_net(seed: int = 1, weight_dtype: str = "fp32") -> NetSpec:
     """A small LIF network wired with the rules beyond fixed in-degree / total
     number (Sec. 2.1): one-to-one A -> B, fixed out-degree B -> C, all-to-all

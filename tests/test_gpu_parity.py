@@ -250,6 +250,78 @@ def test_adex_network_matches_fp32_oracle_statistics(ngb, ctl32):
     assert st["rk_substeps"] > 2000 * 2000
 
 
+def test_adex_alpha_single_neuron_vs_fp64_oracle(ngb):
+    """Alpha-function conductances (Sec. 2.3): a neuron driven by a current
+    and by Poisson input through the alpha conductance (identical counts on
+    both sides), GPU (FP32 state) against the FP64 oracle."""
+    par = W.AeifParams(V_reset=-60.0, tau_ex=1.0, tau_in=1.0, I_e=450.0, rk_h_min=1e-9, rk_max_substeps=100000,
+                       poisson=W.Poisson(n_inputs=1.0, rate_hz=20000.0, weight=0.37, receptor=0))
+    spec = W.NetSpec(name="alpha1", seeds=[1], pops=[W.Population("n", W.AEIF_ALPHA, 1, par)])
+    g = ngb.from_spec(spec)
+    g.finalize()
+    o = oracle.OracleNet(spec, adex_fp64=True)
+    o.finalize()
+    steps = 1500
+    Vg, Vo, Gg, Go = (np.zeros(steps) for _ in range(4))
+    for k in range(steps):
+        g.simulate(1)
+        o.simulate(1)
+        Vg[k], Vo[k] = g.state("V_m")[0], o.state("V_m")[0]
+        Gg[k], Go[k] = g.state("g_ex")[0], o.state("g_ex")[0]
+    assert Go.max() > 5.0  # the alpha conductance carries the drive
+    assert np.abs(Gg - Go).max() <= 1e-4 * Go.max()
+    sg, so = g.spikes()[1], o.spikes()[1]
+    assert len(so) >= 3 and len(sg) == len(so)
+    assert np.all(np.abs(sg - so) <= 1)
+    mask = np.ones(steps, dtype=bool)
+    for s_ in so:
+        mask[max(0, s_ - 20):s_ + 2] = False
+    assert np.abs(Vg - Vo)[mask].max() <= 5e-3
+
+
+def test_adex_alpha_network_matches_fp32_oracle_statistics(ngb):
+    """The paper's balanced network at 2,500 neurons, in-degree 250."""
+    spec = W.paper_balanced(n_ex=2000, ce=200, seed=2)
+    g, o = _pair(ngb, spec)
+    for step in range(40):
+        gin = g.input(0, 0).astype(np.float64)
+        _, oabs, oex = o.input(0, 0)
+        assert np.all(np.abs(gin - oex) <= 1e-5 * oabs + 1e-7), step
+        g.simulate(1)
+        o.simulate(1)
+    g.simulate(1960)
+    o.simulate(1960)
+    ng, no = len(g.spikes()[0]), len(o.spikes()[0])
+    assert no > 5000
+    assert abs(ng - no) <= 0.05 * no, (ng, no)
+    gi, gt = g.spikes(t0=0, t1=30)
+    oi, ot = o.spikes()
+    assert np.array_equal(np.sort(gi), np.sort(oi[ot < 30]))
+
+
+def test_mixed_models_match_oracle_statistics(ngb):
+    """LIF, exponential and alpha AdEx populations in one network: per-step
+    inputs on both receptors within the FP32 bound, per-population spike
+    counts within 5 % of the oracle's over 100 ms."""
+    spec = W.mixed_net(seed=2)
+    g, o = _pair(ngb, spec)
+    for step in range(30):
+        for r in (0, 1):
+            gin = g.input(r, 0).astype(np.float64)
+            _, oabs, oex = o.input(r, 0)
+            assert np.all(np.abs(gin - oex) <= 1e-5 * oabs + 1e-7), (step, r)
+        g.simulate(1)
+        o.simulate(1)
+    g.simulate(970)
+    o.simulate(970)
+    gi, oi = g.spikes()[0], o.spikes()[0]
+    bounds = [0, 400, 700, 1000]
+    for p in range(3):
+        ng = np.count_nonzero((gi >= bounds[p]) & (gi < bounds[p + 1]))
+        no = np.count_nonzero((oi >= bounds[p]) & (oi < bounds[p + 1]))
+        assert no > 100 and abs(ng - no) <= 0.05 * no + 10, (p, ng, no)
+
+
 def test_graph_and_eager_paths_identical(ngb):
     spec = W.microcircuit(scale=0.02, seed=9, keep_indegree=False)
     a = ngb.from_spec(spec, deterministic=True)  # default: 100-step graphs

@@ -55,9 +55,11 @@ def _persistent(ngb, spec, **kw):
     return sim
 
 
-@pytest.mark.parametrize("name", ["balanced_lif", "microcircuit", "adex", "batched"])
+@pytest.mark.parametrize("name", ["balanced_lif", "microcircuit", "adex", "batched", "paper_alpha", "mixed"])
 def test_persistent_equals_per_step_kernels(ngb, name):
     spec = {"balanced_lif": lambda: W.balanced_lif(n=1000, indegree=100, seed=1),
+            "mixed": lambda: W.mixed_net(seed=2),
+            "paper_alpha": lambda: W.paper_balanced(n_ex=1600, ce=160, seed=3),
             "microcircuit": lambda: W.microcircuit(scale=0.03, seed=7, keep_indegree=False),
             "adex": lambda: W.balanced_adex(n=2000, indegree=100, seed=2, weight_dtype="fp32", poisson_weight=4.0,
                                             w_ex=2.0, w_in=4.0),
@@ -73,7 +75,7 @@ def test_persistent_equals_per_step_kernels(ngb, name):
     assert np.array_equal(at, bt) and np.array_equal(ai, bi)
     assert np.array_equal(a.state("V_m"), b.state("V_m"))
     assert a.stats()["events"] == b.stats()["events"]
-    if name == "adex":
+    if name in ("adex", "paper_alpha"):
         assert a.stats()["rk_substeps"] == b.stats()["rk_substeps"]
     if name == "balanced_lif":
         o = oracle.OracleNet(spec, deterministic=True)
@@ -121,9 +123,12 @@ def test_barrier_wait_is_bounded(ngb):
     assert ok.stats()["steps"] == 100
 
 
-@pytest.mark.parametrize("name", ["balanced_lif", "microcircuit", "adex", "batched", "mc_bf16"])
+@pytest.mark.parametrize("name", ["balanced_lif", "microcircuit", "adex", "batched", "mc_bf16", "paper_alpha",
+                                  "mixed"])
 def test_fused_equals_per_step_kernels(ngb, name):
     spec = {"balanced_lif": lambda: W.balanced_lif(n=1000, indegree=100, seed=1),
+            "mixed": lambda: W.mixed_net(seed=2),
+            "paper_alpha": lambda: W.paper_balanced(n_ex=1600, ce=160, seed=3),
             "microcircuit": lambda: W.microcircuit(scale=0.03, seed=7, keep_indegree=False),
             "adex": lambda: W.balanced_adex(n=2000, indegree=100, seed=2, weight_dtype="fp32", poisson_weight=4.0,
                                             w_ex=2.0, w_in=4.0),

@@ -54,6 +54,8 @@ SPECS = {
                                     w_ex=2.0, w_in=4.0),
     "batched": lambda: W.batched_microcircuits(n_instances=3, scale_lo=0.02, scale_hi=0.04, seed=7),
     "microcircuit_bf16": lambda: W.microcircuit(scale=0.03, seed=8, keep_indegree=False, weight_dtype="bf16"),
+    "paper_alpha": lambda: W.paper_balanced(n_ex=1600, ce=160, seed=3),
+    "mixed": lambda: W.mixed_net(seed=2),
 }
 
 
@@ -105,7 +107,7 @@ def test_spike_buffer_equals_oracle_deterministic(ngb):
     assert g.stats()["events"] == o.events
 
 
-@pytest.mark.parametrize("name", ["balanced_lif", "adex", "batched"])
+@pytest.mark.parametrize("name", ["balanced_lif", "adex", "batched", "paper_alpha", "mixed"])
 def test_spike_buffer_persistent_equals_per_step(ngb, name):
     spec = SPECS[name]()
     a = _run(ngb, spec, "spike_buffer", steps=(700,))

@@ -271,3 +271,16 @@ def test_rows_for_sources_equal_the_built_csr():
     sel = np.concatenate([np.arange(sp[s], sp[s + 1]) for s in sorted(srcs)])
     for k in ("tgt", "receptor", "weight", "delay"):
         assert np.array_equal(rows[k], csr[k][sel]), k
+
+
+def test_paper_balanced_network_rate_matches_paper():
+    """The paper's balanced network (Sec. 2.3: AdEx with alpha-function
+    conductances, its parameter tables) fires at 30.7 Hz on average; the
+    oracle's steady-state rate at 10,000 neurons and in-degree 1,000 is within
+    10 % of it."""
+    spec = W.paper_balanced(n_ex=8000, ce=800, seed=2)
+    net = _net(spec)
+    net.simulate(2500)
+    ids, st = net.spikes()
+    rate = np.count_nonzero(st >= 1000) / 10000 / 0.15
+    assert abs(rate - 30.7) <= 3.07, rate
