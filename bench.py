@@ -67,7 +67,8 @@ def _args():
     ap.add_argument("--paper-n", type=str, default="1000000",
                     help="neurons of the paper's balanced network (comma-separated for a sweep)")
     ap.add_argument("--paper-ce", type=int, default=800, help="excitatory in-degree of the paper's balanced network")
-    ap.add_argument("--workload", choices=["microcircuit", "small", "batched", "adex", "paper", "serve", "request"],
+    ap.add_argument("--workload", choices=["microcircuit", "small", "batched", "adex", "paper", "serve", "request",
+                                           "precision"],
                     default="microcircuit",
                     help="microcircuit: the benchmark line; batched: 64 microcircuit instances vs the plain path; "
                          "adex: the 1e6-neuron AdEx network; serve: the served request stream")
@@ -401,6 +402,90 @@ def run_paper(a):
     return 0
 
 
+def _pop_stats(ids, steps, spec, t_lo, t_hi):
+    """Per-population mean rate (Hz) and mean CV of inter-spike intervals."""
+    import numpy as np
+    offs = np.cumsum([0] + [p.n for p in spec.pops])
+    m = (steps >= t_lo) & (steps < t_hi)
+    ids, steps = ids[m], steps[m]
+    dur = (t_hi - t_lo) * spec.dt * 1e-3
+    out = []
+    for k in range(len(spec.pops)):
+        sel = (ids >= offs[k]) & (ids < offs[k + 1])
+        rate = np.count_nonzero(sel) / spec.pops[k].n / dur
+        cvs = []
+        pid, pst = ids[sel], steps[sel]
+        order = np.lexsort((pst, pid))
+        pid, pst = pid[order], pst[order]
+        for nrn in np.unique(pid):
+            isi = np.diff(pst[pid == nrn])
+            if len(isi) >= 3:
+                cvs.append(isi.std() / isi.mean())
+        out.append((rate, float(np.mean(cvs)) if cvs else float("nan")))
+    return out
+
+
+def run_precision(a):
+    """Precision report: for each workload family (at a size the oracle
+    finishes in seconds), the per-step synaptic input of the FP32 GPU path
+    against the oracle's FP64 sum (relative to the summed magnitudes of the
+    contributing weights), and per-population rates and CV ISI of the FP32 and
+    BF16-weight GPU runs against the oracle (FP32 weights)."""
+    import numpy as np
+    import oracle
+    from paper_2007_14236_gb300 import ngb, workloads as W
+    cases = {
+        "balanced_lif_1000": lambda wd: W.balanced_lif(n=1000, indegree=100, seed=1, weight_dtype=wd),
+        "microcircuit_0.1": lambda wd: W.microcircuit(scale=0.1, seed=1, weight_dtype=wd),
+        "balanced_adex_20000_driven": lambda wd: W.balanced_adex(n=20000, indegree=1000, seed=1, weight_dtype=wd,
+                                                           poisson_weight=4.0, w_ex=2.0, w_in=4.0),
+        "paper_balanced_10000": lambda wd: W.paper_balanced(n_ex=8000, ce=800, seed=1, weight_dtype=wd),
+    }
+    T, T0 = 3000, 500
+    report = {}
+    for name, mk in cases.items():
+        spec = mk("fp32")
+        g = ngb.from_spec(spec, delivery=a.delivery)
+        g.finalize()
+        o = oracle.OracleNet(spec, track_abs=True)
+        o.finalize()
+        R = 2 if any(p.model != W.LIF for p in spec.pops) else 1
+        err = 0.0
+        for _ in range(20):
+            for r in range(R):
+                gin = g.input(r, 0).astype(np.float64)
+                _, oabs, oex = o.input(r, 0)
+                nz = oabs > 0
+                if np.any(nz):
+                    err = max(err, float(np.max(np.abs(gin[nz] - oex[nz]) / oabs[nz])))
+            g.simulate(1)
+            o.simulate(1)
+        g.simulate(T - 20)
+        o.simulate(T - 20)
+        so = _pop_stats(*o.spikes(), spec, T0, T)
+        sg = _pop_stats(*g.spikes(), spec, T0, T)
+        g.close()
+        bspec = mk("bf16")
+        b = ngb.from_spec(bspec, delivery=a.delivery)
+        b.simulate(T)
+        sb = _pop_stats(*b.spikes(), bspec, T0, T)
+        b.close()
+
+        def rel(x, y):
+            return abs(x - y) / y if y > 0 else (0.0 if x == 0 else float("inf"))
+        report[name] = {
+            "input_rel_error_max_fp32": err,
+            "rates_hz_oracle": [round(x[0], 3) for x in so],
+            "rate_rel_error_max_fp32": max(rel(x[0], y[0]) for x, y in zip(sg, so)),
+            "rate_rel_error_max_bf16": max(rel(x[0], y[0]) for x, y in zip(sb, so)),
+            "cv_isi_abs_error_max_fp32": max(abs(x[1] - y[1]) for x, y in zip(sg, so) if y[1] == y[1]),
+            "cv_isi_abs_error_max_bf16": max(abs(x[1] - y[1]) for x, y in zip(sb, so) if y[1] == y[1]),
+        }
+    print(json.dumps({"workload": "precision_report", "steps": T, "stats_window_steps": [T0, T], "cases": report}),
+          flush=True)
+    return 0
+
+
 def run_small(a):
     """Config 0: the 1,000-neuron balanced LIF network, 100 ms of biological
     time per bench step, beside the oracle on the host for the same 100 ms."""
@@ -502,7 +587,7 @@ def main():
         os.environ["NGB_MODE"] = a.mode  # read by the library when a network is finalised
     if a.workload != "microcircuit":
         return {"small": run_small, "batched": run_batched, "adex": run_adex, "paper": run_paper,
-                "serve": run_serve, "request": run_request}[a.workload](a)
+                "serve": run_serve, "request": run_request, "precision": run_precision}[a.workload](a)
     ws, rank, local = _dist()
     import numpy as np
     import torch

@@ -61,7 +61,7 @@ extern "C" {
 typedef enum { NGB_WEIGHT_FP32 = 0, NGB_WEIGHT_BF16 = 1, NGB_WEIGHT_FP16 = 2 } ngb_weight_dtype;
 /* Neuron models: LIF with exponential PSCs (Eqs. 1-2); AdEx (Eqs. 3-5) with
  * exponential conductances; AdEx with alpha-function conductances (the
- * paper's balanced network, Sec. 2.3: an input of weight W gives
+ * paper's balanced network, Sec. 2.4: an input of weight W gives
  * g(t) = W (t/tau) e^(1 - t/tau), peak W at t = tau). */
 typedef enum { NGB_LIF_PSC_EXP = 0, NGB_AEIF_COND_EXP = 1, NGB_AEIF_COND_ALPHA = 2 } ngb_model;
 typedef enum {

@@ -380,7 +380,7 @@ void generate(const ora_net* net, const Call& c, std::vector<Synapse>& out) {
 // The AdEx system (Eqs. 3-5) with the synaptic conductances as state:
 // y = {V, w, g_ex, g_in, dg_ex, dg_in}.  Exponential conductances (alpha =
 // false): dg/dt = -g / tau, the last two components stay 0.  Alpha-function
-// conductances (the paper's balanced network, Sec. 2.3): g(t) = W (t/tau)
+// conductances (the paper's balanced network, Sec. 2.4): g(t) = W (t/tau)
 // e^(1 - t/tau) after a spike of weight W, generated by dg/dt = x - g/tau,
 // dx/dt = -x/tau with x jumping by W e / tau at the spike.
 constexpr int kAdexN = 6;

@@ -3,7 +3,7 @@
 // fused step kernel and the persistent step kernel.
 //
 // State y = {V, w, g_ex, g_in} for exponential conductances; with
-// alpha-function conductances (the paper's balanced network, Sec. 2.3)
+// alpha-function conductances (the paper's balanced network, Sec. 2.4)
 // also {x_ex, x_in}: g' = x - g/tau, x' = -x/tau, so that an input of weight
 // W (x += W e / tau) gives g(t) = W (t/tau) e^(1 - t/tau).
 //

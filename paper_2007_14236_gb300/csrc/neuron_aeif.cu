@@ -16,7 +16,7 @@
 // join the warp-ballot spike compaction with the spike multiplicity.  In the
 // spike-buffer delivery scheme the kernel that runs first in the step also
 // scans the pending spikes (as the LIF kernel).  kAlpha: alpha-function
-// conductances (the paper's balanced network, Sec. 2.3) with state x_ex, x_in.
+// conductances (the paper's balanced network, Sec. 2.4) with state x_ex, x_in.
 #include "aeif_rk.cuh"
 #include "neuron_step.cuh"
 

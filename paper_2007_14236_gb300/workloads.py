@@ -160,7 +160,7 @@ def balanced_lif(n: int = 1000, indegree: int = 100, seed: int = 1, rate_hz: flo
 
 def paper_balanced(n_ex: int = 8000, ce: int = 800, seed: int = 1, weight_dtype: str = "fp32",
                    rk_tol: float = 1e-10, rk_control_fp32: bool = False) -> NetSpec:
-    """The paper's balanced network (Sec. 2.3 with its two parameter tables):
+    """The paper's balanced network (Sec. 2.4 with its two parameter tables):
     N_in = N_ex / 4 and CI = CE / 4 (fixed in-degree), AdEx with alpha-function
     conductances (tau_syn 1 ms on both receptors), V_r = -60 mV, weights
     0.05 nS (excitatory) and 0.35 nS (inhibitory, receptor 1), delays

@@ -251,7 +251,7 @@ def test_adex_network_matches_fp32_oracle_statistics(ngb, ctl32):
 
 
 def test_adex_alpha_single_neuron_vs_fp64_oracle(ngb):
-    """Alpha-function conductances (Sec. 2.3): a neuron driven by a current
+    """Alpha-function conductances (Sec. 2.4): a neuron driven by a current
     and by Poisson input through the alpha conductance (identical counts on
     both sides), GPU (FP32 state) against the FP64 oracle."""
     par = W.AeifParams(V_reset=-60.0, tau_ex=1.0, tau_in=1.0, I_e=450.0, rk_h_min=1e-9, rk_max_substeps=100000,

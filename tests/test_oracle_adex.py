@@ -13,7 +13,7 @@
   two receptors of the exponential-conductance model): |dV| <= 1e-4 mV.
 * The FP32-state specification stays within the FP32 error budget of the
   FP64 reference on the same trace.
-* Alpha-function conductances (the paper's balanced network, Sec. 2.3): the
+* Alpha-function conductances (the paper's balanced network, Sec. 2.4): the
   conductance after one input of weight W follows W (t/tau) e^(1 - t/tau)
   (peak W at t = tau) at every grid point; the subthreshold response to inputs
   on both receptors and a spiking run match DOP853 on the same six-variable

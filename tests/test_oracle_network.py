@@ -274,7 +274,7 @@ def test_rows_for_sources_equal_the_built_csr():
 
 
 def test_paper_balanced_network_rate_matches_paper():
-    """The paper's balanced network (Sec. 2.3: AdEx with alpha-function
+    """The paper's balanced network (Sec. 2.4: AdEx with alpha-function
     conductances, its parameter tables) fires at 30.7 Hz on average; the
     oracle's steady-state rate at 10,000 neurons and in-degree 1,000 is within
     10 % of it."""
