@@ -356,7 +356,8 @@ def run_paper(a):
     out = []
     for n in sizes:
         n_ex = (n * 4) // 5
-        spec = W.paper_balanced(n_ex=n_ex, ce=a.paper_ce, seed=1, weight_dtype=a.weights)
+        spec = W.paper_balanced(n_ex=n_ex, ce=a.paper_ce, seed=1, weight_dtype=a.weights,
+                                rk_control_fp32=a.adex_ctl32)
         t0 = time.perf_counter()
         sim = ngb.from_spec(spec, drain_steps=a.sim_steps, record_spikes=False, delivery=a.delivery)
         sim.finalize()
@@ -383,6 +384,7 @@ def run_paper(a):
         sim.close()
         out.append(row)
     line = {"workload": "paper_balanced_alpha", "in_degree": a.paper_ce + a.paper_ce // 4, "weights": a.weights,
+            "rk_control": "fp32" if a.adex_ctl32 else "fp64",
             "bio_s_per_size": a.steps * a.sim_steps * 1e-4, "sizes": out,
             "paper": {"s_per_bio_s_1e6_rtx2080ti": 70.0, "rate_hz": 30.7}}
     if not a.no_cpu_baseline:

@@ -62,18 +62,21 @@ __device__ __forceinline__ float ratio_of(float err, float y, float hf, float fl
   return fabsf(err) / (fabsf(y) + fabsf(hf) + fl);
 }
 
-// Integrate y (NC components) over one step of p.dt; h carries the step-size
-// proposal in and out.  Adds the sub-steps to nsub and the spikes to nspk;
-// cap_hit is set when the sub-step cap ended the step early.  CT is the
+// Integrate y (NC components) over the rest of one step of p.dt, from time
+// t_in inside the step after n attempts; h carries the step-size proposal in
+// and out.  Adds the attempts to nsub and the spikes to nspk; cap_hit is set
+// when the attempt cap (p.max_sub) ended the step early.  Returns true when
+// the step is complete, false when `budget` attempts were made in this call
+// first (the caller may resume later from the same y, h, t_in, n: the
+// sequence of attempts is the same as without a budget).  CT is the
 // precision of the step-size control (h, time inside the step, error-ratio
 // test).
 template <typename CT, int NC>
-__device__ __forceinline__ void aeif_integrate_t(const AeifSeg& p, float y[NC], CT& h, uint32_t& nspk,
-                                                 unsigned long long& nsub, bool& cap_hit) {
+__device__ __forceinline__ bool aeif_integrate_t(const AeifSeg& p, float y[NC], CT& h, CT& t_in, int64_t& n,
+                                                 int budget, uint32_t& nspk, unsigned long long& nsub,
+                                                 bool& cap_hit) {
   const CT dt = (CT)p.dt, h_min = (CT)p.h_min;
   if (!(h > (CT)0)) h = dt;
-  CT t_in = (CT)0;
-  int64_t n = 0;  // sub-steps of this step (the cap applies per neuron and step)
   for (;;) {
     const CT rem = dt - t_in;
     bool last = false;
@@ -129,18 +132,26 @@ __device__ __forceinline__ void aeif_integrate_t(const AeifSeg& p, float y[NC], 
       h = h * (CT)grow;
       if (h < h_min) h = h_min;
       if (cap && !last) cap_hit = true;
-      if (last || cap) break;
+      if (last || cap) return true;
       t_in += h_used;
     } else {
       const float shrink = fmaxf(0.1f, 0.9f * exp2f(-0.25f * __log2f(emax * (float)p.inv_tol)));
       h = h * (CT)shrink;
       if (h < h_min) h = h_min;
     }
+    if (--budget == 0) return false;
   }
 }
 
+// Progress of one neuron inside a step: the step-size proposal, the time
+// reached and the attempts made (FP64; FP32 control keeps FP32 values in them).
+struct RkPos {
+  double h, t_in;
+  int64_t n;
+};
+
 template <int NC>
-__device__ __forceinline__ void aeif_integrate_nc(const AeifSeg& p, St& s, double& h, uint32_t& nspk,
+__device__ __forceinline__ bool aeif_integrate_nc(const AeifSeg& p, St& s, RkPos& r, int budget, uint32_t& nspk,
                                                   unsigned long long& nsub, bool& cap_hit) {
   float y[NC];
   y[0] = s.V;
@@ -151,12 +162,14 @@ __device__ __forceinline__ void aeif_integrate_nc(const AeifSeg& p, St& s, doubl
     y[4] = s.xe;
     y[5] = s.xi;
   }
+  bool done;
   if (p.ctl32) {
-    float hf = (float)h;
-    aeif_integrate_t<float, NC>(p, y, hf, nspk, nsub, cap_hit);
-    h = (double)hf;
+    float hf = (float)r.h, tf = (float)r.t_in;
+    done = aeif_integrate_t<float, NC>(p, y, hf, tf, r.n, budget, nspk, nsub, cap_hit);
+    r.h = (double)hf;
+    r.t_in = (double)tf;
   } else {
-    aeif_integrate_t<double, NC>(p, y, h, nspk, nsub, cap_hit);
+    done = aeif_integrate_t<double, NC>(p, y, r.h, r.t_in, r.n, budget, nspk, nsub, cap_hit);
   }
   s.V = y[0];
   s.w = y[1];
@@ -166,24 +179,40 @@ __device__ __forceinline__ void aeif_integrate_nc(const AeifSeg& p, St& s, doubl
     s.xe = y[4];
     s.xi = y[5];
   }
+  return done;
 }
 
-// One AdEx step of neuron state s: integration (FP64 step-size control by
-// default, FP32 when the population asks for it), then the step's input on
-// the two receptors: a conductance jump (exponential), or x += W e / tau
-// (alpha).  kAlpha selects the conductance model at compile time.
+// The step's input on the two receptors, after the integration: a
+// conductance jump (exponential), or x += W e / tau (alpha).
 template <bool kAlpha>
-__device__ __forceinline__ void aeif_step(const AeifSeg& p, St& s, double& h, float in0, float in1, uint32_t& nspk,
-                                          unsigned long long& nsub, bool& cap_hit) {
+__device__ __forceinline__ void aeif_add_input(const AeifSeg& p, St& s, float in0, float in1) {
   if (kAlpha) {
-    aeif_integrate_nc<6>(p, s, h, nspk, nsub, cap_hit);
     s.xe = __fadd_rn(s.xe, __fmul_rn(in0, p.e_tau_ex));
     s.xi = __fadd_rn(s.xi, __fmul_rn(in1, p.e_tau_in));
   } else {
-    aeif_integrate_nc<4>(p, s, h, nspk, nsub, cap_hit);
     s.ge = __fadd_rn(s.ge, in0);
     s.gi = __fadd_rn(s.gi, in1);
   }
+}
+
+// Integrate one AdEx neuron over (the rest of) a step with at most `budget`
+// attempts (0: no limit); on completion the step's input is added.  Returns
+// whether the step is complete.  kAlpha selects the conductance model.
+template <bool kAlpha>
+__device__ __forceinline__ bool aeif_advance(const AeifSeg& p, St& s, RkPos& r, int budget, float in0, float in1,
+                                             uint32_t& nspk, unsigned long long& nsub, bool& cap_hit) {
+  const bool done = aeif_integrate_nc<kAlpha ? 6 : 4>(p, s, r, budget, nspk, nsub, cap_hit);
+  if (done) aeif_add_input<kAlpha>(p, s, in0, in1);
+  return done;
+}
+
+// A whole step (no attempt budget).
+template <bool kAlpha>
+__device__ __forceinline__ void aeif_step(const AeifSeg& p, St& s, double& h, float in0, float in1, uint32_t& nspk,
+                                          unsigned long long& nsub, bool& cap_hit) {
+  RkPos r{h, 0.0, 0};
+  aeif_advance<kAlpha>(p, s, r, 0, in0, in1, nspk, nsub, cap_hit);
+  h = r.h;
 }
 
 }  // namespace ngb

@@ -45,6 +45,10 @@ __global__ void __launch_bounds__(kDeliverBlock) k_deliver(SpikeBuf sb, Csr csr,
     clk[0] = t + 1;        // next step for the update kernels
     sb.ctr[buf ^ 1] = 0;   // the next step's list starts empty
     if (kAge) sb.pcnt[buf] = 0;  // consumed by this step's scan; refilled by step t + 1's
+    if (sb.dcnt) {               // the step's deferred AdEx neurons are all finished
+      sb.dcnt[0] = 0;
+      sb.dcnt[1] = 0;
+    }
   }
   const uint4* __restrict__ wi = buf ? sb.wi[1] : sb.wi[0];
   const uint32_t warp = (blockIdx.x * (uint32_t)kDeliverBlock + threadIdx.x) >> 5;

@@ -29,9 +29,10 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
                                                             float* __restrict__ ge_, float* __restrict__ gi_,
                                                             float* __restrict__ h_, float* __restrict__ xe_,
                                                             float* __restrict__ xi_, Ring ring, int64_t* clk,
-                                                            const Csr csr, SpikeBuf sb, int scan) {
+                                                            const Csr csr, SpikeBuf sb, int scan, int budget) {
   __shared__ uint32_t s_thr[kMaxThr];
-  const AeifSeg p = segment_of(T, (int64_t)blockIdx.x);
+  const int seg = segment_index_of(T, (int64_t)blockIdx.x);
+  const AeifSeg p = T.n <= kInlineSegs ? T.s[seg] : T.dev[seg];
   const int64_t k = ((int64_t)blockIdx.x - p.blk_begin) * kAeifBlock + threadIdx.x;
   const bool valid = k < p.n;
   const uint32_t gid = (uint32_t)(p.offset + k);
@@ -62,6 +63,8 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
                         ((int64_t)gridDim.x * kAeifBlock) >> 5);
   uint32_t nspk = 0;
   unsigned long long nsub = 0;
+  bool done = true;
+  uint4 rec[4];
   if (valid) {
     const uint64_t slot = (uint64_t)(t & ring.L_mask);
     const uint64_t i0 = (slot * (uint64_t)ring.R) * (uint64_t)ring.N + gid;
@@ -73,38 +76,109 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
       if (p.prec_rcpt == 0) in0 = __fadd_rn(in0, add);
       else in1 = __fadd_rn(in1, add);
     }
-    double h = (double)h0;
+    RkPos r{(double)h0, 0.0, 0};
     bool cap_hit = false;
-    aeif_step<kAlpha>(p, y, h, in0, in1, nspk, nsub, cap_hit);
+    done = aeif_advance<kAlpha>(p, y, r, budget, in0, in1, nspk, nsub, cap_hit);
     if (cap_hit) atomicOr(sb.err, kErrSubstepCap);
-    V_[gid] = y.V;
-    w_[gid] = y.w;
-    ge_[gid] = y.ge;
-    gi_[gid] = y.gi;
-    if (kAlpha) {
-      xe_[gid] = y.xe;
-      xi_[gid] = y.xi;
+    if (done) {
+      V_[gid] = y.V;
+      w_[gid] = y.w;
+      ge_[gid] = y.ge;
+      gi_[gid] = y.gi;
+      if (kAlpha) {
+        xe_[gid] = y.xe;
+        xi_[gid] = y.xi;
+      }
+      h_[gid] = (float)r.h;
+    } else {
+      rec[0] = make_uint4(gid, (uint32_t)seg, nspk, (uint32_t)r.n);
+      rec[1] = make_uint4(__float_as_uint(y.V), __float_as_uint(y.w), __float_as_uint(y.ge), __float_as_uint(y.gi));
+      rec[2] = make_uint4(__float_as_uint(y.xe), __float_as_uint(y.xi), __float_as_uint(in0), __float_as_uint(in1));
+      const unsigned long long hb = (unsigned long long)__double_as_longlong(r.h);
+      const unsigned long long tb = (unsigned long long)__double_as_longlong(r.t_in);
+      rec[3] = make_uint4((uint32_t)hb, (uint32_t)(hb >> 32), (uint32_t)tb, (uint32_t)(tb >> 32));
     }
-    h_[gid] = (float)h;
   }
+  defer_write(!done, rec, sb, kAlpha ? 1 : 0);
   // sub-step statistics: one atomic per warp
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nsub += __shfl_xor_sync(0xffffffffu, nsub, o);
   if ((threadIdx.x & 31) == 0 && nsub) atomicAdd(sb.substeps, nsub);
   const uint32_t mult = nspk > 63u ? 63u : nspk;
-  if (kAge) emit_spikes_age(nspk > 0, gid, mult, t, csr, sb);
-  else emit_spikes(nspk > 0, gid, mult, t, meta, sb);
+  if (kAge) emit_spikes_age(done && nspk > 0, gid, mult, t, csr, sb);
+  else emit_spikes(done && nspk > 0, gid, mult, t, meta, sb);
+}
+
+// Second part of the AdEx step: the neurons whose step did not finish within
+// the update kernel's attempt budget (mostly those crossing V_peak, whose
+// step needs tens of attempts) continue from their saved position, packed
+// 32 to a warp, then write their state and join the spike compaction.
+template <bool kFixed, bool kAge, bool kAlpha>
+__global__ void __launch_bounds__(kAeifBlock) k_aeif_finish(const __grid_constant__ SegTable<AeifSeg> T,
+                                                            float* __restrict__ V_, float* __restrict__ w_,
+                                                            float* __restrict__ ge_, float* __restrict__ gi_,
+                                                            float* __restrict__ h_, float* __restrict__ xe_,
+                                                            float* __restrict__ xi_, int64_t* clk, const Csr csr,
+                                                            SpikeBuf sb) {
+  griddep_wait();
+  griddep_launch();
+  const int kind = kAlpha ? 1 : 0;
+  unsigned long long n = sb.dcnt[kind];
+  if (n > (unsigned long long)sb.dfr_cap) n = (unsigned long long)sb.dfr_cap;
+  const int64_t t = clk[0];
+  const uint4* __restrict__ list = sb.dfr[kind];
+  const int lane = threadIdx.x & 31;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * kAeifBlock + threadIdx.x) >> 5;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * kAeifBlock) >> 5;
+  for (unsigned long long base = warp * 32; base < n; base += nwarps * 32) {
+    const unsigned long long i = base + lane;
+    const bool valid = i < n;
+    uint32_t gid = 0, nspk = 0;
+    unsigned long long nsub = 0;
+    uint4 meta = make_uint4(0, 0, 0, 0);
+    if (valid) {
+      const uint4 r0 = list[4 * i], r1 = list[4 * i + 1], r2 = list[4 * i + 2], r3 = list[4 * i + 3];
+      gid = r0.x;
+      const AeifSeg p = T.dev[r0.y];
+      nspk = r0.z;
+      if (!kAge) meta = __ldg(csr.src_meta + gid);
+      St y{__uint_as_float(r1.x), __uint_as_float(r1.y), __uint_as_float(r1.z), __uint_as_float(r1.w),
+           __uint_as_float(r2.x), __uint_as_float(r2.y)};
+      RkPos r{__longlong_as_double((long long)((unsigned long long)r3.x | ((unsigned long long)r3.y << 32))),
+              __longlong_as_double((long long)((unsigned long long)r3.z | ((unsigned long long)r3.w << 32))),
+              (int64_t)r0.w};
+      bool cap_hit = false;
+      aeif_advance<kAlpha>(p, y, r, 0, __uint_as_float(r2.z), __uint_as_float(r2.w), nspk, nsub, cap_hit);
+      if (cap_hit) atomicOr(sb.err, kErrSubstepCap);
+      V_[gid] = y.V;
+      w_[gid] = y.w;
+      ge_[gid] = y.ge;
+      gi_[gid] = y.gi;
+      if (kAlpha) {
+        xe_[gid] = y.xe;
+        xi_[gid] = y.xi;
+      }
+      h_[gid] = (float)r.h;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nsub += __shfl_xor_sync(0xffffffffu, nsub, o);
+    if (lane == 0 && nsub) atomicAdd(sb.substeps, nsub);
+    const uint32_t mult = nspk > 63u ? 63u : nspk;
+    if (kAge) emit_spikes_age(nspk > 0, gid, mult, t, csr, sb);
+    else emit_spikes(nspk > 0, gid, mult, t, meta, sb);
+  }
 }
 
 cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V,
                                float* w, float* gex, float* gin, float* h, float* xe, float* xi, bool alpha,
                                Ring ring, bool fixed, int64_t* clk, const Csr& csr, SpikeBuf sb, bool age, bool scan,
-                               bool pdl, cudaStream_t st) {
+                               int budget, bool pdl, cudaStream_t st) {
   if (blocks <= 0) return cudaSuccess;
   const dim3 g((unsigned)blocks), b(kAeifBlock);
   const int sc = scan ? 1 : 0;
-#define NGB_AEIF(F, A, P) \
-  return launch_k(k_update_aeif<F, A, P>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, xe, xi, ring, clk, csr, sb, sc)
+#define NGB_AEIF(F, A, P)                                                                                         \
+  return launch_k(k_update_aeif<F, A, P>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, xe, xi, ring, clk, csr, sb, \
+                  sc, budget)
   if (alpha) {
     if (fixed) {
       if (age) NGB_AEIF(true, true, true);
@@ -120,6 +194,28 @@ cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, co
   if (age) NGB_AEIF(false, true, false);
   NGB_AEIF(false, false, false);
 #undef NGB_AEIF
+}
+
+cudaError_t launch_finish_aeif(const SegTable<AeifSeg>& segs, int grid, float* V, float* w, float* gex, float* gin,
+                               float* h, float* xe, float* xi, bool alpha, bool fixed, int64_t* clk, const Csr& csr,
+                               SpikeBuf sb, bool age, bool pdl, cudaStream_t st) {
+  const dim3 g((unsigned)grid), b(kAeifBlock);
+#define NGB_FIN(F, A, P) return launch_k(k_aeif_finish<F, A, P>, g, b, pdl, st, segs, V, w, gex, gin, h, xe, xi, clk, csr, sb)
+  if (alpha) {
+    if (fixed) {
+      if (age) NGB_FIN(true, true, true);
+      NGB_FIN(true, false, true);
+    }
+    if (age) NGB_FIN(false, true, true);
+    NGB_FIN(false, false, true);
+  }
+  if (fixed) {
+    if (age) NGB_FIN(true, true, false);
+    NGB_FIN(true, false, false);
+  }
+  if (age) NGB_FIN(false, true, false);
+  NGB_FIN(false, false, false);
+#undef NGB_FIN
 }
 
 }  // namespace ngb

@@ -153,7 +153,7 @@ uint64_t call_synapses(const ngb_conn_spec& c, int64_t ns, int64_t nt, bool same
   }
 }
 
-constexpr int kCounters = 8;  // device counter words: ctr[2], events, substeps, rec_count, spare, pcnt[2]
+constexpr int kCounters = 10;  // device counter words: ctr[2], events, substeps, rec_count, spare, pcnt[2], dcnt[2]
 
 uint64_t next_pow2(uint64_t x) {
   uint64_t p = 1;
@@ -215,6 +215,7 @@ struct ngb_sim {
   int n_aeif = 0;                 // AdEx segments of both kinds
   int n_aeif_exp = 0, n_aeif_alpha = 0;
   int64_t aeif_blocks = 0, aeifa_blocks = 0;
+  int aeif_budget = 8;  // RK attempts per neuron in the AdEx update kernel before deferral (0: none)
   uint32_t* thr = nullptr;
   int deliver_grid = 0;
   bool pdl = true;  // programmatic dependent launch between the step's kernels
@@ -277,16 +278,28 @@ cudaError_t launch_lif(ngb_sim* s) {
 }
 
 // AdEx update kernels: exponential-conductance segments, then alpha ones.
+// Each kind is an update kernel with an attempt budget, then the kernel that
+// finishes the deferred neurons.
 cudaError_t launch_aeif(ngb_sim* s) {
   cudaError_t e = cudaSuccess;
-  if (s->n_aeif_exp)
+  const bool det = s->cfg.deterministic != 0, age = s->scheme == 2;
+  const int fin_grid = std::max(1, s->sms) * 4;
+  if (s->n_aeif_exp) {
     e = launch_update_aeif(s->aeif_tab, s->aeif_blocks, s->thr, s->st0, s->st1, s->st2, s->st3, s->st4, s->st5,
-                           s->st6, false, ring_of(s), s->cfg.deterministic != 0, s->clk, csr_of(s), s->sb,
-                           s->scheme == 2, s->n_lif == 0, s->pdl, s->stream);
-  if (e == cudaSuccess && s->n_aeif_alpha)
+                           s->st6, false, ring_of(s), det, s->clk, csr_of(s), s->sb, age, s->n_lif == 0,
+                           s->aeif_budget, s->pdl, s->stream);
+    if (e == cudaSuccess && s->aeif_budget > 0)
+      e = launch_finish_aeif(s->aeif_tab, fin_grid, s->st0, s->st1, s->st2, s->st3, s->st4, s->st5, s->st6, false,
+                             det, s->clk, csr_of(s), s->sb, age, s->pdl, s->stream);
+  }
+  if (e == cudaSuccess && s->n_aeif_alpha) {
     e = launch_update_aeif(s->aeifa_tab, s->aeifa_blocks, s->thr, s->st0, s->st1, s->st2, s->st3, s->st4, s->st5,
-                           s->st6, true, ring_of(s), s->cfg.deterministic != 0, s->clk, csr_of(s), s->sb,
-                           s->scheme == 2, s->n_lif == 0 && s->n_aeif_exp == 0, s->pdl, s->stream);
+                           s->st6, true, ring_of(s), det, s->clk, csr_of(s), s->sb, age,
+                           s->n_lif == 0 && s->n_aeif_exp == 0, s->aeif_budget, s->pdl, s->stream);
+    if (e == cudaSuccess && s->aeif_budget > 0)
+      e = launch_finish_aeif(s->aeifa_tab, fin_grid, s->st0, s->st1, s->st2, s->st3, s->st4, s->st5, s->st6, true,
+                             det, s->clk, csr_of(s), s->sb, age, s->pdl, s->stream);
+  }
   return e;
 }
 
@@ -945,6 +958,12 @@ int finalize_impl(ngb_sim* s) {
     CK(s->dalloc(&s->st4, N));
     CK(s->dalloc(&s->st5, N));
     CK(s->dalloc(&s->st6, N));
+    // AdEx neurons deferred to the finishing kernel: one 64-byte record per neuron and conductance model
+    CK(s->dalloc(&s->sb.dfr[0], 4 * (size_t)N));
+    CK(s->dalloc(&s->sb.dfr[1], 4 * (size_t)N));
+    s->sb.dfr_cap = N;
+    const char* env_budget = std::getenv("NGB_AEIF_BUDGET");
+    if (env_budget) s->aeif_budget = std::max(0, std::atoi(env_budget));
     CK(cudaMemsetAsync(s->st5, 0, N * sizeof(float), st));
     CK(cudaMemsetAsync(s->st6, 0, N * sizeof(float), st));
     CK(cudaMemsetAsync(s->st2, 0, N * sizeof(float), st));
@@ -977,6 +996,7 @@ int finalize_impl(ngb_sim* s) {
   s->sb.substeps = ctrs + 3;
   s->sb.rec_count = ctrs + 4;
   s->sb.pcnt = ctrs + 6;
+  s->sb.dcnt = ctrs + 8;
   CK(s->dalloc(&s->sb.err, 1));
   CK(cudaMemsetAsync(s->sb.err, 0, sizeof(uint32_t), st));
   CK(s->dalloc(&s->clk, 2));

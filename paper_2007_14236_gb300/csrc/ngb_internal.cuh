@@ -117,6 +117,12 @@ struct SpikeBuf {
   unsigned long long* pcnt;         // [2] pending-list lengths
   int64_t pend_cap;                 // entries per pending list
   int64_t wi_cap;                   // uint4 entries per work-item / due-item list
+  // AdEx neurons whose step did not finish within the update kernel's attempt
+  // budget (by conductance model: 0 exponential, 1 alpha), finished by a second
+  // kernel with the neurons packed into full warps
+  uint4* dfr[2];                    // 4 uint4 per neuron
+  unsigned long long* dcnt;         // [2]
+  int64_t dfr_cap;                  // neurons per list
 };
 
 struct Csr {
@@ -368,6 +374,33 @@ __device__ __forceinline__ void scan_pending(int64_t t, const Csr& csr, const Sp
   }
 }
 
+// Warp-aggregated append of the 4-entry records of the lanes whose AdEx step
+// is unfinished (d) to deferred list `kind`.  Every lane of the warp must
+// call it.  The list holds one record per neuron, each neuron is deferred at
+// most once per step, so a position beyond the capacity is an internal error
+// (flagged, record dropped).
+__device__ __forceinline__ void defer_write(bool d, const uint4 rec[4], const SpikeBuf& sb, int kind) {
+  const unsigned full = 0xffffffffu;
+  const unsigned b = __ballot_sync(full, d);
+  if (b == 0) return;
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(sb.dcnt + kind, (unsigned long long)__popc(b));
+  base = __shfl_sync(full, base, 0);
+  if (d) {
+    const unsigned long long pos = base + __popc(b & ((1u << lane) - 1u));
+    if (pos < (unsigned long long)sb.dfr_cap) {
+      uint4* q = sb.dfr[kind] + 4 * pos;
+      q[0] = rec[0];
+      q[1] = rec[1];
+      q[2] = rec[2];
+      q[3] = rec[3];
+    } else {
+      atomicOr(sb.err, kErrPendingOverflow);
+    }
+  }
+}
+
 // Programmatic dependent launch (sm_90+): a kernel launched with the
 // programmatic-serialisation attribute may start while its predecessor in
 // the stream finishes; griddep_wait() blocks until the predecessor grid has
@@ -390,6 +423,20 @@ struct SegTable {
 // The segment owning block `blk`: binary search over blk_begin in the inline
 // copy (constant bank) or, for long tables (batched instances), the block's
 // entry of the per-block segment table.
+template <typename Seg>
+__device__ __forceinline__ int segment_index_of(const SegTable<Seg>& T, int64_t blk) {
+  if (T.n <= kInlineSegs) {
+    int lo = 0, hi = T.n;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (T.s[mid].blk_begin <= blk) lo = mid;
+      else hi = mid;
+    }
+    return lo;
+  }
+  return (int)__ldg(T.blk_seg + blk);
+}
+
 template <typename Seg>
 __device__ __forceinline__ Seg segment_of(const SegTable<Seg>& T, int64_t blk) {
   int lo = 0, hi = T.n;
@@ -438,10 +485,15 @@ cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, int 
                               float* I, int32_t* ref, Ring ring, bool fixed, int64_t* clk, const Csr& csr,
                               SpikeBuf sb, bool age, bool scan, bool pdl, cudaStream_t st);
 // alpha: the segments have alpha-function conductances (x_ex, x_in in xe, xi).
+// budget > 0: at most `budget` RK attempts per neuron in this kernel; the
+// unfinished neurons are completed by launch_finish_aeif (same arithmetic).
 cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V,
                                float* w, float* gex, float* gin, float* h, float* xe, float* xi, bool alpha,
                                Ring ring, bool fixed, int64_t* clk, const Csr& csr, SpikeBuf sb, bool age, bool scan,
-                               bool pdl, cudaStream_t st);
+                               int budget, bool pdl, cudaStream_t st);
+cudaError_t launch_finish_aeif(const SegTable<AeifSeg>& segs, int grid, float* V, float* w, float* gex, float* gin,
+                               float* h, float* xe, float* xi, bool alpha, bool fixed, int64_t* clk, const Csr& csr,
+                               SpikeBuf sb, bool age, bool pdl, cudaStream_t st);
 cudaError_t launch_tick(int64_t* clk, bool pdl, cudaStream_t st);
 cudaError_t persistent_max_blocks_per_sm(bool fixed, int wdtype, bool lif, bool aeif, size_t smem, int* out);
 cudaError_t launch_persistent(const PersistArgs& a, bool fixed, int wdtype, bool lif, bool aeif, int grid,

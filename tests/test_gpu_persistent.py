@@ -171,3 +171,34 @@ def test_four_neurons_per_thread_equal_one(ngb, delivery):
     assert np.array_equal(a.state("V_m"), b.state("V_m"))
     assert np.array_equal(a.state("I_syn"), b.state("I_syn"))
     assert a.stats()["events"] == b.stats()["events"]
+
+
+@pytest.mark.parametrize("name", ["adex", "paper_alpha", "mixed"])
+def test_aeif_attempt_budget_does_not_change_results(ngb, name):
+    """AdEx neurons not finished within the update kernel's attempt budget
+    continue in a second kernel from their saved position: budgets 0 (no
+    deferral), 1 (nearly every neuron deferred) and 8 give bit-identical runs,
+    and so do the persistent and fused loops, which never defer."""
+    spec = {"adex": lambda: W.balanced_adex(n=2000, indegree=100, seed=2, weight_dtype="fp32", poisson_weight=4.0,
+                                            w_ex=2.0, w_in=4.0),
+            "paper_alpha": lambda: W.paper_balanced(n_ex=1600, ce=160, seed=3),
+            "mixed": lambda: W.mixed_net(seed=2)}[name]()
+    runs = []
+    for env in ({"NGB_AEIF_BUDGET": 0}, {"NGB_AEIF_BUDGET": 1}, {"NGB_AEIF_BUDGET": 8},
+                {"NGB_MODE": "persistent"}, {"NGB_MODE": "fused"}):
+        with _env(**env):
+            sim = ngb.from_spec(spec, deterministic=True, delivery="ring", drain_steps=250)
+            sim.finalize()
+        sim.simulate(300)
+        sim.simulate(300)
+        runs.append(sim)
+    a = runs[0]
+    ai, at = a.spikes()
+    assert len(ai) > 100
+    for b in runs[1:]:
+        bi, bt = b.spikes()
+        assert np.array_equal(at, bt) and np.array_equal(ai, bi)
+        for var in ("V_m", "w", "g_ex", "g_in", "h"):
+            assert np.array_equal(a.state(var), b.state(var)), var
+        assert a.stats()["rk_substeps"] == b.stats()["rk_substeps"]
+        assert a.stats()["events"] == b.stats()["events"]
