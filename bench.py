@@ -68,7 +68,7 @@ def _args():
                     help="neurons of the paper's balanced network (comma-separated for a sweep)")
     ap.add_argument("--paper-ce", type=int, default=800, help="excitatory in-degree of the paper's balanced network")
     ap.add_argument("--workload", choices=["microcircuit", "small", "batched", "adex", "paper", "serve", "request",
-                                           "precision"],
+                                           "precision", "validate"],
                     default="microcircuit",
                     help="microcircuit: the benchmark line; batched: 64 microcircuit instances vs the plain path; "
                          "adex: the 1e6-neuron AdEx network; serve: the served request stream")
@@ -488,6 +488,37 @@ def run_precision(a):
     return 0
 
 
+def run_validate(a):
+    """The paper's equivalence test (Sec. 3.1) with the oracle in the
+    reference simulator's role: the microcircuit at a reduced scale simulated
+    with several seeds on the GPU and by the oracle; per population, the KL
+    divergences of the smoothed firing-rate, CV ISI and correlation
+    distributions for GPU-oracle pairs and for oracle-oracle pairs (different
+    seeds in every pair)."""
+    import numpy as np
+    import oracle
+    from paper_2007_14236_gb300 import ngb, validate as V, workloads as W
+    n_seeds, T, T0 = 4, 11_000, 1_000  # 1.1 s, the first 0.1 s discarded
+    gpu_stats, ora_stats = [], []
+    for seed in range(1, n_seeds + 1):
+        spec = W.microcircuit(scale=a.scale if a.scale != 1.0 else 0.1, seed=seed, weight_dtype=a.weights)
+        bounds = np.cumsum([0] + [p.n for p in spec.pops])
+        g = ngb.from_spec(spec, delivery=a.delivery, record_capacity=8_000_000, drain_steps=T)
+        g.simulate(T)
+        gpu_stats.append(V.population_statistics(*g.spikes(), bounds, T0, T, spec.dt))
+        g.close()
+        o = oracle.OracleNet(spec)
+        o.finalize()
+        o.simulate(T)
+        ora_stats.append(V.population_statistics(*o.spikes(), bounds, T0, T, spec.dt))
+    go = [V.compare(gpu_stats[i], ora_stats[(i + 1) % n_seeds]) for i in range(n_seeds)]
+    oo = [V.compare(ora_stats[i], ora_stats[(i + 1) % n_seeds]) for i in range(n_seeds)]
+    print(json.dumps({"workload": "validation_microcircuit", "scale": a.scale if a.scale != 1.0 else 0.1,
+                      "seeds": n_seeds, "bio_s": T * 1e-4, "discarded_s": T0 * 1e-4, "populations": W.MC_NAMES,
+                      "kl_gpu_vs_oracle": V.mean_std(go), "kl_oracle_vs_oracle": V.mean_std(oo)}), flush=True)
+    return 0
+
+
 def run_small(a):
     """Config 0: the 1,000-neuron balanced LIF network, 100 ms of biological
     time per bench step, beside the oracle on the host for the same 100 ms."""
@@ -589,7 +620,8 @@ def main():
         os.environ["NGB_MODE"] = a.mode  # read by the library when a network is finalised
     if a.workload != "microcircuit":
         return {"small": run_small, "batched": run_batched, "adex": run_adex, "paper": run_paper,
-                "serve": run_serve, "request": run_request, "precision": run_precision}[a.workload](a)
+                "serve": run_serve, "request": run_request, "precision": run_precision,
+                "validate": run_validate}[a.workload](a)
     ws, rank, local = _dist()
     import numpy as np
     import torch
