@@ -197,7 +197,8 @@ typedef struct {
   int64_t ring_slots;   /* L, a power of two > max delay in steps */
   int64_t max_delay_steps;
   int64_t device_bytes; /* device memory held by the handle */
-  int64_t mode;         /* step loop: 0 per-step kernels in CUDA graphs, 1 persistent step kernel, 2 fused update + delivery */
+  int64_t mode;         /* step loop: 0 per-step kernels in CUDA graphs, 1 persistent step kernel, 2 fused
+                           update + delivery, 3 pipelined (delivery of step t beside the update of t + 1) */
   int64_t launch_grid;  /* blocks of the delivery kernel (mode 0) or of the persistent kernel (mode 1) */
   int64_t delivery;     /* delivery scheme in use: 1 ring, 2 spike buffer */
 } ngb_stats;
@@ -283,7 +284,11 @@ NGB_API int ngb_simulate(ngb_sim* sim, int64_t steps);
 NGB_API int ngb_simulate_profiled(ngb_sim* sim, int64_t steps, double* kernel_ms, int64_t* launches);
 
 /* Autotune the step loop on this network: the per-step kernels in CUDA
- * graphs with the delivery kernel at 1, 2, 4 or 8 blocks per SM; the fused
+ * graphs with the delivery kernel at 1, 2, 4 or 8 blocks per SM; the
+ * pipelined loop (ring scheme: a spike's delay-1 group delivered by the
+ * update kernel at once, its other groups by a delivery kernel that runs
+ * beside the next step's update, in two-stream CUDA graphs) at the same
+ * delivery grids; the fused
  * loop (ring scheme: each update block delivers its own spikes, one launch
  * per step and model, in CUDA graphs); and the persistent step kernel (one
  * cooperative launch for many steps, grid barriers between its phases) at
@@ -295,8 +300,8 @@ NGB_API int ngb_simulate_profiled(ngb_sim* sim, int64_t steps, double* kernel_ms
  * environment variable NGB_AUTOTUNE_CACHE naming a file, results are looked up
  * and appended there per (GPU, network shape) key.  *deliver_grid_out (may be
  * NULL) receives the chosen grid.  The environment variable NGB_MODE
- * ("persistent" or "fused") selects that step loop at finalisation without
- * tuning. */
+ * ("persistent", "fused" or "pipelined") selects that step loop at
+ * finalisation without tuning. */
 NGB_API int ngb_autotune(ngb_sim* sim, int64_t trial_steps, int32_t* deliver_grid_out);
 
 /* Spikes recorded in steps [t0_step, t1_step) of population `pop` (-1 = all,

@@ -21,7 +21,13 @@
 // L2 atomic per synapse, plus 32 bytes of work-item entry and 10 bytes per
 // delay group of the source per work item.
 //
-// Spike-buffer scheme (kAge): the step's list holds due items (one uint4 per
+// Pipelined ring scheme (kEmitPipe): the list of step t = clk[0] + step_off
+// (by t mod 3) holds the work items of the spikes' groups with delay >= 2,
+// delivered beside the update of step t + 1; the clock is not advanced here
+// and the list of step t + 2 is emptied (its last reader, the delivery of
+// step t - 1, ran before this one).
+//
+// Spike-buffer scheme (kEmitAge): the step's list holds due items (one uint4 per
 // <= 1024 synapses of one connection group, written by the update kernel's
 // pending-spike scan); every synapse goes to the single ring slot, the
 // input of step t + 1.  The kernel also empties the pending list that the
@@ -31,10 +37,25 @@
 
 namespace ngb {
 
-template <typename WT, bool kFixed, bool kAge>
-__global__ void __launch_bounds__(kDeliverBlock) k_deliver(SpikeBuf sb, Csr csr, Ring ring, int64_t* clk) {
+template <typename WT, bool kFixed, int kMode>
+__global__ void __launch_bounds__(kDeliverBlock) k_deliver(SpikeBuf sb, Csr csr, Ring ring, int64_t* clk,
+                                                           int64_t step_off) {
+  constexpr bool kAge = kMode == kEmitAge;
   griddep_wait();    // the step's update kernels have completed
   griddep_launch();  // the next step's update may start its prologue
+  const uint32_t warp = (blockIdx.x * (uint32_t)kDeliverBlock + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * (uint32_t)kDeliverBlock) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (kMode == kEmitPipe) {
+    const int64_t tp = clk[0] + step_off;
+    const int q = (int)(tp % 3);
+    const uint32_t n = (uint32_t)(sb.ctr3[q] & kChunkMask);
+    if (blockIdx.x == 0 && threadIdx.x == 0) sb.ctr3[(int)((tp + 2) % 3)] = 0;
+    const uint4* __restrict__ wq = sb.wi3[q];
+    for (uint32_t ch = warp; ch < n; ch += nwarps)
+      deliver_work_item<WT, kFixed>(wq[2 * (uint64_t)ch], wq[2 * (uint64_t)ch + 1], tp, csr, ring, lane);
+    return;
+  }
   // both parities' counters are read together with the step counter (one round trip)
   const unsigned long long c0 = sb.ctr[0], c1 = sb.ctr[1];
   const int64_t t = clk[1];
@@ -45,15 +66,8 @@ __global__ void __launch_bounds__(kDeliverBlock) k_deliver(SpikeBuf sb, Csr csr,
     clk[0] = t + 1;        // next step for the update kernels
     sb.ctr[buf ^ 1] = 0;   // the next step's list starts empty
     if (kAge) sb.pcnt[buf] = 0;  // consumed by this step's scan; refilled by step t + 1's
-    if (sb.dcnt) {               // the step's deferred AdEx neurons are all finished
-      sb.dcnt[0] = 0;
-      sb.dcnt[1] = 0;
-    }
   }
   const uint4* __restrict__ wi = buf ? sb.wi[1] : sb.wi[0];
-  const uint32_t warp = (blockIdx.x * (uint32_t)kDeliverBlock + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * (uint32_t)kDeliverBlock) >> 5;
-  const int lane = threadIdx.x & 31;
   if (kAge) {
     if ((unsigned long long)nch > (unsigned long long)sb.wi_cap) nch = (uint32_t)sb.wi_cap;
     for (uint32_t it = warp; it < nch; it += nwarps) deliver_due_item<WT, kFixed>(wi[it], csr, ring, lane);
@@ -67,24 +81,27 @@ __global__ void __launch_bounds__(kDeliverBlock) k_deliver(SpikeBuf sb, Csr csr,
 
 namespace {
 template <typename WT, bool kFixed>
-cudaError_t launch_deliver_t(SpikeBuf sb, Csr csr, Ring ring, bool age, int64_t* clk, int grid, bool pdl,
-                             cudaStream_t st) {
+cudaError_t launch_deliver_t(SpikeBuf sb, Csr csr, Ring ring, int emit, int64_t* clk, int64_t step_off, int grid,
+                             bool pdl, cudaStream_t st) {
   const dim3 g((unsigned)grid), b(kDeliverBlock);
-  if (age) return launch_k(k_deliver<WT, kFixed, true>, g, b, pdl, st, sb, csr, ring, clk);
-  return launch_k(k_deliver<WT, kFixed, false>, g, b, pdl, st, sb, csr, ring, clk);
+  if (emit == kEmitAge) return launch_k(k_deliver<WT, kFixed, kEmitAge>, g, b, pdl, st, sb, csr, ring, clk, step_off);
+  if (emit == kEmitPipe) return launch_k(k_deliver<WT, kFixed, kEmitPipe>, g, b, pdl, st, sb, csr, ring, clk, step_off);
+  return launch_k(k_deliver<WT, kFixed, kEmitRing>, g, b, pdl, st, sb, csr, ring, clk, step_off);
 }
 }  // namespace
 
-cudaError_t launch_deliver(SpikeBuf sb, Csr csr, int wdtype, Ring ring, bool fixed, bool age, int64_t* clk,
-                           int grid, bool pdl, cudaStream_t st) {
+cudaError_t launch_deliver(SpikeBuf sb, Csr csr, int wdtype, Ring ring, bool fixed, int emit, int64_t* clk,
+                           int64_t step_off, int grid, bool pdl, cudaStream_t st) {
+#define NGB_DEL(T, F) return launch_deliver_t<T, F>(sb, csr, ring, emit, clk, step_off, grid, pdl, st)
   if (fixed) {
-    if (wdtype == 0) return launch_deliver_t<float, true>(sb, csr, ring, age, clk, grid, pdl, st);
-    if (wdtype == 1) return launch_deliver_t<__nv_bfloat16, true>(sb, csr, ring, age, clk, grid, pdl, st);
-    return launch_deliver_t<__half, true>(sb, csr, ring, age, clk, grid, pdl, st);
+    if (wdtype == 0) NGB_DEL(float, true);
+    if (wdtype == 1) NGB_DEL(__nv_bfloat16, true);
+    NGB_DEL(__half, true);
   }
-  if (wdtype == 0) return launch_deliver_t<float, false>(sb, csr, ring, age, clk, grid, pdl, st);
-  if (wdtype == 1) return launch_deliver_t<__nv_bfloat16, false>(sb, csr, ring, age, clk, grid, pdl, st);
-  return launch_deliver_t<__half, false>(sb, csr, ring, age, clk, grid, pdl, st);
+  if (wdtype == 0) NGB_DEL(float, false);
+  if (wdtype == 1) NGB_DEL(__nv_bfloat16, false);
+  NGB_DEL(__half, false);
+#undef NGB_DEL
 }
 
 // ------------------------------------------------------------------ retirement

@@ -144,6 +144,83 @@ __device__ __forceinline__ void deliver_work_item(const uint4 a, const uint4 m2,
   }
 }
 
+// deliver_work_item with the weight storage chosen at run time (a warp-uniform branch).
+template <bool kFixed>
+__device__ __forceinline__ void deliver_work_item_rt(int wdtype, const uint4 a, const uint4 m2, const int64_t t,
+                                                     const Csr& csr, const Ring& ring, const int lane) {
+  if (wdtype == 1) deliver_work_item<__nv_bfloat16, kFixed>(a, m2, t, csr, ring, lane);
+  else if (wdtype == 2) deliver_work_item<__half, kFixed>(a, m2, t, csr, ring, lane);
+  else deliver_work_item<float, kFixed>(a, m2, t, csr, ring, lane);
+}
+
+// New spikes of step t in the pipelined ring scheme.  A source's first
+// connection group, when its delay is one step, is delivered by this warp at
+// once (into slot t + 1, which the next step's update reads); the source's
+// other groups become work items of the list of step t mod 3, delivered by a
+// kernel that may run beside the next step's update because their slots are
+// t + 2 and later.  Spike record and event count as in the other schemes.
+// Every lane of the warp must call it.
+template <bool kFixed>
+__device__ __forceinline__ void emit_spikes_pipe(bool spk, uint32_t gid, uint32_t mult, int64_t t, uint4 meta,
+                                                 const Csr& csr, const Ring& ring, const SpikeBuf& sb) {
+  const unsigned full = 0xffffffffu;
+  const unsigned ball = __ballot_sync(full, spk);
+  if (ball == 0) return;
+  const int lane = threadIdx.x & 31;
+  record_spikes(spk, gid, mult, t, spk ? (unsigned long long)meta.z * mult : 0ull, sb);
+  const uint32_t ngrp = meta.y >> 16;
+  uint2 ag = make_uint2(0, 0);
+  if (spk && ngrp > 0) ag = __ldg(csr.src_age + gid);
+  const bool local = spk && ngrp > 0 && (ag.y & 0xFFFFu) == 1u;
+  const uint64_t b = (uint64_t)meta.x | ((uint64_t)(meta.y & 0xFFFFu) << 32);
+  uint4 rest = meta;
+  if (local) {
+    const uint64_t b2 = b + ag.x;
+    rest = make_uint4((uint32_t)b2, (uint32_t)((b2 >> 32) & 0xFFFFu) | ((ngrp - 1u) << 16), meta.z - ag.x,
+                      meta.w + 1u);
+  }
+  // work items of the remaining groups
+  uint32_t nch = 0;
+  if (spk && rest.z > 0) {
+    const uint64_t rb = (uint64_t)rest.x | ((uint64_t)(rest.y & 0xFFFFu) << 32);
+    nch = (uint32_t)((rb + rest.z - (rb & ~3ull) + kChunk - 1) / kChunk);
+  }
+  uint32_t inc = nch;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t x = __shfl_up_sync(full, inc, o);
+    if (lane >= o) inc += x;
+  }
+  const uint32_t tot = __shfl_sync(full, inc, 31);
+  const int q = (int)(t % 3);
+  unsigned long long base = 0;
+  if (lane == 0 && tot) base = atomicAdd(sb.ctr3 + q, (unsigned long long)tot);
+  base = __shfl_sync(full, base, 0);
+  const uint32_t word = gid | (mult << kIdBits);
+  if (nch) {
+    uint4* const wi = sb.wi3[q];
+    const unsigned long long first = base + inc - nch;
+    for (uint32_t c = 0; c < nch; ++c) {
+      wi[2 * (first + c)] = make_uint4(word, c, rest.x, rest.y);
+      wi[2 * (first + c) + 1] = make_uint4(rest.z, rest.w, 0u, 0u);
+    }
+  }
+  // the delay-1 groups, one spiking lane at a time, by the whole warp
+  for (unsigned lm = __ballot_sync(full, local); lm; lm &= lm - 1) {
+    const int l = __ffs(lm) - 1;
+    const uint32_t wl = __shfl_sync(full, word, l);
+    const uint32_t bx = __shfl_sync(full, meta.x, l);
+    const uint32_t by = __shfl_sync(full, meta.y & 0xFFFFu, l);
+    const uint32_t n0 = __shfl_sync(full, ag.x, l);
+    const uint32_t g0 = __shfl_sync(full, meta.w, l);
+    const uint64_t bb = (uint64_t)bx | ((uint64_t)by << 32);
+    const uint32_t nc = (uint32_t)((bb + n0 - (bb & ~3ull) + kChunk - 1) / kChunk);
+    for (uint32_t c = 0; c < nc; ++c)
+      deliver_work_item_rt<kFixed>(csr.wdtype, make_uint4(wl, c, bx, by | (1u << 16)), make_uint4(n0, g0, 0u, 0u), t,
+                                   csr, ring, lane);
+  }
+}
+
 // The spikes of one thread block, delivered by that block (fused step loop).
 template <int kBlock>
 struct BlockSpikes {

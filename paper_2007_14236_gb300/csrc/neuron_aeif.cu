@@ -18,18 +18,21 @@
 // scans the pending spikes (as the LIF kernel).  kAlpha: alpha-function
 // conductances (the paper's balanced network, Sec. 2.4) with state x_ex, x_in.
 #include "aeif_rk.cuh"
+#include "deliver_item.cuh"
 #include "neuron_step.cuh"
 
 namespace ngb {
 
-template <bool kFixed, bool kAge, bool kAlpha>
+template <bool kFixed, int kMode, bool kAlpha>
 __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constant__ SegTable<AeifSeg> T,
                                                             const uint32_t* __restrict__ thr,
                                                             float* __restrict__ V_, float* __restrict__ w_,
                                                             float* __restrict__ ge_, float* __restrict__ gi_,
                                                             float* __restrict__ h_, float* __restrict__ xe_,
                                                             float* __restrict__ xi_, Ring ring, int64_t* clk,
-                                                            const Csr csr, SpikeBuf sb, int scan, int budget) {
+                                                            int64_t step_off, const Csr csr, SpikeBuf sb, int scan,
+                                                            int budget) {
+  constexpr bool kAge = kMode == kEmitAge;
   __shared__ uint32_t s_thr[kMaxThr];
   const int seg = segment_index_of(T, (int64_t)blockIdx.x);
   const AeifSeg p = T.n <= kInlineSegs ? T.s[seg] : T.dev[seg];
@@ -56,8 +59,8 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
   __syncthreads();
   griddep_wait();
   griddep_launch();
-  const int64_t t = clk[0];
-  if (blockIdx.x == 0 && threadIdx.x == 0) clk[1] = t;
+  const int64_t t = clk[0] + step_off;
+  if (kMode != kEmitPipe && blockIdx.x == 0 && threadIdx.x == 0) clk[1] = t;
   if (kAge && scan)
     scan_pending<false>(t, csr, sb, ((int64_t)blockIdx.x * kAeifBlock + threadIdx.x) >> 5,
                         ((int64_t)gridDim.x * kAeifBlock) >> 5);
@@ -99,13 +102,14 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
       rec[3] = make_uint4((uint32_t)hb, (uint32_t)(hb >> 32), (uint32_t)tb, (uint32_t)(tb >> 32));
     }
   }
-  defer_write(!done, rec, sb, kAlpha ? 1 : 0);
+  defer_write(!done, rec, sb, kAlpha ? 1 : 0, t);
   // sub-step statistics: one atomic per warp
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nsub += __shfl_xor_sync(0xffffffffu, nsub, o);
   if ((threadIdx.x & 31) == 0 && nsub) atomicAdd(sb.substeps, nsub);
   const uint32_t mult = nspk > 63u ? 63u : nspk;
-  if (kAge) emit_spikes_age(done && nspk > 0, gid, mult, t, csr, sb);
+  if (kMode == kEmitAge) emit_spikes_age(done && nspk > 0, gid, mult, t, csr, sb);
+  else if (kMode == kEmitPipe) emit_spikes_pipe<kFixed>(done && nspk > 0, gid, mult, t, meta, csr, ring, sb);
   else emit_spikes(done && nspk > 0, gid, mult, t, meta, sb);
 }
 
@@ -113,19 +117,23 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
 // the update kernel's attempt budget (mostly those crossing V_peak, whose
 // step needs tens of attempts) continue from their saved position, packed
 // 32 to a warp, then write their state and join the spike compaction.
-template <bool kFixed, bool kAge, bool kAlpha>
+template <bool kFixed, int kMode, bool kAlpha>
 __global__ void __launch_bounds__(kAeifBlock) k_aeif_finish(const __grid_constant__ SegTable<AeifSeg> T,
                                                             float* __restrict__ V_, float* __restrict__ w_,
                                                             float* __restrict__ ge_, float* __restrict__ gi_,
                                                             float* __restrict__ h_, float* __restrict__ xe_,
-                                                            float* __restrict__ xi_, int64_t* clk, const Csr csr,
-                                                            SpikeBuf sb) {
+                                                            float* __restrict__ xi_, Ring ring, int64_t* clk,
+                                                            int64_t step_off, const Csr csr, SpikeBuf sb) {
+  constexpr bool kAge = kMode == kEmitAge;
   griddep_wait();
   griddep_launch();
   const int kind = kAlpha ? 1 : 0;
-  unsigned long long n = sb.dcnt[kind];
+  const int64_t t = clk[0] + step_off;
+  unsigned long long n = sb.dcnt[2 * kind + (int)(t & 1)];
   if (n > (unsigned long long)sb.dfr_cap) n = (unsigned long long)sb.dfr_cap;
-  const int64_t t = clk[0];
+  // the previous step's list is finished (this stream ran its finishing kernel
+  // first) and the next step appends to it only after this kernel
+  if (blockIdx.x == 0 && threadIdx.x == 0) sb.dcnt[2 * kind + (int)((t + 1) & 1)] = 0;
   const uint4* __restrict__ list = sb.dfr[kind];
   const int lane = threadIdx.x & 31;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * kAeifBlock + threadIdx.x) >> 5;
@@ -164,57 +172,72 @@ __global__ void __launch_bounds__(kAeifBlock) k_aeif_finish(const __grid_constan
     for (int o = 16; o > 0; o >>= 1) nsub += __shfl_xor_sync(0xffffffffu, nsub, o);
     if (lane == 0 && nsub) atomicAdd(sb.substeps, nsub);
     const uint32_t mult = nspk > 63u ? 63u : nspk;
-    if (kAge) emit_spikes_age(nspk > 0, gid, mult, t, csr, sb);
+    if (kMode == kEmitAge) emit_spikes_age(nspk > 0, gid, mult, t, csr, sb);
+    else if (kMode == kEmitPipe) emit_spikes_pipe<kFixed>(nspk > 0, gid, mult, t, meta, csr, ring, sb);
     else emit_spikes(nspk > 0, gid, mult, t, meta, sb);
   }
 }
 
+namespace {
+template <bool kFixed, int kMode>
+cudaError_t aeif_launch(const SegTable<AeifSeg>& segs, dim3 g, const uint32_t* thr, float* V, float* w, float* gex,
+                        float* gin, float* h, float* xe, float* xi, bool alpha, Ring ring, int64_t* clk,
+                        int64_t step_off, const Csr& csr, SpikeBuf sb, int sc, int budget, bool pdl, cudaStream_t st) {
+  const dim3 b(kAeifBlock);
+  if (alpha)
+    return launch_k(k_update_aeif<kFixed, kMode, true>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, xe, xi, ring, clk,
+                    step_off, csr, sb, sc, budget);
+  return launch_k(k_update_aeif<kFixed, kMode, false>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, xe, xi, ring, clk,
+                  step_off, csr, sb, sc, budget);
+}
+
+template <bool kFixed, int kMode>
+cudaError_t finish_launch(const SegTable<AeifSeg>& segs, dim3 g, float* V, float* w, float* gex, float* gin, float* h,
+                          float* xe, float* xi, bool alpha, Ring ring, int64_t* clk, int64_t step_off, const Csr& csr,
+                          SpikeBuf sb, bool pdl, cudaStream_t st) {
+  const dim3 b(kAeifBlock);
+  if (alpha)
+    return launch_k(k_aeif_finish<kFixed, kMode, true>, g, b, pdl, st, segs, V, w, gex, gin, h, xe, xi, ring, clk,
+                    step_off, csr, sb);
+  return launch_k(k_aeif_finish<kFixed, kMode, false>, g, b, pdl, st, segs, V, w, gex, gin, h, xe, xi, ring, clk,
+                  step_off, csr, sb);
+}
+}  // namespace
+
 cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V,
                                float* w, float* gex, float* gin, float* h, float* xe, float* xi, bool alpha,
-                               Ring ring, bool fixed, int64_t* clk, const Csr& csr, SpikeBuf sb, bool age, bool scan,
-                               int budget, bool pdl, cudaStream_t st) {
+                               Ring ring, bool fixed, int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb,
+                               int emit, bool scan, int budget, bool pdl, cudaStream_t st) {
   if (blocks <= 0) return cudaSuccess;
-  const dim3 g((unsigned)blocks), b(kAeifBlock);
+  const dim3 g((unsigned)blocks);
   const int sc = scan ? 1 : 0;
-#define NGB_AEIF(F, A, P)                                                                                         \
-  return launch_k(k_update_aeif<F, A, P>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, xe, xi, ring, clk, csr, sb, \
-                  sc, budget)
-  if (alpha) {
-    if (fixed) {
-      if (age) NGB_AEIF(true, true, true);
-      NGB_AEIF(true, false, true);
-    }
-    if (age) NGB_AEIF(false, true, true);
-    NGB_AEIF(false, false, true);
-  }
+#define NGB_AEIF(F, M) \
+  return aeif_launch<F, M>(segs, g, thr, V, w, gex, gin, h, xe, xi, alpha, ring, clk, step_off, csr, sb, sc, budget, pdl, st)
   if (fixed) {
-    if (age) NGB_AEIF(true, true, false);
-    NGB_AEIF(true, false, false);
+    if (emit == kEmitAge) NGB_AEIF(true, kEmitAge);
+    if (emit == kEmitPipe) NGB_AEIF(true, kEmitPipe);
+    NGB_AEIF(true, kEmitRing);
   }
-  if (age) NGB_AEIF(false, true, false);
-  NGB_AEIF(false, false, false);
+  if (emit == kEmitAge) NGB_AEIF(false, kEmitAge);
+  if (emit == kEmitPipe) NGB_AEIF(false, kEmitPipe);
+  NGB_AEIF(false, kEmitRing);
 #undef NGB_AEIF
 }
 
 cudaError_t launch_finish_aeif(const SegTable<AeifSeg>& segs, int grid, float* V, float* w, float* gex, float* gin,
-                               float* h, float* xe, float* xi, bool alpha, bool fixed, int64_t* clk, const Csr& csr,
-                               SpikeBuf sb, bool age, bool pdl, cudaStream_t st) {
-  const dim3 g((unsigned)grid), b(kAeifBlock);
-#define NGB_FIN(F, A, P) return launch_k(k_aeif_finish<F, A, P>, g, b, pdl, st, segs, V, w, gex, gin, h, xe, xi, clk, csr, sb)
-  if (alpha) {
-    if (fixed) {
-      if (age) NGB_FIN(true, true, true);
-      NGB_FIN(true, false, true);
-    }
-    if (age) NGB_FIN(false, true, true);
-    NGB_FIN(false, false, true);
-  }
+                               float* h, float* xe, float* xi, bool alpha, Ring ring, bool fixed, int64_t* clk,
+                               int64_t step_off, const Csr& csr, SpikeBuf sb, int emit, bool pdl, cudaStream_t st) {
+  const dim3 g((unsigned)grid);
+#define NGB_FIN(F, M) \
+  return finish_launch<F, M>(segs, g, V, w, gex, gin, h, xe, xi, alpha, ring, clk, step_off, csr, sb, pdl, st)
   if (fixed) {
-    if (age) NGB_FIN(true, true, false);
-    NGB_FIN(true, false, false);
+    if (emit == kEmitAge) NGB_FIN(true, kEmitAge);
+    if (emit == kEmitPipe) NGB_FIN(true, kEmitPipe);
+    NGB_FIN(true, kEmitRing);
   }
-  if (age) NGB_FIN(false, true, false);
-  NGB_FIN(false, false, false);
+  if (emit == kEmitAge) NGB_FIN(false, kEmitAge);
+  if (emit == kEmitPipe) NGB_FIN(false, kEmitPipe);
+  NGB_FIN(false, kEmitRing);
 #undef NGB_FIN
 }
 

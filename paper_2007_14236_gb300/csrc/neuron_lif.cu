@@ -23,6 +23,7 @@
 // only when it fires (no per-neuron metadata prefetch).
 // All FP32 arithmetic uses explicit round-to-nearest intrinsics, so no FMA
 // contraction changes the result: V and I are a fixed function of the input.
+#include "deliver_item.cuh"
 #include "neuron_step.cuh"
 
 namespace ngb {
@@ -31,11 +32,12 @@ namespace ngb {
 // times over): a block covers 256 * kNpt consecutive neurons of one segment,
 // and each thread issues the loads of all its neurons before the first use,
 // so that enough bytes are in flight to cover the memory latency.
-template <bool kFixed, bool kAge, int kNpt>
-__global__ void __launch_bounds__(kLifBlock, kNpt > 1 ? 3 : (kAge ? 6 : 8))
+template <bool kFixed, int kMode, int kNpt>
+__global__ void __launch_bounds__(kLifBlock, kNpt > 1 ? (kMode == kEmitPipe ? 2 : 3) : (kMode == kEmitRing ? 8 : 6))
     k_update_lif(const __grid_constant__ SegTable<LifSeg> T, const uint32_t* __restrict__ thr,
                  float* __restrict__ y_, float* __restrict__ I_, int32_t* __restrict__ ref_, Ring ring, int64_t* clk,
-                 const Csr csr, SpikeBuf sb, int scan) {
+                 int64_t step_off, const Csr csr, SpikeBuf sb, int scan) {
+  constexpr bool kAge = kMode == kEmitAge;
   __shared__ uint32_t s_thr[kMaxThr];
   const LifSeg sg = segment_of(T, (int64_t)blockIdx.x);
   const int64_t k0 = ((int64_t)blockIdx.x - sg.blk_begin) * (kLifBlock * kNpt) + threadIdx.x;
@@ -64,8 +66,8 @@ __global__ void __launch_bounds__(kLifBlock, kNpt > 1 ? 3 : (kAge ? 6 : 8))
   // the previous step's delivery has completed: ring slot t and the counters are final
   griddep_wait();
   griddep_launch();
-  const int64_t t = clk[0];
-  if (blockIdx.x == 0 && threadIdx.x == 0) clk[1] = t;
+  const int64_t t = clk[0] + step_off;
+  if (kMode != kEmitPipe && blockIdx.x == 0 && threadIdx.x == 0) clk[1] = t;
   if (kAge && scan)
     scan_pending<false>(t, csr, sb, ((int64_t)blockIdx.x * kLifBlock + threadIdx.x) >> 5,
                         ((int64_t)gridDim.x * kLifBlock) >> 5);
@@ -93,32 +95,41 @@ __global__ void __launch_bounds__(kLifBlock, kNpt > 1 ? 3 : (kAge ? 6 : 8))
       I_[gid] = I[j];
       ref_[gid] = ref[j];
     }
-    if (kAge) emit_spikes_age(spk, gid, 1u, t, csr, sb);
+    if (kMode == kEmitAge) emit_spikes_age(spk, gid, 1u, t, csr, sb);
+    else if (kMode == kEmitPipe) emit_spikes_pipe<kFixed>(spk, gid, 1u, t, meta[j], csr, ring, sb);
     else emit_spikes(spk, gid, 1u, t, meta[j], sb);
   }
 }
 
+namespace {
+template <bool kFixed, int kMode>
+cudaError_t lif_launch(const SegTable<LifSeg>& segs, dim3 g, int npt, const uint32_t* thr, float* y, float* I,
+                       int32_t* ref, Ring ring, int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, int sc,
+                       bool pdl, cudaStream_t st) {
+  const dim3 b(kLifBlock);
+  if (npt == 4)
+    return launch_k(k_update_lif<kFixed, kMode, 4>, g, b, pdl, st, segs, thr, y, I, ref, ring, clk, step_off, csr, sb,
+                    sc);
+  return launch_k(k_update_lif<kFixed, kMode, 1>, g, b, pdl, st, segs, thr, y, I, ref, ring, clk, step_off, csr, sb,
+                  sc);
+}
+}  // namespace
+
 cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, int npt, const uint32_t* thr, float* y,
-                              float* I, int32_t* ref, Ring ring, bool fixed, int64_t* clk, const Csr& csr,
-                              SpikeBuf sb, bool age, bool scan, bool pdl, cudaStream_t st) {
+                              float* I, int32_t* ref, Ring ring, bool fixed, int64_t* clk, int64_t step_off,
+                              const Csr& csr, SpikeBuf sb, int emit, bool scan, bool pdl, cudaStream_t st) {
   if (blocks <= 0) return cudaSuccess;
-  const dim3 g((unsigned)blocks), b(kLifBlock);
+  const dim3 g((unsigned)blocks);
   const int sc = scan ? 1 : 0;
-#define NGB_LIF(F, A, P) return launch_k(k_update_lif<F, A, P>, g, b, pdl, st, segs, thr, y, I, ref, ring, clk, csr, sb, sc)
-  if (npt == 4) {
-    if (fixed) {
-      if (age) NGB_LIF(true, true, 4);
-      NGB_LIF(true, false, 4);
-    }
-    if (age) NGB_LIF(false, true, 4);
-    NGB_LIF(false, false, 4);
-  }
+#define NGB_LIF(F, M) return lif_launch<F, M>(segs, g, npt, thr, y, I, ref, ring, clk, step_off, csr, sb, sc, pdl, st)
   if (fixed) {
-    if (age) NGB_LIF(true, true, 1);
-    NGB_LIF(true, false, 1);
+    if (emit == kEmitAge) NGB_LIF(true, kEmitAge);
+    if (emit == kEmitPipe) NGB_LIF(true, kEmitPipe);
+    NGB_LIF(true, kEmitRing);
   }
-  if (age) NGB_LIF(false, true, 1);
-  NGB_LIF(false, false, 1);
+  if (emit == kEmitAge) NGB_LIF(false, kEmitAge);
+  if (emit == kEmitPipe) NGB_LIF(false, kEmitPipe);
+  NGB_LIF(false, kEmitRing);
 #undef NGB_LIF
 }
 

@@ -153,7 +153,8 @@ uint64_t call_synapses(const ngb_conn_spec& c, int64_t ns, int64_t nt, bool same
   }
 }
 
-constexpr int kCounters = 10;  // device counter words: ctr[2], events, substeps, rec_count, spare, pcnt[2], dcnt[2]
+// device counter words: ctr[2], events, substeps, rec_count, spare, pcnt[2], dcnt[4], ctr3[3], spare
+constexpr int kCounters = 16;
 
 uint64_t next_pow2(uint64_t x) {
   uint64_t p = 1;
@@ -219,7 +220,9 @@ struct ngb_sim {
   uint32_t* thr = nullptr;
   int deliver_grid = 0;
   bool pdl = true;  // programmatic dependent launch between the step's kernels
-  int mode = 0;     // 0: per-step kernels in CUDA graphs, 1: persistent step kernel, 2: fused update + delivery
+  int mode = 0;  // 0: per-step kernels in CUDA graphs, 1: persistent step kernel, 2: fused update + delivery,
+                 // 3: pipelined (delivery of step t beside the update of step t + 1, two streams)
+  cudaStream_t stream2 = nullptr;  // second stream of the pipelined loop's graphs
   bool persist_ok = false;
   int persist_grid = 0;
   int persist_max_bpsm = 0;
@@ -267,45 +270,63 @@ Ring ring_of(const ngb_sim* s) {
 }
 
 Csr csr_of(const ngb_sim* s) {
-  return Csr{s->src_meta, s->src_syn, s->src_grp, s->grp_start, s->grp_delay, s->tgt, s->w, s->src_age};
+  return Csr{s->src_meta, s->src_syn, s->src_grp, s->grp_start, s->grp_delay, s->tgt, s->w, s->src_age,
+             s->cfg.weight_dtype};
 }
 
+// How the update kernels hand the step's spikes to delivery.
+int emit_of(const ngb_sim* s) { return s->scheme == 2 ? kEmitAge : (s->mode == 3 ? kEmitPipe : kEmitRing); }
+
+// Programmatic dependent launch chains the kernels of one stream; the
+// pipelined loop's kernels depend across two streams and go without it.
+bool pdl_of(const ngb_sim* s) { return s->pdl && s->mode != 3; }
+
 // The first update kernel of the step scans the pending spikes (spike-buffer scheme).
-cudaError_t launch_lif(ngb_sim* s) {
+cudaError_t launch_lif(ngb_sim* s, int64_t step_off = 0) {
   return launch_update_lif(s->lif_tab, s->lif_blocks, s->lif_npt, s->thr, s->st0, s->st1, s->ref, ring_of(s),
-                           s->cfg.deterministic != 0, s->clk, csr_of(s), s->sb, s->scheme == 2, true, s->pdl,
-                           s->stream);
+                           s->cfg.deterministic != 0, s->clk, step_off, csr_of(s), s->sb, emit_of(s), true,
+                           pdl_of(s), s->stream);
 }
 
 // AdEx update kernels: exponential-conductance segments, then alpha ones.
 // Each kind is an update kernel with an attempt budget, then the kernel that
 // finishes the deferred neurons.
-cudaError_t launch_aeif(ngb_sim* s) {
+cudaError_t launch_aeif(ngb_sim* s, int64_t step_off = 0) {
   cudaError_t e = cudaSuccess;
-  const bool det = s->cfg.deterministic != 0, age = s->scheme == 2;
+  const bool det = s->cfg.deterministic != 0;
+  const int emit = emit_of(s);
+  const bool pdl = pdl_of(s);
   const int fin_grid = std::max(1, s->sms) * 4;
   if (s->n_aeif_exp) {
     e = launch_update_aeif(s->aeif_tab, s->aeif_blocks, s->thr, s->st0, s->st1, s->st2, s->st3, s->st4, s->st5,
-                           s->st6, false, ring_of(s), det, s->clk, csr_of(s), s->sb, age, s->n_lif == 0,
-                           s->aeif_budget, s->pdl, s->stream);
+                           s->st6, false, ring_of(s), det, s->clk, step_off, csr_of(s), s->sb, emit, s->n_lif == 0,
+                           s->aeif_budget, pdl, s->stream);
     if (e == cudaSuccess && s->aeif_budget > 0)
       e = launch_finish_aeif(s->aeif_tab, fin_grid, s->st0, s->st1, s->st2, s->st3, s->st4, s->st5, s->st6, false,
-                             det, s->clk, csr_of(s), s->sb, age, s->pdl, s->stream);
+                             ring_of(s), det, s->clk, step_off, csr_of(s), s->sb, emit, pdl, s->stream);
   }
   if (e == cudaSuccess && s->n_aeif_alpha) {
     e = launch_update_aeif(s->aeifa_tab, s->aeifa_blocks, s->thr, s->st0, s->st1, s->st2, s->st3, s->st4, s->st5,
-                           s->st6, true, ring_of(s), det, s->clk, csr_of(s), s->sb, age,
-                           s->n_lif == 0 && s->n_aeif_exp == 0, s->aeif_budget, s->pdl, s->stream);
+                           s->st6, true, ring_of(s), det, s->clk, step_off, csr_of(s), s->sb, emit,
+                           s->n_lif == 0 && s->n_aeif_exp == 0, s->aeif_budget, pdl, s->stream);
     if (e == cudaSuccess && s->aeif_budget > 0)
       e = launch_finish_aeif(s->aeifa_tab, fin_grid, s->st0, s->st1, s->st2, s->st3, s->st4, s->st5, s->st6, true,
-                             det, s->clk, csr_of(s), s->sb, age, s->pdl, s->stream);
+                             ring_of(s), det, s->clk, step_off, csr_of(s), s->sb, emit, pdl, s->stream);
   }
   return e;
 }
 
-cudaError_t launch_del(ngb_sim* s) {
-  return launch_deliver(s->sb, csr_of(s), s->cfg.weight_dtype, ring_of(s), s->cfg.deterministic != 0,
-                        s->scheme == 2, s->clk, s->deliver_grid, s->pdl, s->stream);
+cudaError_t launch_del(ngb_sim* s, int64_t step_off = 0, cudaStream_t st = nullptr) {
+  return launch_deliver(s->sb, csr_of(s), s->cfg.weight_dtype, ring_of(s), s->cfg.deterministic != 0, emit_of(s),
+                        s->clk, step_off, s->deliver_grid, pdl_of(s), st ? st : s->stream);
+}
+
+// The update kernels of one step (step clk[0] + step_off).
+cudaError_t launch_updates(ngb_sim* s, int64_t step_off) {
+  cudaError_t e = cudaSuccess;
+  if (s->n_lif) e = launch_lif(s, step_off);
+  if (e == cudaSuccess && s->n_aeif) e = launch_aeif(s, step_off);
+  return e;
 }
 
 // Switch the delivery scheme (only while no spike is in flight: step 0).
@@ -350,7 +371,13 @@ cudaError_t launch_step(ngb_sim* s) {
   if (s->mode == 2) {
     e = launch_fused(s, 0);
     if (e != cudaSuccess) return e;
-    return launch_tick_add(s->clk, 1, s->sb.ctr, s->pdl, s->stream);
+    return launch_tick_add(s->clk, 1, s->sb.ctr, s->sb.ctr3, s->pdl, s->stream);
+  }
+  if (s->mode == 3) {  // one pipelined step, serialised on the main stream
+    e = launch_updates(s, 0);
+    if (e == cudaSuccess) e = launch_del(s, 0);
+    if (e != cudaSuccess) return e;
+    return launch_tick_add(s->clk, 1, s->sb.ctr, s->sb.ctr3, false, s->stream);
   }
   if (!s->n_lif && !s->n_aeif) {
     e = launch_tick(s->clk, s->pdl, s->stream);
@@ -423,13 +450,38 @@ int capture_graph(ngb_sim* s) {
   cudaGraph_t graph = nullptr;
   CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
+  std::vector<cudaEvent_t> events;
   if (s->mode == 2) {
     for (int i = 0; i < s->graph_steps && e == cudaSuccess; ++i) e = launch_fused(s, i);
-    if (e == cudaSuccess) e = launch_tick_add(s->clk, s->graph_steps, s->sb.ctr, s->pdl, s->stream);
+    if (e == cudaSuccess) e = launch_tick_add(s->clk, s->graph_steps, s->sb.ctr, s->sb.ctr3, s->pdl, s->stream);
+  } else if (s->mode == 3) {
+    // Pipelined: the updates of the steps on the main stream, their
+    // deliveries on the second; the update of step i waits for the delivery
+    // of step i - 2 (the delivery of step i - 1 lands in slots i + 1 and
+    // later), the delivery of step i for the update of step i.
+    const int S = s->graph_steps;
+    events.resize((size_t)(2 * S + 1), nullptr);
+    for (auto& ev : events)
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(events[(size_t)(2 * S)], s->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream2, events[(size_t)(2 * S)], 0);
+    for (int i = 0; i < S && e == cudaSuccess; ++i) {
+      cudaEvent_t eu = events[(size_t)(2 * i)], ed = events[(size_t)(2 * i + 1)];
+      if (i >= 2) e = cudaStreamWaitEvent(s->stream, events[(size_t)(2 * (i - 2) + 1)], 0);
+      if (e == cudaSuccess) e = launch_updates(s, i);
+      if (e == cudaSuccess) e = cudaEventRecord(eu, s->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream2, eu, 0);
+      if (e == cudaSuccess) e = launch_del(s, i, s->stream2);
+      if (e == cudaSuccess) e = cudaEventRecord(ed, s->stream2);
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, events[(size_t)(2 * (S - 1) + 1)], 0);
+    if (e == cudaSuccess) e = launch_tick_add(s->clk, S, s->sb.ctr, s->sb.ctr3, false, s->stream);
   } else {
     for (int i = 0; i < s->graph_steps && e == cudaSuccess; ++i) e = launch_step(s);
   }
   cudaError_t e2 = cudaStreamEndCapture(s->stream, &graph);
+  for (cudaEvent_t ev : events)
+    if (ev) cudaEventDestroy(ev);
   if (e != cudaSuccess) return cuda_fail(e, "graph capture (kernel launch)");
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
   e = cudaGraphInstantiate(&s->gexec, graph, 0);
@@ -918,6 +970,8 @@ int rebuild_tables(ngb_sim* s) {
   }
   // the fused loop runs one LIF neuron per thread and delivers with the ring scheme
   if (s->mode == 2 && (s->lif_npt != 1 || s->scheme != 1)) s->mode = 0;
+  // the pipelined loop delivers with the ring scheme
+  if (s->mode == 3 && (s->scheme != 1 || !s->stream2)) s->mode = 0;
   s->tables_dirty = false;
   return capture_graph(s);
 }
@@ -997,6 +1051,7 @@ int finalize_impl(ngb_sim* s) {
   s->sb.rec_count = ctrs + 4;
   s->sb.pcnt = ctrs + 6;
   s->sb.dcnt = ctrs + 8;
+  s->sb.ctr3 = ctrs + 12;
   CK(s->dalloc(&s->sb.err, 1));
   CK(cudaMemsetAsync(s->sb.err, 0, sizeof(uint32_t), st));
   CK(s->dalloc(&s->clk, 2));
@@ -1107,6 +1162,11 @@ int finalize_impl(ngb_sim* s) {
   s->sb.wi_cap = (int64_t)wi_entries;
   CK(s->dalloc(&s->sb.wi[0], wi_entries));
   CK(s->dalloc(&s->sb.wi[1], wi_entries));
+  if (s->cfg.delivery != 2) {
+    // pipelined ring scheme: work-item lists by step mod 3, and its second stream
+    for (int q = 0; q < 3; ++q) CK(s->dalloc(&s->sb.wi3[q], 2 * s->work_items + 2));
+    CK(cudaStreamCreateWithFlags(&s->stream2, cudaStreamNonBlocking));
+  }
   // ring buffer
   const size_t ring_bytes = (size_t)s->L * s->R * N * (s->cfg.deterministic ? 8 : 4);
   CK(s->dalloc((uint8_t**)&s->ring, ring_bytes));
@@ -1127,6 +1187,7 @@ int finalize_impl(ngb_sim* s) {
   s->mode = 0;
   if (env_mode && std::string(env_mode) == "persistent") s->mode = 1;
   if (env_mode && std::string(env_mode) == "fused" && s->scheme == 1) s->mode = 2;
+  if (env_mode && std::string(env_mode) == "pipelined" && s->scheme == 1 && s->stream2) s->mode = 3;
   s->graph_steps = s->cfg.steps_per_graph == 0 ? 100 : std::max(0, s->cfg.steps_per_graph);
   return rebuild_tables(s);
 }
@@ -1191,12 +1252,13 @@ int simulate_impl(ngb_sim* s, int64_t steps, bool profiled, double* kernel_ms, i
     for (int64_t i = 0; i < chunk; ++i) {
       cudaEvent_t* e = &ev[4 * i];
       CK(cudaEventRecord(e[0], s->stream));
-      if (s->n_lif) CK(fused ? launch_fused_lif(s, 0) : launch_lif(s));
+      if (s->n_lif) CK(fused ? launch_fused_lif(s, 0) : launch_lif(s, 0));
       CK(cudaEventRecord(e[1], s->stream));
-      if (s->n_aeif) CK(fused ? launch_fused_aeif(s, 0) : launch_aeif(s));
+      if (s->n_aeif) CK(fused ? launch_fused_aeif(s, 0) : launch_aeif(s, 0));
       CK(cudaEventRecord(e[2], s->stream));
-      CK(fused ? launch_tick_add(s->clk, 1, s->sb.ctr, s->pdl, s->stream) : launch_del(s));
+      CK(fused ? launch_tick_add(s->clk, 1, s->sb.ctr, s->sb.ctr3, s->pdl, s->stream) : launch_del(s, 0));
       CK(cudaEventRecord(e[3], s->stream));
+      if (s->mode == 3) CK(launch_tick_add(s->clk, 1, s->sb.ctr, s->sb.ctr3, false, s->stream));
     }
     CK(cudaStreamSynchronize(s->stream));
     for (int64_t i = 0; i < chunk; ++i) {
@@ -1328,6 +1390,7 @@ int ngb_destroy(ngb_sim* s) {
   cudaSetDevice(s->cfg.device);
   if (s->stream) cudaStreamSynchronize(s->stream);
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  if (s->stream2) cudaStreamDestroy(s->stream2);
   for (void* p : s->allocs) cudaFree(p);
   for (void* p : s->table_allocs) cudaFree(p);
   if (s->own_stream) cudaStreamDestroy(s->stream);
@@ -1478,7 +1541,8 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
     std::string k;
     int m = 0, g = 0, pg = 0, sc = 0;
     while (in >> k >> m >> g >> pg >> sc) {
-      if (k == key && g > 0 && (m == 0 || (m == 2 && sc == 1) || (s->persist_ok && pg > 0)) &&
+      if (k == key && g > 0 && (m == 0 || (m == 2 && sc == 1) || (m == 3 && sc == 1 && s->stream2) ||
+                                (s->persist_ok && pg > 0)) &&
           (sc == s->scheme || both)) {
         set_scheme(s, sc);
         s->mode = m;
@@ -1531,6 +1595,32 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
         best_grid = s->deliver_grid;
         best_scheme = scheme;
       }
+    }
+    // pipelined loop (ring scheme): delivery blocks per SM
+    if (rc == NGB_OK && scheme == 1 && s->stream2) {
+      for (int b : {1, 2, 4, 8}) {
+        s->mode = 3;
+        s->deliver_grid = b * sms;
+        rc = capture_graph(s);
+        if (rc == NGB_OK) rc = snapshot_restore(s, sn);
+        if (rc != NGB_OK) break;
+        const int64_t reps = std::max<int64_t>(1, trial_steps / s->graph_steps);
+        CK(cudaGraphLaunch(s->gexec, s->stream));  // warm-up replay
+        CK(cudaEventRecord(e0, s->stream));
+        for (int64_t r = 0; r < reps; ++r) CK(cudaGraphLaunch(s->gexec, s->stream));
+        CK(cudaEventRecord(e1, s->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        const double per_step = ms / (double)(reps * s->graph_steps);
+        if (per_step < best_ms) {
+          best_ms = per_step;
+          best_mode = 3;
+          best_grid = s->deliver_grid;
+          best_scheme = scheme;
+        }
+      }
+      s->mode = 0;
     }
     // fused update + delivery in graphs (ring scheme)
     if (rc == NGB_OK && scheme == 1 && s->lif_npt == 1) {
@@ -1741,7 +1831,7 @@ int ngb_get_stats(ngb_sim* s, ngb_stats* out) {
     out->mode = s->mode;
     out->launch_grid = s->mode == 1   ? s->persist_grid
                        : s->mode == 2 ? s->lif_blocks + s->aeif_blocks + s->aeifa_blocks
-                                      : s->deliver_grid;
+                                      : s->deliver_grid;  // graph and pipelined loops: the delivery grid
     out->delivery = s->scheme;
   }
   return NGB_OK;

@@ -121,8 +121,11 @@ struct SpikeBuf {
   // budget (by conductance model: 0 exponential, 1 alpha), finished by a second
   // kernel with the neurons packed into full warps
   uint4* dfr[2];                    // 4 uint4 per neuron
-  unsigned long long* dcnt;         // [2]
+  unsigned long long* dcnt;         // [model * 2 + step parity]
   int64_t dfr_cap;                  // neurons per list
+  // pipelined ring scheme: work-item lists and counters by step mod 3
+  uint4* wi3[3];
+  unsigned long long* ctr3;         // [3]
 };
 
 struct Csr {
@@ -134,6 +137,7 @@ struct Csr {
   const uint32_t* tgt;
   const void* w;
   const uint2* src_age;
+  int32_t wdtype;  // storage of w: 0 FP32, 1 BF16, 2 FP16
 };
 
 struct Ring {
@@ -379,13 +383,13 @@ __device__ __forceinline__ void scan_pending(int64_t t, const Csr& csr, const Sp
 // call it.  The list holds one record per neuron, each neuron is deferred at
 // most once per step, so a position beyond the capacity is an internal error
 // (flagged, record dropped).
-__device__ __forceinline__ void defer_write(bool d, const uint4 rec[4], const SpikeBuf& sb, int kind) {
+__device__ __forceinline__ void defer_write(bool d, const uint4 rec[4], const SpikeBuf& sb, int kind, int64_t t) {
   const unsigned full = 0xffffffffu;
   const unsigned b = __ballot_sync(full, d);
   if (b == 0) return;
   const int lane = threadIdx.x & 31;
   unsigned long long base = 0;
-  if (lane == 0) base = atomicAdd(sb.dcnt + kind, (unsigned long long)__popc(b));
+  if (lane == 0) base = atomicAdd(sb.dcnt + 2 * kind + (int)(t & 1), (unsigned long long)__popc(b));
   base = __shfl_sync(full, base, 0);
   if (d) {
     const unsigned long long pos = base + __popc(b & ((1u << lane) - 1u));
@@ -480,20 +484,27 @@ struct PersistArgs {
 // Kernel launchers (one translation unit each).
 // age: spike-buffer scheme; scan: this kernel also scans the pending list
 // (the first update kernel of the step).
+// Emission modes of the per-step update kernels: the ring scheme, the
+// spike-buffer scheme, and the pipelined ring scheme (the delay-1 group of a
+// spike delivered at once by the update kernel, the other groups queued by
+// step mod 3 for a delivery kernel that runs beside the next update).
+enum : int { kEmitRing = 0, kEmitAge = 1, kEmitPipe = 2 };
+
 // npt: LIF neurons per thread (1 or 4); a block covers kLifBlock * npt neurons.
+// The step is clk[0] + step_off.
 cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, int npt, const uint32_t* thr, float* y,
-                              float* I, int32_t* ref, Ring ring, bool fixed, int64_t* clk, const Csr& csr,
-                              SpikeBuf sb, bool age, bool scan, bool pdl, cudaStream_t st);
+                              float* I, int32_t* ref, Ring ring, bool fixed, int64_t* clk, int64_t step_off,
+                              const Csr& csr, SpikeBuf sb, int emit, bool scan, bool pdl, cudaStream_t st);
 // alpha: the segments have alpha-function conductances (x_ex, x_in in xe, xi).
 // budget > 0: at most `budget` RK attempts per neuron in this kernel; the
 // unfinished neurons are completed by launch_finish_aeif (same arithmetic).
 cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V,
                                float* w, float* gex, float* gin, float* h, float* xe, float* xi, bool alpha,
-                               Ring ring, bool fixed, int64_t* clk, const Csr& csr, SpikeBuf sb, bool age, bool scan,
-                               int budget, bool pdl, cudaStream_t st);
+                               Ring ring, bool fixed, int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb,
+                               int emit, bool scan, int budget, bool pdl, cudaStream_t st);
 cudaError_t launch_finish_aeif(const SegTable<AeifSeg>& segs, int grid, float* V, float* w, float* gex, float* gin,
-                               float* h, float* xe, float* xi, bool alpha, bool fixed, int64_t* clk, const Csr& csr,
-                               SpikeBuf sb, bool age, bool pdl, cudaStream_t st);
+                               float* h, float* xe, float* xi, bool alpha, Ring ring, bool fixed, int64_t* clk,
+                               int64_t step_off, const Csr& csr, SpikeBuf sb, int emit, bool pdl, cudaStream_t st);
 cudaError_t launch_tick(int64_t* clk, bool pdl, cudaStream_t st);
 cudaError_t persistent_max_blocks_per_sm(bool fixed, int wdtype, bool lif, bool aeif, size_t smem, int* out);
 cudaError_t launch_persistent(const PersistArgs& a, bool fixed, int wdtype, bool lif, bool aeif, int grid,
@@ -514,8 +525,10 @@ cudaError_t launch_step_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, cons
                              float* gex, float* gin, float* h, float* xe, float* xi, bool alpha, Ring ring, bool fixed,
                              int wdtype, const int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, bool pdl,
                              cudaStream_t st);
-// clk[0] += n (clk[1] = clk[0] - 1); the ring scheme's step counters are cleared.
-cudaError_t launch_tick_add(int64_t* clk, int64_t n, unsigned long long* ctr, bool pdl, cudaStream_t st);
+// clk[0] += n (clk[1] = clk[0] - 1); the ring scheme's step counters (both
+// the per-step and the pipelined ones) are cleared.
+cudaError_t launch_tick_add(int64_t* clk, int64_t n, unsigned long long* ctr, unsigned long long* ctr3, bool pdl,
+                            cudaStream_t st);
 
 // Launch `kernel` with the programmatic-serialisation attribute when pdl.
 template <typename... KArgs, typename... Args>
@@ -532,8 +545,10 @@ cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, bool pdl, 
   cfg.numAttrs = pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
-cudaError_t launch_deliver(SpikeBuf sb, Csr csr, int wdtype, Ring ring, bool fixed, bool age, int64_t* clk,
-                           int grid, bool pdl, cudaStream_t st);
+// emit: the update kernels' emission mode; kEmitPipe delivers the list of
+// step clk[0] + step_off (without advancing the clock).
+cudaError_t launch_deliver(SpikeBuf sb, Csr csr, int wdtype, Ring ring, bool fixed, int emit, int64_t* clk,
+                           int64_t step_off, int grid, bool pdl, cudaStream_t st);
 // Spike-buffer scheme, serving handles: mark the pending entries of sources
 // in [lo, hi) dead (their instance was retired).
 cudaError_t launch_kill_pending(uint4* list, const unsigned long long* count, int64_t cap, uint32_t lo, uint32_t hi,

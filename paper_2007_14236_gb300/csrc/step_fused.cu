@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kAeifBlock) k_step_aeif(const __grid_constant_
   deliver_block_spikes<WT, kFixed, kAeifBlock>(nspk > 0, gid, mult, meta, t, csr, ring, S);
 }
 
-__global__ void k_tick_add(int64_t* clk, int64_t n, unsigned long long* ctr) {
+__global__ void k_tick_add(int64_t* clk, int64_t n, unsigned long long* ctr, unsigned long long* ctr3) {
   griddep_wait();
   griddep_launch();
   if (threadIdx.x != 0) return;
@@ -133,6 +133,11 @@ __global__ void k_tick_add(int64_t* clk, int64_t n, unsigned long long* ctr) {
   clk[1] = t - 1;
   ctr[0] = 0;
   ctr[1] = 0;
+  if (ctr3) {
+    ctr3[0] = 0;
+    ctr3[1] = 0;
+    ctr3[2] = 0;
+  }
 }
 
 namespace {
@@ -188,8 +193,9 @@ cudaError_t launch_step_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, cons
 #undef NGB_A
 }
 
-cudaError_t launch_tick_add(int64_t* clk, int64_t n, unsigned long long* ctr, bool pdl, cudaStream_t st) {
-  return launch_k(k_tick_add, dim3(1), dim3(32), pdl, st, clk, n, ctr);
+cudaError_t launch_tick_add(int64_t* clk, int64_t n, unsigned long long* ctr, unsigned long long* ctr3, bool pdl,
+                            cudaStream_t st) {
+  return launch_k(k_tick_add, dim3(1), dim3(32), pdl, st, clk, n, ctr, ctr3);
 }
 
 }  // namespace ngb

@@ -1,8 +1,10 @@
 """Step loops against each other: the persistent step kernel (many steps per
 cooperative launch, grid barriers between the update and delivery phases),
 the fused loop (each update block delivers its own spikes, one launch per
-step) and the update kernel at four neurons per thread, against the per-step
-kernels; and the bounded barrier wait.
+step), the pipelined loop (delay-1 groups delivered by the update kernels,
+the other groups by a delivery kernel beside the next step's update) and the
+update kernel at four neurons per thread, against the per-step kernels; and
+the bounded barrier wait.
 
 * Deterministic mode: the persistent kernel gives bit-identical spike trains
   and state to the per-step path (LIF, AdEx, batched instances), and to the
@@ -202,3 +204,50 @@ def test_aeif_attempt_budget_does_not_change_results(ngb, name):
             assert np.array_equal(a.state(var), b.state(var)), var
         assert a.stats()["rk_substeps"] == b.stats()["rk_substeps"]
         assert a.stats()["events"] == b.stats()["events"]
+
+
+_LOOP_SPECS = {
+    "balanced_lif": lambda: W.balanced_lif(n=1000, indegree=100, seed=1),
+    "microcircuit": lambda: W.microcircuit(scale=0.03, seed=7, keep_indegree=False),
+    "adex": lambda: W.balanced_adex(n=2000, indegree=100, seed=2, weight_dtype="fp32", poisson_weight=4.0,
+                                    w_ex=2.0, w_in=4.0),
+    "batched": lambda: W.batched_microcircuits(n_instances=3, scale_lo=0.02, scale_hi=0.04, seed=7),
+    "mc_bf16": lambda: W.microcircuit(scale=0.03, seed=8, keep_indegree=False, weight_dtype="bf16"),
+    "paper_alpha": lambda: W.paper_balanced(n_ex=1600, ce=160, seed=3),
+    "mixed": lambda: W.mixed_net(seed=2),
+}
+
+
+@pytest.mark.parametrize("name", sorted(_LOOP_SPECS))
+def test_pipelined_equals_per_step_kernels(ngb, name):
+    spec = _LOOP_SPECS[name]()
+    a = ngb.from_spec(spec, deterministic=True, delivery="ring")
+    with _env(NGB_MODE="pipelined"):
+        b = ngb.from_spec(spec, deterministic=True, delivery="ring", drain_steps=250)
+        b.finalize()
+    assert b.stats()["mode"] == 3
+    a.simulate(700)
+    b.simulate(250)  # 100-step graphs and eager steps, in chunks of 250
+    b.simulate_profiled(50)
+    b.simulate(400)
+    ai, at = a.spikes()
+    bi, bt = b.spikes()
+    assert len(ai) > 50
+    assert np.array_equal(at, bt) and np.array_equal(ai, bi)
+    assert np.array_equal(a.state("V_m"), b.state("V_m"))
+    assert a.stats()["events"] == b.stats()["events"]
+    for off in range(0, 4):
+        assert np.array_equal(a.input(0, off), b.input(0, off))
+
+
+def test_pipelined_with_four_neurons_per_thread(ngb):
+    spec = W.microcircuit(scale=0.05, seed=5, keep_indegree=False)
+    a = ngb.from_spec(spec, deterministic=True, delivery="ring")
+    with _env(NGB_MODE="pipelined", NGB_LIF_NPT=4):
+        b = ngb.from_spec(spec, deterministic=True, delivery="ring")
+        b.finalize()
+    assert b.stats()["mode"] == 3
+    a.simulate(600)
+    b.simulate(600)
+    assert np.array_equal(a.spikes()[0], b.spikes()[0]) and np.array_equal(a.spikes()[1], b.spikes()[1])
+    assert np.array_equal(a.state("I_syn"), b.state("I_syn"))
