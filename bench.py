@@ -36,7 +36,7 @@ if ROOT not in sys.path:
 METRIC = "real-time factor & synaptic events/s; batched/served vs plain at stated tol"
 UNIT = "synaptic events/s"
 DELIVERY = {1: "ring", 2: "spike_buffer"}
-LOOPS = {0: "graph", 1: "persistent", 2: "fused"}
+LOOPS = {0: "graph", 1: "persistent", 2: "fused", 3: "pipelined"}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches) from one ncu
 # capture of the full-size microcircuit with FP32 weights in this configuration (delivery scheme, step loop);
 # a kernel or configuration without a capture reports null
@@ -61,9 +61,10 @@ def _args():
     ap.add_argument("--no-variant", action="store_true", help="skip the BF16-weight variant")
     ap.add_argument("--delivery", choices=["auto", "ring", "spike_buffer"], default="auto",
                     help="spike delivery scheme (auto: chosen at finalisation, and by the autotuner at step 0)")
-    ap.add_argument("--mode", choices=["auto", "graph", "persistent", "fused"], default="auto",
+    ap.add_argument("--mode", choices=["auto", "graph", "persistent", "fused", "pipelined"], default="auto",
                     help="step loop: autotuned (default), per-step kernels in CUDA graphs, the persistent kernel, "
-                         "or the fused update + delivery kernels in CUDA graphs")
+                         "the fused update + delivery kernels, or the pipelined loop (delivery beside the next "
+                         "step's update, two-stream CUDA graphs)")
     ap.add_argument("--paper-n", type=str, default="1000000",
                     help="neurons of the paper's balanced network (comma-separated for a sweep)")
     ap.add_argument("--paper-ce", type=int, default=800, help="excitatory in-degree of the paper's balanced network")
@@ -616,7 +617,7 @@ def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
-    if a.mode in ("persistent", "fused"):
+    if a.mode in ("persistent", "fused", "pipelined"):
         os.environ["NGB_MODE"] = a.mode  # read by the library when a network is finalised
     if a.workload != "microcircuit":
         return {"small": run_small, "batched": run_batched, "adex": run_adex, "paper": run_paper,
@@ -649,7 +650,7 @@ def main():
         sim.autotune(1000)
         tune_s = time.perf_counter() - t1
     st0 = sim.stats()
-    mode = {0: "graph", 1: "persistent", 2: "fused"}[st0["mode"]]
+    mode = LOOPS[st0["mode"]]
 
     for _ in range(a.warmup):
         sim.simulate(a.sim_steps)
@@ -773,6 +774,7 @@ def main():
         "autotune_s": tune_s,
         "gpu_launches": int(a.steps if mode == "persistent" else
                             a.steps * (a.sim_steps + (a.sim_steps + 99) // 100) if mode == "fused" else
+                            a.steps * (2 * a.sim_steps + (a.sim_steps + 99) // 100) if mode == "pipelined" else
                             a.steps * a.sim_steps * 2),
         "e2e": {"value": e2e_events / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(d2h / a.steps), "real_time_factor": e2e_s / bio_s_rank},
