@@ -162,50 +162,16 @@ __device__ __forceinline__ void deliver_work_item_rt(int wdtype, const uint4 a, 
 // Every lane of the warp must call it.
 template <bool kFixed>
 __device__ __forceinline__ void emit_spikes_pipe(bool spk, uint32_t gid, uint32_t mult, int64_t t, uint4 meta,
-                                                 const Csr& csr, const Ring& ring, const SpikeBuf& sb) {
+                                                 uint2 ag, const Csr& csr, const Ring& ring, const SpikeBuf& sb) {
   const unsigned full = 0xffffffffu;
   const unsigned ball = __ballot_sync(full, spk);
   if (ball == 0) return;
   const int lane = threadIdx.x & 31;
-  record_spikes(spk, gid, mult, t, spk ? (unsigned long long)meta.z * mult : 0ull, sb);
   const uint32_t ngrp = meta.y >> 16;
-  uint2 ag = make_uint2(0, 0);
-  if (spk && ngrp > 0) ag = __ldg(csr.src_age + gid);
   const bool local = spk && ngrp > 0 && (ag.y & 0xFFFFu) == 1u;
-  const uint64_t b = (uint64_t)meta.x | ((uint64_t)(meta.y & 0xFFFFu) << 32);
-  uint4 rest = meta;
-  if (local) {
-    const uint64_t b2 = b + ag.x;
-    rest = make_uint4((uint32_t)b2, (uint32_t)((b2 >> 32) & 0xFFFFu) | ((ngrp - 1u) << 16), meta.z - ag.x,
-                      meta.w + 1u);
-  }
-  // work items of the remaining groups
-  uint32_t nch = 0;
-  if (spk && rest.z > 0) {
-    const uint64_t rb = (uint64_t)rest.x | ((uint64_t)(rest.y & 0xFFFFu) << 32);
-    nch = (uint32_t)((rb + rest.z - (rb & ~3ull) + kChunk - 1) / kChunk);
-  }
-  uint32_t inc = nch;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t x = __shfl_up_sync(full, inc, o);
-    if (lane >= o) inc += x;
-  }
-  const uint32_t tot = __shfl_sync(full, inc, 31);
-  const int q = (int)(t % 3);
-  unsigned long long base = 0;
-  if (lane == 0 && tot) base = atomicAdd(sb.ctr3 + q, (unsigned long long)tot);
-  base = __shfl_sync(full, base, 0);
   const uint32_t word = gid | (mult << kIdBits);
-  if (nch) {
-    uint4* const wi = sb.wi3[q];
-    const unsigned long long first = base + inc - nch;
-    for (uint32_t c = 0; c < nch; ++c) {
-      wi[2 * (first + c)] = make_uint4(word, c, rest.x, rest.y);
-      wi[2 * (first + c) + 1] = make_uint4(rest.z, rest.w, 0u, 0u);
-    }
-  }
-  // the delay-1 groups, one spiking lane at a time, by the whole warp
+  // the delay-1 groups first (one spiking lane at a time, by the whole warp):
+  // their loads are in flight while the bookkeeping below waits on atomics
   for (unsigned lm = __ballot_sync(full, local); lm; lm &= lm - 1) {
     const int l = __ffs(lm) - 1;
     const uint32_t wl = __shfl_sync(full, word, l);
@@ -218,6 +184,67 @@ __device__ __forceinline__ void emit_spikes_pipe(bool spk, uint32_t gid, uint32_
     for (uint32_t c = 0; c < nc; ++c)
       deliver_work_item_rt<kFixed>(csr.wdtype, make_uint4(wl, c, bx, by | (1u << 16)), make_uint4(n0, g0, 0u, 0u), t,
                                    csr, ring, lane);
+  }
+  const uint64_t b = (uint64_t)meta.x | ((uint64_t)(meta.y & 0xFFFFu) << 32);
+  uint4 rest = meta;
+  if (local) {
+    const uint64_t b2 = b + ag.x;
+    rest = make_uint4((uint32_t)b2, (uint32_t)((b2 >> 32) & 0xFFFFu) | ((ngrp - 1u) << 16), meta.z - ag.x,
+                      meta.w + 1u);
+  }
+  // work items of the remaining groups and the spike record: both positions
+  // reserved in one round of atomics
+  uint32_t nch = 0, m = 0;
+  unsigned long long nev = 0;
+  if (spk) {
+    if (rest.z > 0) {
+      const uint64_t rb = (uint64_t)rest.x | ((uint64_t)(rest.y & 0xFFFFu) << 32);
+      nch = (uint32_t)((rb + rest.z - (rb & ~3ull) + kChunk - 1) / kChunk);
+    }
+    m = mult;
+    nev = (unsigned long long)meta.z * mult;
+  }
+  uint32_t inc = nch, inc_m = m;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t x = __shfl_up_sync(full, inc, o);
+    const uint32_t y = __shfl_up_sync(full, inc_m, o);
+    if (lane >= o) {
+      inc += x;
+      inc_m += y;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nev += __shfl_xor_sync(full, nev, o);
+  const uint32_t tot = __shfl_sync(full, inc, 31);
+  const uint32_t tot_m = __shfl_sync(full, inc_m, 31);
+  const int q = (int)(t % 3);
+  unsigned long long base = 0, rbase = 0;
+  if (lane == 0) {
+    if (tot) base = atomicAdd(sb.ctr3 + q, (unsigned long long)tot);
+    rbase = atomicAdd(sb.rec_count, (unsigned long long)tot_m);
+    atomicAdd(sb.events, nev);
+  }
+  base = __shfl_sync(full, base, 0);
+  rbase = __shfl_sync(full, rbase, 0);
+  if (nch) {
+    uint4* const wi = sb.wi3[q];
+    const unsigned long long first = base + inc - nch;
+    for (uint32_t c = 0; c < nch; ++c) {
+      wi[2 * (first + c)] = make_uint4(word, c, rest.x, rest.y);
+      wi[2 * (first + c) + 1] = make_uint4(rest.z, rest.w, 0u, 0u);
+    }
+  }
+  if (spk && sb.rec_cap > 0) {
+    const unsigned long long r0 = rbase + inc_m - m;
+    for (uint32_t k = 0; k < m; ++k) {
+      if (r0 + k < (unsigned long long)sb.rec_cap) {
+        sb.rec_id[r0 + k] = gid;
+        sb.rec_step[r0 + k] = t;
+      } else {
+        atomicOr(sb.err, kErrRecordOverflow);
+      }
+    }
   }
 }
 

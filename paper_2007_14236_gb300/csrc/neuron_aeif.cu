@@ -109,7 +109,9 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
   if ((threadIdx.x & 31) == 0 && nsub) atomicAdd(sb.substeps, nsub);
   const uint32_t mult = nspk > 63u ? 63u : nspk;
   if (kMode == kEmitAge) emit_spikes_age(done && nspk > 0, gid, mult, t, csr, sb);
-  else if (kMode == kEmitPipe) emit_spikes_pipe<kFixed>(done && nspk > 0, gid, mult, t, meta, csr, ring, sb);
+  else if (kMode == kEmitPipe)
+    emit_spikes_pipe<kFixed>(done && nspk > 0, gid, mult, t, meta,
+                             (done && nspk > 0) ? __ldg(csr.src_age + gid) : make_uint2(0, 0), csr, ring, sb);
   else emit_spikes(done && nspk > 0, gid, mult, t, meta, sb);
 }
 
@@ -173,7 +175,9 @@ __global__ void __launch_bounds__(kAeifBlock) k_aeif_finish(const __grid_constan
     if (lane == 0 && nsub) atomicAdd(sb.substeps, nsub);
     const uint32_t mult = nspk > 63u ? 63u : nspk;
     if (kMode == kEmitAge) emit_spikes_age(nspk > 0, gid, mult, t, csr, sb);
-    else if (kMode == kEmitPipe) emit_spikes_pipe<kFixed>(nspk > 0, gid, mult, t, meta, csr, ring, sb);
+    else if (kMode == kEmitPipe)
+      emit_spikes_pipe<kFixed>(nspk > 0, gid, mult, t, meta, nspk > 0 ? __ldg(csr.src_age + gid) : make_uint2(0, 0),
+                               csr, ring, sb);
     else emit_spikes(nspk > 0, gid, mult, t, meta, sb);
   }
 }

@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(kLifBlock, kNpt > 1 ? (kMode == kEmitPipe ? 2 
   float y[kNpt], I[kNpt];
   int32_t ref[kNpt];
   uint4 meta[kNpt];
+  uint2 ag[kNpt];
 #pragma unroll
   for (int j = 0; j < kNpt; ++j) {
     const int64_t k = k0 + j * kLifBlock;
@@ -54,11 +55,13 @@ __global__ void __launch_bounds__(kLifBlock, kNpt > 1 ? (kMode == kEmitPipe ? 2 
     I[j] = 0.0f;
     ref[j] = 0;
     meta[j] = make_uint4(0, 0, 0, 0);
+    ag[j] = make_uint2(0, 0);
     if (k < sg.n) {
       y[j] = y_[gid];
       I[j] = I_[gid];
       ref[j] = ref_[gid];
       if (!kAge) meta[j] = __ldg(csr.src_meta + gid);
+      if (kMode == kEmitPipe) ag[j] = __ldg(csr.src_age + gid);
     }
   }
   for (uint32_t i = threadIdx.x; i < sg.n_thr; i += kLifBlock) s_thr[i] = __ldg(thr + sg.thr_off + i);
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(kLifBlock, kNpt > 1 ? (kMode == kEmitPipe ? 2 
       ref_[gid] = ref[j];
     }
     if (kMode == kEmitAge) emit_spikes_age(spk, gid, 1u, t, csr, sb);
-    else if (kMode == kEmitPipe) emit_spikes_pipe<kFixed>(spk, gid, 1u, t, meta[j], csr, ring, sb);
+    else if (kMode == kEmitPipe) emit_spikes_pipe<kFixed>(spk, gid, 1u, t, meta[j], ag[j], csr, ring, sb);
     else emit_spikes(spk, gid, 1u, t, meta[j], sb);
   }
 }
