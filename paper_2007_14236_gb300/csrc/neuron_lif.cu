@@ -33,7 +33,7 @@ namespace ngb {
 // and each thread issues the loads of all its neurons before the first use,
 // so that enough bytes are in flight to cover the memory latency.
 template <bool kFixed, int kMode, int kNpt>
-__global__ void __launch_bounds__(kLifBlock, kNpt > 1 ? (kMode == kEmitPipe ? 2 : 3) : (kMode == kEmitRing ? 8 : 6))
+__global__ void __launch_bounds__(kLifBlock, kNpt > 1 ? (kMode == kEmitPipe ? 2 : 3) : (kMode == kEmitRing ? 8 : (kMode == kEmitPipe ? 5 : 6)))
     k_update_lif(const __grid_constant__ SegTable<LifSeg> T, const uint32_t* __restrict__ thr,
                  float* __restrict__ y_, float* __restrict__ I_, int32_t* __restrict__ ref_, Ring ring, int64_t* clk,
                  int64_t step_off, const Csr csr, SpikeBuf sb, int scan) {
