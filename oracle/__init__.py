@@ -15,7 +15,8 @@ from . import build as _build
 
 _lib = None
 
-_VAR = {"V_m": 0, "I_syn": 1, "w": 1, "g_ex": 2, "g_in": 3, "refractory": 4, "h": 5, "dg_ex": 6, "dg_in": 7}
+_VAR = {"V_m": 0, "I_syn": 1, "w": 1, "g_ex": 2, "g_in": 3, "refractory": 4, "h": 5, "dg_ex": 6, "dg_in": 7,
+        "g_0": 2, "g_1": 3, "g_2": 8, "g_3": 9, "x_0": 6, "x_1": 7, "x_2": 10, "x_3": 11}
 
 
 def lib():
@@ -118,10 +119,15 @@ def _lif_vec(p):
 
 
 def _aeif_vec(p, fp64):
-    return [p.C_m, p.g_L, p.E_L, p.V_T, p.Delta_T, p.a, p.b, p.tau_w, p.V_peak, p.V_reset, p.E_ex, p.E_in,
-            p.tau_ex, p.tau_in, p.I_e, p.V_init_mean, p.V_init_sd, p.w_init, p.rk_tol, p.rk_h_min,
-            p.rk_h_init, float(p.rk_max_substeps), p.poisson.n_inputs, p.poisson.rate_hz, p.poisson.weight,
-            p.poisson.receptor, 1.0 if fp64 else 0.0]
+    v = [p.C_m, p.g_L, p.E_L, p.V_T, p.Delta_T, p.a, p.b, p.tau_w, p.V_peak, p.V_reset, p.E_ex, p.E_in,
+         p.tau_ex, p.tau_in, p.I_e, p.V_init_mean, p.V_init_sd, p.w_init, p.rk_tol, p.rk_h_min,
+         p.rk_h_init, float(p.rk_max_substeps), p.poisson.n_inputs, p.poisson.rate_hz, p.poisson.weight,
+         p.poisson.receptor, 1.0 if fp64 else 0.0]
+    # beta multisynapse ports: count, E_rev[4], tau_rise[4], tau_decay[4]
+    ports = list(p.ports or [])
+    pad = ports + [(0.0, 1.0, 1.0)] * (4 - len(ports))
+    v += [float(len(ports))] + [q[0] for q in pad] + [q[1] for q in pad] + [q[2] for q in pad]
+    return v
 
 
 class OracleNet:
@@ -142,7 +148,7 @@ class OracleNet:
                 _check(L.ora_add_population(self.h, p.instance, 0, p.n, v.ctypes.data_as(C.POINTER(C.c_double))))
             else:
                 v = np.array(_aeif_vec(p.params, adex_fp64), dtype=np.float64)
-                model = 2 if p.model == "aeif_cond_alpha" else 1
+                model = {"aeif_cond_alpha": 2, "aeif_cond_beta": 3}.get(p.model, 1)
                 _check(L.ora_add_population(self.h, p.instance, model, p.n,
                                             v.ctypes.data_as(C.POINTER(C.c_double))))
         for c in spec.conns:

@@ -194,6 +194,11 @@ struct AeifPar {
   double pn, prate, pw;
   int prec_rcpt;
   int fp64;
+  // synaptic ports: exponential (model 1) and alpha (model 2) use two, (E_ex, tau_ex) and
+  // (E_in, tau_in); the beta multisynapse model (3) up to four with their own E, rise and decay
+  int n_ports;
+  double E[4], tau_r[4], tau_d[4];
+  double g0[4];  // jump of x per unit input weight: the peak of g equals the weight
 };
 
 struct Population {
@@ -253,7 +258,8 @@ struct ora_net {
   int R = 1;
   // per-neuron state (double arrays; FP32 models keep float-representable values)
   std::vector<double> s0, s1, s2, s3, s4;  // LIF: y, I, ref | AdEx: V, w, gex, gin, h
-  std::vector<double> s5, s6;              // AdEx with alpha conductances: dg_ex, dg_in
+  std::vector<double> s5, s6;              // AdEx alpha / beta: x of ports 0, 1
+  std::vector<double> s7, s8, s9, s10;     // AdEx beta: g of ports 2, 3, x of ports 2, 3
   std::vector<int> pop_of;
   // ring[(slot * R + r) * N + i]
   std::vector<float> ring;
@@ -378,39 +384,77 @@ void generate(const ora_net* net, const Call& c, std::vector<Synapse>& out) {
 }
 
 // The AdEx system (Eqs. 3-5) with the synaptic conductances as state:
-// y = {V, w, g_ex, g_in, dg_ex, dg_in}.  Exponential conductances (alpha =
-// false): dg/dt = -g / tau, the last two components stay 0.  Alpha-function
-// conductances (the paper's balanced network, Sec. 2.4): g(t) = W (t/tau)
-// e^(1 - t/tau) after a spike of weight W, generated by dg/dt = x - g/tau,
-// dx/dt = -x/tau with x jumping by W e / tau at the spike.
-constexpr int kAdexN = 6;
+// y = {V, w, g_0 .. g_3, x_0 .. x_3} for up to four synaptic ports (unused
+// ports stay 0).  Exponential conductances (model 1): g' = -g / tau.
+// Alpha-function conductances (model 2, the paper's balanced network, Sec.
+// 2.4): g(t) = W (t/tau) e^(1 - t/tau) after a spike of weight W, generated
+// by g' = x - g/tau, x' = -x/tau with x jumping by W e / tau at the spike.
+// Beta-function conductances (model 3, the multisynapse model of the paper's
+// interface example, Sec. 2.1): g' = x - g/tau_decay, x' = -x/tau_rise, x
+// jumping by W g0 with g0 chosen so that the peak of g equals W.
+constexpr int kAdexN = 10;
 constexpr double kEuler = 2.718281828459045;  // e
 
 template <typename T>
 struct AdexSystem {
-  T g_L, E_L, V_T, Delta_T, inv_Delta_T, a, inv_tau_w, V_peak, E_ex, E_in, inv_tau_ex, inv_tau_in, I_e,
-      inv_C;
-  bool alpha;
+  T g_L, E_L, V_T, Delta_T, inv_Delta_T, a, inv_tau_w, V_peak, I_e, inv_C;
+  int n_ports;
+  bool rise;  // alpha / beta: g driven by x
+  T E[4], inv_tau_r[4], inv_tau_d[4];
   void deriv(const T y[kAdexN], T f[kAdexN]) const {
     const T V = std::min(y[0], V_peak);  // the exponential is evaluated at most at V_peak
     const T I_spike = (Delta_T > T(0)) ? g_L * Delta_T * std::exp((V - V_T) * inv_Delta_T) : T(0);
     // reading of Eq. 4: I_syn = sum_i g_i (E_rev,i - V), so excitation depolarises
-    const T I_syn = y[2] * (E_ex - V) + y[3] * (E_in - V);
+    T I_syn = T(0);
+    for (int k = 0; k < n_ports; ++k) I_syn = I_syn + y[2 + k] * (E[k] - V);
     f[0] = (-g_L * (V - E_L) + I_spike + I_syn - y[1] + I_e) * inv_C;
     f[1] = (a * (V - E_L) - y[1]) * inv_tau_w;
-    if (alpha) {
-      f[2] = y[4] - y[2] * inv_tau_ex;
-      f[3] = y[5] - y[3] * inv_tau_in;
-      f[4] = -y[4] * inv_tau_ex;
-      f[5] = -y[5] * inv_tau_in;
-    } else {
-      f[2] = -y[2] * inv_tau_ex;
-      f[3] = -y[3] * inv_tau_in;
-      f[4] = T(0);
-      f[5] = T(0);
+    for (int k = 0; k < 4; ++k) {
+      if (k >= n_ports) {
+        f[2 + k] = T(0);
+        f[6 + k] = T(0);
+      } else if (rise) {
+        f[2 + k] = y[6 + k] - y[2 + k] * inv_tau_d[k];
+        f[6 + k] = -y[6 + k] * inv_tau_r[k];
+      } else {
+        f[2 + k] = -y[2 + k] * inv_tau_d[k];
+        f[6 + k] = T(0);
+      }
     }
   }
 };
+
+template <typename T>
+AdexSystem<T> adex_system(const AeifPar& q, int model) {
+  AdexSystem<T> s;
+  s.g_L = T(q.g_L);
+  s.E_L = T(q.E_L);
+  s.V_T = T(q.V_T);
+  s.Delta_T = T(q.Delta_T);
+  s.inv_Delta_T = T(1.0 / q.Delta_T);
+  s.a = T(q.a);
+  s.inv_tau_w = T(1.0 / q.tau_w);
+  s.V_peak = T(q.V_peak);
+  s.I_e = T(q.I_e);
+  s.inv_C = T(1.0 / q.C_m);
+  s.n_ports = q.n_ports;
+  s.rise = model != 1;
+  for (int k = 0; k < 4; ++k) {
+    s.E[k] = T(q.E[k]);
+    s.inv_tau_r[k] = T(1.0 / q.tau_r[k]);
+    s.inv_tau_d[k] = T(1.0 / q.tau_d[k]);
+  }
+  return s;
+}
+
+// Jump of x per unit weight so that g peaks at the weight: e / tau for equal
+// rise and decay, else (1/tau_r - 1/tau_d) / (e^(-t_p/tau_d) - e^(-t_p/tau_r))
+// with the time of the peak t_p = tau_d tau_r ln(tau_d / tau_r) / (tau_d - tau_r).
+double beta_normalisation(double tau_r, double tau_d) {
+  if (tau_r == tau_d) return kEuler / tau_d;
+  const double tp = tau_d * tau_r * std::log(tau_d / tau_r) / (tau_d - tau_r);
+  return (1.0 / tau_r - 1.0 / tau_d) / (std::exp(-tp / tau_d) - std::exp(-tp / tau_r));
+}
 
 // One embedded Cash-Karp step from y over h: the fifth-order solution in y5
 // and its difference to the fourth-order one in err.
@@ -447,7 +491,8 @@ void ck_step(const AdexSystem<T>& sys, const Tableau& tab, const T y[kAdexN], co
 template <typename T>
 int adex_advance(const AdexSystem<T>& sys, const Tableau& tab, const AeifPar& p, double dt, double tol,
                  T y[kAdexN], double& h, int64_t& substeps, int64_t& cap_hits) {
-  const T floor_[kAdexN] = {T(1.0), T(1.0), T(1e-3), T(1e-3), T(1e-3), T(1e-3)};
+  const T floor_[kAdexN] = {T(1.0), T(1.0), T(1e-3), T(1e-3), T(1e-3), T(1e-3), T(1e-3), T(1e-3), T(1e-3),
+                            T(1e-3)};
   int spikes = 0;
   double t_in = 0.0;
   int64_t n = 0;
@@ -534,7 +579,7 @@ int32_t ora_add_instance(ora_net* net, uint64_t seed) {
 int32_t ora_add_population(ora_net* net, int32_t instance, int32_t model, int64_t n, const double* p) {
   if (!net || net->finalized) return fail("ora_add_population: bad state");
   if (instance < 0 || instance >= (int32_t)net->inst.size()) return fail("ora_add_population: instance");
-  if (n <= 0 || n > 0x7FFFFFFF || model < 0 || model > 2) return fail("ora_add_population: n/model");
+  if (n <= 0 || n > 0x7FFFFFFF || model < 0 || model > 3) return fail("ora_add_population: n/model");
   Population P;
   std::memset(&P, 0, sizeof(P));
   P.model = model;
@@ -570,9 +615,31 @@ int32_t ora_add_population(ora_net* net, int32_t instance, int32_t model, int64_
     if (!(q.C_m > 0 && q.tau_w > 0 && q.tau_ex > 0 && q.tau_in > 0 && q.tol > 0 && q.h_min > 0 &&
           q.h_init > 0 && q.max_sub > 0))
       return fail("ora: AdEx params");
+    if (model == 3) {
+      // beta multisynapse: p[27] ports, p[28..31] E_rev, p[32..35] tau_rise, p[36..39] tau_decay
+      q.n_ports = (int)p[27];
+      if (q.n_ports < 1 || q.n_ports > 4) return fail("ora: beta ports");
+      for (int k = 0; k < 4; ++k) {
+        q.E[k] = k < q.n_ports ? p[28 + k] : 0.0;
+        q.tau_r[k] = k < q.n_ports ? p[32 + k] : 1.0;
+        q.tau_d[k] = k < q.n_ports ? p[36 + k] : 1.0;
+        if (!(q.tau_r[k] > 0 && q.tau_d[k] > 0)) return fail("ora: beta time constants");
+        q.g0[k] = beta_normalisation(q.tau_r[k], q.tau_d[k]);
+      }
+    } else {
+      q.n_ports = 2;
+      q.E[0] = q.E_ex;
+      q.E[1] = q.E_in;
+      q.tau_r[0] = q.tau_d[0] = q.tau_ex;
+      q.tau_r[1] = q.tau_d[1] = q.tau_in;
+      q.E[2] = q.E[3] = 0.0;
+      q.tau_r[2] = q.tau_r[3] = q.tau_d[2] = q.tau_d[3] = 1.0;
+      for (int k = 0; k < 4; ++k) q.g0[k] = kEuler / q.tau_d[k];
+    }
+    if (q.prec_rcpt < 0 || q.prec_rcpt >= q.n_ports) return fail("ora: Poisson receptor");
     P.lambda = q.pn * q.prate * dt * 1e-3;
     P.w_ext = (float)q.pw;
-    net->R = 2;
+    net->R = std::max(net->R, std::max(2, q.n_ports));
   }
   if (!(P.lambda >= 0.0 && P.lambda <= 100.0)) return fail("ora: Poisson mean per step must be in [0,100]");
   net->pops.push_back(P);
@@ -591,8 +658,12 @@ int32_t ora_connect(ora_net* net, int32_t src_pop, int32_t tgt_pop, int32_t rule
   if (K < 0 || rule < 0 || rule > 4) return fail("ora_connect: rule/K");
   if (rule == 3 && (net->pops[src_pop].n != net->pops[tgt_pop].n || (src_pop == tgt_pop && !allow_autapses)))
     return fail("ora_connect: one-to-one sizes");
-  if (receptor < 0 || receptor > 1) return fail("ora_connect: receptor");
-  if (receptor == 1 && net->pops[tgt_pop].model == 0) return fail("ora_connect: LIF has one receptor");
+  if (receptor < 0 || receptor > 3) return fail("ora_connect: receptor");
+  {
+    const Population& pt = net->pops[tgt_pop];
+    const int ports = pt.model == 0 ? 1 : pt.aeif.n_ports;
+    if (receptor >= ports) return fail("ora_connect: receptor beyond the target's synaptic ports");
+  }
   if (src_pop == tgt_pop && !allow_autapses && net->pops[src_pop].n < 2 && K > 0)
     return fail("ora_connect: no admissible source without autapses");
   Instance& I = net->inst[net->pops[src_pop].instance];
@@ -641,6 +712,8 @@ int32_t ora_finalize(ora_net* net) {
   net->s0.assign((size_t)N, 0.0); net->s1.assign((size_t)N, 0.0); net->s2.assign((size_t)N, 0.0);
   net->s3.assign((size_t)N, 0.0); net->s4.assign((size_t)N, 0.0);
   net->s5.assign((size_t)N, 0.0); net->s6.assign((size_t)N, 0.0);
+  net->s7.assign((size_t)N, 0.0); net->s8.assign((size_t)N, 0.0);
+  net->s9.assign((size_t)N, 0.0); net->s10.assign((size_t)N, 0.0);
   net->pop_of.assign((size_t)N, 0);
   for (size_t pi = 0; pi < net->pops.size(); ++pi) {
     const Population& P = net->pops[pi];
@@ -697,7 +770,7 @@ int32_t ora_simulate(ora_net* net, int64_t steps) {
       const uint64_t seed = net->inst[P.instance].seed;
       for (int64_t k = 0; k < P.n; ++k) {
         const int64_t i = P.offset + k;
-        float in[2] = {0.0f, 0.0f};
+        float in[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int r = 0; r < net->R; ++r) {
           const int64_t idx = ring_index(net, t, r, i);
           if (net->deterministic) {
@@ -742,45 +815,34 @@ int32_t ora_simulate(ora_net* net, int64_t steps) {
           net->s2[(size_t)i] = ref;
         } else {
           const AeifPar& q = P.aeif;
-          const bool alpha = P.model == 2;
+          const bool rise = P.model != 1;
           double h = net->s4[(size_t)i];
+          const size_t u = (size_t)i;
           if (q.fp64) {
-            AdexSystem<double> sys{q.g_L, q.E_L, q.V_T, q.Delta_T, 1.0 / q.Delta_T, q.a, 1.0 / q.tau_w,
-                                   q.V_peak, q.E_ex, q.E_in, 1.0 / q.tau_ex, 1.0 / q.tau_in, q.I_e,
-                                   1.0 / q.C_m, alpha};
-            double y[kAdexN] = {net->s0[(size_t)i], net->s1[(size_t)i], net->s2[(size_t)i], net->s3[(size_t)i],
-                                net->s5[(size_t)i], net->s6[(size_t)i]};
+            const AdexSystem<double> sys = adex_system<double>(q, P.model);
+            double y[kAdexN] = {net->s0[u], net->s1[u], net->s2[u], net->s3[u], net->s7[u],
+                                net->s8[u], net->s5[u], net->s6[u], net->s9[u], net->s10[u]};
             nspk = adex_advance<double>(sys, tab, q, net->dt, q.tol, y, h, net->rk_substeps, net->rk_cap_hits);
-            // input of step t: a conductance jump (exponential), or a jump of dg/dt by W e / tau (alpha)
-            if (alpha) {
-              y[4] += (double)in[0] * (kEuler / q.tau_ex);
-              y[5] += (double)in[1] * (kEuler / q.tau_in);
-            } else {
-              y[2] += (double)in[0];
-              y[3] += (double)in[1];
+            // input of step t: a conductance jump (exponential), or a jump of x by W g0 (alpha, beta)
+            for (int k = 0; k < q.n_ports; ++k) {
+              if (rise) y[6 + k] += (double)in[k] * q.g0[k];
+              else y[2 + k] += (double)in[k];
             }
-            net->s0[(size_t)i] = y[0]; net->s1[(size_t)i] = y[1];
-            net->s2[(size_t)i] = y[2]; net->s3[(size_t)i] = y[3];
-            net->s5[(size_t)i] = y[4]; net->s6[(size_t)i] = y[5];
+            net->s0[u] = y[0]; net->s1[u] = y[1]; net->s2[u] = y[2]; net->s3[u] = y[3]; net->s7[u] = y[4];
+            net->s8[u] = y[5]; net->s5[u] = y[6]; net->s6[u] = y[7]; net->s9[u] = y[8]; net->s10[u] = y[9];
           } else {
-            AdexSystem<float> sys{(float)q.g_L, (float)q.E_L, (float)q.V_T, (float)q.Delta_T,
-                                  (float)(1.0 / q.Delta_T), (float)q.a, (float)(1.0 / q.tau_w),
-                                  (float)q.V_peak, (float)q.E_ex, (float)q.E_in, (float)(1.0 / q.tau_ex),
-                                  (float)(1.0 / q.tau_in), (float)q.I_e, (float)(1.0 / q.C_m), alpha};
-            float y[kAdexN] = {(float)net->s0[(size_t)i], (float)net->s1[(size_t)i], (float)net->s2[(size_t)i],
-                               (float)net->s3[(size_t)i], (float)net->s5[(size_t)i], (float)net->s6[(size_t)i]};
+            const AdexSystem<float> sys = adex_system<float>(q, P.model);
+            float y[kAdexN] = {(float)net->s0[u], (float)net->s1[u], (float)net->s2[u], (float)net->s3[u],
+                               (float)net->s7[u], (float)net->s8[u], (float)net->s5[u], (float)net->s6[u],
+                               (float)net->s9[u], (float)net->s10[u]};
             const double tol_eff = std::max(q.tol, 8.0 * 0x1p-24);
             nspk = adex_advance<float>(sys, tab, q, net->dt, tol_eff, y, h, net->rk_substeps, net->rk_cap_hits);
-            if (alpha) {
-              y[4] = y[4] + in[0] * (float)(kEuler / q.tau_ex);
-              y[5] = y[5] + in[1] * (float)(kEuler / q.tau_in);
-            } else {
-              y[2] = y[2] + in[0];
-              y[3] = y[3] + in[1];
+            for (int k = 0; k < q.n_ports; ++k) {
+              if (rise) y[6 + k] = y[6 + k] + in[k] * (float)q.g0[k];
+              else y[2 + k] = y[2 + k] + in[k];
             }
-            net->s0[(size_t)i] = y[0]; net->s1[(size_t)i] = y[1];
-            net->s2[(size_t)i] = y[2]; net->s3[(size_t)i] = y[3];
-            net->s5[(size_t)i] = y[4]; net->s6[(size_t)i] = y[5];
+            net->s0[u] = y[0]; net->s1[u] = y[1]; net->s2[u] = y[2]; net->s3[u] = y[3]; net->s7[u] = y[4];
+            net->s8[u] = y[5]; net->s5[u] = y[6]; net->s6[u] = y[7]; net->s9[u] = y[8]; net->s10[u] = y[9];
             h = (double)(float)h;  // the step-size proposal is carried in FP32 between steps
           }
           net->s4[(size_t)i] = h;
@@ -874,6 +936,10 @@ int32_t ora_get_state(const ora_net* net, int32_t var, double* out) {
       else if (var == 5) v = net->s4[(size_t)i];
       else if (var == 6) v = net->s5[(size_t)i];
       else if (var == 7) v = net->s6[(size_t)i];
+      else if (var == 8) v = net->s7[(size_t)i];   // beta: g of port 2
+      else if (var == 9) v = net->s8[(size_t)i];   // g of port 3
+      else if (var == 10) v = net->s9[(size_t)i];  // x of port 2
+      else if (var == 11) v = net->s10[(size_t)i]; // x of port 3
     }
     out[i] = v;
   }

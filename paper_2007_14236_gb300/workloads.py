@@ -27,6 +27,7 @@ import numpy as np
 LIF = "lif_psc_exp"
 AEIF = "aeif_cond_exp"
 AEIF_ALPHA = "aeif_cond_alpha"  # AdEx with alpha-function conductances
+AEIF_BETA = "aeif_cond_beta"    # multisynapse AdEx with beta-function conductances
 INDEGREE = "fixed_indegree"
 TOTAL = "fixed_total_number"
 OUTDEGREE = "fixed_outdegree"
@@ -83,6 +84,9 @@ class AeifParams:
     rk_max_substeps: int = 10000
     rk_control_fp32: bool = False
     poisson: Poisson = field(default_factory=Poisson)
+    # AEIF_BETA only: up to four synaptic ports (E_rev mV, tau_rise ms, tau_decay ms); the
+    # E_ex / E_in / tau_ex / tau_in fields are then unused
+    ports: Optional[List[Tuple[float, float, float]]] = None
 
 
 @dataclass

@@ -18,6 +18,12 @@
   (peak W at t = tau) at every grid point; the subthreshold response to inputs
   on both receptors and a spiking run match DOP853 on the same six-variable
   system.
+* Beta-function multisynapse conductances (the paper's interface example,
+  Sec. 2.1): the conductance after one input follows the closed form
+  W (e^(-t/tau_d) - e^(-t/tau_r)) normalised to a peak of W (the peak found
+  numerically in the test); with equal rise and decay times the model equals
+  the alpha model bit for bit; three inputs on three ports (Fig. 9 setting)
+  match DOP853 on the eight-variable system.
 """
 import math
 
@@ -223,3 +229,74 @@ def test_alpha_spiking_matches_dop853():
     assert np.array_equal(sp_o, sp_s), (sp_o, sp_s)
     m = _away_from_spikes(steps, sp_s)
     assert np.abs(V_o - V_s)[m].max() <= 1e-5
+
+
+def _beta(ports, **kw):
+    par = _table2(**kw)
+    par.ports = ports
+    return par
+
+
+def test_beta_conductance_closed_form_and_peak():
+    tr, td, Wt, k0 = 0.5, 3.0, 2.5, 10
+    par = _beta([(0.0, tr, td)], I_e=0.0)
+    out, _ = _oracle_trace(par, 200, fp64=True, injections=[(k0, 0, Wt)], model=W.AEIF_BETA,
+                           record=("g_0", "x_0"))
+    t = (np.arange(200) - k0) * DT
+    shape = lambda tt: np.exp(-tt / td) - np.exp(-tt / tr)
+    fine = np.linspace(0.0, 20.0, 2_000_001)
+    norm = Wt / shape(fine).max()  # the factor that makes the peak equal to W, found numerically
+    ref = np.where(t > 0, norm * shape(np.maximum(t, 0.0)), 0.0)
+    assert np.abs(out["g_0"] - ref).max() <= 1e-7 * Wt
+    t_peak = td * tr * np.log(td / tr) / (td - tr)
+    assert abs(out["g_0"].max() - Wt) <= Wt * 1e-3 and abs(np.argmax(out["g_0"]) - (k0 + t_peak / DT)) <= 1
+
+
+def test_beta_with_equal_times_is_the_alpha_model():
+    alpha = _table2(I_e=450.0, tau_ex=1.0, tau_in=2.0,
+                    poisson=W.Poisson(n_inputs=1.0, rate_hz=20000.0, weight=0.37, receptor=0))
+    beta = _table2(I_e=450.0, poisson=W.Poisson(n_inputs=1.0, rate_hz=20000.0, weight=0.37, receptor=0))
+    beta.ports = [(alpha.E_ex, 1.0, 1.0), (alpha.E_in, 2.0, 2.0)]
+    ra = _oracle_trace(alpha, 800, fp64=False, model=W.AEIF_ALPHA, record=("V_m", "g_0", "x_0"))
+    rb = _oracle_trace(beta, 800, fp64=False, model=W.AEIF_BETA, record=("V_m", "g_0", "x_0"))
+    assert len(ra[1]) >= 3 and np.array_equal(ra[1], rb[1])
+    for v in ("V_m", "g_0", "x_0"):
+        assert np.array_equal(ra[0][v], rb[0][v])
+
+
+def test_beta_three_ports_subthreshold_match_dop853():
+    integ = pytest.importorskip("scipy.integrate")
+    ports = [(0.0, 0.3, 2.0), (-85.0, 1.0, 5.0), (0.0, 2.0, 8.0)]
+    par = _beta(ports, I_e=0.0)
+    inj = [(50, 0, 3.0), (150, 1, 4.0), (250, 2, 2.0)]
+    steps = 450
+    V_o, sp_o = _oracle_trace(par, steps, fp64=True, injections=inj, model=W.AEIF_BETA)
+    p = par
+
+    def rhs(tt, y):
+        V = min(y[0], p.V_peak)
+        I_syn = sum(y[2 + k] * (ports[k][0] - V) for k in range(3))
+        f = [(-p.g_L * (V - p.E_L) + p.g_L * p.Delta_T * math.exp((V - p.V_T) / p.Delta_T) + I_syn - y[1]) / p.C_m,
+             (p.a * (V - p.E_L) - y[1]) / p.tau_w]
+        f += [y[5 + k] - y[2 + k] / ports[k][2] for k in range(3)]
+        f += [-y[5 + k] / ports[k][1] for k in range(3)]
+        return f
+
+    def peak_factor(tr, td):  # the factor that makes the peak of g equal to the weight, numerically
+        tt = np.linspace(0, 50, 2_000_001)
+        g = (np.exp(-tt / td) - np.exp(-tt / tr)) / (1 / tr - 1 / td)
+        return 1.0 / g.max()
+    fac = [peak_factor(tr, td) for _, tr, td in ports]
+    y = np.array([p.V_init_mean, 0.0] + [0.0] * 6)
+    V_s = np.zeros(steps)
+    injd = {s_: (r, w_) for s_, r, w_ in inj}
+    for k in range(steps):
+        sol = integ.solve_ivp(rhs, (k * DT, (k + 1) * DT), y, method="DOP853", rtol=1e-12, atol=1e-12)
+        y = sol.y[:, -1].copy()
+        if k in injd:
+            r, w_ = injd[k]
+            y[5 + r] += w_ * fac[r]
+        V_s[k] = y[0]
+    assert len(sp_o) == 0
+    assert np.abs(V_o - V_s).max() <= 1e-4
+    assert V_o[80] > V_o[45] + 0.1 and V_o[200] < V_o[145] - 0.1 and V_o[300] > V_o[245] + 0.05
