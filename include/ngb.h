@@ -62,8 +62,20 @@ typedef enum { NGB_WEIGHT_FP32 = 0, NGB_WEIGHT_BF16 = 1, NGB_WEIGHT_FP16 = 2 } n
 /* Neuron models: LIF with exponential PSCs (Eqs. 1-2); AdEx (Eqs. 3-5) with
  * exponential conductances; AdEx with alpha-function conductances (the
  * paper's balanced network, Sec. 2.4: an input of weight W gives
- * g(t) = W (t/tau) e^(1 - t/tau), peak W at t = tau). */
-typedef enum { NGB_LIF_PSC_EXP = 0, NGB_AEIF_COND_EXP = 1, NGB_AEIF_COND_ALPHA = 2 } ngb_model;
+ * g(t) = W (t/tau) e^(1 - t/tau), peak W at t = tau); the multisynapse AdEx
+ * of the paper's interface example (Sec. 2.1) with 1-4 receptor ports of
+ * beta-function conductances: port k has reversal potential E_k, rise time
+ * tau_r,k and decay time tau_d,k, g_k' = x_k - g_k / tau_d,k,
+ * x_k' = -x_k / tau_r,k, and an input of weight W raises x_k by W g0_k with
+ * g0_k set so that g_k peaks at W (the alpha function when tau_r = tau_d).
+ * Beta populations run in the per-step kernel loops (graph, pipelined); a
+ * handle holding one never uses the persistent or fused loop. */
+typedef enum {
+  NGB_LIF_PSC_EXP = 0,
+  NGB_AEIF_COND_EXP = 1,
+  NGB_AEIF_COND_ALPHA = 2,
+  NGB_AEIF_COND_BETA = 3
+} ngb_model;
 typedef enum {
   NGB_RULE_FIXED_INDEGREE = 0,
   NGB_RULE_FIXED_TOTAL_NUMBER = 1,
@@ -91,8 +103,12 @@ typedef enum {
   NGB_VAR_G_IN = 3,    /* AdEx: inhibitory conductance, nS */
   NGB_VAR_REFRACT = 4, /* LIF: refractory steps left */
   NGB_VAR_H = 5,       /* AdEx: carried Runge-Kutta step proposal, ms */
-  NGB_VAR_DG_EX = 6,   /* AdEx alpha: x_ex with g_ex' = x_ex - g_ex / tau_ex, nS/ms */
-  NGB_VAR_DG_IN = 7    /* AdEx alpha: x_in, nS/ms */
+  NGB_VAR_DG_EX = 6,   /* AdEx alpha: x_ex with g_ex' = x_ex - g_ex / tau_ex, nS/ms (beta: x_0) */
+  NGB_VAR_DG_IN = 7,   /* AdEx alpha: x_in, nS/ms (beta: x_1) */
+  NGB_VAR_G_2 = 8,     /* AdEx beta: conductance of port 2, nS (ports 0, 1: G_EX, G_IN) */
+  NGB_VAR_G_3 = 9,     /* AdEx beta: conductance of port 3, nS */
+  NGB_VAR_X_2 = 10,    /* AdEx beta: x of port 2, nS/ms */
+  NGB_VAR_X_3 = 11     /* AdEx beta: x of port 3, nS/ms */
 } ngb_state_var;
 
 /* ------------------------------------------------------------ structures */
@@ -116,7 +132,7 @@ typedef struct {
 /* External Poisson drive of a population (Sec. 2.1, Poisson generator device):
  * every neuron independently receives k ~ Poisson(n_inputs * rate_hz * dt)
  * input spikes per step, each of weight `weight` (pA for LIF, nS for AdEx),
- * on receptor `receptor` (AdEx: 0 excitatory, 1 inhibitory). */
+ * on receptor `receptor` (AdEx: 0 excitatory, 1 inhibitory; beta: the port). */
 typedef struct {
   double n_inputs;
   double rate_hz;
@@ -132,9 +148,12 @@ typedef struct {
   ngb_poisson_drive poisson;
 } ngb_lif_params;
 
-/* AdEx (Eqs. 3-5), for both conductance models (NGB_AEIF_COND_EXP,
- * NGB_AEIF_COND_ALPHA; tau_ex / tau_in are the decay or alpha time
- * constants).  No refractory period.
+/* AdEx (Eqs. 3-5), for the three conductance models.  NGB_AEIF_COND_EXP,
+ * NGB_AEIF_COND_ALPHA: receptors 0 (E_ex, tau_ex) and 1 (E_in, tau_in), the
+ * taus being the decay or alpha time constants.  NGB_AEIF_COND_BETA: ports
+ * 0 .. n_ports-1 with E_rev_mV, tau_rise_ms, tau_decay_ms (E_ex, E_in,
+ * tau_ex, tau_in are not used then; the other two models ignore the port
+ * fields).  No refractory period.
  * rk_tol: relative tolerance of the adaptive Runge-Kutta step; with FP32 state
  * the effective tolerance is max(rk_tol, 8 * 2^-24).  The step size, the time
  * inside the step and the error-ratio test are FP64 unless rk_control_fp32 is
@@ -148,6 +167,9 @@ typedef struct {
   int32_t rk_control_fp32;
   int32_t pad_;
   ngb_poisson_drive poisson;
+  int32_t n_ports; /* NGB_AEIF_COND_BETA: 1..4 */
+  int32_t pad2_;
+  double E_rev_mV[4], tau_rise_ms[4], tau_decay_ms[4];
 } ngb_aeif_params;
 
 /* Connection rule (Sec. 2.1).  FIXED_INDEGREE: every target draws K sources
@@ -177,7 +199,8 @@ typedef struct {
 
 /* Synapse parameters: weight (pA for LIF targets, nS for AdEx targets; an
  * inhibitory AdEx synapse has a positive weight on receptor 1), delay in ms
- * (rounded to the nearest step, ties to even, at least one step). */
+ * (rounded to the nearest step, ties to even, at least one step), receptor
+ * (LIF 0; AdEx 0, 1; beta 0 .. n_ports-1). */
 typedef struct {
   ngb_dist_spec weight;
   ngb_dist_spec delay_ms;
@@ -241,7 +264,8 @@ NGB_API int ngb_connect(ngb_sim* sim, int32_t src_pop, int32_t tgt_pop, const ng
 /* Make the handle a serving handle: reserve pools for max_neurons neurons,
  * max_synapses synapses and max_groups (source, delay) connection groups, a
  * ring of ring_slots (power of two, > every delay in steps) slots and
- * `receptors` receptors (2 if any AdEx instance will come).  Call before the
+ * `receptors` receptors (1-4: at least 2 if any AdEx instance will come,
+ * at least n_ports for beta instances).  Call before the
  * handle is finalised.  Afterwards instances may be added (ngb_add_instance,
  * ngb_add_population_in, ngb_connect) and committed or retired between
  * simulate calls, while the other instances keep running in the same kernels.
@@ -340,8 +364,8 @@ NGB_API int ngb_get_synapses(ngb_sim* sim, int64_t first, int64_t n, uint32_t* t
 /* Device-resident CSR described by caller-owned DEVICE pointers (the layout
  * ngb_finalize builds): src_syn[N+1] first synapse of each source,
  * src_grp[N+1] first delay group of each source, grp_start[G+1] first synapse
- * of each group, grp_delay[G] its delay in steps, tgt[K] target id with the
- * receptor in bit 31, weight[K] in weight_dtype. */
+ * of each group, grp_delay[G] its delay in steps, tgt[K] target id in bits
+ * 0-29 with the receptor in bits 30-31, weight[K] in weight_dtype. */
 typedef struct {
   const uint64_t* src_syn;
   const uint32_t* src_grp;

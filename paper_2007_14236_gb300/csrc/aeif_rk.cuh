@@ -5,7 +5,11 @@
 // State y = {V, w, g_ex, g_in} for exponential conductances; with
 // alpha-function conductances (the paper's balanced network, Sec. 2.4)
 // also {x_ex, x_in}: g' = x - g/tau, x' = -x/tau, so that an input of weight
-// W (x += W e / tau) gives g(t) = W (t/tau) e^(1 - t/tau).
+// W (x += W e / tau) gives g(t) = W (t/tau) e^(1 - t/tau).  The beta
+// multisynapse model (Sec. 2.1) integrates four ports,
+// y = {V, w, g_0..g_3, x_0..x_3} with g_k' = x_k - g_k/tau_d,k and
+// x_k' = -x_k/tau_r,k; ports beyond the population's count stay zero and add
+// nothing to the current or to the error.
 //
 // Cash & Karp (1990) 4(5) tableau; FP32 state and stages; the step size h,
 // the time inside the step and the error-ratio test in FP64 (or FP32 when the
@@ -35,19 +39,38 @@ constexpr float E4 = (float)(125.0 / 594.0 - 13525.0 / 55296.0);
 constexpr float E5 = (float)(-277.0 / 14336.0);
 constexpr float E6 = (float)(512.0 / 1771.0 - 1.0 / 4.0);
 
-// Neuron state in registers: V, w, g_ex, g_in and (alpha conductances) x_ex, x_in.
+// Neuron state in registers: V, w, g_ex, g_in, (alpha, beta) x_ex, x_in and
+// (beta ports 2-3) g_2, g_3, x_2, x_3.
 struct St {
   float V, w, ge, gi, xe, xi;
+  float g2, g3, x2, x3;
 };
+
+// Integrated components per conductance model.
+template <int kM>
+constexpr int kAeifNC = kM == kAeifExp ? 4 : kM == kAeifAlpha ? 6 : 10;
 
 template <int NC>
 __device__ __forceinline__ void deriv(const AeifSeg& p, const float y[NC], float f[NC]) {
   const float V = fminf(y[0], p.V_peak);
   const float I_spk = (p.Delta_T > 0.0f) ? p.g_L * p.Delta_T * expf((V - p.V_T) * p.inv_Delta_T) : 0.0f;
-  const float I_syn = y[2] * (p.E_ex - V) + y[3] * (p.E_in - V);
+  float I_syn;
+  if constexpr (NC == 10) {
+    I_syn = y[2] * (p.E_p[0] - V);
+#pragma unroll
+    for (int k = 1; k < 4; ++k) I_syn += y[2 + k] * (p.E_p[k] - V);
+  } else {
+    I_syn = y[2] * (p.E_ex - V) + y[3] * (p.E_in - V);
+  }
   f[0] = (-p.g_L * (V - p.E_L) + I_spk + I_syn - y[1] + p.I_e) * p.inv_C;
   f[1] = (p.a * (V - p.E_L) - y[1]) * p.inv_tau_w;
-  if constexpr (NC == 6) {
+  if constexpr (NC == 10) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      f[2 + k] = y[6 + k] - y[2 + k] * p.itd_p[k];
+      f[6 + k] = -y[6 + k] * p.itr_p[k];
+    }
+  } else if constexpr (NC == 6) {
     f[2] = y[4] - y[2] * p.inv_tau_ex;
     f[3] = y[5] - y[3] * p.inv_tau_in;
     f[4] = -y[4] * p.inv_tau_ex;
@@ -161,6 +184,13 @@ __device__ __forceinline__ bool aeif_integrate_nc(const AeifSeg& p, St& s, RkPos
   if constexpr (NC == 6) {
     y[4] = s.xe;
     y[5] = s.xi;
+  } else if constexpr (NC == 10) {
+    y[4] = s.g2;
+    y[5] = s.g3;
+    y[6] = s.xe;
+    y[7] = s.xi;
+    y[8] = s.x2;
+    y[9] = s.x3;
   }
   bool done;
   if (p.ctl32) {
@@ -178,40 +208,53 @@ __device__ __forceinline__ bool aeif_integrate_nc(const AeifSeg& p, St& s, RkPos
   if constexpr (NC == 6) {
     s.xe = y[4];
     s.xi = y[5];
+  } else if constexpr (NC == 10) {
+    s.g2 = y[4];
+    s.g3 = y[5];
+    s.xe = y[6];
+    s.xi = y[7];
+    s.x2 = y[8];
+    s.x3 = y[9];
   }
   return done;
 }
 
-// The step's input on the two receptors, after the integration: a
-// conductance jump (exponential), or x += W e / tau (alpha).
-template <bool kAlpha>
-__device__ __forceinline__ void aeif_add_input(const AeifSeg& p, St& s, float in0, float in1) {
-  if (kAlpha) {
-    s.xe = __fadd_rn(s.xe, __fmul_rn(in0, p.e_tau_ex));
-    s.xi = __fadd_rn(s.xi, __fmul_rn(in1, p.e_tau_in));
+// The step's input on the receptors (in.x .. in.w: ports 0-3), after the
+// integration: a conductance jump (exponential), or x += W e / tau (alpha),
+// or x += W g0 (beta, g0 making the peak of g equal to W).
+template <int kM>
+__device__ __forceinline__ void aeif_add_input(const AeifSeg& p, St& s, float4 in) {
+  if (kM == kAeifBeta) {
+    s.xe = __fadd_rn(s.xe, __fmul_rn(in.x, p.jmp_p[0]));
+    s.xi = __fadd_rn(s.xi, __fmul_rn(in.y, p.jmp_p[1]));
+    s.x2 = __fadd_rn(s.x2, __fmul_rn(in.z, p.jmp_p[2]));
+    s.x3 = __fadd_rn(s.x3, __fmul_rn(in.w, p.jmp_p[3]));
+  } else if (kM == kAeifAlpha) {
+    s.xe = __fadd_rn(s.xe, __fmul_rn(in.x, p.e_tau_ex));
+    s.xi = __fadd_rn(s.xi, __fmul_rn(in.y, p.e_tau_in));
   } else {
-    s.ge = __fadd_rn(s.ge, in0);
-    s.gi = __fadd_rn(s.gi, in1);
+    s.ge = __fadd_rn(s.ge, in.x);
+    s.gi = __fadd_rn(s.gi, in.y);
   }
 }
 
 // Integrate one AdEx neuron over (the rest of) a step with at most `budget`
 // attempts (0: no limit); on completion the step's input is added.  Returns
-// whether the step is complete.  kAlpha selects the conductance model.
-template <bool kAlpha>
-__device__ __forceinline__ bool aeif_advance(const AeifSeg& p, St& s, RkPos& r, int budget, float in0, float in1,
+// whether the step is complete.  kM selects the conductance model.
+template <int kM>
+__device__ __forceinline__ bool aeif_advance(const AeifSeg& p, St& s, RkPos& r, int budget, float4 in,
                                              uint32_t& nspk, unsigned long long& nsub, bool& cap_hit) {
-  const bool done = aeif_integrate_nc<kAlpha ? 6 : 4>(p, s, r, budget, nspk, nsub, cap_hit);
-  if (done) aeif_add_input<kAlpha>(p, s, in0, in1);
+  const bool done = aeif_integrate_nc<kAeifNC<kM>>(p, s, r, budget, nspk, nsub, cap_hit);
+  if (done) aeif_add_input<kM>(p, s, in);
   return done;
 }
 
-// A whole step (no attempt budget).
-template <bool kAlpha>
+// A whole step (no attempt budget) of the two-receptor models.
+template <int kM>
 __device__ __forceinline__ void aeif_step(const AeifSeg& p, St& s, double& h, float in0, float in1, uint32_t& nspk,
                                           unsigned long long& nsub, bool& cap_hit) {
   RkPos r{h, 0.0, 0};
-  aeif_advance<kAlpha>(p, s, r, 0, in0, in1, nspk, nsub, cap_hit);
+  aeif_advance<kM>(p, s, r, 0, make_float4(in0, in1, 0.f, 0.f), nspk, nsub, cap_hit);
   h = r.h;
 }
 

@@ -119,7 +119,7 @@ __global__ void k_draw(CallDev c, uint64_t base, unsigned long long* __restrict_
     const uint64_t pos = base + q;
     keys[pos] = ((unsigned long long)src << kDelayBits) | d;
     vals[pos] = (uint32_t)pos;
-    st_tgt[pos] = (c.tgt_off + tgt) | (c.receptor ? kRcptBit : 0u);
+    st_tgt[pos] = (c.tgt_off + tgt) | ((uint32_t)c.receptor << kRcptShift);
     st_w[pos] = w;
     atomicAdd(src_cnt + c.src_off + src, 1ull);
     dmax = d > (uint32_t)dmax ? (int)d : dmax;
@@ -284,8 +284,8 @@ __global__ void k_expand(uint64_t first, uint64_t n, const uint32_t* __restrict_
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
     const uint64_t j = first + i;
     const uint32_t tw = tgt[j];
-    o_tgt[i] = tw & 0x7FFFFFFFu;
-    o_rc[i] = (uint8_t)(tw >> 31);
+    o_tgt[i] = tw & kTgtMask;
+    o_rc[i] = (uint8_t)(tw >> kRcptShift);
     float v;
     if (wdtype == 0) v = reinterpret_cast<const float*>(w)[j];
     else if (wdtype == 1) v = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(w)[j]);

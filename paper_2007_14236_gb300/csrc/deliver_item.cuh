@@ -132,8 +132,8 @@ __device__ __forceinline__ void deliver_work_item(const uint4 a, const uint4 m2,
     if (!any || j < b || j >= e) continue;
     const uint32_t twq = q == 0 ? tv.x : q == 1 ? tv.y : q == 2 ? tv.z : tv.w;
     const uint64_t slot = (uint64_t)((t + d) & ring.L_mask);
-    const uint32_t r = twq >> 31;
-    const uint64_t idx = (slot * (uint64_t)ring.R + r) * (uint64_t)ring.N + (twq & 0x7FFFFFFFu);
+    const uint32_t r = twq >> kRcptShift;
+    const uint64_t idx = (slot * (uint64_t)ring.R + r) * (uint64_t)ring.N + (twq & kTgtMask);
     if (kFixed) {
       const long long qv = __float2ll_rn(wv[q] * 4294967296.0f) * (long long)mult;
       atomicAdd(reinterpret_cast<unsigned long long*>(ring.p) + idx, (unsigned long long)qv);
@@ -352,7 +352,7 @@ __device__ __forceinline__ void deliver_due_item(const uint4 it, const Csr& csr,
         const uint64_t j = j0 + q;
         if (j < b || j >= e) continue;
         const uint32_t twq = q == 0 ? tv[u].x : q == 1 ? tv[u].y : q == 2 ? tv[u].z : tv[u].w;
-        const uint64_t idx = (uint64_t)(twq >> 31) * (uint64_t)ring.N + (twq & 0x7FFFFFFFu);
+        const uint64_t idx = (uint64_t)(twq >> kRcptShift) * (uint64_t)ring.N + (twq & kTgtMask);
         if (kFixed) {
           const long long qv = __float2ll_rn(wv[u][q] * 4294967296.0f) * (long long)mult;
           atomicAdd(reinterpret_cast<unsigned long long*>(ring.p) + idx, (unsigned long long)qv);

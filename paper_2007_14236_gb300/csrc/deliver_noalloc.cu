@@ -131,10 +131,10 @@ __global__ void __launch_bounds__(256) k_na_deliver(const unsigned char* scratch
       while (g + 1 < glo + ngrp && g + 1 < G && csr.grp_start[g + 1] <= j) ++g;
       const uint32_t d = csr.grp_delay[g];
       const uint32_t tw = csr.tgt[j];
-      if ((tw & 0x7FFFFFFFu) >= N || (int32_t)(tw >> 31) >= R) continue;  // outside the ring: skipped
+      if ((tw & kTgtMask) >= N || (int32_t)(tw >> kRcptShift) >= R) continue;  // outside the ring: skipped
       const float w = load_w<WT>(csr.weight, j);
       const uint64_t slot = (uint64_t)((t + d) & L_mask);
-      const uint64_t idx = (slot * (uint64_t)R + (tw >> 31)) * N + (tw & 0x7FFFFFFFu);
+      const uint64_t idx = (slot * (uint64_t)R + (tw >> kRcptShift)) * N + (tw & kTgtMask);
       if (kFixed) {
         const long long qv = __float2ll_rn(w * 4294967296.0f);
         atomicAdd(reinterpret_cast<unsigned long long*>(ring) + idx, (unsigned long long)qv);
@@ -167,7 +167,7 @@ extern "C" int ngb_deliver_spikes_noalloc(const ngb_csr_device* csr, const uint3
   if (n_spikes < 0 || n_spikes > kNaMaxSpikes)
     return na_fail(NGB_ERR_INVALID_ARG, "ngb_deliver_spikes_noalloc: n_spikes must be in [0, " +
                                             std::to_string(kNaMaxSpikes) + "]");
-  if (ring_slots < 2 || (ring_slots & (ring_slots - 1)) != 0 || receptors < 1 || receptors > 2 || t < 0)
+  if (ring_slots < 2 || (ring_slots & (ring_slots - 1)) != 0 || receptors < 1 || receptors > kMaxPorts || t < 0)
     return na_fail(NGB_ERR_INVALID_ARG, "ngb_deliver_spikes_noalloc: ring_slots (power of two), receptors or t");
   if (csr->num_neurons <= 0 || csr->num_synapses < 0 || csr->num_groups < 0 || csr->weight_dtype < 0 ||
       csr->weight_dtype > 2 || !csr->src_syn || !csr->src_grp || !csr->grp_start || !csr->grp_delay ||

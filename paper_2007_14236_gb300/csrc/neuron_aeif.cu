@@ -15,44 +15,134 @@
 // is evaluated at min(V, V_peak)), then add the step's conductance input and
 // join the warp-ballot spike compaction with the spike multiplicity.  In the
 // spike-buffer delivery scheme the kernel that runs first in the step also
-// scans the pending spikes (as the LIF kernel).  kAlpha: alpha-function
-// conductances (the paper's balanced network, Sec. 2.4) with state x_ex, x_in.
+// scans the pending spikes (as the LIF kernel).  kM: the conductance model,
+// exponential, alpha (the paper's balanced network, Sec. 2.4; state x_ex,
+// x_in) or the beta multisynapse model of Sec. 2.1 (up to four receptor
+// ports, each with g and x; the step reads one input plane per port in use).
 #include "aeif_rk.cuh"
 #include "deliver_item.cuh"
 #include "neuron_step.cuh"
 
 namespace ngb {
 
-template <bool kFixed, int kMode, bool kAlpha>
+namespace {
+
+// uint4 words of a deferred neuron's record.
+template <int kM>
+constexpr int kRecWords = kM == kAeifBeta ? 6 : 4;
+
+__device__ __forceinline__ uint32_t fu(float x) { return __float_as_uint(x); }
+__device__ __forceinline__ float uf(uint32_t x) { return __uint_as_float(x); }
+
+template <int kM>
+__device__ __forceinline__ void load_state(const AeifState& S, uint32_t gid, int n_ports, St& y, float& h) {
+  y.V = S.V[gid];
+  y.w = S.w[gid];
+  y.ge = S.g0[gid];
+  y.gi = S.g1[gid];
+  if (kM != kAeifExp) {
+    y.xe = S.x0[gid];
+    y.xi = S.x1[gid];
+  }
+  if (kM == kAeifBeta && n_ports > 2) {
+    y.g2 = S.ext[gid];
+    y.g3 = S.ext[S.N + gid];
+    y.x2 = S.ext[2 * S.N + gid];
+    y.x3 = S.ext[3 * S.N + gid];
+  }
+  h = S.h[gid];
+}
+
+template <int kM>
+__device__ __forceinline__ void store_state(const AeifState& S, uint32_t gid, int n_ports, const St& y, float h) {
+  S.V[gid] = y.V;
+  S.w[gid] = y.w;
+  S.g0[gid] = y.ge;
+  S.g1[gid] = y.gi;
+  if (kM != kAeifExp) {
+    S.x0[gid] = y.xe;
+    S.x1[gid] = y.xi;
+  }
+  if (kM == kAeifBeta && n_ports > 2) {
+    S.ext[gid] = y.g2;
+    S.ext[S.N + gid] = y.g3;
+    S.ext[2 * S.N + gid] = y.x2;
+    S.ext[3 * S.N + gid] = y.x3;
+  }
+  S.h[gid] = h;
+}
+
+// Record of a neuron whose step is unfinished: {gid, segment, spikes so far,
+// attempts}, the state, the step's input and the position inside the step.
+template <int kM>
+__device__ __forceinline__ void pack_rec(uint4* rec, uint32_t gid, uint32_t seg, uint32_t nspk, const St& y,
+                                         const RkPos& r, float4 in) {
+  const unsigned long long hb = (unsigned long long)__double_as_longlong(r.h);
+  const unsigned long long tb = (unsigned long long)__double_as_longlong(r.t_in);
+  const uint4 pos = make_uint4((uint32_t)hb, (uint32_t)(hb >> 32), (uint32_t)tb, (uint32_t)(tb >> 32));
+  rec[0] = make_uint4(gid, seg, nspk, (uint32_t)r.n);
+  rec[1] = make_uint4(fu(y.V), fu(y.w), fu(y.ge), fu(y.gi));
+  if constexpr (kM == kAeifBeta) {
+    rec[2] = make_uint4(fu(y.g2), fu(y.g3), fu(y.xe), fu(y.xi));
+    rec[3] = make_uint4(fu(y.x2), fu(y.x3), fu(in.x), fu(in.y));
+    rec[4] = make_uint4(fu(in.z), fu(in.w), 0u, 0u);
+    rec[5] = pos;
+  } else {
+    rec[2] = make_uint4(fu(y.xe), fu(y.xi), fu(in.x), fu(in.y));
+    rec[3] = pos;
+  }
+}
+
+template <int kM>
+__device__ __forceinline__ void unpack_rec(const uint4* q, St& y, RkPos& r, float4& in) {
+  const uint4 r0 = q[0], r1 = q[1];
+  const uint4 pos = q[kRecWords<kM> - 1];
+  y.V = uf(r1.x);
+  y.w = uf(r1.y);
+  y.ge = uf(r1.z);
+  y.gi = uf(r1.w);
+  if constexpr (kM == kAeifBeta) {
+    const uint4 r2 = q[2], r3 = q[3], r4 = q[4];
+    y.g2 = uf(r2.x);
+    y.g3 = uf(r2.y);
+    y.xe = uf(r2.z);
+    y.xi = uf(r2.w);
+    y.x2 = uf(r3.x);
+    y.x3 = uf(r3.y);
+    in = make_float4(uf(r3.z), uf(r3.w), uf(r4.x), uf(r4.y));
+  } else {
+    const uint4 r2 = q[2];
+    y.xe = uf(r2.x);
+    y.xi = uf(r2.y);
+    in = make_float4(uf(r2.z), uf(r2.w), 0.f, 0.f);
+  }
+  r.h = __longlong_as_double((long long)((unsigned long long)pos.x | ((unsigned long long)pos.y << 32)));
+  r.t_in = __longlong_as_double((long long)((unsigned long long)pos.z | ((unsigned long long)pos.w << 32)));
+  r.n = (int64_t)r0.w;
+}
+
+}  // namespace
+
+template <bool kFixed, int kMode, int kM>
 __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constant__ SegTable<AeifSeg> T,
-                                                            const uint32_t* __restrict__ thr,
-                                                            float* __restrict__ V_, float* __restrict__ w_,
-                                                            float* __restrict__ ge_, float* __restrict__ gi_,
-                                                            float* __restrict__ h_, float* __restrict__ xe_,
-                                                            float* __restrict__ xi_, Ring ring, int64_t* clk,
-                                                            int64_t step_off, const Csr csr, SpikeBuf sb, int scan,
-                                                            int budget) {
+                                                            const uint32_t* __restrict__ thr, const AeifState S,
+                                                            Ring ring, int64_t* clk, int64_t step_off, const Csr csr,
+                                                            SpikeBuf sb, int scan, int budget) {
   constexpr bool kAge = kMode == kEmitAge;
+  constexpr int kW = kRecWords<kM>;
   __shared__ uint32_t s_thr[kMaxThr];
   const int seg = segment_index_of(T, (int64_t)blockIdx.x);
   const AeifSeg p = T.n <= kInlineSegs ? T.s[seg] : T.dev[seg];
   const int64_t k = ((int64_t)blockIdx.x - p.blk_begin) * kAeifBlock + threadIdx.x;
   const bool valid = k < p.n;
   const uint32_t gid = (uint32_t)(p.offset + k);
+  const int n_ports = kM == kAeifBeta ? p.n_ports : 2;
   // prologue (overlaps the previous kernel): state, source metadata, Poisson table
-  St y{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  St y{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   float h0 = 0.f;
   uint4 meta = make_uint4(0, 0, 0, 0);
   if (valid) {
-    y.V = V_[gid];
-    y.w = w_[gid];
-    y.ge = ge_[gid];
-    y.gi = gi_[gid];
-    if (kAlpha) {
-      y.xe = xe_[gid];
-      y.xi = xi_[gid];
-    }
-    h0 = h_[gid];
+    load_state<kM>(S, gid, n_ports, y, h0);
     if (!kAge) meta = __ldg(csr.src_meta + gid);
   }
   for (uint32_t i = threadIdx.x; i < p.n_thr; i += kAeifBlock) s_thr[i] = __ldg(thr + p.thr_off + i);
@@ -67,42 +157,35 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
   uint32_t nspk = 0;
   unsigned long long nsub = 0;
   bool done = true;
-  uint4 rec[4];
+  uint4 rec[kW];
   if (valid) {
     const uint64_t slot = (uint64_t)(t & ring.L_mask);
     const uint64_t i0 = (slot * (uint64_t)ring.R) * (uint64_t)ring.N + gid;
-    float in0 = ring_take<kFixed, false>(ring.p, i0);
-    float in1 = ring_take<kFixed, false>(ring.p, i0 + (uint64_t)ring.N);
+    float4 in = make_float4(0.f, 0.f, 0.f, 0.f);
+    in.x = ring_take<kFixed, false>(ring.p, i0);
+    in.y = ring_take<kFixed, false>(ring.p, i0 + (uint64_t)ring.N);
+    if (kM == kAeifBeta) {
+      if (n_ports > 2) in.z = ring_take<kFixed, false>(ring.p, i0 + 2 * (uint64_t)ring.N);
+      if (n_ports > 3) in.w = ring_take<kFixed, false>(ring.p, i0 + 3 * (uint64_t)ring.N);
+    }
     if (p.n_thr > 0) {
       const uint32_t kp = poisson_count(p.seed, t - p.t0, p.local_off + (uint32_t)k, s_thr, p.n_thr);
       const float add = __fmul_rn((float)kp, p.w_ext);
-      if (p.prec_rcpt == 0) in0 = __fadd_rn(in0, add);
-      else in1 = __fadd_rn(in1, add);
+      switch (p.prec_rcpt) {
+        case 0: in.x = __fadd_rn(in.x, add); break;
+        case 1: in.y = __fadd_rn(in.y, add); break;
+        case 2: in.z = __fadd_rn(in.z, add); break;
+        default: in.w = __fadd_rn(in.w, add); break;
+      }
     }
     RkPos r{(double)h0, 0.0, 0};
     bool cap_hit = false;
-    done = aeif_advance<kAlpha>(p, y, r, budget, in0, in1, nspk, nsub, cap_hit);
+    done = aeif_advance<kM>(p, y, r, budget, in, nspk, nsub, cap_hit);
     if (cap_hit) atomicOr(sb.err, kErrSubstepCap);
-    if (done) {
-      V_[gid] = y.V;
-      w_[gid] = y.w;
-      ge_[gid] = y.ge;
-      gi_[gid] = y.gi;
-      if (kAlpha) {
-        xe_[gid] = y.xe;
-        xi_[gid] = y.xi;
-      }
-      h_[gid] = (float)r.h;
-    } else {
-      rec[0] = make_uint4(gid, (uint32_t)seg, nspk, (uint32_t)r.n);
-      rec[1] = make_uint4(__float_as_uint(y.V), __float_as_uint(y.w), __float_as_uint(y.ge), __float_as_uint(y.gi));
-      rec[2] = make_uint4(__float_as_uint(y.xe), __float_as_uint(y.xi), __float_as_uint(in0), __float_as_uint(in1));
-      const unsigned long long hb = (unsigned long long)__double_as_longlong(r.h);
-      const unsigned long long tb = (unsigned long long)__double_as_longlong(r.t_in);
-      rec[3] = make_uint4((uint32_t)hb, (uint32_t)(hb >> 32), (uint32_t)tb, (uint32_t)(tb >> 32));
-    }
+    if (done) store_state<kM>(S, gid, n_ports, y, (float)r.h);
+    else pack_rec<kM>(rec, gid, (uint32_t)seg, nspk, y, r, in);
   }
-  defer_write(!done, rec, sb, kAlpha ? 1 : 0, t);
+  defer_write<kW>(!done, rec, sb, kM, t);
   // sub-step statistics: one atomic per warp
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nsub += __shfl_xor_sync(0xffffffffu, nsub, o);
@@ -119,24 +202,21 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
 // the update kernel's attempt budget (mostly those crossing V_peak, whose
 // step needs tens of attempts) continue from their saved position, packed
 // 32 to a warp, then write their state and join the spike compaction.
-template <bool kFixed, int kMode, bool kAlpha>
+template <bool kFixed, int kMode, int kM>
 __global__ void __launch_bounds__(kAeifBlock) k_aeif_finish(const __grid_constant__ SegTable<AeifSeg> T,
-                                                            float* __restrict__ V_, float* __restrict__ w_,
-                                                            float* __restrict__ ge_, float* __restrict__ gi_,
-                                                            float* __restrict__ h_, float* __restrict__ xe_,
-                                                            float* __restrict__ xi_, Ring ring, int64_t* clk,
+                                                            const AeifState S, Ring ring, int64_t* clk,
                                                             int64_t step_off, const Csr csr, SpikeBuf sb) {
   constexpr bool kAge = kMode == kEmitAge;
+  constexpr int kW = kRecWords<kM>;
   griddep_wait();
   griddep_launch();
-  const int kind = kAlpha ? 1 : 0;
   const int64_t t = clk[0] + step_off;
-  unsigned long long n = sb.dcnt[2 * kind + (int)(t & 1)];
+  unsigned long long n = sb.dcnt[2 * kM + (int)(t & 1)];
   if (n > (unsigned long long)sb.dfr_cap) n = (unsigned long long)sb.dfr_cap;
   // the previous step's list is finished (this stream ran its finishing kernel
   // first) and the next step appends to it only after this kernel
-  if (blockIdx.x == 0 && threadIdx.x == 0) sb.dcnt[2 * kind + (int)((t + 1) & 1)] = 0;
-  const uint4* __restrict__ list = sb.dfr[kind];
+  if (blockIdx.x == 0 && threadIdx.x == 0) sb.dcnt[2 * kM + (int)((t + 1) & 1)] = 0;
+  const uint4* __restrict__ list = sb.dfr[kM];
   const int lane = threadIdx.x & 31;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * kAeifBlock + threadIdx.x) >> 5;
   const unsigned long long nwarps = ((unsigned long long)gridDim.x * kAeifBlock) >> 5;
@@ -147,28 +227,20 @@ __global__ void __launch_bounds__(kAeifBlock) k_aeif_finish(const __grid_constan
     unsigned long long nsub = 0;
     uint4 meta = make_uint4(0, 0, 0, 0);
     if (valid) {
-      const uint4 r0 = list[4 * i], r1 = list[4 * i + 1], r2 = list[4 * i + 2], r3 = list[4 * i + 3];
+      const uint4* q = list + (unsigned long long)kW * i;
+      const uint4 r0 = q[0];
       gid = r0.x;
       const AeifSeg p = T.dev[r0.y];
       nspk = r0.z;
       if (!kAge) meta = __ldg(csr.src_meta + gid);
-      St y{__uint_as_float(r1.x), __uint_as_float(r1.y), __uint_as_float(r1.z), __uint_as_float(r1.w),
-           __uint_as_float(r2.x), __uint_as_float(r2.y)};
-      RkPos r{__longlong_as_double((long long)((unsigned long long)r3.x | ((unsigned long long)r3.y << 32))),
-              __longlong_as_double((long long)((unsigned long long)r3.z | ((unsigned long long)r3.w << 32))),
-              (int64_t)r0.w};
+      St y{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      RkPos r{0.0, 0.0, 0};
+      float4 in;
+      unpack_rec<kM>(q, y, r, in);
       bool cap_hit = false;
-      aeif_advance<kAlpha>(p, y, r, 0, __uint_as_float(r2.z), __uint_as_float(r2.w), nspk, nsub, cap_hit);
+      aeif_advance<kM>(p, y, r, 0, in, nspk, nsub, cap_hit);
       if (cap_hit) atomicOr(sb.err, kErrSubstepCap);
-      V_[gid] = y.V;
-      w_[gid] = y.w;
-      ge_[gid] = y.ge;
-      gi_[gid] = y.gi;
-      if (kAlpha) {
-        xe_[gid] = y.xe;
-        xi_[gid] = y.xi;
-      }
-      h_[gid] = (float)r.h;
+      store_state<kM>(S, gid, kM == kAeifBeta ? p.n_ports : 2, y, (float)r.h);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nsub += __shfl_xor_sync(0xffffffffu, nsub, o);
@@ -184,39 +256,40 @@ __global__ void __launch_bounds__(kAeifBlock) k_aeif_finish(const __grid_constan
 
 namespace {
 template <bool kFixed, int kMode>
-cudaError_t aeif_launch(const SegTable<AeifSeg>& segs, dim3 g, const uint32_t* thr, float* V, float* w, float* gex,
-                        float* gin, float* h, float* xe, float* xi, bool alpha, Ring ring, int64_t* clk,
-                        int64_t step_off, const Csr& csr, SpikeBuf sb, int sc, int budget, bool pdl, cudaStream_t st) {
+cudaError_t aeif_launch(const SegTable<AeifSeg>& segs, dim3 g, const uint32_t* thr, const AeifState& S, int model,
+                        Ring ring, int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, int sc, int budget,
+                        bool pdl, cudaStream_t st) {
   const dim3 b(kAeifBlock);
-  if (alpha)
-    return launch_k(k_update_aeif<kFixed, kMode, true>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, xe, xi, ring, clk,
-                    step_off, csr, sb, sc, budget);
-  return launch_k(k_update_aeif<kFixed, kMode, false>, g, b, pdl, st, segs, thr, V, w, gex, gin, h, xe, xi, ring, clk,
-                  step_off, csr, sb, sc, budget);
+  if (model == kAeifBeta)
+    return launch_k(k_update_aeif<kFixed, kMode, kAeifBeta>, g, b, pdl, st, segs, thr, S, ring, clk, step_off, csr,
+                    sb, sc, budget);
+  if (model == kAeifAlpha)
+    return launch_k(k_update_aeif<kFixed, kMode, kAeifAlpha>, g, b, pdl, st, segs, thr, S, ring, clk, step_off, csr,
+                    sb, sc, budget);
+  return launch_k(k_update_aeif<kFixed, kMode, kAeifExp>, g, b, pdl, st, segs, thr, S, ring, clk, step_off, csr, sb,
+                  sc, budget);
 }
 
 template <bool kFixed, int kMode>
-cudaError_t finish_launch(const SegTable<AeifSeg>& segs, dim3 g, float* V, float* w, float* gex, float* gin, float* h,
-                          float* xe, float* xi, bool alpha, Ring ring, int64_t* clk, int64_t step_off, const Csr& csr,
-                          SpikeBuf sb, bool pdl, cudaStream_t st) {
+cudaError_t finish_launch(const SegTable<AeifSeg>& segs, dim3 g, const AeifState& S, int model, Ring ring,
+                          int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, bool pdl, cudaStream_t st) {
   const dim3 b(kAeifBlock);
-  if (alpha)
-    return launch_k(k_aeif_finish<kFixed, kMode, true>, g, b, pdl, st, segs, V, w, gex, gin, h, xe, xi, ring, clk,
-                    step_off, csr, sb);
-  return launch_k(k_aeif_finish<kFixed, kMode, false>, g, b, pdl, st, segs, V, w, gex, gin, h, xe, xi, ring, clk,
-                  step_off, csr, sb);
+  if (model == kAeifBeta)
+    return launch_k(k_aeif_finish<kFixed, kMode, kAeifBeta>, g, b, pdl, st, segs, S, ring, clk, step_off, csr, sb);
+  if (model == kAeifAlpha)
+    return launch_k(k_aeif_finish<kFixed, kMode, kAeifAlpha>, g, b, pdl, st, segs, S, ring, clk, step_off, csr, sb);
+  return launch_k(k_aeif_finish<kFixed, kMode, kAeifExp>, g, b, pdl, st, segs, S, ring, clk, step_off, csr, sb);
 }
 }  // namespace
 
-cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V,
-                               float* w, float* gex, float* gin, float* h, float* xe, float* xi, bool alpha,
-                               Ring ring, bool fixed, int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb,
-                               int emit, bool scan, int budget, bool pdl, cudaStream_t st) {
+cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr,
+                               const AeifState& S, int model, Ring ring, bool fixed, int64_t* clk, int64_t step_off,
+                               const Csr& csr, SpikeBuf sb, int emit, bool scan, int budget, bool pdl,
+                               cudaStream_t st) {
   if (blocks <= 0) return cudaSuccess;
   const dim3 g((unsigned)blocks);
   const int sc = scan ? 1 : 0;
-#define NGB_AEIF(F, M) \
-  return aeif_launch<F, M>(segs, g, thr, V, w, gex, gin, h, xe, xi, alpha, ring, clk, step_off, csr, sb, sc, budget, pdl, st)
+#define NGB_AEIF(F, M) return aeif_launch<F, M>(segs, g, thr, S, model, ring, clk, step_off, csr, sb, sc, budget, pdl, st)
   if (fixed) {
     if (emit == kEmitAge) NGB_AEIF(true, kEmitAge);
     if (emit == kEmitPipe) NGB_AEIF(true, kEmitPipe);
@@ -228,12 +301,11 @@ cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, co
 #undef NGB_AEIF
 }
 
-cudaError_t launch_finish_aeif(const SegTable<AeifSeg>& segs, int grid, float* V, float* w, float* gex, float* gin,
-                               float* h, float* xe, float* xi, bool alpha, Ring ring, bool fixed, int64_t* clk,
-                               int64_t step_off, const Csr& csr, SpikeBuf sb, int emit, bool pdl, cudaStream_t st) {
+cudaError_t launch_finish_aeif(const SegTable<AeifSeg>& segs, int grid, const AeifState& S, int model, Ring ring,
+                               bool fixed, int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, int emit,
+                               bool pdl, cudaStream_t st) {
   const dim3 g((unsigned)grid);
-#define NGB_FIN(F, M) \
-  return finish_launch<F, M>(segs, g, V, w, gex, gin, h, xe, xi, alpha, ring, clk, step_off, csr, sb, pdl, st)
+#define NGB_FIN(F, M) return finish_launch<F, M>(segs, g, S, model, ring, clk, step_off, csr, sb, pdl, st)
   if (fixed) {
     if (emit == kEmitAge) NGB_FIN(true, kEmitAge);
     if (emit == kEmitPipe) NGB_FIN(true, kEmitPipe);

@@ -108,6 +108,14 @@ struct PopHost {
   uint64_t g_off = 0, g_len = 0;  // their delay groups in the group pool
 };
 
+// Synaptic receptors of a population's model: ports a synapse may target.
+int ports_of(const PopHost& p) {
+  if (p.model == NGB_LIF_PSC_EXP) return 1;
+  return p.model == NGB_AEIF_COND_BETA ? p.aeif.n_ports : 2;
+}
+// Receptor planes the ring needs for it (AdEx kernels read at least two).
+int receptors_of(const PopHost& p) { return p.model == NGB_LIF_PSC_EXP ? 1 : std::max(2, ports_of(p)); }
+
 struct InstHost {
   uint64_t seed;
   int64_t n;
@@ -153,13 +161,27 @@ uint64_t call_synapses(const ngb_conn_spec& c, int64_t ns, int64_t nt, bool same
   }
 }
 
-// device counter words: ctr[2], events, substeps, rec_count, spare, pcnt[2], dcnt[4], ctr3[3], spare
-constexpr int kCounters = 16;
+// device counter words: ctr[2], events, substeps, rec_count, spare, pcnt[2], dcnt[6], ctr3[3], spare
+constexpr int kCounters = 18;
 
 uint64_t next_pow2(uint64_t x) {
   uint64_t p = 1;
   while (p < x) p <<= 1;
   return p;
+}
+
+// Jump of x per unit weight for a beta-function conductance with rise time
+// tr and decay time td (Sec. 2.1 multisynapse model): after x jumps by 1, g
+// follows (e^(-t/td) - e^(-t/tr)) / (1/tr - 1/td), peaking at
+// t_peak = tr td ln(td / tr) / (td - tr); the jump is the reciprocal of that
+// peak, so a weight-W input peaks at W.  Equal times give g = t e^(-t/td),
+// peak td / e at t = td, hence the jump e / td (the alpha function).
+double beta_jump(double tr, double td) {
+  constexpr double kE = 2.718281828459045;
+  if (tr == td) return kE / td;
+  const double t_peak = tr * td * std::log(td / tr) / (td - tr);
+  const double peak = (std::exp(-t_peak / td) - std::exp(-t_peak / tr)) / (1.0 / tr - 1.0 / td);
+  return 1.0 / peak;
 }
 
 int bits_for(uint64_t n) {  // bits to represent values 0 .. n-1
@@ -194,6 +216,7 @@ struct ngb_sim {
   size_t dev_bytes = 0;
   float *st0 = nullptr, *st1 = nullptr, *st2 = nullptr, *st3 = nullptr, *st4 = nullptr;
   float *st5 = nullptr, *st6 = nullptr;  // AdEx alpha conductances: x_ex, x_in
+  float* ext = nullptr;                  // beta ports 2-3: [4][N_cap] g_2, g_3, x_2, x_3 (R > 2)
   int32_t* ref = nullptr;
   void* ring = nullptr;
   uint64_t* src_syn = nullptr;
@@ -213,9 +236,10 @@ struct ngb_sim {
   int lif_npt = 1;  // LIF neurons per thread of the per-step update kernel (1 or 4)
   SegTable<AeifSeg> aeif_tab{};   // AdEx segments with exponential conductances
   SegTable<AeifSeg> aeifa_tab{};  // AdEx segments with alpha-function conductances
-  int n_aeif = 0;                 // AdEx segments of both kinds
-  int n_aeif_exp = 0, n_aeif_alpha = 0;
-  int64_t aeif_blocks = 0, aeifa_blocks = 0;
+  SegTable<AeifSeg> aeifb_tab{};  // beta multisynapse AdEx segments
+  int n_aeif = 0;                 // AdEx segments of all kinds
+  int n_aeif_exp = 0, n_aeif_alpha = 0, n_aeif_beta = 0;
+  int64_t aeif_blocks = 0, aeifa_blocks = 0, aeifb_blocks = 0;
   int aeif_budget = 8;  // RK attempts per neuron in the AdEx update kernel before deferral (0: none)
   uint32_t* thr = nullptr;
   int deliver_grid = 0;
@@ -277,6 +301,10 @@ Csr csr_of(const ngb_sim* s) {
 // How the update kernels hand the step's spikes to delivery.
 int emit_of(const ngb_sim* s) { return s->scheme == 2 ? kEmitAge : (s->mode == 3 ? kEmitPipe : kEmitRing); }
 
+// The fused step loop takes one LIF neuron per thread and the two-receptor
+// AdEx models.
+bool fused_ok(const ngb_sim* s) { return s->lif_npt == 1 && s->n_aeif_beta == 0; }
+
 // Programmatic dependent launch chains the kernels of one stream; the
 // pipelined loop's kernels depend across two streams and go without it.
 bool pdl_of(const ngb_sim* s) { return s->pdl && s->mode != 3; }
@@ -288,30 +316,36 @@ cudaError_t launch_lif(ngb_sim* s, int64_t step_off = 0) {
                            pdl_of(s), s->stream);
 }
 
-// AdEx update kernels: exponential-conductance segments, then alpha ones.
-// Each kind is an update kernel with an attempt budget, then the kernel that
-// finishes the deferred neurons.
+AeifState aeif_state_of(const ngb_sim* s) {
+  return AeifState{s->st0, s->st1, s->st2, s->st3, s->st4, s->st5, s->st6, s->ext, s->N_cap};
+}
+
+// AdEx update kernels: exponential-conductance segments, then alpha ones,
+// then beta ones.  Each kind is an update kernel with an attempt budget, then
+// the kernel that finishes the deferred neurons.
 cudaError_t launch_aeif(ngb_sim* s, int64_t step_off = 0) {
   cudaError_t e = cudaSuccess;
   const bool det = s->cfg.deterministic != 0;
   const int emit = emit_of(s);
   const bool pdl = pdl_of(s);
   const int fin_grid = std::max(1, s->sms) * 4;
-  if (s->n_aeif_exp) {
-    e = launch_update_aeif(s->aeif_tab, s->aeif_blocks, s->thr, s->st0, s->st1, s->st2, s->st3, s->st4, s->st5,
-                           s->st6, false, ring_of(s), det, s->clk, step_off, csr_of(s), s->sb, emit, s->n_lif == 0,
-                           s->aeif_budget, pdl, s->stream);
+  const AeifState S = aeif_state_of(s);
+  const struct {
+    int model, n;
+    const SegTable<AeifSeg>* tab;
+    int64_t blocks;
+  } kinds[3] = {{kAeifExp, s->n_aeif_exp, &s->aeif_tab, s->aeif_blocks},
+                {kAeifAlpha, s->n_aeif_alpha, &s->aeifa_tab, s->aeifa_blocks},
+                {kAeifBeta, s->n_aeif_beta, &s->aeifb_tab, s->aeifb_blocks}};
+  bool scan = s->n_lif == 0;  // the first update kernel of the step scans the pending spikes
+  for (const auto& k : kinds) {
+    if (!k.n || e != cudaSuccess) continue;
+    e = launch_update_aeif(*k.tab, k.blocks, s->thr, S, k.model, ring_of(s), det, s->clk, step_off, csr_of(s), s->sb,
+                           emit, scan, s->aeif_budget, pdl, s->stream);
     if (e == cudaSuccess && s->aeif_budget > 0)
-      e = launch_finish_aeif(s->aeif_tab, fin_grid, s->st0, s->st1, s->st2, s->st3, s->st4, s->st5, s->st6, false,
-                             ring_of(s), det, s->clk, step_off, csr_of(s), s->sb, emit, pdl, s->stream);
-  }
-  if (e == cudaSuccess && s->n_aeif_alpha) {
-    e = launch_update_aeif(s->aeifa_tab, s->aeifa_blocks, s->thr, s->st0, s->st1, s->st2, s->st3, s->st4, s->st5,
-                           s->st6, true, ring_of(s), det, s->clk, step_off, csr_of(s), s->sb, emit,
-                           s->n_lif == 0 && s->n_aeif_exp == 0, s->aeif_budget, pdl, s->stream);
-    if (e == cudaSuccess && s->aeif_budget > 0)
-      e = launch_finish_aeif(s->aeifa_tab, fin_grid, s->st0, s->st1, s->st2, s->st3, s->st4, s->st5, s->st6, true,
-                             ring_of(s), det, s->clk, step_off, csr_of(s), s->sb, emit, pdl, s->stream);
+      e = launch_finish_aeif(*k.tab, fin_grid, S, k.model, ring_of(s), det, s->clk, step_off, csr_of(s), s->sb, emit,
+                             pdl, s->stream);
+    scan = false;
   }
   return e;
 }
@@ -540,6 +574,8 @@ int place_population(ngb_sim* s, int pi) {
     CK(cudaMemsetAsync(s->st3 + off, 0, p.n * sizeof(float), st));
     CK(cudaMemsetAsync(s->st5 + off, 0, p.n * sizeof(float), st));
     CK(cudaMemsetAsync(s->st6 + off, 0, p.n * sizeof(float), st));
+    if (s->ext)
+      CK(cudaMemset2DAsync(s->ext + off, (size_t)s->N_cap * sizeof(float), 0, (size_t)p.n * sizeof(float), 4, st));
     CK(launch_init_state(1, p.n, q.V_init_mean_mV, q.V_init_sd_mV, q.E_L_mV, q.w_init_pA, q.rk_h_init_ms, seed,
                          p.local_off, s->st0 + off, s->st1 + off, s->st4 + off, st));
   }
@@ -758,11 +794,12 @@ int rebuild_tables(ngb_sim* s) {
   };
   const double dt = s->cfg.dt_ms;
   std::vector<LifSeg> lsegs;
-  std::vector<AeifSeg> asegs_exp, asegs_alpha;
+  std::vector<AeifSeg> asegs_exp, asegs_alpha, asegs_beta;
   std::vector<uint32_t> thr_all;
   s->lif_blocks = 0;
   s->aeif_blocks = 0;
   s->aeifa_blocks = 0;
+  s->aeifb_blocks = 0;
   s->n_active = 0;
   {
     // several LIF neurons per thread when the update grid would fill the GPU
@@ -812,11 +849,15 @@ int rebuild_tables(ngb_sim* s) {
       s->lif_blocks += (p.n + lif_tile - 1) / lif_tile;
     } else {
       const ngb_aeif_params& q = p.aeif;
+      const int kind = p.model == NGB_AEIF_COND_BETA    ? kAeifBeta
+                       : p.model == NGB_AEIF_COND_ALPHA ? kAeifAlpha
+                                                        : kAeifExp;
+      int64_t& kind_blocks = kind == kAeifBeta ? s->aeifb_blocks : kind == kAeifAlpha ? s->aeifa_blocks : s->aeif_blocks;
       AeifSeg g{};
       g.offset = p.offset;
       g.n = p.n;
-      g.alpha = p.model == NGB_AEIF_COND_ALPHA ? 1 : 0;
-      g.blk_begin = g.alpha ? s->aeifa_blocks : s->aeif_blocks;
+      g.alpha = kind == kAeifAlpha ? 1 : 0;
+      g.blk_begin = kind_blocks;
       g.t0 = I.t0;
       g.seed = I.seed;
       g.local_off = p.local_off;
@@ -851,19 +892,42 @@ int rebuild_tables(ngb_sim* s) {
       constexpr double kEuler = 2.718281828459045;
       g.e_tau_ex = (float)(kEuler / q.tau_ex_ms);
       g.e_tau_in = (float)(kEuler / q.tau_in_ms);
-      (g.alpha ? asegs_alpha : asegs_exp).push_back(g);
-      (g.alpha ? s->aeifa_blocks : s->aeif_blocks) += (p.n + kAeifBlock - 1) / kAeifBlock;
+      // receptor ports: the beta model's own, else the two receptors
+      g.n_ports = kind == kAeifBeta ? q.n_ports : 2;
+      for (int k = 0; k < kMaxPorts; ++k) {
+        double E = 0.0, tr = 1.0, td = 1.0;
+        bool used = k < g.n_ports;
+        if (kind == kAeifBeta && used) {
+          E = q.E_rev_mV[k];
+          tr = q.tau_rise_ms[k];
+          td = q.tau_decay_ms[k];
+        } else if (kind != kAeifBeta && k < 2) {
+          E = k == 0 ? q.E_ex_mV : q.E_in_mV;
+          tr = td = k == 0 ? q.tau_ex_ms : q.tau_in_ms;
+        }
+        g.E_p[k] = (float)E;
+        g.itd_p[k] = (float)(1.0 / td);
+        g.itr_p[k] = (float)(1.0 / tr);
+        g.jmp_p[k] = used ? (float)beta_jump(tr, td) : 0.0f;
+      }
+      (kind == kAeifBeta ? asegs_beta : kind == kAeifAlpha ? asegs_alpha : asegs_exp).push_back(g);
+      kind_blocks += (p.n + kAeifBlock - 1) / kAeifBlock;
     }
   }
   s->n_lif = (int)lsegs.size();
   s->n_aeif_exp = (int)asegs_exp.size();
   s->n_aeif_alpha = (int)asegs_alpha.size();
-  s->n_aeif = s->n_aeif_exp + s->n_aeif_alpha;
-  std::vector<AeifSeg> asegs(asegs_exp);  // every AdEx segment, for the persistent kernel
+  s->n_aeif_beta = (int)asegs_beta.size();
+  s->n_aeif = s->n_aeif_exp + s->n_aeif_alpha + s->n_aeif_beta;
+  // the beta model's deferred-neuron list (6 words per neuron), on first use
+  if (s->n_aeif_beta && !s->sb.dfr[kAeifBeta]) CK(s->dalloc(&s->sb.dfr[kAeifBeta], 6 * (size_t)s->N_cap));
+  // every AdEx segment of the two-receptor models, for the persistent kernel
+  std::vector<AeifSeg> asegs(asegs_exp);
   asegs.insert(asegs.end(), asegs_alpha.begin(), asegs_alpha.end());
   s->lif_tab = SegTable<LifSeg>{};
   s->aeif_tab = SegTable<AeifSeg>{};
   s->aeifa_tab = SegTable<AeifSeg>{};
+  s->aeifb_tab = SegTable<AeifSeg>{};
   if (s->n_lif) {
     LifSeg* d = nullptr;
     CK(talloc((void**)&d, lsegs.size() * sizeof(LifSeg)));
@@ -903,6 +967,7 @@ int rebuild_tables(ngb_sim* s) {
   };
   CK(aeif_table(asegs_exp, s->aeif_blocks, s->aeif_tab));
   CK(aeif_table(asegs_alpha, s->aeifa_blocks, s->aeifa_tab));
+  CK(aeif_table(asegs_beta, s->aeifb_blocks, s->aeifb_tab));
   AeifSeg* d_asegs = nullptr;
   if (!asegs.empty()) {
     CK(talloc((void**)&d_asegs, asegs.size() * sizeof(AeifSeg)));
@@ -955,7 +1020,8 @@ int rebuild_tables(ngb_sim* s) {
     s->persist_smem = a.off_thr + a16(thr_all.size() * 4);
     const bool was_ok = s->persist_ok;
     s->persist_ok = false;
-    if (s->persist_smem <= 200 * 1024) {
+    // the persistent kernel integrates the two-receptor models only
+    if (s->persist_smem <= 200 * 1024 && s->n_aeif_beta == 0) {
       int bpsm = 0;
       if (persistent_max_blocks_per_sm(s->cfg.deterministic != 0, s->cfg.weight_dtype, s->n_lif > 0,
                                        s->n_aeif > 0, s->persist_smem, &bpsm) == cudaSuccess && bpsm > 0) {
@@ -968,8 +1034,9 @@ int rebuild_tables(ngb_sim* s) {
     }
     if (!s->persist_ok && s->mode == 1) s->mode = 0;
   }
-  // the fused loop runs one LIF neuron per thread and delivers with the ring scheme
-  if (s->mode == 2 && (s->lif_npt != 1 || s->scheme != 1)) s->mode = 0;
+  // the fused loop runs one LIF neuron per thread, the two-receptor AdEx
+  // models, and delivers with the ring scheme
+  if (s->mode == 2 && (!fused_ok(s) || s->scheme != 1)) s->mode = 0;
   // the pipelined loop delivers with the ring scheme
   if (s->mode == 3 && (s->scheme != 1 || !s->stream2)) s->mode = 0;
   s->tables_dirty = false;
@@ -985,8 +1052,7 @@ int finalize_impl(ngb_sim* s) {
   if (!s->serving) {
     if (s->N <= 0) return fail(NGB_ERR_STATE, "ngb_finalize: no neurons");
     s->R = 1;
-    for (const PopHost& p : s->pops)
-      if (p.model != NGB_LIF_PSC_EXP) s->R = 2;
+    for (const PopHost& p : s->pops) s->R = std::max(s->R, receptors_of(p));
     s->N_cap = s->N;
     uint64_t K = 0;
     for (const CallHost& c : s->calls) {
@@ -1006,7 +1072,7 @@ int finalize_impl(ngb_sim* s) {
   CK(cudaMemsetAsync(s->st0, 0, N * sizeof(float), st));
   CK(cudaMemsetAsync(s->st1, 0, N * sizeof(float), st));
   CK(cudaMemsetAsync(s->ref, 0, N * sizeof(int32_t), st));
-  if (s->R == 2) {
+  if (s->R >= 2) {
     CK(s->dalloc(&s->st2, N));
     CK(s->dalloc(&s->st3, N));
     CK(s->dalloc(&s->st4, N));
@@ -1023,6 +1089,10 @@ int finalize_impl(ngb_sim* s) {
     CK(cudaMemsetAsync(s->st2, 0, N * sizeof(float), st));
     CK(cudaMemsetAsync(s->st3, 0, N * sizeof(float), st));
     CK(cudaMemsetAsync(s->st4, 0, N * sizeof(float), st));
+  }
+  if (s->R > 2) {  // beta ports 2-3
+    CK(s->dalloc(&s->ext, 4 * (size_t)N));
+    CK(cudaMemsetAsync(s->ext, 0, 4 * (size_t)N * sizeof(float), st));
   }
   CK(s->dalloc(&s->src_syn, N + 1));
   CK(s->dalloc(&s->src_grp, N + 1));
@@ -1043,7 +1113,7 @@ int finalize_impl(ngb_sim* s) {
 
   // counters, clock, spike record, barrier
   unsigned long long* ctrs = nullptr;
-  CK(s->dalloc(&ctrs, kCounters));  // ctr[2], events, substeps, rec_count, spare, pcnt[2]
+  CK(s->dalloc(&ctrs, kCounters));  // ctr[2], events, substeps, rec_count, spare, pcnt[2], dcnt[6], ctr3[3]
   CK(cudaMemsetAsync(ctrs, 0, kCounters * sizeof(unsigned long long), st));
   s->sb.ctr = ctrs;
   s->sb.events = ctrs + 2;
@@ -1051,7 +1121,7 @@ int finalize_impl(ngb_sim* s) {
   s->sb.rec_count = ctrs + 4;
   s->sb.pcnt = ctrs + 6;
   s->sb.dcnt = ctrs + 8;
-  s->sb.ctr3 = ctrs + 12;
+  s->sb.ctr3 = ctrs + 14;
   CK(s->dalloc(&s->sb.err, 1));
   CK(cudaMemsetAsync(s->sb.err, 0, sizeof(uint32_t), st));
   CK(s->dalloc(&s->clk, 2));
@@ -1311,6 +1381,7 @@ int snapshot_take(ngb_sim* s, Snapshot& sn) {
     sn.parts.push_back({s->st5, N * 4});
     sn.parts.push_back({s->st6, N * 4});
   }
+  if (s->ext) sn.parts.push_back({s->ext, 4 * N * 4});
   for (auto& p : sn.parts) {
     void* c = nullptr;
     CK(cudaMalloc(&c, p.second));
@@ -1336,10 +1407,10 @@ std::string tune_key(ngb_sim* s) {
   cudaDeviceProp prop{};
   cudaGetDeviceProperties(&prop, s->cfg.device);
   char buf[512];
-  std::snprintf(buf, sizeof(buf), "%s|sm%d|N%lld|K%llu|G%llu|L%lld|R%d|w%d|det%d|lif%d|aeif%d|dl%d", prop.name,
-                prop.multiProcessorCount, (long long)s->N, (unsigned long long)s->K, (unsigned long long)s->G,
-                (long long)s->L, s->R, s->cfg.weight_dtype, s->cfg.deterministic, s->n_lif, s->n_aeif * 100 + s->n_aeif_alpha,
-                s->cfg.delivery);
+  std::snprintf(buf, sizeof(buf), "%s|sm%d|N%lld|K%llu|G%llu|L%lld|R%d|w%d|det%d|lif%d|aeif%d.%d.%d|dl%d",
+                prop.name, prop.multiProcessorCount, (long long)s->N, (unsigned long long)s->K,
+                (unsigned long long)s->G, (long long)s->L, s->R, s->cfg.weight_dtype, s->cfg.deterministic, s->n_lif,
+                s->n_aeif_exp, s->n_aeif_alpha, s->n_aeif_beta, s->cfg.delivery);
   for (char* c = buf; *c; ++c)
     if (*c == ' ') *c = '_';
   return buf;
@@ -1429,12 +1500,21 @@ int ngb_add_population_in(ngb_sim* s, int32_t instance, int32_t model, int64_t n
       return fail(NGB_ERR_INVALID_ARG, "ngb_add_population: LIF parameters");
     lambda = q.poisson.n_inputs * q.poisson.rate_hz * dt * 1e-3;
     s->pop_E_L.push_back(q.E_L_mV);
-  } else if (model == NGB_AEIF_COND_EXP || model == NGB_AEIF_COND_ALPHA) {
+  } else if (model == NGB_AEIF_COND_EXP || model == NGB_AEIF_COND_ALPHA || model == NGB_AEIF_COND_BETA) {
     p.aeif = *(const ngb_aeif_params*)params;
     const ngb_aeif_params& q = p.aeif;
-    if (!(q.C_m_pF > 0 && q.tau_w_ms > 0 && q.tau_ex_ms > 0 && q.tau_in_ms > 0 && q.rk_tol > 0 &&
+    const bool beta = model == NGB_AEIF_COND_BETA;
+    if (beta) {
+      if (q.n_ports < 1 || q.n_ports > kMaxPorts)
+        return fail(NGB_ERR_INVALID_ARG, "ngb_add_population: beta model needs 1-4 ports");
+      for (int k = 0; k < q.n_ports; ++k)
+        if (!(q.tau_rise_ms[k] > 0 && q.tau_decay_ms[k] > 0))
+          return fail(NGB_ERR_INVALID_ARG, "ngb_add_population: beta port time constants");
+    }
+    const int ports = beta ? q.n_ports : 2;
+    if (!(q.C_m_pF > 0 && q.tau_w_ms > 0 && (beta || (q.tau_ex_ms > 0 && q.tau_in_ms > 0)) && q.rk_tol > 0 &&
           q.rk_h_min_ms > 0 && q.rk_h_init_ms > 0 && q.rk_max_substeps > 0 && q.Delta_T_mV >= 0 &&
-          q.V_init_sd_mV >= 0 && (q.poisson.receptor == 0 || q.poisson.receptor == 1)))
+          q.V_init_sd_mV >= 0 && q.poisson.receptor >= 0 && q.poisson.receptor < ports))
       return fail(NGB_ERR_INVALID_ARG, "ngb_add_population: AdEx parameters");
     lambda = q.poisson.n_inputs * q.poisson.rate_hz * dt * 1e-3;
     s->pop_E_L.push_back(0.0);
@@ -1471,8 +1551,8 @@ int ngb_connect(ngb_sim* s, int32_t src_pop, int32_t tgt_pop, const ngb_conn_spe
   if (conn->K < 0) return fail(NGB_ERR_INVALID_ARG, "ngb_connect: K < 0");
   if (!valid_dist(syn->weight) || !valid_dist(syn->delay_ms))
     return fail(NGB_ERR_INVALID_ARG, "ngb_connect: distribution");
-  if (syn->receptor < 0 || syn->receptor > 1 || (syn->receptor == 1 && pt.model == NGB_LIF_PSC_EXP))
-    return fail(NGB_ERR_INVALID_ARG, "ngb_connect: receptor");
+  if (syn->receptor < 0 || syn->receptor >= ports_of(pt))
+    return fail(NGB_ERR_INVALID_ARG, "ngb_connect: receptor beyond the target model's ports");
   if (syn->delay_ms.dist == NGB_DIST_NORMAL && !(syn->delay_ms.p1 >= 0))
     return fail(NGB_ERR_INVALID_ARG, "ngb_connect: delay sd");
   if (syn->delay_ms.dist == NGB_DIST_CONST && !(syn->delay_ms.p0 >= 0))
@@ -1541,7 +1621,7 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
     std::string k;
     int m = 0, g = 0, pg = 0, sc = 0;
     while (in >> k >> m >> g >> pg >> sc) {
-      if (k == key && g > 0 && (m == 0 || (m == 2 && sc == 1) || (m == 3 && sc == 1 && s->stream2) ||
+      if (k == key && g > 0 && (m == 0 || (m == 2 && sc == 1 && fused_ok(s)) || (m == 3 && sc == 1 && s->stream2) ||
                                 (s->persist_ok && pg > 0)) &&
           (sc == s->scheme || both)) {
         set_scheme(s, sc);
@@ -1623,7 +1703,7 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
       s->mode = 0;
     }
     // fused update + delivery in graphs (ring scheme)
-    if (rc == NGB_OK && scheme == 1 && s->lif_npt == 1) {
+    if (rc == NGB_OK && scheme == 1 && fused_ok(s)) {
       s->mode = 2;
       rc = capture_graph(s);
       if (rc == NGB_OK) rc = snapshot_restore(s, sn);
@@ -1698,12 +1778,12 @@ int ngb_reserve(ngb_sim* s, int64_t max_neurons, int64_t max_synapses, int64_t m
   if (s->finalized) return fail(NGB_ERR_STATE, "ngb_reserve: network already finalised");
   if (max_neurons <= 0 || max_neurons >= (int64_t)kIdMask || max_synapses < 0 || max_groups < 0 ||
       ring_slots < 2 || ring_slots > 4096 || (ring_slots & (ring_slots - 1)) != 0 || receptors < 1 ||
-      receptors > 2)
+      receptors > kMaxPorts)
     return fail(NGB_ERR_INVALID_ARG, "ngb_reserve: capacities");
   if (max_neurons < s->N) return fail(NGB_ERR_INVALID_ARG, "ngb_reserve: fewer neurons than already added");
   for (const PopHost& p : s->pops)
-    if (p.model != NGB_LIF_PSC_EXP && receptors < 2)
-      return fail(NGB_ERR_INVALID_ARG, "ngb_reserve: AdEx populations need two receptors");
+    if (receptors_of(p) > receptors)
+      return fail(NGB_ERR_INVALID_ARG, "ngb_reserve: a population needs more receptors");
   s->serving = true;
   s->N_cap = max_neurons;
   s->K_cap = (uint64_t)max_synapses;
@@ -1721,8 +1801,8 @@ int ngb_commit_instance(ngb_sim* s, int32_t instance) {
   if (instance < 0 || instance >= (int32_t)s->inst.size())
     return fail(NGB_ERR_INVALID_ARG, "ngb_commit_instance: instance");
   for (const PopHost& p : s->pops)
-    if (p.instance == instance && p.model != NGB_LIF_PSC_EXP && s->R < 2)
-      return fail(NGB_ERR_INVALID_ARG, "ngb_commit_instance: AdEx needs two receptors");
+    if (p.instance == instance && receptors_of(p) > s->R)
+      return fail(NGB_ERR_INVALID_ARG, "ngb_commit_instance: a population needs more receptors than reserved");
   if (!s->finalized) {
     rc = finalize_impl(s);
     if (rc != NGB_OK) {
@@ -1861,6 +1941,12 @@ int ngb_get_state(ngb_sim* s, int32_t var, int64_t first, int64_t n, float* out)
     case NGB_VAR_H: src = s->st4; break;
     case NGB_VAR_DG_EX: src = s->st5; break;
     case NGB_VAR_DG_IN: src = s->st6; break;
+    case NGB_VAR_G_2:
+    case NGB_VAR_G_3:
+    case NGB_VAR_X_2:
+    case NGB_VAR_X_3:
+      src = s->ext ? s->ext + (size_t)(var - NGB_VAR_G_2) * (size_t)s->N_cap : nullptr;
+      break;
     case NGB_VAR_REFRACT: is_ref = true; break;
     default: return fail(NGB_ERR_INVALID_ARG, "ngb_get_state: var");
   }

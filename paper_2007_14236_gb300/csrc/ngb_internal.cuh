@@ -4,14 +4,16 @@
 // Data layout in HBM (N neurons, K synapses, G connection groups, L ring
 // slots, R receptors):
 //   state      SoA FP32 arrays of N (LIF: y = V - E_L, I, refractory counter;
-//              AdEx: V, w, g_ex, g_in, h)
+//              AdEx: V, w, g_ex, g_in, h, x_ex, x_in; beta multisynapse
+//              ports 0-1 in g_ex, g_in, x_ex, x_in and ports 2-3 in a
+//              [4][N] block g_2, g_3, x_2, x_3)
 //   ring       [L][R][N] FP32 (or int64 fixed point in deterministic mode);
 //              slot (t + d) & (L - 1) receives the spikes of step t with delay d
 //   CSR        src_syn[N+1] u64 (first synapse of each source),
 //              src_grp[N+1] u32 (first delay group of each source),
 //              grp_start[G+1] u64 and grp_delay[G] u16 (Sec. 2.2 connection
 //              groups: a source's synapses with equal delay, in delay order),
-//              tgt[K] u32 (bit 31 = receptor, bits 0-30 = global target),
+//              tgt[K] u32 (bits 30-31 = receptor, bits 0-29 = global target),
 //              w[K] FP32 / BF16 / FP16
 //   src_meta   uint4 per source {row start lo, row start hi (16 bits) | groups
 //              << 16, synapses, first group}: everything delivery needs about
@@ -59,7 +61,9 @@ constexpr uint32_t kIdMask = (1u << kIdBits) - 1;
 constexpr int kMaxThr = 255;         // Poisson inversion table length (largest count drawn)
 constexpr int kDelayBits = 12;       // delays up to 4095 steps
 constexpr int kMaxDelay = (1 << kDelayBits) - 1;
-constexpr uint32_t kRcptBit = 0x80000000u;
+constexpr int kRcptShift = 30;       // synapse target word: receptor << 30 | global target
+constexpr uint32_t kTgtMask = (1u << kRcptShift) - 1;
+constexpr int kMaxPorts = 4;         // receptor ports of the beta multisynapse AdEx
 
 // error flags (device word)
 constexpr uint32_t kErrRecordOverflow = 1u;
@@ -97,7 +101,10 @@ struct AeifSeg {
   float g_L, E_L, V_T, Delta_T, inv_Delta_T, a, inv_tau_w, V_peak, V_reset, b;
   float E_ex, E_in, inv_tau_ex, inv_tau_in, I_e, inv_C, w_ext;
   float e_tau_ex, e_tau_in;  // e / tau: the jump of x per unit input weight (alpha)
-  float pad_;
+  int32_t n_ports;           // beta multisynapse: ports in use (1-4)
+  // beta ports (unused ports: E 0, 1/tau 1, jump 0): reversal potential, 1 / decay
+  // time, 1 / rise time, jump of x per unit weight (the peak of g equals the weight)
+  float E_p[4], itd_p[4], itr_p[4], jmp_p[4];
   double inv_tol, h_min, dt;
   int64_t max_sub;
 };
@@ -118,9 +125,9 @@ struct SpikeBuf {
   int64_t pend_cap;                 // entries per pending list
   int64_t wi_cap;                   // uint4 entries per work-item / due-item list
   // AdEx neurons whose step did not finish within the update kernel's attempt
-  // budget (by conductance model: 0 exponential, 1 alpha), finished by a second
-  // kernel with the neurons packed into full warps
-  uint4* dfr[2];                    // 4 uint4 per neuron
+  // budget (by conductance model: 0 exponential, 1 alpha, 2 beta), finished by
+  // a second kernel with the neurons packed into full warps
+  uint4* dfr[3];                    // 4 uint4 per neuron (beta: 6)
   unsigned long long* dcnt;         // [model * 2 + step parity]
   int64_t dfr_cap;                  // neurons per list
   // pipelined ring scheme: work-item lists and counters by step mod 3
@@ -378,12 +385,13 @@ __device__ __forceinline__ void scan_pending(int64_t t, const Csr& csr, const Sp
   }
 }
 
-// Warp-aggregated append of the 4-entry records of the lanes whose AdEx step
+// Warp-aggregated append of the kW-entry records of the lanes whose AdEx step
 // is unfinished (d) to deferred list `kind`.  Every lane of the warp must
 // call it.  The list holds one record per neuron, each neuron is deferred at
 // most once per step, so a position beyond the capacity is an internal error
 // (flagged, record dropped).
-__device__ __forceinline__ void defer_write(bool d, const uint4 rec[4], const SpikeBuf& sb, int kind, int64_t t) {
+template <int kW>
+__device__ __forceinline__ void defer_write(bool d, const uint4 rec[kW], const SpikeBuf& sb, int kind, int64_t t) {
   const unsigned full = 0xffffffffu;
   const unsigned b = __ballot_sync(full, d);
   if (b == 0) return;
@@ -394,11 +402,9 @@ __device__ __forceinline__ void defer_write(bool d, const uint4 rec[4], const Sp
   if (d) {
     const unsigned long long pos = base + __popc(b & ((1u << lane) - 1u));
     if (pos < (unsigned long long)sb.dfr_cap) {
-      uint4* q = sb.dfr[kind] + 4 * pos;
-      q[0] = rec[0];
-      q[1] = rec[1];
-      q[2] = rec[2];
-      q[3] = rec[3];
+      uint4* q = sb.dfr[kind] + kW * pos;
+#pragma unroll
+      for (int i = 0; i < kW; ++i) q[i] = rec[i];
     } else {
       atomicOr(sb.err, kErrPendingOverflow);
     }
@@ -495,16 +501,26 @@ enum : int { kEmitRing = 0, kEmitAge = 1, kEmitPipe = 2 };
 cudaError_t launch_update_lif(const SegTable<LifSeg>& segs, int64_t blocks, int npt, const uint32_t* thr, float* y,
                               float* I, int32_t* ref, Ring ring, bool fixed, int64_t* clk, int64_t step_off,
                               const Csr& csr, SpikeBuf sb, int emit, bool scan, bool pdl, cudaStream_t st);
-// alpha: the segments have alpha-function conductances (x_ex, x_in in xe, xi).
+// AdEx state arrays (N_cap entries each): V, w, conductances and x of ports
+// 0-1 (g_ex, g_in, x_ex, x_in), the carried RK step proposal h, and for beta
+// ports 2-3 the block ext[4][N] = g_2, g_3, x_2, x_3 (NULL when no population
+// has more than two ports).
+struct AeifState {
+  float *V, *w, *g0, *g1, *h, *x0, *x1, *ext;
+  int64_t N;
+};
+// AdEx conductance models of the per-step kernels.
+enum : int { kAeifExp = 0, kAeifAlpha = 1, kAeifBeta = 2 };
+// model: kAeif*, the conductance model of every segment of the table.
 // budget > 0: at most `budget` RK attempts per neuron in this kernel; the
 // unfinished neurons are completed by launch_finish_aeif (same arithmetic).
-cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr, float* V,
-                               float* w, float* gex, float* gin, float* h, float* xe, float* xi, bool alpha,
-                               Ring ring, bool fixed, int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb,
-                               int emit, bool scan, int budget, bool pdl, cudaStream_t st);
-cudaError_t launch_finish_aeif(const SegTable<AeifSeg>& segs, int grid, float* V, float* w, float* gex, float* gin,
-                               float* h, float* xe, float* xi, bool alpha, Ring ring, bool fixed, int64_t* clk,
-                               int64_t step_off, const Csr& csr, SpikeBuf sb, int emit, bool pdl, cudaStream_t st);
+cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr,
+                               const AeifState& S, int model, Ring ring, bool fixed, int64_t* clk, int64_t step_off,
+                               const Csr& csr, SpikeBuf sb, int emit, bool scan, int budget, bool pdl,
+                               cudaStream_t st);
+cudaError_t launch_finish_aeif(const SegTable<AeifSeg>& segs, int grid, const AeifState& S, int model, Ring ring,
+                               bool fixed, int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, int emit,
+                               bool pdl, cudaStream_t st);
 cudaError_t launch_tick(int64_t* clk, bool pdl, cudaStream_t st);
 cudaError_t persistent_max_blocks_per_sm(bool fixed, int wdtype, bool lif, bool aeif, size_t smem, int* out);
 cudaError_t launch_persistent(const PersistArgs& a, bool fixed, int wdtype, bool lif, bool aeif, int grid,

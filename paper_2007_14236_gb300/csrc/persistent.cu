@@ -204,8 +204,8 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(PersistArgs a) {
             if (p.prec_rcpt == 0) in0 = __fadd_rn(in0, add);
             else in1 = __fadd_rn(in1, add);
           }
-          if (p.alpha) aeif_step<true>(p, y, h, in0, in1, nspk, nsub, cap_hit);
-          else aeif_step<false>(p, y, h, in0, in1, nspk, nsub, cap_hit);
+          if (p.alpha) aeif_step<kAeifAlpha>(p, y, h, in0, in1, nspk, nsub, cap_hit);
+          else aeif_step<kAeifExp>(p, y, h, in0, in1, nspk, nsub, cap_hit);
           a.st0[gid] = y.V;
           a.st1[gid] = y.w;
           a.st2[gid] = y.ge;

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kAeifBlock) k_step_aeif(const __grid_constant_
       else in1 = __fadd_rn(in1, add);
     }
     bool cap_hit = false;
-    aeif_step<kAlpha>(p, y, h, in0, in1, nspk, nsub, cap_hit);
+    aeif_step<kAlpha ? kAeifAlpha : kAeifExp>(p, y, h, in0, in1, nspk, nsub, cap_hit);
     if (cap_hit) atomicOr(sb.err, kErrSubstepCap);
     V_[gid] = y.V;
     w_[gid] = y.w;

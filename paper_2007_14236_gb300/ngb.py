@@ -20,11 +20,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 OK = 0
 ERRORS = {-1: "INVALID_ARG", -2: "STATE", -3: "OOM", -4: "CUDA", -5: "TIMEOUT", -6: "OVERFLOW"}
 WEIGHT_DTYPES = {"fp32": 0, "bf16": 1, "fp16": 2}
-MODELS = {W.LIF: 0, W.AEIF: 1, W.AEIF_ALPHA: 2}
+MODELS = {W.LIF: 0, W.AEIF: 1, W.AEIF_ALPHA: 2, W.AEIF_BETA: 3}
 RULES = {W.INDEGREE: 0, W.TOTAL: 1, W.OUTDEGREE: 2, W.ONE_TO_ONE: 3, W.ALL_TO_ALL: 4}
 DISTS = {"const": 0, "normal": 1, "uniform": 2}
 DELIVERY = {"auto": 0, "ring": 1, "spike_buffer": 2}
-VARS = {"V_m": 0, "I_syn": 1, "w": 1, "g_ex": 2, "g_in": 3, "refractory": 4, "h": 5, "dg_ex": 6, "dg_in": 7}
+VARS = {"V_m": 0, "I_syn": 1, "w": 1, "g_ex": 2, "g_in": 3, "refractory": 4, "h": 5, "dg_ex": 6, "dg_in": 7,
+        "g_0": 2, "g_1": 3, "g_2": 8, "g_3": 9, "x_0": 6, "x_1": 7, "x_2": 10, "x_3": 11}
 
 
 class SimConfig(C.Structure):
@@ -52,7 +53,8 @@ class AeifParams(C.Structure):
                                           "V_init_sd_mV", "w_init_pA", "rk_tol", "rk_h_min_ms",
                                           "rk_h_init_ms")] + \
                [("rk_max_substeps", C.c_int64), ("rk_control_fp32", C.c_int32), ("pad_", C.c_int32),
-                ("poisson", PoissonDrive)]
+                ("poisson", PoissonDrive), ("n_ports", C.c_int32), ("pad2_", C.c_int32),
+                ("E_rev_mV", C.c_double * 4), ("tau_rise_ms", C.c_double * 4), ("tau_decay_ms", C.c_double * 4)]
 
 
 class ConnSpec(C.Structure):
@@ -155,9 +157,14 @@ def lif_params(p: W.LifParams) -> LifParams:
 
 
 def aeif_params(p: W.AeifParams) -> AeifParams:
-    return AeifParams(p.C_m, p.g_L, p.E_L, p.V_T, p.Delta_T, p.a, p.b, p.tau_w, p.V_peak, p.V_reset, p.E_ex, p.E_in,
-                      p.tau_ex, p.tau_in, p.I_e, p.V_init_mean, p.V_init_sd, p.w_init, p.rk_tol, p.rk_h_min,
-                      p.rk_h_init, int(p.rk_max_substeps), int(p.rk_control_fp32), 0, _poisson(p.poisson))
+    q = AeifParams(p.C_m, p.g_L, p.E_L, p.V_T, p.Delta_T, p.a, p.b, p.tau_w, p.V_peak, p.V_reset, p.E_ex, p.E_in,
+                   p.tau_ex, p.tau_in, p.I_e, p.V_init_mean, p.V_init_sd, p.w_init, p.rk_tol, p.rk_h_min,
+                   p.rk_h_init, int(p.rk_max_substeps), int(p.rk_control_fp32), 0, _poisson(p.poisson))
+    ports = list(p.ports or [])
+    q.n_ports = len(ports)
+    for k, (E, tr, td) in enumerate(ports[:4]):
+        q.E_rev_mV[k], q.tau_rise_ms[k], q.tau_decay_ms[k] = E, tr, td
+    return q
 
 
 class Simulator:

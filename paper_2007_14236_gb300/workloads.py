@@ -201,6 +201,33 @@ def mixed_net(seed: int = 1, weight_dtype: str = "fp32") -> NetSpec:
     return spec
 
 
+def beta_net(seed: int = 1, weight_dtype: str = "fp32", w_ex: float = 1.0, w_slow: float = 0.1,
+             w_in: float = 2.0, drive: float = 0.4) -> NetSpec:
+    """Multisynapse AdEx neurons with beta-function conductances (Sec. 2.1):
+    a 3-port population (fast excitatory, slow excitatory, inhibitory), a
+    4-port population (the same three plus a second inhibitory port whose
+    rise and decay times are equal) and a 1-port population, each driven by
+    Poisson input on port 0 and connected across all ports."""
+    fast, slow, inh, inh2 = (0.0, 0.2, 2.0), (0.0, 1.0, 8.0), (-85.0, 0.5, 5.0), (-75.0, 1.0, 1.0)
+    def par(ports):
+        return AeifParams(V_reset=-60.0, V_init_sd=3.0, ports=ports,
+                          poisson=Poisson(n_inputs=1.0, rate_hz=20000.0, weight=drive, receptor=0))
+    spec = NetSpec(name="beta_net", seeds=[seed], weight_dtype=weight_dtype)
+    spec.pops = [Population("B3", AEIF_BETA, 400, par([fast, slow, inh])),
+                 Population("B4", AEIF_BETA, 350, par([fast, slow, inh, inh2])),
+                 Population("B1", AEIF_BETA, 250, par([fast]))]
+    spec.conns = [
+        Connection(0, 1, INDEGREE, 40, Dist("const", w_ex), Dist("uniform", 0.5, 1.5), 0),
+        Connection(0, 0, INDEGREE, 40, Dist("const", w_slow), Dist("const", 1.0), 1),
+        Connection(1, 1, INDEGREE, 30, Dist("const", w_slow), Dist("const", 1.2), 1),
+        Connection(1, 0, INDEGREE, 30, Dist("const", w_in), Dist("const", 0.8), 2),
+        Connection(1, 1, INDEGREE, 20, Dist("const", w_in), Dist("const", 0.6), 2),
+        Connection(2, 1, INDEGREE, 25, Dist("const", w_in), Dist("uniform", 0.5, 2.0), 3),
+        Connection(0, 2, INDEGREE, 30, Dist("const", w_ex), Dist("const", 1.5), 0),
+    ]
+    return spec
+
+
 def rules_net(seed: int = 1, weight_dtype: str = "fp32") -> NetSpec:
     """A small LIF network wired with the rules beyond fixed in-degree / total
     number (Sec. 2.1): one-to-one A -> B, fixed out-degree B -> C, all-to-all

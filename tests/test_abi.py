@@ -60,6 +60,8 @@ def test_struct_layouts_match_c(tmp_path):
     body = "".join('printf("%s %%zu\\n", sizeof(%s));\n' % (k, k) for k in structs)
     body += 'printf("aeif_poisson %zu\\n", offsetof(ngb_aeif_params, poisson));\n'
     body += 'printf("cfg_stream %zu\\n", offsetof(ngb_sim_config, stream));\n'
+    body += 'printf("aeif_ports %zu\\n", offsetof(ngb_aeif_params, n_ports));\n'
+    body += 'printf("aeif_tau_decay %zu\\n", offsetof(ngb_aeif_params, tau_decay_ms));\n'
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "ngb.h"\nint main(void){\n%s return 0;}\n' % body)
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -69,6 +71,8 @@ def test_struct_layouts_match_c(tmp_path):
         assert int(got[k]) == ctypes.sizeof(cls), k
     assert int(got["aeif_poisson"]) == ngb.AeifParams.poisson.offset
     assert int(got["cfg_stream"]) == ngb.SimConfig.stream.offset
+    assert int(got["aeif_ports"]) == ngb.AeifParams.n_ports.offset
+    assert int(got["aeif_tau_decay"]) == ngb.AeifParams.tau_decay_ms.offset
 
 
 def test_invalid_arguments_fail_without_touching_a_gpu(libpath):

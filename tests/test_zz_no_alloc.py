@@ -56,7 +56,7 @@ def _device_csr(torch, sim, keep):
     grp_start = np.append(starts, K).astype(np.int64)
     grp_delay = d[starts].astype(np.int16)
     src_grp = np.searchsorted(starts, sp).astype(np.int32)  # first group at or after each row start
-    tw = (syn["tgt"].astype(np.uint64) | (syn["receptor"].astype(np.uint64) << 31)).astype(np.uint32)
+    tw = (syn["tgt"].astype(np.uint64) | (syn["receptor"].astype(np.uint64) << 30)).astype(np.uint32)
     dev = dict(src_syn=torch.from_numpy(sp).cuda(), src_grp=torch.from_numpy(src_grp).cuda(),
                grp_start=torch.from_numpy(grp_start).cuda(), grp_delay=torch.from_numpy(grp_delay).cuda(),
                tgt=torch.from_numpy(tw.view(np.int32)).cuda(), w=torch.from_numpy(syn["weight"]).cuda())
