@@ -35,6 +35,7 @@ def lib():
     L.ora_add_population.argtypes = [P, C.c_int32, C.c_int32, C.c_int64, C.POINTER(C.c_double)]
     L.ora_connect.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.c_int32,
                               C.c_double, C.c_double, C.c_int32, C.c_double, C.c_double, C.c_int32]
+    L.ora_set_stdp.argtypes = [P, C.c_int32, C.POINTER(C.c_double)]
     L.ora_finalize.argtypes = [P]
     L.ora_simulate.argtypes = [P, C.c_int64]
     L.ora_inject.argtypes = [P, C.c_int64, C.c_int32, C.c_int64, C.c_double]
@@ -154,9 +155,13 @@ class OracleNet:
         for c in spec.conns:
             rule = {"fixed_indegree": 0, "fixed_total_number": 1, "fixed_outdegree": 2, "one_to_one": 3,
                     "all_to_all": 4}[c.rule]
-            _check(L.ora_connect(self.h, c.src, c.tgt, rule, c.K, int(c.allow_autapses), _DIST[c.weight.kind],
+            call = _check(L.ora_connect(self.h, c.src, c.tgt, rule, c.K, int(c.allow_autapses), _DIST[c.weight.kind],
                                  c.weight.p0, c.weight.p1, _DIST[c.delay.kind], c.delay.p0, c.delay.p1,
                                  c.receptor))
+            if c.stdp is not None:
+                q = c.stdp
+                v = np.array([q.tau_plus, q.tau_minus, q.lam, q.alpha, q.mu_plus, q.mu_minus, q.W_max], dtype=np.float64)
+                _check(L.ora_set_stdp(self.h, call, v.ctypes.data_as(C.POINTER(C.c_double))))
 
     def __del__(self):
         if getattr(self, "h", None):

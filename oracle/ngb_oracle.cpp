@@ -226,6 +226,7 @@ struct Call {
   int64_t K;
   double w0, w1, d0, d1;
   uint32_t stream;  // connect-call index within the instance
+  int stdp;         // 0: static synapses; k > 0: plastic with STDP rule k - 1
 };
 
 struct Synapse {
@@ -233,7 +234,47 @@ struct Synapse {
   float w;
   uint16_t delay;
   uint8_t receptor;
+  uint8_t stdp;
 };
+
+// Nearest-neighbour spike-timing-dependent plasticity (Sec. 2.1, after
+// Morrison et al. 2008), with the weight dependence of Guetig et al. (2003).
+// A spike of the source reaches the synapse `delay` steps after it was fired
+// (its arrival step a).  At every arrival the weight is depressed by the
+// target's latest spike p < a, and at every spike of the target at step p
+// the weight is potentiated by the synapse's latest arrival a <= p
+// (symmetric nearest-neighbour pairing; lags n in steps, time n * dt):
+//   potentiation  w <- w + lambda W_max (1 - w / W_max)^mu_plus e^(-n dt / tau_plus)
+//   depression    w <- w - alpha lambda W_max (w / W_max)^mu_minus e^(-n dt / tau_minus)
+// each followed by clipping to [0, W_max].  A lag beyond 20 tau changes
+// nothing (the factor e^-20 is below FP32 resolution next to the weight).
+// The weight a spike delivers is the weight after the depression of its
+// arrival.  Arithmetic in FP32, the exponentials tabulated in FP64 and
+// rounded once.
+struct StdpRule {
+  float A_plus, A_minus, inv_W_max, W_max, mu_plus, mu_minus;
+  std::vector<float> k_plus, k_minus;  // e^(-n dt / tau) for lags n = 0 .. 20 tau / dt
+};
+
+float stdp_power(float x, float mu) {
+  if (mu == 0.0f) return 1.0f;
+  if (mu == 1.0f) return x;
+  return std::pow(std::max(x, 0.0f), mu);
+}
+
+float stdp_clip(float w, float W_max) { return std::min(std::max(w, 0.0f), W_max); }
+
+float stdp_potentiate(const StdpRule& r, float w, int64_t lag) {
+  if (lag < 0 || lag >= (int64_t)r.k_plus.size()) return w;
+  const float f = stdp_power(1.0f - w * r.inv_W_max, r.mu_plus);
+  return stdp_clip(w + (r.A_plus * f) * r.k_plus[(size_t)lag], r.W_max);
+}
+
+float stdp_depress(const StdpRule& r, float w, int64_t lag) {
+  if (lag < 0 || lag >= (int64_t)r.k_minus.size()) return w;
+  const float f = stdp_power(w * r.inv_W_max, r.mu_minus);
+  return stdp_clip(w - (r.A_minus * f) * r.k_minus[(size_t)lag], r.W_max);
+}
 
 }  // namespace
 
@@ -253,7 +294,17 @@ struct ora_net {
   std::vector<uint8_t> rcpt;
   std::vector<float> w;
   std::vector<uint16_t> delay;
+  std::vector<uint8_t> plast;  // STDP rule + 1 of each synapse (0: static)
   int max_delay = 1;
+  // STDP: rules, the latest arrival step of every synapse (-1: none), the
+  // latest spike step of every neuron (-1: none), the plastic synapses of
+  // every target (in_ptr[N+1] into in_syn), and the spike multiplicities of
+  // the last max_delay + 1 steps (hist[(step mod H) * N + neuron])
+  std::vector<StdpRule> stdp;
+  std::vector<int64_t> arrival, last_spike;
+  std::vector<uint64_t> in_ptr, in_syn;
+  std::vector<int> hist;
+  bool plastic = false;
   int64_t L = 2;
   int R = 1;
   // per-neuron state (double arrays; FP32 models keep float-representable values)
@@ -362,6 +413,7 @@ Synapse draw_synapse(const ora_net* net, const Call& c, uint64_t q) {
   s.w = round_weight((float)draw_weight(net, c, seed, q), net->prec);
   s.delay = delay_steps(draw_delay(net, c, seed, q), net->dt);
   s.receptor = (uint8_t)c.receptor;
+  s.stdp = (uint8_t)c.stdp;
   return s;
 }
 
@@ -667,9 +719,33 @@ int32_t ora_connect(ora_net* net, int32_t src_pop, int32_t tgt_pop, int32_t rule
   if (src_pop == tgt_pop && !allow_autapses && net->pops[src_pop].n < 2 && K > 0)
     return fail("ora_connect: no admissible source without autapses");
   Instance& I = net->inst[net->pops[src_pop].instance];
-  Call c{src_pop, tgt_pop, rule, allow_autapses ? 1 : 0, wdist, ddist, receptor, K, w0, w1, d0, d1, I.n_calls};
+  Call c{src_pop, tgt_pop, rule, allow_autapses ? 1 : 0, wdist, ddist, receptor, K, w0, w1, d0, d1, I.n_calls, 0};
   I.n_calls += 1;
   net->calls.push_back(c);
+  return (int32_t)net->calls.size() - 1;
+}
+
+int32_t ora_set_stdp(ora_net* net, int32_t call, const double* p) {
+  if (!net || net->finalized || call < 0 || call >= (int32_t)net->calls.size() || !p)
+    return fail("ora_set_stdp: bad state or call");
+  const double tau_plus = p[0], tau_minus = p[1], lambda = p[2], alpha = p[3], mu_plus = p[4], mu_minus = p[5],
+               W_max = p[6];
+  if (!(tau_plus > 0 && tau_minus > 0 && lambda >= 0 && alpha >= 0 && mu_plus >= 0 && mu_minus >= 0 && W_max > 0))
+    return fail("ora_set_stdp: parameters");
+  if (net->stdp.size() >= 15) return fail("ora_set_stdp: at most 15 rules");
+  StdpRule r;
+  r.A_plus = (float)(lambda * W_max);
+  r.A_minus = (float)(alpha * lambda * W_max);
+  r.inv_W_max = (float)(1.0 / W_max);
+  r.W_max = (float)W_max;
+  r.mu_plus = (float)mu_plus;
+  r.mu_minus = (float)mu_minus;
+  const int64_t n_plus = (int64_t)std::floor(20.0 * tau_plus / net->dt) + 1;
+  const int64_t n_minus = (int64_t)std::floor(20.0 * tau_minus / net->dt) + 1;
+  for (int64_t n = 0; n < n_plus; ++n) r.k_plus.push_back((float)std::exp(-(double)n * net->dt / tau_plus));
+  for (int64_t n = 0; n < n_minus; ++n) r.k_minus.push_back((float)std::exp(-(double)n * net->dt / tau_minus));
+  net->stdp.push_back(r);
+  net->calls[(size_t)call].stdp = (int)net->stdp.size();
   return 0;
 }
 
@@ -695,12 +771,14 @@ int32_t ora_finalize(ora_net* net) {
   net->rcpt.assign(K, 0);
   net->w.assign(K, 0.0f);
   net->delay.assign(K, 0);
+  net->plast.assign(K, 0);
   for (const Synapse& s : syn) {
     const size_t pos = (size_t)bucket[(size_t)(s.src * D + s.delay)]++;
     net->tgt[pos] = s.tgt;
     net->rcpt[pos] = s.receptor;
     net->w[pos] = s.w;
     net->delay[pos] = s.delay;
+    net->plast[pos] = s.stdp;
   }
   net->src_ptr.assign((size_t)N + 1, 0);
   for (const Synapse& s : syn) net->src_ptr[(size_t)s.src + 1] += 1;
@@ -708,6 +786,22 @@ int32_t ora_finalize(ora_net* net) {
   std::vector<Synapse>().swap(syn);
   net->max_delay = maxd;
   net->L = maxd + 1;
+  // STDP bookkeeping: incoming plastic synapses of every target, in CSR order
+  net->plastic = false;
+  for (size_t j = 0; j < K; ++j) net->plastic = net->plastic || net->plast[j] != 0;
+  if (net->plastic) {
+    net->arrival.assign(K, -1);
+    net->last_spike.assign((size_t)N, -1);
+    net->in_ptr.assign((size_t)N + 1, 0);
+    for (size_t j = 0; j < K; ++j)
+      if (net->plast[j]) net->in_ptr[(size_t)net->tgt[j] + 1] += 1;
+    for (int64_t i = 0; i < N; ++i) net->in_ptr[(size_t)i + 1] += net->in_ptr[(size_t)i];
+    net->in_syn.assign((size_t)net->in_ptr[(size_t)N], 0);
+    std::vector<uint64_t> cur(net->in_ptr.begin(), net->in_ptr.end() - 1);
+    for (size_t j = 0; j < K; ++j)
+      if (net->plast[j]) net->in_syn[(size_t)cur[(size_t)net->tgt[j]]++] = j;
+    net->hist.assign((size_t)((maxd + 1) * N), 0);
+  }
   // 3. state
   net->s0.assign((size_t)N, 0.0); net->s1.assign((size_t)N, 0.0); net->s2.assign((size_t)N, 0.0);
   net->s3.assign((size_t)N, 0.0); net->s4.assign((size_t)N, 0.0);
@@ -853,13 +947,29 @@ int32_t ora_simulate(ora_net* net, int64_t steps) {
         }
       }
     }
-    // --- delivery of the spikes of step t to the inputs of step t + delay (Sec. 2.2)
+    // --- STDP: the targets that fired potentiate their plastic inputs with
+    // the latest arrival of each (arrivals up to step t are recorded)
+    if (net->plastic) {
+      for (size_t f = 0; f < fired.size(); ++f) {
+        const int64_t i = fired[f];
+        net->last_spike[(size_t)i] = t;
+        for (uint64_t k = net->in_ptr[(size_t)i]; k < net->in_ptr[(size_t)i + 1]; ++k) {
+          const uint64_t j = net->in_syn[(size_t)k];
+          if (net->arrival[(size_t)j] < 0) continue;
+          const StdpRule& r = net->stdp[(size_t)net->plast[(size_t)j] - 1];
+          net->w[(size_t)j] = stdp_potentiate(r, net->w[(size_t)j], t - net->arrival[(size_t)j]);
+        }
+      }
+    }
+    // --- delivery of the spikes of step t to the inputs of step t + delay (Sec. 2.2);
+    // plastic synapses deliver when the spike arrives (below)
     for (size_t f = 0; f < fired.size(); ++f) {
       const int64_t src = fired[f];
       for (int m = 0; m < mult[f]; ++m) {
         net->spk_id.push_back(src);
         net->spk_step.push_back(t);
         for (uint64_t j = net->src_ptr[(size_t)src]; j < net->src_ptr[(size_t)src + 1]; ++j) {
+          if (net->plastic && net->plast[j]) continue;
           const int64_t idx = ring_index(net, t + net->delay[j], net->rcpt[j], net->tgt[j]);
           if (net->deterministic)
             net->ring_fx[(size_t)idx] += (int64_t)std::llrint((double)net->w[j] * kFixScale);
@@ -871,6 +981,40 @@ int32_t ora_simulate(ora_net* net, int64_t steps) {
           }
         }
         net->events += (int64_t)(net->src_ptr[(size_t)src + 1] - net->src_ptr[(size_t)src]);
+      }
+    }
+    // --- STDP: spikes reaching their plastic synapses at step t + 1 (fired at
+    // step t + 1 - delay) depress them by the target's latest spike, then
+    // deliver the depressed weight into the input of step t + 1
+    if (net->plastic) {
+      const int64_t H = net->max_delay + 1;
+      int* row = net->hist.data() + (size_t)((t % H) * N);
+      std::fill(row, row + N, 0);
+      for (size_t f = 0; f < fired.size(); ++f) row[fired[f]] = mult[f];
+      const int64_t a = t + 1;
+      for (int64_t src = 0; src < N; ++src) {
+        for (uint64_t j = net->src_ptr[(size_t)src]; j < net->src_ptr[(size_t)src + 1]; ++j) {
+          if (!net->plast[j]) continue;
+          const int64_t fired_at = a - net->delay[j];
+          if (fired_at < 0) continue;
+          const int m = net->hist[(size_t)((fired_at % H) * N + src)];
+          if (m == 0) continue;
+          const StdpRule& r = net->stdp[(size_t)net->plast[j] - 1];
+          const int64_t post = net->last_spike[(size_t)net->tgt[j]];
+          if (post >= 0) net->w[j] = stdp_depress(r, net->w[j], a - post);
+          net->arrival[j] = a;
+          const int64_t idx = ring_index(net, a, net->rcpt[j], net->tgt[j]);
+          for (int k = 0; k < m; ++k) {
+            if (net->deterministic)
+              net->ring_fx[(size_t)idx] += (int64_t)std::llrint((double)net->w[j] * kFixScale);
+            else
+              net->ring[(size_t)idx] = net->ring[(size_t)idx] + net->w[j];
+            if (net->track_abs) {
+              net->ring_abs[(size_t)idx] += std::fabs((double)net->w[j]);
+              net->ring_exact[(size_t)idx] += (double)net->w[j];
+            }
+          }
+        }
       }
     }
     net->t += 1;

@@ -6,8 +6,9 @@
  * connected spiking cortical models using GPUs" (NeuronGPU): the clock-driven
  * update of LIF neurons with exponential PSCs by exact integration (Sec. 2.1,
  * Eqs. 1-2), AdEx neurons with conductance synapses by adaptive fifth-order
- * Runge-Kutta (Sec. 2.1, Eqs. 3-5), Poisson drive (Sec. 2.1, devices) and
- * delay-exact spike delivery (Sec. 2.2).  Only the test suite, the smoke check
+ * Runge-Kutta (Sec. 2.1, Eqs. 3-5), Poisson drive (Sec. 2.1, devices),
+ * delay-exact spike delivery (Sec. 2.2) and nearest-neighbour STDP synapses
+ * (Sec. 2.1).  Only the test suite, the smoke check
  * and the CPU-baseline leg of the benchmark may load it.  It shares no code,
  * header or constant with the GPU library.
  *
@@ -55,7 +56,11 @@ int32_t ora_add_population(ora_net* net, int32_t instance, int32_t model /*0 LIF
                            int64_t n, const double* params);
 int32_t ora_connect(ora_net* net, int32_t src_pop, int32_t tgt_pop, int32_t rule /*0 indeg, 1 total, 2 outdeg, 3 one-to-one, 4 all-to-all*/,
                     int64_t K, int32_t allow_autapses, int32_t wdist, double w0, double w1,
-                    int32_t ddist, double d0, double d1, int32_t receptor);
+                    int32_t ddist, double d0, double d1, int32_t receptor);  /* returns the call index */
+/* Make the synapses of connect call `call` plastic: nearest-neighbour STDP
+ * (Sec. 2.1, after Morrison et al. 2008) with p = {tau_plus_ms, tau_minus_ms,
+ * lambda, alpha, mu_plus, mu_minus, W_max}; at most 15 rules per network. */
+int32_t ora_set_stdp(ora_net* net, int32_t call, const double* p);
 int32_t ora_finalize(ora_net* net);
 int32_t ora_simulate(ora_net* net, int64_t steps);
 int32_t ora_inject(ora_net* net, int64_t neuron, int32_t receptor, int64_t step_offset, double value);

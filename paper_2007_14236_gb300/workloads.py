@@ -106,6 +106,20 @@ class Population:
 
 
 @dataclass
+class Stdp:
+    """Nearest-neighbour STDP of a connection's synapses (Sec. 2.1): pair
+    time constants (ms), learning rate lambda, depression ratio alpha, weight
+    exponents mu (0 additive, 1 multiplicative) and the weight bound W_max."""
+    tau_plus: float = 20.0
+    tau_minus: float = 20.0
+    lam: float = 0.01
+    alpha: float = 1.0
+    mu_plus: float = 1.0
+    mu_minus: float = 1.0
+    W_max: float = 100.0
+
+
+@dataclass
 class Connection:
     src: int
     tgt: int
@@ -115,6 +129,7 @@ class Connection:
     delay: Dist
     receptor: int = 0
     allow_autapses: bool = True
+    stdp: Optional[Stdp] = None
 
 
 @dataclass
