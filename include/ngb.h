@@ -208,6 +208,23 @@ typedef struct {
   int32_t pad_;
 } ngb_syn_spec;
 
+/* Nearest-neighbour STDP (Sec. 2.1, after Morrison et al. 2008) with the
+ * power-law weight dependence of Guetig et al. (2003).  A spike reaches a
+ * synapse `delay` steps after it was fired (its arrival).  At an arrival the
+ * synapse is depressed by the target's latest spike at an earlier step (lag
+ * n >= 1 steps): w -= alpha lambda W_max (w / W_max)^mu_minus e^(-n dt / tau_minus),
+ * and delivers the depressed weight; at a spike of the target every plastic
+ * input is potentiated by its latest arrival at or before that step (lag
+ * n >= 0): w += lambda W_max (1 - w / W_max)^mu_plus e^(-n dt / tau_plus).
+ * Each update is clipped to [0, W_max]; a lag beyond 20 tau changes nothing;
+ * FP32 arithmetic with the exponentials tabulated per lag. */
+typedef struct {
+  double tau_plus_ms, tau_minus_ms; /* > 0 */
+  double lambda, alpha;             /* learning rate, depression / potentiation ratio, >= 0 */
+  double mu_plus, mu_minus;         /* weight exponents: 0 additive, 1 multiplicative, >= 0 */
+  double W_max;                     /* weight bound, > 0 */
+} ngb_stdp_params;
+
 /* Counters accumulated since ngb_create. */
 typedef struct {
   int64_t steps;        /* steps simulated */
@@ -259,6 +276,16 @@ NGB_API int ngb_add_population_in(ngb_sim* sim, int32_t instance, int32_t model,
  * network is finalised (first ngb_simulate or ngb_finalize). */
 NGB_API int ngb_connect(ngb_sim* sim, int32_t src_pop, int32_t tgt_pop, const ngb_conn_spec* conn,
                 const ngb_syn_spec* syn);
+
+/* As ngb_connect, with plastic synapses (ngb_stdp_params; each call is its
+ * own rule, at most 15 per handle).  Plastic synapses need FP32 weight
+ * storage and the spike-buffer delivery scheme (NGB_DELIVERY_AUTO chooses
+ * it; NGB_DELIVERY_RING is NGB_ERR_INVALID_ARG), run in the per-step kernel
+ * loop, and are not available in serving handles (NGB_ERR_STATE).  Steps are
+ * counted in 31 bits for them: simulating beyond step 2^31 - 1 is
+ * NGB_ERR_OVERFLOW.  ngb_get_synapses returns the current weights. */
+NGB_API int ngb_connect_stdp(ngb_sim* sim, int32_t src_pop, int32_t tgt_pop, const ngb_conn_spec* conn,
+                             const ngb_syn_spec* syn, const ngb_stdp_params* stdp);
 
 /* ----------------------------------------------------- continuous batching */
 /* Make the handle a serving handle: reserve pools for max_neurons neurons,
@@ -365,7 +392,8 @@ NGB_API int ngb_get_synapses(ngb_sim* sim, int64_t first, int64_t n, uint32_t* t
  * ngb_finalize builds): src_syn[N+1] first synapse of each source,
  * src_grp[N+1] first delay group of each source, grp_start[G+1] first synapse
  * of each group, grp_delay[G] its delay in steps, tgt[K] target id in bits
- * 0-29 with the receptor in bits 30-31, weight[K] in weight_dtype. */
+ * 0-25 with the receptor in bits 30-31 (bits 26-29 zero), weight[K] in
+ * weight_dtype. */
 typedef struct {
   const uint64_t* src_syn;
   const uint32_t* src_grp;

@@ -119,7 +119,7 @@ __global__ void k_draw(CallDev c, uint64_t base, unsigned long long* __restrict_
     const uint64_t pos = base + q;
     keys[pos] = ((unsigned long long)src << kDelayBits) | d;
     vals[pos] = (uint32_t)pos;
-    st_tgt[pos] = (c.tgt_off + tgt) | ((uint32_t)c.receptor << kRcptShift);
+    st_tgt[pos] = (c.tgt_off + tgt) | ((uint32_t)c.receptor << kRcptShift) | ((uint32_t)c.stdp << kPlastShift);
     st_w[pos] = w;
     atomicAdd(src_cnt + c.src_off + src, 1ull);
     dmax = d > (uint32_t)dmax ? (int)d : dmax;

@@ -18,6 +18,8 @@ struct CallDev {
   int32_t rule;        // 0 fixed indegree, 1 fixed total number
   int32_t no_autapse;  // source == target population and autapses excluded
   int32_t wdist, ddist, receptor, prec;
+  int32_t stdp;        // STDP rule + 1 of the call's synapses (0: static)
+  int32_t pad_;
   uint32_t n_src, n_tgt;
   uint32_t src_off, tgt_off;  // global id of the first source / target neuron
 };

@@ -31,15 +31,17 @@
 // <= 1024 synapses of one connection group, written by the update kernel's
 // pending-spike scan); every synapse goes to the single ring slot, the
 // input of step t + 1.  The kernel also empties the pending list that the
-// step's update kernel has consumed.
+// step's update kernel has consumed.  With plastic synapses (kPlastic) each
+// one is depressed at its arrival before it delivers (nearest-neighbour
+// STDP, Sec. 2.1; stdp.cu has the potentiation).
 #include "deliver_item.cuh"
 #include "ngb_internal.cuh"
 
 namespace ngb {
 
-template <typename WT, bool kFixed, int kMode>
+template <typename WT, bool kFixed, int kMode, bool kPlastic = false>
 __global__ void __launch_bounds__(kDeliverBlock) k_deliver(SpikeBuf sb, Csr csr, Ring ring, int64_t* clk,
-                                                           int64_t step_off) {
+                                                           int64_t step_off, StdpArgs sa) {
   constexpr bool kAge = kMode == kEmitAge;
   griddep_wait();    // the step's update kernels have completed
   griddep_launch();  // the next step's update may start its prologue
@@ -70,7 +72,8 @@ __global__ void __launch_bounds__(kDeliverBlock) k_deliver(SpikeBuf sb, Csr csr,
   const uint4* __restrict__ wi = buf ? sb.wi[1] : sb.wi[0];
   if (kAge) {
     if ((unsigned long long)nch > (unsigned long long)sb.wi_cap) nch = (uint32_t)sb.wi_cap;
-    for (uint32_t it = warp; it < nch; it += nwarps) deliver_due_item<WT, kFixed>(wi[it], csr, ring, lane);
+    for (uint32_t it = warp; it < nch; it += nwarps)
+      deliver_due_item<WT, kFixed, kPlastic>(wi[it], csr, ring, lane, t, &sb, &sa);
     return;
   }
   for (uint32_t ch = warp; ch < nch; ch += nwarps) {
@@ -84,14 +87,24 @@ template <typename WT, bool kFixed>
 cudaError_t launch_deliver_t(SpikeBuf sb, Csr csr, Ring ring, int emit, int64_t* clk, int64_t step_off, int grid,
                              bool pdl, cudaStream_t st) {
   const dim3 g((unsigned)grid), b(kDeliverBlock);
-  if (emit == kEmitAge) return launch_k(k_deliver<WT, kFixed, kEmitAge>, g, b, pdl, st, sb, csr, ring, clk, step_off);
-  if (emit == kEmitPipe) return launch_k(k_deliver<WT, kFixed, kEmitPipe>, g, b, pdl, st, sb, csr, ring, clk, step_off);
-  return launch_k(k_deliver<WT, kFixed, kEmitRing>, g, b, pdl, st, sb, csr, ring, clk, step_off);
+  const StdpArgs none{};
+  if (emit == kEmitAge)
+    return launch_k(k_deliver<WT, kFixed, kEmitAge>, g, b, pdl, st, sb, csr, ring, clk, step_off, none);
+  if (emit == kEmitPipe)
+    return launch_k(k_deliver<WT, kFixed, kEmitPipe>, g, b, pdl, st, sb, csr, ring, clk, step_off, none);
+  return launch_k(k_deliver<WT, kFixed, kEmitRing>, g, b, pdl, st, sb, csr, ring, clk, step_off, none);
 }
 }  // namespace
 
 cudaError_t launch_deliver(SpikeBuf sb, Csr csr, int wdtype, Ring ring, bool fixed, int emit, int64_t* clk,
-                           int64_t step_off, int grid, bool pdl, cudaStream_t st) {
+                           int64_t step_off, int grid, bool pdl, cudaStream_t st, const StdpArgs* stdp) {
+  if (stdp) {  // plastic synapses: FP32 weights, spike-buffer scheme
+    if (wdtype != 0 || emit != kEmitAge) return cudaErrorInvalidValue;
+    const dim3 g((unsigned)grid), b(kDeliverBlock);
+    if (fixed)
+      return launch_k(k_deliver<float, true, kEmitAge, true>, g, b, pdl, st, sb, csr, ring, clk, step_off, *stdp);
+    return launch_k(k_deliver<float, false, kEmitAge, true>, g, b, pdl, st, sb, csr, ring, clk, step_off, *stdp);
+  }
 #define NGB_DEL(T, F) return launch_deliver_t<T, F>(sb, csr, ring, emit, clk, step_off, grid, pdl, st)
   if (fixed) {
     if (wdtype == 0) NGB_DEL(float, true);

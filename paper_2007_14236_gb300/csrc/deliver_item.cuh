@@ -14,6 +14,7 @@
 #include <cuda_fp16.h>
 
 #include "ngb_internal.cuh"
+#include "stdp_rule.cuh"
 
 namespace ngb {
 
@@ -317,14 +318,18 @@ __device__ __forceinline__ void deliver_block_spikes(bool spk, uint32_t gid, uin
   }
 }
 
-// Spike-buffer scheme (Sec. 2.2): one due item is up to 1024 consecutive
-// synapses of one connection group (equal delay), all of which go to the
+// Delivery of one due item (spike-buffer scheme): its synapses go to the
 // single ring slot (the input of the next step).  it = {first synapse lo, hi
 // | multiplicity << 16, synapses, -}.  The warp walks the item in aligned
 // chunks of 128 synapses, two chunks per pass so that both chunks' loads are
-// in flight together.
-template <typename WT, bool kFixed>
-__device__ __forceinline__ void deliver_due_item(const uint4 it, const Csr& csr, const Ring& ring, const int lane) {
+// in flight together.  kPlastic (FP32 weights): a plastic synapse is
+// depressed by its target's latest spike, records arrival step t + 1 and
+// delivers the depressed weight (nearest-neighbour STDP, Sec. 2.1; each
+// synapse belongs to one due item per step, so no other thread touches it).
+template <typename WT, bool kFixed, bool kPlastic = false>
+__device__ __forceinline__ void deliver_due_item(const uint4 it, const Csr& csr, const Ring& ring, const int lane,
+                                                 int64_t t = 0, const SpikeBuf* sb = nullptr,
+                                                 const StdpArgs* sa = nullptr) {
   const uint64_t b = (uint64_t)it.x | ((uint64_t)(it.y & 0xFFFFu) << 32);
   const uint32_t mult = it.y >> 16;
   const uint64_t e = b + it.z;
@@ -352,12 +357,23 @@ __device__ __forceinline__ void deliver_due_item(const uint4 it, const Csr& csr,
         const uint64_t j = j0 + q;
         if (j < b || j >= e) continue;
         const uint32_t twq = q == 0 ? tv[u].x : q == 1 ? tv[u].y : q == 2 ? tv[u].z : tv[u].w;
+        float wq = wv[u][q];
+        if (kPlastic) {
+          const uint32_t cls = (twq >> kPlastShift) & kPlastMask;
+          if (cls) {
+            const int32_t arrive = (int32_t)(t + 1);
+            const int32_t post = sb->last_spike[twq & kTgtMask];
+            if (post >= 0) wq = stdp_depress(sa->rules[cls - 1], wq, (int64_t)arrive - (int64_t)post);
+            sa->w[j] = wq;
+            sa->arrival[j] = arrive;
+          }
+        }
         const uint64_t idx = (uint64_t)(twq >> kRcptShift) * (uint64_t)ring.N + (twq & kTgtMask);
         if (kFixed) {
-          const long long qv = __float2ll_rn(wv[u][q] * 4294967296.0f) * (long long)mult;
+          const long long qv = __float2ll_rn(wq * 4294967296.0f) * (long long)mult;
           atomicAdd(reinterpret_cast<unsigned long long*>(ring.p) + idx, (unsigned long long)qv);
         } else {
-          const float v = mult == 1u ? wv[u][q] : wv[u][q] * (float)mult;
+          const float v = mult == 1u ? wq : wq * (float)mult;
           atomicAdd(reinterpret_cast<float*>(ring.p) + idx, v);
         }
       }

@@ -129,6 +129,7 @@ struct CallHost {
   ngb_conn_spec conn;
   ngb_syn_spec syn;
   uint32_t stream;
+  int stdp = 0;  // STDP rule + 1 (0: static synapses)
 };
 
 // Poisson(lambda) inversion thresholds: ceil(F(k) * 2^32) for the CDF F built
@@ -161,8 +162,9 @@ uint64_t call_synapses(const ngb_conn_spec& c, int64_t ns, int64_t nt, bool same
   }
 }
 
-// device counter words: ctr[2], events, substeps, rec_count, spare, pcnt[2], dcnt[6], ctr3[3], spare
-constexpr int kCounters = 18;
+// device counter words: ctr[2], events, substeps, rec_count, spare, pcnt[2], dcnt[6], ctr3[3], spare,
+// post_cnt[2]
+constexpr int kCounters = 20;
 
 uint64_t next_pow2(uint64_t x) {
   uint64_t p = 1;
@@ -272,6 +274,14 @@ struct ngb_sim {
   std::vector<int64_t> rec_steps;
   size_t rec_sorted_upto = 0;  // records [0, upto) are sorted by (step, id)
   std::vector<double> pop_E_L;  // per population, for V of LIF (state holds V - E_L)
+  // STDP (Sec. 2.1): rules of the plastic connect calls, their device table,
+  // the latest arrival step of every synapse and the reverse index
+  std::vector<ngb_stdp_params> stdp_params;
+  StdpRule* d_rules = nullptr;
+  int32_t* arrival = nullptr;
+  uint64_t* in_ptr = nullptr;
+  uint64_t* in_syn = nullptr;
+  uint64_t n_plastic = 0;
 
   template <typename T>
   cudaError_t dalloc(T** p, size_t count) {
@@ -350,9 +360,19 @@ cudaError_t launch_aeif(ngb_sim* s, int64_t step_off = 0) {
   return e;
 }
 
+StdpArgs stdp_of(const ngb_sim* s) { return StdpArgs{s->d_rules, (float*)s->w, s->arrival, s->in_syn}; }
+
 cudaError_t launch_del(ngb_sim* s, int64_t step_off = 0, cudaStream_t st = nullptr) {
+  const StdpArgs sa = stdp_of(s);
   return launch_deliver(s->sb, csr_of(s), s->cfg.weight_dtype, ring_of(s), s->cfg.deterministic != 0, emit_of(s),
-                        s->clk, step_off, s->deliver_grid, pdl_of(s), st ? st : s->stream);
+                        s->clk, step_off, s->deliver_grid, pdl_of(s), st ? st : s->stream,
+                        s->d_rules ? &sa : nullptr);
+}
+
+// STDP potentiation of the step's firing targets, between the update kernels and the delivery.
+cudaError_t launch_post(ngb_sim* s) {
+  if (!s->d_rules) return cudaSuccess;
+  return launch_stdp_post(s->sb, stdp_of(s), s->clk, std::max(1, s->sms) * 4, s->pdl, s->stream);
 }
 
 // The update kernels of one step (step clk[0] + step_off).
@@ -425,6 +445,8 @@ cudaError_t launch_step(ngb_sim* s) {
     e = launch_aeif(s);
     if (e != cudaSuccess) return e;
   }
+  e = launch_post(s);
+  if (e != cudaSuccess) return e;
   return launch_del(s);
 }
 
@@ -620,6 +642,7 @@ int build_populations(ngb_sim* s, const std::vector<int>& srcs, std::vector<PopP
       d.wdist = c.syn.weight.dist;
       d.ddist = c.syn.delay_ms.dist;
       d.receptor = c.syn.receptor;
+      d.stdp = c.stdp;
       d.prec = prec;
       d.n_src = (uint32_t)ps.n;
       d.n_tgt = (uint32_t)pt.n;
@@ -1034,6 +1057,11 @@ int rebuild_tables(ngb_sim* s) {
     }
     if (!s->persist_ok && s->mode == 1) s->mode = 0;
   }
+  // plastic synapses run in the per-step kernel loop (spike-buffer scheme)
+  if (s->d_rules) {
+    s->persist_ok = false;
+    s->mode = 0;
+  }
   // the fused loop runs one LIF neuron per thread, the two-receptor AdEx
   // models, and delivers with the ring scheme
   if (s->mode == 2 && (!fused_ok(s) || s->scheme != 1)) s->mode = 0;
@@ -1041,6 +1069,59 @@ int rebuild_tables(ngb_sim* s) {
   if (s->mode == 3 && (s->scheme != 1 || !s->stream2)) s->mode = 0;
   s->tables_dirty = false;
   return capture_graph(s);
+}
+
+// STDP state of a finalised network (Sec. 2.1): the rules' device table with
+// their pair factors e^(-n dt / tau) tabulated for lags up to 20 tau (FP64,
+// rounded once), the latest arrival step of every synapse and the latest
+// spike step of every neuron (-1: none), the per-step lists of firing
+// targets and the reverse index of the plastic synapses.
+int setup_stdp(ngb_sim* s) {
+  cudaStream_t st = s->stream;
+  const int64_t N = s->N_cap;
+  const double dt = s->cfg.dt_ms;
+  std::vector<StdpRule> rules;
+  for (const ngb_stdp_params& q : s->stdp_params) {
+    StdpRule r{};
+    r.A_plus = (float)(q.lambda * q.W_max);
+    r.A_minus = (float)(q.alpha * q.lambda * q.W_max);
+    r.inv_W_max = (float)(1.0 / q.W_max);
+    r.W_max = (float)q.W_max;
+    r.mu_plus = (float)q.mu_plus;
+    r.mu_minus = (float)q.mu_minus;
+    const double np = std::floor(20.0 * q.tau_plus_ms / dt) + 1.0;
+    const double nm = std::floor(20.0 * q.tau_minus_ms / dt) + 1.0;
+    if (np > (double)(1 << 24) || nm > (double)(1 << 24))
+      return fail(NGB_ERR_INVALID_ARG, "ngb_finalize: STDP time constant longer than 2^24 / 20 steps");
+    std::vector<float> k((size_t)(np + nm));
+    for (int64_t n = 0; n < (int64_t)np; ++n) k[(size_t)n] = (float)std::exp(-(double)n * dt / q.tau_plus_ms);
+    for (int64_t n = 0; n < (int64_t)nm; ++n)
+      k[(size_t)np + (size_t)n] = (float)std::exp(-(double)n * dt / q.tau_minus_ms);
+    float* d = nullptr;
+    CK(s->dalloc(&d, k.size()));
+    CK(cudaMemcpy(d, k.data(), k.size() * sizeof(float), cudaMemcpyHostToDevice));
+    r.n_plus = (int32_t)np;
+    r.n_minus = (int32_t)nm;
+    r.k_plus = d;
+    r.k_minus = d + (size_t)np;
+    rules.push_back(r);
+  }
+  CK(s->dalloc(&s->d_rules, rules.size()));
+  CK(cudaMemcpy(s->d_rules, rules.data(), rules.size() * sizeof(StdpRule), cudaMemcpyHostToDevice));
+  CK(s->dalloc(&s->arrival, s->K_cap + 1));
+  CK(cudaMemsetAsync(s->arrival, 0xFF, (s->K_cap + 1) * sizeof(int32_t), st));
+  CK(s->dalloc(&s->sb.last_spike, N));
+  CK(cudaMemsetAsync(s->sb.last_spike, 0xFF, N * sizeof(int32_t), st));
+  CK(s->dalloc(&s->sb.post[0], N));
+  CK(s->dalloc(&s->sb.post[1], N));
+  CK(s->dalloc(&s->in_ptr, N + 1));
+  uint64_t* in_syn = nullptr;
+  CK(build_stdp_index(s->tgt, s->K_cap, N, s->in_ptr, &in_syn, &s->n_plastic, st));
+  s->allocs.push_back(in_syn);
+  s->dev_bytes += std::max<uint64_t>(1, s->n_plastic) * sizeof(uint64_t);
+  s->in_syn = in_syn;
+  s->sb.in_ptr = s->in_ptr;
+  return NGB_OK;
 }
 
 int finalize_impl(ngb_sim* s) {
@@ -1122,6 +1203,7 @@ int finalize_impl(ngb_sim* s) {
   s->sb.pcnt = ctrs + 6;
   s->sb.dcnt = ctrs + 8;
   s->sb.ctr3 = ctrs + 14;
+  s->sb.post_cnt = ctrs + 18;
   CK(s->dalloc(&s->sb.err, 1));
   CK(cudaMemsetAsync(s->sb.err, 0, sizeof(uint32_t), st));
   CK(s->dalloc(&s->clk, 2));
@@ -1203,6 +1285,11 @@ int finalize_impl(ngb_sim* s) {
     if (s->cfg.delivery == 1) s->scheme = 1;
     else if (s->cfg.delivery == 2) s->scheme = 2;
     else s->scheme = ring_full > 0.5 * (double)l2 ? 2 : 1;
+    if (!s->stdp_params.empty()) {  // plastic synapses deliver at arrival: spike buffer
+      if (s->cfg.delivery == 1)
+        return fail(NGB_ERR_INVALID_ARG, "ngb_finalize: STDP synapses need the spike-buffer delivery scheme");
+      s->scheme = 2;
+    }
   }
   // pending-spike lists (spike-buffer scheme): a source has at most one spike
   // per refractory period + 1 steps in flight, and none older than the
@@ -1241,6 +1328,10 @@ int finalize_impl(ngb_sim* s) {
   const size_t ring_bytes = (size_t)s->L * s->R * N * (s->cfg.deterministic ? 8 : 4);
   CK(s->dalloc((uint8_t**)&s->ring, ring_bytes));
   CK(cudaMemsetAsync(s->ring, 0, ring_bytes, st));
+  if (!s->stdp_params.empty()) {
+    int rc = setup_stdp(s);
+    if (rc != NGB_OK) return rc;
+  }
   CK(cudaStreamSynchronize(st));
   s->finalized = true;
   if (s->serving) {
@@ -1272,6 +1363,8 @@ int check_handle(ngb_sim* s) {
 
 int simulate_impl(ngb_sim* s, int64_t steps, bool profiled, double* kernel_ms, int64_t* launches) {
   if (steps < 0) return fail(NGB_ERR_INVALID_ARG, "ngb_simulate: steps < 0");
+  if (!s->stdp_params.empty() && s->t + steps > (int64_t)INT32_MAX)
+    return fail(NGB_ERR_OVERFLOW, "ngb_simulate: STDP synapses count steps in 31 bits");
   if (!s->finalized) {
     const int rc = finalize_impl(s);
     if (rc != NGB_OK) {
@@ -1326,6 +1419,7 @@ int simulate_impl(ngb_sim* s, int64_t steps, bool profiled, double* kernel_ms, i
       CK(cudaEventRecord(e[1], s->stream));
       if (s->n_aeif) CK(fused ? launch_fused_aeif(s, 0) : launch_aeif(s, 0));
       CK(cudaEventRecord(e[2], s->stream));
+      if (!fused) CK(launch_post(s));
       CK(fused ? launch_tick_add(s->clk, 1, s->sb.ctr, s->sb.ctr3, s->pdl, s->stream) : launch_del(s, 0));
       CK(cudaEventRecord(e[3], s->stream));
       if (s->mode == 3) CK(launch_tick_add(s->clk, 1, s->sb.ctr, s->sb.ctr3, false, s->stream));
@@ -1382,6 +1476,11 @@ int snapshot_take(ngb_sim* s, Snapshot& sn) {
     sn.parts.push_back({s->st6, N * 4});
   }
   if (s->ext) sn.parts.push_back({s->ext, 4 * N * 4});
+  if (s->d_rules) {  // plastic weights, arrivals and latest spikes change while trial steps run
+    sn.parts.push_back({s->w, s->K_cap * 4});
+    sn.parts.push_back({s->arrival, s->K_cap * 4});
+    sn.parts.push_back({s->sb.last_spike, N * 4});
+  }
   for (auto& p : sn.parts) {
     void* c = nullptr;
     CK(cudaMalloc(&c, p.second));
@@ -1572,6 +1671,28 @@ int ngb_connect(ngb_sim* s, int32_t src_pop, int32_t tgt_pop, const ngb_conn_spe
   return NGB_OK;
 }
 
+int ngb_connect_stdp(ngb_sim* s, int32_t src_pop, int32_t tgt_pop, const ngb_conn_spec* conn, const ngb_syn_spec* syn,
+                     const ngb_stdp_params* p) {
+  if (!s || !p) return fail(NGB_ERR_INVALID_ARG, "ngb_connect_stdp: NULL argument");
+  if (s->serving) return fail(NGB_ERR_STATE, "ngb_connect_stdp: STDP synapses are not served");
+  if (s->cfg.weight_dtype != NGB_WEIGHT_FP32)
+    return fail(NGB_ERR_INVALID_ARG, "ngb_connect_stdp: plastic weights need FP32 storage");
+  if (s->cfg.delivery == NGB_DELIVERY_RING)
+    return fail(NGB_ERR_INVALID_ARG, "ngb_connect_stdp: STDP synapses need the spike-buffer delivery scheme");
+  if (!(p->tau_plus_ms > 0 && p->tau_minus_ms > 0 && p->lambda >= 0 && p->alpha >= 0 && p->mu_plus >= 0 &&
+        p->mu_minus >= 0 && p->W_max > 0))
+    return fail(NGB_ERR_INVALID_ARG, "ngb_connect_stdp: STDP parameters");
+  if ((int)s->stdp_params.size() >= kMaxStdpRules)
+    return fail(NGB_ERR_INVALID_ARG, "ngb_connect_stdp: at most 15 STDP rules per handle");
+  const size_t before = s->calls.size();
+  const int rc = ngb_connect(s, src_pop, tgt_pop, conn, syn);
+  if (rc != NGB_OK) return rc;
+  if (s->calls.size() != before + 1) return fail(NGB_ERR_STATE, "ngb_connect_stdp: internal");
+  s->stdp_params.push_back(*p);
+  s->calls.back().stdp = (int)s->stdp_params.size();
+  return NGB_OK;
+}
+
 int ngb_finalize(ngb_sim* s) {
   int rc = check_handle(s);
   if (rc != NGB_OK) return rc;
@@ -1613,7 +1734,7 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   // Both delivery schemes are candidates only while no spike is in flight
   // (step 0) and the configuration leaves the choice open.
-  const bool both = s->cfg.delivery == 0 && s->t == 0 && !s->serving && s->sb.pend[0] != nullptr;
+  const bool both = s->cfg.delivery == 0 && s->t == 0 && !s->serving && s->sb.pend[0] != nullptr && !s->d_rules;
   const std::string key = tune_key(s);
   const char* cache = std::getenv("NGB_AUTOTUNE_CACHE");
   if (cache && *cache) {
@@ -1776,6 +1897,7 @@ int ngb_reserve(ngb_sim* s, int64_t max_neurons, int64_t max_synapses, int64_t m
                 int32_t receptors) {
   if (!s) return fail(NGB_ERR_INVALID_ARG, "NULL handle");
   if (s->finalized) return fail(NGB_ERR_STATE, "ngb_reserve: network already finalised");
+  if (!s->stdp_params.empty()) return fail(NGB_ERR_STATE, "ngb_reserve: STDP synapses are not served");
   if (max_neurons <= 0 || max_neurons >= (int64_t)kIdMask || max_synapses < 0 || max_groups < 0 ||
       ring_slots < 2 || ring_slots > 4096 || (ring_slots & (ring_slots - 1)) != 0 || receptors < 1 ||
       receptors > kMaxPorts)

@@ -13,7 +13,8 @@
 //              src_grp[N+1] u32 (first delay group of each source),
 //              grp_start[G+1] u64 and grp_delay[G] u16 (Sec. 2.2 connection
 //              groups: a source's synapses with equal delay, in delay order),
-//              tgt[K] u32 (bits 30-31 = receptor, bits 0-29 = global target),
+//              tgt[K] u32 (bits 30-31 = receptor, bits 26-29 = STDP rule + 1
+//              or 0 for a static synapse, bits 0-25 = global target),
 //              w[K] FP32 / BF16 / FP16
 //   src_meta   uint4 per source {row start lo, row start hi (16 bits) | groups
 //              << 16, synapses, first group}: everything delivery needs about
@@ -61,8 +62,12 @@ constexpr uint32_t kIdMask = (1u << kIdBits) - 1;
 constexpr int kMaxThr = 255;         // Poisson inversion table length (largest count drawn)
 constexpr int kDelayBits = 12;       // delays up to 4095 steps
 constexpr int kMaxDelay = (1 << kDelayBits) - 1;
-constexpr int kRcptShift = 30;       // synapse target word: receptor << 30 | global target
-constexpr uint32_t kTgtMask = (1u << kRcptShift) - 1;
+constexpr int kRcptShift = 30;       // synapse target word: receptor << 30 | rule << 26 | target
+constexpr int kPlastShift = 26;      // STDP rule + 1 (0: static synapse), 4 bits
+constexpr uint32_t kPlastMask = 15u;
+constexpr uint32_t kTgtMask = (1u << kPlastShift) - 1;
+constexpr int kMaxStdpRules = 15;
+constexpr int kStdpRuleShift = 40;   // incoming-plastic-synapse word: rule << 40 | synapse index
 constexpr int kMaxPorts = 4;         // receptor ports of the beta multisynapse AdEx
 
 // error flags (device word)
@@ -133,6 +138,33 @@ struct SpikeBuf {
   // pipelined ring scheme: work-item lists and counters by step mod 3
   uint4* wi3[3];
   unsigned long long* ctr3;         // [3]
+  // STDP (NULL without plastic synapses): the latest spike step of every
+  // neuron (-1: none), the first incoming plastic synapse of every neuron
+  // (in_ptr[N+1]), and the neurons with plastic inputs that fired in the
+  // step, by step parity (post[2], counts post_cnt[2], capacity N each)
+  int32_t* last_spike;
+  const uint64_t* in_ptr;
+  uint32_t* post[2];
+  unsigned long long* post_cnt;
+};
+
+// Nearest-neighbour STDP rule (Sec. 2.1): FP32 constants and the tabulated
+// pair factors e^(-n dt / tau) for lags n < n_plus / n_minus.
+struct StdpRule {
+  float A_plus, A_minus, inv_W_max, W_max, mu_plus, mu_minus;
+  int32_t n_plus, n_minus;
+  const float* k_plus;
+  const float* k_minus;
+};
+
+// Plastic synapses: the rules, the mutable FP32 weights (the CSR's), the
+// latest arrival step of every synapse (-1: none) and the incoming plastic
+// synapses of every neuron (rule << 40 | synapse index).
+struct StdpArgs {
+  const StdpRule* rules;
+  float* w;
+  int32_t* arrival;
+  const uint64_t* in_syn;
 };
 
 struct Csr {
@@ -312,10 +344,32 @@ __device__ __forceinline__ void record_spikes(bool spk, uint32_t gid, uint32_t m
 // has delay 1 is due at once (its synapses go to the due-item list of step
 // t); otherwise, and while groups remain, it joins the pending list of step
 // t + 1.  Synaptic events are counted at spike time, as in the ring scheme.
+// STDP bookkeeping of the neurons that fired at step t: the step is recorded
+// as their latest spike, and those with plastic inputs join the step's list
+// for potentiation (each neuron at most once per step, so the list of
+// capacity N cannot overflow).  Every lane of the warp must call it.
+__device__ __forceinline__ void stdp_post_spike(bool spk, uint32_t gid, int64_t t, const SpikeBuf& sb) {
+  bool listed = false;
+  if (spk) {
+    sb.last_spike[gid] = (int32_t)t;
+    listed = __ldg(sb.in_ptr + gid + 1) > __ldg(sb.in_ptr + gid);
+  }
+  const unsigned b = __ballot_sync(0xffffffffu, listed);
+  if (b == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int pb = (int)(t & 1);
+  const int leader = __ffs(b) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(sb.post_cnt + pb, (unsigned long long)__popc(b));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (listed) (pb ? sb.post[1] : sb.post[0])[base + __popc(b & ((1u << lane) - 1u))] = gid;
+}
+
 __device__ __forceinline__ void emit_spikes_age(bool spk, uint32_t gid, uint32_t mult, int64_t t, const Csr& csr,
                                                 const SpikeBuf& sb) {
   const unsigned ball = __ballot_sync(0xffffffffu, spk);
   if (ball == 0) return;
+  if (sb.last_spike) stdp_post_spike(spk, gid, t, sb);
   uint4 meta = make_uint4(0, 0, 0, 0);
   uint2 ag = make_uint2(0, 0);
   if (spk) {
@@ -562,9 +616,19 @@ cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, bool pdl, 
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 // emit: the update kernels' emission mode; kEmitPipe delivers the list of
-// step clk[0] + step_off (without advancing the clock).
+// step clk[0] + step_off (without advancing the clock).  stdp (spike-buffer
+// scheme, FP32 weights; NULL: no plastic synapses): plastic synapses are
+// depressed at their arrival and deliver the depressed weight.
 cudaError_t launch_deliver(SpikeBuf sb, Csr csr, int wdtype, Ring ring, bool fixed, int emit, int64_t* clk,
-                           int64_t step_off, int grid, bool pdl, cudaStream_t st);
+                           int64_t step_off, int grid, bool pdl, cudaStream_t st, const StdpArgs* stdp = nullptr);
+// STDP potentiation of the plastic inputs of the neurons that fired at step
+// clk[1] (after the step's update kernels, before its delivery).
+cudaError_t launch_stdp_post(SpikeBuf sb, StdpArgs a, const int64_t* clk, int grid, bool pdl, cudaStream_t st);
+// Reverse index of the plastic synapses of a built CSR (N targets, K synapse
+// words): in_ptr[N+1] (device, caller-owned) and a new device array of
+// rule << 40 | synapse index (caller frees), grouped by target.
+cudaError_t build_stdp_index(const uint32_t* tgt, uint64_t K, int64_t N, uint64_t* in_ptr, uint64_t** in_syn_out,
+                             uint64_t* n_plastic_out, cudaStream_t st);
 // Spike-buffer scheme, serving handles: mark the pending entries of sources
 // in [lo, hi) dead (their instance was retired).
 cudaError_t launch_kill_pending(uint4* list, const unsigned long long* count, int64_t cap, uint32_t lo, uint32_t hi,

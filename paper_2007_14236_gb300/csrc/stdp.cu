@@ -1,0 +1,119 @@
+// stdp.cu -- nearest-neighbour spike-timing-dependent plasticity (Sec. 2.1,
+// after Morrison et al. 2008; weight dependence of Guetig et al. 2003).
+//
+// A spike reaches its synapse `delay` steps after it was fired (its arrival
+// step).  Depression happens at the arrival, inside the spike-buffer
+// delivery of the due group (deliver_item.cuh): the synapse is depressed by
+// its target's latest spike, records the arrival step and delivers the
+// depressed weight.  Potentiation happens here, after the update kernels of
+// step t and before the delivery of step t: every neuron that fired at step
+// t and has plastic inputs (listed by the update kernels) potentiates each
+// of them by that synapse's latest arrival (at or before step t, as the
+// arrivals for step t + 1 are recorded only by the delivery that follows).
+//
+// Work: one warp per listed neuron, lanes over its incoming plastic
+// synapses (the reverse index built at finalisation).  Bytes per synapse
+// update: 8 (index word) + 4 (arrival) + 4 + 4 (weight read and write).
+#include <cuda_runtime.h>
+
+#include "builder.h"
+#include "ngb_internal.cuh"
+#include "stdp_rule.cuh"
+
+namespace ngb {
+
+__global__ void __launch_bounds__(256) k_stdp_post(SpikeBuf sb, StdpArgs a, const int64_t* clk) {
+  griddep_wait();  // the step's update kernels have completed
+  griddep_launch();
+  const int64_t t = clk[1];
+  const int pb = (int)(t & 1);
+  const unsigned long long n = sb.post_cnt[pb];
+  // the next step's list starts empty (its update kernels run after this kernel)
+  if (blockIdx.x == 0 && threadIdx.x == 0) sb.post_cnt[pb ^ 1] = 0;
+  const uint32_t* __restrict__ list = pb ? sb.post[1] : sb.post[0];
+  const int lane = threadIdx.x & 31;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  for (unsigned long long i = warp; i < n; i += nwarps) {
+    const uint32_t gid = list[i];
+    const uint64_t lo = sb.in_ptr[gid], hi = sb.in_ptr[gid + 1];
+    for (uint64_t k = lo + (uint64_t)lane; k < hi; k += 32) {
+      const uint64_t word = a.in_syn[k];
+      const uint64_t j = word & ((1ull << kStdpRuleShift) - 1);
+      const int32_t arr = a.arrival[j];
+      if (arr < 0) continue;
+      const StdpRule& r = a.rules[word >> kStdpRuleShift];
+      a.w[j] = stdp_potentiate(r, a.w[j], (int64_t)t - (int64_t)arr);
+    }
+  }
+}
+
+cudaError_t launch_stdp_post(SpikeBuf sb, StdpArgs a, const int64_t* clk, int grid, bool pdl, cudaStream_t st) {
+  return launch_k(k_stdp_post, dim3((unsigned)grid), dim3(256), pdl, st, sb, a, clk);
+}
+
+// Reverse index of the plastic synapses: count per target, scan, fill.
+namespace {
+__global__ void k_count_plastic(const uint32_t* __restrict__ tgt, uint64_t K, unsigned long long* cnt) {
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < K; j += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t tw = tgt[j];
+    if ((tw >> kPlastShift) & kPlastMask) atomicAdd(cnt + (tw & kTgtMask), 1ull);
+  }
+}
+
+__global__ void k_fill_plastic(const uint32_t* __restrict__ tgt, uint64_t K, unsigned long long* cursor,
+                               uint64_t* in_syn) {
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < K; j += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t tw = tgt[j];
+    const uint32_t cls = (tw >> kPlastShift) & kPlastMask;
+    if (!cls) continue;
+    const unsigned long long pos = atomicAdd(cursor + (tw & kTgtMask), 1ull);
+    in_syn[pos] = ((uint64_t)(cls - 1) << kStdpRuleShift) | j;
+  }
+}
+}  // namespace
+
+cudaError_t build_stdp_index(const uint32_t* tgt, uint64_t K, int64_t N, uint64_t* in_ptr, uint64_t** in_syn_out,
+                             uint64_t* n_plastic_out, cudaStream_t st) {
+  *in_syn_out = nullptr;
+  *n_plastic_out = 0;
+  unsigned long long* cnt = nullptr;
+  void* tmp = nullptr;
+  size_t tmp_bytes = 0;
+  const int grid = 1024;
+  cudaError_t e = cudaMalloc(&cnt, (size_t)(N + 1) * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, (size_t)(N + 1) * sizeof(unsigned long long), st);
+  if (e == cudaSuccess && K > 0) {
+    k_count_plastic<<<grid, 256, 0, st>>>(tgt, K, cnt);
+    e = cudaGetLastError();
+  }
+  // in_ptr = exclusive scan of the counts (N + 1 entries: the last is the total)
+  if (e == cudaSuccess) e = scan_scratch_bytes_u64((uint64_t)N + 1, &tmp_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&tmp, tmp_bytes > 0 ? tmp_bytes : 1);
+  if (e == cudaSuccess)
+    e = exclusive_scan_u64(cnt, reinterpret_cast<unsigned long long*>(in_ptr), (uint64_t)N + 1, tmp, tmp_bytes, st);
+  uint64_t total = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&total, in_ptr + N, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  uint64_t* in_syn = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&in_syn, (size_t)(total > 0 ? total : 1) * sizeof(uint64_t));
+  // the counts become fill cursors starting at in_ptr
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(cnt, in_ptr, (size_t)N * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && K > 0) {
+    k_fill_plastic<<<grid, 256, 0, st>>>(tgt, K, cnt, in_syn);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(cnt);
+  cudaFree(tmp);
+  if (e != cudaSuccess) {
+    cudaFree(in_syn);
+    return e;
+  }
+  *in_syn_out = in_syn;
+  *n_plastic_out = total;
+  return cudaSuccess;
+}
+
+}  // namespace ngb

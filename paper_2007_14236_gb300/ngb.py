@@ -57,6 +57,11 @@ class AeifParams(C.Structure):
                 ("E_rev_mV", C.c_double * 4), ("tau_rise_ms", C.c_double * 4), ("tau_decay_ms", C.c_double * 4)]
 
 
+class StdpParams(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("tau_plus_ms", "tau_minus_ms", "lambda_", "alpha", "mu_plus", "mu_minus",
+                                          "W_max")]
+
+
 class ConnSpec(C.Structure):
     _fields_ = [("rule", C.c_int32), ("allow_autapses", C.c_int32), ("K", C.c_int64)]
 
@@ -79,7 +84,7 @@ _lib = None
 
 # every symbol the header declares (checked by the tests)
 EXPORTS = ["ngb_create", "ngb_destroy", "ngb_last_error", "ngb_add_instance", "ngb_add_population",
-           "ngb_add_population_in", "ngb_connect", "ngb_finalize", "ngb_simulate", "ngb_simulate_profiled",
+           "ngb_add_population_in", "ngb_connect", "ngb_connect_stdp", "ngb_finalize", "ngb_simulate", "ngb_simulate_profiled",
            "ngb_get_spikes", "ngb_get_stats", "ngb_population_range", "ngb_get_state", "ngb_get_input",
            "ngb_get_src_ptr", "ngb_get_synapses", "ngb_autotune", "ngb_deliver_spikes_noalloc",
            "ngb_reserve", "ngb_commit_instance", "ngb_retire_instance", "ngb_instance_info"]
@@ -109,6 +114,8 @@ def load(build_if_missing: bool = True):
     L.ngb_add_population.argtypes = [P, C.c_int32, C.c_int64, P, C.POINTER(C.c_int32)]
     L.ngb_add_population_in.argtypes = [P, C.c_int32, C.c_int32, C.c_int64, P, C.POINTER(C.c_int32)]
     L.ngb_connect.argtypes = [P, C.c_int32, C.c_int32, C.POINTER(ConnSpec), C.POINTER(SynSpec)]
+    L.ngb_connect_stdp.argtypes = [P, C.c_int32, C.c_int32, C.POINTER(ConnSpec), C.POINTER(SynSpec),
+                                   C.POINTER(StdpParams)]
     L.ngb_finalize.argtypes = [P]
     L.ngb_simulate.argtypes = [P, C.c_int64]
     L.ngb_simulate_profiled.argtypes = [P, C.c_int64, P, P]
@@ -210,11 +217,16 @@ class Simulator:
         return out.value
 
     def connect(self, src: int, tgt: int, rule: str, K: int, weight: W.Dist, delay: W.Dist, receptor: int = 0,
-                allow_autapses: bool = True):
+                allow_autapses: bool = True, stdp: Optional[W.Stdp] = None):
         conn = ConnSpec(RULES[rule], int(allow_autapses), K)
         syn = SynSpec(DistSpec(DISTS[weight.kind], 0, weight.p0, weight.p1),
                       DistSpec(DISTS[delay.kind], 0, delay.p0, delay.p1), receptor, 0)
-        self._c(load().ngb_connect(self.h, src, tgt, C.byref(conn), C.byref(syn)))
+        if stdp is None:
+            self._c(load().ngb_connect(self.h, src, tgt, C.byref(conn), C.byref(syn)))
+        else:
+            q = StdpParams(stdp.tau_plus, stdp.tau_minus, stdp.lam, stdp.alpha, stdp.mu_plus, stdp.mu_minus,
+                           stdp.W_max)
+            self._c(load().ngb_connect_stdp(self.h, src, tgt, C.byref(conn), C.byref(syn), C.byref(q)))
 
     def finalize(self):
         self._c(load().ngb_finalize(self.h))
@@ -320,5 +332,5 @@ def from_spec(spec: W.NetSpec, **kw) -> Simulator:
     for p in spec.pops:
         sim.add_population(p.model, p.n, p.params, instance=p.instance)
     for c in spec.conns:
-        sim.connect(c.src, c.tgt, c.rule, c.K, c.weight, c.delay, c.receptor, c.allow_autapses)
+        sim.connect(c.src, c.tgt, c.rule, c.K, c.weight, c.delay, c.receptor, c.allow_autapses, c.stdp)
     return sim

@@ -177,6 +177,23 @@ def balanced_lif(n: int = 1000, indegree: int = 100, seed: int = 1, rate_hz: flo
     return spec
 
 
+def stdp_net(n: int = 1000, indegree: int = 100, seed: int = 1, mu: float = 1.0, lam: float = 0.01,
+             alpha: float = 1.05, j_ex: float = 87.8, rate_hz: float = 8.0, V_init_sd: float = 4.0) -> NetSpec:
+    """The small balanced LIF net with plastic excitatory-to-excitatory
+    synapses (nearest-neighbour STDP, Sec. 2.1): initial weights
+    Normal(j_ex, 0.1 j_ex), W_max = 2 j_ex, delays Uniform(1, 2) ms, pair time
+    constants 16.8 / 33.7 ms, weight exponents mu (0 additive, 1
+    multiplicative)."""
+    spec = balanced_lif(n=n, indegree=indegree, seed=seed, rate_hz=rate_hz, j_ex=j_ex, V_init_sd=V_init_sd)
+    spec.name = "stdp_net_%d" % n
+    ee = spec.conns[0]
+    assert ee.src == 0 and ee.tgt == 0
+    ee.weight = Dist("normal", j_ex, 0.1 * j_ex)
+    ee.delay = Dist("uniform", 1.0, 2.0)
+    ee.stdp = Stdp(tau_plus=16.8, tau_minus=33.7, lam=lam, alpha=alpha, mu_plus=mu, mu_minus=mu, W_max=2.0 * j_ex)
+    return spec
+
+
 def paper_balanced(n_ex: int = 8000, ce: int = 800, seed: int = 1, weight_dtype: str = "fp32",
                    rk_tol: float = 1e-10, rk_control_fp32: bool = False) -> NetSpec:
     """The paper's balanced network (Sec. 2.4 with its two parameter tables):

@@ -56,7 +56,8 @@ def test_struct_layouts_match_c(tmp_path):
     src = tmp_path / "layout.c"
     structs = {"ngb_sim_config": ngb.SimConfig, "ngb_poisson_drive": ngb.PoissonDrive,
                "ngb_lif_params": ngb.LifParams, "ngb_aeif_params": ngb.AeifParams, "ngb_conn_spec": ngb.ConnSpec,
-               "ngb_dist_spec": ngb.DistSpec, "ngb_syn_spec": ngb.SynSpec, "ngb_stats": ngb.Stats}
+               "ngb_dist_spec": ngb.DistSpec, "ngb_syn_spec": ngb.SynSpec, "ngb_stats": ngb.Stats,
+               "ngb_stdp_params": ngb.StdpParams}
     body = "".join('printf("%s %%zu\\n", sizeof(%s));\n' % (k, k) for k in structs)
     body += 'printf("aeif_poisson %zu\\n", offsetof(ngb_aeif_params, poisson));\n'
     body += 'printf("cfg_stream %zu\\n", offsetof(ngb_sim_config, stream));\n'
