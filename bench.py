@@ -69,7 +69,7 @@ def _args():
                     help="neurons of the paper's balanced network (comma-separated for a sweep)")
     ap.add_argument("--paper-ce", type=int, default=800, help="excitatory in-degree of the paper's balanced network")
     ap.add_argument("--workload", choices=["microcircuit", "small", "batched", "adex", "paper", "serve", "request",
-                                           "precision", "validate"],
+                                           "precision", "validate", "stdp"],
                     default="microcircuit",
                     help="microcircuit: the benchmark line; batched: 64 microcircuit instances vs the plain path; "
                          "adex: the 1e6-neuron AdEx network; serve: the served request stream")
@@ -78,6 +78,7 @@ def _args():
     ap.add_argument("--req-k", type=int, default=1000, help="in-degree of the single-request workload")
     ap.add_argument("--adex-n", type=int, default=1_000_000, help="neurons of the AdEx workload")
     ap.add_argument("--adex-ctl32", action="store_true", help="AdEx step-size control in FP32")
+    ap.add_argument("--stdp-n", type=int, default=100_000, help="neurons of the STDP workload (in-degree 1000)")
     ap.add_argument("--serve-duration", type=float, default=60.0)
     ap.add_argument("--scale", type=float, default=1.0,
                     help="microcircuit scale (population sizes and per-pathway counts); 1.0 is the benchmark")
@@ -343,6 +344,73 @@ def run_adex(a):
                       "step_loop": LOOPS[s1["mode"]],
                       "delivery": DELIVERY[s1["delivery"]],
                       "rk_control": "fp32" if a.adex_ctl32 else "fp64", "cpu_baseline": cpu}), flush=True)
+    return 0
+
+
+def run_stdp(a):
+    """Balanced LIF network with plastic excitatory-to-excitatory synapses
+    (nearest-neighbour STDP, multiplicative), in-degree 1000, FP32 weights:
+    real-time factor, synaptic events/s, and the potentiation + plastic
+    delivery kernels against the HBM roofline."""
+    from paper_2007_14236_gb300 import ngb, workloads as W
+    n = a.stdp_n
+    spec = W.stdp_net(n=n, indegree=1000, seed=1, mu=1.0, j_ex=25.0, rate_hz=32.0)
+    t0 = time.perf_counter()
+    sim = ngb.from_spec(spec, drain_steps=a.sim_steps)
+    sim.finalize()
+    build_s = time.perf_counter() - t0
+    if a.mode == "auto":
+        sim.autotune(200)
+    sim.simulate(1000)
+    s0 = sim.stats()
+    t1 = time.perf_counter()
+    for _ in range(a.steps):
+        sim.simulate(a.sim_steps)
+    wall = time.perf_counter() - t1
+    s1 = sim.stats()
+    bio = a.steps * a.sim_steps * 1e-4
+    ev = s1["events"] - s0["events"]
+    ms, nl = sim.simulate_profiled(500)
+    s2 = sim.stats()
+    ev_prof = s2["events"] - s1["events"]
+    sim.close()
+    # algorithmic bytes of the potentiation + delivery bracket per step: every synaptic event reads its
+    # target word, weight and adds into the input (12 B); a plastic one also reads the target's latest
+    # spike and writes weight and arrival (12 B); every potentiation reads the index word, the arrival and
+    # the weight and writes the weight (20 B).  Plastic fraction 0.64 (E -> E of 1000 inputs); potentiations
+    # per step = excitatory spikes x 800 plastic inputs (estimated from the excitatory share of spikes, 0.8).
+    spk_prof = (s2["spikes"] - s1["spikes"]) / 500.0
+    events_step = ev_prof / 500.0
+    pot_step = 0.8 * spk_prof * 800
+    bytes_step = events_step * (12 + 0.64 * 12) + pot_step * 20
+    us_del = 1e3 * ms[2] / max(1, nl[2])
+    peak, peak_src = _peaks()
+    achieved = bytes_step / (us_del * 1e-6) / 1e9
+    cpu = None
+    if not a.no_cpu_baseline:
+        import oracle
+        n_s = 10_000
+        small = W.stdp_net(n=n_s, indegree=1000, seed=1, mu=1.0, j_ex=25.0, rate_hz=32.0)
+        o = oracle.OracleNet(small)
+        o.finalize()
+        o.simulate(50)
+        e0 = o.events
+        c0 = time.perf_counter()
+        o.simulate(200)
+        cw = time.perf_counter() - c0
+        cpu = {"value": (o.events - e0) / cw, "unit": "synaptic events/s", "cores": 1, "kind": "oracle",
+               "sample": "%d-neuron network of the same recipe, 200 steps after 50, single-threaded C++ oracle "
+                         "on %s" % (n_s, _cpu_info())}
+    print(json.dumps({"workload": "stdp_balanced_lif_%d" % n, "neurons": s1["num_neurons"],
+                      "synapses": s1["num_synapses"], "build_s": build_s, "real_time_factor": wall / bio,
+                      "synaptic_events_per_s": ev / wall, "rate_hz": (s1["spikes"] - s0["spikes"]) / n / bio,
+                      "us_per_step": {"k_update_lif": 1e3 * ms[0] / max(1, nl[0]),
+                                      "k_stdp_post+k_deliver": us_del},
+                      "roofline": {"bound": "hbm", "kernel": "k_stdp_post+k_deliver", "achieved": achieved,
+                                   "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                                   "algorithmic_bytes_per_step": bytes_step},
+                      "step_loop": LOOPS[s1["mode"]], "delivery": DELIVERY[s1["delivery"]],
+                      "cpu_baseline": cpu}), flush=True)
     return 0
 
 
@@ -622,7 +690,7 @@ def main():
     if a.workload != "microcircuit":
         return {"small": run_small, "batched": run_batched, "adex": run_adex, "paper": run_paper,
                 "serve": run_serve, "request": run_request, "precision": run_precision,
-                "validate": run_validate}[a.workload](a)
+                "validate": run_validate, "stdp": run_stdp}[a.workload](a)
     ws, rank, local = _dist()
     import numpy as np
     import torch

@@ -11,9 +11,13 @@
 // of them by that synapse's latest arrival (at or before step t, as the
 // arrivals for step t + 1 are recorded only by the delivery that follows).
 //
-// Work: one warp per listed neuron, lanes over its incoming plastic
-// synapses (the reverse index built at finalisation).  Bytes per synapse
-// update: 8 (index word) + 4 (arrival) + 4 + 4 (weight read and write).
+// Work: the grid's warps are spread over the listed neurons, G warps per
+// neuron (G = warps / neurons, at least 1), each taking every G-th group of
+// 32 of the neuron's incoming plastic synapses (the reverse index built at
+// finalisation), so that a step with few firing targets still has every warp
+// issuing its gathers; each lane handles two synapses per pass with both
+// chains of loads in flight.  Bytes per synapse update: 8 (index word) + 4
+// (arrival) + 4 + 4 (weight read and write).
 #include <cuda_runtime.h>
 
 #include "builder.h"
@@ -34,16 +38,25 @@ __global__ void __launch_bounds__(256) k_stdp_post(SpikeBuf sb, StdpArgs a, cons
   const int lane = threadIdx.x & 31;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long nwarps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
-  for (unsigned long long i = warp; i < n; i += nwarps) {
-    const uint32_t gid = list[i];
+  if (n == 0) return;
+  const unsigned long long G = n >= nwarps ? 1ull : nwarps / n;
+  const uint64_t stride = 32ull * G;
+  const uint64_t kMask = (1ull << kStdpRuleShift) - 1;
+  for (unsigned long long v = warp; v < n * G; v += nwarps) {
+    const uint32_t gid = list[v / G];
+    const uint64_t sub = v % G;
     const uint64_t lo = sb.in_ptr[gid], hi = sb.in_ptr[gid + 1];
-    for (uint64_t k = lo + (uint64_t)lane; k < hi; k += 32) {
-      const uint64_t word = a.in_syn[k];
-      const uint64_t j = word & ((1ull << kStdpRuleShift) - 1);
-      const int32_t arr = a.arrival[j];
-      if (arr < 0) continue;
-      const StdpRule& r = a.rules[word >> kStdpRuleShift];
-      a.w[j] = stdp_potentiate(r, a.w[j], (int64_t)t - (int64_t)arr);
+    for (uint64_t k = lo + sub * 32 + (uint64_t)lane; k < hi; k += 2 * stride) {
+      const bool two = k + stride < hi;
+      const uint64_t w0 = a.in_syn[k];
+      const uint64_t w1 = two ? a.in_syn[k + stride] : 0ull;
+      const uint64_t j0 = w0 & kMask, j1 = w1 & kMask;
+      const int32_t r0 = a.arrival[j0];
+      const int32_t r1 = two ? a.arrival[j1] : -1;
+      const float x0 = a.w[j0];
+      const float x1 = two ? a.w[j1] : 0.f;
+      if (r0 >= 0) a.w[j0] = stdp_potentiate(a.rules[w0 >> kStdpRuleShift], x0, (int64_t)t - (int64_t)r0);
+      if (r1 >= 0) a.w[j1] = stdp_potentiate(a.rules[w1 >> kStdpRuleShift], x1, (int64_t)t - (int64_t)r1);
     }
   }
 }
