@@ -104,14 +104,171 @@ __global__ void __launch_bounds__(kLifBlock, kNpt > 1 ? (kMode == kEmitPipe ? 2 
   }
 }
 
+// Large networks (kNpt = 2 or 4 neurons per thread, ring or spike-buffer
+// scheme): a grid of resident blocks walks the tiles of kNpt x 256 neurons,
+// block b taking
+// tiles b, b + G, b + 2G, ...  Each thread loads the state and the ring slot
+// of its next tile while it computes the current one, so two tiles' loads
+// are in flight per thread.  The Poisson thresholds are read through the L1
+// cache (no shared-memory staging, so no barrier when the next tile lies in
+// another population).  The block's new spikes are collected in shared
+// memory and compacted once at the end (or when the buffer nears capacity),
+// so the list atomics leave the per-tile path and happen once per 32 spikes
+// instead of once per warp with a spike; the ring scheme reads a spiking
+// source's metadata only then.  Same arithmetic and spike lists as
+// k_update_lif.
+constexpr int kTileSpkCap = 4096;  // spikes buffered per block before a compaction
+
+template <bool kFixed, int kMode>
+__device__ __forceinline__ void flush_block_spikes(const uint32_t* s_spk, int n, int64_t t, const Csr& csr,
+                                                   const SpikeBuf& sb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int c = warp * 32; c < n; c += kLifBlock) {
+    const bool spk = c + lane < n;
+    const uint32_t gid = spk ? s_spk[c + lane] : 0u;
+    if (kMode == kEmitAge) {
+      emit_spikes_age(spk, gid, 1u, t, csr, sb);
+    } else {
+      const uint4 meta = spk ? __ldg(csr.src_meta + gid) : make_uint4(0, 0, 0, 0);
+      emit_spikes(spk, gid, 1u, t, meta, sb);
+    }
+  }
+}
+
+template <bool kFixed, int kMode, int kNpt>
+__global__ void __launch_bounds__(kLifBlock, kNpt == 4 ? 2 : 4)
+    k_update_lif_tiles(const __grid_constant__ SegTable<LifSeg> T, const uint32_t* __restrict__ thr,
+                       float* __restrict__ y_, float* __restrict__ I_, int32_t* __restrict__ ref_, Ring ring,
+                       int64_t* clk, int64_t step_off, const Csr csr, SpikeBuf sb, int scan, int64_t n_tiles) {
+  constexpr bool kAge = kMode == kEmitAge;
+  __shared__ uint32_t s_spk[kTileSpkCap];
+  __shared__ int s_n;
+  float y[kNpt], I[kNpt], in[kNpt], yn[kNpt], In[kNpt], inn[kNpt];
+  int32_t ref[kNpt], rn[kNpt];
+  auto load_state = [&](int64_t tile, const LifSeg& g, float* yy, float* ii, int32_t* rr) {
+    const int64_t k0 = (tile - g.blk_begin) * (kLifBlock * kNpt) + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < kNpt; ++j) {
+      const int64_t k = k0 + j * kLifBlock;
+      const uint32_t gid = (uint32_t)(g.offset + k);
+      yy[j] = 0.0f;
+      ii[j] = 0.0f;
+      rr[j] = 0;
+      if (k < g.n) {
+        yy[j] = y_[gid];
+        ii[j] = I_[gid];
+        rr[j] = ref_[gid];
+      }
+    }
+  };
+  auto load_input = [&](int64_t tile, const LifSeg& g, uint64_t slot_base, float* xx) {
+    const int64_t k0 = (tile - g.blk_begin) * (kLifBlock * kNpt) + threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < kNpt; ++j) {
+      const int64_t k = k0 + j * kLifBlock;
+      xx[j] = k < g.n ? ring_read<kFixed, false>(ring.p, slot_base + (uint32_t)(g.offset + k)) : 0.0f;
+    }
+  };
+  int64_t tile = blockIdx.x;
+  LifSeg sg = segment_of(T, tile < n_tiles ? tile : 0);
+  if (tile < n_tiles) load_state(tile, sg, y, I, ref);
+  if (threadIdx.x == 0) s_n = 0;
+  griddep_wait();  // the previous step's delivery has completed
+  griddep_launch();
+  const int64_t t = clk[0] + step_off;
+  if (blockIdx.x == 0 && threadIdx.x == 0) clk[1] = t;
+  const uint64_t slot_base = (uint64_t)(t & ring.L_mask) * (uint64_t)ring.R * (uint64_t)ring.N;
+  if (tile < n_tiles) load_input(tile, sg, slot_base, in);
+  if (kAge && scan)
+    scan_pending<false>(t, csr, sb, ((int64_t)blockIdx.x * kLifBlock + threadIdx.x) >> 5,
+                        ((int64_t)gridDim.x * kLifBlock) >> 5);
+  __syncthreads();  // s_n initialised
+  for (; tile < n_tiles; tile += gridDim.x) {
+    const int64_t k0 = (tile - sg.blk_begin) * (kLifBlock * kNpt) + threadIdx.x;
+    // the next tile's state and input, in flight while this tile is computed
+    const int64_t nxt = tile + gridDim.x;
+    LifSeg sn = sg;
+    if (nxt < n_tiles) {
+      sn = segment_of(T, nxt);
+      load_state(nxt, sn, yn, In, rn);
+      load_input(nxt, sn, slot_base, inn);
+    }
+#pragma unroll
+    for (int j = 0; j < kNpt; ++j) {
+      const int64_t k = k0 + j * kLifBlock;
+      if (k >= sg.n) continue;
+      const uint32_t gid = (uint32_t)(sg.offset + k);
+      ring_clear<kFixed>(ring.p, slot_base + gid);
+      float x = in[j];
+      if (sg.n_thr > 0) {
+        const uint32_t kp =
+            poisson_count(sg.seed, t - sg.t0, sg.local_off + (uint32_t)k, thr + sg.thr_off, sg.n_thr);
+        x = __fadd_rn(x, __fmul_rn((float)kp, sg.w_ext));
+      }
+      const bool spk = lif_step(sg, y[j], I[j], ref[j], x);
+      y_[gid] = y[j];
+      I_[gid] = I[j];
+      ref_[gid] = ref[j];
+      if (spk) s_spk[atomicAdd(&s_n, 1)] = gid;
+    }
+    // compact the buffered spikes when the next tile could overflow the buffer
+    __syncthreads();
+    const int n_now = s_n;
+    if (n_now > kTileSpkCap - kLifBlock * kNpt) {
+      flush_block_spikes<kFixed, kMode>(s_spk, n_now, t, csr, sb);
+      __syncthreads();
+      if (threadIdx.x == 0) s_n = 0;
+      __syncthreads();
+    }
+    sg = sn;
+#pragma unroll
+    for (int j = 0; j < kNpt; ++j) {
+      y[j] = yn[j];
+      I[j] = In[j];
+      ref[j] = rn[j];
+      in[j] = inn[j];
+    }
+  }
+  __syncthreads();
+  flush_block_spikes<kFixed, kMode>(s_spk, s_n, t, csr, sb);
+}
+
 namespace {
+// Resident blocks per SM of the tiled kernel (queried once per instantiation).
+template <bool kFixed, int kMode, int kNpt>
+int tiles_grid(int64_t n_tiles) {
+  static int per_sm = -1, sms = 0;
+  if (per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_lif_tiles<kFixed, kMode, kNpt>, kLifBlock,
+                                                      0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+  }
+  return (int)std::min<int64_t>(n_tiles, (int64_t)sms * per_sm);
+}
+
 template <bool kFixed, int kMode>
 cudaError_t lif_launch(const SegTable<LifSeg>& segs, dim3 g, int npt, const uint32_t* thr, float* y, float* I,
                        int32_t* ref, Ring ring, int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, int sc,
                        bool pdl, cudaStream_t st) {
   const dim3 b(kLifBlock);
+  constexpr int kM = kMode == kEmitPipe ? kEmitRing : kMode;  // the tiled kernel has no pipelined variant
+  if (npt > 1 && kMode != kEmitPipe) {
+    const int64_t n_tiles = (int64_t)g.x;
+    if (npt == 2)
+      return launch_k(k_update_lif_tiles<kFixed, kM, 2>, dim3((unsigned)tiles_grid<kFixed, kM, 2>(n_tiles)), b, pdl,
+                      st, segs, thr, y, I, ref, ring, clk, step_off, csr, sb, sc, n_tiles);
+    return launch_k(k_update_lif_tiles<kFixed, kM, 4>, dim3((unsigned)tiles_grid<kFixed, kM, 4>(n_tiles)), b, pdl, st,
+                    segs, thr, y, I, ref, ring, clk, step_off, csr, sb, sc, n_tiles);
+  }
   if (npt == 4)
     return launch_k(k_update_lif<kFixed, kMode, 4>, g, b, pdl, st, segs, thr, y, I, ref, ring, clk, step_off, csr, sb,
+                    sc);
+  if (npt == 2)
+    return launch_k(k_update_lif<kFixed, kMode, 2>, g, b, pdl, st, segs, thr, y, I, ref, ring, clk, step_off, csr, sb,
                     sc);
   return launch_k(k_update_lif<kFixed, kMode, 1>, g, b, pdl, st, segs, thr, y, I, ref, ring, clk, step_off, csr, sb,
                   sc);

@@ -235,7 +235,7 @@ struct ngb_sim {
   SegTable<LifSeg> lif_tab{};
   int n_lif = 0;
   int64_t lif_blocks = 0;
-  int lif_npt = 1;  // LIF neurons per thread of the per-step update kernel (1 or 4)
+  int lif_npt = 1;  // LIF neurons per thread of the per-step update kernel (1, 2 or 4)
   SegTable<AeifSeg> aeif_tab{};   // AdEx segments with exponential conductances
   SegTable<AeifSeg> aeifa_tab{};  // AdEx segments with alpha-function conductances
   SegTable<AeifSeg> aeifb_tab{};  // beta multisynapse AdEx segments
@@ -825,14 +825,16 @@ int rebuild_tables(ngb_sim* s) {
   s->aeifb_blocks = 0;
   s->n_active = 0;
   {
-    // several LIF neurons per thread when the update grid would fill the GPU
-    // more than twice over at one neuron per thread
+    // two LIF neurons per thread (the tiled kernel: resident blocks walking
+    // the tiles with the next tile's loads in flight) when the update grid
+    // would fill the GPU more than twice over at one neuron per thread
     int64_t n_lif_total = 0;
     for (const PopHost& p : s->pops)
       if (p.placed && s->inst[(size_t)p.instance].state == 1 && p.model == NGB_LIF_PSC_EXP) n_lif_total += p.n;
-    s->lif_npt = n_lif_total > 2 * (int64_t)std::max(1, s->sms) * 2048 ? 4 : 1;
+    s->lif_npt = n_lif_total > 2 * (int64_t)std::max(1, s->sms) * 2048 ? 2 : 1;
     const char* env_npt = std::getenv("NGB_LIF_NPT");
-    if (env_npt && (std::atoi(env_npt) == 1 || std::atoi(env_npt) == 4)) s->lif_npt = std::atoi(env_npt);
+    if (env_npt && (std::atoi(env_npt) == 1 || std::atoi(env_npt) == 2 || std::atoi(env_npt) == 4))
+      s->lif_npt = std::atoi(env_npt);
   }
   const int64_t lif_tile = (int64_t)kLifBlock * s->lif_npt;
   for (const PopHost& p : s->pops) {

@@ -96,6 +96,7 @@ class Server:
         built: Dict[int, tuple] = {}  # requests added as pending instances, waiting for room
         done: List[Done] = []
         ev0 = self.sim.stats()["events"]
+        host = {"build_s": 0.0, "simulate_s": 0.0, "retire_s": 0.0}  # wall time by activity
         wall0 = time.perf_counter()
         clock = 0.0  # trace time, seconds since the first arrival window opened
         last_wall = wall0
@@ -119,6 +120,7 @@ class Server:
                 fp = footprint(spec)
                 if not self._fits(fp):
                     break
+                tb = time.perf_counter()
                 if i not in built:
                     built[i] = self.sim.add_spec_instance(spec)
                 inst, pops = built[i]
@@ -128,6 +130,8 @@ class Server:
                     if e.code == -3:  # pool fragmentation: retry after the next retirements
                         break
                     raise
+                finally:
+                    host["build_s"] += time.perf_counter() - tb
                 del built[i]
                 waiting.popleft()
                 for k in fp:
@@ -145,8 +149,11 @@ class Server:
                         clock = max(clock, nxt)
                 continue
             adv = min(self.chunk, min(a["end"] for a in active.values()) - self.step)
+            ts = time.perf_counter()
             self.sim.simulate(adv)
+            host["simulate_s"] += time.perf_counter() - ts
             self.step += adv
+            tr = time.perf_counter()
             for inst in [k for k, a in active.items() if a["end"] <= self.step]:
                 a = active.pop(inst)
                 ids_all, st_all = [], []
@@ -172,13 +179,15 @@ class Server:
                     o = np.lexsort((ids, st))
                     d.ids, d.steps = ids[o], st[o]
                 done.append(d)
+            host["retire_s"] += time.perf_counter() - tr
         wall = time.perf_counter() - wall0
         events = self.sim.stats()["events"] - ev0
         lat = np.array([d.latency_s for d in done]) if done else np.zeros(1)
         summary = {"requests": len(done), "wall_s": wall, "trace_s": clock, "events": int(events),
                    "events_per_s": events / wall if wall > 0 else 0.0,
                    "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-                   "max_active": max_active, "realtime": realtime}
+                   "max_active": max_active, "realtime": realtime, "steps": self.step}
+        summary.update(host)
         return done, summary
 
     def close(self):

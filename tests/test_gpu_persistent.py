@@ -175,6 +175,35 @@ def test_four_neurons_per_thread_equal_one(ngb, delivery):
     assert a.stats()["events"] == b.stats()["events"]
 
 
+@pytest.mark.parametrize("delivery", ["ring", "spike_buffer"])
+def test_tiled_update_with_several_tiles_per_block(ngb, delivery):
+    """Two or four neurons per thread on a network of more tiles than
+    resident blocks (each block walks several tiles, crossing population
+    boundaries, with the next tile's state prefetched and the spikes compacted
+    once per block): bit-identical to one neuron per thread."""
+    spec = W.NetSpec(name="tiles", seeds=[])
+    for i in range(4):
+        W.request_net(W.Request(arrival_s=0.0, n=110_000 + 333 * i, indegree=40, bio_time_ms=30.0, seed=100 + i),
+                      spec, instance=i)
+    sims = []
+    for npt in (1, 2, 4):
+        with _env(NGB_LIF_NPT=npt):
+            s = ngb.from_spec(spec, deterministic=True, delivery=delivery)
+            s.finalize()
+        s.simulate(300)
+        sims.append(s)
+    a = sims[0]
+    assert a.stats()["num_neurons"] > 400_000
+    ai, at = a.spikes()
+    assert len(ai) > 1000
+    for b in sims[1:]:
+        bi, bt = b.spikes()
+        assert np.array_equal(at, bt) and np.array_equal(ai, bi)
+        assert np.array_equal(a.state("V_m"), b.state("V_m"))
+        assert np.array_equal(a.state("I_syn"), b.state("I_syn"))
+        assert a.stats()["events"] == b.stats()["events"]
+
+
 @pytest.mark.parametrize("name", ["adex", "paper_alpha", "mixed"])
 def test_aeif_attempt_budget_does_not_change_results(ngb, name):
     """AdEx neurons not finished within the update kernel's attempt budget
