@@ -41,7 +41,9 @@ LOOPS = {0: "graph", 1: "persistent", 2: "fused", 3: "pipelined"}
 # capture of the full-size microcircuit with FP32 weights in this configuration (delivery scheme, step loop);
 # a kernel or configuration without a capture reports null
 NCU_TRAFFIC = {("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "graph", "k_update_lif"): 2483840,
-               ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "graph", "k_deliver"): 3033728}
+               ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "graph", "k_deliver"): 3033728,
+               ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "pipelined", "k_update_lif"): 3171200,
+               ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "pipelined", "k_deliver"): 3112960}
 SIM_STEPS_PER_BENCH_STEP = 10_000  # 1 s of biological time at dt = 0.1 ms
 
 
