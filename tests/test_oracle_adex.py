@@ -18,6 +18,10 @@
   (peak W at t = tau) at every grid point; the subthreshold response to inputs
   on both receptors and a spiking run match DOP853 on the same six-variable
   system.
+* Special case a = b = 0, Delta_T = 0: the model is a conductance-based leaky
+  integrator with threshold V_peak; under a constant current V follows
+  E_L + (I_e / g_L)(1 - e^(-t g_L / C)) and the first spike falls in the step
+  holding the analytic crossing time.
 * Beta-function multisynapse conductances (the paper's interface example,
   Sec. 2.1): the conductance after one input follows the closed form
   W (e^(-t/tau_d) - e^(-t/tau_r)) normalised to a peak of W (the peak found
@@ -300,3 +304,16 @@ def test_beta_three_ports_subthreshold_match_dop853():
     assert len(sp_o) == 0
     assert np.abs(V_o - V_s).max() <= 1e-4
     assert V_o[80] > V_o[45] + 0.1 and V_o[200] < V_o[145] - 0.1 and V_o[300] > V_o[245] + 0.05
+
+
+def test_adex_without_adaptation_and_exponential_is_a_leaky_integrator():
+    I_e, g_L, C, E_L, V_peak = 800.0, 30.0, 281.0, -70.6, -50.0
+    par = _table2(a=0.0, b=0.0, Delta_T=0.0, I_e=I_e, V_peak=V_peak, V_reset=E_L)
+    out, sp = _oracle_trace(par, 300, fp64=True, record=("V_m", "w"))
+    t_star = -(C / g_L) * math.log(1.0 - (V_peak - E_L) * g_L / I_e)  # analytic crossing time, ms
+    first = int(t_star / DT)  # the step [first dt, (first + 1) dt) holds the crossing
+    assert len(sp) >= 2 and sp[0] == first
+    t = (np.arange(first) + 1) * DT
+    closed = E_L + (I_e / g_L) * (1.0 - np.exp(-t * g_L / C))
+    assert np.abs(out["V_m"][:first] - closed).max() <= 1e-7
+    assert np.all(out["w"] == 0.0)
