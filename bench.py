@@ -36,7 +36,7 @@ if ROOT not in sys.path:
 METRIC = "real-time factor & synaptic events/s; batched/served vs plain at stated tol"
 UNIT = "synaptic events/s"
 DELIVERY = {1: "ring", 2: "spike_buffer"}
-LOOPS = {0: "graph", 1: "persistent", 2: "fused", 3: "pipelined"}
+LOOPS = {0: "graph", 1: "persistent", 2: "fused", 3: "pipelined", 4: "persistent_pipelined"}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches) from one ncu
 # capture of the full-size microcircuit with FP32 weights in this configuration (delivery scheme, step loop);
 # a kernel or configuration without a capture reports null
@@ -63,10 +63,12 @@ def _args():
     ap.add_argument("--no-variant", action="store_true", help="skip the BF16-weight variant")
     ap.add_argument("--delivery", choices=["auto", "ring", "spike_buffer"], default="auto",
                     help="spike delivery scheme (auto: chosen at finalisation, and by the autotuner at step 0)")
-    ap.add_argument("--mode", choices=["auto", "graph", "persistent", "fused", "pipelined"], default="auto",
+    ap.add_argument("--mode", choices=["auto", "graph", "persistent", "fused", "pipelined", "persistent_pipelined"],
+                    default="auto",
                     help="step loop: autotuned (default), per-step kernels in CUDA graphs, the persistent kernel, "
-                         "the fused update + delivery kernels, or the pipelined loop (delivery beside the next "
-                         "step's update, two-stream CUDA graphs)")
+                         "the fused update + delivery kernels, the pipelined loop (delivery beside the next "
+                         "step's update, two-stream CUDA graphs), or the pipelined persistent kernel (one grid "
+                         "barrier per step)")
     ap.add_argument("--paper-n", type=str, default="1000000",
                     help="neurons of the paper's balanced network (comma-separated for a sweep)")
     ap.add_argument("--paper-ce", type=int, default=800, help="excitatory in-degree of the paper's balanced network")
@@ -687,7 +689,7 @@ def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
-    if a.mode in ("persistent", "fused", "pipelined"):
+    if a.mode in ("persistent", "fused", "pipelined", "persistent_pipelined"):
         os.environ["NGB_MODE"] = a.mode  # read by the library when a network is finalised
     if a.workload != "microcircuit":
         return {"small": run_small, "batched": run_batched, "adex": run_adex, "paper": run_paper,
@@ -809,7 +811,7 @@ def main():
                           "events_per_launch": ev_per_launch},
         }
     peak, peak_kind = _peaks()
-    if mode == "persistent":
+    if mode in ("persistent", "persistent_pipelined"):
         # one launch per bench step (sim_steps steps); its duration from the timed region's events
         ev_step = events / max(1, ws) / a.steps
         bytes_launch = a.sim_steps * lif_bytes + ev_step * (4 + wbytes + 4)
@@ -842,7 +844,7 @@ def main():
         "real_time_factor": rtf,
         "build_s": build_s,
         "autotune_s": tune_s,
-        "gpu_launches": int(a.steps if mode == "persistent" else
+        "gpu_launches": int(a.steps if mode in ("persistent", "persistent_pipelined") else
                             a.steps * (a.sim_steps + (a.sim_steps + 99) // 100) if mode == "fused" else
                             a.steps * (2 * a.sim_steps + (a.sim_steps + 99) // 100) if mode == "pipelined" else
                             a.steps * a.sim_steps * 2),

@@ -238,8 +238,9 @@ typedef struct {
   int64_t max_delay_steps;
   int64_t device_bytes; /* device memory held by the handle */
   int64_t mode;         /* step loop: 0 per-step kernels in CUDA graphs, 1 persistent step kernel, 2 fused
-                           update + delivery, 3 pipelined (delivery of step t beside the update of t + 1) */
-  int64_t launch_grid;  /* blocks of the delivery kernel (mode 0) or of the persistent kernel (mode 1) */
+                           update + delivery, 3 pipelined (delivery of step t beside the update of t + 1),
+                           4 pipelined persistent step kernel (one grid barrier per step) */
+  int64_t launch_grid;  /* blocks of the delivery kernel (modes 0, 3) or of the persistent kernel (modes 1, 4) */
   int64_t delivery;     /* delivery scheme in use: 1 ring, 2 spike buffer */
 } ngb_stats;
 
@@ -341,9 +342,11 @@ NGB_API int ngb_simulate_profiled(ngb_sim* sim, int64_t steps, double* kernel_ms
  * beside the next step's update, in two-stream CUDA graphs) at the same
  * delivery grids; the fused
  * loop (ring scheme: each update block delivers its own spikes, one launch
- * per step and model, in CUDA graphs); and the persistent step kernel (one
- * cooperative launch for many steps, grid barriers between its phases) at
- * 1, 2 or 4 blocks per SM; at step 0 with delivery AUTO, under both delivery
+ * per step and model, in CUDA graphs); the persistent step kernel (one
+ * cooperative launch for many steps, grid barriers between its phases) and,
+ * with the ring scheme, its pipelined variant (one grid barrier per step: the
+ * update phase delivers delay-1 groups and the queued groups of the previous
+ * step) at 1 to 4 blocks per SM; at step 0 with delivery AUTO, under both delivery
  * schemes (ngb_stats.delivery).  Each candidate is
  * timed over trial_steps steps (0 = 500); the simulation state is saved
  * before and restored after the trials, so the simulation does not advance.
@@ -351,7 +354,7 @@ NGB_API int ngb_simulate_profiled(ngb_sim* sim, int64_t steps, double* kernel_ms
  * environment variable NGB_AUTOTUNE_CACHE naming a file, results are looked up
  * and appended there per (GPU, network shape) key.  *deliver_grid_out (may be
  * NULL) receives the chosen grid.  The environment variable NGB_MODE
- * ("persistent", "fused" or "pipelined") selects that step loop at
+ * ("persistent", "persistent_pipelined", "fused" or "pipelined") selects that step loop at
  * finalisation without tuning. */
 NGB_API int ngb_autotune(ngb_sim* sim, int64_t trial_steps, int32_t* deliver_grid_out);
 

@@ -247,7 +247,8 @@ struct ngb_sim {
   int deliver_grid = 0;
   bool pdl = true;  // programmatic dependent launch between the step's kernels
   int mode = 0;  // 0: per-step kernels in CUDA graphs, 1: persistent step kernel, 2: fused update + delivery,
-                 // 3: pipelined (delivery of step t beside the update of step t + 1, two streams)
+                 // 3: pipelined (delivery of step t beside the update of step t + 1, two streams),
+                 // 4: pipelined persistent step kernel (ring scheme, one grid barrier per step)
   cudaStream_t stream2 = nullptr;  // second stream of the pipelined loop's graphs
   bool persist_ok = false;
   int persist_grid = 0;
@@ -454,9 +455,15 @@ cudaError_t launch_step(ngb_sim* s) {
 cudaError_t launch_persistent_chunk(ngb_sim* s, int64_t steps) {
   cudaError_t e = cudaMemsetAsync(s->bar, 0, 4 * sizeof(unsigned), s->stream);
   if (e != cudaSuccess) return e;
+  // the pipelined variant starts with empty queue counters (every launch
+  // delivers its last queue before it ends; steps run by other loops in
+  // between leave the counters stale)
+  if (s->mode == 4) e = cudaMemsetAsync(s->sb.ctr3, 0, 3 * sizeof(unsigned long long), s->stream);
+  if (e != cudaSuccess) return e;
   s->pa.steps = steps;
   s->pa.sb = s->sb;
   return launch_persistent(s->pa, s->cfg.deterministic != 0, s->cfg.weight_dtype, s->n_lif > 0, s->n_aeif > 0,
+                           s->mode == 4,
                            s->persist_grid, s->persist_smem, s->stream);
 }
 
@@ -1045,11 +1052,16 @@ int rebuild_tables(ngb_sim* s) {
     s->persist_smem = a.off_thr + a16(thr_all.size() * 4);
     const bool was_ok = s->persist_ok;
     s->persist_ok = false;
-    // the persistent kernel integrates the two-receptor models only
+    // the persistent kernel integrates the two-receptor models only; its grid
+    // fits both variants (per-step barriers, pipelined)
     if (s->persist_smem <= 200 * 1024 && s->n_aeif_beta == 0) {
-      int bpsm = 0;
+      int bpsm = 0, bpsm_pipe = 0;
       if (persistent_max_blocks_per_sm(s->cfg.deterministic != 0, s->cfg.weight_dtype, s->n_lif > 0,
-                                       s->n_aeif > 0, s->persist_smem, &bpsm) == cudaSuccess && bpsm > 0) {
+                                       s->n_aeif > 0, false, s->persist_smem, &bpsm) == cudaSuccess &&
+          persistent_max_blocks_per_sm(s->cfg.deterministic != 0, s->cfg.weight_dtype, s->n_lif > 0,
+                                       s->n_aeif > 0, true, s->persist_smem, &bpsm_pipe) == cudaSuccess &&
+          std::min(bpsm, bpsm_pipe) > 0) {
+        bpsm = std::min(bpsm, bpsm_pipe);
         s->persist_ok = true;
         s->persist_max_bpsm = bpsm;
         if (!was_ok || s->persist_grid <= 0 || s->persist_grid > s->sms * bpsm)
@@ -1057,8 +1069,10 @@ int rebuild_tables(ngb_sim* s) {
       }
       cudaGetLastError();
     }
-    if (!s->persist_ok && s->mode == 1) s->mode = 0;
+    if (!s->persist_ok && (s->mode == 1 || s->mode == 4)) s->mode = 0;
   }
+  // the pipelined persistent kernel delivers with the ring scheme
+  if (s->mode == 4 && (s->scheme != 1 || !s->sb.wi3[0])) s->mode = 0;
   // plastic synapses run in the per-step kernel loop (spike-buffer scheme)
   if (s->d_rules) {
     s->persist_ok = false;
@@ -1349,6 +1363,7 @@ int finalize_impl(ngb_sim* s) {
   const char* env_mode = std::getenv("NGB_MODE");
   s->mode = 0;
   if (env_mode && std::string(env_mode) == "persistent") s->mode = 1;
+  if (env_mode && std::string(env_mode) == "persistent_pipelined" && s->scheme == 1) s->mode = 4;
   if (env_mode && std::string(env_mode) == "fused" && s->scheme == 1) s->mode = 2;
   if (env_mode && std::string(env_mode) == "pipelined" && s->scheme == 1 && s->stream2) s->mode = 3;
   s->graph_steps = s->cfg.steps_per_graph == 0 ? 100 : std::max(0, s->cfg.steps_per_graph);
@@ -1384,7 +1399,7 @@ int simulate_impl(ngb_sim* s, int64_t steps, bool profiled, double* kernel_ms, i
     while (left > 0) {
       const int64_t chunk = std::min<int64_t>(left, s->drain_steps);
       int64_t done = 0;
-      if (s->mode == 1) {
+      if (s->mode == 1 || s->mode == 4) {
         CK(launch_persistent_chunk(s, chunk));
         done = chunk;
       }
@@ -1745,14 +1760,15 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
     int m = 0, g = 0, pg = 0, sc = 0;
     while (in >> k >> m >> g >> pg >> sc) {
       if (k == key && g > 0 && (m == 0 || (m == 2 && sc == 1 && fused_ok(s)) || (m == 3 && sc == 1 && s->stream2) ||
-                                (s->persist_ok && pg > 0)) &&
+                                (m == 1 && s->persist_ok && pg > 0) ||
+                                (m == 4 && s->persist_ok && pg > 0 && sc == 1 && s->sb.wi3[0])) &&
           (sc == s->scheme || both)) {
         set_scheme(s, sc);
         s->mode = m;
         s->deliver_grid = g;
         if (pg > 0) s->persist_grid = pg;
         rc = capture_graph(s);
-        if (rc == NGB_OK && deliver_grid_out) *deliver_grid_out = m == 1 ? s->persist_grid : g;
+        if (rc == NGB_OK && deliver_grid_out) *deliver_grid_out = (m == 1 || m == 4) ? s->persist_grid : g;
         return rc;
       }
     }
@@ -1848,9 +1864,11 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
       }
       s->mode = 0;
     }
-    // persistent step kernel: blocks per SM
-    if (rc == NGB_OK && s->persist_ok) {
-      for (int b : {1, 2, 4}) {
+    // persistent step kernel (and its pipelined variant with the ring scheme): blocks per SM
+    for (int pm : {1, 4}) {
+      if (rc != NGB_OK || !s->persist_ok || (pm == 4 && (scheme != 1 || !s->sb.wi3[0]))) continue;
+      s->mode = pm;
+      for (int b : {1, 2, 3, 4}) {
         if (b > s->persist_max_bpsm) break;
         s->persist_grid = b * sms;
         rc = snapshot_restore(s, sn);
@@ -1868,11 +1886,12 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
         const double per_step = ms / (double)trial_steps;
         if (per_step < best_ms) {
           best_ms = per_step;
-          best_mode = 1;
+          best_mode = pm;
           best_pgrid = s->persist_grid;
           best_scheme = scheme;
         }
       }
+      s->mode = 0;
     }
   }
   cudaEventDestroy(e0);
@@ -1891,7 +1910,7 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
     out << key << " " << best_mode << " " << best_grid << " " << (s->persist_ok ? best_pgrid : 0) << " "
         << best_scheme << "\n";
   }
-  if (deliver_grid_out) *deliver_grid_out = best_mode == 1 ? best_pgrid : best_grid;
+  if (deliver_grid_out) *deliver_grid_out = (best_mode == 1 || best_mode == 4) ? best_pgrid : best_grid;
   return NGB_OK;
 }
 
@@ -2033,7 +2052,7 @@ int ngb_get_stats(ngb_sim* s, ngb_stats* out) {
     out->max_delay_steps = s->max_delay;
     out->device_bytes = (int64_t)s->dev_bytes;
     out->mode = s->mode;
-    out->launch_grid = s->mode == 1   ? s->persist_grid
+    out->launch_grid = (s->mode == 1 || s->mode == 4) ? s->persist_grid
                        : s->mode == 2 ? s->lif_blocks + s->aeif_blocks + s->aeifa_blocks
                                       : s->deliver_grid;  // graph and pipelined loops: the delivery grid
     out->delivery = s->scheme;

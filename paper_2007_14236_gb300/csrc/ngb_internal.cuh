@@ -576,8 +576,10 @@ cudaError_t launch_finish_aeif(const SegTable<AeifSeg>& segs, int grid, const Ae
                                bool fixed, int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, int emit,
                                bool pdl, cudaStream_t st);
 cudaError_t launch_tick(int64_t* clk, bool pdl, cudaStream_t st);
-cudaError_t persistent_max_blocks_per_sm(bool fixed, int wdtype, bool lif, bool aeif, size_t smem, int* out);
-cudaError_t launch_persistent(const PersistArgs& a, bool fixed, int wdtype, bool lif, bool aeif, int grid,
+// pipe: the pipelined variant (ring scheme; one grid barrier per step).
+cudaError_t persistent_max_blocks_per_sm(bool fixed, int wdtype, bool lif, bool aeif, bool pipe, size_t smem,
+                                         int* out);
+cudaError_t launch_persistent(const PersistArgs& a, bool fixed, int wdtype, bool lif, bool aeif, bool pipe, int grid,
                               size_t smem, cudaStream_t st);
 
 // Per-source metadata for the update kernels' spike lists; *total_items

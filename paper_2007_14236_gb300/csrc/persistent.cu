@@ -20,6 +20,18 @@
 // spikes join that list or the pending list, and the delivery phase scatters
 // the due items into the single ring slot.
 //
+// Pipelined variant (kPipe, ring scheme): one grid barrier per step.  The
+// update phase of step t also delivers each new spike's delay-1 group into
+// slot t + 1 and queues its other groups (list t mod 3); in the same phase the
+// warps deliver the queue of step t - 1, whose groups land in slots t + 1 and
+// later, so nothing written in the phase is read in it (slot t, read and
+// cleared by the update, receives no write after the barrier that ends step
+// t - 1).  After the last step the launch delivers that step's queue, so no
+// queued work crosses a launch boundary; the host zeroes the queue counters
+// before each launch.  The barrier is a monotonic arrival
+// counter (zeroed before each launch) polled until it reaches the number of
+// arrivals of the barrier: one atomic per block and no reset round trip.
+//
 // The step counter lives in registers.  The arithmetic is the same device
 // code as the per-step kernels (neuron_step.cuh, aeif_rk.cuh,
 // deliver_item.cuh), so both paths give identical results.  Data written by
@@ -106,6 +118,41 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned long long spin
   return s_ok != 0;
 }
 
+// Grid barrier `k` (0, 1, ...) of the launch on a monotonic arrival counter:
+// each block arrives with a release reduction and waits (bounded, acquire
+// polls) until all gridDim.x * (k + 1) arrivals are in.  Returns false when the
+// launch must stop (this block or another gave up).
+__device__ __forceinline__ void red_add_release_u32(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ bool grid_sync_mono(unsigned* bar, unsigned k, unsigned long long spin_limit,
+                                               uint32_t* err, bool withhold) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (!withhold) red_add_release_u32(bar, 1u);
+    const unsigned target = gridDim.x * (k + 1u);
+    unsigned long long spins = 0;
+    while (ld_acquire_u32(bar) < target) {
+      if ((spins & 63u) == 63u && ld_acquire_u32(bar + 2) != 0u) {  // another block gave up
+        ok = 0;
+        break;
+      }
+      if (++spins > spin_limit) {
+        atomicOr(err, kErrBarrierTimeout);
+        atomicExch(bar + 2, 1u);
+        ok = 0;
+        break;
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 template <typename Seg>
 __device__ __forceinline__ int seg_of(const int64_t* voff, int n, int64_t v) {
   int lo = 0, hi = n;
@@ -119,7 +166,7 @@ __device__ __forceinline__ int seg_of(const int64_t* voff, int n, int64_t v) {
 
 }  // namespace
 
-template <bool kFixed, typename WT, bool kLif, bool kAeif>
+template <bool kFixed, typename WT, bool kLif, bool kAeif, bool kPipe>
 __global__ void __launch_bounds__(kPersistBlock) k_persistent(PersistArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   LifSeg* s_lseg = reinterpret_cast<LifSeg*>(smem);
@@ -137,18 +184,25 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(PersistArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * kPersistBlock + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * kPersistBlock) >> 5;
+  // pipelined variant: the last quarter of the warps delivers the previous
+  // step's queue while the others update, so the two overlap within a phase
+  const int64_t dwarps = kPipe ? (nwarps / 4 > 0 ? nwarps / 4 : 1) : 0;
+  const int64_t uwarps = kPipe && nwarps > 1 ? nwarps - dwarps : nwarps;
+  const bool updater = warp < uwarps;
   const Ring ring = a.ring;
   const uint64_t plane = (uint64_t)ring.R * (uint64_t)ring.N;
   int64_t t = a.clk[0];
+  const int64_t t_first = t;  // clk[0] is rewritten by block 0 at the end of the launch
   unsigned long long nsub = 0;
   bool cap_hit = false;
   bool first_barrier = true;
   for (int64_t step = 0; step < a.steps; ++step) {
     const uint64_t slot = (uint64_t)(t & ring.L_mask);
     // ------------------------------------------------------------ update phase
-    if (a.age) scan_pending<true>(t, a.csr, a.sb, warp, nwarps);
-    if (kLif) {
-      for (int64_t vb = warp * 32; vb < a.n_lif; vb += nwarps * 32) {
+    if (kPipe && blockIdx.x == 0 && threadIdx.x == 0) a.sb.ctr3[(int)((t + 1) % 3)] = 0;  // consumed in phase t - 1
+    if (!kPipe && a.age) scan_pending<true>(t, a.csr, a.sb, warp, nwarps);
+    if (kLif && updater) {
+      for (int64_t vb = warp * 32; vb < a.n_lif; vb += uwarps * 32) {
         const int64_t v = vb + lane;
         const bool valid = v < a.n_lif;
         const int si = valid ? seg_of<LifSeg>(s_lvoff, a.n_lseg, v) : 0;
@@ -172,12 +226,15 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(PersistArgs a) {
           a.st1[gid] = I;
           a.ref[gid] = ref;
         }
-        if (a.age) emit_spikes_age(spk, gid, 1u, t, a.csr, a.sb);
+        if (kPipe)
+          emit_spikes_pipe<kFixed>(spk, gid, 1u, t, meta, spk ? __ldg(a.csr.src_age + gid) : make_uint2(0, 0), a.csr,
+                                   ring, a.sb);
+        else if (a.age) emit_spikes_age(spk, gid, 1u, t, a.csr, a.sb);
         else emit_spikes(spk, gid, 1u, t, meta, a.sb);
       }
     }
-    if (kAeif) {
-      for (int64_t vb = warp * 32; vb < a.n_aeif; vb += nwarps * 32) {
+    if (kAeif && updater) {
+      for (int64_t vb = warp * 32; vb < a.n_aeif; vb += uwarps * 32) {
         const int64_t v = vb + lane;
         const bool valid = v < a.n_aeif;
         const int si = valid ? seg_of<AeifSeg>(s_avoff, a.n_aseg, v) : 0;
@@ -217,9 +274,30 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(PersistArgs a) {
           a.st4[gid] = (float)h;
         }
         const uint32_t mult = nspk > 63u ? 63u : nspk;
-        if (a.age) emit_spikes_age(nspk > 0, gid, mult, t, a.csr, a.sb);
+        if (kPipe)
+          emit_spikes_pipe<kFixed>(nspk > 0, gid, mult, t, meta,
+                                   nspk > 0 ? __ldg(a.csr.src_age + gid) : make_uint2(0, 0), a.csr, ring, a.sb);
+        else if (a.age) emit_spikes_age(nspk > 0, gid, mult, t, a.csr, a.sb);
         else emit_spikes(nspk > 0, gid, mult, t, meta, a.sb);
       }
+    }
+    if (kPipe) {
+      // the queue of step t - 1 (groups with delay >= 2: slots t + 1 and later)
+      if (step > 0) {
+        const int q = (int)((t - 1) % 3);
+        const uint32_t n = (uint32_t)(__ldcg(a.sb.ctr3 + q) & kChunkMask);
+        const uint4* wq = a.sb.wi3[q];
+        const int64_t w0 = uwarps < nwarps ? warp - uwarps : warp;  // a one-warp grid does both
+        if (w0 >= 0)
+          for (int64_t ch = w0; ch < (int64_t)n; ch += (uwarps < nwarps ? dwarps : nwarps))
+            deliver_work_item<WT, kFixed>(__ldcg(wq + 2 * ch), __ldcg(wq + 2 * ch + 1), t - 1, a.csr, ring, lane);
+      }
+      if (!grid_sync_mono(a.bar, (unsigned)step, a.spin_limit, a.sb.err,
+                          first_barrier && (int)blockIdx.x == a.withhold_block))
+        break;
+      first_barrier = false;
+      ++t;
+      continue;
     }
     if (!grid_sync(a.bar, a.spin_limit, a.sb.err, first_barrier && (int)blockIdx.x == a.withhold_block)) break;
     first_barrier = false;
@@ -245,6 +323,14 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(PersistArgs a) {
     if (!grid_sync(a.bar, a.spin_limit, a.sb.err, false)) break;
     ++t;
   }
+  if (kPipe && t > t_first && ld_acquire_u32(a.bar + 2) == 0u) {
+    // the last step's queue: delivered before the launch ends
+    const int q = (int)((t - 1) % 3);
+    const uint32_t n = (uint32_t)(__ldcg(a.sb.ctr3 + q) & kChunkMask);
+    const uint4* wq = a.sb.wi3[q];
+    for (int64_t ch = warp; ch < (int64_t)n; ch += nwarps)
+      deliver_work_item<WT, kFixed>(__ldcg(wq + 2 * ch), __ldcg(wq + 2 * ch + 1), t - 1, a.csr, ring, lane);
+  }
   if (kAeif) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nsub += __shfl_xor_sync(0xffffffffu, nsub, o);
@@ -260,40 +346,42 @@ __global__ void __launch_bounds__(kPersistBlock) k_persistent(PersistArgs a) {
 namespace {
 
 template <bool kFixed, typename WT, bool kLif, bool kAeif>
-void* pick() {
-  return reinterpret_cast<void*>(&k_persistent<kFixed, WT, kLif, kAeif>);
+void* pick(bool pipe) {
+  if (pipe) return reinterpret_cast<void*>(&k_persistent<kFixed, WT, kLif, kAeif, true>);
+  return reinterpret_cast<void*>(&k_persistent<kFixed, WT, kLif, kAeif, false>);
 }
 
 template <bool kFixed, typename WT>
-void* pick_models(bool lif, bool aeif) {
-  if (lif && aeif) return pick<kFixed, WT, true, true>();
-  if (aeif) return pick<kFixed, WT, false, true>();
-  return pick<kFixed, WT, true, false>();
+void* pick_models(bool lif, bool aeif, bool pipe) {
+  if (lif && aeif) return pick<kFixed, WT, true, true>(pipe);
+  if (aeif) return pick<kFixed, WT, false, true>(pipe);
+  return pick<kFixed, WT, true, false>(pipe);
 }
 
-void* persistent_kernel(bool fixed, int wdtype, bool lif, bool aeif) {
+void* persistent_kernel(bool fixed, int wdtype, bool lif, bool aeif, bool pipe) {
   if (fixed) {
-    if (wdtype == 0) return pick_models<true, float>(lif, aeif);
-    if (wdtype == 1) return pick_models<true, __nv_bfloat16>(lif, aeif);
-    return pick_models<true, __half>(lif, aeif);
+    if (wdtype == 0) return pick_models<true, float>(lif, aeif, pipe);
+    if (wdtype == 1) return pick_models<true, __nv_bfloat16>(lif, aeif, pipe);
+    return pick_models<true, __half>(lif, aeif, pipe);
   }
-  if (wdtype == 0) return pick_models<false, float>(lif, aeif);
-  if (wdtype == 1) return pick_models<false, __nv_bfloat16>(lif, aeif);
-  return pick_models<false, __half>(lif, aeif);
+  if (wdtype == 0) return pick_models<false, float>(lif, aeif, pipe);
+  if (wdtype == 1) return pick_models<false, __nv_bfloat16>(lif, aeif, pipe);
+  return pick_models<false, __half>(lif, aeif, pipe);
 }
 
 }  // namespace
 
-cudaError_t persistent_max_blocks_per_sm(bool fixed, int wdtype, bool lif, bool aeif, size_t smem, int* out) {
-  void* k = persistent_kernel(fixed, wdtype, lif, aeif);
+cudaError_t persistent_max_blocks_per_sm(bool fixed, int wdtype, bool lif, bool aeif, bool pipe, size_t smem,
+                                         int* out) {
+  void* k = persistent_kernel(fixed, wdtype, lif, aeif, pipe);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, kPersistBlock, smem);
 }
 
-cudaError_t launch_persistent(const PersistArgs& a, bool fixed, int wdtype, bool lif, bool aeif, int grid,
+cudaError_t launch_persistent(const PersistArgs& a, bool fixed, int wdtype, bool lif, bool aeif, bool pipe, int grid,
                               size_t smem, cudaStream_t st) {
-  void* k = persistent_kernel(fixed, wdtype, lif, aeif);
+  void* k = persistent_kernel(fixed, wdtype, lif, aeif, pipe);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3(kPersistBlock);

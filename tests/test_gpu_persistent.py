@@ -86,6 +86,59 @@ def test_persistent_equals_per_step_kernels(ngb, name):
         assert np.array_equal(ot, bt) and np.array_equal(oi, bi)
 
 
+@pytest.mark.parametrize("name", ["balanced_lif", "microcircuit", "adex", "batched", "paper_alpha", "mixed",
+                                  "mc_bf16"])
+def test_pipelined_persistent_equals_per_step_kernels(ngb, name):
+    """The pipelined persistent kernel (one grid barrier per step; delay-1
+    groups delivered by the update phase, the others one phase later), in
+    launches of uneven length: bit-identical spike trains, state, inputs of the
+    coming steps and event counts."""
+    spec = {"balanced_lif": lambda: W.balanced_lif(n=1000, indegree=100, seed=1),
+            "mixed": lambda: W.mixed_net(seed=2),
+            "paper_alpha": lambda: W.paper_balanced(n_ex=1600, ce=160, seed=3),
+            "microcircuit": lambda: W.microcircuit(scale=0.03, seed=7, keep_indegree=False),
+            "mc_bf16": lambda: W.microcircuit(scale=0.03, seed=8, keep_indegree=False, weight_dtype="bf16"),
+            "adex": lambda: W.balanced_adex(n=2000, indegree=100, seed=2, weight_dtype="fp32", poisson_weight=4.0,
+                                            w_ex=2.0, w_in=4.0),
+            "batched": lambda: W.batched_microcircuits(n_instances=3, scale_lo=0.02, scale_hi=0.04, seed=7)}[name]()
+    a = ngb.from_spec(spec, deterministic=True, delivery="ring")
+    with _env(NGB_MODE="persistent_pipelined"):
+        b = ngb.from_spec(spec, deterministic=True, delivery="ring", drain_steps=250)
+        b.finalize()
+    assert b.stats()["mode"] == 4
+    a.simulate(700)
+    for chunk in (1, 2, 97, 300, 300):  # 1- and 2-step launches, then chunks of 250
+        b.simulate(chunk)
+    ai, at = a.spikes()
+    bi, bt = b.spikes()
+    assert len(ai) > 50
+    assert np.array_equal(at, bt) and np.array_equal(ai, bi)
+    assert np.array_equal(a.state("V_m"), b.state("V_m"))
+    assert a.stats()["events"] == b.stats()["events"]
+    for off in range(0, 4):
+        assert np.array_equal(a.input(0, off), b.input(0, off))
+    b.simulate_profiled(20)  # per-step kernels after a pipelined persistent launch, then back
+    b.simulate(30)
+    a.simulate(50)
+    assert np.array_equal(a.spikes()[0], b.spikes()[0]) and np.array_equal(a.state("V_m"), b.state("V_m"))
+
+
+def test_pipelined_persistent_barrier_wait_is_bounded(ngb):
+    spec = W.balanced_lif(n=1000, indegree=100, seed=1)
+    with _env(NGB_TEST_WITHHOLD_BLOCK=0, NGB_BARRIER_SPIN_LIMIT=20000, NGB_MODE="persistent_pipelined"):
+        sim = ngb.from_spec(spec, delivery="ring")
+        sim.finalize()
+    assert sim.stats()["mode"] == 4
+    with pytest.raises(ngb.NgbError) as e:
+        sim.simulate(50)
+    assert e.value.code == -5  # NGB_ERR_TIMEOUT
+    sim.close()
+    with _env(NGB_MODE="persistent_pipelined"):
+        ok = ngb.from_spec(spec, deterministic=True, delivery="ring")
+        ok.simulate(100)
+    assert ok.stats()["steps"] == 100
+
+
 def test_persistent_fp32_rates(ngb):
     spec = W.microcircuit(scale=0.05, seed=5, keep_indegree=False)
     a = ngb.from_spec(spec)
@@ -104,7 +157,7 @@ def test_autotune_does_not_advance_the_simulation(ngb):
     b.simulate(200)
     grid = b.autotune(300)
     st = b.stats()
-    assert grid > 0 and st["steps"] == 200 and st["mode"] in (0, 1, 2, 3)
+    assert grid > 0 and st["steps"] == 200 and st["mode"] in (0, 1, 2, 3, 4)
     a.simulate(500)
     b.simulate(500)
     assert np.array_equal(a.spikes()[0], b.spikes()[0]) and np.array_equal(a.spikes()[1], b.spikes()[1])
