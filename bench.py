@@ -89,6 +89,20 @@ def _args():
     return ap.parse_args()
 
 
+def reduce_over_ranks(pg, seconds: float, events: float, device: str = "cuda"):
+    """Whole-job figures over independent replicas (one network per rank, no
+    collective on the data path): the slowest rank's time and the sum of the
+    ranks' synaptic events.  pg is torch.distributed (or None for one rank)."""
+    if pg is None:
+        return seconds, events
+    import torch
+    t = torch.tensor([seconds, float(events)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -748,12 +762,7 @@ def main():
     clocks = sampler.stop()
     ms = e_start.elapsed_time(e_end)
     events = sim.stats()["events"] - ev_before
-    if pg is not None:
-        t = torch.tensor([ms, float(events)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
-        pg.all_reduce(t, op=pg.ReduceOp.SUM)
-        ms, events = float(tmax[0]), float(t[1])
+    ms, events = reduce_over_ranks(pg, ms, events)
     bio_s_rank = a.steps * a.sim_steps * spec.dt * 1e-3
     value = events / (ms * 1e-3)
     rtf = (ms * 1e-3) / bio_s_rank
@@ -772,12 +781,7 @@ def main():
     barrier()
     e2e_s = time.perf_counter() - h0
     e2e_events = sim.stats()["events"] - ev_b
-    if pg is not None:
-        t = torch.tensor([e2e_s, float(e2e_events)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
-        pg.all_reduce(t, op=pg.ReduceOp.SUM)
-        e2e_s, e2e_events = float(tmax[0]), float(t[1])
+    e2e_s, e2e_events = reduce_over_ranks(pg, e2e_s, e2e_events)
 
     # ---------------------------------------------------------------- per-kernel times (CUDA events)
     ev_p0 = sim.stats()["events"]
