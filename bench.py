@@ -36,7 +36,8 @@ if ROOT not in sys.path:
 METRIC = "real-time factor & synaptic events/s; batched/served vs plain at stated tol"
 UNIT = "synaptic events/s"
 DELIVERY = {1: "ring", 2: "spike_buffer"}
-LOOPS = {0: "graph", 1: "persistent", 2: "fused", 3: "pipelined", 4: "persistent_pipelined"}
+LOOPS = {0: "graph", 1: "persistent", 2: "fused", 3: "pipelined", 4: "persistent_pipelined",
+         5: "pipelined_one_kernel"}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches) from one ncu
 # capture of the full-size microcircuit with FP32 weights in this configuration (delivery scheme, step loop);
 # a kernel or configuration without a capture reports null
@@ -63,7 +64,8 @@ def _args():
     ap.add_argument("--no-variant", action="store_true", help="skip the BF16-weight variant")
     ap.add_argument("--delivery", choices=["auto", "ring", "spike_buffer"], default="auto",
                     help="spike delivery scheme (auto: chosen at finalisation, and by the autotuner at step 0)")
-    ap.add_argument("--mode", choices=["auto", "graph", "persistent", "fused", "pipelined", "persistent_pipelined"],
+    ap.add_argument("--mode", choices=["auto", "graph", "persistent", "fused", "pipelined", "persistent_pipelined",
+                                       "pipelined_one_kernel"],
                     default="auto",
                     help="step loop: autotuned (default), per-step kernels in CUDA graphs, the persistent kernel, "
                          "the fused update + delivery kernels, the pipelined loop (delivery beside the next "
@@ -703,7 +705,7 @@ def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
-    if a.mode in ("persistent", "fused", "pipelined", "persistent_pipelined"):
+    if a.mode in ("persistent", "fused", "pipelined", "persistent_pipelined", "pipelined_one_kernel"):
         os.environ["NGB_MODE"] = a.mode  # read by the library when a network is finalised
     if a.workload != "microcircuit":
         return {"small": run_small, "batched": run_batched, "adex": run_adex, "paper": run_paper,
@@ -851,6 +853,8 @@ def main():
         "gpu_launches": int(a.steps if mode in ("persistent", "persistent_pipelined") else
                             a.steps * (a.sim_steps + (a.sim_steps + 99) // 100) if mode == "fused" else
                             a.steps * (2 * a.sim_steps + (a.sim_steps + 99) // 100) if mode == "pipelined" else
+                            a.steps * (a.sim_steps + 2 * ((a.sim_steps + 99) // 100)) if mode == "pipelined_one_kernel"
+                            else
                             a.steps * a.sim_steps * 2),
         "e2e": {"value": e2e_events / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(d2h / a.steps), "real_time_factor": e2e_s / bio_s_rank},

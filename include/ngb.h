@@ -239,7 +239,8 @@ typedef struct {
   int64_t device_bytes; /* device memory held by the handle */
   int64_t mode;         /* step loop: 0 per-step kernels in CUDA graphs, 1 persistent step kernel, 2 fused
                            update + delivery, 3 pipelined (delivery of step t beside the update of t + 1),
-                           4 pipelined persistent step kernel (one grid barrier per step) */
+                           4 pipelined persistent step kernel (one grid barrier per step), 5 pipelined
+                           with one kernel per step (LIF networks) */
   int64_t launch_grid;  /* blocks of the delivery kernel (modes 0, 3) or of the persistent kernel (modes 1, 4) */
   int64_t delivery;     /* delivery scheme in use: 1 ring, 2 spike buffer */
 } ngb_stats;
@@ -339,8 +340,9 @@ NGB_API int ngb_simulate_profiled(ngb_sim* sim, int64_t steps, double* kernel_ms
  * graphs with the delivery kernel at 1, 2, 4 or 8 blocks per SM; the
  * pipelined loop (ring scheme: a spike's delay-1 group delivered by the
  * update kernel at once, its other groups by a delivery kernel that runs
- * beside the next step's update, in two-stream CUDA graphs) at the same
- * delivery grids; the fused
+ * beside the next step's update, in two-stream CUDA graphs; for LIF
+ * networks also with one kernel per step whose extra blocks deliver the
+ * previous step's queue) at the same delivery grids; the fused
  * loop (ring scheme: each update block delivers its own spikes, one launch
  * per step and model, in CUDA graphs); the persistent step kernel (one
  * cooperative launch for many steps, grid barriers between its phases) and,
@@ -354,7 +356,7 @@ NGB_API int ngb_simulate_profiled(ngb_sim* sim, int64_t steps, double* kernel_ms
  * environment variable NGB_AUTOTUNE_CACHE naming a file, results are looked up
  * and appended there per (GPU, network shape) key.  *deliver_grid_out (may be
  * NULL) receives the chosen grid.  The environment variable NGB_MODE
- * ("persistent", "persistent_pipelined", "fused" or "pipelined") selects that step loop at
+ * ("persistent", "persistent_pipelined", "fused", "pipelined" or "pipelined_one_kernel") selects that step loop at
  * finalisation without tuning. */
 NGB_API int ngb_autotune(ngb_sim* sim, int64_t trial_steps, int32_t* deliver_grid_out);
 

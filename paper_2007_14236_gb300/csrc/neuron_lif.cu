@@ -32,15 +32,21 @@ namespace ngb {
 // times over): a block covers 256 * kNpt consecutive neurons of one segment,
 // and each thread issues the loads of all its neurons before the first use,
 // so that enough bytes are in flight to cover the memory latency.
-template <bool kFixed, int kMode, int kNpt>
-__global__ void __launch_bounds__(kLifBlock, kNpt > 1 ? (kMode == kEmitPipe ? 2 : 3) : (kMode == kEmitRing ? 8 : (kMode == kEmitPipe ? 5 : 6)))
-    k_update_lif(const __grid_constant__ SegTable<LifSeg> T, const uint32_t* __restrict__ thr,
-                 float* __restrict__ y_, float* __restrict__ I_, int32_t* __restrict__ ref_, Ring ring, int64_t* clk,
-                 int64_t step_off, const Csr csr, SpikeBuf sb, int scan) {
+// The body of one update block: block `blk` of a grid of `nblk` update
+// blocks (the LIF update kernel's own block, or a block of the pipelined step
+// kernel that also delivers).  kEarlyState: the neuron state is loaded before
+// griddep_wait (the previous kernel in the stream does not write it); else
+// after it.
+template <bool kFixed, int kMode, int kNpt, bool kEarlyState = true>
+__device__ __forceinline__ void lif_update_block(const SegTable<LifSeg>& T, const uint32_t* __restrict__ thr,
+                                                 float* __restrict__ y_, float* __restrict__ I_,
+                                                 int32_t* __restrict__ ref_, const Ring& ring, int64_t* clk,
+                                                 int64_t step_off, const Csr& csr, const SpikeBuf& sb, int scan,
+                                                 int64_t blk, int64_t nblk) {
   constexpr bool kAge = kMode == kEmitAge;
   __shared__ uint32_t s_thr[kMaxThr];
-  const LifSeg sg = segment_of(T, (int64_t)blockIdx.x);
-  const int64_t k0 = ((int64_t)blockIdx.x - sg.blk_begin) * (kLifBlock * kNpt) + threadIdx.x;
+  const LifSeg sg = segment_of(T, blk);
+  const int64_t k0 = (blk - sg.blk_begin) * (kLifBlock * kNpt) + threadIdx.x;
   // Prologue, overlapping the previous kernel (programmatic dependent launch):
   // state written two launches ago, static source metadata, Poisson table.
   float y[kNpt], I[kNpt];
@@ -57,9 +63,11 @@ __global__ void __launch_bounds__(kLifBlock, kNpt > 1 ? (kMode == kEmitPipe ? 2 
     meta[j] = make_uint4(0, 0, 0, 0);
     ag[j] = make_uint2(0, 0);
     if (k < sg.n) {
-      y[j] = y_[gid];
-      I[j] = I_[gid];
-      ref[j] = ref_[gid];
+      if (kEarlyState) {
+        y[j] = y_[gid];
+        I[j] = I_[gid];
+        ref[j] = ref_[gid];
+      }
       if (!kAge) meta[j] = __ldg(csr.src_meta + gid);
       if (kMode == kEmitPipe) ag[j] = __ldg(csr.src_age + gid);
     }
@@ -69,11 +77,21 @@ __global__ void __launch_bounds__(kLifBlock, kNpt > 1 ? (kMode == kEmitPipe ? 2 
   // the previous step's delivery has completed: ring slot t and the counters are final
   griddep_wait();
   griddep_launch();
+  if (!kEarlyState) {
+#pragma unroll
+    for (int j = 0; j < kNpt; ++j) {
+      const int64_t k = k0 + j * kLifBlock;
+      if (k < sg.n) {
+        const uint32_t gid = (uint32_t)(sg.offset + k);
+        y[j] = y_[gid];
+        I[j] = I_[gid];
+        ref[j] = ref_[gid];
+      }
+    }
+  }
   const int64_t t = clk[0] + step_off;
-  if (kMode != kEmitPipe && blockIdx.x == 0 && threadIdx.x == 0) clk[1] = t;
-  if (kAge && scan)
-    scan_pending<false>(t, csr, sb, ((int64_t)blockIdx.x * kLifBlock + threadIdx.x) >> 5,
-                        ((int64_t)gridDim.x * kLifBlock) >> 5);
+  if (kMode != kEmitPipe && blk == 0 && threadIdx.x == 0) clk[1] = t;
+  if (kAge && scan) scan_pending<false>(t, csr, sb, (blk * kLifBlock + threadIdx.x) >> 5, (nblk * kLifBlock) >> 5);
   const uint64_t slot_base = (uint64_t)(t & ring.L_mask) * (uint64_t)ring.R * (uint64_t)ring.N;
   float in[kNpt];
 #pragma unroll
@@ -102,6 +120,67 @@ __global__ void __launch_bounds__(kLifBlock, kNpt > 1 ? (kMode == kEmitPipe ? 2 
     else if (kMode == kEmitPipe) emit_spikes_pipe<kFixed>(spk, gid, 1u, t, meta[j], ag[j], csr, ring, sb);
     else emit_spikes(spk, gid, 1u, t, meta[j], sb);
   }
+}
+
+template <bool kFixed, int kMode, int kNpt>
+__global__ void __launch_bounds__(kLifBlock, kNpt > 1 ? (kMode == kEmitPipe ? 2 : 3) : (kMode == kEmitRing ? 8 : (kMode == kEmitPipe ? 5 : 6)))
+    k_update_lif(const __grid_constant__ SegTable<LifSeg> T, const uint32_t* __restrict__ thr,
+                 float* __restrict__ y_, float* __restrict__ I_, int32_t* __restrict__ ref_, Ring ring, int64_t* clk,
+                 int64_t step_off, const Csr csr, SpikeBuf sb, int scan) {
+  lif_update_block<kFixed, kMode, kNpt>(T, thr, y_, I_, ref_, ring, clk, step_off, csr, sb, scan,
+                                        (int64_t)blockIdx.x, (int64_t)gridDim.x);
+}
+
+// Pipelined step kernel (ring scheme, LIF networks, one launch per step):
+// blocks [0, n_upd) update step t = clk[0] + step_off (delivering each new
+// spike's delay-1 group and queueing its other groups for step t mod 3), the
+// other blocks deliver the queue of step t - 1 (slots t + 1 and later, so
+// nothing the update reads), when deliver_prev is set.  The queue of step
+// t + 1 mod 3, last read by the previous launch, is emptied here.  Launched
+// one per step in a single stream with programmatic dependent launch.
+template <bool kFixed, typename WT>
+__global__ void __launch_bounds__(kLifBlock, 5)
+    k_step_pipe(const __grid_constant__ SegTable<LifSeg> T, const uint32_t* __restrict__ thr, float* __restrict__ y_,
+                float* __restrict__ I_, int32_t* __restrict__ ref_, Ring ring, int64_t* clk, int64_t step_off,
+                const Csr csr, SpikeBuf sb, int64_t n_upd, int deliver_prev) {
+  if ((int64_t)blockIdx.x < n_upd) {
+    // the previous launch (the previous step) writes the state: loaded after the wait
+    lif_update_block<kFixed, kEmitPipe, 1, false>(T, thr, y_, I_, ref_, ring, clk, step_off, csr, sb, 0,
+                                                  (int64_t)blockIdx.x, n_upd);
+    return;
+  }
+  griddep_wait();  // the previous step's kernel (and its queue) has completed
+  griddep_launch();
+  const int64_t t = clk[0] + step_off;
+  if ((int64_t)blockIdx.x == n_upd && threadIdx.x == 0) sb.ctr3[(int)((t + 1) % 3)] = 0;
+  if (!deliver_prev) return;
+  const uint32_t warp = (uint32_t)((((int64_t)blockIdx.x - n_upd) * kLifBlock + threadIdx.x) >> 5);
+  const uint32_t nwarps = (uint32_t)((((int64_t)gridDim.x - n_upd) * kLifBlock) >> 5);
+  const int lane = threadIdx.x & 31;
+  const int q = (int)((t - 1) % 3);
+  const uint32_t n = (uint32_t)(sb.ctr3[q] & kChunkMask);
+  const uint4* __restrict__ wq = sb.wi3[q];
+  for (uint32_t ch = warp; ch < n; ch += nwarps)
+    deliver_work_item<WT, kFixed>(wq[2 * (uint64_t)ch], wq[2 * (uint64_t)ch + 1], t - 1, csr, ring, lane);
+}
+
+cudaError_t launch_step_pipe(const SegTable<LifSeg>& segs, int64_t upd_blocks, int del_blocks, const uint32_t* thr,
+                             float* y, float* I, int32_t* ref, Ring ring, bool fixed, int wdtype, int64_t* clk,
+                             int64_t step_off, const Csr& csr, SpikeBuf sb, bool deliver_prev, bool pdl,
+                             cudaStream_t st) {
+  const dim3 g((unsigned)(upd_blocks + del_blocks)), b(kLifBlock);
+  const int dp = deliver_prev ? 1 : 0;
+#define NGB_SP(F, W) \
+  return launch_k(k_step_pipe<F, W>, g, b, pdl, st, segs, thr, y, I, ref, ring, clk, step_off, csr, sb, upd_blocks, dp)
+  if (fixed) {
+    if (wdtype == 0) NGB_SP(true, float);
+    if (wdtype == 1) NGB_SP(true, __nv_bfloat16);
+    NGB_SP(true, __half);
+  }
+  if (wdtype == 0) NGB_SP(false, float);
+  if (wdtype == 1) NGB_SP(false, __nv_bfloat16);
+  NGB_SP(false, __half);
+#undef NGB_SP
 }
 
 // Large networks (kNpt = 2 or 4 neurons per thread, ring or spike-buffer

@@ -248,7 +248,9 @@ struct ngb_sim {
   bool pdl = true;  // programmatic dependent launch between the step's kernels
   int mode = 0;  // 0: per-step kernels in CUDA graphs, 1: persistent step kernel, 2: fused update + delivery,
                  // 3: pipelined (delivery of step t beside the update of step t + 1, two streams),
-                 // 4: pipelined persistent step kernel (ring scheme, one grid barrier per step)
+                 // 4: pipelined persistent step kernel (ring scheme, one grid barrier per step),
+                 // 5: pipelined, one kernel per step (LIF networks: update and delivery of the
+                 //    previous step's queue in the same launch, chained by programmatic dependent launch)
   cudaStream_t stream2 = nullptr;  // second stream of the pipelined loop's graphs
   bool persist_ok = false;
   int persist_grid = 0;
@@ -310,7 +312,15 @@ Csr csr_of(const ngb_sim* s) {
 }
 
 // How the update kernels hand the step's spikes to delivery.
-int emit_of(const ngb_sim* s) { return s->scheme == 2 ? kEmitAge : (s->mode == 3 ? kEmitPipe : kEmitRing); }
+int emit_of(const ngb_sim* s) {
+  return s->scheme == 2 ? kEmitAge : ((s->mode == 3 || s->mode == 5) ? kEmitPipe : kEmitRing);
+}
+
+// The one-kernel pipelined loop takes LIF networks at one neuron per thread
+// with the ring scheme.
+bool pipe1_ok(const ngb_sim* s) {
+  return s->scheme == 1 && s->n_aeif == 0 && s->n_lif > 0 && s->lif_npt == 1 && s->sb.wi3[0] != nullptr;
+}
 
 // The fused step loop takes one LIF neuron per thread and the two-receptor
 // AdEx models.
@@ -428,7 +438,7 @@ cudaError_t launch_step(ngb_sim* s) {
     if (e != cudaSuccess) return e;
     return launch_tick_add(s->clk, 1, s->sb.ctr, s->sb.ctr3, s->pdl, s->stream);
   }
-  if (s->mode == 3) {  // one pipelined step, serialised on the main stream
+  if (s->mode == 3 || s->mode == 5) {  // one pipelined step, serialised on the main stream
     e = launch_updates(s, 0);
     if (e == cudaSuccess) e = launch_del(s, 0);
     if (e != cudaSuccess) return e;
@@ -517,6 +527,18 @@ int capture_graph(ngb_sim* s) {
   if (s->mode == 2) {
     for (int i = 0; i < s->graph_steps && e == cudaSuccess; ++i) e = launch_fused(s, i);
     if (e == cudaSuccess) e = launch_tick_add(s->clk, s->graph_steps, s->sb.ctr, s->sb.ctr3, s->pdl, s->stream);
+  } else if (s->mode == 5) {
+    // One kernel per step: the update of step i and the delivery of step
+    // i - 1's queue; then the last step's queue and the clock.
+    const int S = s->graph_steps;
+    const bool det = s->cfg.deterministic != 0;
+    for (int i = 0; i < S && e == cudaSuccess; ++i)
+      e = launch_step_pipe(s->lif_tab, s->lif_blocks, s->deliver_grid, s->thr, s->st0, s->st1, s->ref, ring_of(s), det,
+                           s->cfg.weight_dtype, s->clk, i, csr_of(s), s->sb, i > 0, s->pdl, s->stream);
+    if (e == cudaSuccess)
+      e = launch_deliver(s->sb, csr_of(s), s->cfg.weight_dtype, ring_of(s), det, kEmitPipe, s->clk, S - 1,
+                         s->deliver_grid, s->pdl, s->stream);
+    if (e == cudaSuccess) e = launch_tick_add(s->clk, S, s->sb.ctr, s->sb.ctr3, s->pdl, s->stream);
   } else if (s->mode == 3) {
     // Pipelined: the updates of the steps on the main stream, their
     // deliveries on the second; the update of step i waits for the delivery
@@ -1083,6 +1105,7 @@ int rebuild_tables(ngb_sim* s) {
   if (s->mode == 2 && (!fused_ok(s) || s->scheme != 1)) s->mode = 0;
   // the pipelined loop delivers with the ring scheme
   if (s->mode == 3 && (s->scheme != 1 || !s->stream2)) s->mode = 0;
+  if (s->mode == 5 && !pipe1_ok(s)) s->mode = 0;
   s->tables_dirty = false;
   return capture_graph(s);
 }
@@ -1366,6 +1389,7 @@ int finalize_impl(ngb_sim* s) {
   if (env_mode && std::string(env_mode) == "persistent_pipelined" && s->scheme == 1) s->mode = 4;
   if (env_mode && std::string(env_mode) == "fused" && s->scheme == 1) s->mode = 2;
   if (env_mode && std::string(env_mode) == "pipelined" && s->scheme == 1 && s->stream2) s->mode = 3;
+  if (env_mode && std::string(env_mode) == "pipelined_one_kernel" && s->scheme == 1) s->mode = 5;
   s->graph_steps = s->cfg.steps_per_graph == 0 ? 100 : std::max(0, s->cfg.steps_per_graph);
   return rebuild_tables(s);
 }
@@ -1439,7 +1463,7 @@ int simulate_impl(ngb_sim* s, int64_t steps, bool profiled, double* kernel_ms, i
       if (!fused) CK(launch_post(s));
       CK(fused ? launch_tick_add(s->clk, 1, s->sb.ctr, s->sb.ctr3, s->pdl, s->stream) : launch_del(s, 0));
       CK(cudaEventRecord(e[3], s->stream));
-      if (s->mode == 3) CK(launch_tick_add(s->clk, 1, s->sb.ctr, s->sb.ctr3, false, s->stream));
+      if (s->mode == 3 || s->mode == 5) CK(launch_tick_add(s->clk, 1, s->sb.ctr, s->sb.ctr3, false, s->stream));
     }
     CK(cudaStreamSynchronize(s->stream));
     for (int64_t i = 0; i < chunk; ++i) {
@@ -1760,6 +1784,7 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
     int m = 0, g = 0, pg = 0, sc = 0;
     while (in >> k >> m >> g >> pg >> sc) {
       if (k == key && g > 0 && (m == 0 || (m == 2 && sc == 1 && fused_ok(s)) || (m == 3 && sc == 1 && s->stream2) ||
+                                (m == 5 && sc == 1 && pipe1_ok(s)) ||
                                 (m == 1 && s->persist_ok && pg > 0) ||
                                 (m == 4 && s->persist_ok && pg > 0 && sc == 1 && s->sb.wi3[0])) &&
           (sc == s->scheme || both)) {
@@ -1815,10 +1840,14 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
         best_scheme = scheme;
       }
     }
-    // pipelined loop (ring scheme): delivery blocks per SM
-    if (rc == NGB_OK && scheme == 1 && s->stream2) {
+    // pipelined loops (ring scheme): two-stream graphs, and one kernel per
+    // step for LIF networks; delivery blocks per SM
+    for (int pm : {3, 5}) {
+      if (rc != NGB_OK || scheme != 1 || !s->stream2) break;
+      s->mode = pm;
+      if (pm == 5 && !pipe1_ok(s)) break;
       for (int b : {1, 2, 4, 8}) {
-        s->mode = 3;
+        s->mode = pm;
         s->deliver_grid = b * sms;
         rc = capture_graph(s);
         if (rc == NGB_OK) rc = snapshot_restore(s, sn);
@@ -1834,7 +1863,7 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
         const double per_step = ms / (double)(reps * s->graph_steps);
         if (per_step < best_ms) {
           best_ms = per_step;
-          best_mode = 3;
+          best_mode = pm;
           best_grid = s->deliver_grid;
           best_scheme = scheme;
         }

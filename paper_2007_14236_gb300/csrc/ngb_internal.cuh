@@ -597,6 +597,13 @@ cudaError_t launch_step_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, cons
                              float* gex, float* gin, float* h, float* xe, float* xi, bool alpha, Ring ring, bool fixed,
                              int wdtype, const int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, bool pdl,
                              cudaStream_t st);
+// Pipelined step kernel for LIF-only networks (ring scheme): upd_blocks update
+// blocks (one LIF neuron per thread) and del_blocks blocks delivering the queue
+// of the previous step when deliver_prev.
+cudaError_t launch_step_pipe(const SegTable<LifSeg>& segs, int64_t upd_blocks, int del_blocks, const uint32_t* thr,
+                             float* y, float* I, int32_t* ref, Ring ring, bool fixed, int wdtype, int64_t* clk,
+                             int64_t step_off, const Csr& csr, SpikeBuf sb, bool deliver_prev, bool pdl,
+                             cudaStream_t st);
 // clk[0] += n (clk[1] = clk[0] - 1); the ring scheme's step counters (both
 // the per-step and the pipelined ones) are cleared.
 cudaError_t launch_tick_add(int64_t* clk, int64_t n, unsigned long long* ctr, unsigned long long* ctr3, bool pdl,

@@ -157,7 +157,7 @@ def test_autotune_does_not_advance_the_simulation(ngb):
     b.simulate(200)
     grid = b.autotune(300)
     st = b.stats()
-    assert grid > 0 and st["steps"] == 200 and st["mode"] in (0, 1, 2, 3, 4)
+    assert grid > 0 and st["steps"] == 200 and st["mode"] in (0, 1, 2, 3, 4, 5)
     a.simulate(500)
     b.simulate(500)
     assert np.array_equal(a.spikes()[0], b.spikes()[0]) and np.array_equal(a.spikes()[1], b.spikes()[1])
@@ -312,6 +312,33 @@ def test_pipelined_equals_per_step_kernels(ngb, name):
     b.simulate(250)  # 100-step graphs and eager steps, in chunks of 250
     b.simulate_profiled(50)
     b.simulate(400)
+    ai, at = a.spikes()
+    bi, bt = b.spikes()
+    assert len(ai) > 50
+    assert np.array_equal(at, bt) and np.array_equal(ai, bi)
+    assert np.array_equal(a.state("V_m"), b.state("V_m"))
+    assert a.stats()["events"] == b.stats()["events"]
+    for off in range(0, 4):
+        assert np.array_equal(a.input(0, off), b.input(0, off))
+
+
+@pytest.mark.parametrize("name", ["balanced_lif", "microcircuit", "batched", "mc_bf16", "adex"])
+def test_pipelined_one_kernel_equals_per_step_kernels(ngb, name):
+    """The one-kernel pipelined loop (update of step t and delivery of step
+    t - 1's queue in one launch, chained by programmatic dependent launch):
+    bit-identical to the per-step kernels through graphs, eager and profiled
+    steps; networks with AdEx populations use the per-step kernels."""
+    spec = _LOOP_SPECS[name]()
+    a = ngb.from_spec(spec, deterministic=True, delivery="ring")
+    with _env(NGB_MODE="pipelined_one_kernel"):
+        b = ngb.from_spec(spec, deterministic=True, delivery="ring", drain_steps=250)
+        b.finalize()
+    assert b.stats()["mode"] == (0 if name == "adex" else 5)
+    a.simulate(700)
+    b.simulate(250)
+    b.simulate_profiled(50)
+    b.simulate(7)
+    b.simulate(393)
     ai, at = a.spikes()
     bi, bt = b.spikes()
     assert len(ai) > 50
