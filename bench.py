@@ -44,7 +44,9 @@ LOOPS = {0: "graph", 1: "persistent", 2: "fused", 3: "pipelined", 4: "persistent
 NCU_TRAFFIC = {("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "graph", "k_update_lif"): 2483840,
                ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "graph", "k_deliver"): 3033728,
                ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "pipelined", "k_update_lif"): 3171200,
-               ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "pipelined", "k_deliver"): 3112960}
+               ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "pipelined", "k_deliver"): 3112960,
+               ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "pipelined_one_kernel", "k_step_pipe"):
+                   6284672}
 SIM_STEPS_PER_BENCH_STEP = 10_000  # 1 s of biological time at dt = 0.1 ms
 
 
@@ -826,6 +828,15 @@ def main():
                                 "algorithmic_bytes_per_launch": bytes_launch, "steps_per_launch": a.sim_steps,
                                 "grid": st0["launch_grid"]}
         dom = "k_persistent"
+    elif mode == "pipelined_one_kernel":
+        # one launch per simulation step, back to back in the stream (chained by programmatic dependent
+        # launch): its average duration from the timed region's events
+        ev_step = events / max(1, ws) / (a.steps * a.sim_steps)
+        n_launch = a.steps * a.sim_steps
+        kern["k_step_pipe"] = {"launches": n_launch, "ms_total": ms, "us_per_launch": ms * 1e3 / n_launch,
+                               "algorithmic_bytes_per_launch": lif_bytes + ev_step * (4 + wbytes + 4),
+                               "grid": st0["launch_grid"]}
+        dom = "k_step_pipe"
     else:
         dom = max(kern, key=lambda k: kern[k]["ms_total"])
     ach = kern[dom]["algorithmic_bytes_per_launch"] / (kern[dom]["us_per_launch"] * 1e-6) / 1e9
