@@ -35,6 +35,7 @@ import numpy as np
 import pytest
 
 import oracle
+from conftest import paper_values
 from paper_2007_14236_gb300 import workloads as W
 
 DT = 0.1
@@ -71,10 +72,12 @@ def test_cash_karp_order_conditions():
 
 
 def _table2(**kw):
-    # AdEx table of the paper (Sec. 2.4): V_r = -60 mV; no synaptic input
-    base = dict(C_m=281.0, g_L=30.0, E_L=-70.6, V_T=-50.4, Delta_T=2.0, tau_w=144.0, a=4.0, b=80.5,
-                V_reset=-60.0, E_ex=0.0, E_in=-85.0, tau_ex=1.0, tau_in=1.0, V_peak=0.0,
-                V_init_mean=-70.6, w_init=0.0, rk_tol=1e-10, rk_h_min=1e-9, rk_max_substeps=100000)
+    # AdEx table of the paper (Sec. 2.4; golden fixture); no synaptic input
+    t = paper_values()["adex_table"]
+    base = dict(C_m=t["C_m_pF"], g_L=t["g_L_nS"], E_L=t["E_L_mV"], V_T=t["V_T_mV"], Delta_T=t["Delta_T_mV"],
+                tau_w=t["tau_w_ms"], a=t["a_nS"], b=t["b_pA"], V_reset=t["V_reset_mV"], E_ex=t["E_ex_mV"],
+                E_in=t["E_in_mV"], tau_ex=t["tau_syn_ms"], tau_in=t["tau_syn_ms"], V_peak=0.0,
+                V_init_mean=t["E_L_mV"], w_init=0.0, rk_tol=1e-10, rk_h_min=1e-9, rk_max_substeps=100000)
     base.update(kw)
     return W.AeifParams(**base)
 
@@ -161,7 +164,7 @@ def _away_from_spikes(steps, spikes, before=20, after=2):
 
 
 def test_adex_700pA_matches_dop853():
-    par = _table2(I_e=700.0)
+    par = _table2(I_e=paper_values()["single_neuron_experiments"]["injected_current_pA"])
     steps = 1500
     V_o, sp_o = _oracle_trace(par, steps, fp64=True)
     V_s, sp_s = _scipy_trace(par, steps)

@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
+from conftest import paper_values
 from paper_2007_14236_gb300 import workloads as W
 
 stats = pytest.importorskip("scipy.stats")
@@ -179,9 +180,32 @@ def test_uniform_delay_histogram():
 def test_microcircuit_synapse_total_matches_formula_and_paper():
     K = sum(c.K for c in W.microcircuit(scale=1.0).conns)
     assert K == 298_880_968
-    # the paper gives ~77,000 neurons and ~3e8 connections
-    assert abs(sum(W.MC_SIZES) - 77_000) < 500
-    assert abs(K - 3e8) / 3e8 < 0.01
+    # the paper's approximate neuron and connection counts (golden fixture)
+    mc = paper_values()["microcircuit"]
+    assert abs(sum(W.MC_SIZES) - mc["neurons_about"]) < 500
+    assert abs(K - mc["connections_about"]) / mc["connections_about"] < 0.01
+
+
+def test_paper_balanced_workload_follows_the_paper_table():
+    """The workload recipe of the balanced network against the paper's
+    parameter table (golden fixture): population and in-degree ratios,
+    weights, delay distribution and Poisson drive."""
+    tab = paper_values()["balanced_network_table"]
+    adex = paper_values()["adex_table"]
+    spec = W.paper_balanced(n_ex=8000, ce=800, seed=1)
+    ex, inh = spec.pops
+    assert inh.n / ex.n == tab["N_in_over_N_ex"]
+    ee, ie = spec.conns[0], spec.conns[1]
+    assert ie.K / ee.K == tab["CI_over_CE"]
+    assert ee.weight.p0 == tab["W_ex_nS"] and ie.weight.p0 == tab["W_in_nS"] and ie.receptor == 1
+    assert ee.delay.kind == "normal" and (ee.delay.p0, ee.delay.p1) == (tab["delay_mean_ms"], tab["delay_sd_ms"])
+    for p in spec.pops:
+        q = p.params
+        assert (q.poisson.weight, q.poisson.n_inputs * q.poisson.rate_hz) == (tab["W_poisson_nS"], tab["rate_poisson_hz"])
+        assert (q.C_m, q.g_L, q.E_L, q.V_T, q.Delta_T, q.tau_w, q.a, q.b, q.V_reset, q.E_ex, q.E_in) == (
+            adex["C_m_pF"], adex["g_L_nS"], adex["E_L_mV"], adex["V_T_mV"], adex["Delta_T_mV"], adex["tau_w_ms"],
+            adex["a_nS"], adex["b_pA"], adex["V_reset_mV"], adex["E_ex_mV"], adex["E_in_mV"])
+        assert q.tau_ex == q.tau_in == adex["tau_syn_ms"]
 
 
 def _run_with_inputs(spec, steps, **kw):
@@ -283,4 +307,5 @@ def test_paper_balanced_network_rate_matches_paper():
     net.simulate(2500)
     ids, st = net.spikes()
     rate = np.count_nonzero(st >= 1000) / 10000 / 0.15
-    assert abs(rate - 30.7) <= 3.07, rate
+    paper = paper_values()["balanced_network_table"]["mean_firing_rate_hz"]
+    assert abs(rate - paper) <= 0.1 * paper, rate
