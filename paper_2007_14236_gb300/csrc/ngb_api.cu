@@ -2026,20 +2026,36 @@ int ngb_get_spikes(ngb_sim* s, int32_t pop, int64_t t0_step, int64_t t1_step, in
     // every drain appends spikes of later steps than all earlier drains, so
     // sorting the new tail keeps the whole record sorted by (step, id)
     const size_t a = s->rec_sorted_upto, n = s->rec_ids.size() - a;
-    std::vector<size_t> idx(n);
-    for (size_t i = 0; i < n; ++i) idx[i] = a + i;
-    std::sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
-      if (s->rec_steps[x] != s->rec_steps[y]) return s->rec_steps[x] < s->rec_steps[y];
-      return s->rec_ids[x] < s->rec_ids[y];
-    });
-    std::vector<uint32_t> ni(n);
-    std::vector<int64_t> ns(n);
-    for (size_t i = 0; i < n; ++i) {
-      ni[i] = s->rec_ids[idx[i]];
-      ns[i] = s->rec_steps[idx[i]];
+    int64_t smin = s->rec_steps[a], smax = smin;
+    for (size_t i = a; i < a + n; ++i) {
+      smin = std::min(smin, s->rec_steps[i]);
+      smax = std::max(smax, s->rec_steps[i]);
     }
-    std::copy(ni.begin(), ni.end(), s->rec_ids.begin() + a);
-    std::copy(ns.begin(), ns.end(), s->rec_steps.begin() + a);
+    const uint64_t span = (uint64_t)(smax - smin) + 1;
+    if (span <= 4 * (uint64_t)n + 4096) {
+      // counting sort by step (the tail covers the steps of the last drains),
+      // then the ids of each step in place
+      std::vector<size_t> start(span + 1, 0);
+      for (size_t i = a; i < a + n; ++i) start[(size_t)(s->rec_steps[i] - smin) + 1] += 1;
+      for (size_t k = 1; k <= span; ++k) start[k] += start[k - 1];
+      std::vector<uint32_t> ni(n);
+      std::vector<size_t> cur(start.begin(), start.end() - 1);
+      for (size_t i = a; i < a + n; ++i) ni[cur[(size_t)(s->rec_steps[i] - smin)]++] = s->rec_ids[i];
+      for (size_t k = 0; k < span; ++k) {
+        std::sort(ni.begin() + (ptrdiff_t)start[k], ni.begin() + (ptrdiff_t)start[k + 1]);
+        std::fill(s->rec_steps.begin() + (ptrdiff_t)(a + start[k]), s->rec_steps.begin() + (ptrdiff_t)(a + start[k + 1]),
+                  smin + (int64_t)k);
+      }
+      std::copy(ni.begin(), ni.end(), s->rec_ids.begin() + (ptrdiff_t)a);
+    } else {
+      std::vector<std::pair<int64_t, uint32_t>> kv(n);
+      for (size_t i = 0; i < n; ++i) kv[i] = {s->rec_steps[a + i], s->rec_ids[a + i]};
+      std::sort(kv.begin(), kv.end());
+      for (size_t i = 0; i < n; ++i) {
+        s->rec_steps[a + i] = kv[i].first;
+        s->rec_ids[a + i] = kv[i].second;
+      }
+    }
     s->rec_sorted_upto = s->rec_ids.size();
   }
   const int64_t lo = pop >= 0 ? s->pops[pop].offset : 0;
