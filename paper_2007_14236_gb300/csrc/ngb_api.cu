@@ -940,6 +940,7 @@ int rebuild_tables(ngb_sim* s) {
       g.w_ext = (float)q.poisson.weight;
       const double tol_eff = std::max(q.rk_tol, 8.0 * 5.9604644775390625e-08);  // FP32 floor 8 * 2^-24
       g.inv_tol = 1.0 / tol_eff;
+      g.inv_tol_f = (float)g.inv_tol;
       g.h_min = q.rk_h_min_ms;
       g.dt = dt;
       g.max_sub = q.rk_max_substeps;

@@ -110,6 +110,7 @@ struct AeifSeg {
   // beta ports (unused ports: E 0, 1/tau 1, jump 0): reversal potential, 1 / decay
   // time, 1 / rise time, jump of x per unit weight (the peak of g equals the weight)
   float E_p[4], itd_p[4], itr_p[4], jmp_p[4];
+  float inv_tol_f;     // 1 / tolerance rounded to FP32 (the FP32 side of the error-ratio test)
   double inv_tol, h_min, dt;
   int64_t max_sub;
 };
