@@ -10,6 +10,9 @@ launch configuration bench.py times (100-step CUDA graphs, FP32 weights).
 * Whole-network counts: per-pathway synapse totals are exact.
 * The same delivery property for the spike-buffer scheme, whose only input
   slot is the next step's.
+* The same property in the step loop the benchmark times: the handle built and
+  autotuned as bench.py does (the one-kernel pipelined loop on this network),
+  checked on every pending slot after graph replays.
 """
 import numpy as np
 import pytest
@@ -132,3 +135,22 @@ def test_fullsize_pending_inputs_equal_delivered_weights(mc):
     for off in range(0, D + 1):
         got = sim.input(0, off).astype(np.float64)
         assert np.all(np.abs(got - expect[off]) <= 1e-5 * absw[off] + 1e-4), off
+
+
+def test_fullsize_autotuned_loop_pending_inputs_equal_delivered_weights():
+    from paper_2007_14236_gb300 import ngb
+    spec = W.microcircuit(scale=1.0, seed=1)
+    sim = ngb.from_spec(spec, steps_per_graph=100, drain_steps=10_000, record_capacity=4_000_000)
+    sim.finalize()
+    sim.autotune(1000)
+    st = sim.stats()
+    assert st["steps"] == 0 and st["mode"] in (0, 1, 2, 3, 4, 5)
+    sim.simulate(1200)
+    st = sim.stats()
+    D = st["max_delay_steps"]
+    L = 1 if st["delivery"] == 2 else D + 1
+    expect, absw = _expected_inputs(sim, L)
+    for off in range(L):
+        got = sim.input(0, off).astype(np.float64)
+        assert np.all(np.abs(got - expect[off]) <= 1e-5 * absw[off] + 1e-4), (off, st["mode"])
+    sim.close()
