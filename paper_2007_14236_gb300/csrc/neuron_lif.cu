@@ -36,13 +36,16 @@ namespace ngb {
 // blocks (the LIF update kernel's own block, or a block of the pipelined step
 // kernel that also delivers).  kEarlyState: the neuron state is loaded before
 // griddep_wait (the previous kernel in the stream does not write it); else
-// after it.
+// after it.  early_clk: the previous kernel does not write the step counter
+// either, so the step and the Poisson counts (which depend on nothing else)
+// are computed before griddep_wait, and the state and the ring slot are then
+// loaded together.
 template <bool kFixed, int kMode, int kNpt, bool kEarlyState = true>
 __device__ __forceinline__ void lif_update_block(const SegTable<LifSeg>& T, const uint32_t* __restrict__ thr,
                                                  float* __restrict__ y_, float* __restrict__ I_,
                                                  int32_t* __restrict__ ref_, const Ring& ring, int64_t* clk,
                                                  int64_t step_off, const Csr& csr, const SpikeBuf& sb, int scan,
-                                                 int64_t blk, int64_t nblk) {
+                                                 int64_t blk, int64_t nblk, bool early_clk = false) {
   constexpr bool kAge = kMode == kEmitAge;
   __shared__ uint32_t s_thr[kMaxThr];
   const LifSeg sg = segment_of(T, blk);
@@ -74,9 +77,25 @@ __device__ __forceinline__ void lif_update_block(const SegTable<LifSeg>& T, cons
   }
   for (uint32_t i = threadIdx.x; i < sg.n_thr; i += kLifBlock) s_thr[i] = __ldg(thr + sg.thr_off + i);
   __syncthreads();
+  int64_t t = 0;
+  uint32_t kp[kNpt];
+  auto draw_counts = [&]() {
+#pragma unroll
+    for (int j = 0; j < kNpt; ++j) {
+      const int64_t k = k0 + j * kLifBlock;
+      kp[j] = (k < sg.n && sg.n_thr > 0)
+                  ? poisson_count(sg.seed, t - sg.t0, sg.local_off + (uint32_t)k, s_thr, sg.n_thr)
+                  : 0u;
+    }
+  };
+  if (early_clk) {
+    t = clk[0] + step_off;
+    draw_counts();
+  }
   // the previous step's delivery has completed: ring slot t and the counters are final
   griddep_wait();
   griddep_launch();
+  if (!early_clk) t = clk[0] + step_off;
   if (!kEarlyState) {
 #pragma unroll
     for (int j = 0; j < kNpt; ++j) {
@@ -89,7 +108,6 @@ __device__ __forceinline__ void lif_update_block(const SegTable<LifSeg>& T, cons
       }
     }
   }
-  const int64_t t = clk[0] + step_off;
   if (kMode != kEmitPipe && blk == 0 && threadIdx.x == 0) clk[1] = t;
   if (kAge && scan) scan_pending<false>(t, csr, sb, (blk * kLifBlock + threadIdx.x) >> 5, (nblk * kLifBlock) >> 5);
   const uint64_t slot_base = (uint64_t)(t & ring.L_mask) * (uint64_t)ring.R * (uint64_t)ring.N;
@@ -99,6 +117,7 @@ __device__ __forceinline__ void lif_update_block(const SegTable<LifSeg>& T, cons
     const int64_t k = k0 + j * kLifBlock;
     in[j] = k < sg.n ? ring_read<kFixed, false>(ring.p, slot_base + (uint32_t)(sg.offset + k)) : 0.0f;
   }
+  if (!early_clk) draw_counts();
 #pragma unroll
   for (int j = 0; j < kNpt; ++j) {
     const int64_t k = k0 + j * kLifBlock;
@@ -107,10 +126,7 @@ __device__ __forceinline__ void lif_update_block(const SegTable<LifSeg>& T, cons
     if (k < sg.n) {
       ring_clear<kFixed>(ring.p, slot_base + gid);
       float x = in[j];
-      if (sg.n_thr > 0) {
-        const uint32_t kp = poisson_count(sg.seed, t - sg.t0, sg.local_off + (uint32_t)k, s_thr, sg.n_thr);
-        x = __fadd_rn(x, __fmul_rn((float)kp, sg.w_ext));
-      }
+      if (sg.n_thr > 0) x = __fadd_rn(x, __fmul_rn((float)kp[j], sg.w_ext));
       spk = lif_step(sg, y[j], I[j], ref[j], x);
       y_[gid] = y[j];
       I_[gid] = I[j];
@@ -145,8 +161,10 @@ __global__ void __launch_bounds__(kLifBlock, 5)
                 const Csr csr, SpikeBuf sb, int64_t n_upd, int deliver_prev) {
   if ((int64_t)blockIdx.x < n_upd) {
     // the previous launch (the previous step) writes the state: loaded after the wait
+    // the step counter changes only between graphs (the previous launch of a
+    // graph's first step is the clock tick): known before the wait elsewhere
     lif_update_block<kFixed, kEmitPipe, 1, false>(T, thr, y_, I_, ref_, ring, clk, step_off, csr, sb, 0,
-                                                  (int64_t)blockIdx.x, n_upd);
+                                                  (int64_t)blockIdx.x, n_upd, step_off > 0);
     return;
   }
   griddep_wait();  // the previous step's kernel (and its queue) has completed
