@@ -37,7 +37,7 @@ METRIC = "real-time factor & synaptic events/s; batched/served vs plain at state
 UNIT = "synaptic events/s"
 DELIVERY = {1: "ring", 2: "spike_buffer"}
 LOOPS = {0: "graph", 1: "persistent", 2: "fused", 3: "pipelined", 4: "persistent_pipelined",
-         5: "pipelined_one_kernel"}
+         5: "pipelined_one_kernel", 6: "target_owned"}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches) from one ncu
 # capture of the full-size microcircuit with FP32 weights in this configuration (delivery scheme, step loop);
 # a kernel or configuration without a capture reports null
@@ -67,12 +67,13 @@ def _args():
     ap.add_argument("--delivery", choices=["auto", "ring", "spike_buffer"], default="auto",
                     help="spike delivery scheme (auto: chosen at finalisation, and by the autotuner at step 0)")
     ap.add_argument("--mode", choices=["auto", "graph", "persistent", "fused", "pipelined", "persistent_pipelined",
-                                       "pipelined_one_kernel"],
+                                       "pipelined_one_kernel", "target_owned"],
                     default="auto",
                     help="step loop: autotuned (default), per-step kernels in CUDA graphs, the persistent kernel, "
                          "the fused update + delivery kernels, the pipelined loop (delivery beside the next "
-                         "step's update, two-stream CUDA graphs), or the pipelined persistent kernel (one grid "
-                         "barrier per step)")
+                         "step's update, two-stream CUDA graphs), the pipelined persistent kernel (one grid "
+                         "barrier per step), the one-kernel pipelined loop, or the target-owned persistent "
+                         "kernel (rings in shared memory, spikes exchanged through mailboxes)")
     ap.add_argument("--paper-n", type=str, default="1000000",
                     help="neurons of the paper's balanced network (comma-separated for a sweep)")
     ap.add_argument("--paper-ce", type=int, default=800, help="excitatory in-degree of the paper's balanced network")
@@ -707,7 +708,7 @@ def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
-    if a.mode in ("persistent", "fused", "pipelined", "persistent_pipelined", "pipelined_one_kernel"):
+    if a.mode in ("persistent", "fused", "pipelined", "persistent_pipelined", "pipelined_one_kernel", "target_owned"):
         os.environ["NGB_MODE"] = a.mode  # read by the library when a network is finalised
     if a.workload != "microcircuit":
         return {"small": run_small, "batched": run_batched, "adex": run_adex, "paper": run_paper,
@@ -819,15 +820,15 @@ def main():
                           "events_per_launch": ev_per_launch},
         }
     peak, peak_kind = _peaks()
-    if mode in ("persistent", "persistent_pipelined"):
+    if mode in ("persistent", "persistent_pipelined", "target_owned"):
         # one launch per bench step (sim_steps steps); its duration from the timed region's events
         ev_step = events / max(1, ws) / a.steps
         bytes_launch = a.sim_steps * lif_bytes + ev_step * (4 + wbytes + 4)
         us_launch = ms / a.steps * 1e3
-        kern["k_persistent"] = {"launches": a.steps, "ms_total": ms, "us_per_launch": us_launch,
-                                "algorithmic_bytes_per_launch": bytes_launch, "steps_per_launch": a.sim_steps,
-                                "grid": st0["launch_grid"]}
-        dom = "k_persistent"
+        dom = "k_owned" if mode == "target_owned" else "k_persistent"
+        kern[dom] = {"launches": a.steps, "ms_total": ms, "us_per_launch": us_launch,
+                     "algorithmic_bytes_per_launch": bytes_launch, "steps_per_launch": a.sim_steps,
+                     "grid": st0["launch_grid"]}
     elif mode == "pipelined_one_kernel":
         # one launch per simulation step, back to back in the stream (chained by programmatic dependent
         # launch): its average duration from the timed region's events
@@ -861,7 +862,7 @@ def main():
         "real_time_factor": rtf,
         "build_s": build_s,
         "autotune_s": tune_s,
-        "gpu_launches": int(a.steps if mode in ("persistent", "persistent_pipelined") else
+        "gpu_launches": int(a.steps if mode in ("persistent", "persistent_pipelined", "target_owned") else
                             a.steps * (a.sim_steps + (a.sim_steps + 99) // 100) if mode == "fused" else
                             a.steps * (2 * a.sim_steps + (a.sim_steps + 99) // 100) if mode == "pipelined" else
                             a.steps * (a.sim_steps + 2 * ((a.sim_steps + 99) // 100)) if mode == "pipelined_one_kernel"

@@ -240,8 +240,11 @@ typedef struct {
   int64_t mode;         /* step loop: 0 per-step kernels in CUDA graphs, 1 persistent step kernel, 2 fused
                            update + delivery, 3 pipelined (delivery of step t beside the update of t + 1),
                            4 pipelined persistent step kernel (one grid barrier per step), 5 pipelined
-                           with one kernel per step (LIF networks) */
-  int64_t launch_grid;  /* blocks of the delivery kernel (modes 0, 3) or of the persistent kernel (modes 1, 4) */
+                           with one kernel per step (LIF networks), 6 target-owned persistent kernel
+                           (LIF networks: one block per SM owns every G-th neuron, with the ring of its
+                           neurons in shared memory; spikes exchanged through step-stamped mailboxes) */
+  int64_t launch_grid;  /* blocks of the delivery kernel (modes 0, 3, 5) or of the persistent kernel
+                           (modes 1, 4, 6) */
   int64_t delivery;     /* delivery scheme in use: 1 ring, 2 spike buffer */
 } ngb_stats;
 
@@ -348,7 +351,11 @@ NGB_API int ngb_simulate_profiled(ngb_sim* sim, int64_t steps, double* kernel_ms
  * cooperative launch for many steps, grid barriers between its phases) and,
  * with the ring scheme, its pipelined variant (one grid barrier per step: the
  * update phase delivers delay-1 groups and the queued groups of the previous
- * step) at 1 to 4 blocks per SM; at step 0 with delivery AUTO, under both delivery
+ * step) at 1 to 4 blocks per SM; for static LIF networks with the ring
+ * scheme whose per-block ring fits in shared memory, the target-owned
+ * persistent kernel (its tile-major synapse layout, about 1.5 - 2 times the
+ * CSR's bytes, is built on first use; deterministic mode gives bit-identical
+ * results to every other loop); at step 0 with delivery AUTO, under both delivery
  * schemes (ngb_stats.delivery).  Each candidate is
  * timed over trial_steps steps (0 = 500); the simulation state is saved
  * before and restored after the trials, so the simulation does not advance.
@@ -356,8 +363,9 @@ NGB_API int ngb_simulate_profiled(ngb_sim* sim, int64_t steps, double* kernel_ms
  * environment variable NGB_AUTOTUNE_CACHE naming a file, results are looked up
  * and appended there per (GPU, network shape) key.  *deliver_grid_out (may be
  * NULL) receives the chosen grid.  The environment variable NGB_MODE
- * ("persistent", "persistent_pipelined", "fused", "pipelined" or "pipelined_one_kernel") selects that step loop at
- * finalisation without tuning. */
+ * ("persistent", "persistent_pipelined", "fused", "pipelined", "pipelined_one_kernel" or "target_owned")
+ * selects that step loop at finalisation without tuning (networks the loop does not take keep the per-step
+ * kernels). */
 NGB_API int ngb_autotune(ngb_sim* sim, int64_t trial_steps, int32_t* deliver_grid_out);
 
 /* Spikes recorded in steps [t0_step, t1_step) of population `pop` (-1 = all,

@@ -61,21 +61,42 @@ __device__ __forceinline__ uint32_t poisson_count(uint64_t seed, int64_t tl, uin
   return kp;
 }
 
+// One exact-integration step of a LIF neuron in two parts.  V is propagated
+// with the current of the previous grid point, so the membrane potential of
+// the step and its threshold test depend on the state after the previous
+// step only, not on the step's input (lif_propagate); the input enters the
+// current (lif_apply).  lif_step is the two in sequence.
+__device__ __forceinline__ bool lif_propagate(const LifSeg& sg, float y, float I, int32_t ref, float& yp,
+                                              int32_t& rp) {
+  yp = y;
+  rp = ref;
+  if (rp > 0) {
+    rp -= 1;  // absolute refractory period: V held at V_reset
+  } else {
+    yp = __fadd_rn(__fadd_rn(__fmul_rn(sg.P22, y), __fmul_rn(sg.P21, I)), sg.P20Ie);
+  }
+  return yp >= sg.theta;
+}
+
+__device__ __forceinline__ void lif_apply(const LifSeg& sg, float& y, float& I, int32_t& ref, float yp, int32_t rp,
+                                          bool spk, float in) {
+  y = yp;
+  ref = rp;
+  I = __fadd_rn(__fmul_rn(sg.P11, I), in);
+  if (spk) {
+    y = sg.y_reset;
+    ref = sg.ref_steps;
+  }
+}
+
 // One exact-integration step of a LIF neuron with input `in` (ring + Poisson);
 // returns whether it spiked.
 __device__ __forceinline__ bool lif_step(const LifSeg& sg, float& y, float& I, int32_t& ref, float in) {
-  if (ref > 0) {
-    ref -= 1;  // absolute refractory period: V held at V_reset
-  } else {
-    y = __fadd_rn(__fadd_rn(__fmul_rn(sg.P22, y), __fmul_rn(sg.P21, I)), sg.P20Ie);
-  }
-  I = __fadd_rn(__fmul_rn(sg.P11, I), in);
-  if (y >= sg.theta) {
-    y = sg.y_reset;
-    ref = sg.ref_steps;
-    return true;
-  }
-  return false;
+  float yp;
+  int32_t rp;
+  const bool spk = lif_propagate(sg, y, I, ref, yp, rp);
+  lif_apply(sg, y, I, ref, yp, rp, spk, in);
+  return spk;
 }
 
 }  // namespace ngb

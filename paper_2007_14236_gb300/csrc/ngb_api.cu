@@ -250,7 +250,9 @@ struct ngb_sim {
                  // 3: pipelined (delivery of step t beside the update of step t + 1, two streams),
                  // 4: pipelined persistent step kernel (ring scheme, one grid barrier per step),
                  // 5: pipelined, one kernel per step (LIF networks: update and delivery of the
-                 //    previous step's queue in the same launch, chained by programmatic dependent launch)
+                 //    previous step's queue in the same launch, chained by programmatic dependent launch),
+                 // 6: target-owned persistent kernel (LIF networks, ring scheme: each block owns a tile
+                 //    of neurons with its ring in shared memory; spikes exchanged through mailboxes)
   cudaStream_t stream2 = nullptr;  // second stream of the pipelined loop's graphs
   bool persist_ok = false;
   int persist_grid = 0;
@@ -285,6 +287,15 @@ struct ngb_sim {
   uint64_t* in_ptr = nullptr;
   uint64_t* in_syn = nullptr;
   uint64_t n_plastic = 0;
+  // target-owned loop (mode 6): tile-major synapse layout (built on first
+  // use), mailboxes, overflow areas and the launch shape
+  bool lif_contig = false;  // LIF segments contiguous from neuron 0 (the kernel's segment search)
+  bool own_tried = false;
+  OwnedLayout own{};
+  unsigned long long* own_mb = nullptr;
+  unsigned long long* own_ovf = nullptr;
+  uint32_t own_T = 0;
+  size_t own_smem = 0;
 
   template <typename T>
   cudaError_t dalloc(T** p, size_t count) {
@@ -329,6 +340,110 @@ bool fused_ok(const ngb_sim* s) { return s->lif_npt == 1 && s->n_aeif_beta == 0;
 // Programmatic dependent launch chains the kernels of one stream; the
 // pipelined loop's kernels depend across two streams and go without it.
 bool pdl_of(const ngb_sim* s) { return s->pdl && s->mode != 3; }
+
+// The target-owned loop takes static LIF networks with the ring scheme and
+// one receptor, at most 2,048 neurons per block (one block per SM), and a
+// tile ring that fits in shared memory.
+bool owned_shape_ok(const ngb_sim* s, uint32_t* T_out, size_t* smem_out) {
+  if (s->serving || s->scheme != 1 || s->n_aeif || !s->n_lif || s->d_rules || s->R != 1 || !s->lif_contig ||
+      s->sms <= 0 || s->sms * 8 > 4 * 512 || s->n_lif > 64 || s->N <= 0)
+    return false;
+  const int64_t T = (s->N + s->sms - 1) / s->sms;
+  if (T > 2048) return false;
+  const size_t smem = owned_smem_bytes(s->cfg.deterministic != 0, (uint32_t)s->L, (uint32_t)T, s->n_lif, s->pa.n_thr);
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->cfg.device) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (smem + 4096 > (size_t)optin) return false;
+  *T_out = (uint32_t)T;
+  *smem_out = smem;
+  return true;
+}
+
+// Whether the target-owned loop can run; builds its synapse layout on the
+// first call (at most half of the free device memory; a failure leaves the
+// loop unavailable, not the handle).
+bool owned_ready(ngb_sim* s) {
+  uint32_t T = 0;
+  size_t smem = 0;
+  if (!owned_shape_ok(s, &T, &smem)) return false;
+  if (s->own.items) return true;
+  if (s->own_tried) return false;
+  s->own_tried = true;
+  int bpsm = 0;
+  if (owned_max_blocks_per_sm(s->cfg.deterministic != 0, T, smem, &bpsm) != cudaSuccess || bpsm < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  OwnedLayout L{};
+  cudaError_t e = owned_build(csr_of(s), s->src_syn, s->N, s->sms, (uint64_t)(free_b / 2 / sizeof(uint2)), &L,
+                              s->stream);
+  if (e != cudaSuccess || !L.items) {
+    cudaGetLastError();
+    return false;
+  }
+  s->allocs.push_back(L.items);
+  s->allocs.push_back(L.pub);
+  s->dev_bytes += (size_t)L.G * L.S * sizeof(uint2) + (size_t)s->N * sizeof(uint64_t);
+  if (s->dalloc(&s->own_mb, (size_t)4 * L.G * 8) != cudaSuccess ||
+      s->dalloc(&s->own_ovf, (size_t)4 * L.G * T) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  s->own = L;
+  s->own_T = T;
+  s->own_smem = smem;
+  return true;
+}
+
+// One target-owned launch per kMaxOwnedSteps steps, each with fresh
+// mailboxes, overflow areas and abort word.
+cudaError_t launch_owned_chunk(ngb_sim* s, int64_t steps) {
+  cudaError_t e = cudaSuccess;
+  while (steps > 0 && e == cudaSuccess) {
+    const int64_t n = std::min<int64_t>(steps, kMaxOwnedSteps);
+    e = cudaMemsetAsync(s->bar, 0, 4 * sizeof(unsigned), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->own_mb, 0xFF, (size_t)4 * s->own.G * 8 * 8, s->stream);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(s->own_ovf, 0xFF, (size_t)4 * s->own.G * s->own_T * 8, s->stream);
+    if (e != cudaSuccess) break;
+    OwnedArgs a{};
+    a.seg = s->lif_tab.dev;
+    a.thr = s->thr;
+    a.y = s->st0;
+    a.I = s->st1;
+    a.ref = s->ref;
+    a.ring = s->ring;
+    a.ring_N = s->N_cap;
+    a.N = s->N;
+    a.items = s->own.items;
+    a.pub = s->own.pub;
+    a.src_syn = s->src_syn;
+    a.mb = s->own_mb;
+    a.ovf = s->own_ovf;
+    a.sb = s->sb;
+    a.clk = s->clk;
+    a.abort = s->bar + 2;
+    a.steps = n;
+    a.S = s->own.S;
+    a.spin_limit = s->pa.spin_limit;
+    a.T = s->own_T;
+    a.L_mask = (uint32_t)(s->L - 1);
+    a.n_thr = s->pa.n_thr;
+    a.n_seg = s->n_lif;
+    a.withhold_block = s->pa.withhold_block;
+    e = launch_owned(a, s->cfg.deterministic != 0, s->own.G, s->stream);
+    steps -= n;
+  }
+  return e;
+}
 
 // The first update kernel of the step scans the pending spikes (spike-buffer scheme).
 cudaError_t launch_lif(ngb_sim* s, int64_t step_off = 0) {
@@ -970,6 +1085,15 @@ int rebuild_tables(ngb_sim* s) {
     }
   }
   s->n_lif = (int)lsegs.size();
+  {
+    int64_t next = 0;
+    bool contig = true;
+    for (const LifSeg& g : lsegs) {
+      contig = contig && g.offset == next;
+      next += g.n;
+    }
+    s->lif_contig = contig && next == s->N;
+  }
   s->n_aeif_exp = (int)asegs_exp.size();
   s->n_aeif_alpha = (int)asegs_alpha.size();
   s->n_aeif_beta = (int)asegs_beta.size();
@@ -1107,6 +1231,7 @@ int rebuild_tables(ngb_sim* s) {
   // the pipelined loop delivers with the ring scheme
   if (s->mode == 3 && (s->scheme != 1 || !s->stream2)) s->mode = 0;
   if (s->mode == 5 && !pipe1_ok(s)) s->mode = 0;
+  if (s->mode == 6 && !owned_ready(s)) s->mode = 0;
   s->tables_dirty = false;
   return capture_graph(s);
 }
@@ -1391,6 +1516,7 @@ int finalize_impl(ngb_sim* s) {
   if (env_mode && std::string(env_mode) == "fused" && s->scheme == 1) s->mode = 2;
   if (env_mode && std::string(env_mode) == "pipelined" && s->scheme == 1 && s->stream2) s->mode = 3;
   if (env_mode && std::string(env_mode) == "pipelined_one_kernel" && s->scheme == 1) s->mode = 5;
+  if (env_mode && std::string(env_mode) == "target_owned" && s->scheme == 1) s->mode = 6;
   s->graph_steps = s->cfg.steps_per_graph == 0 ? 100 : std::max(0, s->cfg.steps_per_graph);
   return rebuild_tables(s);
 }
@@ -1426,6 +1552,10 @@ int simulate_impl(ngb_sim* s, int64_t steps, bool profiled, double* kernel_ms, i
       int64_t done = 0;
       if (s->mode == 1 || s->mode == 4) {
         CK(launch_persistent_chunk(s, chunk));
+        done = chunk;
+      }
+      if (s->mode == 6) {
+        CK(launch_owned_chunk(s, chunk));
         done = chunk;
       }
       if (s->gexec) {
@@ -1785,7 +1915,7 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
     int m = 0, g = 0, pg = 0, sc = 0;
     while (in >> k >> m >> g >> pg >> sc) {
       if (k == key && g > 0 && (m == 0 || (m == 2 && sc == 1 && fused_ok(s)) || (m == 3 && sc == 1 && s->stream2) ||
-                                (m == 5 && sc == 1 && pipe1_ok(s)) ||
+                                (m == 5 && sc == 1 && pipe1_ok(s)) || (m == 6 && sc == 1 && owned_ready(s)) ||
                                 (m == 1 && s->persist_ok && pg > 0) ||
                                 (m == 4 && s->persist_ok && pg > 0 && sc == 1 && s->sb.wi3[0])) &&
           (sc == s->scheme || both)) {
@@ -1794,7 +1924,8 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
         s->deliver_grid = g;
         if (pg > 0) s->persist_grid = pg;
         rc = capture_graph(s);
-        if (rc == NGB_OK && deliver_grid_out) *deliver_grid_out = (m == 1 || m == 4) ? s->persist_grid : g;
+        if (rc == NGB_OK && deliver_grid_out)
+          *deliver_grid_out = (m == 1 || m == 4) ? s->persist_grid : m == 6 ? s->own.G : g;
         return rc;
       }
     }
@@ -1923,6 +2054,29 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
       }
       s->mode = 0;
     }
+    // target-owned persistent kernel (LIF networks, ring scheme; layout built on first use)
+    if (rc == NGB_OK && scheme == 1 && owned_ready(s)) {
+      s->mode = 6;
+      rc = snapshot_restore(s, sn);
+      if (rc == NGB_OK) {
+        CK(launch_owned_chunk(s, 100));  // warm-up
+        CK(cudaEventRecord(e0, s->stream));
+        CK(launch_owned_chunk(s, trial_steps));
+        CK(cudaEventRecord(e1, s->stream));
+        CK(cudaEventSynchronize(e1));
+        uint32_t err = 0;
+        CK(cudaMemcpy(&err, s->sb.err, sizeof(err), cudaMemcpyDeviceToHost));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        const double per_step = ms / (double)trial_steps;
+        if (!(err & kErrBarrierTimeout) && per_step < best_ms) {
+          best_ms = per_step;
+          best_mode = 6;
+          best_scheme = scheme;
+        }
+      }
+      s->mode = 0;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1940,7 +2094,8 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
     out << key << " " << best_mode << " " << best_grid << " " << (s->persist_ok ? best_pgrid : 0) << " "
         << best_scheme << "\n";
   }
-  if (deliver_grid_out) *deliver_grid_out = (best_mode == 1 || best_mode == 4) ? best_pgrid : best_grid;
+  if (deliver_grid_out)
+    *deliver_grid_out = (best_mode == 1 || best_mode == 4) ? best_pgrid : best_mode == 6 ? s->own.G : best_grid;
   return NGB_OK;
 }
 
@@ -2099,6 +2254,7 @@ int ngb_get_stats(ngb_sim* s, ngb_stats* out) {
     out->device_bytes = (int64_t)s->dev_bytes;
     out->mode = s->mode;
     out->launch_grid = (s->mode == 1 || s->mode == 4) ? s->persist_grid
+                       : s->mode == 6 ? s->own.G
                        : s->mode == 2 ? s->lif_blocks + s->aeif_blocks + s->aeifa_blocks
                                       : s->deliver_grid;  // graph and pipelined loops: the delivery grid
     out->delivery = s->scheme;

@@ -541,6 +541,46 @@ struct PersistArgs {
   uint32_t off_aseg, off_lvoff, off_avoff, off_thr;  // dynamic shared memory layout
 };
 
+// Target-owned persistent step loop (owned.cu): tile-major synapse items
+// (G tiles of S items each, padded per source) and the per-neuron spike entry
+// (C_s / 4) << 36 | off_s (0: no synapses).
+struct OwnedLayout {
+  uint2* items;
+  uint64_t* pub;
+  uint64_t S;
+  int G;
+  uint32_t max_width;
+};
+
+constexpr int64_t kMaxOwnedSteps = 4 * 65535;  // steps per launch (mailbox stamps are 16 bits)
+
+struct OwnedArgs {
+  const LifSeg* seg;     // LIF segments in neuron order, contiguous from 0
+  const uint32_t* thr;   // Poisson thresholds of all segments
+  float *y, *I;
+  int32_t* ref;
+  void* ring;            // [L][ring_N] FP32 (int64 fixed point in deterministic mode), one receptor
+  int64_t ring_N;
+  int64_t N;             // neurons
+  const uint2* items;    // [G][S]
+  const uint64_t* pub;   // [N]
+  const uint64_t* src_syn;
+  unsigned long long* mb;   // [4][G][8] mailboxes, by step mod 4
+  unsigned long long* ovf;  // [4][G][T] overflow entries
+  SpikeBuf sb;
+  int64_t* clk;
+  unsigned* abort;       // nonzero: a block gave up waiting
+  int64_t steps;
+  uint64_t S;
+  unsigned long long spin_limit;
+  uint32_t T;            // neurons per tile (block): ceil(N / G)
+  uint32_t L_mask;
+  uint32_t n_thr;
+  int32_t n_seg;
+  int32_t withhold_block;  // test hook: this block does not publish its first step (-1: none)
+  uint32_t off_seg, off_thr, off_pub, off_ids, off_rec;  // dynamic shared memory layout (set by launch_owned)
+};
+
 // ------------------------------------------------------------------ host side
 // Kernel launchers (one translation unit each).
 // age: spike-buffer scheme; scan: this kernel also scans the pending list
@@ -605,6 +645,16 @@ cudaError_t launch_step_pipe(const SegTable<LifSeg>& segs, int64_t upd_blocks, i
                              float* y, float* I, int32_t* ref, Ring ring, bool fixed, int wdtype, int64_t* clk,
                              int64_t step_off, const Csr& csr, SpikeBuf sb, bool deliver_prev, bool pdl,
                              cudaStream_t st);
+// Target-owned loop: build the tile-major layout of a finalised CSR for G
+// tiles (out->items NULL when C_s or the layout exceeds its limits or
+// max_items; the caller frees pub and items), the dynamic shared memory of its
+// kernel, its occupancy, and one cooperative launch of a.steps steps (grid G,
+// mailboxes and overflow areas reset by the caller).
+cudaError_t owned_build(const Csr& csr, const uint64_t* src_syn, int64_t N, int G, uint64_t max_items,
+                        OwnedLayout* out, cudaStream_t st);
+size_t owned_smem_bytes(bool fixed, uint32_t L, uint32_t T, int n_seg, uint32_t n_thr);
+cudaError_t owned_max_blocks_per_sm(bool fixed, uint32_t T, size_t smem, int* out);
+cudaError_t launch_owned(OwnedArgs a, bool fixed, int grid, cudaStream_t st);
 // clk[0] += n (clk[1] = clk[0] - 1); the ring scheme's step counters (both
 // the per-step and the pipelined ones) are cleared.
 cudaError_t launch_tick_add(int64_t* clk, int64_t n, unsigned long long* ctr, unsigned long long* ctr3, bool pdl,

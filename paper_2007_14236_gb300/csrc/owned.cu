@@ -1,0 +1,669 @@
+// owned.cu -- target-owned persistent step loop (LIF networks, ring scheme).
+//
+// One resident block per SM for the whole launch.  Block b of the G blocks
+// owns the neurons gid = b, b + G, b + 2G, ... (its tile: T = ceil(N / G)
+// neurons, local index gid / G), keeps their state in registers and their
+// ring buffer ([L][T] words, Sec. 2.2 ring of slots t + d) in shared memory.
+// No kernel boundary and no grid barrier separate the steps: the blocks
+// exchange only the step's spikes, through per-block mailboxes whose words
+// carry a step stamp, so a word is valid exactly when its stamp is the
+// step's.
+//
+// Synapses in tile-major order: the synapses of source s onto the neurons of
+// tile b are the items [b S + off_s, b S + off_s + c_bs) of one array, padded
+// to C_s = max_b c_bs items per source (S = sum of C_s), each item
+// {local target | delay << 16, FP32 weight} or the filler 0xFFFFFFFF.  The
+// tile of a neuron is gid mod G, so every tile holds the same share of every
+// population and C_s stays close to the mean per-tile count.  A spike thus
+// needs no per-tile index lookup: the firing block publishes (off_s, C_s),
+// and every block reads its own C_s items in one round of loads.
+//
+// Step t, in every block:
+//   update    slot t of the tile's ring read and cleared, Poisson drive
+//             (counts drawn while the previous step's mailboxes were
+//             awaited), exact LIF step (Eqs. 1-2), threshold; new spikes of
+//             sources with synapses collected in shared memory
+//   publish   mailbox of the block for step t (buffer t mod 2): 8 stamped
+//             words, 7 spike entries (off_s, C_s) and the count; further
+//             entries in the block's overflow area, same format.  The
+//             spike record is buffered in shared memory and flushed to the
+//             device record (one atomic per flush) when it could overflow and
+//             at the end of the launch; the event count is added at the end
+//   exchange  every mailbox word of step t polled until stamped (bounded
+//             spin); the entries gathered in shared memory
+//   deliver   warps take the entries and add each item into the shared ring
+//             at slot (t + delay) & (L - 1): FP32 atomics, or int64 fixed
+//             point (units of 2^-32, as the other loops) in deterministic mode
+// A block publishes step t + 2 into the buffer of step t only after reading
+// every block's step t + 1 mailbox, which each block publishes only after
+// reading all of step t: a buffer is never overwritten while it is read.
+// The mailboxes and overflow areas are reset before each launch, and a launch
+// runs at most kMaxOwnedSteps steps, so a stale word never carries the
+// current stamp.  Every wait is bounded: a block that gives up sets the
+// timeout flag and the abort word, and the others stop at their next poll.
+//
+// The arithmetic of the update (neuron_step.cuh) and the fixed-point
+// conversion are those of the per-step kernels, so deterministic runs are
+// bit-identical to every other step loop.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+#include <vector>
+
+#include "builder.h"
+#include "neuron_step.cuh"
+
+namespace ngb {
+
+namespace {
+
+constexpr int kOwnedBlock = 512;
+constexpr int kMbWords = 8;        // mailbox words per block and step: 7 entries + count
+constexpr int kPollWords = 4;      // mailbox words polled per thread: G * 8 <= 4 * 512
+constexpr int kIdsCap = 2048;      // spike entries gathered per step in shared memory
+constexpr int kRecCap = 4096;      // spike-record entries buffered per block (>= 2 x the largest tile)
+constexpr uint32_t kFiller = 0xFFFFFFFFu;
+constexpr int kStampShift = 48;    // word = stamp << 48 | payload
+constexpr uint64_t kPayloadMask = (1ull << kStampShift) - 1;
+constexpr int kOffBits = 36;       // entry payload = (C_s / 4) << 36 | off_s
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <bool kFixed>
+__device__ __forceinline__ void ring_add(void* ring_s, uint32_t idx, float w) {
+  if (kFixed) {
+    const long long q = __float2ll_rn(w * 4294967296.0f);
+    atomicAdd(reinterpret_cast<unsigned long long*>(ring_s) + idx, (unsigned long long)q);
+  } else {
+    atomicAdd(reinterpret_cast<float*>(ring_s) + idx, w);
+  }
+}
+
+// Items of one spike entry (C_s items from b S + off_s), by the whole warp.
+template <bool kFixed>
+__device__ __forceinline__ void deliver_entry_warp(uint64_t e, const OwnedArgs& a, uint64_t tile_base, int64_t t,
+                                                   void* ring_s, int lane) {
+  const uint64_t off = e & ((1ull << kOffBits) - 1);
+  const uint32_t C = (uint32_t)(e >> kOffBits) * 4u;
+  const uint2* it = a.items + tile_base + off;
+  uint32_t k = (uint32_t)lane;
+  // two chunks of 32 items in flight per pass
+  for (; k < C; k += 64) {
+    const uint2 x0 = __ldg(it + k);
+    const uint2 x1 = k + 32 < C ? __ldg(it + k + 32) : make_uint2(kFiller, 0u);
+    if (x0.x != kFiller)
+      ring_add<kFixed>(ring_s, ((uint32_t)(t + (x0.x >> 16)) & a.L_mask) * a.T + (x0.x & 0xFFFFu),
+                       __uint_as_float(x0.y));
+    if (x1.x != kFiller)
+      ring_add<kFixed>(ring_s, ((uint32_t)(t + (x1.x >> 16)) & a.L_mask) * a.T + (x1.x & 0xFFFFu),
+                       __uint_as_float(x1.y));
+  }
+}
+
+// The first two 32-item chunks of an entry (lane's items lane and lane + 32;
+// the filler past the entry's width), and the rest of it.
+__device__ __forceinline__ void load_head(uint64_t e, const OwnedArgs& a, uint64_t tile_base, int lane, uint2& x0,
+                                          uint2& x1) {
+  const uint64_t off = e & ((1ull << kOffBits) - 1);
+  const uint32_t C = (uint32_t)(e >> kOffBits) * 4u;
+  const uint2* it = a.items + tile_base + off;
+  x0 = (uint32_t)lane < C ? __ldg(it + lane) : make_uint2(kFiller, 0u);
+  x1 = (uint32_t)lane + 32 < C ? __ldg(it + lane + 32) : make_uint2(kFiller, 0u);
+}
+
+template <bool kFixed>
+__device__ __forceinline__ void add_item(uint2 x, const OwnedArgs& a, int64_t t, void* ring_s) {
+  if (x.x != kFiller)
+    ring_add<kFixed>(ring_s, ((uint32_t)(t + (x.x >> 16)) & a.L_mask) * a.T + (x.x & 0xFFFFu), __uint_as_float(x.y));
+}
+
+template <bool kFixed>
+__device__ __forceinline__ void deliver_entry_tail(uint64_t e, const OwnedArgs& a, uint64_t tile_base, int64_t t,
+                                                   void* ring_s, int lane) {
+  const uint64_t off = e & ((1ull << kOffBits) - 1);
+  const uint32_t C = (uint32_t)(e >> kOffBits) * 4u;
+  const uint2* it = a.items + tile_base + off;
+  for (uint32_t k = 64u + (uint32_t)lane; k < C; k += 32) add_item<kFixed>(__ldg(it + k), a, t, ring_s);
+}
+
+// The same by one thread (entries beyond the shared-memory list).
+template <bool kFixed>
+__device__ __forceinline__ void deliver_entry_thread(uint64_t e, const OwnedArgs& a, uint64_t tile_base, int64_t t,
+                                                     void* ring_s) {
+  const uint64_t off = e & ((1ull << kOffBits) - 1);
+  const uint32_t C = (uint32_t)(e >> kOffBits) * 4u;
+  const uint2* it = a.items + tile_base + off;
+  for (uint32_t k = 0; k < C; ++k) {
+    const uint2 x = __ldg(it + k);
+    if (x.x != kFiller)
+      ring_add<kFixed>(ring_s, ((uint32_t)(t + (x.x >> 16)) & a.L_mask) * a.T + (x.x & 0xFFFFu),
+                       __uint_as_float(x.y));
+  }
+}
+
+}  // namespace
+
+template <bool kFixed, int kNpt>
+__global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
+  using RW = typename std::conditional<kFixed, long long, float>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  RW* ring_s = reinterpret_cast<RW*>(smem);
+  LifSeg* s_seg = reinterpret_cast<LifSeg*>(smem + a.off_seg);
+  uint32_t* s_thr = reinterpret_cast<uint32_t*>(smem + a.off_thr);
+  uint64_t* s_pub = reinterpret_cast<uint64_t*>(smem + a.off_pub);  // [T]
+  uint64_t* s_ids = reinterpret_cast<uint64_t*>(smem + a.off_ids);  // [2][kIdsCap], by step parity
+  uint2* s_rec = reinterpret_cast<uint2*>(smem + a.off_rec);        // [kRecCap] {neuron, step - t0}
+  __shared__ int s_np[2], s_nid[2], s_novm[2];
+  __shared__ int s_ovm[2][kMbWords * 32];  // mailboxes with overflow (block ids)
+  __shared__ int s_abort, s_rn;
+  __shared__ unsigned long long s_rbase;
+
+  const int b = (int)blockIdx.x, G = (int)gridDim.x;
+  const int tid = (int)threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kWarps = kOwnedBlock / 32;
+  const uint32_t T = a.T;
+  const int64_t N = a.N;
+  const uint64_t tile_base = (uint64_t)b * a.S;
+
+  for (int i = tid; i < a.n_seg; i += kOwnedBlock) s_seg[i] = a.seg[i];
+  for (uint32_t i = tid; i < a.n_thr; i += kOwnedBlock) s_thr[i] = a.thr[i];
+  if (tid == 0) {
+    s_np[0] = s_np[1] = 0;
+    s_nid[0] = s_nid[1] = 0;
+    s_novm[0] = s_novm[1] = 0;
+    s_abort = 0;
+    s_rn = 0;
+  }
+  // the tile's ring slots, from the global ring [L][N]
+  for (uint32_t slot = 0; slot <= a.L_mask; ++slot)
+    for (uint32_t lt = tid; lt < T; lt += kOwnedBlock) {
+      const int64_t gid = (int64_t)lt * G + b;
+      RW v = (RW)0;
+      if (gid < N) v = reinterpret_cast<const RW*>(a.ring)[(uint64_t)slot * (uint64_t)a.ring_N + (uint64_t)gid];
+      ring_s[slot * T + lt] = v;
+    }
+  __syncthreads();
+
+  // the thread's neurons: local index lt = tid + j * 512, gid = lt * G + b
+  float y[kNpt], I[kNpt];
+  int32_t ref[kNpt];
+  int si[kNpt];
+  uint64_t pub[kNpt];
+  uint32_t outdeg[kNpt], kp[kNpt];
+  bool valid[kNpt];
+#pragma unroll
+  for (int j = 0; j < kNpt; ++j) {
+    const uint32_t lt = (uint32_t)(tid + j * kOwnedBlock);
+    const int64_t gid = (int64_t)lt * G + b;
+    valid[j] = lt < T && gid < N;
+    y[j] = I[j] = 0.f;
+    ref[j] = 0;
+    si[j] = 0;
+    pub[j] = 0;
+    outdeg[j] = 0;
+    kp[j] = 0;
+    if (valid[j]) {
+      y[j] = a.y[gid];
+      I[j] = a.I[gid];
+      ref[j] = a.ref[gid];
+      pub[j] = a.pub[gid];
+      outdeg[j] = (uint32_t)(a.src_syn[gid + 1] - a.src_syn[gid]);
+      int lo = 0, hi = a.n_seg;  // segment: the last one whose offset <= gid
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (s_seg[mid].offset <= gid) lo = mid;
+        else hi = mid;
+      }
+      si[j] = lo;
+    }
+  }
+  const int64_t t0 = a.clk[0];
+  // the buffered spike record to the device record (block-wide, after a barrier)
+  auto flush_record = [&]() {
+    const int n = s_rn;
+    if (tid == 0) s_rbase = atomicAdd(a.sb.rec_count, (unsigned long long)n);
+    __syncthreads();
+    const unsigned long long base = s_rbase;
+    if (a.sb.rec_cap > 0)
+      for (int i = tid; i < n; i += kOwnedBlock) {
+        if (base + (unsigned long long)i < (unsigned long long)a.sb.rec_cap) {
+          a.sb.rec_id[base + i] = s_rec[i].x;
+          a.sb.rec_step[base + i] = t0 + (int64_t)s_rec[i].y;
+        } else {
+          atomicOr(a.sb.err, kErrRecordOverflow);
+        }
+      }
+    __syncthreads();
+    if (tid == 0) s_rn = 0;
+    __syncthreads();
+  };
+  unsigned long long nev = 0;  // synaptic events of this thread's spikes
+  auto draw_counts = [&](int64_t t) {
+#pragma unroll
+    for (int j = 0; j < kNpt; ++j) {
+      kp[j] = 0;
+      if (!valid[j]) continue;
+      const LifSeg& sg = s_seg[si[j]];
+      if (sg.n_thr > 0) {
+        const int64_t gid = (int64_t)(tid + j * kOwnedBlock) * G + b;
+        kp[j] = poisson_count(sg.seed, t - sg.t0, sg.local_off + (uint32_t)(gid - sg.offset), s_thr + sg.thr_off,
+                              sg.n_thr);
+      }
+    }
+  };
+  draw_counts(t0);
+  const int nwords = G * kMbWords;
+  // mailbox buffer and stamp of the spikes of step t0 + r
+  auto mb_of = [&](int64_t r) { return a.mb + (size_t)(r & 3) * nwords; };
+  auto ovf_of = [&](int64_t r, int m) { return a.ovf + ((size_t)(r & 3) * G + m) * T; };
+  auto stamp_of = [](int64_t r) { return (uint64_t)((r >> 2) % 65535) << kStampShift; };
+  // The threshold test of a step depends only on the state after the previous
+  // step (lif_propagate), so the spikes of step t + 1 are known once step t is
+  // updated: they are published then, and delivered during the next step.
+  float yp[kNpt];
+  int32_t rp[kNpt];
+  bool sp[kNpt];
+  auto predict = [&](int q) {  // entries of the spikes of the next step to s_pub, counted in s_np[q]
+#pragma unroll
+    for (int j = 0; j < kNpt; ++j) {
+      sp[j] = false;
+      if (!valid[j]) continue;
+      sp[j] = lif_propagate(s_seg[si[j]], y[j], I[j], ref[j], yp[j], rp[j]);
+      if (sp[j] && pub[j] != 0) s_pub[atomicAdd(&s_np[q], 1)] = pub[j];
+    }
+  };
+  auto publish = [&](int64_t r, int np) {
+    const uint64_t st = stamp_of(r);
+    if (tid < kMbWords) {
+      const uint64_t payload = tid < kMbWords - 1 ? (tid < np ? s_pub[tid] : 0ull) : (uint64_t)np;
+      st_relaxed_u64(mb_of(r) + (size_t)b * kMbWords + tid, st | payload);
+    }
+    for (int k = kMbWords - 1 + tid; k < np; k += kOwnedBlock)
+      st_relaxed_u64(ovf_of(r, b) + (k - (kMbWords - 1)), st | s_pub[k]);
+  };
+  // Entries of the spikes of step t0 + r, from every mailbox, to s_ids[q]
+  // (count s_nid[q]); entries beyond the list are delivered at once by the
+  // thread that read them.  Returns false when the launch must stop.
+  auto gather = [&](int64_t r, int q) -> bool {
+    const int64_t tr = t0 + r;
+    const uint64_t stamp = stamp_of(r);
+    const unsigned long long* mbp = mb_of(r);
+    unsigned long long v[kPollWords];
+    // (addresses clamped rather than the loads predicated: one round of loads)
+#pragma unroll
+    for (int i = 0; i < kPollWords; ++i) v[i] = ld_relaxed_u64(mbp + min(tid + i * kOwnedBlock, nwords - 1));
+    unsigned pend = 0;
+#pragma unroll
+    for (int i = 0; i < kPollWords; ++i)
+      if (tid + i * kOwnedBlock < nwords && (v[i] & ~kPayloadMask) != stamp) pend |= 1u << i;
+    bool gave_up = false;
+    unsigned long long spins = 0;
+    while (pend) {
+#pragma unroll
+      for (int i = 0; i < kPollWords; ++i)
+        if (pend & (1u << i)) {
+          v[i] = ld_relaxed_u64(mbp + tid + i * kOwnedBlock);
+          if ((v[i] & ~kPayloadMask) == stamp) pend &= ~(1u << i);
+        }
+      if (!pend) break;
+      ++spins;
+      if ((spins & 63u) == 0 && (ld_relaxed_u32(a.abort) != 0u || s_abort)) {
+        gave_up = true;
+        break;
+      }
+      if (spins > a.spin_limit) {
+        atomicOr(a.sb.err, kErrBarrierTimeout);
+        atomicExch(a.abort, 1u);
+        gave_up = true;
+        break;
+      }
+    }
+    if (gave_up) s_abort = 1;
+    if (!gave_up) {
+#pragma unroll
+      for (int i = 0; i < kPollWords; ++i) {
+        const int w = tid + i * kOwnedBlock;
+        if (w >= nwords) continue;
+        const uint64_t pl = v[i] & kPayloadMask;
+        if ((w & (kMbWords - 1)) == kMbWords - 1) {
+          if (pl > (uint64_t)(kMbWords - 1)) s_ovm[q][atomicAdd(&s_novm[q], 1)] = w / kMbWords;
+        } else if (pl != 0) {
+          const int pos = atomicAdd(&s_nid[q], 1);
+          if (pos < kIdsCap) s_ids[q * kIdsCap + pos] = pl;
+          else deliver_entry_thread<kFixed>(pl, a, tile_base, tr, ring_s);
+        }
+      }
+    }
+    __syncthreads();
+    if (s_abort) return false;
+    if (s_novm[q] > 0) {
+      // blocks with more than 7 spikes: their overflow words, a warp per block
+      for (int k = warp; k < s_novm[q]; k += kWarps) {
+        const int m = s_ovm[q][k];
+        const uint64_t cnt = ld_relaxed_u64(mbp + (size_t)m * kMbWords + (kMbWords - 1)) & kPayloadMask;
+        const unsigned long long* op = ovf_of(r, m);
+        for (uint64_t i = (uint64_t)lane; i + (kMbWords - 1) < cnt; i += 32) {
+          unsigned long long x = ld_relaxed_u64(op + i);
+          unsigned long long sp2 = 0;
+          while ((x & ~kPayloadMask) != stamp) {
+            ++sp2;
+            if ((sp2 & 63u) == 0 && ld_relaxed_u32(a.abort) != 0u) break;
+            if (sp2 > a.spin_limit) {
+              atomicOr(a.sb.err, kErrBarrierTimeout);
+              atomicExch(a.abort, 1u);
+              break;
+            }
+            x = ld_relaxed_u64(op + i);
+          }
+          if ((x & ~kPayloadMask) != stamp) {
+            s_abort = 1;
+            break;
+          }
+          const uint64_t pl = x & kPayloadMask;
+          const int pos = atomicAdd(&s_nid[q], 1);
+          if (pos < kIdsCap) s_ids[q * kIdsCap + pos] = pl;
+          else deliver_entry_thread<kFixed>(pl, a, tile_base, tr, ring_s);
+        }
+      }
+      __syncthreads();
+      if (s_abort) return false;
+    }
+    return true;
+  };
+  // the spikes of step t0, published and gathered
+  predict(0);
+  __syncthreads();
+  if (b != a.withhold_block) publish(0, s_np[0]);
+  bool aborted = !gather(0, 0);
+  for (int64_t r = 0; r < a.steps && !aborted; ++r) {
+    const int64_t t = t0 + r;
+    const int par = (int)(r & 1);  // s_ids[par]: entries of step r (gathered during the previous step)
+    if (tid == 0) {
+      s_np[par] = 0;         // published during the previous step; next used by the predictions of step r + 1
+      s_nid[par ^ 1] = 0;    // entries of step r + 1, gathered below
+      s_novm[par ^ 1] = 0;
+    }
+    if (s_rn > kRecCap - (int)T) flush_record();  // room for one step's spikes of the tile
+    // the first two chunks of the warp's first two entries of step r: the
+    // loads are in flight during the update, the publication and the Poisson
+    // draws of step t + 1
+    const int n = min(s_nid[par], kIdsCap);
+    const uint64_t* ids = s_ids + par * kIdsCap;
+    const uint64_t e0 = warp < n ? ids[warp] : 0ull;
+    const uint64_t e1 = warp + kWarps < n ? ids[warp + kWarps] : 0ull;
+    uint2 x[4];
+    load_head(e0, a, tile_base, lane, x[0], x[1]);
+    load_head(e1, a, tile_base, lane, x[2], x[3]);
+    // ------------------------------------------------------------ update
+    const uint32_t slot = (uint32_t)t & a.L_mask;
+#pragma unroll
+    for (int j = 0; j < kNpt; ++j) {
+      if (!valid[j]) continue;
+      const uint32_t lt = (uint32_t)(tid + j * kOwnedBlock);
+      const LifSeg& sg = s_seg[si[j]];
+      float xin;
+      if (kFixed) {
+        const long long q = ring_s[slot * T + lt];
+        xin = __double2float_rn(__dmul_rn(__ll2double_rn(q), 2.3283064365386963e-10));  // x 2^-32
+      } else {
+        xin = ring_s[slot * T + lt];
+      }
+      ring_s[slot * T + lt] = (RW)0;
+      if (sg.n_thr > 0) xin = __fadd_rn(xin, __fmul_rn((float)kp[j], sg.w_ext));
+      lif_apply(sg, y[j], I[j], ref[j], yp[j], rp[j], sp[j], xin);
+      if (sp[j]) {
+        s_rec[atomicAdd(&s_rn, 1)] = make_uint2((uint32_t)((int64_t)lt * G + b), (uint32_t)r);
+        nev += outdeg[j];
+      }
+    }
+    // ------------------------------------------------------------ spikes of step r + 1
+    const bool more = r + 1 < a.steps;
+    if (more) predict(par ^ 1);
+    __syncthreads();  // s_pub complete; slot t read and cleared
+    if (more) {
+      publish(r + 1, s_np[par ^ 1]);
+      draw_counts(t + 1);
+    }
+    // ------------------------------------------------------------ deliver the spikes of step r
+#pragma unroll
+    for (int q = 0; q < 4; ++q) add_item<kFixed>(x[q], a, t, ring_s);
+    deliver_entry_tail<kFixed>(e0, a, tile_base, t, ring_s, lane);
+    deliver_entry_tail<kFixed>(e1, a, tile_base, t, ring_s, lane);
+    for (int i = warp + 2 * kWarps; i < n; i += kWarps)
+      deliver_entry_warp<kFixed>(ids[i], a, tile_base, t, ring_s, lane);
+    // ------------------------------------------------------------ entries of step r + 1
+    if (more) {
+      if (!gather(r + 1, par ^ 1)) aborted = true;  // ends with a barrier: slot t + 1 complete
+    } else {
+      __syncthreads();
+    }
+  }
+  if (!aborted) {
+    flush_record();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nev += __shfl_xor_sync(0xffffffffu, nev, o);
+    if (lane == 0 && nev) atomicAdd(a.sb.events, nev);
+#pragma unroll
+    for (int j = 0; j < kNpt; ++j) {
+      if (!valid[j]) continue;
+      const int64_t gid = (int64_t)(tid + j * kOwnedBlock) * G + b;
+      a.y[gid] = y[j];
+      a.I[gid] = I[j];
+      a.ref[gid] = ref[j];
+    }
+    for (uint32_t slot = 0; slot <= a.L_mask; ++slot)
+      for (uint32_t lt = tid; lt < T; lt += kOwnedBlock) {
+        const int64_t gid = (int64_t)lt * G + b;
+        if (gid < N)
+          reinterpret_cast<RW*>(a.ring)[(uint64_t)slot * (uint64_t)a.ring_N + (uint64_t)gid] = ring_s[slot * T + lt];
+      }
+    if (b == 0 && tid == 0) {
+      a.clk[0] = t0 + a.steps;
+      a.clk[1] = t0 + a.steps - 1;
+    }
+  }
+}
+
+namespace {
+
+void* owned_kernel(bool fixed, int npt) {
+  if (fixed) {
+    if (npt == 1) return reinterpret_cast<void*>(&k_owned<true, 1>);
+    if (npt == 2) return reinterpret_cast<void*>(&k_owned<true, 2>);
+    return reinterpret_cast<void*>(&k_owned<true, 4>);
+  }
+  if (npt == 1) return reinterpret_cast<void*>(&k_owned<false, 1>);
+  if (npt == 2) return reinterpret_cast<void*>(&k_owned<false, 2>);
+  return reinterpret_cast<void*>(&k_owned<false, 4>);
+}
+
+// ----------------------------------------------------------------- layout
+// Items per (source, tile): one warp per source.
+__global__ void k_owned_count(const uint64_t* __restrict__ src_syn, const uint32_t* __restrict__ tgt, int64_t N,
+                              int G, uint32_t* cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = w0; s < N; s += nw) {
+    const uint64_t lo = src_syn[s], hi = src_syn[s + 1];
+    for (uint64_t j = lo + (uint64_t)lane; j < hi; j += 32)
+      atomicAdd(cnt + (uint64_t)s * G + ((tgt[j] & kTgtMask) % (uint32_t)G), 1u);
+  }
+}
+
+// C_s = max over tiles, rounded up to 4; the counts become fill cursors.
+__global__ void k_owned_width(int64_t N, int G, uint32_t* cnt, unsigned long long* width) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t m = 0;
+    for (int b = 0; b < G; ++b) {
+      m = max(m, cnt[(uint64_t)s * G + b]);
+      cnt[(uint64_t)s * G + b] = 0;
+    }
+    width[s] = (m + 3u) & ~3u;
+  }
+}
+
+__global__ void k_owned_pub(int64_t N, const unsigned long long* width, const unsigned long long* off,
+                            uint64_t* pub) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < N; s += (int64_t)gridDim.x * blockDim.x)
+    pub[s] = width[s] ? ((width[s] / 4) << kOffBits) | off[s] : 0ull;
+}
+
+__device__ __forceinline__ float weight_at(const void* w, int wdtype, uint64_t j) {
+  if (wdtype == 1) return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(w)[j]);
+  if (wdtype == 2) return __half2float(reinterpret_cast<const __half*>(w)[j]);
+  return reinterpret_cast<const float*>(w)[j];
+}
+
+__global__ void k_owned_fill(const uint64_t* __restrict__ src_syn, const uint32_t* __restrict__ src_grp,
+                             const uint64_t* __restrict__ grp_start, const uint16_t* __restrict__ grp_delay,
+                             const uint32_t* __restrict__ tgt, const void* w, int wdtype, int64_t N, int G,
+                             uint64_t S, const unsigned long long* __restrict__ off, uint32_t* cursor, uint2* items) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = w0; s < N; s += nw) {
+    for (uint32_t g = src_grp[s]; g < src_grp[s + 1]; ++g) {
+      const uint32_t d = grp_delay[g];
+      for (uint64_t j = grp_start[g] + (uint64_t)lane; j < grp_start[g + 1]; j += 32) {
+        const uint32_t target = tgt[j] & kTgtMask;
+        const uint32_t tile = target % (uint32_t)G, lt = target / (uint32_t)G;
+        const uint32_t pos = atomicAdd(cursor + (uint64_t)s * G + tile, 1u);
+        items[(uint64_t)tile * S + off[s] + pos] = make_uint2(lt | (d << 16), __float_as_uint(weight_at(w, wdtype, j)));
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t owned_build(const Csr& csr, const uint64_t* src_syn, int64_t N, int G, uint64_t max_items,
+                        OwnedLayout* out, cudaStream_t st) {
+  *out = OwnedLayout{};
+  uint32_t* cnt = nullptr;
+  unsigned long long *width = nullptr, *off = nullptr;
+  void* tmp = nullptr;
+  size_t tmp_bytes = 0;
+  uint64_t S = 0;
+  const int grid = 1024;
+  cudaError_t e = cudaMalloc(&cnt, (size_t)N * G * sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&width, (size_t)(N + 1) * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&off, (size_t)(N + 1) * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&out->pub, (size_t)N * sizeof(uint64_t));
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, (size_t)N * G * sizeof(uint32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(width + N, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) {
+    k_owned_count<<<grid, 256, 0, st>>>(src_syn, csr.tgt, N, G, cnt);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    k_owned_width<<<grid, 256, 0, st>>>(N, G, cnt, width);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = scan_scratch_bytes_u64((uint64_t)N + 1, &tmp_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&tmp, tmp_bytes > 0 ? tmp_bytes : 1);
+  if (e == cudaSuccess) e = exclusive_scan_u64(width, off, (uint64_t)N + 1, tmp, tmp_bytes, st);
+  unsigned long long wmax = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&S, off + N, sizeof(uint64_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  // widest source (the entry holds C_s / 4 in 12 bits)
+  if (e == cudaSuccess && N > 0) {
+    std::vector<unsigned long long> wv((size_t)N);
+    e = cudaMemcpy(wv.data(), width, (size_t)N * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    for (unsigned long long x : wv) wmax = x > wmax ? x : wmax;
+  }
+  bool fits = e == cudaSuccess && wmax / 4 < (1ull << (kStampShift - kOffBits)) && S < (1ull << kOffBits) &&
+              (uint64_t)G * S <= max_items;
+  if (fits) {
+    e = cudaMalloc(&out->items, (size_t)((uint64_t)G * S > 0 ? (uint64_t)G * S : 1) * sizeof(uint2));
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      fits = false;
+      e = cudaSuccess;
+    }
+  }
+  if (fits && e == cudaSuccess) e = cudaMemsetAsync(out->items, 0xFF, (size_t)G * S * sizeof(uint2), st);
+  if (fits && e == cudaSuccess) {
+    k_owned_pub<<<grid, 256, 0, st>>>(N, width, off, out->pub);
+    e = cudaGetLastError();
+  }
+  if (fits && e == cudaSuccess) {
+    k_owned_fill<<<grid, 256, 0, st>>>(src_syn, csr.src_grp, csr.grp_start, csr.grp_delay, csr.tgt, csr.w,
+                                       csr.wdtype, N, G, S, off, cnt, out->items);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(cnt);
+  cudaFree(width);
+  cudaFree(off);
+  cudaFree(tmp);
+  if (e != cudaSuccess || !fits) {
+    cudaFree(out->pub);
+    cudaFree(out->items);
+    *out = OwnedLayout{};
+    return e;
+  }
+  out->S = S;
+  out->G = G;
+  out->max_width = (uint32_t)wmax;
+  return cudaSuccess;
+}
+
+size_t owned_smem_bytes(bool fixed, uint32_t L, uint32_t T, int n_seg, uint32_t n_thr) {
+  auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  return a16((size_t)L * T * (fixed ? 8 : 4)) + a16((size_t)n_seg * sizeof(LifSeg)) + a16((size_t)n_thr * 4) +
+         a16((size_t)T * 8) + (size_t)2 * kIdsCap * 8 + (size_t)kRecCap * 8;
+}
+
+cudaError_t launch_owned(OwnedArgs a, bool fixed, int grid, cudaStream_t st) {
+  auto a16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  a.off_seg = (uint32_t)a16((size_t)(a.L_mask + 1) * a.T * (fixed ? 8 : 4));
+  a.off_thr = a.off_seg + (uint32_t)a16((size_t)a.n_seg * sizeof(LifSeg));
+  a.off_pub = a.off_thr + (uint32_t)a16((size_t)a.n_thr * 4);
+  a.off_ids = a.off_pub + (uint32_t)a16((size_t)a.T * 8);
+  a.off_rec = a.off_ids + (uint32_t)(2 * kIdsCap * 8);
+  const size_t smem = a.off_rec + (size_t)kRecCap * 8;
+  const int npt = a.T <= kOwnedBlock ? 1 : (a.T <= 2 * kOwnedBlock ? 2 : 4);
+  if (a.T > 4 * kOwnedBlock || grid * kMbWords > kPollWords * kOwnedBlock || a.steps > kMaxOwnedSteps)
+    return cudaErrorInvalidValue;
+  void* k = owned_kernel(fixed, npt);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kOwnedBlock);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  void* args[] = {&a};
+  return cudaLaunchKernelExC(&cfg, k, args);
+}
+
+cudaError_t owned_max_blocks_per_sm(bool fixed, uint32_t T, size_t smem, int* out) {
+  const int npt = T <= kOwnedBlock ? 1 : (T <= 2 * kOwnedBlock ? 2 : 4);
+  void* k = owned_kernel(fixed, npt);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, kOwnedBlock, smem);
+}
+
+}  // namespace ngb

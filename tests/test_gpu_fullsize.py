@@ -144,7 +144,7 @@ def test_fullsize_autotuned_loop_pending_inputs_equal_delivered_weights():
     sim.finalize()
     sim.autotune(1000)
     st = sim.stats()
-    assert st["steps"] == 0 and st["mode"] in (0, 1, 2, 3, 4, 5)
+    assert st["steps"] == 0 and st["mode"] in (0, 1, 2, 3, 4, 5, 6)
     sim.simulate(1200)
     st = sim.stats()
     D = st["max_delay_steps"]
@@ -153,4 +153,37 @@ def test_fullsize_autotuned_loop_pending_inputs_equal_delivered_weights():
     for off in range(L):
         got = sim.input(0, off).astype(np.float64)
         assert np.all(np.abs(got - expect[off]) <= 1e-5 * absw[off] + 1e-4), (off, st["mode"])
+    sim.close()
+
+
+def test_fullsize_target_owned_pending_inputs_equal_delivered_weights():
+    """The target-owned persistent kernel at full size (152 tiles of 508
+    neurons, their 64-slot rings in shared memory, one 10,000-step launch
+    split here into launches of 1,200 and 7 steps): every pending slot
+    written back to the ring equals the FP64 sums of the recorded spikes'
+    synapses."""
+    import os
+    from paper_2007_14236_gb300 import ngb
+    spec = W.microcircuit(scale=1.0, seed=1)
+    old = os.environ.get("NGB_MODE")
+    os.environ["NGB_MODE"] = "target_owned"
+    try:
+        sim = ngb.from_spec(spec, steps_per_graph=100, drain_steps=10_000, record_capacity=4_000_000,
+                            delivery="ring")
+        sim.finalize()
+    finally:
+        if old is None:
+            os.environ.pop("NGB_MODE", None)
+        else:
+            os.environ["NGB_MODE"] = old
+    st = sim.stats()
+    assert st["mode"] == 6 and st["launch_grid"] > 0
+    sim.simulate(1200)
+    sim.simulate(7)
+    st = sim.stats()
+    L = st["max_delay_steps"] + 1
+    expect, absw = _expected_inputs(sim, L)
+    for off in range(L):
+        got = sim.input(0, off).astype(np.float64)
+        assert np.all(np.abs(got - expect[off]) <= 1e-5 * absw[off] + 1e-4), off
     sim.close()

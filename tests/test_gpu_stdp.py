@@ -132,7 +132,7 @@ def test_stdp_restrictions(ngb):
     spec_bf.weight_dtype = "bf16"
     with pytest.raises(RuntimeError, match="INVALID_ARG"):
         ngb.from_spec(spec_bf)
-    for mode in ("persistent", "fused", "pipelined"):
+    for mode in ("persistent", "fused", "pipelined", "target_owned"):
         with _env(NGB_MODE=mode):
             sim = ngb.from_spec(spec, deterministic=True)
             sim.finalize()
