@@ -60,7 +60,8 @@ namespace {
 
 constexpr int kOwnedBlock = 512;
 constexpr int kMbWords = 8;        // mailbox words per block and step: 7 entries + count
-constexpr int kPollWords = 4;      // mailbox words polled per thread: G * 8 <= 4 * 512
+constexpr int kPollPairs = 2;      // 16-byte mailbox loads per thread: G * 8 <= 2 * 2 * 512 words
+constexpr int kPollWords = 2 * kPollPairs;
 constexpr int kIdsCap = 2048;      // spike entries gathered per step in shared memory
 constexpr int kRecCap = 4096;      // spike-record entries buffered per block (>= 2 x the largest tile)
 constexpr uint32_t kFiller = 0xFFFFFFFFu;
@@ -72,6 +73,13 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
+}
+
+// Two adjacent mailbox words in one 16-byte load (each word is validated by
+// its own stamp, so the pair need not be read atomically).
+__device__ __forceinline__ void ld_relaxed_v2u64(const unsigned long long* p, unsigned long long& a,
+                                                 unsigned long long& b) {
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
 
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
@@ -304,21 +312,26 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
     const uint64_t stamp = stamp_of(r);
     const unsigned long long* mbp = mb_of(r);
     unsigned long long v[kPollWords];
-    // (addresses clamped rather than the loads predicated: one round of loads)
+    // 16-byte loads of word pairs (addresses clamped rather than the loads
+    // predicated, so that nothing consumes the values before they are checked)
+    const int npairs = nwords / 2;
 #pragma unroll
-    for (int i = 0; i < kPollWords; ++i) v[i] = ld_relaxed_u64(mbp + min(tid + i * kOwnedBlock, nwords - 1));
+    for (int i = 0; i < kPollPairs; ++i)
+      ld_relaxed_v2u64(mbp + 2 * min(tid + i * kOwnedBlock, npairs - 1), v[2 * i], v[2 * i + 1]);
     unsigned pend = 0;
 #pragma unroll
-    for (int i = 0; i < kPollWords; ++i)
-      if (tid + i * kOwnedBlock < nwords && (v[i] & ~kPayloadMask) != stamp) pend |= 1u << i;
+    for (int i = 0; i < kPollPairs; ++i)
+      if (tid + i * kOwnedBlock < npairs &&
+          ((v[2 * i] & ~kPayloadMask) != stamp || (v[2 * i + 1] & ~kPayloadMask) != stamp))
+        pend |= 1u << i;
     bool gave_up = false;
     unsigned long long spins = 0;
     while (pend) {
 #pragma unroll
-      for (int i = 0; i < kPollWords; ++i)
+      for (int i = 0; i < kPollPairs; ++i)
         if (pend & (1u << i)) {
-          v[i] = ld_relaxed_u64(mbp + tid + i * kOwnedBlock);
-          if ((v[i] & ~kPayloadMask) == stamp) pend &= ~(1u << i);
+          ld_relaxed_v2u64(mbp + 2 * (tid + i * kOwnedBlock), v[2 * i], v[2 * i + 1]);
+          if ((v[2 * i] & ~kPayloadMask) == stamp && (v[2 * i + 1] & ~kPayloadMask) == stamp) pend &= ~(1u << i);
         }
       if (!pend) break;
       ++spins;
@@ -337,7 +350,7 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
     if (!gave_up) {
 #pragma unroll
       for (int i = 0; i < kPollWords; ++i) {
-        const int w = tid + i * kOwnedBlock;
+        const int w = 2 * (tid + (i >> 1) * kOwnedBlock) + (i & 1);
         if (w >= nwords) continue;
         const uint64_t pl = v[i] & kPayloadMask;
         if ((w & (kMbWords - 1)) == kMbWords - 1) {
