@@ -60,8 +60,7 @@ namespace {
 
 constexpr int kOwnedBlock = 512;
 constexpr int kMbWords = 8;        // mailbox words per block and step: 7 entries + count
-constexpr int kPollPairs = 2;      // 16-byte mailbox loads per thread: G * 8 <= 2 * 2 * 512 words
-constexpr int kPollWords = 2 * kPollPairs;
+constexpr int kPollWords = 4;      // mailbox words polled per thread, in one 32-byte load: G * 8 <= 4 * 512
 constexpr int kIdsCap = 2048;      // spike entries gathered per step in shared memory
 constexpr int kRecCap = 4096;      // spike-record entries buffered per block (>= 2 x the largest tile)
 constexpr uint32_t kFiller = 0xFFFFFFFFu;
@@ -75,11 +74,13 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
   return v;
 }
 
-// Two adjacent mailbox words in one 16-byte load (each word is validated by
-// its own stamp, so the pair need not be read atomically).
-__device__ __forceinline__ void ld_relaxed_v2u64(const unsigned long long* p, unsigned long long& a,
-                                                 unsigned long long& b) {
-  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+// Four adjacent mailbox words in one 32-byte load (each word is validated by
+// its own stamp, so the four need not be read atomically).
+__device__ __forceinline__ void ld_relaxed_v4u64(const unsigned long long* p, unsigned long long v[4]) {
+  asm volatile("ld.relaxed.gpu.global.v4.u64 {%0, %1, %2, %3}, [%4];"
+               : "=l"(v[0]), "=l"(v[1]), "=l"(v[2]), "=l"(v[3])
+               : "l"(p)
+               : "memory");
 }
 
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
@@ -312,27 +313,21 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
     const uint64_t stamp = stamp_of(r);
     const unsigned long long* mbp = mb_of(r);
     unsigned long long v[kPollWords];
-    // 16-byte loads of word pairs (addresses clamped rather than the loads
-    // predicated, so that nothing consumes the values before they are checked)
-    const int npairs = nwords / 2;
-#pragma unroll
-    for (int i = 0; i < kPollPairs; ++i)
-      ld_relaxed_v2u64(mbp + 2 * min(tid + i * kOwnedBlock, npairs - 1), v[2 * i], v[2 * i + 1]);
-    unsigned pend = 0;
-#pragma unroll
-    for (int i = 0; i < kPollPairs; ++i)
-      if (tid + i * kOwnedBlock < npairs &&
-          ((v[2 * i] & ~kPayloadMask) != stamp || (v[2 * i + 1] & ~kPayloadMask) != stamp))
-        pend |= 1u << i;
+    // one 32-byte load of four words per thread (the address clamped rather
+    // than the load predicated, so that nothing consumes the values before
+    // they are checked)
+    const int nquads = nwords / 4;
+    ld_relaxed_v4u64(mbp + 4 * min(tid, nquads - 1), v);
+    auto stale = [&]() {
+      return (v[0] & ~kPayloadMask) != stamp || (v[1] & ~kPayloadMask) != stamp ||
+             (v[2] & ~kPayloadMask) != stamp || (v[3] & ~kPayloadMask) != stamp;
+    };
+    bool pend = tid < nquads && stale();
     bool gave_up = false;
     unsigned long long spins = 0;
     while (pend) {
-#pragma unroll
-      for (int i = 0; i < kPollPairs; ++i)
-        if (pend & (1u << i)) {
-          ld_relaxed_v2u64(mbp + 2 * (tid + i * kOwnedBlock), v[2 * i], v[2 * i + 1]);
-          if ((v[2 * i] & ~kPayloadMask) == stamp && (v[2 * i + 1] & ~kPayloadMask) == stamp) pend &= ~(1u << i);
-        }
+      ld_relaxed_v4u64(mbp + 4 * tid, v);
+      pend = stale();
       if (!pend) break;
       ++spins;
       if ((spins & 63u) == 0 && (ld_relaxed_u32(a.abort) != 0u || s_abort)) {
@@ -350,7 +345,7 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
     if (!gave_up) {
 #pragma unroll
       for (int i = 0; i < kPollWords; ++i) {
-        const int w = 2 * (tid + (i >> 1) * kOwnedBlock) + (i & 1);
+        const int w = 4 * tid + i;
         if (w >= nwords) continue;
         const uint64_t pl = v[i] & kPayloadMask;
         if ((w & (kMbWords - 1)) == kMbWords - 1) {
