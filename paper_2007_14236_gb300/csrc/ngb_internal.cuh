@@ -565,7 +565,7 @@ struct OwnedArgs {
   const uint2* items;    // [G][S]
   const uint64_t* pub;   // [N]
   const uint64_t* src_syn;
-  unsigned long long* mb;   // [4][G][8] mailboxes, by step mod 4
+  unsigned long long* mb;   // [4][G][4] mailboxes, by step mod 4
   unsigned long long* ovf;  // [4][G][T] overflow entries
   SpikeBuf sb;
   int64_t* clk;

@@ -18,29 +18,36 @@
 // needs no per-tile index lookup: the firing block publishes (off_s, C_s),
 // and every block reads its own C_s items in one round of loads.
 //
-// Step t, in every block:
-//   update    slot t of the tile's ring read and cleared, Poisson drive
-//             (counts drawn while the previous step's mailboxes were
-//             awaited), exact LIF step (Eqs. 1-2), threshold; new spikes of
-//             sources with synapses collected in shared memory
-//   publish   mailbox of the block for step t (buffer t mod 2): 8 stamped
-//             words, 7 spike entries (off_s, C_s) and the count; further
-//             entries in the block's overflow area, same format.  The
-//             spike record is buffered in shared memory and flushed to the
-//             device record (one atomic per flush) when it could overflow and
-//             at the end of the launch; the event count is added at the end
-//   exchange  every mailbox word of step t polled until stamped (bounded
-//             spin); the entries gathered in shared memory
-//   deliver   warps take the entries and add each item into the shared ring
-//             at slot (t + delay) & (L - 1): FP32 atomics, or int64 fixed
-//             point (units of 2^-32, as the other loops) in deterministic mode
-// A block publishes step t + 2 into the buffer of step t only after reading
-// every block's step t + 1 mailbox, which each block publishes only after
-// reading all of step t: a buffer is never overwritten while it is read.
-// The mailboxes and overflow areas are reset before each launch, and a launch
-// runs at most kMaxOwnedSteps steps, so a stale word never carries the
-// current stamp.  Every wait is bounded: a block that gives up sets the
-// timeout flag and the abort word, and the others stop at their next poll.
+// The threshold test of a step depends only on the state after the previous
+// step (V is propagated with the current of the previous grid point; the
+// step's input enters the current), so the spikes of step t + 1 are known
+// as soon as step t is updated.  Step t, in every block:
+//   items     the first synapse chunks of step t's spike entries (gathered
+//             during step t - 1) are loaded; the loads are in flight during
+//             the next three phases
+//   update    slot t of the tile's ring read and cleared, Poisson drive,
+//             exact LIF step (Eqs. 1-2) with the threshold decided a step
+//             ago; spike record buffered in shared memory (flushed to the
+//             device record with one atomic when it could overflow, and at
+//             the end of the launch); event count kept per thread
+//   predict   threshold test of step t + 1; entries (off_s, C_s) of the
+//             sources that will fire, collected in shared memory
+//   publish   the block's mailbox for step t + 1 (buffer (t + 1) mod 4):
+//             4 stamped words, 3 entries and the count, further entries in
+//             the block's overflow area; then the Poisson counts of t + 1
+//   deliver   the items of step t's spikes added into the shared ring at
+//             slot (t + delay) & (L - 1): FP32 atomics, or int64 fixed point
+//             (units of 2^-32, as the other loops) in deterministic mode
+//   gather    every block's mailbox for step t + 1 polled (one 32-byte load
+//             per block; bounded spin) and its entries kept for step t + 1
+// A block writes the buffer of step t + 4 only after it has gathered step
+// t + 3, which needs every block's step t + 3 mailbox, which each block
+// writes only after gathering step t + 2 and so after reading step t: a
+// buffer is never overwritten while it is read.  The mailboxes and overflow
+// areas are reset before each launch, and a launch runs at most
+// kMaxOwnedSteps steps, so a stale word never carries the current stamp.
+// Every wait is bounded: a block that gives up sets the timeout flag and the
+// abort word, and the others stop at their next poll.
 //
 // The arithmetic of the update (neuron_step.cuh) and the fixed-point
 // conversion are those of the per-step kernels, so deterministic runs are
@@ -59,7 +66,8 @@ namespace ngb {
 namespace {
 
 constexpr int kOwnedBlock = 512;
-constexpr int kMbWords = 8;        // mailbox words per block and step: 7 entries + count
+constexpr int kMbWords = 4;        // mailbox words per block and step (32 bytes): 3 entries + count
+constexpr int kMaxTiles = 256;     // blocks of the launch
 constexpr int kPollWords = 4;      // mailbox words polled per thread, in one 32-byte load: G * 8 <= 4 * 512
 constexpr int kIdsCap = 2048;      // spike entries gathered per step in shared memory
 constexpr int kRecCap = 4096;      // spike-record entries buffered per block (>= 2 x the largest tile)
@@ -178,7 +186,7 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
   uint64_t* s_ids = reinterpret_cast<uint64_t*>(smem + a.off_ids);  // [2][kIdsCap], by step parity
   uint2* s_rec = reinterpret_cast<uint2*>(smem + a.off_rec);        // [kRecCap] {neuron, step - t0}
   __shared__ int s_np[2], s_nid[2], s_novm[2];
-  __shared__ int s_ovm[2][kMbWords * 32];  // mailboxes with overflow (block ids)
+  __shared__ int s_ovm[2][kMaxTiles];  // mailboxes with overflow (block ids)
   __shared__ int s_abort, s_rn;
   __shared__ unsigned long long s_rbase;
 
@@ -360,7 +368,7 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
     __syncthreads();
     if (s_abort) return false;
     if (s_novm[q] > 0) {
-      // blocks with more than 7 spikes: their overflow words, a warp per block
+      // blocks with more than 3 spikes: their overflow words, a warp per block
       for (int k = warp; k < s_novm[q]; k += kWarps) {
         const int m = s_ovm[q][k];
         const uint64_t cnt = ld_relaxed_u64(mbp + (size_t)m * kMbWords + (kMbWords - 1)) & kPayloadMask;
@@ -647,7 +655,8 @@ cudaError_t launch_owned(OwnedArgs a, bool fixed, int grid, cudaStream_t st) {
   a.off_rec = a.off_ids + (uint32_t)(2 * kIdsCap * 8);
   const size_t smem = a.off_rec + (size_t)kRecCap * 8;
   const int npt = a.T <= kOwnedBlock ? 1 : (a.T <= 2 * kOwnedBlock ? 2 : 4);
-  if (a.T > 4 * kOwnedBlock || grid * kMbWords > kPollWords * kOwnedBlock || a.steps > kMaxOwnedSteps)
+  if (a.T > 4 * kOwnedBlock || grid > kMaxTiles || grid * kMbWords > kPollWords * kOwnedBlock ||
+      a.steps > kMaxOwnedSteps)
     return cudaErrorInvalidValue;
   void* k = owned_kernel(fixed, npt);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
