@@ -267,6 +267,32 @@ cudaError_t exclusive_scan_u64(const unsigned long long* in, unsigned long long*
   return cub::DeviceScan::ExclusiveSum(tmp, b, in, out, (int64_t)n, st);
 }
 
+namespace {
+// Spike-record key: step << 26 | neuron (neurons < 2^26, steps < 2^38).
+__global__ void k_record_keys(const uint32_t* __restrict__ ids, const int64_t* __restrict__ steps, uint64_t n,
+                              unsigned long long* keys) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    keys[i] = ((unsigned long long)steps[i] << 26) | ids[i];
+}
+}  // namespace
+
+cudaError_t record_sort_scratch_bytes(uint64_t n, size_t* bytes) {
+  *bytes = 0;
+  return cub::DeviceRadixSort::SortKeys(nullptr, *bytes, (const unsigned long long*)nullptr,
+                                        (unsigned long long*)nullptr, (int64_t)n);
+}
+
+cudaError_t sort_record(const uint32_t* ids, const int64_t* steps, uint64_t n, unsigned long long* keys,
+                        unsigned long long* sorted, void* tmp, size_t tmp_bytes, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = (unsigned)std::min<uint64_t>((n + 255) / 256, 4096);
+  k_record_keys<<<grid, 256, 0, st>>>(ids, steps, n, keys);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  size_t b = tmp_bytes;
+  return cub::DeviceRadixSort::SortKeys(tmp, b, keys, sorted, (int64_t)n, 0, 64, st);
+}
+
 cudaError_t scan_scratch_bytes_u64(uint64_t n, size_t* bytes) {
   *bytes = 0;
   return cub::DeviceScan::ExclusiveSum(nullptr, *bytes, (const unsigned long long*)nullptr,

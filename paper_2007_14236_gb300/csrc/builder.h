@@ -65,6 +65,10 @@ cudaError_t fill_meta(uint64_t n, uint64_t off, uint64_t k_off, uint64_t g_off, 
                       const unsigned long long* grp_scan, const uint64_t* grp_start, const uint16_t* grp_delay,
                       uint4* meta, uint64_t* src_syn, uint32_t* src_grp, uint2* src_age, unsigned long long* items,
                       cudaStream_t st);
+// The spike record (ids, steps; n entries) as sorted keys step << 26 | neuron.
+cudaError_t record_sort_scratch_bytes(uint64_t n, size_t* bytes);
+cudaError_t sort_record(const uint32_t* ids, const int64_t* steps, uint64_t n, unsigned long long* keys,
+                        unsigned long long* sorted, void* tmp, size_t tmp_bytes, cudaStream_t st);
 cudaError_t narrow_u64_to_u32(const unsigned long long* in, uint32_t* out, uint64_t n, cudaStream_t st);
 
 }  // namespace ngb

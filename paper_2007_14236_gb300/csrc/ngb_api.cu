@@ -275,6 +275,13 @@ struct ngb_sim {
   int drain_steps = 1000;
   int64_t t = 0;  // steps done
   int64_t spikes_total = 0;
+  // device-side sort of each drained record (keys step << 26 | neuron) and
+  // its pinned host staging buffer
+  unsigned long long* rec_keys = nullptr;
+  unsigned long long* rec_sorted = nullptr;
+  unsigned char* rec_sort_tmp = nullptr;
+  size_t rec_sort_bytes = 0;
+  unsigned long long* rec_pinned = nullptr;
   std::vector<uint32_t> rec_ids;
   std::vector<int64_t> rec_steps;
   size_t rec_sorted_upto = 0;  // records [0, upto) are sorted by (step, id)
@@ -601,14 +608,24 @@ int drain(ngb_sim* s) {
   CK(cudaStreamSynchronize(s->stream));
   s->spikes_total += (int64_t)cnt;
   if (s->sb.rec_cap > 0 && cnt > 0) {
+    // sorted by (step, neuron) on the device, then appended: every drain
+    // holds later steps than the earlier ones, so the record stays sorted
     const size_t n = (size_t)std::min<unsigned long long>(cnt, (unsigned long long)s->sb.rec_cap);
+    CK(sort_record(s->sb.rec_id, s->sb.rec_step, n, s->rec_keys, s->rec_sorted, s->rec_sort_tmp, s->rec_sort_bytes,
+                   s->stream));
+    CK(cudaMemcpyAsync(s->rec_pinned, s->rec_sorted, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    const bool was_sorted = s->rec_sorted_upto == s->rec_ids.size();
     const size_t old = s->rec_ids.size();
     s->rec_ids.resize(old + n);
     s->rec_steps.resize(old + n);
-    CK(cudaMemcpyAsync(s->rec_ids.data() + old, s->sb.rec_id, n * sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                       s->stream));
-    CK(cudaMemcpyAsync(s->rec_steps.data() + old, s->sb.rec_step, n * sizeof(int64_t), cudaMemcpyDeviceToHost,
-                       s->stream));
+    for (size_t i = 0; i < n; ++i) {
+      const unsigned long long k = s->rec_pinned[i];
+      s->rec_ids[old + i] = (uint32_t)(k & ((1ull << 26) - 1));
+      s->rec_steps[old + i] = (int64_t)(k >> 26);
+    }
+    if (was_sorted) s->rec_sorted_upto = s->rec_ids.size();
   }
   CK(cudaMemsetAsync(s->sb.rec_count, 0, sizeof(unsigned long long), s->stream));
   CK(cudaMemsetAsync(s->sb.err, 0, sizeof(uint32_t), s->stream));
@@ -1381,6 +1398,11 @@ int finalize_impl(ngb_sim* s) {
                                      : std::max<int64_t>(1 << 20, N * (int64_t)s->drain_steps / 100);
     CK(s->dalloc(&s->sb.rec_id, cap));
     CK(s->dalloc(&s->sb.rec_step, cap));
+    CK(s->dalloc(&s->rec_keys, cap));
+    CK(s->dalloc(&s->rec_sorted, cap));
+    CK(record_sort_scratch_bytes((uint64_t)cap, &s->rec_sort_bytes));
+    CK(s->dalloc(&s->rec_sort_tmp, s->rec_sort_bytes));
+    CK(cudaMallocHost((void**)&s->rec_pinned, (size_t)cap * sizeof(unsigned long long)));
   }
   s->sb.rec_cap = cap;
   {
@@ -1735,6 +1757,7 @@ int ngb_destroy(ngb_sim* s) {
   if (s->stream2) cudaStreamDestroy(s->stream2);
   for (void* p : s->allocs) cudaFree(p);
   for (void* p : s->table_allocs) cudaFree(p);
+  if (s->rec_pinned) cudaFreeHost(s->rec_pinned);
   if (s->own_stream) cudaStreamDestroy(s->stream);
   delete s;
   return NGB_OK;
