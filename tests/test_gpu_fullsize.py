@@ -1,5 +1,5 @@
 """Full-size parity: the 77,169-neuron, 298,880,968-synapse microcircuit in the
-launch configuration bench.py times (100-step CUDA graphs, FP32 weights).
+handle configuration bench.py uses (100-step CUDA graphs, 10,000-step drains, FP32 weights).
 
 * Sampled connectivity: the CSR rows of sampled sources equal the oracle's
   rows, which it computes draw by draw without building the network.
@@ -11,8 +11,10 @@ launch configuration bench.py times (100-step CUDA graphs, FP32 weights).
 * The same delivery property for the spike-buffer scheme, whose only input
   slot is the next step's.
 * The same property in the step loop the benchmark times: the handle built and
-  autotuned as bench.py does (the one-kernel pipelined loop on this network),
-  checked on every pending slot after graph replays.
+  autotuned as bench.py does (the target-owned loop on this network),
+  checked on every pending slot.
+* The target-owned loop forced, in launches of 1,200 and 7 steps: every
+  pending slot written back to the ring.
 """
 import numpy as np
 import pytest
