@@ -14,7 +14,8 @@ mailboxes) against the per-step kernels, through the C ABI (needs a GB300).
   per-step kernels within the FP32 summation bound (1e-5 of the summed
   magnitudes), and spike counts agree within 5 % over 3,000 steps.
 * Networks the loop does not take (AdEx populations, the spike-buffer
-  scheme) run the per-step kernels.
+  scheme, serving handles, more than 2,048 neurons per block) run the
+  per-step kernels.
 * A block that never publishes (test hook) makes every mailbox wait give up
   after its poll limit: ngb_simulate returns NGB_ERR_TIMEOUT, and the GPU
   stays usable.
@@ -155,6 +156,18 @@ def test_target_owned_not_taken(ngb):
     assert sb.stats()["mode"] == 0 and sb.stats()["delivery"] == 2
     sb.simulate(20)
     assert sb.stats()["steps"] == 20
+    with _env(NGB_MODE="target_owned"):  # serving handles: instances come and go, no static layout
+        sv = ngb.Simulator(deterministic=True)
+        sv.reserve(5000, 400_000, 5000, 16, 1)
+        a, _ = sv.add_spec_instance(W.balanced_lif(n=3000, indegree=100, seed=1))
+        sv.commit(a)
+        sv.simulate(50)
+    assert sv.stats()["mode"] == 0 and sv.stats()["steps"] == 50
+    big = W.balanced_lif(n=400_000, indegree=10, seed=1)  # more than 2,048 neurons per block
+    bg = _owned(ngb, big, delivery="ring")
+    assert bg.stats()["mode"] == 0
+    bg.simulate(5)
+    assert bg.stats()["steps"] == 5
 
 
 def test_target_owned_mailbox_wait_is_bounded(ngb):
