@@ -6,7 +6,7 @@ mailboxes) against the per-step kernels, through the C ABI (needs a GB300).
   membrane state, synaptic current, inputs of the coming steps and event
   counts, over launches of 1, 2, 97 and 250 steps and a switch to the
   profiled per-step kernels and back; LIF networks with one and several
-  populations, batched instances, BF16 weights, fewer neurons than blocks,
+  populations, batched instances, BF16 and FP16 weights, fewer neurons than blocks,
   no synapses at all, and a network whose first step fires thousands of
   neurons (mailbox overflow areas, more spikes than the shared-memory list
   holds).
@@ -59,6 +59,7 @@ _SPECS = {
     "mc_burst": lambda: W.microcircuit(scale=0.3, seed=9, keep_indegree=False),
     "batched": lambda: W.batched_microcircuits(n_instances=3, scale_lo=0.02, scale_hi=0.04, seed=7),
     "mc_bf16": lambda: W.microcircuit(scale=0.03, seed=8, keep_indegree=False, weight_dtype="bf16"),
+    "mc_fp16": lambda: W.microcircuit(scale=0.03, seed=8, keep_indegree=False, weight_dtype="fp16"),
     "adex": lambda: W.balanced_adex(n=2000, indegree=100, seed=2, weight_dtype="fp32", poisson_weight=4.0,
                                     w_ex=2.0, w_in=4.0),
     "tiny": lambda: W.balanced_lif(n=100, indegree=10, seed=3),  # fewer neurons than blocks
@@ -182,3 +183,31 @@ def test_target_owned_mailbox_wait_is_bounded(ngb):
     ok = _owned(ngb, spec, deterministic=True, delivery="ring")
     ok.simulate(100)
     assert ok.stats()["steps"] == 100 and ok.stats()["mode"] == 6
+
+
+def test_autotune_cache_round_trip(ngb, tmp_path):
+    """NGB_AUTOTUNE_CACHE: the first tuning appends one line per network shape
+    and a second handle of the same shape takes its loop from the file without
+    timing; a line naming the target-owned loop selects it, and the run is
+    bit-identical to the per-step kernels."""
+    spec = W.microcircuit(scale=0.03, seed=3, keep_indegree=False)
+    cache = tmp_path / "tune.txt"
+    with _env(NGB_AUTOTUNE_CACHE=str(cache)):
+        a = ngb.from_spec(spec, deterministic=True, delivery="ring")
+        ga = a.autotune(200)
+        b = ngb.from_spec(spec, deterministic=True, delivery="ring")
+        gb = b.autotune(200)
+    lines = [ln for ln in cache.read_text().splitlines() if ln.strip()]
+    assert len(lines) == 1 and len(lines[0].split()) == 5
+    assert a.stats()["mode"] == b.stats()["mode"] and ga == gb
+    key, _, g, pg, _ = lines[0].split()
+    forced = tmp_path / "forced.txt"
+    forced.write_text("%s 6 %s %s 1\n" % (key, g, pg))
+    with _env(NGB_AUTOTUNE_CACHE=str(forced)):
+        c = ngb.from_spec(spec, deterministic=True, delivery="ring")
+        c.autotune(200)
+    assert c.stats()["mode"] == 6 and c.stats()["steps"] == 0
+    ref = ngb.from_spec(spec, deterministic=True, delivery="ring")
+    c.simulate(400)
+    ref.simulate(400)
+    assert np.array_equal(c.spikes()[0], ref.spikes()[0]) and np.array_equal(c.spikes()[1], ref.spikes()[1])
