@@ -288,7 +288,9 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
   // mailbox buffer and stamp of the spikes of step t0 + r
   auto mb_of = [&](int64_t r) { return a.mb + (size_t)(r & 3) * nwords; };
   auto ovf_of = [&](int64_t r, int m) { return a.ovf + ((size_t)(r & 3) * G + m) * T; };
-  auto stamp_of = [](int64_t r) { return (uint64_t)((r >> 2) % 65535) << kStampShift; };
+  // (a launch runs fewer than 4 x 65535 steps, so r >> 2 < 65535: never the
+  // all-ones stamp of a reset word)
+  auto stamp_of = [](int64_t r) { return (uint64_t)((uint32_t)r >> 2) << kStampShift; };
   // The threshold test of a step depends only on the state after the previous
   // step (lif_propagate), so the spikes of step t + 1 are known once step t is
   // updated: they are published then, and delivered during the next step.
