@@ -48,7 +48,7 @@ NCU_TRAFFIC = {("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "gra
                ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "pipelined_one_kernel", "k_step_pipe"):
                    6284672,
                # one launch = one bench step (10,000 simulation steps); mean of four steady-state launches
-               ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "target_owned", "k_owned"): 16019236480}
+               ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "target_owned", "k_owned"): 16018345984}
 SIM_STEPS_PER_BENCH_STEP = 10_000  # 1 s of biological time at dt = 0.1 ms
 
 
