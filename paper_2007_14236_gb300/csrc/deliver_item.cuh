@@ -336,6 +336,7 @@ __device__ __forceinline__ void deliver_due_item(const uint4 it, const Csr& csr,
   for (uint64_t c = b & ~3ull; c < e; c += 2 * kChunk) {
     uint4 tv[2];
     float wv[2][4];
+    uint4 pw[2][2];  // plastic synapses: the four weight-and-arrival words of the lane's synapses
     bool any[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
@@ -343,9 +344,14 @@ __device__ __forceinline__ void deliver_due_item(const uint4 it, const Csr& csr,
       any[u] = j0 < e && j0 + 4 > b;
       tv[u] = make_uint4(0, 0, 0, 0);
       wv[u][0] = wv[u][1] = wv[u][2] = wv[u][3] = 0.f;
+      pw[u][0] = pw[u][1] = make_uint4(0, 0, 0, 0);
       if (any[u]) {
         tv[u] = __ldg(reinterpret_cast<const uint4*>(csr.tgt + j0));
         W4<WT>::load(csr.w, j0, wv[u]);
+        if (kPlastic) {
+          pw[u][0] = *reinterpret_cast<const uint4*>(sa->wa + j0);
+          pw[u][1] = *reinterpret_cast<const uint4*>(sa->wa + j0 + 2);
+        }
       }
     }
 #pragma unroll
@@ -361,11 +367,12 @@ __device__ __forceinline__ void deliver_due_item(const uint4 it, const Csr& csr,
         if (kPlastic) {
           const uint32_t cls = (twq >> kPlastShift) & kPlastMask;
           if (cls) {
+            const uint4 pp = pw[u][q >> 1];
+            wq = __uint_as_float((q & 1) ? pp.z : pp.x);  // the current plastic weight
             const int32_t arrive = (int32_t)(t + 1);
             const int32_t post = sb->last_spike[twq & kTgtMask];
             if (post >= 0) wq = stdp_depress(sa->rules[cls - 1], wq, (int64_t)arrive - (int64_t)post);
-            sa->w[j] = wq;
-            sa->arrival[j] = arrive;
+            sa->wa[j] = make_uint2(__float_as_uint(wq), (uint32_t)arrive);
           }
         }
         const uint64_t idx = (uint64_t)(twq >> kRcptShift) * (uint64_t)ring.N + (twq & kTgtMask);

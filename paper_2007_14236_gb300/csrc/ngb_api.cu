@@ -290,7 +290,7 @@ struct ngb_sim {
   // the latest arrival step of every synapse and the reverse index
   std::vector<ngb_stdp_params> stdp_params;
   StdpRule* d_rules = nullptr;
-  int32_t* arrival = nullptr;
+  uint2* wa = nullptr;  // per synapse {FP32 weight bits, latest arrival step}
   uint64_t* in_ptr = nullptr;
   uint64_t* in_syn = nullptr;
   uint64_t n_plastic = 0;
@@ -493,7 +493,7 @@ cudaError_t launch_aeif(ngb_sim* s, int64_t step_off = 0) {
   return e;
 }
 
-StdpArgs stdp_of(const ngb_sim* s) { return StdpArgs{s->d_rules, (float*)s->w, s->arrival, s->in_syn}; }
+StdpArgs stdp_of(const ngb_sim* s) { return StdpArgs{s->d_rules, s->wa, s->in_syn}; }
 
 cudaError_t launch_del(ngb_sim* s, int64_t step_off = 0, cudaStream_t st = nullptr) {
   const StdpArgs sa = stdp_of(s);
@@ -1290,8 +1290,10 @@ int setup_stdp(ngb_sim* s) {
   }
   CK(s->dalloc(&s->d_rules, rules.size()));
   CK(cudaMemcpy(s->d_rules, rules.data(), rules.size() * sizeof(StdpRule), cudaMemcpyHostToDevice));
-  CK(s->dalloc(&s->arrival, s->K_cap + 1));
-  CK(cudaMemsetAsync(s->arrival, 0xFF, (s->K_cap + 1) * sizeof(int32_t), st));
+  // (+4: the delivery reads the words of 4 consecutive synapses at a time)
+  CK(s->dalloc(&s->wa, s->K_cap + 4));
+  CK(cudaMemsetAsync(s->wa, 0, (s->K_cap + 4) * sizeof(uint2), st));
+  CK(init_stdp_words((const float*)s->w, s->K_cap, s->wa, st));
   CK(s->dalloc(&s->sb.last_spike, N));
   CK(cudaMemsetAsync(s->sb.last_spike, 0xFF, N * sizeof(int32_t), st));
   CK(s->dalloc(&s->sb.post[0], N));
@@ -1671,8 +1673,7 @@ int snapshot_take(ngb_sim* s, Snapshot& sn) {
   }
   if (s->ext) sn.parts.push_back({s->ext, 4 * N * 4});
   if (s->d_rules) {  // plastic weights, arrivals and latest spikes change while trial steps run
-    sn.parts.push_back({s->w, s->K_cap * 4});
-    sn.parts.push_back({s->arrival, s->K_cap * 4});
+    sn.parts.push_back({s->wa, s->K_cap * 8});
     sn.parts.push_back({s->sb.last_spike, N * 4});
   }
   for (auto& p : sn.parts) {
@@ -2391,8 +2392,11 @@ int ngb_get_synapses(ngb_sim* s, int64_t first, int64_t n, uint32_t* tgt, uint8_
   float* d_w = reinterpret_cast<float*>(tmp + (size_t)n * 4);
   uint16_t* d_d = reinterpret_cast<uint16_t*>(tmp + (size_t)n * 8);
   uint8_t* d_r = tmp + (size_t)n * 10;
-  cudaError_t e = expand_synapses((uint64_t)first, (uint64_t)n, s->tgt, s->w, s->cfg.weight_dtype, s->grp_start,
-                                  s->G, s->grp_delay, d_t, d_r, d_w, d_d, s->stream);
+  cudaError_t e = cudaSuccess;
+  if (s->wa) e = sync_stdp_weights(s->wa, s->tgt, (uint64_t)first, (uint64_t)n, (float*)s->w, s->stream);
+  if (e == cudaSuccess)
+    e = expand_synapses((uint64_t)first, (uint64_t)n, s->tgt, s->w, s->cfg.weight_dtype, s->grp_start, s->G,
+                        s->grp_delay, d_t, d_r, d_w, d_d, s->stream);
   if (e == cudaSuccess && tgt) e = cudaMemcpyAsync(tgt, d_t, n * 4, cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess && weight) e = cudaMemcpyAsync(weight, d_w, n * 4, cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess && delay) e = cudaMemcpyAsync(delay, d_d, n * 2, cudaMemcpyDeviceToHost, s->stream);

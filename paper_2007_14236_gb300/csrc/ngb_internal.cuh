@@ -158,13 +158,15 @@ struct StdpRule {
   const float* k_minus;
 };
 
-// Plastic synapses: the rules, the mutable FP32 weights (the CSR's), the
-// latest arrival step of every synapse (-1: none) and the incoming plastic
-// synapses of every neuron (rule << 40 | synapse index).
+// Plastic synapses: the rules, per synapse its mutable FP32 weight and its
+// latest arrival step (-1: none) side by side in one 8-byte word {weight
+// bits, arrival} (a potentiation then touches one random sector, not two; the
+// CSR's FP32 weight of a plastic synapse is refreshed from it only for
+// introspection), and the incoming plastic synapses of every neuron
+// (rule << 40 | synapse index).
 struct StdpArgs {
   const StdpRule* rules;
-  float* w;
-  int32_t* arrival;
+  uint2* wa;
   const uint64_t* in_syn;
 };
 
@@ -687,6 +689,12 @@ cudaError_t launch_stdp_post(SpikeBuf sb, StdpArgs a, const int64_t* clk, int gr
 // Reverse index of the plastic synapses of a built CSR (N targets, K synapse
 // words): in_ptr[N+1] (device, caller-owned) and a new device array of
 // rule << 40 | synapse index (caller frees), grouped by target.
+// The weight-and-arrival words of a CSR's K synapses: {weights[j], -1}.
+cudaError_t init_stdp_words(const float* w, uint64_t K, uint2* wa, cudaStream_t st);
+// The CSR weights of the plastic synapses among [first, first + n) from
+// their weight-and-arrival words.
+cudaError_t sync_stdp_weights(const uint2* wa, const uint32_t* tgt, uint64_t first, uint64_t n, float* w,
+                              cudaStream_t st);
 cudaError_t build_stdp_index(const uint32_t* tgt, uint64_t K, int64_t N, uint64_t* in_ptr, uint64_t** in_syn_out,
                              uint64_t* n_plastic_out, cudaStream_t st);
 // Spike-buffer scheme, serving handles: mark the pending entries of sources

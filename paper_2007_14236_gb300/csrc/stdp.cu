@@ -51,18 +51,50 @@ __global__ void __launch_bounds__(256) k_stdp_post(SpikeBuf sb, StdpArgs a, cons
       const uint64_t w0 = a.in_syn[k];
       const uint64_t w1 = two ? a.in_syn[k + stride] : 0ull;
       const uint64_t j0 = w0 & kMask, j1 = w1 & kMask;
-      const int32_t r0 = a.arrival[j0];
-      const int32_t r1 = two ? a.arrival[j1] : -1;
-      const float x0 = a.w[j0];
-      const float x1 = two ? a.w[j1] : 0.f;
-      if (r0 >= 0) a.w[j0] = stdp_potentiate(a.rules[w0 >> kStdpRuleShift], x0, (int64_t)t - (int64_t)r0);
-      if (r1 >= 0) a.w[j1] = stdp_potentiate(a.rules[w1 >> kStdpRuleShift], x1, (int64_t)t - (int64_t)r1);
+      const uint2 p0 = a.wa[j0];
+      const uint2 p1 = two ? a.wa[j1] : make_uint2(0u, 0xFFFFFFFFu);
+      const int32_t r0 = (int32_t)p0.y, r1 = (int32_t)p1.y;
+      uint32_t* const w32 = reinterpret_cast<uint32_t*>(a.wa);
+      if (r0 >= 0)
+        w32[2 * j0] = __float_as_uint(
+            stdp_potentiate(a.rules[w0 >> kStdpRuleShift], __uint_as_float(p0.x), (int64_t)t - (int64_t)r0));
+      if (r1 >= 0)
+        w32[2 * j1] = __float_as_uint(
+            stdp_potentiate(a.rules[w1 >> kStdpRuleShift], __uint_as_float(p1.x), (int64_t)t - (int64_t)r1));
     }
   }
 }
 
 cudaError_t launch_stdp_post(SpikeBuf sb, StdpArgs a, const int64_t* clk, int grid, bool pdl, cudaStream_t st) {
   return launch_k(k_stdp_post, dim3((unsigned)grid), dim3(256), pdl, st, sb, a, clk);
+}
+
+namespace {
+__global__ void k_init_stdp_words(const float* __restrict__ w, uint64_t K, uint2* wa) {
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < K; j += (uint64_t)gridDim.x * blockDim.x)
+    wa[j] = make_uint2(__float_as_uint(w[j]), 0xFFFFFFFFu);
+}
+
+__global__ void k_sync_stdp_weights(const uint2* __restrict__ wa, const uint32_t* __restrict__ tgt, uint64_t first,
+                                    uint64_t n, float* w) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t j = first + i;
+    if ((tgt[j] >> kPlastShift) & kPlastMask) w[j] = __uint_as_float(wa[j].x);
+  }
+}
+}  // namespace
+
+cudaError_t init_stdp_words(const float* w, uint64_t K, uint2* wa, cudaStream_t st) {
+  if (K == 0) return cudaSuccess;
+  k_init_stdp_words<<<1024, 256, 0, st>>>(w, K, wa);
+  return cudaGetLastError();
+}
+
+cudaError_t sync_stdp_weights(const uint2* wa, const uint32_t* tgt, uint64_t first, uint64_t n, float* w,
+                              cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_sync_stdp_weights<<<1024, 256, 0, st>>>(wa, tgt, first, n, w);
+  return cudaGetLastError();
 }
 
 // Reverse index of the plastic synapses: count per target, scan, fill.
