@@ -4,11 +4,18 @@ and synaptic events/s), printed as one JSON line.
 A bench step is one second of biological time (10,000 simulation steps of
 dt = 0.1 ms) of the 8-population microcircuit (77,169 LIF neurons,
 298,880,968 synapses, Poisson background), run through the C ABI
-(ngb_simulate): per simulation step the fused LIF update (Poisson drive,
-exact integration, threshold/reset, spike compaction) and the spike delivery
-into the ring buffer, replayed from CUDA graphs.  The network is built on the
+(ngb_simulate): per simulation step the LIF update (Poisson drive, exact
+integration, threshold/reset, spike compaction) and the spike delivery into
+the targets' input ring, in the step loop the autotuner picks (the
+target-owned persistent kernel on this network).  The network is built on the
 device before the timed region.  The CSR (2.4 GB) is larger than L2 and is
 streamed per spike; the state and ring (~21 MB) stay resident by design.
+
+The same line carries, under "variants", the other configurations measured
+once per run: BF16 weights, 64 batched microcircuit instances against each
+instance alone (both autotuned), the served request stream (60 s of Poisson
+arrivals) with p50/p99 latency against each request alone, and the
+1e6-neuron AdEx network's real-time factor.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -37,7 +44,7 @@ METRIC = "real-time factor & synaptic events/s; batched/served vs plain at state
 UNIT = "synaptic events/s"
 DELIVERY = {1: "ring", 2: "spike_buffer"}
 LOOPS = {0: "graph", 1: "persistent", 2: "fused", 3: "pipelined", 4: "persistent_pipelined",
-         5: "pipelined_one_kernel", 6: "target_owned"}
+         5: "pipelined_one_kernel", 6: "target_owned", 7: "graph_tiled"}
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean of two launches) from one ncu
 # capture of the full-size microcircuit with FP32 weights in this configuration (delivery scheme, step loop);
 # a kernel or configuration without a capture reports null
@@ -66,10 +73,12 @@ def _args():
                     help="oracle simulation steps timed for the CPU baseline")
     ap.add_argument("--profile-steps", type=int, default=2000)
     ap.add_argument("--no-variant", action="store_true", help="skip the BF16-weight variant")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the batched, served and AdEx measurements of the default line")
     ap.add_argument("--delivery", choices=["auto", "ring", "spike_buffer"], default="auto",
                     help="spike delivery scheme (auto: chosen at finalisation, and by the autotuner at step 0)")
     ap.add_argument("--mode", choices=["auto", "graph", "persistent", "fused", "pipelined", "persistent_pipelined",
-                                       "pipelined_one_kernel", "target_owned"],
+                                       "pipelined_one_kernel", "target_owned", "tiled"],
                     default="auto",
                     help="step loop: autotuned (default), per-step kernels in CUDA graphs, the persistent kernel, "
                          "the fused update + delivery kernels, the pipelined loop (delivery beside the next "
@@ -258,34 +267,37 @@ def run_reference(a):
     return 0
 
 
-def run_batched(a):
+def batched_variant(n_instances: int, sim_steps: int, weights: str = "fp32", delivery: str = "auto",
+                    mode: str = "auto", plain_sample: int = 8):
     """Config 3: independent microcircuit instances of random scale advanced in
-    the same kernels, against the plain path (each instance alone)."""
+    the same kernels, against the plain path (a sample of the instances, each
+    alone in its own handle).  Both sides are autotuned before timing (the
+    tuning is not timed) and run the same simulation steps after a 1,000-step
+    warm-up; events/s of each."""
     import numpy as np
     from paper_2007_14236_gb300 import ngb, workloads as W
-    spec = W.batched_microcircuits(n_instances=a.instances, weight_dtype=a.weights)
+    spec = W.batched_microcircuits(n_instances=n_instances, weight_dtype=weights)
     t0 = time.perf_counter()
-    sim = ngb.from_spec(spec, drain_steps=a.sim_steps, record_capacity=16_000_000, delivery=a.delivery)
+    sim = ngb.from_spec(spec, drain_steps=sim_steps, record_capacity=16_000_000, delivery=delivery)
     sim.finalize()
     build_s = time.perf_counter() - t0
-    if a.mode == "auto":
+    if mode == "auto":
         sim.autotune(500)
     st = sim.stats()
     sim.simulate(1000)
     e0 = sim.stats()["events"]
     t1 = time.perf_counter()
-    for _ in range(a.steps):
-        sim.simulate(a.sim_steps)
+    sim.simulate(sim_steps)
     wall = time.perf_counter() - t1
     ev = sim.stats()["events"] - e0
     batched = ev / wall
-    mode = LOOPS[sim.stats()["mode"]]
+    mode_used = LOOPS[sim.stats()["mode"]]
     sim_delivery = sim.stats()["delivery"]
     # per-kernel CUDA-event times of the per-step kernels on the batch
     ep0 = sim.stats()["events"]
     kms, nl = sim.simulate_profiled(300)
     evl = (sim.stats()["events"] - ep0) / max(1, nl[2])
-    wbytes = 4 if a.weights == "fp32" else 2
+    wbytes = 4 if weights == "fp32" else 2
     peak, _ = _peaks()
     us_d = 1e3 * kms[2] / max(1, nl[2])
     us_u = 1e3 * kms[0] / max(1, nl[0])
@@ -295,80 +307,95 @@ def run_batched(a):
             "k_update_lif": {"us_per_launch": us_u, "achieved_gbs": st["num_neurons"] * 32 / (us_u * 1e-6) / 1e9,
                              "frac_of_measured_hbm": st["num_neurons"] * 32 / (us_u * 1e-6) / 1e9 / peak}}
     sim.close()
-    # plain path: a sample of instances, each alone
+    # plain path: a sample of instances, each alone, autotuned like the batch
     rng = np.random.default_rng(0)
-    sample = sorted(rng.choice(a.instances, size=min(8, a.instances), replace=False).tolist())
+    sample = sorted(rng.choice(n_instances, size=min(plain_sample, n_instances), replace=False).tolist())
     pw, pe = 0.0, 0
+    plain_loops = []
     for i in sample:
-        one = ngb.from_spec(W.instance_spec(spec, i), drain_steps=a.sim_steps)  # the library's default choices
+        one = ngb.from_spec(W.instance_spec(spec, i), drain_steps=sim_steps, delivery=delivery)
         one.finalize()
+        if mode == "auto":
+            one.autotune(500)
+        plain_loops.append(LOOPS[one.stats()["mode"]])
         one.simulate(1000)
         e1 = one.stats()["events"]
         t2 = time.perf_counter()
-        for _ in range(a.steps):
-            one.simulate(a.sim_steps)
+        one.simulate(sim_steps)
         pw += time.perf_counter() - t2
         pe += one.stats()["events"] - e1
         one.close()
     plain = pe / pw
-    print(json.dumps({"workload": "batched_microcircuits", "instances": a.instances, "neurons": st["num_neurons"],
-                      "synapses": st["num_synapses"], "build_s": build_s, "step_loop": mode,
-                      "delivery": DELIVERY[sim_delivery],
-                      "batched_events_per_s": batched, "plain_events_per_s": plain, "batched_vs_plain": batched / plain,
-                      "bio_s": a.steps * a.sim_steps * 1e-4, "plain_sample": sample, "kernels": kern}), flush=True)
+    return {"workload": "batched_microcircuits", "instances": n_instances, "neurons": st["num_neurons"],
+            "synapses": st["num_synapses"], "build_s": build_s, "step_loop": mode_used,
+            "delivery": DELIVERY[sim_delivery], "bio_s": sim_steps * 1e-4,
+            "batched_events_per_s": batched, "plain_events_per_s": plain, "batched_vs_plain": batched / plain,
+            "plain_sample": sample, "plain_step_loops": plain_loops, "kernels": kern}
+
+
+def run_batched(a):
+    print(json.dumps(batched_variant(a.instances, a.sim_steps, a.weights, a.delivery, a.mode)), flush=True)
     return 0
 
 
-def run_adex(a):
-    """Config 2: 1e6 AdEx neurons, in-degree 1000, BF16 weights."""
+def adex_variant(n: int, sim_steps: int, steps: int, ctl32: bool = False, delivery: str = "auto",
+                 mode: str = "auto", cpu: bool = True):
+    """Config 2: n AdEx neurons (exponential conductances), in-degree 1000,
+    BF16 weights, adaptive RK45 with FP64 step-size control (FP32 with
+    ctl32): real-time factor over `steps` x `sim_steps` simulation steps after
+    a 1,000-step warm-up, and the oracle's time on a bounded sample."""
     from paper_2007_14236_gb300 import ngb, workloads as W
-    spec = W.balanced_adex(n=a.adex_n, indegree=1000, seed=1, weight_dtype="bf16")
+    spec = W.balanced_adex(n=n, indegree=1000, seed=1, weight_dtype="bf16")
     for p in spec.pops:
-        p.params.rk_control_fp32 = a.adex_ctl32
+        p.params.rk_control_fp32 = ctl32
     t0 = time.perf_counter()
-    sim = ngb.from_spec(spec, drain_steps=a.sim_steps, delivery=a.delivery)
+    sim = ngb.from_spec(spec, drain_steps=sim_steps, delivery=delivery)
     sim.finalize()
     build_s = time.perf_counter() - t0
-    if a.mode == "auto":
+    if mode == "auto":
         sim.autotune(200)
     sim.simulate(1000)
     s0 = sim.stats()
     t1 = time.perf_counter()
-    for _ in range(a.steps):
-        sim.simulate(a.sim_steps)
+    for _ in range(steps):
+        sim.simulate(sim_steps)
     wall = time.perf_counter() - t1
     s1 = sim.stats()
-    bio = a.steps * a.sim_steps * 1e-4
+    bio = steps * sim_steps * 1e-4
     ms, nl = sim.simulate_profiled(200)
     sim.close()
-    cpu = None
-    if not a.no_cpu_baseline:
+    out = {"workload": "balanced_adex_%d" % n, "neurons": s1["num_neurons"], "synapses": s1["num_synapses"],
+           "build_s": build_s, "real_time_factor": wall / bio, "bio_s": bio,
+           "spikes": s1["spikes"] - s0["spikes"], "events": s1["events"] - s0["events"],
+           "rate_hz": (s1["spikes"] - s0["spikes"]) / n / bio,
+           "rk_substeps_per_neuron_step": (s1["rk_substeps"] - s0["rk_substeps"]) / n / (bio * 1e4),
+           "us_per_launch": {"k_update_aeif": 1e3 * ms[1] / max(1, nl[1]), "k_deliver": 1e3 * ms[2] / max(1, nl[2])},
+           "step_loop": LOOPS[s1["mode"]], "delivery": DELIVERY[s1["delivery"]],
+           "rk_control": "fp32" if ctl32 else "fp64", "cpu_baseline": None}
+    if cpu:
         # the oracle (FP32-state replica at the same tolerance) on a bounded sample: 20,000 neurons of the
         # same network for 100 steps after 20; scaled per neuron-step to the full network
         import oracle
         n_s = 20_000
         small = W.balanced_adex(n=n_s, indegree=1000, seed=1, weight_dtype="bf16")
         for p in small.pops:
-            p.params.rk_control_fp32 = a.adex_ctl32
+            p.params.rk_control_fp32 = ctl32
         o = oracle.OracleNet(small)
         o.finalize()
         o.simulate(20)
         c0 = time.perf_counter()
         o.simulate(100)
         cw = time.perf_counter() - c0
-        cpu = {"real_time_factor": cw / 100 / n_s * a.adex_n / 1e-4, "cores": 1, "kind": "oracle",
-               "sample": "%d neurons of the same network (in-degree 1000), 100 steps after 20, single-threaded "
-                         "C++ oracle on %s; scaled per neuron-step to %d neurons" % (n_s, _cpu_info(), a.adex_n)}
-    print(json.dumps({"workload": "balanced_adex_%d" % a.adex_n, "neurons": s1["num_neurons"], "synapses": s1["num_synapses"],
-                      "build_s": build_s, "real_time_factor": wall / bio, "bio_s": bio,
-                      "spikes": s1["spikes"] - s0["spikes"], "events": s1["events"] - s0["events"],
-                      "rate_hz": (s1["spikes"] - s0["spikes"]) / a.adex_n / bio,
-                      "rk_substeps_per_neuron_step": (s1["rk_substeps"] - s0["rk_substeps"]) / a.adex_n / (bio * 1e4),
-                      "us_per_launch": {"k_update_aeif": 1e3 * ms[1] / max(1, nl[1]),
-                                        "k_deliver": 1e3 * ms[2] / max(1, nl[2])},
-                      "step_loop": LOOPS[s1["mode"]],
-                      "delivery": DELIVERY[s1["delivery"]],
-                      "rk_control": "fp32" if a.adex_ctl32 else "fp64", "cpu_baseline": cpu}), flush=True)
+        out["cpu_baseline"] = {
+            "real_time_factor": cw / 100 / n_s * n / 1e-4, "cores": 1, "kind": "oracle",
+            "sample": "%d neurons of the same network (in-degree 1000), 100 steps after 20, single-threaded "
+                      "C++ oracle on %s; scaled per neuron-step to %d neurons" % (n_s, _cpu_info(), n)}
+    return out
+
+
+def run_adex(a):
+    print(json.dumps(adex_variant(a.adex_n, a.sim_steps, a.steps, a.adex_ctl32, a.delivery, a.mode,
+                                  not a.no_cpu_baseline)), flush=True)
     return 0
 
 
@@ -399,15 +426,16 @@ def run_stdp(a):
     s2 = sim.stats()
     ev_prof = s2["events"] - s1["events"]
     sim.close()
-    # algorithmic bytes of the potentiation + delivery bracket per step: every synaptic event reads its
-    # target word, weight and adds into the input (12 B); a plastic one also reads the target's latest
-    # spike and writes weight and arrival (12 B); every potentiation reads the index word, the arrival and
-    # the weight and writes the weight (20 B).  Plastic fraction 0.64 (E -> E of 1000 inputs); potentiations
-    # per step = excitatory spikes x 800 plastic inputs (estimated from the excitatory share of spikes, 0.8).
+    # algorithmic bytes of the potentiation + delivery bracket per step: a static synaptic event reads its
+    # target word and weight and adds into the input (12 B); a plastic one reads its target word and its
+    # 8-byte weight-and-arrival word, the target's latest spike (4 B), adds into the input and writes the
+    # 8-byte word back (28 B); every potentiation reads the index word and the weight-and-arrival word and
+    # writes the weight (20 B).  Plastic fraction 0.64 (E -> E of 1000 inputs); potentiations per step =
+    # excitatory spikes x 800 plastic inputs (estimated from the excitatory share of spikes, 0.8).
     spk_prof = (s2["spikes"] - s1["spikes"]) / 500.0
     events_step = ev_prof / 500.0
     pot_step = 0.8 * spk_prof * 800
-    bytes_step = events_step * (12 + 0.64 * 12) + pot_step * 20
+    bytes_step = events_step * (0.36 * 12 + 0.64 * 28) + pot_step * 20
     us_del = 1e3 * ms[2] / max(1, nl[2])
     peak, peak_src = _peaks()
     achieved = bytes_step / (us_del * 1e-6) / 1e9
@@ -521,62 +549,107 @@ def _pop_stats(ids, steps, spec, t_lo, t_hi):
     return out
 
 
-def run_precision(a):
-    """Precision report: for each workload family (at a size the oracle
-    finishes in seconds), the per-step synaptic input of the FP32 GPU path
-    against the oracle's FP64 sum (relative to the summed magnitudes of the
-    contributing weights), and per-population rates and CV ISI of the FP32 and
-    BF16-weight GPU runs against the oracle (FP32 weights)."""
-    import numpy as np
+def _oracle_job(job):
+    """Spawned worker of the precision report: the oracle run of one network
+    (spec, steps, input steps, receptors) -> spikes and the FP64 sums of the
+    first input steps."""
+    spec, steps, n_in, R = job
     import oracle
+    o = oracle.OracleNet(spec, track_abs=n_in > 0)
+    o.finalize()
+    inputs = []
+    for _ in range(n_in):
+        for r in range(R):
+            _, ab, ex = o.input(r, 0)
+            inputs.append((ex, ab))
+        o.simulate(1)
+    o.simulate(steps - n_in)
+    ids, st = o.spikes()
+    return ids, st, inputs
+
+
+def run_precision(a):
+    """Precision report: for each network, the FP32-weight, BF16-weight and
+    FP16-weight GPU runs against the oracle (FP32 weights) on the same seeds:
+    the per-step synaptic input of the first 20 steps of the FP32 path against
+    the oracle's FP64 sum (relative to the summed magnitudes of the
+    contributing weights), and per-population rates and mean CV ISI over 2 s
+    after a 0.5 s transient, for three seeds (the oracle runs in parallel
+    worker processes)."""
+    import multiprocessing as mp
+    import numpy as np
     from paper_2007_14236_gb300 import ngb, workloads as W
+    T0, T = 5000, 25000
+    n_in = 20
+    seeds = (1, 2, 3)
     cases = {
-        "balanced_lif_1000": lambda wd: W.balanced_lif(n=1000, indegree=100, seed=1, weight_dtype=wd),
-        "microcircuit_0.1": lambda wd: W.microcircuit(scale=0.1, seed=1, weight_dtype=wd),
-        "balanced_adex_20000_driven": lambda wd: W.balanced_adex(n=20000, indegree=1000, seed=1, weight_dtype=wd,
-                                                           poisson_weight=4.0, w_ex=2.0, w_in=4.0),
-        "paper_balanced_10000": lambda wd: W.paper_balanced(n_ex=8000, ce=800, seed=1, weight_dtype=wd),
+        "microcircuit_full_scale": lambda s, wd: W.microcircuit(scale=1.0, seed=s, weight_dtype=wd),
+        "balanced_lif_1000": lambda s, wd: W.balanced_lif(n=1000, indegree=100, seed=s, weight_dtype=wd),
+        "balanced_adex_20000_driven": lambda s, wd: W.balanced_adex(n=20000, indegree=1000, seed=s, weight_dtype=wd,
+                                                                    poisson_weight=4.0, w_ex=2.0, w_in=4.0),
+        "paper_balanced_alpha_2500": lambda s, wd: W.paper_balanced(n_ex=2000, ce=200, seed=s, weight_dtype=wd),
     }
-    T, T0 = 3000, 500
+    jobs, keys = [], []
+    for name, mk in cases.items():
+        for s in seeds:
+            spec = mk(s, "fp32")
+            R = 2 if any(p.model != W.LIF for p in spec.pops) else 1
+            jobs.append((spec, T, n_in if s == seeds[0] else 0, R))
+            keys.append((name, s))
+    pool = mp.get_context("spawn").Pool(max(1, min(len(jobs), (os.cpu_count() or 2) - 1)))
+    res = pool.map_async(_oracle_job, jobs, chunksize=1)
+    gpu = {}
+    for name, mk in cases.items():
+        for s in seeds:
+            for wd in ("fp32", "bf16", "fp16"):
+                spec = mk(s, wd)
+                R = 2 if any(p.model != W.LIF for p in spec.pops) else 1
+                kw = dict(record_capacity=8_000_000, drain_steps=5000)
+                if name.startswith("microcircuit"):
+                    kw.update(steps_per_graph=100, drain_steps=10_000)
+                g = ngb.from_spec(spec, **kw)
+                g.finalize()
+                g.autotune(500)
+                gin = []
+                if wd == "fp32" and s == seeds[0]:
+                    for _ in range(n_in):
+                        for r in range(R):
+                            gin.append(g.input(r, 0).astype(np.float64))
+                        g.simulate(1)
+                g.simulate(T - g.stats()["steps"])
+                ids, st = g.spikes()
+                gpu[(name, s, wd)] = (ids, st, gin, LOOPS[g.stats()["mode"]])
+                g.close()
+    ora = dict(zip(keys, res.get()))
+    pool.close()
+    pool.join()
+
+    def rel(x, y):
+        return abs(x - y) / y if y > 0 else (0.0 if x == 0 else float("inf"))
     report = {}
     for name, mk in cases.items():
-        spec = mk("fp32")
-        g = ngb.from_spec(spec, delivery=a.delivery)
-        g.finalize()
-        o = oracle.OracleNet(spec, track_abs=True)
-        o.finalize()
-        R = 2 if any(p.model != W.LIF for p in spec.pops) else 1
+        spec = mk(seeds[0], "fp32")
+        ids0, st0, oin = ora[(name, seeds[0])]
+        gin = gpu[(name, seeds[0], "fp32")][2]
         err = 0.0
-        for _ in range(20):
-            for r in range(R):
-                gin = g.input(r, 0).astype(np.float64)
-                _, oabs, oex = o.input(r, 0)
-                nz = oabs > 0
-                if np.any(nz):
-                    err = max(err, float(np.max(np.abs(gin[nz] - oex[nz]) / oabs[nz])))
-            g.simulate(1)
-            o.simulate(1)
-        g.simulate(T - 20)
-        o.simulate(T - 20)
-        so = _pop_stats(*o.spikes(), spec, T0, T)
-        sg = _pop_stats(*g.spikes(), spec, T0, T)
-        g.close()
-        bspec = mk("bf16")
-        b = ngb.from_spec(bspec, delivery=a.delivery)
-        b.simulate(T)
-        sb = _pop_stats(*b.spikes(), bspec, T0, T)
-        b.close()
-
-        def rel(x, y):
-            return abs(x - y) / y if y > 0 else (0.0 if x == 0 else float("inf"))
-        report[name] = {
-            "input_rel_error_max_fp32": err,
-            "rates_hz_oracle": [round(x[0], 3) for x in so],
-            "rate_rel_error_max_fp32": max(rel(x[0], y[0]) for x, y in zip(sg, so)),
-            "rate_rel_error_max_bf16": max(rel(x[0], y[0]) for x, y in zip(sb, so)),
-            "cv_isi_abs_error_max_fp32": max(abs(x[1] - y[1]) for x, y in zip(sg, so) if y[1] == y[1]),
-            "cv_isi_abs_error_max_bf16": max(abs(x[1] - y[1]) for x, y in zip(sb, so) if y[1] == y[1]),
-        }
+        for g_, (ex, ab) in zip(gin, oin):
+            nz = ab > 0
+            if np.any(nz):
+                err = max(err, float(np.max(np.abs(g_[nz] - ex[nz]) / ab[nz])))
+        row = {"input_rel_error_max_fp32": err, "seeds": list(seeds), "stats_window_s": [T0 * 1e-4, T * 1e-4],
+               "step_loop": gpu[(name, seeds[0], "fp32")][3]}
+        so_all = {s: _pop_stats(*ora[(name, s)][:2], spec, T0, T) for s in seeds}
+        row["rates_hz_oracle_seed1"] = [round(x[0], 3) for x in so_all[seeds[0]]]
+        for wd in ("fp32", "bf16", "fp16"):
+            rmax, cmax = 0.0, 0.0
+            for s in seeds:
+                sg = _pop_stats(*gpu[(name, s, wd)][:2], spec, T0, T)
+                so = so_all[s]
+                rmax = max(rmax, max(rel(x[0], y[0]) for x, y in zip(sg, so)))
+                cmax = max(cmax, max(abs(x[1] - y[1]) for x, y in zip(sg, so) if y[1] == y[1]))
+            row["rate_rel_error_max_" + wd] = rmax
+            row["cv_isi_abs_error_max_" + wd] = cmax
+        report[name] = row
     print(json.dumps({"workload": "precision_report", "steps": T, "stats_window_steps": [T0, T], "cases": report}),
           flush=True)
     return 0
@@ -683,26 +756,47 @@ def run_request(a):
     return 0
 
 
-def run_serve(a):
+def served_variant(duration_s: float, delivery: str = "auto", plain_sample: int = 30):
+    """Config 4: the served request stream (Poisson arrivals at 20/s over
+    duration_s seconds) through one serving handle, with p50/p99 completion
+    latency, against the plain path: a sample of the requests, each alone in
+    its own handle, (a) end to end through the library's default choices
+    (build, simulate, read back) and (b) autotuned, the simulation alone timed.
+    served_vs_plain divides by (b), the faster plain figure."""
     import numpy as np
-    from paper_2007_14236_gb300 import serve, workloads as W
-    reqs = W.served_requests(duration_s=a.serve_duration)
-    srv = serve.Server(8_000_000, 4_000_000_000, 8_000_000, ring_slots=32, delivery=a.delivery)
-    delivery = DELIVERY[srv.sim.stats()["delivery"]]
+    from paper_2007_14236_gb300 import ngb, serve, workloads as W
+    reqs = W.served_requests(duration_s=duration_s)
+    srv = serve.Server(8_000_000, 4_000_000_000, 8_000_000, ring_slots=32, delivery=delivery)
+    sdelivery = DELIVERY[srv.sim.stats()["delivery"]]
     done, summary = srv.run(reqs)
     srv.close()
-    summary["delivery"] = delivery
+    summary["delivery"] = sdelivery
     rng = np.random.default_rng(0)
-    sample = rng.choice(len(reqs), size=min(30, len(reqs)), replace=False)
-    pw, pe = 0.0, 0
+    sample = rng.choice(len(reqs), size=min(plain_sample, len(reqs)), replace=False)
+    pw, pe, tw, te = 0.0, 0, 0.0, 0
     for i in sample:
-        w, ev, _, _ = serve.run_alone(reqs[int(i)])
+        r = reqs[int(i)]
+        w, ev, _, _ = serve.run_alone(r)
         pw += w
         pe += ev
-    summary.update({"workload": "served_requests", "arrival_rate_per_s": 20.0, "window_s": a.serve_duration,
-                    "plain_events_per_s": pe / pw, "served_vs_plain": summary["events_per_s"] / (pe / pw),
-                    "plain_sample": len(sample)})
-    print(json.dumps(summary), flush=True)
+        one = ngb.from_spec(W.request_net(r), drain_steps=1000, record_spikes=False, delivery=delivery)
+        one.finalize()
+        one.autotune(300)
+        steps = int(round(r.bio_time_ms / 0.1))
+        t0 = time.perf_counter()
+        one.simulate(steps)
+        tw += time.perf_counter() - t0
+        te += one.stats()["events"]
+        one.close()
+    summary.update({"workload": "served_requests", "arrival_rate_per_s": 20.0, "window_s": duration_s,
+                    "plain_e2e_events_per_s": pe / pw, "plain_tuned_events_per_s": te / tw,
+                    "served_vs_plain": summary["events_per_s"] / (te / tw),
+                    "served_vs_plain_e2e": summary["events_per_s"] / (pe / pw), "plain_sample": len(sample)})
+    return summary
+
+
+def run_serve(a):
+    print(json.dumps(served_variant(a.serve_duration, a.delivery)), flush=True)
     return 0
 
 
@@ -710,7 +804,8 @@ def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
-    if a.mode in ("persistent", "fused", "pipelined", "persistent_pipelined", "pipelined_one_kernel", "target_owned"):
+    if a.mode in ("persistent", "fused", "pipelined", "persistent_pipelined", "pipelined_one_kernel", "target_owned",
+                  "tiled"):
         os.environ["NGB_MODE"] = a.mode  # read by the library when a network is finalised
     if a.workload != "microcircuit":
         return {"small": run_small, "batched": run_batched, "adex": run_adex, "paper": run_paper,
@@ -900,6 +995,24 @@ def main():
                                              "real_time_factor": vms * 1e-3 / vb,
                                              "step_loop": LOOPS[v.stats()["mode"]]}}
         v.close()
+
+    if rank == 0 and ws == 1 and not a.no_variants:
+        # the other configurations, each measured once per run: batched and served throughput against the
+        # plain path, and the AdEx network's real-time factor
+        line.setdefault("variants", {})
+        b = batched_variant(64, 5000, "fp32", a.delivery, a.mode)
+        line["variants"]["batched_64_microcircuits"] = {
+            k: b[k] for k in ("batched_events_per_s", "plain_events_per_s", "batched_vs_plain", "step_loop",
+                              "delivery", "neurons", "synapses", "bio_s", "plain_step_loops", "kernels")}
+        v = served_variant(a.serve_duration, a.delivery)
+        line["variants"]["served_requests"] = {
+            k: v[k] for k in ("requests", "window_s", "events_per_s", "plain_tuned_events_per_s",
+                              "plain_e2e_events_per_s", "served_vs_plain", "served_vs_plain_e2e", "p50_latency_s",
+                              "p99_latency_s", "max_active", "wall_s", "delivery")}
+        x = adex_variant(1_000_000, 10_000, 1, False, a.delivery, a.mode, cpu=not a.no_cpu_baseline)
+        line["variants"]["adex_1e6_config2"] = {
+            k: x[k] for k in ("real_time_factor", "rate_hz", "rk_substeps_per_neuron_step", "us_per_launch",
+                              "step_loop", "delivery", "rk_control", "cpu_baseline", "neurons", "synapses")}
 
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a.weights, a.cpu_sample_steps)

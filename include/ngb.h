@@ -242,8 +242,12 @@ typedef struct {
                            4 pipelined persistent step kernel (one grid barrier per step), 5 pipelined
                            with one kernel per step (LIF networks), 6 target-owned persistent kernel
                            (LIF networks: one block per SM owns every G-th neuron, with the ring of its
-                           neurons in shared memory; spikes exchanged through step-stamped mailboxes) */
-  int64_t launch_grid;  /* blocks of the delivery kernel (modes 0, 3, 5) or of the persistent kernel
+                           neurons in shared memory; spikes exchanged through step-stamped mailboxes),
+                           7 per-step kernels in CUDA graphs with target-tiled delivery (spike-buffer
+                           scheme: the due groups' synapses, stored a second time partitioned by target
+                           tile, are summed per tile in shared memory and each tile's input written once,
+                           instead of one global atomic per synaptic event) */
+  int64_t launch_grid;  /* blocks of the delivery kernel (modes 0, 3, 5, 7) or of the persistent kernel
                            (modes 1, 4, 6) */
   int64_t delivery;     /* delivery scheme in use: 1 ring, 2 spike buffer */
 } ngb_stats;
@@ -363,9 +367,13 @@ NGB_API int ngb_simulate_profiled(ngb_sim* sim, int64_t steps, double* kernel_ms
  * environment variable NGB_AUTOTUNE_CACHE naming a file, results are looked up
  * and appended there per (GPU, network shape) key.  *deliver_grid_out (may be
  * NULL) receives the chosen grid.  The environment variable NGB_MODE
- * ("persistent", "persistent_pipelined", "fused", "pipelined", "pipelined_one_kernel" or "target_owned")
- * selects that step loop at finalisation without tuning (networks the loop does not take keep the per-step
- * kernels). */
+ * ("persistent", "persistent_pipelined", "fused", "pipelined", "pipelined_one_kernel", "target_owned" or
+ * "tiled") selects that step loop at finalisation without tuning (networks the loop does not take keep the
+ * per-step kernels); "tiled" selects target-tiled delivery with the spike-buffer scheme (stats mode 7;
+ * its layout, another copy of the synapses partitioned by target tile, is built at finalisation; the
+ * autotuner does not consider it, being slower than the plain delivery kernel on the networks measured),
+ * with NGB_TILED = "T,P" setting the tile size (neurons) and the blocks per tile (1-8, a thread-block
+ * cluster when above 1). */
 NGB_API int ngb_autotune(ngb_sim* sim, int64_t trial_steps, int32_t* deliver_grid_out);
 
 /* Spikes recorded in steps [t0_step, t1_step) of population `pop` (-1 = all,
@@ -399,6 +407,17 @@ NGB_API int ngb_get_src_ptr(ngb_sim* sim, uint64_t* src_ptr);
  * FP32, delay in steps. Any output pointer may be NULL. */
 NGB_API int ngb_get_synapses(ngb_sim* sim, int64_t first, int64_t n, uint32_t* tgt, uint8_t* receptor, float* weight,
                      uint16_t* delay);
+
+/* Evaluate, on the current device, the factor r^(-1/k) (k = 5 or 4) that
+ * sizes the next sub-step of the adaptive Runge-Kutta integration of AdEx
+ * neurons (Sec. 2.1: fifth-order Runge-Kutta with adaptive step size), for
+ * the n ratios r[n] (error / tolerance) into out[n] (host arrays).  The
+ * factor is an exactly specified sequence of FP32 operations (r = m 2^e,
+ * e = k q + s; 2^-q * (c(m - 1) * 2^(-s/k)) with a fixed cubic c), so an
+ * implementation on another processor can reproduce it bit for bit; ratios
+ * below 2^-100 give 2^20, those of 2^100 and above or not finite give 0.
+ * Blocking; allocates a temporary device buffer. */
+NGB_API int ngb_eval_step_factor(const float* r, int64_t n, int32_t k, float* out);
 
 /* --------------------------------------------------- allocation-free entry */
 /* Device-resident CSR described by caller-owned DEVICE pointers (the layout

@@ -61,6 +61,8 @@ def lib():
     L.ora_round_weight.argtypes = [C.c_float, C.c_int32]
     L.ora_normal_from_words.restype = C.c_double
     L.ora_normal_from_words.argtypes = [P]
+    L.ora_step_factor_root.restype = C.c_float
+    L.ora_step_factor_root.argtypes = [C.c_float, C.c_int32]
     _lib = L
     return L
 
@@ -102,6 +104,10 @@ def cash_karp_tableau():
 
 def round_weight(w: float, prec: int) -> float:
     return float(lib().ora_round_weight(w, prec))
+
+
+def step_factor_root(r: float, k: int) -> float:
+    return float(lib().ora_step_factor_root(r, k))
 
 
 def normal_from_words(words) -> float:

@@ -32,6 +32,7 @@
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 namespace {
@@ -535,11 +536,54 @@ void ck_step(const AdexSystem<T>& sys, const Tableau& tab, const T y[kAdexN], co
   }
 }
 
+// Step-size factor of the FP32-state integration: r^(-1/k) for k = 5 (after
+// an accepted sub-step) or k = 4 (after a rejected one), defined as a fixed
+// sequence of FP32 operations so that the GPU path, which follows the same
+// definition, produces the same bits.  The definition: write r = m 2^e with
+// m in [1, 2) and e = k q + s, 0 <= s < k; then
+//   r^(-1/k) = 2^(-q) * (c(m - 1) * K_k[s]),  K_k[s] = 2^(-s/k) rounded to FP32,
+// with c the cubic below (least-squares fit of m^(-1/k) on [1, 2), relative
+// error < 2e-4), evaluated by Horner's rule with fused multiply-adds.  Ratios
+// below 2^-100 give 2^20 and ratios of 2^100 and above (or not finite) give 0;
+// both are then clamped by the caller.
+float step_factor_root(float r, int k) {
+  if (!(r < 0x1p100f)) return 0.0f;
+  if (r < 0x1p-100f) return 0x1p20f;
+  uint32_t bits;
+  std::memcpy(&bits, &r, 4);
+  const int e = (int)((bits >> 23) & 0xffu) - 127;
+  const uint32_t mbits = (bits & 0x7fffffu) | 0x3f800000u;
+  float m;
+  std::memcpy(&m, &mbits, 4);
+  const float t = m - 1.0f;  // exact
+  int q = e / k;
+  if (e < 0 && q * k != e) q -= 1;  // floor division
+  const int s = e - q * k;
+  float c, ks;
+  if (k == 5) {
+    static const float K5[5] = {0x1p+0f, 0x1.bdb8cep-1f, 0x1.8406p-1f, 0x1.51cb46p-1f, 0x1.261118p-1f};
+    c = std::fma(std::fma(std::fma(-0x1.ae3294p-6f, t, 0x1.78f37cp-4f), t, -0x1.8fb646p-3f), t, 0x1.ffed6cp-1f);
+    ks = K5[s];
+  } else {
+    static const float K4[4] = {0x1p+0f, 0x1.ae89fap-1f, 0x1.6a09e6p-1f, 0x1.306fep-1f};
+    c = std::fma(std::fma(std::fma(-0x1.18bd56p-5f, t, 0x1.e6677ep-4f), t, -0x1.f2b6f8p-3f), t, 0x1.ffe6dcp-1f);
+    ks = K4[s];
+  }
+  const uint32_t pbits = (uint32_t)(127 - q) << 23;  // 2^(-q), |q| <= 20
+  float p2;
+  std::memcpy(&p2, &pbits, 4);
+  return (c * ks) * p2;
+}
+
 // Integrate one AdEx neuron over one step dt (adaptive step size, error
 // relative to |y| + |h f| + floor, safety factor 0.9, growth exponent -1/5,
 // shrink exponent -1/4, growth at most 5x, shrink at most 10x), resetting
 // V -> V_reset and w -> w + b after every accepted sub-step that ends with
 // V >= V_peak.  Returns the number of spikes; h carries the proposed step.
+// The FP64 reference (T = double) tests emax / tol <= 1 and takes the factors
+// with pow in FP64.  The FP32-state replica (T = float) follows the GPU's
+// step control: the test (double)emax * (1 / tol) <= 1 in FP64, and the
+// factors 0.9 * step_factor_root(r) in FP32 with r = emax * (float)(1 / tol).
 template <typename T>
 int adex_advance(const AdexSystem<T>& sys, const Tableau& tab, const AeifPar& p, double dt, double tol,
                  T y[kAdexN], double& h, int64_t& substeps, int64_t& cap_hits) {
@@ -565,7 +609,9 @@ int adex_advance(const AdexSystem<T>& sys, const Tableau& tab, const AeifPar& p,
       const T r = std::fabs(err[i]) / scale;
       if (r > emax) emax = r;
     }
-    const double ratio = (double)emax / tol;
+    constexpr bool replica = std::is_same<T, float>::value;
+    const double ratio = replica ? (double)emax * (1.0 / tol) : (double)emax / tol;
+    const float rf = (float)emax * (float)(1.0 / tol);
     ++n;
     if (ratio <= 1.0 || h <= p.h_min || n >= p.max_sub) {
       for (int i = 0; i < kAdexN; ++i) y[i] = y5[i];
@@ -575,14 +621,19 @@ int adex_advance(const AdexSystem<T>& sys, const Tableau& tab, const AeifPar& p,
         ++spikes;
       }
       double grow = 5.0;
-      if (ratio > 0.0) grow = std::min(5.0, 0.9 * std::pow(ratio, -0.2));
+      if (replica) {
+        if (rf > 0.0f) grow = (double)std::min(5.0f, 0.9f * step_factor_root(rf, 5));
+      } else if (ratio > 0.0) {
+        grow = std::min(5.0, 0.9 * std::pow(ratio, -0.2));
+      }
       const double h_used = h;
       h = std::max(h * grow, p.h_min);
       if (n >= p.max_sub && !last) cap_hits += 1;
       if (last || n >= p.max_sub) break;
       t_in += h_used;
     } else {
-      const double shrink = std::max(0.1, 0.9 * std::pow(ratio, -0.25));
+      const double shrink = replica ? (double)std::max(0.1f, 0.9f * step_factor_root(rf, 4))
+                                    : std::max(0.1, 0.9 * std::pow(ratio, -0.25));
       h = std::max(h * shrink, p.h_min);
     }
   }
@@ -1174,5 +1225,6 @@ void ora_cash_karp_tableau(double c[6], double a[36], double b5[6], double b4[6]
 }
 float ora_round_weight(float w, int32_t prec) { return round_weight(w, prec); }
 double ora_normal_from_words(const uint32_t w[4]) { return normal_from(w); }
+float ora_step_factor_root(float r, int32_t k) { return (k == 4 || k == 5) ? step_factor_root(r, k) : 0.0f; }
 
 }  // extern "C"

@@ -95,6 +95,9 @@ void ora_lif_propagators(double tau_m, double C_m, double tau_syn, double h, dou
 void ora_cash_karp_tableau(double c[6], double a[36], double b5[6], double b4[6]);
 float ora_round_weight(float w, int32_t prec);
 double ora_normal_from_words(const uint32_t w[4]);
+/* r^(-1/k) (k = 4 or 5) by the fixed FP32 operation sequence that sizes the
+ * next Runge-Kutta sub-step of the FP32-state AdEx integration (Sec. 2.1). */
+float ora_step_factor_root(float r, int32_t k);
 
 #ifdef __cplusplus
 }

@@ -16,7 +16,8 @@
 // population asks for it).  The error of component i is taken relative to
 // |y_i| + |h f_i| + floor_i (floors 1 mV, 1 pA, 1e-3 nS, 1e-3 nS, 1e-3 nS/ms,
 // 1e-3 nS/ms); accepted steps grow h by min(5, 0.9 r^-1/5), rejected ones
-// shrink it by max(0.1, 0.9 r^-1/4); h >= h_min is always accepted.  After
+// shrink it by max(0.1, 0.9 r^-1/4), the roots taken by step_factor_root (an
+// exactly specified FP32 operation sequence); h >= h_min is always accepted.  After
 // every accepted sub-step ending at V >= V_peak: V -> V_reset, w -> w + b,
 // and the spike is counted (the exponential term uses min(V, V_peak)).
 #pragma once
@@ -81,6 +82,35 @@ __device__ __forceinline__ void deriv(const AeifSeg& p, const float y[NC], float
   }
 }
 
+// r^(-1/K) for K = 5 (growth after an accepted sub-step) or 4 (shrink after a
+// rejected one), as one fixed sequence of FP32 operations, so that every
+// implementation of this definition returns the same bits: with
+// r = m 2^e (m in [1, 2)) and e = K q + s (0 <= s < K),
+//   r^(-1/K) = 2^(-q) * (c_K(m - 1) * 2^(-s/K)),
+// 2^(-s/K) rounded to FP32 and c_K the cubic below (least-squares fit of
+// m^(-1/K) on [1, 2), relative error < 2e-4) by Horner's rule with fused
+// multiply-adds.  r < 2^-100 gives 2^20; r >= 2^100, infinite or NaN gives 0.
+template <int K>
+__device__ __forceinline__ float step_factor_root(float r) {
+  if (!(r < 0x1p100f)) return 0.0f;
+  if (r < 0x1p-100f) return 0x1p20f;
+  const uint32_t u = __float_as_uint(r);
+  const int e = (int)(u >> 23) - 127;  // sign bit is 0 here
+  const float t = __uint_as_float((u & 0x7fffffu) | 0x3f800000u) - 1.0f;
+  const int q = (e >= 0) ? e / K : -((K - 1 - e) / K);
+  const int s = e - K * q;
+  float c, ks;
+  if constexpr (K == 5) {
+    c = __fmaf_rn(__fmaf_rn(__fmaf_rn(-0x1.ae3294p-6f, t, 0x1.78f37cp-4f), t, -0x1.8fb646p-3f), t, 0x1.ffed6cp-1f);
+    ks = s == 0 ? 0x1p+0f : s == 1 ? 0x1.bdb8cep-1f : s == 2 ? 0x1.8406p-1f : s == 3 ? 0x1.51cb46p-1f
+                                                                                      : 0x1.261118p-1f;
+  } else {
+    c = __fmaf_rn(__fmaf_rn(__fmaf_rn(-0x1.18bd56p-5f, t, 0x1.e6677ep-4f), t, -0x1.f2b6f8p-3f), t, 0x1.ffe6dcp-1f);
+    ks = s == 0 ? 0x1p+0f : s == 1 ? 0x1.ae89fap-1f : s == 2 ? 0x1.6a09e6p-1f : 0x1.306fep-1f;
+  }
+  return __fmul_rn(__fmul_rn(c, ks), __uint_as_float((uint32_t)(127 - q) << 23));
+}
+
 __device__ __forceinline__ float ratio_of(float err, float y, float hf, float fl) {
   return fabsf(err) / (fabsf(y) + fabsf(hf) + fl);
 }
@@ -139,7 +169,7 @@ __device__ __forceinline__ bool aeif_integrate_t(const AeifSeg& p, float y[NC], 
     // error ratio emax / tol <= 1 in the control precision CT; the FP32
     // product rf differs from it by at most 2.4e-7 relative, so it decides
     // alone outside [0.999999, 1.000001] (same decision, fewer FP64 operations)
-    const float rf = emax * p.inv_tol_f;
+    const float rf = __fmul_rn(emax, p.inv_tol_f);
     bool within;
     if (rf <= 0.999999f) within = true;
     else if (rf > 1.000001f) within = false;
@@ -156,7 +186,7 @@ __device__ __forceinline__ bool aeif_integrate_t(const AeifSeg& p, float y[NC], 
         ++nspk;
       }
       float grow = 5.0f;
-      if (rf > 0.0f) grow = fminf(5.0f, 0.9f * exp2f(-0.2f * __log2f(rf)));
+      if (rf > 0.0f) grow = fminf(5.0f, __fmul_rn(0.9f, step_factor_root<5>(rf)));
       const CT h_used = h;
       h = h * (CT)grow;
       if (h < h_min) h = h_min;
@@ -164,7 +194,7 @@ __device__ __forceinline__ bool aeif_integrate_t(const AeifSeg& p, float y[NC], 
       if (last || cap) return true;
       t_in += h_used;
     } else {
-      const float shrink = fmaxf(0.1f, 0.9f * exp2f(-0.25f * __log2f(rf)));
+      const float shrink = fmaxf(0.1f, __fmul_rn(0.9f, step_factor_root<4>(rf)));
       h = h * (CT)shrink;
       if (h < h_min) h = h_min;
     }

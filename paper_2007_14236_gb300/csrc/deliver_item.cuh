@@ -347,10 +347,19 @@ __device__ __forceinline__ void deliver_due_item(const uint4 it, const Csr& csr,
       pw[u][0] = pw[u][1] = make_uint4(0, 0, 0, 0);
       if (any[u]) {
         tv[u] = __ldg(reinterpret_cast<const uint4*>(csr.tgt + j0));
-        W4<WT>::load(csr.w, j0, wv[u]);
         if (kPlastic) {
-          pw[u][0] = *reinterpret_cast<const uint4*>(sa->wa + j0);
-          pw[u][1] = *reinterpret_cast<const uint4*>(sa->wa + j0 + 2);
+          // the weight-and-arrival words only where a synapse of the four is plastic, the CSR
+          // weights only where one is static (a plastic synapse's weight lives in its word)
+          const uint32_t pl = (tv[u].x | tv[u].y | tv[u].z | tv[u].w) >> kPlastShift & kPlastMask;
+          const bool all_pl = ((tv[u].x >> kPlastShift) & kPlastMask) && ((tv[u].y >> kPlastShift) & kPlastMask) &&
+                              ((tv[u].z >> kPlastShift) & kPlastMask) && ((tv[u].w >> kPlastShift) & kPlastMask);
+          if (!all_pl) W4<WT>::load(csr.w, j0, wv[u]);
+          if (pl) {
+            pw[u][0] = *reinterpret_cast<const uint4*>(sa->wa + j0);
+            pw[u][1] = *reinterpret_cast<const uint4*>(sa->wa + j0 + 2);
+          }
+        } else {
+          W4<WT>::load(csr.w, j0, wv[u]);
         }
       }
     }

@@ -19,7 +19,10 @@
 // exponential, alpha (the paper's balanced network, Sec. 2.4; state x_ex,
 // x_in) or the beta multisynapse model of Sec. 2.1 (up to four receptor
 // ports, each with g and x; the step reads one input plane per port in use).
+#include <string>
+
 #include "aeif_rk.cuh"
+#include "ngb.h"
 #include "deliver_item.cuh"
 #include "neuron_step.cuh"
 
@@ -318,3 +321,37 @@ cudaError_t launch_finish_aeif(const SegTable<AeifSeg>& segs, int grid, const Ae
 }
 
 }  // namespace ngb
+
+namespace ngb {
+namespace {
+
+__global__ void k_step_factor(const float* r, int64_t n, int k, float* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  out[i] = k == 4 ? step_factor_root<4>(r[i]) : step_factor_root<5>(r[i]);
+}
+
+}  // namespace
+
+int set_last_error(int code, const std::string& msg);  // ngb_api.cu: message for ngb_last_error()
+
+}  // namespace ngb
+
+extern "C" int ngb_eval_step_factor(const float* r, int64_t n, int32_t k, float* out) {
+  using namespace ngb;
+  if (n < 0 || (n > 0 && (!r || !out)) || (k != 4 && k != 5))
+    return set_last_error(NGB_ERR_INVALID_ARG, "ngb_eval_step_factor: arguments");
+  if (n == 0) return NGB_OK;
+  float* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, (size_t)n * 2 * sizeof(float));
+  if (e != cudaSuccess) return set_last_error(NGB_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  e = cudaMemcpy(d, r, (size_t)n * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    k_step_factor<<<(unsigned)((n + 255) / 256), 256>>>(d, n, k, d + n);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, d + n, (size_t)n * sizeof(float), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return set_last_error(NGB_ERR_CUDA, std::string("ngb_eval_step_factor: ") + cudaGetErrorString(e));
+  return NGB_OK;
+}

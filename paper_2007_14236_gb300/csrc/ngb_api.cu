@@ -252,7 +252,8 @@ struct ngb_sim {
                  // 5: pipelined, one kernel per step (LIF networks: update and delivery of the
                  //    previous step's queue in the same launch, chained by programmatic dependent launch),
                  // 6: target-owned persistent kernel (LIF networks, ring scheme: each block owns a tile
-                 //    of neurons with its ring in shared memory; spikes exchanged through mailboxes)
+                 //    of neurons with its ring in shared memory; spikes exchanged through mailboxes),
+                 // 7: per-step kernels in CUDA graphs with target-tiled delivery (spike-buffer scheme)
   cudaStream_t stream2 = nullptr;  // second stream of the pipelined loop's graphs
   bool persist_ok = false;
   int persist_grid = 0;
@@ -298,6 +299,11 @@ struct ngb_sim {
   // use), mailboxes, overflow areas and the launch shape
   bool lif_contig = false;  // LIF segments contiguous from neuron 0 (the kernel's segment search)
   bool own_tried = false;
+  // target-tiled delivery (mode 7: per-step kernels in CUDA graphs, spike-buffer
+  // scheme, due groups accumulated per target tile in shared memory): the
+  // layout (built on first use, for one tile size) and blocks per tile
+  TiledLayout tl{};
+  uint32_t tl_P = 1;
   OwnedLayout own{};
   unsigned long long* own_mb = nullptr;
   unsigned long long* own_ovf = nullptr;
@@ -452,6 +458,80 @@ cudaError_t launch_owned_chunk(ngb_sim* s, int64_t steps) {
   return e;
 }
 
+// Target-tiled delivery takes static networks with the spike-buffer scheme
+// and no plastic synapses.
+bool tiled_shape_ok(const ngb_sim* s) {
+  return !s->serving && s->scheme == 2 && !s->d_rules && s->G > 0 && s->N > 0 && s->R >= 1 && s->R <= kMaxPorts;
+}
+
+// Largest tile (neurons) whose accumulators fit 64 KB of shared memory.
+uint32_t tiled_max_T(const ngb_sim* s) {
+  return (uint32_t)(65536 / ((size_t)s->R * (s->cfg.deterministic ? 8 : 4)));
+}
+
+// Build the tiled layout for tiles of T neurons (replacing one of another
+// tile size); at most half of the free device memory.  A failure leaves the
+// layout absent, not the handle.
+bool tiled_ready(ngb_sim* s, uint32_t T) {
+  if (!tiled_shape_ok(s) || T < 32 || T > tiled_max_T(s)) return false;
+  if (s->tl.pairs && s->tl.T == T) return true;
+  if (s->tl.pairs) {
+    s->dev_bytes -= s->tl.bytes;
+    tiled_free(&s->tl);
+  }
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  TiledLayout L{};
+  cudaError_t e = tiled_build(s->grp_start, s->G, s->tgt, s->w, s->cfg.weight_dtype, s->K, s->N, T,
+                              (uint64_t)(free_b / 2), &L, s->stream);
+  if (e != cudaSuccess || !L.pairs) {
+    cudaGetLastError();
+    return false;
+  }
+  int optin = 0;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->cfg.device) != cudaSuccess ||
+      tiled_smem_bytes(s->cfg.deterministic != 0, s->R, T, L.n_tiles) + 1024 > (size_t)optin) {
+    cudaGetLastError();
+    tiled_free(&L);
+    return false;
+  }
+  s->tl = L;
+  s->dev_bytes += L.bytes;
+  return true;
+}
+
+// Tile size for about `tiles` tiles (at least 32 neurons, within the shared-memory limit).
+uint32_t tiled_T_for(const ngb_sim* s, int64_t tiles) {
+  tiles = std::max<int64_t>(1, tiles);
+  const int64_t T = std::max<int64_t>(32, (s->N + tiles - 1) / tiles);
+  return (uint32_t)std::min<int64_t>(T, tiled_max_T(s));
+}
+
+// Point the update kernels' spike-buffer emission at the tiled buckets (mode
+// 7) or at the plain due-item list; entering mode 7 starts with empty buckets.
+void set_tiled(ngb_sim* s, bool on) {
+  SpikeBuf& b = s->sb;
+  if (on && s->tl.pairs) {
+    b.tile_grp = s->tl.tile_grp;
+    b.bkt[0] = s->tl.bkt;
+    b.bkt[1] = s->tl.bkt + s->G;
+    b.boff = s->tl.boff;
+    b.bcnt = s->tl.bcnt;
+    b.n_tiles = s->tl.n_tiles;
+    cudaMemsetAsync(s->tl.bcnt, 0, (size_t)2 * s->tl.n_tiles * sizeof(unsigned int), s->stream);
+  } else {
+    b.tile_grp = nullptr;
+    b.bkt[0] = b.bkt[1] = nullptr;
+    b.boff = nullptr;
+    b.bcnt = nullptr;
+    b.n_tiles = 0;
+  }
+  s->pa.sb = s->sb;
+}
+
 // The first update kernel of the step scans the pending spikes (spike-buffer scheme).
 cudaError_t launch_lif(ngb_sim* s, int64_t step_off = 0) {
   return launch_update_lif(s->lif_tab, s->lif_blocks, s->lif_npt, s->thr, s->st0, s->st1, s->ref, ring_of(s),
@@ -496,6 +576,9 @@ cudaError_t launch_aeif(ngb_sim* s, int64_t step_off = 0) {
 StdpArgs stdp_of(const ngb_sim* s) { return StdpArgs{s->d_rules, s->wa, s->in_syn}; }
 
 cudaError_t launch_del(ngb_sim* s, int64_t step_off = 0, cudaStream_t st = nullptr) {
+  if (s->mode == 7)
+    return launch_deliver_tiled(s->sb, s->tl, s->tl_P, s->cfg.weight_dtype, ring_of(s), s->R, s->N,
+                                s->cfg.deterministic != 0, s->clk, pdl_of(s), st ? st : s->stream);
   const StdpArgs sa = stdp_of(s);
   return launch_deliver(s->sb, csr_of(s), s->cfg.weight_dtype, ring_of(s), s->cfg.deterministic != 0, emit_of(s),
                         s->clk, step_off, s->deliver_grid, pdl_of(s), st ? st : s->stream,
@@ -651,6 +734,8 @@ int capture_graph(ngb_sim* s) {
     cudaGraphExecDestroy(s->gexec);
     s->gexec = nullptr;
   }
+  if (s->mode == 7 && !s->tl.pairs) s->mode = 0;
+  set_tiled(s, s->mode == 7);
   if (s->graph_steps <= 0) return NGB_OK;
   cudaGraph_t graph = nullptr;
   CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
@@ -1247,6 +1332,8 @@ int rebuild_tables(ngb_sim* s) {
   if (s->mode == 2 && (!fused_ok(s) || s->scheme != 1)) s->mode = 0;
   // the pipelined loop delivers with the ring scheme
   if (s->mode == 3 && (s->scheme != 1 || !s->stream2)) s->mode = 0;
+  // target-tiled delivery: static networks, spike-buffer scheme, layout built
+  if (s->mode == 7 && (!tiled_shape_ok(s) || !s->tl.pairs)) s->mode = 0;
   if (s->mode == 5 && !pipe1_ok(s)) s->mode = 0;
   if (s->mode == 6 && !owned_ready(s)) s->mode = 0;
   s->tables_dirty = false;
@@ -1541,6 +1628,21 @@ int finalize_impl(ngb_sim* s) {
   if (env_mode && std::string(env_mode) == "pipelined" && s->scheme == 1 && s->stream2) s->mode = 3;
   if (env_mode && std::string(env_mode) == "pipelined_one_kernel" && s->scheme == 1) s->mode = 5;
   if (env_mode && std::string(env_mode) == "target_owned" && s->scheme == 1) s->mode = 6;
+  if (env_mode && std::string(env_mode) == "tiled" && s->scheme == 2) {
+    // tile size (neurons) and blocks per tile from NGB_TILED ("T,P"); else two tiles per SM, one block each
+    uint32_t T = tiled_T_for(s, 2 * (int64_t)s->sms), P = 1;
+    if (const char* tv = std::getenv("NGB_TILED")) {
+      unsigned a = 0, b = 0;
+      if (std::sscanf(tv, "%u,%u", &a, &b) == 2 && a >= 32 && a <= tiled_max_T(s) && b >= 1 && b <= 8) {
+        T = a;
+        P = b;
+      }
+    }
+    if (tiled_ready(s, T)) {
+      s->mode = 7;
+      s->tl_P = P;
+    }
+  }
   s->graph_steps = s->cfg.steps_per_graph == 0 ? 100 : std::max(0, s->cfg.steps_per_graph);
   return rebuild_tables(s);
 }
@@ -1688,6 +1790,8 @@ int snapshot_take(ngb_sim* s, Snapshot& sn) {
 int snapshot_restore(ngb_sim* s, const Snapshot& sn) {
   for (size_t i = 0; i < sn.parts.size(); ++i)
     CK(cudaMemcpyAsync(sn.parts[i].first, sn.copies[i], sn.parts[i].second, cudaMemcpyDeviceToDevice, s->stream));
+  // snapshots are taken between steps, when no due group waits in a bucket
+  if (s->tl.bcnt) CK(cudaMemsetAsync(s->tl.bcnt, 0, (size_t)2 * s->tl.n_tiles * sizeof(unsigned int), s->stream));
   CK(cudaStreamSynchronize(s->stream));
   return NGB_OK;
 }
@@ -1758,6 +1862,7 @@ int ngb_destroy(ngb_sim* s) {
   if (s->stream2) cudaStreamDestroy(s->stream2);
   for (void* p : s->allocs) cudaFree(p);
   for (void* p : s->table_allocs) cudaFree(p);
+  tiled_free(&s->tl);
   if (s->rec_pinned) cudaFreeHost(s->rec_pinned);
   if (s->own_stream) cudaStreamDestroy(s->stream);
   delete s;
@@ -1779,7 +1884,10 @@ int ngb_add_population_in(ngb_sim* s, int32_t instance, int32_t model, int64_t n
     return fail(NGB_ERR_INVALID_ARG, "ngb_add_population: unknown instance");
   if ((s->finalized && !s->serving) || s->inst[(size_t)instance].state != 0)
     return fail(NGB_ERR_STATE, "ngb_add_population: network (instance) already built");
-  if (n <= 0 || s->N + n >= (int64_t)kIdMask) return fail(NGB_ERR_INVALID_ARG, "ngb_add_population: n");
+  // neuron ids (26 bits) are positions: the network's for a static handle, the pool's for a serving
+  // handle (whose populations come and go, so only the pool bounds one)
+  if (n <= 0 || (s->serving ? n > s->N_cap : s->N + n >= (int64_t)kIdMask))
+    return fail(NGB_ERR_INVALID_ARG, "ngb_add_population: n");
   PopHost p{};
   p.model = model;
   p.instance = instance;
@@ -2110,13 +2218,17 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
   set_scheme(s, best_scheme);
   s->deliver_grid = best_grid;
   s->persist_grid = best_pgrid;
+  if (s->tl.pairs) {  // a target-tiled layout (selected at finalisation) is no longer used
+    s->dev_bytes -= s->tl.bytes;
+    tiled_free(&s->tl);
+  }
   s->mode = best_mode;
   if (rc == NGB_OK) rc = capture_graph(s);
   if (rc != NGB_OK) return rc;
   if (cache && *cache) {
     std::ofstream out(cache, std::ios::app);
-    out << key << " " << best_mode << " " << best_grid << " " << (s->persist_ok ? best_pgrid : 0) << " "
-        << best_scheme << "\n";
+    out << key << " " << best_mode << " " << best_grid << " "
+        << (s->persist_ok ? best_pgrid : 0) << " " << best_scheme << "\n";
   }
   if (deliver_grid_out)
     *deliver_grid_out = (best_mode == 1 || best_mode == 4) ? best_pgrid : best_mode == 6 ? s->own.G : best_grid;
@@ -2279,6 +2391,7 @@ int ngb_get_stats(ngb_sim* s, ngb_stats* out) {
     out->mode = s->mode;
     out->launch_grid = (s->mode == 1 || s->mode == 4) ? s->persist_grid
                        : s->mode == 6 ? s->own.G
+                       : s->mode == 7 ? (int64_t)s->tl.n_tiles * s->tl_P
                        : s->mode == 2 ? s->lif_blocks + s->aeif_blocks + s->aeifa_blocks
                                       : s->deliver_grid;  // graph and pipelined loops: the delivery grid
     out->delivery = s->scheme;

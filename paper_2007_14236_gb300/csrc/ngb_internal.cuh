@@ -147,6 +147,16 @@ struct SpikeBuf {
   const uint64_t* in_ptr;
   uint32_t* post[2];
   unsigned long long* post_cnt;
+  // target-tiled delivery (spike-buffer scheme in the graph loop, mode 7;
+  // NULL otherwise): each due connection group is one item {first pair of
+  // the group in the tiled copy lo, hi | multiplicity << 16, first target
+  // tile, boundary-pool offset},
+  // appended to the bucket of the first target tile its synapses reach
+  const uint4* tile_grp;            // per group {boundary-pool offset, first target tile, first pair lo, hi}
+  uint4* bkt[2];                    // bucket items by step parity (bucket j at boff[j])
+  const unsigned long long* boff;   // [n_tiles + 1]: bucket j holds the groups whose first tile is j
+  unsigned int* bcnt;               // [2][n_tiles] bucket fill counts by step parity
+  uint32_t n_tiles;
 };
 
 // Nearest-neighbour STDP rule (Sec. 2.1): FP32 constants and the tabulated
@@ -268,10 +278,33 @@ __device__ __forceinline__ void emit_spikes(bool spk, uint32_t gid, uint32_t mul
 // due-item list of parity ib, and, if keep, the pending entry ent to the
 // pending list of parity pb.  Positions beyond the lists' capacities are
 // dropped and raise kErrPendingOverflow.
+// With target-tiled delivery (sb.bkt set) the lane's due group g (n_it > 0)
+// becomes one item in the bucket of its first target tile instead, with one
+// atomic per bucket and warp.
 __device__ __forceinline__ void age_emit(uint32_t n_it, uint64_t b, uint32_t n, uint32_t mult, bool keep, uint4 ent,
-                                         int ib, int pb, const SpikeBuf& sb) {
+                                         int ib, int pb, const SpikeBuf& sb, uint32_t g = 0) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
+  if (sb.bkt[0]) {
+    const bool has = n_it > 0;
+    const unsigned act = __ballot_sync(full, has);
+    if (has) {
+      const uint4 tg = __ldg(sb.tile_grp + g);
+      const uint32_t j = tg.y;
+      const unsigned peers = __match_any_sync(act, j);
+      const int leader = __ffs(peers) - 1;
+      unsigned int base = 0;
+      if (lane == leader) base = atomicAdd(sb.bcnt + (size_t)ib * sb.n_tiles + j, (unsigned int)__popc(peers));
+      base = __shfl_sync(peers, base, leader);
+      const unsigned long long slot = (unsigned long long)base + __popc(peers & ((1u << lane) - 1u));
+      const unsigned long long b0 = __ldg(sb.boff + j);
+      if (slot < __ldg(sb.boff + j + 1) - b0)
+        (ib ? sb.bkt[1] : sb.bkt[0])[b0 + slot] = make_uint4(tg.z, (tg.w & 0xFFFFu) | (mult << 16), j, tg.x);
+      else
+        atomicOr(sb.err, kErrPendingOverflow);
+    }
+    n_it = 0;
+  }
   const unsigned kb = __ballot_sync(full, keep);
   uint32_t inc = n_it;
 #pragma unroll
@@ -390,7 +423,7 @@ __device__ __forceinline__ void emit_spikes_age(bool spk, uint32_t gid, uint32_t
   const uint4 ent = now ? make_uint4(word, meta.w + 1u, meta.w + ngrp, (uint32_t)(t + d1))
                         : make_uint4(word, meta.w, meta.w + ngrp, (uint32_t)(t + d0));
   record_spikes(spk, gid, mult, t, spk ? (unsigned long long)meta.z * mult : 0ull, sb);
-  age_emit(n_it, bsrc, ag.x, mult, keep, ent, (int)(t & 1), (int)((t + 1) & 1), sb);
+  age_emit(n_it, bsrc, ag.x, mult, keep, ent, (int)(t & 1), (int)((t + 1) & 1), sb, meta.w);
 }
 
 // Pending spikes at the update of step t (spike-buffer scheme): a spike whose
@@ -438,7 +471,7 @@ __device__ __forceinline__ void scan_pending(int64_t t, const Csr& csr, const Sp
       keep = more;
       ent = make_uint4(e.x, ig + 1u, e.z, e.w - dcur + dnext);
     }
-    age_emit(n_it, b, sz, e.x >> kIdBits, keep, ent, pb, pb ^ 1, sb);
+    age_emit(n_it, b, sz, e.x >> kIdBits, keep, ent, pb, pb ^ 1, sb, e.y);
   }
 }
 
@@ -686,15 +719,15 @@ cudaError_t launch_deliver(SpikeBuf sb, Csr csr, int wdtype, Ring ring, bool fix
 // STDP potentiation of the plastic inputs of the neurons that fired at step
 // clk[1] (after the step's update kernels, before its delivery).
 cudaError_t launch_stdp_post(SpikeBuf sb, StdpArgs a, const int64_t* clk, int grid, bool pdl, cudaStream_t st);
-// Reverse index of the plastic synapses of a built CSR (N targets, K synapse
-// words): in_ptr[N+1] (device, caller-owned) and a new device array of
-// rule << 40 | synapse index (caller frees), grouped by target.
 // The weight-and-arrival words of a CSR's K synapses: {weights[j], -1}.
 cudaError_t init_stdp_words(const float* w, uint64_t K, uint2* wa, cudaStream_t st);
 // The CSR weights of the plastic synapses among [first, first + n) from
 // their weight-and-arrival words.
 cudaError_t sync_stdp_weights(const uint2* wa, const uint32_t* tgt, uint64_t first, uint64_t n, float* w,
                               cudaStream_t st);
+// Reverse index of the plastic synapses of a built CSR (N targets, K synapse
+// words): in_ptr[N+1] (device, caller-owned) and a new device array of
+// rule << 40 | synapse index (caller frees), grouped by target.
 cudaError_t build_stdp_index(const uint32_t* tgt, uint64_t K, int64_t N, uint64_t* in_ptr, uint64_t** in_syn_out,
                              uint64_t* n_plastic_out, cudaStream_t st);
 // Spike-buffer scheme, serving handles: mark the pending entries of sources
@@ -706,6 +739,45 @@ cudaError_t launch_kill_pending(uint4* list, const unsigned long long* count, in
 // LIF (model 0): a = y = V0 - E_L.  AdEx (model 1): a = V0, b = w0, h = h0.
 cudaError_t launch_init_state(int model, int64_t n, double mean, double sd, double E_L, double w0, double h0,
                               uint64_t seed, uint32_t local_off, float* a, float* b, float* h, cudaStream_t st);
+
+// Target-tiled delivery (tiled.cu): the synapses of every connection group
+// partitioned by target tile (T consecutive neurons), the per-group
+// boundary pool, the bucket lists of the due groups and the first bucket
+// each tile reads.
+struct TiledLayout {
+  uint2* pairs = nullptr;             // {target word, weight bits}: groups partitioned by tile, parts padded
+  uint32_t* pool = nullptr;           // per group: span, then span + 1 padded part offsets in the group
+  uint4* tile_grp = nullptr;          // [G] {pool offset, first tile, first pair lo, hi}
+  uint4* bkt = nullptr;               // [2][G] bucket items by step parity
+  unsigned long long* boff = nullptr; // [n_tiles + 1] bucket offsets
+  unsigned int* bcnt = nullptr;       // [2][n_tiles] bucket fill counts
+  uint32_t* lo = nullptr;             // [n_tiles] first bucket read by each tile
+  uint32_t n_tiles = 0, T = 0, max_buckets = 0;
+  uint64_t pairs_n = 0, bytes = 0;
+};
+
+struct TiledArgs {
+  const uint2* pairs;
+  const uint32_t* pool;
+  const uint32_t* lo;
+  uint32_t n_tiles, T, P;
+  int32_t R;
+  int64_t N;
+};
+
+// Build the tiled layout of a finalised CSR (group starts grp_start[G+1],
+// target words tgt, weights w in precision wdtype) for N neurons and tiles
+// of T neurons; fails softly (out->pairs NULL, cudaSuccess) when it would need
+// more than max_bytes or the pool exceeds 32-bit offsets.
+cudaError_t tiled_build(const uint64_t* grp_start, uint64_t G, const uint32_t* tgt, const void* w, int wdtype,
+                        uint64_t K, int64_t N, uint32_t T, uint64_t max_bytes, TiledLayout* out,
+                        cudaStream_t st);
+void tiled_free(TiledLayout* L);
+size_t tiled_smem_bytes(bool fixed, int R, uint32_t T, uint32_t n_tiles);
+// Deliver the step's due groups (buckets of parity clk[1] & 1) with P blocks
+// per tile; advances the clock as the plain spike-buffer delivery does.
+cudaError_t launch_deliver_tiled(SpikeBuf sb, const TiledLayout& L, uint32_t P, int wdtype, Ring ring, int R,
+                                 int64_t N, bool fixed, int64_t* clk, bool pdl, cudaStream_t st);
 
 constexpr int kLifBlock = 256;
 constexpr int kAeifBlock = 128;

@@ -16,8 +16,8 @@
 // 32 of the neuron's incoming plastic synapses (the reverse index built at
 // finalisation), so that a step with few firing targets still has every warp
 // issuing its gathers; each lane handles two synapses per pass with both
-// chains of loads in flight.  Bytes per synapse update: 8 (index word) + 4
-// (arrival) + 4 + 4 (weight read and write).
+// chains of loads in flight.  Bytes per synapse update: 8 (index word) + 8
+// (weight-and-arrival word read) + 4 (weight write).
 #include <cuda_runtime.h>
 
 #include "builder.h"

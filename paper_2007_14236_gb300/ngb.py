@@ -87,7 +87,8 @@ EXPORTS = ["ngb_create", "ngb_destroy", "ngb_last_error", "ngb_add_instance", "n
            "ngb_add_population_in", "ngb_connect", "ngb_connect_stdp", "ngb_finalize", "ngb_simulate", "ngb_simulate_profiled",
            "ngb_get_spikes", "ngb_get_stats", "ngb_population_range", "ngb_get_state", "ngb_get_input",
            "ngb_get_src_ptr", "ngb_get_synapses", "ngb_autotune", "ngb_deliver_spikes_noalloc",
-           "ngb_reserve", "ngb_commit_instance", "ngb_retire_instance", "ngb_instance_info"]
+           "ngb_reserve", "ngb_commit_instance", "ngb_retire_instance", "ngb_instance_info",
+           "ngb_eval_step_factor"]
 
 
 def lib_path() -> str:
@@ -131,6 +132,7 @@ def load(build_if_missing: bool = True):
     L.ngb_commit_instance.argtypes = [P, C.c_int32]
     L.ngb_retire_instance.argtypes = [P, C.c_int32]
     L.ngb_instance_info.argtypes = [P, C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+    L.ngb_eval_step_factor.argtypes = [P, C.c_int64, C.c_int32, P]
     for name in EXPORTS:
         if name not in ("ngb_last_error",):
             getattr(L, name).restype = C.c_int
@@ -152,6 +154,14 @@ def _check(rc: int, h=None):
 
 def _ptr(a: Optional[np.ndarray]):
     return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def eval_step_factor(r: np.ndarray, k: int) -> np.ndarray:
+    """The GPU's Runge-Kutta step-size factor r^(-1/k) (k = 4 or 5) for each ratio in r."""
+    r = np.ascontiguousarray(r, dtype=np.float32)
+    out = np.zeros_like(r)
+    _check(load().ngb_eval_step_factor(_ptr(r), r.size, k, _ptr(out)))
+    return out
 
 
 def _poisson(p: W.Poisson) -> PoissonDrive:

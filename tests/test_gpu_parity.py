@@ -140,32 +140,79 @@ def test_deterministic_bf16_weights_bit_exact(ngb):
     assert np.array_equal(gt, ot) and np.array_equal(gi, oi)
 
 
+def _arrival_counts(csr, ids, steps, step, N):
+    """Synapses whose spike arrives at `step`, per target neuron (each adds one
+    term to the target's input sum of that step)."""
+    sp = csr["src_ptr"].astype(np.int64)
+    cnt = np.zeros(N, dtype=np.int64)
+    D = int(csr["delay"].max(initial=0))
+    sel = (steps >= step - D) & (steps < step)
+    for s_, t_ in zip(ids[sel], steps[sel]):
+        row = slice(sp[s_], sp[s_ + 1])
+        hit = csr["delay"][row].astype(np.int64) == step - t_
+        np.add.at(cnt, csr["tgt"][row][hit].astype(np.int64), 1)
+    return cnt
+
+
 def test_fp32_inputs_and_spikes_until_summation_order_decides(ngb):
+    """FP32 mode: per-step inputs within 1e-5 of the summed magnitudes; the GPU
+    state stays within a rounding bound of the oracle's, and the first step
+    whose spikes differ is one where summation order decides: every differing
+    neuron's pre-threshold potential, from the ORACLE's state, lies within
+    that bound of the threshold.  The bound follows the sums' rounding: an
+    input of n terms summed in any order in FP32 differs from another order by
+    at most (n - 1) 2^-23 sum|w|; it enters I, and V through the propagators
+    (I -> P11 I, V -> P22 V + P21 I), with one ulp per FP32 operation of the
+    update once the two states differ, and 4 ulp of the threshold for the test
+    itself."""
     spec = W.balanced_lif(n=1000, indegree=100, seed=1)
     g, o = _pair(ngb, spec)
+    N = 1000
     lif = spec.pops[0].params
     P = oracle.lif_propagators(lif.tau_m, lif.C_m, lif.tau_syn, spec.dt)
     theta = lif.V_th - lif.E_L
+    csr = o.csr()
+    ulp = lambda x: np.spacing(np.abs(x).astype(np.float32)).astype(np.float64)
+    eY = np.zeros(N)  # bounds of |y_gpu - y_oracle| and |I_gpu - I_oracle| before the step
+    eI = np.zeros(N)
     steps_same = 0
     for step in range(1000):
         gin = g.input(0, 0)
         oin, oabs, oex = o.input(0, 0)
         # per-step input: within 1e-5 of the summed magnitudes of the contributing weights
         assert np.all(np.abs(gin.astype(np.float64) - oex) <= 1e-5 * oabs + 1e-6), step
-        yg, Ig, rg = g.state("V_m") - lif.E_L, g.state("I_syn"), g.state("refractory")
+        Vo, Io, ro = o.state("V_m"), o.state("I_syn"), o.state("refractory")
+        yo = Vo - lif.E_L
+        Vg, Ig = g.state("V_m").astype(np.float64), g.state("I_syn").astype(np.float64)
+        # the state differences stay within the bound (the GPU reports V = y + E_L rounded to FP32: one
+        # more half ulp of V)
+        assert np.all(np.abs(Vg - Vo) <= eY + ulp(Vo)) and np.all(np.abs(Ig - Io) <= eI), step
+        oi_all, ot_all = o.spikes()
+        n_terms = _arrival_counts(csr, oi_all, ot_all, step, N)
+        delta = np.maximum(n_terms - 1, 0) * 2.0 ** -23 * oabs
+        y_pre = P["P22"] * yo + P["P21"] * Io + P["P20"] * lif.I_e
+        busy = (eY > 0) | (eI > 0)
+        e_pre = P["P22"] * eY + P["P21"] * eI + np.where(busy, 4 * ulp(np.maximum(np.abs(yo), np.abs(y_pre))), 0.0)
         g.simulate(1)
         o.simulate(1)
         gi, gt = g.spikes(t0=step, t1=step + 1)
-        oi, ot = o.spikes()
-        oi = oi[ot == step]
+        oi_new, ot_new = o.spikes()
+        oi = oi_new[ot_new == step]
         if not np.array_equal(np.sort(gi), np.sort(oi)):
-            # first divergence: every differing neuron crossed within rounding of threshold
+            # first divergence: every differing neuron sat within the rounding bound of threshold
             diff = np.setxor1d(gi, oi)
-            y_pre = P["P22"] * yg.astype(np.float64) + P["P21"] * Ig.astype(np.float64) + P["P20"] * lif.I_e
             near = np.abs(y_pre[diff] - theta)
-            assert np.all(rg[diff] == 0) and np.all(near < 1e-3), (step, diff, near)
+            assert np.all(ro[diff] == 0) and np.all(near <= e_pre[diff] + 4 * ulp(np.float32(theta))), \
+                (step, diff, near, e_pre[diff])
             break
         steps_same += 1
+        spiked = np.zeros(N, dtype=bool)
+        spiked[oi] = True
+        held = (ro > 0) | spiked  # V held or reset identically on both sides
+        I_new = P["P11"] * Io + oex
+        eY = np.where(held, 0.0, e_pre)
+        mag = np.maximum(np.maximum(np.abs(Io), np.abs(I_new)), np.abs(oex))
+        eI = P["P11"] * eI + delta + np.where((eI > 0) | (delta > 0), 3 * ulp(mag), 0.0)
     assert steps_same >= 50
 
 
@@ -197,6 +244,20 @@ def test_fp32_long_run_rates_and_cv(ngb):
         rg.append(a[0]); cg.append(a[1]); ro.append(b[0]); co.append(b[1])
     assert abs(np.mean(rg) - np.mean(ro)) <= 0.02 * np.mean(ro), (rg, ro)
     assert abs(np.mean(cg) - np.mean(co)) <= 0.05, (cg, co)
+
+
+@pytest.mark.parametrize("k", [4, 5])
+def test_adex_step_factor_bit_exact_against_oracle(ngb, k):
+    """The Runge-Kutta step-size factor of the FP32-state AdEx integration is
+    one exactly specified FP32 operation sequence: the kernel's and the
+    oracle's agree bit for bit over 60 binades and at the range edges."""
+    rng = np.random.default_rng(10 + k)
+    r = np.concatenate([np.float32(2.0) ** rng.uniform(-30, 30, 20000),
+                        rng.uniform(0.5, 2.0, 5000), [1e-31, 2.0 ** -100, 2.0 ** 100, np.inf, np.nan, 1.0]])
+    r = r.astype(np.float32)
+    got = ngb.eval_step_factor(r, k)
+    want = np.array([oracle.step_factor_root(float(x), k) for x in r], dtype=np.float32)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
 
 
 def _adex_single(I_e, ctl32=False):

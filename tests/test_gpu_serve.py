@@ -3,7 +3,9 @@ retired from the pools while others run in the same kernels.
 
 * Each served network's spikes equal the same network run alone through the
   plain path, bit for bit in deterministic mode, although networks join and
-  leave at different steps and reuse each other's pool ranges.
+  leave at different steps and reuse each other's pool ranges; the first and
+  the last admitted networks also equal the CPU oracle's run of the same
+  network, spike for spike.
 * FP32 mode: spike counts within tolerance of the plain path.
 * A commit that does not fit the pools fails with NGB_ERR_OOM and leaves the
   running networks untouched; it succeeds once space is freed.
@@ -11,6 +13,7 @@ retired from the pools while others run in the same kernels.
 import numpy as np
 import pytest
 
+import oracle
 from paper_2007_14236_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -49,6 +52,17 @@ def test_served_equals_alone_deterministic(mods):
         o = np.lexsort((ids, st))
         assert len(ids) > 0
         assert np.array_equal(d.steps, st[o]) and np.array_equal(d.ids, ids[o]), d.req.seed
+    # anchor to the oracle: served networks that joined late, after others had left (pool ranges
+    # reused), and the first one, spike for spike against the CPU oracle of the same network
+    late = sorted(done, key=lambda d: d.admit_s)
+    for d in (late[0], late[-2], late[-1]):
+        ora = oracle.OracleNet(W.request_net(d.req), deterministic=True)
+        ora.finalize()
+        ora.simulate(int(round(d.req.bio_time_ms / 0.1)))
+        oi, ot = ora.spikes()
+        o = np.lexsort((oi, ot))
+        assert len(oi) > 0
+        assert np.array_equal(d.steps, ot[o]) and np.array_equal(d.ids, oi[o]), d.req.seed
 
 
 def test_served_fp32_counts_close_to_alone(mods):

@@ -13,6 +13,10 @@
   two receptors of the exponential-conductance model): |dV| <= 1e-4 mV.
 * The FP32-state specification stays within the FP32 error budget of the
   FP64 reference on the same trace.
+* The FP32 specification's step-size factor r^(-1/k) (k = 5 after an
+  accepted sub-step, 4 after a rejected one): within 2e-4 of the exact power
+  over 60 binades, exact powers of two land on the cubic's constant term
+  times 2^-q, and the out-of-range conventions hold.
 * Alpha-function conductances (the paper's balanced network, Sec. 2.4): the
   conductance after one input of weight W follows W (t/tau) e^(1 - t/tau)
   (peak W at t = tau) at every grid point; the subthreshold response to inputs
@@ -186,6 +190,25 @@ def test_adex_subthreshold_three_inputs_match_dop853():
     assert np.abs(V_o - V_s).max() <= 1e-4
     # the inputs really moved V (depolarising, hyperpolarising, depolarising)
     assert V_o[60] > V_o[45] + 0.1 and V_o[170] < V_o[145] - 0.1 and V_o[260] > V_o[245] + 0.1
+
+
+@pytest.mark.parametrize("k", [4, 5])
+def test_step_factor_root_close_to_exact_power(k):
+    rng = np.random.default_rng(k)
+    r = np.concatenate([np.float32(2.0) ** rng.uniform(-30, 30, 4000), np.float32([1.0, 0.5, 2.0, 1.5])])
+    r = r.astype(np.float32)
+    got = np.array([oracle.step_factor_root(float(x), k) for x in r])
+    exact = r.astype(np.float64) ** (-1.0 / k)
+    assert np.max(np.abs(got / exact - 1.0)) < 2e-4
+    # r = 2^(k j): m = 1, s = 0, so the result is the cubic's constant term scaled by 2^-j exactly
+    c0 = oracle.step_factor_root(1.0, k)
+    assert abs(c0 - 1.0) < 2e-4
+    for j in range(-15, 16):
+        assert oracle.step_factor_root(2.0 ** (k * j), k) == c0 * 2.0 ** (-j)
+    # conventions outside [2^-100, 2^100)
+    assert oracle.step_factor_root(1e-31, k) == 2.0 ** 20
+    for x in (2.0 ** 100, float("inf"), float("nan")):
+        assert oracle.step_factor_root(x, k) == 0.0
 
 
 def test_adex_fp32_specification_close_to_fp64_reference():
