@@ -87,7 +87,8 @@ def _args():
                          "kernel (rings in shared memory, spikes exchanged through mailboxes)")
     ap.add_argument("--paper-n", type=str, default="1000000",
                     help="neurons of the paper's balanced network (comma-separated for a sweep)")
-    ap.add_argument("--paper-ce", type=int, default=800, help="excitatory in-degree of the paper's balanced network")
+    ap.add_argument("--paper-ce", type=str, default="800",
+                    help="excitatory in-degree(s) of the paper's balanced network (comma-separated for a sweep)")
     ap.add_argument("--workload", choices=["microcircuit", "small", "batched", "adex", "paper", "serve", "request",
                                            "precision", "validate", "stdp"],
                     default="microcircuit",
@@ -469,59 +470,68 @@ def run_stdp(a):
 
 def run_paper(a):
     """The paper's balanced network (AdEx with alpha-function conductances,
-    in-degree CE + CE/4 = 1000 by default), at one or several sizes: time per
-    biological second, synaptic events/s and the mean rate, beside the paper's
+    in-degree CE + CE/4) over sizes and in-degrees (Sec. 3.2: the size sweep
+    at 1,000 synapses per neuron, Fig. 10, and the synapse sweep at 30,000
+    neurons, Fig. 11): time per biological second, synaptic events/s and the
+    mean rate, each point beside the oracle on a bounded sample (the same
+    in-degree, 10,000 neurons, or 3,000 above 5,000 inputs per neuron; 100
+    steps after 500, scaled per neuron to the point's size); the paper's
     figures on one RTX 2080 Ti (about 70 s per biological second at 1e6
-    neurons x 1,000 synapses; 30.7 Hz)."""
+    neurons x 1,000 synapses; 30.7 Hz) as context."""
     from paper_2007_14236_gb300 import ngb, workloads as W
     sizes = [int(x) for x in a.paper_n.split(",")]
+    ces = [int(x) for x in str(a.paper_ce).split(",")]
     out = []
-    for n in sizes:
-        n_ex = (n * 4) // 5
-        spec = W.paper_balanced(n_ex=n_ex, ce=a.paper_ce, seed=1, weight_dtype=a.weights,
-                                rk_control_fp32=a.adex_ctl32)
-        t0 = time.perf_counter()
-        sim = ngb.from_spec(spec, drain_steps=a.sim_steps, record_spikes=False, delivery=a.delivery)
-        sim.finalize()
-        build_s = time.perf_counter() - t0
-        if a.mode == "auto":
-            sim.autotune(200)
-        sim.simulate(1000)  # 100 ms: past the onset transient
-        s0 = sim.stats()
-        t1 = time.perf_counter()
-        for _ in range(a.steps):
-            sim.simulate(a.sim_steps)
-        wall = time.perf_counter() - t1
-        s1 = sim.stats()
-        ms, nl = sim.simulate_profiled(100)
-        nn = s1["num_neurons"]
-        bio = a.steps * a.sim_steps * spec.dt * 1e-3
-        row = {"neurons": nn, "synapses": s1["num_synapses"], "build_s": build_s, "real_time_factor": wall / bio,
-               "events_per_s": (s1["events"] - s0["events"]) / wall,
-               "rate_hz": (s1["spikes"] - s0["spikes"]) / nn / bio,
-               "rk_substeps_per_neuron_step": (s1["rk_substeps"] - s0["rk_substeps"]) / nn / (bio / spec.dt * 1e3),
-               "us_per_launch": {"k_update_aeif": 1e3 * ms[1] / max(1, nl[1]),
-                                 "k_deliver": 1e3 * ms[2] / max(1, nl[2])},
-               "step_loop": LOOPS[s1["mode"]], "delivery": DELIVERY[s1["delivery"]]}
-        sim.close()
-        out.append(row)
-    line = {"workload": "paper_balanced_alpha", "in_degree": a.paper_ce + a.paper_ce // 4, "weights": a.weights,
-            "rk_control": "fp32" if a.adex_ctl32 else "fp64",
-            "bio_s_per_size": a.steps * a.sim_steps * 1e-4, "sizes": out,
+    for ce in ces:
+        for n in sizes:
+            n_ex = (n * 4) // 5
+            spec = W.paper_balanced(n_ex=n_ex, ce=ce, seed=1, weight_dtype=a.weights, rk_control_fp32=a.adex_ctl32)
+            t0 = time.perf_counter()
+            sim = ngb.from_spec(spec, drain_steps=a.sim_steps, record_spikes=False, delivery=a.delivery)
+            sim.finalize()
+            build_s = time.perf_counter() - t0
+            if a.mode == "auto":
+                sim.autotune(200)
+            sim.simulate(1000)  # 100 ms: past the onset transient
+            s0 = sim.stats()
+            t1 = time.perf_counter()
+            for _ in range(a.steps):
+                sim.simulate(a.sim_steps)
+            wall = time.perf_counter() - t1
+            s1 = sim.stats()
+            ms, nl = sim.simulate_profiled(100)
+            nn = s1["num_neurons"]
+            bio = a.steps * a.sim_steps * spec.dt * 1e-3
+            row = {"neurons": nn, "in_degree": ce + ce // 4, "synapses": s1["num_synapses"], "build_s": build_s,
+                   "real_time_factor": wall / bio, "events_per_s": (s1["events"] - s0["events"]) / wall,
+                   "rate_hz": (s1["spikes"] - s0["spikes"]) / nn / bio,
+                   "rk_substeps_per_neuron_step": (s1["rk_substeps"] - s0["rk_substeps"]) / nn / (bio / spec.dt * 1e3),
+                   "us_per_launch": {"k_update_aeif": 1e3 * ms[1] / max(1, nl[1]),
+                                     "k_deliver": 1e3 * ms[2] / max(1, nl[2])},
+                   "step_loop": LOOPS[s1["mode"]], "delivery": DELIVERY[s1["delivery"]]}
+            sim.close()
+            if not a.no_cpu_baseline:
+                import oracle
+                n_s = 10_000 if ce + ce // 4 <= 5000 else 3_000
+                small = W.paper_balanced(n_ex=(n_s * 4) // 5, ce=ce, seed=1, weight_dtype=a.weights)
+                o = oracle.OracleNet(small)
+                o.finalize()
+                o.simulate(500)
+                e0 = o.events
+                c0 = time.perf_counter()
+                o.simulate(100)
+                cw = time.perf_counter() - c0
+                row["cpu_baseline"] = {
+                    "s_per_bio_s": cw / 0.01 * nn / small.num_neurons(), "events_per_s": (o.events - e0) / cw,
+                    "cores": 1, "kind": "oracle",
+                    "sample": "%d neurons of the same network (same in-degree), 100 steps after 500, single-threaded "
+                              "C++ oracle on %s; scaled per neuron to %d neurons" % (small.num_neurons(), _cpu_info(),
+                                                                                   nn)}
+            print(json.dumps(row), flush=True)
+            out.append(row)
+    line = {"workload": "paper_balanced_alpha", "weights": a.weights, "rk_control": "fp32" if a.adex_ctl32 else "fp64",
+            "bio_s_per_point": a.steps * a.sim_steps * 1e-4, "points": out,
             "paper": {"s_per_bio_s_1e6_rtx2080ti": 70.0, "rate_hz": 30.7}}
-    if not a.no_cpu_baseline:
-        # the oracle on 10,000 neurons of the same network (same in-degree), 200 steps after 1,000
-        import oracle
-        small = W.paper_balanced(n_ex=8000, ce=a.paper_ce, seed=1, weight_dtype=a.weights)
-        o = oracle.OracleNet(small)
-        o.finalize()
-        o.simulate(1000)
-        c0 = time.perf_counter()
-        o.simulate(200)
-        cw = time.perf_counter() - c0
-        line["cpu_baseline"] = {"s_per_bio_s_per_1e6_neurons": cw / 0.02 * 100.0, "cores": 1, "kind": "oracle",
-                                "sample": "10,000 neurons of the same network, 200 steps after 1,000, single-threaded "
-                                          "C++ oracle on %s; scaled per neuron to 1e6 neurons" % _cpu_info()}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -386,7 +386,7 @@ bool owned_ready(ngb_sim* s) {
   if (s->own_tried) return false;
   s->own_tried = true;
   int bpsm = 0;
-  if (owned_max_blocks_per_sm(s->cfg.deterministic != 0, T, smem, &bpsm) != cudaSuccess || bpsm < 1) {
+  if (owned_max_blocks_per_sm(s->cfg.deterministic != 0, T, smem, 0, &bpsm) != cudaSuccess || bpsm < 1) {
     cudaGetLastError();
     return false;
   }
@@ -396,7 +396,7 @@ bool owned_ready(ngb_sim* s) {
     return false;
   }
   OwnedLayout L{};
-  cudaError_t e = owned_build(csr_of(s), s->src_syn, s->N, s->sms, (uint64_t)(free_b / 2 / sizeof(uint2)), &L,
+  cudaError_t e = owned_build(csr_of(s), s->src_syn, s->N, s->sms, (uint32_t)s->L, (uint64_t)(free_b / 2), &L,
                               s->stream);
   if (e != cudaSuccess || !L.items) {
     cudaGetLastError();
@@ -404,7 +404,7 @@ bool owned_ready(ngb_sim* s) {
   }
   s->allocs.push_back(L.items);
   s->allocs.push_back(L.pub);
-  s->dev_bytes += (size_t)L.G * L.S * sizeof(uint2) + (size_t)s->N * sizeof(uint64_t);
+  s->dev_bytes += (size_t)L.G * L.S * (L.wfmt ? 4 : 8) + (size_t)s->N * sizeof(uint64_t);
   if (s->dalloc(&s->own_mb, (size_t)4 * L.G * 8) != cudaSuccess ||
       s->dalloc(&s->own_ovf, (size_t)4 * L.G * T) != cudaSuccess) {
     cudaGetLastError();
@@ -437,6 +437,7 @@ cudaError_t launch_owned_chunk(ngb_sim* s, int64_t steps) {
     a.ring_N = s->N_cap;
     a.N = s->N;
     a.items = s->own.items;
+    a.wfmt = s->own.wfmt;
     a.pub = s->own.pub;
     a.src_syn = s->src_syn;
     a.mb = s->own_mb;

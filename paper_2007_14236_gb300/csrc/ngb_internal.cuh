@@ -580,7 +580,8 @@ struct PersistArgs {
 // (G tiles of S items each, padded per source) and the per-neuron spike entry
 // (C_s / 4) << 36 | off_s (0: no synapses).
 struct OwnedLayout {
-  uint2* items;
+  void* items;      // uint2 items (wfmt 0) or 4-byte items (wfmt 1 BF16, 2 FP16 weights)
+  int32_t wfmt;
   uint64_t* pub;
   uint64_t S;
   int G;
@@ -597,7 +598,8 @@ struct OwnedArgs {
   void* ring;            // [L][ring_N] FP32 (int64 fixed point in deterministic mode), one receptor
   int64_t ring_N;
   int64_t N;             // neurons
-  const uint2* items;    // [G][S]
+  const void* items;     // [G][S] items in format wfmt
+  int32_t wfmt;          // 0: {local | delay << 16, FP32 weight}; 1, 2: BF16, FP16 bits << 16 | delay << 10 | local
   const uint64_t* pub;   // [N]
   const uint64_t* src_syn;
   unsigned long long* mb;   // [4][G][4] mailboxes, by step mod 4
@@ -681,14 +683,16 @@ cudaError_t launch_step_pipe(const SegTable<LifSeg>& segs, int64_t upd_blocks, i
                              int64_t step_off, const Csr& csr, SpikeBuf sb, bool deliver_prev, bool pdl,
                              cudaStream_t st);
 // Target-owned loop: build the tile-major layout of a finalised CSR for G
-// tiles (out->items NULL when C_s or the layout exceeds its limits or
-// max_items; the caller frees pub and items), the dynamic shared memory of its
-// kernel, its occupancy, and one cooperative launch of a.steps steps (grid G,
-// mailboxes and overflow areas reset by the caller).
-cudaError_t owned_build(const Csr& csr, const uint64_t* src_syn, int64_t N, int G, uint64_t max_items,
+// tiles and a ring of L slots (4-byte items with BF16 / FP16 weights when the
+// tile holds at most 1,024 neurons and L <= 64, else 8-byte items; out->items
+// NULL when C_s or the layout exceeds its limits or max_bytes; the caller
+// frees pub and items), the dynamic shared memory of its kernel, its
+// occupancy, and one cooperative launch of a.steps steps (grid G, mailboxes
+// and overflow areas reset by the caller).
+cudaError_t owned_build(const Csr& csr, const uint64_t* src_syn, int64_t N, int G, uint32_t L, uint64_t max_bytes,
                         OwnedLayout* out, cudaStream_t st);
 size_t owned_smem_bytes(bool fixed, uint32_t L, uint32_t T, int n_seg, uint32_t n_thr);
-cudaError_t owned_max_blocks_per_sm(bool fixed, uint32_t T, size_t smem, int* out);
+cudaError_t owned_max_blocks_per_sm(bool fixed, uint32_t T, size_t smem, int wfmt, int* out);
 cudaError_t launch_owned(OwnedArgs a, bool fixed, int grid, cudaStream_t st);
 // clk[0] += n (clk[1] = clk[0] - 1); the ring scheme's step counters (both
 // the per-step and the pipelined ones) are cleared.

@@ -12,7 +12,10 @@
 // Synapses in tile-major order: the synapses of source s onto the neurons of
 // tile b are the items [b S + off_s, b S + off_s + c_bs) of one array, padded
 // to C_s = max_b c_bs items per source (S = sum of C_s), each item
-// {local target | delay << 16, FP32 weight} or the filler 0xFFFFFFFF.  The
+// {local target | delay << 16, FP32 weight} (8 bytes) or, with BF16 or FP16
+// weight storage, a tile of at most 1,024 neurons and delays below 64 steps,
+// weight bits << 16 | delay << 10 | local target (4 bytes, the storage
+// precision kept), or the filler 0xFFFFFFFF (all ones).  The
 // tile of a neuron is gid mod G, so every tile holds the same share of every
 // population and C_s stays close to the mean per-tile count.  A spike thus
 // needs no per-tile index lookup: the firing block publishes (off_s, C_s),
@@ -111,71 +114,92 @@ __device__ __forceinline__ void ring_add(void* ring_s, uint32_t idx, float w) {
   }
 }
 
+// Item formats: kW 0 {local target | delay << 16, FP32 weight} (uint2);
+// kW 1 / 2 BF16 / FP16 bits << 16 | delay << 10 | local target (uint32).
+template <int kW>
+struct OwnedItem {
+  using T = typename std::conditional<kW == 0, uint2, uint32_t>::type;
+  static __device__ __forceinline__ T filler() {
+    if constexpr (kW == 0) return make_uint2(kFiller, 0u);
+    else return kFiller;
+  }
+  static __device__ __forceinline__ bool valid(T x) {
+    if constexpr (kW == 0) return x.x != kFiller;
+    else return x != kFiller;
+  }
+  // ring index (slot of step t + delay, local target) and weight
+  static __device__ __forceinline__ uint32_t index(T x, int64_t t, const OwnedArgs& a) {
+    if constexpr (kW == 0) return ((uint32_t)(t + (x.x >> 16)) & a.L_mask) * a.T + (x.x & 0xFFFFu);
+    else return ((uint32_t)(t + ((x >> 10) & 63u)) & a.L_mask) * a.T + (x & 0x3FFu);
+  }
+  static __device__ __forceinline__ float weight(T x) {
+    if constexpr (kW == 0) return __uint_as_float(x.y);
+    else if constexpr (kW == 1) return __uint_as_float(x & 0xFFFF0000u);
+    else return __half2float(__ushort_as_half((unsigned short)(x >> 16)));
+  }
+};
+
+template <bool kFixed, int kW>
+__device__ __forceinline__ void add_item(typename OwnedItem<kW>::T x, const OwnedArgs& a, int64_t t, void* ring_s) {
+  using IT = OwnedItem<kW>;
+  if (IT::valid(x)) ring_add<kFixed>(ring_s, IT::index(x, t, a), IT::weight(x));
+}
+
 // Items of one spike entry (C_s items from b S + off_s), by the whole warp.
-template <bool kFixed>
+template <bool kFixed, int kW>
 __device__ __forceinline__ void deliver_entry_warp(uint64_t e, const OwnedArgs& a, uint64_t tile_base, int64_t t,
                                                    void* ring_s, int lane) {
+  using IT = OwnedItem<kW>;
   const uint64_t off = e & ((1ull << kOffBits) - 1);
   const uint32_t C = (uint32_t)(e >> kOffBits) * 4u;
-  const uint2* it = a.items + tile_base + off;
+  const typename IT::T* it = reinterpret_cast<const typename IT::T*>(a.items) + tile_base + off;
   uint32_t k = (uint32_t)lane;
   // two chunks of 32 items in flight per pass
   for (; k < C; k += 64) {
-    const uint2 x0 = __ldg(it + k);
-    const uint2 x1 = k + 32 < C ? __ldg(it + k + 32) : make_uint2(kFiller, 0u);
-    if (x0.x != kFiller)
-      ring_add<kFixed>(ring_s, ((uint32_t)(t + (x0.x >> 16)) & a.L_mask) * a.T + (x0.x & 0xFFFFu),
-                       __uint_as_float(x0.y));
-    if (x1.x != kFiller)
-      ring_add<kFixed>(ring_s, ((uint32_t)(t + (x1.x >> 16)) & a.L_mask) * a.T + (x1.x & 0xFFFFu),
-                       __uint_as_float(x1.y));
+    const typename IT::T x0 = __ldg(it + k);
+    const typename IT::T x1 = k + 32 < C ? __ldg(it + k + 32) : IT::filler();
+    add_item<kFixed, kW>(x0, a, t, ring_s);
+    add_item<kFixed, kW>(x1, a, t, ring_s);
   }
 }
 
 // The first two 32-item chunks of an entry (lane's items lane and lane + 32;
 // the filler past the entry's width), and the rest of it.
-__device__ __forceinline__ void load_head(uint64_t e, const OwnedArgs& a, uint64_t tile_base, int lane, uint2& x0,
-                                          uint2& x1) {
+template <int kW>
+__device__ __forceinline__ void load_head(uint64_t e, const OwnedArgs& a, uint64_t tile_base, int lane,
+                                          typename OwnedItem<kW>::T& x0, typename OwnedItem<kW>::T& x1) {
+  using IT = OwnedItem<kW>;
   const uint64_t off = e & ((1ull << kOffBits) - 1);
   const uint32_t C = (uint32_t)(e >> kOffBits) * 4u;
-  const uint2* it = a.items + tile_base + off;
-  x0 = (uint32_t)lane < C ? __ldg(it + lane) : make_uint2(kFiller, 0u);
-  x1 = (uint32_t)lane + 32 < C ? __ldg(it + lane + 32) : make_uint2(kFiller, 0u);
+  const typename IT::T* it = reinterpret_cast<const typename IT::T*>(a.items) + tile_base + off;
+  x0 = (uint32_t)lane < C ? __ldg(it + lane) : IT::filler();
+  x1 = (uint32_t)lane + 32 < C ? __ldg(it + lane + 32) : IT::filler();
 }
 
-template <bool kFixed>
-__device__ __forceinline__ void add_item(uint2 x, const OwnedArgs& a, int64_t t, void* ring_s) {
-  if (x.x != kFiller)
-    ring_add<kFixed>(ring_s, ((uint32_t)(t + (x.x >> 16)) & a.L_mask) * a.T + (x.x & 0xFFFFu), __uint_as_float(x.y));
-}
-
-template <bool kFixed>
+template <bool kFixed, int kW>
 __device__ __forceinline__ void deliver_entry_tail(uint64_t e, const OwnedArgs& a, uint64_t tile_base, int64_t t,
                                                    void* ring_s, int lane) {
+  using IT = OwnedItem<kW>;
   const uint64_t off = e & ((1ull << kOffBits) - 1);
   const uint32_t C = (uint32_t)(e >> kOffBits) * 4u;
-  const uint2* it = a.items + tile_base + off;
-  for (uint32_t k = 64u + (uint32_t)lane; k < C; k += 32) add_item<kFixed>(__ldg(it + k), a, t, ring_s);
+  const typename IT::T* it = reinterpret_cast<const typename IT::T*>(a.items) + tile_base + off;
+  for (uint32_t k = 64u + (uint32_t)lane; k < C; k += 32) add_item<kFixed, kW>(__ldg(it + k), a, t, ring_s);
 }
 
 // The same by one thread (entries beyond the shared-memory list).
-template <bool kFixed>
+template <bool kFixed, int kW>
 __device__ __forceinline__ void deliver_entry_thread(uint64_t e, const OwnedArgs& a, uint64_t tile_base, int64_t t,
                                                      void* ring_s) {
+  using IT = OwnedItem<kW>;
   const uint64_t off = e & ((1ull << kOffBits) - 1);
   const uint32_t C = (uint32_t)(e >> kOffBits) * 4u;
-  const uint2* it = a.items + tile_base + off;
-  for (uint32_t k = 0; k < C; ++k) {
-    const uint2 x = __ldg(it + k);
-    if (x.x != kFiller)
-      ring_add<kFixed>(ring_s, ((uint32_t)(t + (x.x >> 16)) & a.L_mask) * a.T + (x.x & 0xFFFFu),
-                       __uint_as_float(x.y));
-  }
+  const typename IT::T* it = reinterpret_cast<const typename IT::T*>(a.items) + tile_base + off;
+  for (uint32_t k = 0; k < C; ++k) add_item<kFixed, kW>(__ldg(it + k), a, t, ring_s);
 }
 
 }  // namespace
 
-template <bool kFixed, int kNpt>
+template <bool kFixed, int kNpt, int kW>
 __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
   using RW = typename std::conditional<kFixed, long long, float>::type;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -363,7 +387,7 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
         } else if (pl != 0) {
           const int pos = atomicAdd(&s_nid[q], 1);
           if (pos < kIdsCap) s_ids[q * kIdsCap + pos] = pl;
-          else deliver_entry_thread<kFixed>(pl, a, tile_base, tr, ring_s);
+          else deliver_entry_thread<kFixed, kW>(pl, a, tile_base, tr, ring_s);
         }
       }
     }
@@ -395,7 +419,7 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
           const uint64_t pl = x & kPayloadMask;
           const int pos = atomicAdd(&s_nid[q], 1);
           if (pos < kIdsCap) s_ids[q * kIdsCap + pos] = pl;
-          else deliver_entry_thread<kFixed>(pl, a, tile_base, tr, ring_s);
+          else deliver_entry_thread<kFixed, kW>(pl, a, tile_base, tr, ring_s);
         }
       }
       __syncthreads();
@@ -424,9 +448,9 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
     const uint64_t* ids = s_ids + par * kIdsCap;
     const uint64_t e0 = warp < n ? ids[warp] : 0ull;
     const uint64_t e1 = warp + kWarps < n ? ids[warp + kWarps] : 0ull;
-    uint2 x[4];
-    load_head(e0, a, tile_base, lane, x[0], x[1]);
-    load_head(e1, a, tile_base, lane, x[2], x[3]);
+    typename OwnedItem<kW>::T x[4];
+    load_head<kW>(e0, a, tile_base, lane, x[0], x[1]);
+    load_head<kW>(e1, a, tile_base, lane, x[2], x[3]);
     // ------------------------------------------------------------ update
     const uint32_t slot = (uint32_t)t & a.L_mask;
 #pragma unroll
@@ -459,11 +483,11 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
     }
     // ------------------------------------------------------------ deliver the spikes of step r
 #pragma unroll
-    for (int q = 0; q < 4; ++q) add_item<kFixed>(x[q], a, t, ring_s);
-    deliver_entry_tail<kFixed>(e0, a, tile_base, t, ring_s, lane);
-    deliver_entry_tail<kFixed>(e1, a, tile_base, t, ring_s, lane);
+    for (int q = 0; q < 4; ++q) add_item<kFixed, kW>(x[q], a, t, ring_s);
+    deliver_entry_tail<kFixed, kW>(e0, a, tile_base, t, ring_s, lane);
+    deliver_entry_tail<kFixed, kW>(e1, a, tile_base, t, ring_s, lane);
     for (int i = warp + 2 * kWarps; i < n; i += kWarps)
-      deliver_entry_warp<kFixed>(ids[i], a, tile_base, t, ring_s, lane);
+      deliver_entry_warp<kFixed, kW>(ids[i], a, tile_base, t, ring_s, lane);
     // ------------------------------------------------------------ entries of step r + 1
     if (more) {
       if (!gather(r + 1, par ^ 1)) aborted = true;  // ends with a barrier: slot t + 1 complete
@@ -499,15 +523,22 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
 
 namespace {
 
-void* owned_kernel(bool fixed, int npt) {
+template <int kW>
+void* owned_kernel_w(bool fixed, int npt) {
   if (fixed) {
-    if (npt == 1) return reinterpret_cast<void*>(&k_owned<true, 1>);
-    if (npt == 2) return reinterpret_cast<void*>(&k_owned<true, 2>);
-    return reinterpret_cast<void*>(&k_owned<true, 4>);
+    if (npt == 1) return reinterpret_cast<void*>(&k_owned<true, 1, kW>);
+    if (npt == 2) return reinterpret_cast<void*>(&k_owned<true, 2, kW>);
+    return reinterpret_cast<void*>(&k_owned<true, 4, kW>);
   }
-  if (npt == 1) return reinterpret_cast<void*>(&k_owned<false, 1>);
-  if (npt == 2) return reinterpret_cast<void*>(&k_owned<false, 2>);
-  return reinterpret_cast<void*>(&k_owned<false, 4>);
+  if (npt == 1) return reinterpret_cast<void*>(&k_owned<false, 1, kW>);
+  if (npt == 2) return reinterpret_cast<void*>(&k_owned<false, 2, kW>);
+  return reinterpret_cast<void*>(&k_owned<false, 4, kW>);
+}
+
+void* owned_kernel(bool fixed, int npt, int wfmt) {
+  if (wfmt == 1) return owned_kernel_w<1>(fixed, npt);
+  if (wfmt == 2) return owned_kernel_w<2>(fixed, npt);
+  return owned_kernel_w<0>(fixed, npt);
 }
 
 // ----------------------------------------------------------------- layout
@@ -551,7 +582,8 @@ __device__ __forceinline__ float weight_at(const void* w, int wdtype, uint64_t j
 __global__ void k_owned_fill(const uint64_t* __restrict__ src_syn, const uint32_t* __restrict__ src_grp,
                              const uint64_t* __restrict__ grp_start, const uint16_t* __restrict__ grp_delay,
                              const uint32_t* __restrict__ tgt, const void* w, int wdtype, int64_t N, int G,
-                             uint64_t S, const unsigned long long* __restrict__ off, uint32_t* cursor, uint2* items) {
+                             uint64_t S, const unsigned long long* __restrict__ off, uint32_t* cursor, void* items,
+                             int wfmt) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -562,7 +594,13 @@ __global__ void k_owned_fill(const uint64_t* __restrict__ src_syn, const uint32_
         const uint32_t target = tgt[j] & kTgtMask;
         const uint32_t tile = target % (uint32_t)G, lt = target / (uint32_t)G;
         const uint32_t pos = atomicAdd(cursor + (uint64_t)s * G + tile, 1u);
-        items[(uint64_t)tile * S + off[s] + pos] = make_uint2(lt | (d << 16), __float_as_uint(weight_at(w, wdtype, j)));
+        const uint64_t at = (uint64_t)tile * S + off[s] + pos;
+        if (wfmt == 0) {
+          reinterpret_cast<uint2*>(items)[at] = make_uint2(lt | (d << 16), __float_as_uint(weight_at(w, wdtype, j)));
+        } else {  // the 16 storage bits of the weight, as stored
+          const uint32_t wb = reinterpret_cast<const uint16_t*>(w)[j];
+          reinterpret_cast<uint32_t*>(items)[at] = wb << 16 | d << 10 | lt;
+        }
       }
     }
   }
@@ -570,9 +608,13 @@ __global__ void k_owned_fill(const uint64_t* __restrict__ src_syn, const uint32_
 
 }  // namespace
 
-cudaError_t owned_build(const Csr& csr, const uint64_t* src_syn, int64_t N, int G, uint64_t max_items,
+cudaError_t owned_build(const Csr& csr, const uint64_t* src_syn, int64_t N, int G, uint32_t L, uint64_t max_bytes,
                         OwnedLayout* out, cudaStream_t st) {
   *out = OwnedLayout{};
+  const int64_t T = (N + G - 1) / G;
+  const int wfmt = (csr.wdtype == 1 || csr.wdtype == 2) && T <= 1024 && L <= 64 ? csr.wdtype : 0;
+  const size_t ib = wfmt ? 4 : 8;
+  const uint64_t max_items = max_bytes / ib;
   uint32_t* cnt = nullptr;
   unsigned long long *width = nullptr, *off = nullptr;
   void* tmp = nullptr;
@@ -608,21 +650,21 @@ cudaError_t owned_build(const Csr& csr, const uint64_t* src_syn, int64_t N, int 
   bool fits = e == cudaSuccess && wmax / 4 < (1ull << (kStampShift - kOffBits)) && S < (1ull << kOffBits) &&
               (uint64_t)G * S <= max_items;
   if (fits) {
-    e = cudaMalloc(&out->items, (size_t)((uint64_t)G * S > 0 ? (uint64_t)G * S : 1) * sizeof(uint2));
+    e = cudaMalloc(&out->items, (size_t)((uint64_t)G * S > 0 ? (uint64_t)G * S : 1) * ib);
     if (e == cudaErrorMemoryAllocation) {
       cudaGetLastError();
       fits = false;
       e = cudaSuccess;
     }
   }
-  if (fits && e == cudaSuccess) e = cudaMemsetAsync(out->items, 0xFF, (size_t)G * S * sizeof(uint2), st);
+  if (fits && e == cudaSuccess) e = cudaMemsetAsync(out->items, 0xFF, (size_t)G * S * ib, st);
   if (fits && e == cudaSuccess) {
     k_owned_pub<<<grid, 256, 0, st>>>(N, width, off, out->pub);
     e = cudaGetLastError();
   }
   if (fits && e == cudaSuccess) {
     k_owned_fill<<<grid, 256, 0, st>>>(src_syn, csr.src_grp, csr.grp_start, csr.grp_delay, csr.tgt, csr.w,
-                                       csr.wdtype, N, G, S, off, cnt, out->items);
+                                       csr.wdtype, N, G, S, off, cnt, out->items, wfmt);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -639,6 +681,7 @@ cudaError_t owned_build(const Csr& csr, const uint64_t* src_syn, int64_t N, int 
   out->S = S;
   out->G = G;
   out->max_width = (uint32_t)wmax;
+  out->wfmt = wfmt;
   return cudaSuccess;
 }
 
@@ -660,7 +703,7 @@ cudaError_t launch_owned(OwnedArgs a, bool fixed, int grid, cudaStream_t st) {
   if (a.T > 4 * kOwnedBlock || grid > kMaxTiles || grid * kMbWords > kPollWords * kOwnedBlock ||
       a.steps > kMaxOwnedSteps)
     return cudaErrorInvalidValue;
-  void* k = owned_kernel(fixed, npt);
+  void* k = owned_kernel(fixed, npt, a.wfmt);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -677,9 +720,9 @@ cudaError_t launch_owned(OwnedArgs a, bool fixed, int grid, cudaStream_t st) {
   return cudaLaunchKernelExC(&cfg, k, args);
 }
 
-cudaError_t owned_max_blocks_per_sm(bool fixed, uint32_t T, size_t smem, int* out) {
+cudaError_t owned_max_blocks_per_sm(bool fixed, uint32_t T, size_t smem, int wfmt, int* out) {
   const int npt = T <= kOwnedBlock ? 1 : (T <= 2 * kOwnedBlock ? 2 : 4);
-  void* k = owned_kernel(fixed, npt);
+  void* k = owned_kernel(fixed, npt, wfmt);
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k, kOwnedBlock, smem);

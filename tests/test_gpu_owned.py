@@ -211,3 +211,28 @@ def test_autotune_cache_round_trip(ngb, tmp_path):
     c.simulate(400)
     ref.simulate(400)
     assert np.array_equal(c.spikes()[0], ref.spikes()[0]) and np.array_equal(c.spikes()[1], ref.spikes()[1])
+
+
+def test_target_owned_16bit_items_bit_exact_against_oracle(ngb):
+    """BF16 and FP16 weights travel as 4-byte items (weight bits, delay and
+    local target in one word): spike trains bit-exact against the oracle in
+    deterministic mode, and the item layout half the bytes of the FP32 one."""
+    import oracle
+    held = {}
+    for wd in ("bf16", "fp16", "fp32"):
+        spec = W.microcircuit(scale=0.05, seed=8, keep_indegree=False, weight_dtype=wd)
+        b = _owned(ngb, spec, deterministic=True, delivery="ring")
+        assert b.stats()["mode"] == 6
+        o = oracle.OracleNet(spec, deterministic=True)
+        o.finalize()
+        b.simulate(400)
+        o.simulate(400)
+        bi, bt = b.spikes()
+        oi, ot = o.spikes()
+        assert len(oi) > 100
+        assert np.array_equal(bt, ot) and np.array_equal(bi, oi), wd
+        held[wd] = b.stats()["device_bytes"]
+        b.close()
+    # same network: the 16-bit handles hold 2-byte weights and 4-byte items against 4 + 8
+    K = W.microcircuit(scale=0.05, seed=8, keep_indegree=False).num_synapses()
+    assert held["fp32"] - held["bf16"] > 2 * K
