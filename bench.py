@@ -57,6 +57,12 @@ NCU_TRAFFIC = {("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "gra
                # one launch = one bench step (10,000 simulation steps); mean of four steady-state launches
                ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "target_owned", "k_owned"): 16018345984}
 SIM_STEPS_PER_BENCH_STEP = 10_000  # 1 s of biological time at dt = 0.1 ms
+# AdEx update (exponential conductances): FP32 and FP64 operations per Runge-Kutta attempt, counted by ncu
+# (FADD + FMUL + 2 FFMA; DADD + DMUL + 2 DFMA) over one launch on the 2e5-neuron network of the same recipe,
+# 2.0 attempts per neuron and step: 1.85e8 FP32 and 1.0e6 FP64 operations for 4e5 attempts
+ADEX_FP32_FLOPS_PER_ATTEMPT = 462.5
+ADEX_FP64_FLOPS_PER_ATTEMPT = 2.5
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x (multiply + add) x maximum SM clock
 
 
 def _args():
@@ -365,7 +371,17 @@ def adex_variant(n: int, sim_steps: int, steps: int, ctl32: bool = False, delive
     bio = steps * sim_steps * 1e-4
     ms, nl = sim.simulate_profiled(200)
     sim.close()
+    # ALU roofline of the update kernel: FP32 operations per Runge-Kutta attempt of an exponential-conductance
+    # neuron (ncu: FADD + FMUL + 2 FFMA per attempt of the update kernel on this network, 2e5 neurons), against
+    # the FP32 peak from the unit counts and the clock (152 SMs x 128 FP32 lanes x 2 x 2.07 GHz = 80.5 TFLOP/s)
+    attempts = (s1["rk_substeps"] - s0["rk_substeps"]) / (steps * sim_steps)
+    us_upd = 1e3 * ms[1] / max(1, nl[1])
+    ach = attempts * ADEX_FP32_FLOPS_PER_ATTEMPT / (us_upd * 1e-6) / 1e12
     out = {"workload": "balanced_adex_%d" % n, "neurons": s1["num_neurons"], "synapses": s1["num_synapses"],
+           "roofline": {"bound": "alu", "kernel": "k_update_aeif", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                        "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "peak_source": "derived",
+                        "fp32_flops_per_rk_attempt": ADEX_FP32_FLOPS_PER_ATTEMPT,
+                        "fp64_flops_per_rk_attempt": ADEX_FP64_FLOPS_PER_ATTEMPT, "rk_attempts_per_step": attempts},
            "build_s": build_s, "real_time_factor": wall / bio, "bio_s": bio,
            "spikes": s1["spikes"] - s0["spikes"], "events": s1["events"] - s0["events"],
            "rate_hz": (s1["spikes"] - s0["spikes"]) / n / bio,
@@ -1022,7 +1038,8 @@ def main():
         x = adex_variant(1_000_000, 10_000, 1, False, a.delivery, a.mode, cpu=not a.no_cpu_baseline)
         line["variants"]["adex_1e6_config2"] = {
             k: x[k] for k in ("real_time_factor", "rate_hz", "rk_substeps_per_neuron_step", "us_per_launch",
-                              "step_loop", "delivery", "rk_control", "cpu_baseline", "neurons", "synapses")}
+                              "step_loop", "delivery", "rk_control", "cpu_baseline", "neurons", "synapses",
+                              "roofline")}
 
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a.weights, a.cpu_sample_steps)

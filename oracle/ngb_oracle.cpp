@@ -930,11 +930,12 @@ int32_t ora_simulate(ora_net* net, int64_t steps) {
             net->ring_exact[(size_t)idx] = 0.0;
           }
         }
-        // Poisson drive of step t: k ~ Poisson(lambda), adds k * w_ext
+        // Poisson drive of step t: k ~ Poisson(lambda), adds k * w_ext; the uniform word of
+        // instance-local step t is word t mod 4 of the Philox block with index t div 4
         if (P.lambda > 0.0) {
           uint32_t r[4];
-          draw(seed, (uint64_t)t, kPoisson, 0, (uint32_t)(P.local_off + k), r);
-          const int kp = poisson_inversion(P.lambda, r[0]);
+          draw(seed, (uint64_t)t >> 2, kPoisson, 0, (uint32_t)(P.local_off + k), r);
+          const int kp = poisson_inversion(P.lambda, r[(uint64_t)t & 3u]);
           const int rc = P.model == 0 ? 0 : P.aeif.prec_rcpt;
           const float add = (float)kp * P.w_ext;
           in[rc] = in[rc] + add;

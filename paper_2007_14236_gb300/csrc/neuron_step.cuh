@@ -5,8 +5,9 @@
 //    (FP32, or int64 fixed point in units of 2^-32 converted once to FP32).
 //  * poisson_count: the Poisson drive of the step (Sec. 2.1 Poisson
 //    generator): the number of inverse-CDF thresholds ceil(F(k) * 2^32) not
-//    above one Philox word (key = instance seed, counter = (instance-local
-//    step, -, purpose 4, instance-local neuron)).
+//    above one Philox word: word tl mod 4 of the block with key = instance
+//    seed, counter = (instance-local step tl div 4, -, purpose 4,
+//    instance-local neuron), so one block serves four consecutive steps.
 //  * lif_step: exact integration of Eqs. 1-2 over one step (Sec. 2.1),
 //    threshold, reset and refractory count, with round-to-nearest intrinsics
 //    so that no FMA contraction changes the result.
@@ -53,12 +54,25 @@ __device__ __forceinline__ void ring_clear(void* ring, uint64_t idx) {
   else reinterpret_cast<float*>(ring)[idx] = 0.0f;
 }
 
+// The Philox block of the Poisson words of steps 4q .. 4q + 3.
+__device__ __forceinline__ U4 poisson_block(uint64_t seed, uint64_t q, uint32_t sid) {
+  return draw4(seed, q, kPurPoisson, 0u, sid);
+}
+
+__device__ __forceinline__ uint32_t poisson_word(const U4& r, int64_t tl) {
+  const uint32_t k = (uint32_t)tl & 3u;
+  return k == 0 ? r.x : k == 1 ? r.y : k == 2 ? r.z : r.w;
+}
+
+__device__ __forceinline__ uint32_t poisson_from_word(uint32_t x, const uint32_t* thr, uint32_t n_thr) {
+  uint32_t kp = 0;
+  while (kp < n_thr && x >= thr[kp]) ++kp;
+  return kp;
+}
+
 __device__ __forceinline__ uint32_t poisson_count(uint64_t seed, int64_t tl, uint32_t sid, const uint32_t* thr,
                                                   uint32_t n_thr) {
-  const U4 r = draw4(seed, (uint64_t)tl, kPurPoisson, 0u, sid);
-  uint32_t kp = 0;
-  while (kp < n_thr && r.x >= thr[kp]) ++kp;
-  return kp;
+  return poisson_from_word(poisson_word(poisson_block(seed, (uint64_t)tl >> 2, sid), tl), thr, n_thr);
 }
 
 // One exact-integration step of a LIF neuron in two parts.  V is propagated

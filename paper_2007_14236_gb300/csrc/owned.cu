@@ -294,6 +294,11 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
     __syncthreads();
   };
   unsigned long long nev = 0;  // synaptic events of this thread's spikes
+  // The Poisson words of four consecutive steps come from one Philox block:
+  // each neuron keeps its current block in registers and draws the next one
+  // every fourth step.
+  U4 pblk[kNpt];
+  bool pblk_ok = false;
   auto draw_counts = [&](int64_t t) {
 #pragma unroll
     for (int j = 0; j < kNpt; ++j) {
@@ -302,10 +307,13 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
       const LifSeg& sg = s_seg[si[j]];
       if (sg.n_thr > 0) {
         const int64_t gid = (int64_t)(tid + j * kOwnedBlock) * G + b;
-        kp[j] = poisson_count(sg.seed, t - sg.t0, sg.local_off + (uint32_t)(gid - sg.offset), s_thr + sg.thr_off,
-                              sg.n_thr);
+        const int64_t tl = t - sg.t0;
+        if (!pblk_ok || (tl & 3) == 0)
+          pblk[j] = poisson_block(sg.seed, (uint64_t)tl >> 2, sg.local_off + (uint32_t)(gid - sg.offset));
+        kp[j] = poisson_from_word(poisson_word(pblk[j], tl), s_thr + sg.thr_off, sg.n_thr);
       }
     }
+    pblk_ok = true;
   };
   draw_counts(t0);
   const int nwords = G * kMbWords;
