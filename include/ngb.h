@@ -250,6 +250,10 @@ typedef struct {
   int64_t launch_grid;  /* blocks of the delivery kernel (modes 0, 3, 5, 7) or of the persistent kernel
                            (modes 1, 4, 6) */
   int64_t delivery;     /* delivery scheme in use: 1 ring, 2 spike buffer */
+  int64_t hot_steps;    /* AdEx neuron steps run by the hot-list kernel (per-step kernels: a neuron whose
+                           step ended above V_T + c Delta_T runs its next step, whole, in a warp of such
+                           neurons beside the update kernel; c = 4, environment NGB_AEIF_HOT = c, 0 off;
+                           the arithmetic of each step is the same either way) */
 } ngb_stats;
 
 typedef struct ngb_sim ngb_sim;
@@ -360,7 +364,8 @@ NGB_API int ngb_simulate_profiled(ngb_sim* sim, int64_t steps, double* kernel_ms
  * persistent kernel (its tile-major synapse layout, about 1.5 - 2 times the
  * CSR's bytes, is built on first use; deterministic mode gives bit-identical
  * results to every other loop); at step 0 with delivery AUTO, under both delivery
- * schemes (ngb_stats.delivery).  Each candidate is
+ * schemes (ngb_stats.delivery); for AdEx networks, the chosen per-step or
+ * pipelined loop also without the hot lists (ngb_stats.hot_steps).  Each candidate is
  * timed over trial_steps steps (0 = 500); the simulation state is saved
  * before and restored after the trials, so the simulation does not advance.
  * The fastest candidate is kept (see ngb_stats.mode / launch_grid).  With the

@@ -126,11 +126,144 @@ __device__ __forceinline__ void unpack_rec(const uint4* q, St& y, RkPos& r, floa
 
 }  // namespace
 
+// List neuron gid (segment seg) as hot for step t + 1 when h: warp-aggregated
+// append to the model's list of that step's parity, then the tag.  A full
+// list drops the entry and leaves the tag, so the neuron stays with the
+// neuron blocks (a list holds every neuron once, so it cannot fill).
+__device__ __forceinline__ void hot_append(bool h, uint32_t gid, uint32_t seg, const SpikeBuf& sb, int kind,
+                                           int64_t t) {
+  const unsigned full = 0xffffffffu;
+  const unsigned b = __ballot_sync(full, h);
+  if (b == 0 || !sb.htag || !sb.hot[kind]) return;
+  const int q = (int)((uint64_t)(t + 1) % 3u);
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(sb.hcnt + 3 * kind + q, (unsigned long long)__popc(b));
+  base = __shfl_sync(full, base, 0);
+  if (h) {
+    const unsigned long long pos = base + __popc(b & ((1u << lane) - 1u));
+    if (pos < (unsigned long long)sb.hot_cap) {
+      sb.hot[kind][(uint64_t)q * (uint64_t)sb.hot_cap + pos] = make_uint2(gid, seg);
+      sb.htag[gid] = (uint32_t)(t + 1);
+    }
+  }
+}
+
+// One neuron's step t: the receptor slots (read and zeroed), the Poisson
+// drive (thresholds thr of its segment), then the integration with at most
+// `budget` attempts (0: to the end of the step).  A finished step stores the
+// state; an unfinished one is packed into rec for the finishing kernel.
+template <bool kFixed, int kM>
+__device__ __forceinline__ bool aeif_neuron_step(const AeifSeg& p, uint32_t gid, int64_t k, uint32_t seg,
+                                                 const uint32_t* thr, int64_t t, Ring ring, const AeifState& S,
+                                                 int n_ports, St& y, float h0, int budget, uint32_t& nspk,
+                                                 unsigned long long& nsub, uint4* rec, const SpikeBuf& sb) {
+  const uint64_t slot = (uint64_t)(t & ring.L_mask);
+  const uint64_t i0 = (slot * (uint64_t)ring.R) * (uint64_t)ring.N + gid;
+  float4 in = make_float4(0.f, 0.f, 0.f, 0.f);
+  in.x = ring_take<kFixed, false>(ring.p, i0);
+  in.y = ring_take<kFixed, false>(ring.p, i0 + (uint64_t)ring.N);
+  if (kM == kAeifBeta) {
+    if (n_ports > 2) in.z = ring_take<kFixed, false>(ring.p, i0 + 2 * (uint64_t)ring.N);
+    if (n_ports > 3) in.w = ring_take<kFixed, false>(ring.p, i0 + 3 * (uint64_t)ring.N);
+  }
+  if (p.n_thr > 0) {
+    const uint32_t kp = poisson_count(p.seed, t - p.t0, p.local_off + (uint32_t)k, thr, p.n_thr);
+    const float add = __fmul_rn((float)kp, p.w_ext);
+    switch (p.prec_rcpt) {
+      case 0: in.x = __fadd_rn(in.x, add); break;
+      case 1: in.y = __fadd_rn(in.y, add); break;
+      case 2: in.z = __fadd_rn(in.z, add); break;
+      default: in.w = __fadd_rn(in.w, add); break;
+    }
+  }
+  RkPos r{(double)h0, 0.0, 0};
+  bool cap_hit = false;
+  const bool done = aeif_advance<kM>(p, y, r, budget, in, nspk, nsub, cap_hit);
+  if (cap_hit) atomicOr(sb.err, kErrSubstepCap);
+  if (done) store_state<kM>(S, gid, n_ports, y, (float)r.h);
+  else pack_rec<kM>(rec, gid, seg, nspk, y, r, in);
+  return done;
+}
+
+// The warp's end of step t (every lane takes part): unfinished neurons to the
+// deferred list, finished ones above V_hot to the next step's hot list, the
+// attempt statistics, and the spike compaction.
+template <bool kFixed, int kMode, int kM>
+__device__ __forceinline__ void aeif_warp_end(bool on, bool done, const uint4* rec, uint32_t gid, uint32_t seg,
+                                              uint32_t nspk, unsigned long long nsub, bool hot_next, uint4 meta,
+                                              int64_t t, const Csr& csr, Ring ring, const SpikeBuf& sb) {
+  constexpr int kW = kRecWords<kM>;
+  defer_write<kW>(on && !done, rec, sb, kM, t);
+  hot_append(on && done && hot_next, gid, seg, sb, kM, t);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nsub += __shfl_xor_sync(0xffffffffu, nsub, o);
+  if ((threadIdx.x & 31) == 0 && nsub) atomicAdd(sb.substeps, nsub);
+  const bool spk = on && done && nspk > 0;
+  const uint32_t mult = nspk > 63u ? 63u : nspk;
+  if (kMode == kEmitAge) emit_spikes_age(spk, gid, mult, t, csr, sb);
+  else if (kMode == kEmitPipe)
+    emit_spikes_pipe<kFixed>(spk, gid, mult, t, meta, spk ? __ldg(csr.src_age + gid) : make_uint2(0, 0), csr, ring,
+                             sb);
+  else emit_spikes(spk, gid, mult, t, meta, sb);
+}
+
+// The neurons listed hot for step t, 32 to a warp, whole steps (no attempt
+// budget), in a kernel that runs beside the update kernel of the same step
+// (which skips them): their tens of attempts start with the step instead of
+// after it.  The previous step's kernels have completed before this one.
+template <bool kFixed, int kMode, int kM>
+__global__ void __launch_bounds__(kAeifBlock) k_aeif_hot(const __grid_constant__ SegTable<AeifSeg> T,
+                                                         const uint32_t* __restrict__ thr, const AeifState S,
+                                                         Ring ring, const int64_t* clk, int64_t step_off,
+                                                         const Csr csr, SpikeBuf sb) {
+  constexpr bool kAge = kMode == kEmitAge;
+  constexpr int kW = kRecWords<kM>;
+  const int64_t t = clk[0] + step_off;
+  const int q = (int)((uint64_t)t % 3u);
+  unsigned long long n = sb.hcnt[3 * kM + q];
+  if (n > (unsigned long long)sb.hot_cap) n = (unsigned long long)sb.hot_cap;
+  const uint2* __restrict__ list = sb.hot[kM] + (uint64_t)q * (uint64_t)sb.hot_cap;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * kAeifBlock + threadIdx.x) >> 5;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * kAeifBlock) >> 5;
+  for (unsigned long long base = warp * 32; base < n; base += nwarps * 32) {
+    const unsigned long long i = base + lane;
+    uint2 e = make_uint2(0, 0);
+    bool on = i < n;
+    if (on) {
+      e = list[i];
+      on = sb.htag[e.x] == (uint32_t)t;  // listed for this step (else a stale entry)
+    }
+    uint32_t nspk = 0;
+    unsigned long long nsub = 0;
+    bool hot_next = false;
+    uint4 meta = make_uint4(0, 0, 0, 0);
+    if (on) {
+      const AeifSeg p = T.dev[e.y];
+      const int n_ports = kM == kAeifBeta ? p.n_ports : 2;
+      if (!kAge) meta = __ldg(csr.src_meta + e.x);
+      St y{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float h0 = 0.f;
+      uint4 rec[kW];  // unused: without a budget every step finishes
+      load_state<kM>(S, e.x, n_ports, y, h0);
+      aeif_neuron_step<kFixed, kM>(p, e.x, (int64_t)e.x - p.offset, e.y, thr + p.thr_off, t, ring, S, n_ports, y, h0,
+                                   0, nspk, nsub, rec, sb);
+      hot_next = y.V > p.V_hot;
+    }
+    const unsigned ran = __ballot_sync(0xffffffffu, on);
+    if (lane == 0 && ran) atomicAdd(sb.hot_steps, (unsigned long long)__popc(ran));
+    aeif_warp_end<kFixed, kMode, kM>(on, true, nullptr, e.x, e.y, nspk, nsub, hot_next, meta, t, csr, ring, sb);
+  }
+}
+
+// hot != 0: the hot-list kernel runs this step's listed neurons beside this
+// kernel; they are skipped here, and neurons ending above V_hot are listed.
 template <bool kFixed, int kMode, int kM>
 __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constant__ SegTable<AeifSeg> T,
                                                             const uint32_t* __restrict__ thr, const AeifState S,
                                                             Ring ring, int64_t* clk, int64_t step_off, const Csr csr,
-                                                            SpikeBuf sb, int scan, int budget) {
+                                                            SpikeBuf sb, int scan, int budget, int hot) {
   constexpr bool kAge = kMode == kEmitAge;
   constexpr int kW = kRecWords<kM>;
   __shared__ uint32_t s_thr[kMaxThr];
@@ -140,12 +273,14 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
   const bool valid = k < p.n;
   const uint32_t gid = (uint32_t)(p.offset + k);
   const int n_ports = kM == kAeifBeta ? p.n_ports : 2;
-  // prologue (overlaps the previous kernel): state, source metadata, Poisson table
+  // prologue (overlaps the previous kernel): state, hot tag, source metadata, Poisson table
   St y{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   float h0 = 0.f;
   uint4 meta = make_uint4(0, 0, 0, 0);
+  uint32_t tag = 0xffffffffu;
   if (valid) {
     load_state<kM>(S, gid, n_ports, y, h0);
+    if (hot) tag = sb.htag[gid];
     if (!kAge) meta = __ldg(csr.src_meta + gid);
   }
   for (uint32_t i = threadIdx.x; i < p.n_thr; i += kAeifBlock) s_thr[i] = __ldg(thr + p.thr_off + i);
@@ -153,64 +288,41 @@ __global__ void __launch_bounds__(kAeifBlock) k_update_aeif(const __grid_constan
   griddep_wait();
   griddep_launch();
   const int64_t t = clk[0] + step_off;
-  if (kMode != kEmitPipe && blockIdx.x == 0 && threadIdx.x == 0) clk[1] = t;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (kMode != kEmitPipe) clk[1] = t;
+    // the finishing kernel of this step starts its queue at 0; the hot list of
+    // step t + 2 (last read in step t - 1) starts empty for the appends of step t + 1
+    if (sb.dfetch) sb.dfetch[kM] = 0;
+    if (hot) sb.hcnt[3 * kM + (int)((uint64_t)(t + 2) % 3u)] = 0;
+  }
   if (kAge && scan)
     scan_pending<false>(t, csr, sb, ((int64_t)blockIdx.x * kAeifBlock + threadIdx.x) >> 5,
                         ((int64_t)gridDim.x * kAeifBlock) >> 5);
+  // listed for this step: the hot-list kernel runs it (and may already have listed it for the next)
+  const bool on = valid && tag != (uint32_t)t && tag != (uint32_t)(t + 1);
   uint32_t nspk = 0;
   unsigned long long nsub = 0;
   bool done = true;
   uint4 rec[kW];
-  if (valid) {
-    const uint64_t slot = (uint64_t)(t & ring.L_mask);
-    const uint64_t i0 = (slot * (uint64_t)ring.R) * (uint64_t)ring.N + gid;
-    float4 in = make_float4(0.f, 0.f, 0.f, 0.f);
-    in.x = ring_take<kFixed, false>(ring.p, i0);
-    in.y = ring_take<kFixed, false>(ring.p, i0 + (uint64_t)ring.N);
-    if (kM == kAeifBeta) {
-      if (n_ports > 2) in.z = ring_take<kFixed, false>(ring.p, i0 + 2 * (uint64_t)ring.N);
-      if (n_ports > 3) in.w = ring_take<kFixed, false>(ring.p, i0 + 3 * (uint64_t)ring.N);
-    }
-    if (p.n_thr > 0) {
-      const uint32_t kp = poisson_count(p.seed, t - p.t0, p.local_off + (uint32_t)k, s_thr, p.n_thr);
-      const float add = __fmul_rn((float)kp, p.w_ext);
-      switch (p.prec_rcpt) {
-        case 0: in.x = __fadd_rn(in.x, add); break;
-        case 1: in.y = __fadd_rn(in.y, add); break;
-        case 2: in.z = __fadd_rn(in.z, add); break;
-        default: in.w = __fadd_rn(in.w, add); break;
-      }
-    }
-    RkPos r{(double)h0, 0.0, 0};
-    bool cap_hit = false;
-    done = aeif_advance<kM>(p, y, r, budget, in, nspk, nsub, cap_hit);
-    if (cap_hit) atomicOr(sb.err, kErrSubstepCap);
-    if (done) store_state<kM>(S, gid, n_ports, y, (float)r.h);
-    else pack_rec<kM>(rec, gid, (uint32_t)seg, nspk, y, r, in);
-  }
-  defer_write<kW>(!done, rec, sb, kM, t);
-  // sub-step statistics: one atomic per warp
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) nsub += __shfl_xor_sync(0xffffffffu, nsub, o);
-  if ((threadIdx.x & 31) == 0 && nsub) atomicAdd(sb.substeps, nsub);
-  const uint32_t mult = nspk > 63u ? 63u : nspk;
-  if (kMode == kEmitAge) emit_spikes_age(done && nspk > 0, gid, mult, t, csr, sb);
-  else if (kMode == kEmitPipe)
-    emit_spikes_pipe<kFixed>(done && nspk > 0, gid, mult, t, meta,
-                             (done && nspk > 0) ? __ldg(csr.src_age + gid) : make_uint2(0, 0), csr, ring, sb);
-  else emit_spikes(done && nspk > 0, gid, mult, t, meta, sb);
+  if (on) done = aeif_neuron_step<kFixed, kM>(p, gid, k, (uint32_t)seg, s_thr, t, ring, S, n_ports, y, h0, budget,
+                                              nspk, nsub, rec, sb);
+  aeif_warp_end<kFixed, kMode, kM>(on, done, rec, gid, (uint32_t)seg, nspk, nsub, hot && on && done && y.V > p.V_hot,
+                                   meta, t, csr, ring, sb);
 }
 
 // Second part of the AdEx step: the neurons whose step did not finish within
-// the update kernel's attempt budget (mostly those crossing V_peak, whose
-// step needs tens of attempts) continue from their saved position, packed
-// 32 to a warp, then write their state and join the spike compaction.
+// the update kernel's attempt budget continue from their saved position.  A
+// lane takes one deferred neuron at a time from the list (a queue shared by
+// the grid) and makes one attempt per pass; a lane whose neuron finished
+// writes it back, joins the warp's spike compaction and takes the next one,
+// so the warp's lanes stay busy however unequal the neurons' attempt counts.
 template <bool kFixed, int kMode, int kM>
 __global__ void __launch_bounds__(kAeifBlock) k_aeif_finish(const __grid_constant__ SegTable<AeifSeg> T,
                                                             const AeifState S, Ring ring, int64_t* clk,
-                                                            int64_t step_off, const Csr csr, SpikeBuf sb) {
+                                                            int64_t step_off, const Csr csr, SpikeBuf sb, int hot) {
   constexpr bool kAge = kMode == kEmitAge;
   constexpr int kW = kRecWords<kM>;
+  const unsigned full = 0xffffffffu;
   griddep_wait();
   griddep_launch();
   const int64_t t = clk[0] + step_off;
@@ -221,78 +333,110 @@ __global__ void __launch_bounds__(kAeifBlock) k_aeif_finish(const __grid_constan
   if (blockIdx.x == 0 && threadIdx.x == 0) sb.dcnt[2 * kM + (int)((t + 1) & 1)] = 0;
   const uint4* __restrict__ list = sb.dfr[kM];
   const int lane = threadIdx.x & 31;
-  const unsigned long long warp = ((unsigned long long)blockIdx.x * kAeifBlock + threadIdx.x) >> 5;
-  const unsigned long long nwarps = ((unsigned long long)gridDim.x * kAeifBlock) >> 5;
-  for (unsigned long long base = warp * 32; base < n; base += nwarps * 32) {
-    const unsigned long long i = base + lane;
-    const bool valid = i < n;
-    uint32_t gid = 0, nspk = 0;
-    unsigned long long nsub = 0;
-    uint4 meta = make_uint4(0, 0, 0, 0);
-    if (valid) {
-      const uint4* q = list + (unsigned long long)kW * i;
-      const uint4 r0 = q[0];
-      gid = r0.x;
-      const AeifSeg p = T.dev[r0.y];
-      nspk = r0.z;
-      if (!kAge) meta = __ldg(csr.src_meta + gid);
-      St y{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      RkPos r{0.0, 0.0, 0};
-      float4 in;
-      unpack_rec<kM>(q, y, r, in);
-      bool cap_hit = false;
-      aeif_advance<kM>(p, y, r, 0, in, nspk, nsub, cap_hit);
-      if (cap_hit) atomicOr(sb.err, kErrSubstepCap);
-      store_state<kM>(S, gid, kM == kAeifBeta ? p.n_ports : 2, y, (float)r.h);
+  bool busy = false;  // this lane holds a neuron
+  uint32_t gid = 0, nspk = 0, seg = 0;
+  unsigned long long nsub = 0;
+  St y{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  RkPos r{0.0, 0.0, 0};
+  float4 in = make_float4(0.f, 0.f, 0.f, 0.f);
+  bool more = true;  // the queue may hold neurons
+  for (;;) {
+    // idle lanes take the next neurons of the queue
+    const unsigned want = __ballot_sync(full, !busy && more);
+    if (want) {
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(sb.dfetch + kM, (unsigned long long)__popc(want));
+      base = __shfl_sync(full, base, 0);
+      if (!busy && more) {
+        const unsigned long long i = base + __popc(want & ((1u << lane) - 1u));
+        if (i < n) {
+          const uint4* q = list + (unsigned long long)kW * i;
+          const uint4 r0 = q[0];
+          gid = r0.x;
+          seg = r0.y;
+          nspk = r0.z;
+          unpack_rec<kM>(q, y, r, in);
+          busy = true;
+        }
+      }
+      if (base + __popc(want) >= n) more = false;  // every lane saw the queue run out
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nsub += __shfl_xor_sync(0xffffffffu, nsub, o);
-    if (lane == 0 && nsub) atomicAdd(sb.substeps, nsub);
-    const uint32_t mult = nspk > 63u ? 63u : nspk;
-    if (kMode == kEmitAge) emit_spikes_age(nspk > 0, gid, mult, t, csr, sb);
-    else if (kMode == kEmitPipe)
-      emit_spikes_pipe<kFixed>(nspk > 0, gid, mult, t, meta, nspk > 0 ? __ldg(csr.src_age + gid) : make_uint2(0, 0),
-                               csr, ring, sb);
-    else emit_spikes(nspk > 0, gid, mult, t, meta, sb);
+    if (!__any_sync(full, busy)) break;
+    bool fin = false, hot_next = false;
+    uint4 meta = make_uint4(0, 0, 0, 0);
+    if (busy) {
+      const AeifSeg p = T.dev[seg];
+      bool cap_hit = false;
+      fin = aeif_advance<kM>(p, y, r, 1, in, nspk, nsub, cap_hit);
+      if (cap_hit) atomicOr(sb.err, kErrSubstepCap);
+      if (fin) {
+        store_state<kM>(S, gid, kM == kAeifBeta ? p.n_ports : 2, y, (float)r.h);
+        hot_next = hot && y.V > p.V_hot;
+        if (!kAge) meta = __ldg(csr.src_meta + gid);
+        busy = false;
+      }
+    }
+    aeif_warp_end<kFixed, kMode, kM>(fin, true, nullptr, gid, seg, nspk, 0ull, hot_next, meta, t, csr, ring, sb);
+    if (fin) nspk = 0;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nsub += __shfl_xor_sync(full, nsub, o);
+  if (lane == 0 && nsub) atomicAdd(sb.substeps, nsub);
 }
 
 namespace {
 template <bool kFixed, int kMode>
 cudaError_t aeif_launch(const SegTable<AeifSeg>& segs, dim3 g, const uint32_t* thr, const AeifState& S, int model,
                         Ring ring, int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, int sc, int budget,
-                        bool pdl, cudaStream_t st) {
+                        int hot, bool pdl, cudaStream_t st) {
   const dim3 b(kAeifBlock);
   if (model == kAeifBeta)
     return launch_k(k_update_aeif<kFixed, kMode, kAeifBeta>, g, b, pdl, st, segs, thr, S, ring, clk, step_off, csr,
-                    sb, sc, budget);
+                    sb, sc, budget, hot);
   if (model == kAeifAlpha)
     return launch_k(k_update_aeif<kFixed, kMode, kAeifAlpha>, g, b, pdl, st, segs, thr, S, ring, clk, step_off, csr,
-                    sb, sc, budget);
+                    sb, sc, budget, hot);
   return launch_k(k_update_aeif<kFixed, kMode, kAeifExp>, g, b, pdl, st, segs, thr, S, ring, clk, step_off, csr, sb,
-                  sc, budget);
+                  sc, budget, hot);
+}
+
+template <bool kFixed, int kMode>
+cudaError_t hot_launch(const SegTable<AeifSeg>& segs, dim3 g, const uint32_t* thr, const AeifState& S, int model,
+                       Ring ring, const int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, cudaStream_t st) {
+  const dim3 b(kAeifBlock);
+  if (model == kAeifBeta)
+    return launch_k(k_aeif_hot<kFixed, kMode, kAeifBeta>, g, b, false, st, segs, thr, S, ring, clk, step_off, csr,
+                    sb);
+  if (model == kAeifAlpha)
+    return launch_k(k_aeif_hot<kFixed, kMode, kAeifAlpha>, g, b, false, st, segs, thr, S, ring, clk, step_off, csr,
+                    sb);
+  return launch_k(k_aeif_hot<kFixed, kMode, kAeifExp>, g, b, false, st, segs, thr, S, ring, clk, step_off, csr, sb);
 }
 
 template <bool kFixed, int kMode>
 cudaError_t finish_launch(const SegTable<AeifSeg>& segs, dim3 g, const AeifState& S, int model, Ring ring,
-                          int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, bool pdl, cudaStream_t st) {
+                          int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, int hot, bool pdl,
+                          cudaStream_t st) {
   const dim3 b(kAeifBlock);
   if (model == kAeifBeta)
-    return launch_k(k_aeif_finish<kFixed, kMode, kAeifBeta>, g, b, pdl, st, segs, S, ring, clk, step_off, csr, sb);
+    return launch_k(k_aeif_finish<kFixed, kMode, kAeifBeta>, g, b, pdl, st, segs, S, ring, clk, step_off, csr, sb,
+                    hot);
   if (model == kAeifAlpha)
-    return launch_k(k_aeif_finish<kFixed, kMode, kAeifAlpha>, g, b, pdl, st, segs, S, ring, clk, step_off, csr, sb);
-  return launch_k(k_aeif_finish<kFixed, kMode, kAeifExp>, g, b, pdl, st, segs, S, ring, clk, step_off, csr, sb);
+    return launch_k(k_aeif_finish<kFixed, kMode, kAeifAlpha>, g, b, pdl, st, segs, S, ring, clk, step_off, csr, sb,
+                    hot);
+  return launch_k(k_aeif_finish<kFixed, kMode, kAeifExp>, g, b, pdl, st, segs, S, ring, clk, step_off, csr, sb, hot);
 }
 }  // namespace
 
 cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr,
                                const AeifState& S, int model, Ring ring, bool fixed, int64_t* clk, int64_t step_off,
-                               const Csr& csr, SpikeBuf sb, int emit, bool scan, int budget, bool pdl,
+                               const Csr& csr, SpikeBuf sb, int emit, bool scan, int budget, bool hot, bool pdl,
                                cudaStream_t st) {
   if (blocks <= 0) return cudaSuccess;
   const dim3 g((unsigned)blocks);
   const int sc = scan ? 1 : 0;
-#define NGB_AEIF(F, M) return aeif_launch<F, M>(segs, g, thr, S, model, ring, clk, step_off, csr, sb, sc, budget, pdl, st)
+  const int h = hot && budget > 0 && sb.htag && sb.hot[model] ? 1 : 0;
+#define NGB_AEIF(F, M) return aeif_launch<F, M>(segs, g, thr, S, model, ring, clk, step_off, csr, sb, sc, budget, h, pdl, st)
   if (fixed) {
     if (emit == kEmitAge) NGB_AEIF(true, kEmitAge);
     if (emit == kEmitPipe) NGB_AEIF(true, kEmitPipe);
@@ -304,11 +448,29 @@ cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, co
 #undef NGB_AEIF
 }
 
+cudaError_t launch_hot_aeif(const SegTable<AeifSeg>& segs, int grid, const uint32_t* thr, const AeifState& S,
+                            int model, Ring ring, bool fixed, const int64_t* clk, int64_t step_off, const Csr& csr,
+                            SpikeBuf sb, int emit, cudaStream_t st) {
+  if (grid <= 0 || !sb.htag || !sb.hot[model]) return cudaSuccess;
+  const dim3 g((unsigned)grid);
+#define NGB_HOT(F, M) return hot_launch<F, M>(segs, g, thr, S, model, ring, clk, step_off, csr, sb, st)
+  if (fixed) {
+    if (emit == kEmitAge) NGB_HOT(true, kEmitAge);
+    if (emit == kEmitPipe) NGB_HOT(true, kEmitPipe);
+    NGB_HOT(true, kEmitRing);
+  }
+  if (emit == kEmitAge) NGB_HOT(false, kEmitAge);
+  if (emit == kEmitPipe) NGB_HOT(false, kEmitPipe);
+  NGB_HOT(false, kEmitRing);
+#undef NGB_HOT
+}
+
 cudaError_t launch_finish_aeif(const SegTable<AeifSeg>& segs, int grid, const AeifState& S, int model, Ring ring,
                                bool fixed, int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, int emit,
-                               bool pdl, cudaStream_t st) {
+                               bool hot, bool pdl, cudaStream_t st) {
   const dim3 g((unsigned)grid);
-#define NGB_FIN(F, M) return finish_launch<F, M>(segs, g, S, model, ring, clk, step_off, csr, sb, pdl, st)
+  const int h = hot && sb.htag && sb.hot[model] ? 1 : 0;
+#define NGB_FIN(F, M) return finish_launch<F, M>(segs, g, S, model, ring, clk, step_off, csr, sb, h, pdl, st)
   if (fixed) {
     if (emit == kEmitAge) NGB_FIN(true, kEmitAge);
     if (emit == kEmitPipe) NGB_FIN(true, kEmitPipe);

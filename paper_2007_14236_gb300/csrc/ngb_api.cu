@@ -162,7 +162,7 @@ uint64_t call_synapses(const ngb_conn_spec& c, int64_t ns, int64_t nt, bool same
   }
 }
 
-// device counter words: ctr[2], events, substeps, rec_count, spare, pcnt[2], dcnt[6], ctr3[3], spare,
+// device counter words: ctr[2], events, substeps, rec_count, hot_steps, pcnt[2], dcnt[6], ctr3[3], spare,
 // post_cnt[2]
 constexpr int kCounters = 20;
 
@@ -243,9 +243,16 @@ struct ngb_sim {
   int n_aeif_exp = 0, n_aeif_alpha = 0, n_aeif_beta = 0;
   int64_t aeif_blocks = 0, aeifa_blocks = 0, aeifb_blocks = 0;
   int aeif_budget = 8;  // RK attempts per neuron in the AdEx update kernel before deferral (0: none)
+  // hot lists of the AdEx update kernels: a neuron whose step ends above V_T + hot_c * Delta_T runs its next
+  // step in a warp of listed neurons from the start of the update kernel (off: budget 0 or NGB_AEIF_HOT=0)
+  bool hot_on = true;   // lists allocated
+  bool hot_use = true;  // and used by the step loop (the autotuner may turn them off)
+  float hot_c = 4.0f;
+  bool hot_kind[3] = {false, false, false};  // a list per conductance model with a finite V_hot
   uint32_t* thr = nullptr;
   int deliver_grid = 0;
   bool pdl = true;  // programmatic dependent launch between the step's kernels
+  bool pdl_hold = false;  // the next kernel follows a join from another stream: launch it without PDL
   int mode = 0;  // 0: per-step kernels in CUDA graphs, 1: persistent step kernel, 2: fused update + delivery,
                  // 3: pipelined (delivery of step t beside the update of step t + 1, two streams),
                  // 4: pipelined persistent step kernel (ring scheme, one grid barrier per step),
@@ -255,6 +262,8 @@ struct ngb_sim {
                  //    of neurons with its ring in shared memory; spikes exchanged through mailboxes),
                  // 7: per-step kernels in CUDA graphs with target-tiled delivery (spike-buffer scheme)
   cudaStream_t stream2 = nullptr;  // second stream of the pipelined loop's graphs
+  cudaStream_t hstream = nullptr;  // stream of the AdEx hot-list kernels (highest priority)
+  cudaEvent_t hev[2] = {nullptr, nullptr};  // fork to and join from it
   bool persist_ok = false;
   int persist_grid = 0;
   int persist_max_bpsm = 0;
@@ -352,7 +361,26 @@ bool fused_ok(const ngb_sim* s) { return s->lif_npt == 1 && s->n_aeif_beta == 0;
 
 // Programmatic dependent launch chains the kernels of one stream; the
 // pipelined loop's kernels depend across two streams and go without it.
-bool pdl_of(const ngb_sim* s) { return s->pdl && s->mode != 3; }
+bool pdl_of(const ngb_sim* s) { return s->pdl && s->mode != 3 && !s->pdl_hold; }
+
+// pdl_of for a kernel launch that consumes a pending hold (the first kernel
+// after a join from another stream waits for that stream's work in full).
+bool take_pdl(ngb_sim* s) {
+  const bool p = pdl_of(s);
+  s->pdl_hold = false;
+  return p;
+}
+
+// Empty the AdEx hot lists and clear the neurons' tags: after steps run by a
+// loop that does not keep them (persistent, fused), a restored snapshot or
+// rebuilt tables no neuron is listed until a step of the per-step kernels
+// lists it again.
+cudaError_t hot_reset(ngb_sim* s) {
+  if (!s->sb.htag) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(s->sb.htag, 0xFF, (size_t)s->N_cap * sizeof(uint32_t), s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->sb.hcnt, 0, 9 * sizeof(unsigned long long), s->stream);
+  return e;
+}
 
 // The target-owned loop takes static LIF networks with the ring scheme and
 // one receptor, at most 2,048 neurons per block (one block per SM), and a
@@ -537,7 +565,7 @@ void set_tiled(ngb_sim* s, bool on) {
 cudaError_t launch_lif(ngb_sim* s, int64_t step_off = 0) {
   return launch_update_lif(s->lif_tab, s->lif_blocks, s->lif_npt, s->thr, s->st0, s->st1, s->ref, ring_of(s),
                            s->cfg.deterministic != 0, s->clk, step_off, csr_of(s), s->sb, emit_of(s), true,
-                           pdl_of(s), s->stream);
+                           take_pdl(s), s->stream);
 }
 
 AeifState aeif_state_of(const ngb_sim* s) {
@@ -551,7 +579,6 @@ cudaError_t launch_aeif(ngb_sim* s, int64_t step_off = 0) {
   cudaError_t e = cudaSuccess;
   const bool det = s->cfg.deterministic != 0;
   const int emit = emit_of(s);
-  const bool pdl = pdl_of(s);
   const int fin_grid = std::max(1, s->sms) * 4;
   const AeifState S = aeif_state_of(s);
   const struct {
@@ -564,11 +591,27 @@ cudaError_t launch_aeif(ngb_sim* s, int64_t step_off = 0) {
   bool scan = s->n_lif == 0;  // the first update kernel of the step scans the pending spikes
   for (const auto& k : kinds) {
     if (!k.n || e != cudaSuccess) continue;
-    e = launch_update_aeif(*k.tab, k.blocks, s->thr, S, k.model, ring_of(s), det, s->clk, step_off, csr_of(s), s->sb,
-                           emit, scan, s->aeif_budget, pdl, s->stream);
+    // the hot list's kernel on its own stream, forked after the previous step, beside the update kernel
+    const bool hot = s->hot_on && s->hot_use && s->hot_kind[k.model] && s->hstream && s->aeif_budget > 0;
+    if (hot) {
+      e = cudaEventRecord(s->hev[0], s->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s->hstream, s->hev[0], 0);
+      if (e == cudaSuccess)
+        e = launch_hot_aeif(*k.tab, std::max(1, s->sms), s->thr, S, k.model, ring_of(s), det, s->clk, step_off,
+                            csr_of(s), s->sb, emit, s->hstream);
+      if (e == cudaSuccess) e = cudaEventRecord(s->hev[1], s->hstream);
+    }
+    if (e == cudaSuccess)
+      e = launch_update_aeif(*k.tab, k.blocks, s->thr, S, k.model, ring_of(s), det, s->clk, step_off, csr_of(s),
+                             s->sb, emit, scan, s->aeif_budget, hot, take_pdl(s), s->stream);
     if (e == cudaSuccess && s->aeif_budget > 0)
       e = launch_finish_aeif(*k.tab, fin_grid, S, k.model, ring_of(s), det, s->clk, step_off, csr_of(s), s->sb, emit,
-                             pdl, s->stream);
+                             hot, take_pdl(s), s->stream);
+    // the hot neurons' spikes and state before anything that follows the step's updates
+    if (e == cudaSuccess && hot) {
+      e = cudaStreamWaitEvent(s->stream, s->hev[1], 0);
+      s->pdl_hold = true;
+    }
     scan = false;
   }
   return e;
@@ -579,17 +622,19 @@ StdpArgs stdp_of(const ngb_sim* s) { return StdpArgs{s->d_rules, s->wa, s->in_sy
 cudaError_t launch_del(ngb_sim* s, int64_t step_off = 0, cudaStream_t st = nullptr) {
   if (s->mode == 7)
     return launch_deliver_tiled(s->sb, s->tl, s->tl_P, s->cfg.weight_dtype, ring_of(s), s->R, s->N,
-                                s->cfg.deterministic != 0, s->clk, pdl_of(s), st ? st : s->stream);
+                                s->cfg.deterministic != 0, s->clk, take_pdl(s), st ? st : s->stream);
   const StdpArgs sa = stdp_of(s);
   return launch_deliver(s->sb, csr_of(s), s->cfg.weight_dtype, ring_of(s), s->cfg.deterministic != 0, emit_of(s),
-                        s->clk, step_off, s->deliver_grid, pdl_of(s), st ? st : s->stream,
+                        s->clk, step_off, s->deliver_grid, take_pdl(s), st ? st : s->stream,
                         s->d_rules ? &sa : nullptr);
 }
 
 // STDP potentiation of the step's firing targets, between the update kernels and the delivery.
 cudaError_t launch_post(ngb_sim* s) {
   if (!s->d_rules) return cudaSuccess;
-  return launch_stdp_post(s->sb, stdp_of(s), s->clk, std::max(1, s->sms) * 4, s->pdl, s->stream);
+  const bool pdl = s->pdl && !s->pdl_hold;
+  s->pdl_hold = false;
+  return launch_stdp_post(s->sb, stdp_of(s), s->clk, std::max(1, s->sms) * 4, pdl, s->stream);
 }
 
 // The update kernels of one step (step clk[0] + step_off).
@@ -1071,6 +1116,7 @@ int rebuild_tables(ngb_sim* s) {
   s->aeifa_blocks = 0;
   s->aeifb_blocks = 0;
   s->n_active = 0;
+  for (bool& h : s->hot_kind) h = false;
   {
     // two LIF neurons per thread (the tiled kernel: resident blocks walking
     // the tiles with the next tile's loads in flight) when the update grid
@@ -1162,6 +1208,8 @@ int rebuild_tables(ngb_sim* s) {
       g.h_min = q.rk_h_min_ms;
       g.dt = dt;
       g.max_sub = q.rk_max_substeps;
+      g.V_hot = s->hot_on && q.Delta_T_mV > 0 ? (float)(q.V_T_mV + s->hot_c * q.Delta_T_mV) : INFINITY;
+      if (g.V_hot < INFINITY) s->hot_kind[kind] = true;
       constexpr double kEuler = 2.718281828459045;
       g.e_tau_ex = (float)(kEuler / q.tau_ex_ms);
       g.e_tau_in = (float)(kEuler / q.tau_in_ms);
@@ -1203,6 +1251,10 @@ int rebuild_tables(ngb_sim* s) {
   s->n_aeif = s->n_aeif_exp + s->n_aeif_alpha + s->n_aeif_beta;
   // the beta model's deferred-neuron list (6 words per neuron), on first use
   if (s->n_aeif_beta && !s->sb.dfr[kAeifBeta]) CK(s->dalloc(&s->sb.dfr[kAeifBeta], 6 * (size_t)s->N_cap));
+  // hot lists (both step parities) of the conductance models that list neurons, on first use
+  for (int kind = 0; kind < 3; ++kind)
+    if (s->hot_kind[kind] && s->sb.htag && !s->sb.hot[kind]) CK(s->dalloc(&s->sb.hot[kind], 3 * (size_t)s->N_cap));
+  CK(hot_reset(s));
   // every AdEx segment of the two-receptor models, for the persistent kernel
   std::vector<AeifSeg> asegs(asegs_exp);
   asegs.insert(asegs.end(), asegs_alpha.begin(), asegs_alpha.end());
@@ -1437,6 +1489,25 @@ int finalize_impl(ngb_sim* s) {
     s->sb.dfr_cap = N;
     const char* env_budget = std::getenv("NGB_AEIF_BUDGET");
     if (env_budget) s->aeif_budget = std::max(0, std::atoi(env_budget));
+    const char* env_hot = std::getenv("NGB_AEIF_HOT");
+    if (env_hot) {
+      const double c = std::atof(env_hot);
+      if (c > 0.0) s->hot_c = (float)c;
+      else s->hot_on = false;
+    }
+    if (s->aeif_budget <= 0) s->hot_on = false;  // the finishing kernel empties the lists
+    CK(s->dalloc(&s->sb.dfetch, 3));
+    CK(cudaMemsetAsync(s->sb.dfetch, 0, 3 * sizeof(unsigned long long), st));
+    if (s->hot_on) {
+      CK(s->dalloc(&s->sb.htag, N));
+      CK(s->dalloc(&s->sb.hcnt, 9));
+      s->sb.hot_cap = N;
+      int lo = 0, hi = 0;
+      CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      CK(cudaStreamCreateWithPriority(&s->hstream, cudaStreamNonBlocking, hi));
+      CK(cudaEventCreateWithFlags(&s->hev[0], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&s->hev[1], cudaEventDisableTiming));
+    }
     CK(cudaMemsetAsync(s->st5, 0, N * sizeof(float), st));
     CK(cudaMemsetAsync(s->st6, 0, N * sizeof(float), st));
     CK(cudaMemsetAsync(s->st2, 0, N * sizeof(float), st));
@@ -1466,11 +1537,12 @@ int finalize_impl(ngb_sim* s) {
 
   // counters, clock, spike record, barrier
   unsigned long long* ctrs = nullptr;
-  CK(s->dalloc(&ctrs, kCounters));  // ctr[2], events, substeps, rec_count, spare, pcnt[2], dcnt[6], ctr3[3]
+  CK(s->dalloc(&ctrs, kCounters));  // ctr[2], events, substeps, rec_count, hot_steps, pcnt[2], dcnt[6], ctr3[3]
   CK(cudaMemsetAsync(ctrs, 0, kCounters * sizeof(unsigned long long), st));
   s->sb.ctr = ctrs;
   s->sb.events = ctrs + 2;
   s->sb.substeps = ctrs + 3;
+  s->sb.hot_steps = ctrs + 5;
   s->sb.rec_count = ctrs + 4;
   s->sb.pcnt = ctrs + 6;
   s->sb.dcnt = ctrs + 8;
@@ -1671,6 +1743,9 @@ int simulate_impl(ngb_sim* s, int64_t steps, bool profiled, double* kernel_ms, i
     const int rc = rebuild_tables(s);
     if (rc != NGB_OK) return rc;
   }
+  // loops whose AdEx update is not the per-step kernels' leave the hot lists stale
+  if (s->n_aeif && (profiled ? s->mode == 2 : (s->mode == 1 || s->mode == 2 || s->mode == 4 || s->mode == 6)))
+    CK(hot_reset(s));
   int rc_overflow = NGB_OK;
   if (!profiled) {
     int64_t left = steps;
@@ -1793,6 +1868,7 @@ int snapshot_restore(ngb_sim* s, const Snapshot& sn) {
     CK(cudaMemcpyAsync(sn.parts[i].first, sn.copies[i], sn.parts[i].second, cudaMemcpyDeviceToDevice, s->stream));
   // snapshots are taken between steps, when no due group waits in a bucket
   if (s->tl.bcnt) CK(cudaMemsetAsync(s->tl.bcnt, 0, (size_t)2 * s->tl.n_tiles * sizeof(unsigned int), s->stream));
+  CK(hot_reset(s));
   CK(cudaStreamSynchronize(s->stream));
   return NGB_OK;
 }
@@ -1861,6 +1937,10 @@ int ngb_destroy(ngb_sim* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   if (s->stream2) cudaStreamDestroy(s->stream2);
+  if (s->hstream) cudaStreamSynchronize(s->hstream);
+  if (s->hstream) cudaStreamDestroy(s->hstream);
+  for (cudaEvent_t ev : s->hev)
+    if (ev) cudaEventDestroy(ev);
   for (void* p : s->allocs) cudaFree(p);
   for (void* p : s->table_allocs) cudaFree(p);
   tiled_free(&s->tl);
@@ -2211,6 +2291,34 @@ int ngb_autotune(ngb_sim* s, int64_t trial_steps, int32_t* deliver_grid_out) {
       s->mode = 0;
     }
   }
+  // the AdEx hot lists (on in the trials above) against none, in the chosen per-step loop
+  bool best_hot = s->hot_use;
+  if (rc == NGB_OK && s->hot_on && s->hot_use && s->n_aeif && (best_mode == 0 || best_mode == 3)) {
+    set_scheme(s, best_scheme);
+    s->mode = best_mode;
+    s->deliver_grid = best_grid;
+    s->hot_use = false;
+    rc = capture_graph(s);
+    if (rc == NGB_OK) rc = snapshot_restore(s, sn);
+    if (rc == NGB_OK) {
+      const int64_t reps = std::max<int64_t>(1, trial_steps / s->graph_steps);
+      CK(cudaGraphLaunch(s->gexec, s->stream));  // warm-up replay
+      CK(cudaEventRecord(e0, s->stream));
+      for (int64_t r = 0; r < reps; ++r) CK(cudaGraphLaunch(s->gexec, s->stream));
+      CK(cudaEventRecord(e1, s->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      const double per_step = ms / (double)(reps * s->graph_steps);
+      if (per_step < best_ms) {
+        best_ms = per_step;
+        best_hot = false;
+      }
+    }
+    s->mode = 0;
+  }
+  // a loop other than the per-step kernels keeps no lists (and profiled per-step runs then match it)
+  s->hot_use = best_hot && (best_mode == 0 || best_mode == 3);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc == NGB_OK) rc = snapshot_restore(s, sn);
@@ -2379,11 +2487,12 @@ int ngb_get_stats(ngb_sim* s, ngb_stats* out) {
   if (s->finalized) {
     const int rc = check_handle(s);
     if (rc != NGB_OK) return rc;
-    unsigned long long c[2] = {0, 0};
-    CK(cudaMemcpyAsync(c, s->sb.events, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->stream));
+    unsigned long long c[4] = {0, 0, 0, 0};  // events, substeps, rec_count, hot_steps
+    CK(cudaMemcpyAsync(c, s->sb.events, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     out->events = (int64_t)c[0];
     out->rk_substeps = (int64_t)c[1];
+    out->hot_steps = (int64_t)c[3];
     out->num_synapses = (int64_t)s->K;
     out->num_groups = (int64_t)s->G;
     out->ring_slots = s->L;

@@ -111,6 +111,7 @@ struct AeifSeg {
   // time, 1 / rise time, jump of x per unit weight (the peak of g equals the weight)
   float E_p[4], itd_p[4], itr_p[4], jmp_p[4];
   float inv_tol_f;     // 1 / tolerance rounded to FP32 (the FP32 side of the error-ratio test)
+  float V_hot;         // a step ending above this V lists the neuron as hot for the next step (+inf: never)
   double inv_tol, h_min, dt;
   int64_t max_sub;
 };
@@ -120,6 +121,7 @@ struct SpikeBuf {
   unsigned long long* ctr;          // [2] packed per-step counters
   unsigned long long* events;       // synaptic events delivered (cumulative)
   unsigned long long* substeps;     // RK sub-steps (cumulative)
+  unsigned long long* hot_steps;    // AdEx neuron steps run from the hot lists (cumulative)
   uint32_t* rec_id;                 // spike record, rec_cap entries
   int64_t* rec_step;
   unsigned long long* rec_count;    // spikes since the last drain (with multiplicity)
@@ -136,6 +138,19 @@ struct SpikeBuf {
   uint4* dfr[3];                    // 4 uint4 per neuron (beta: 6)
   unsigned long long* dcnt;         // [model * 2 + step parity]
   int64_t dfr_cap;                  // neurons per list
+  // the finishing kernel's queue position in the deferred list, by model
+  // (zeroed by the step's update kernel)
+  unsigned long long* dfetch;
+  // AdEx neurons listed as hot for a step (their previous step ended above
+  // V_hot: mostly those about to cross V_peak, whose step takes tens of
+  // attempts): {neuron, segment} by conductance model, three lists of hot_cap
+  // entries by step mod 3, run by a kernel of their own beside the update
+  // kernel, which skips them.  htag[n] holds the step (low 32 bits) neuron n was
+  // last listed for; an entry counts only when its neuron's tag names the step.
+  uint2* hot[3];
+  unsigned long long* hcnt;         // [model * 3 + step mod 3]
+  uint32_t* htag;
+  int64_t hot_cap;                  // entries per list
   // pipelined ring scheme: work-item lists and counters by step mod 3
   uint4* wi3[3];
   unsigned long long* ctr3;         // [3]
@@ -646,13 +661,20 @@ enum : int { kAeifExp = 0, kAeifAlpha = 1, kAeifBeta = 2 };
 // model: kAeif*, the conductance model of every segment of the table.
 // budget > 0: at most `budget` RK attempts per neuron in this kernel; the
 // unfinished neurons are completed by launch_finish_aeif (same arithmetic).
+// hot: the step's hot list runs in launch_hot_aeif beside this kernel, which
+// skips the listed neurons and lists those ending above V_hot for the next step.
 cudaError_t launch_update_aeif(const SegTable<AeifSeg>& segs, int64_t blocks, const uint32_t* thr,
                                const AeifState& S, int model, Ring ring, bool fixed, int64_t* clk, int64_t step_off,
-                               const Csr& csr, SpikeBuf sb, int emit, bool scan, int budget, bool pdl,
+                               const Csr& csr, SpikeBuf sb, int emit, bool scan, int budget, bool hot, bool pdl,
                                cudaStream_t st);
+// The hot list of step clk[0] + step_off, whole steps, on a stream of its own
+// forked after the previous step and joined before launch_finish_aeif.
+cudaError_t launch_hot_aeif(const SegTable<AeifSeg>& segs, int grid, const uint32_t* thr, const AeifState& S,
+                            int model, Ring ring, bool fixed, const int64_t* clk, int64_t step_off, const Csr& csr,
+                            SpikeBuf sb, int emit, cudaStream_t st);
 cudaError_t launch_finish_aeif(const SegTable<AeifSeg>& segs, int grid, const AeifState& S, int model, Ring ring,
                                bool fixed, int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, int emit,
-                               bool pdl, cudaStream_t st);
+                               bool hot, bool pdl, cudaStream_t st);
 cudaError_t launch_tick(int64_t* clk, bool pdl, cudaStream_t st);
 // pipe: the pipelined variant (ring scheme; one grid barrier per step).
 cudaError_t persistent_max_blocks_per_sm(bool fixed, int wdtype, bool lif, bool aeif, bool pipe, size_t smem,

@@ -77,7 +77,7 @@ class SynSpec(C.Structure):
 class Stats(C.Structure):
     _fields_ = [(n, C.c_int64) for n in ("steps", "spikes", "events", "rk_substeps", "num_neurons", "num_synapses",
                                          "num_groups", "ring_slots", "max_delay_steps", "device_bytes", "mode",
-                                         "launch_grid", "delivery")]
+                                         "launch_grid", "delivery", "hot_steps")]
 
 
 _lib = None
