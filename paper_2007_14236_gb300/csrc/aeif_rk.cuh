@@ -124,19 +124,29 @@ __device__ __forceinline__ float ratio_of(float err, float y, float hf, float fl
 // sequence of attempts is the same as without a budget).  CT is the
 // precision of the step-size control (h, time inside the step, error-ratio
 // test).
+// a < b for the control values (step sizes, remaining time: never negative
+// nor NaN); for FP64 the comparison of the bit patterns as integers, which
+// orders such doubles exactly and keeps the comparison off the FP64 units.
+__device__ __forceinline__ bool ctl_lt(double a, double b) { return __double_as_longlong(a) < __double_as_longlong(b); }
+__device__ __forceinline__ bool ctl_lt(float a, float b) { return a < b; }
+
 template <typename CT, int NC>
 __device__ __forceinline__ bool aeif_integrate_t(const AeifSeg& p, float y[NC], CT& h, CT& t_in, int64_t& n,
                                                  int budget, uint32_t& nspk, unsigned long long& nsub,
                                                  bool& cap_hit) {
   const CT dt = (CT)p.dt, h_min = (CT)p.h_min;
   if (!(h > (CT)0)) h = dt;
+  CT rem = dt - t_in;
   for (;;) {
-    const CT rem = dt - t_in;
     bool last = false;
-    if (h >= rem) {
+    if (!ctl_lt(h, rem)) {  // h >= rem
       h = rem;
       last = true;
     }
+    // the time reached and the time left if this attempt is accepted, computed
+    // before the attempt (the same operations as after it)
+    const CT t_next = t_in + h;
+    const CT rem_next = dt - t_next;
     const float hf = (float)h;
     float k1[NC], k2[NC], k3[NC], k4[NC], k5[NC], k6[NC], ys[NC];
     deriv<NC>(p, y, k1);
@@ -177,7 +187,7 @@ __device__ __forceinline__ bool aeif_integrate_t(const AeifSeg& p, float y[NC], 
     ++nsub;
     ++n;
     const bool cap = n >= p.max_sub;
-    if (within || h <= h_min || cap) {
+    if (within || !ctl_lt(h_min, h) || cap) {  // h <= h_min
 #pragma unroll
       for (int i = 0; i < NC; ++i) y[i] = y5[i];
       if (y[0] >= p.V_peak) {
@@ -187,16 +197,16 @@ __device__ __forceinline__ bool aeif_integrate_t(const AeifSeg& p, float y[NC], 
       }
       float grow = 5.0f;
       if (rf > 0.0f) grow = fminf(5.0f, __fmul_rn(0.9f, step_factor_root<5>(rf)));
-      const CT h_used = h;
       h = h * (CT)grow;
-      if (h < h_min) h = h_min;
+      if (ctl_lt(h, h_min)) h = h_min;
       if (cap && !last) cap_hit = true;
       if (last || cap) return true;
-      t_in += h_used;
+      t_in = t_next;
+      rem = rem_next;
     } else {
       const float shrink = fmaxf(0.1f, __fmul_rn(0.9f, step_factor_root<4>(rf)));
       h = h * (CT)shrink;
-      if (h < h_min) h = h_min;
+      if (ctl_lt(h, h_min)) h = h_min;
     }
     if (--budget == 0) return false;
   }

@@ -212,8 +212,13 @@ __device__ __forceinline__ void aeif_warp_end(bool on, bool done, const uint4* r
 // budget), in a kernel that runs beside the update kernel of the same step
 // (which skips them): their tens of attempts start with the step instead of
 // after it.  The previous step's kernels have completed before this one.
+// One warp per block: the busy warps (the list's first entries) are spread one
+// to an SM, since each attempt's FP64 step-size control queues for the SM's
+// few FP64 units (16 busy warps on one SM ran their steps 1.6 times slower).
+constexpr int kHotBlock = 32;
+
 template <bool kFixed, int kMode, int kM>
-__global__ void __launch_bounds__(kAeifBlock) k_aeif_hot(const __grid_constant__ SegTable<AeifSeg> T,
+__global__ void __launch_bounds__(kHotBlock) k_aeif_hot(const __grid_constant__ SegTable<AeifSeg> T,
                                                          const uint32_t* __restrict__ thr, const AeifState S,
                                                          Ring ring, const int64_t* clk, int64_t step_off,
                                                          const Csr csr, SpikeBuf sb) {
@@ -225,8 +230,8 @@ __global__ void __launch_bounds__(kAeifBlock) k_aeif_hot(const __grid_constant__
   if (n > (unsigned long long)sb.hot_cap) n = (unsigned long long)sb.hot_cap;
   const uint2* __restrict__ list = sb.hot[kM] + (uint64_t)q * (uint64_t)sb.hot_cap;
   const int lane = threadIdx.x & 31;
-  const unsigned long long warp = ((unsigned long long)blockIdx.x * kAeifBlock + threadIdx.x) >> 5;
-  const unsigned long long nwarps = ((unsigned long long)gridDim.x * kAeifBlock) >> 5;
+  const unsigned long long warp = ((unsigned long long)blockIdx.x * kHotBlock + threadIdx.x) >> 5;
+  const unsigned long long nwarps = ((unsigned long long)gridDim.x * kHotBlock) >> 5;
   for (unsigned long long base = warp * 32; base < n; base += nwarps * 32) {
     const unsigned long long i = base + lane;
     uint2 e = make_uint2(0, 0);
@@ -403,7 +408,7 @@ cudaError_t aeif_launch(const SegTable<AeifSeg>& segs, dim3 g, const uint32_t* t
 template <bool kFixed, int kMode>
 cudaError_t hot_launch(const SegTable<AeifSeg>& segs, dim3 g, const uint32_t* thr, const AeifState& S, int model,
                        Ring ring, const int64_t* clk, int64_t step_off, const Csr& csr, SpikeBuf sb, cudaStream_t st) {
-  const dim3 b(kAeifBlock);
+  const dim3 b(kHotBlock);
   if (model == kAeifBeta)
     return launch_k(k_aeif_hot<kFixed, kMode, kAeifBeta>, g, b, false, st, segs, thr, S, ring, clk, step_off, csr,
                     sb);

@@ -597,7 +597,7 @@ cudaError_t launch_aeif(ngb_sim* s, int64_t step_off = 0) {
       e = cudaEventRecord(s->hev[0], s->stream);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(s->hstream, s->hev[0], 0);
       if (e == cudaSuccess)
-        e = launch_hot_aeif(*k.tab, std::max(1, s->sms), s->thr, S, k.model, ring_of(s), det, s->clk, step_off,
+        e = launch_hot_aeif(*k.tab, 4 * std::max(1, s->sms), s->thr, S, k.model, ring_of(s), det, s->clk, step_off,
                             csr_of(s), s->sb, emit, s->hstream);
       if (e == cudaSuccess) e = cudaEventRecord(s->hev[1], s->hstream);
     }
