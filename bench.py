@@ -752,7 +752,7 @@ def run_request(a):
     """One served-request network alone (balanced LIF, config-0 neurons and
     weights) at a given size and in-degree: the high-load delivery case."""
     from paper_2007_14236_gb300 import ngb, workloads as W
-    spec = W.balanced_lif(n=a.req_n, indegree=a.req_k, seed=7)
+    spec = W.balanced_lif(n=a.req_n, indegree=a.req_k, seed=7, weight_dtype=a.weights)
     sim = ngb.from_spec(spec, drain_steps=a.sim_steps, record_spikes=False, delivery=a.delivery)
     sim.finalize()
     if a.mode == "auto":
@@ -770,13 +770,23 @@ def run_request(a):
     peak, _ = _peaks()
     us_d = 1e3 * kms[2] / max(1, nl[2])
     bio = a.steps * a.sim_steps * 1e-4
+    ev_b = 12 if a.weights == "fp32" else 10  # target index + weight + ring add per synaptic event
+    n_steps = a.steps * a.sim_steps
+    # the whole step of the loop that ran (update 32 B per neuron + delivery per event) over its wall time
+    step_bytes = 32 * a.req_n + ev_b * (s1["events"] - s0["events"]) / n_steps
+    step_gbs = step_bytes / (wall / n_steps) / 1e9
     print(json.dumps({"workload": "request_n%d_k%d" % (a.req_n, a.req_k), "synapses": s1["num_synapses"],
+                      "weights": a.weights,
                       "events_per_s": (s1["events"] - s0["events"]) / wall, "real_time_factor": wall / bio,
                       "rate_hz": (s1["spikes"] - s0["spikes"]) / a.req_n / bio,
-                      "k_deliver": {"us_per_launch": us_d, "events_per_launch": evl,
-                                    "achieved_gbs": evl * 12 / (us_d * 1e-6) / 1e9,
-                                    "frac_of_measured_hbm": evl * 12 / (us_d * 1e-6) / 1e9 / peak},
-                      "k_update_lif_us": 1e3 * kms[0] / max(1, nl[0]),
+                      "us_per_step": 1e6 * wall / n_steps,
+                      "step_roofline": {"algorithmic_bytes_per_step": step_bytes, "achieved_gbs": step_gbs,
+                                        "frac_of_measured_hbm": step_gbs / peak},
+                      "per_step_kernels": {"k_deliver": {"us_per_launch": us_d, "events_per_launch": evl,
+                                                         "achieved_gbs": evl * ev_b / (us_d * 1e-6) / 1e9,
+                                                         "frac_of_measured_hbm":
+                                                             evl * ev_b / (us_d * 1e-6) / 1e9 / peak},
+                                           "k_update_lif_us": 1e3 * kms[0] / max(1, nl[0])},
                       "step_loop": LOOPS[s1["mode"]],
                       "delivery": DELIVERY[s1["delivery"]]}), flush=True)
     return 0

@@ -299,6 +299,19 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
   // every fourth step.
   U4 pblk[kNpt];
   bool pblk_ok = false;
+  // With one neuron per thread, the first kThrReg Poisson thresholds of its
+  // segment stay in registers: the count is the number of thresholds at or
+  // below the word (they ascend), taken without the chain of dependent
+  // shared-memory loads of the search; the search goes on in shared memory
+  // only past them.  Thresholds past n_thr read as all ones, and the count is
+  // capped at n_thr, so the result is the search's exactly.
+  constexpr int kThrReg = kNpt == 1 ? 8 : 1;
+  uint32_t thr_r[kThrReg];
+  if (kNpt == 1) {
+    const LifSeg& sg = s_seg[si[0]];
+#pragma unroll
+    for (int i = 0; i < kThrReg; ++i) thr_r[i] = (uint32_t)i < sg.n_thr ? s_thr[sg.thr_off + i] : 0xFFFFFFFFu;
+  }
   auto draw_counts = [&](int64_t t) {
 #pragma unroll
     for (int j = 0; j < kNpt; ++j) {
@@ -310,7 +323,18 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
         const int64_t tl = t - sg.t0;
         if (!pblk_ok || (tl & 3) == 0)
           pblk[j] = poisson_block(sg.seed, (uint64_t)tl >> 2, sg.local_off + (uint32_t)(gid - sg.offset));
-        kp[j] = poisson_from_word(poisson_word(pblk[j], tl), s_thr + sg.thr_off, sg.n_thr);
+        const uint32_t x = poisson_word(pblk[j], tl);
+        if (kNpt == 1) {
+          uint32_t c = 0;
+#pragma unroll
+          for (int i = 0; i < kThrReg; ++i) c += x >= thr_r[i] ? 1u : 0u;
+          uint32_t k = c < sg.n_thr ? c : sg.n_thr;
+          if (k == (uint32_t)kThrReg)
+            while (k < sg.n_thr && x >= s_thr[sg.thr_off + k]) ++k;
+          kp[j] = k;
+        } else {
+          kp[j] = poisson_from_word(x, s_thr + sg.thr_off, sg.n_thr);
+        }
       }
     }
     pblk_ok = true;

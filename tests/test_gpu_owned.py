@@ -7,9 +7,13 @@ mailboxes) against the per-step kernels, through the C ABI (needs a GB300).
   counts, over launches of 1, 2, 97 and 250 steps and a switch to the
   profiled per-step kernels and back; LIF networks with one and several
   populations, batched instances, BF16 and FP16 weights, fewer neurons than blocks,
-  no synapses at all, and a network whose first step fires thousands of
+  no synapses at all, a network whose first step fires thousands of
   neurons (mailbox overflow areas, more spikes than the shared-memory list
-  holds).
+  holds), and busy networks of 160,000 neurons with 1,000 inputs each that
+  fire thousands of spikes in every step, in bursts of well over 2,048
+  (tiles of 1,053 neurons, more than 1,024 per block: 8-byte items for BF16
+  weights too; every step through the overflow areas, and the bursts past
+  the shared-memory entry list).
 * FP32 mode: after one step the ring slots hold the same sums as the
   per-step kernels within the FP32 summation bound (1e-5 of the summed
   magnitudes), and spike counts agree within 5 % over 3,000 steps.
@@ -64,6 +68,9 @@ _SPECS = {
                                     w_ex=2.0, w_in=4.0),
     "tiny": lambda: W.balanced_lif(n=100, indegree=10, seed=3),  # fewer neurons than blocks
     "unconnected": lambda: _unconnected(),                       # no synapses at all
+    # thousands of spikes in every step; more than 1,024 neurons per tile
+    "busy": lambda: W.balanced_lif(n=160_000, indegree=1000, seed=5),
+    "busy_bf16": lambda: W.balanced_lif(n=160_000, indegree=1000, seed=6, weight_dtype="bf16"),
 }
 
 
@@ -84,8 +91,9 @@ def _owned(ngb, spec, **kw):
 @pytest.mark.parametrize("name", sorted(_SPECS))
 def test_target_owned_equals_per_step_kernels(ngb, name):
     spec = _SPECS[name]()
-    a = ngb.from_spec(spec, deterministic=True, delivery="ring")
-    b = _owned(ngb, spec, deterministic=True, delivery="ring", drain_steps=250)
+    kw = {"record_capacity": 8_000_000} if name.startswith("busy") else {}  # ~3,000 spikes per step
+    a = ngb.from_spec(spec, deterministic=True, delivery="ring", **kw)
+    b = _owned(ngb, spec, deterministic=True, delivery="ring", drain_steps=250, **kw)
     assert b.stats()["mode"] == (0 if name == "adex" else 6)
     if name != "adex":
         assert b.stats()["launch_grid"] > 0
@@ -97,6 +105,8 @@ def test_target_owned_equals_per_step_kernels(ngb, name):
     assert len(ai) > 50
     if name == "mc_burst":
         assert np.count_nonzero(at == 0) > 3000  # the first step fires thousands of neurons
+    if name.startswith("busy"):
+        assert len(ai) > 1000 * 1000  # over a thousand spikes per step on average
     assert np.array_equal(at, bt) and np.array_equal(ai, bi)
     assert np.array_equal(a.state("V_m"), b.state("V_m"))
     assert np.array_equal(a.state("I_syn"), b.state("I_syn"))
