@@ -305,6 +305,14 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
   // shared-memory loads of the search; the search goes on in shared memory
   // only past them.  Thresholds past n_thr read as all ones, and the count is
   // capped at n_thr, so the result is the search's exactly.
+  // (and the constants of the update in registers too: a copy of the
+  // segment, of which the update reads only the propagators, threshold,
+  // reset, refractory steps and drive weight)
+  LifSeg sg1 = s_seg[si[0]];
+  auto seg_of = [&](int j) -> const LifSeg& {
+    if constexpr (kNpt == 1) return sg1;
+    else return s_seg[si[j]];
+  };
   constexpr int kThrReg = kNpt == 1 ? 8 : 1;
   uint32_t thr_r[kThrReg];
   if (kNpt == 1) {
@@ -358,7 +366,7 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
     for (int j = 0; j < kNpt; ++j) {
       sp[j] = false;
       if (!valid[j]) continue;
-      sp[j] = lif_propagate(s_seg[si[j]], y[j], I[j], ref[j], yp[j], rp[j]);
+      sp[j] = lif_propagate(seg_of(j), y[j], I[j], ref[j], yp[j], rp[j]);
       if (sp[j] && pub[j] != 0) s_pub[atomicAdd(&s_np[q], 1)] = pub[j];
     }
   };
@@ -489,7 +497,7 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
     for (int j = 0; j < kNpt; ++j) {
       if (!valid[j]) continue;
       const uint32_t lt = (uint32_t)(tid + j * kOwnedBlock);
-      const LifSeg& sg = s_seg[si[j]];
+      const LifSeg& sg = seg_of(j);
       float xin;
       if (kFixed) {
         const long long q = ring_s[slot * T + lt];
