@@ -9,9 +9,12 @@
 // carry a step stamp, so a word is valid exactly when its stamp is the
 // step's.
 //
-// Synapses in tile-major order: the synapses of source s onto the neurons of
-// tile b are the items [b S + off_s, b S + off_s + c_bs) of one array, padded
-// to C_s = max_b c_bs items per source (S = sum of C_s), each item
+// Synapses grouped by source, then tile: the synapses of source s onto the
+// neurons of tile b are the items [G off_s + b C_s, G off_s + b C_s + c_bs)
+// of one array, padded to C_s = max_b c_bs items per source (off_s = sum of
+// C_s' over the sources before s), so that the G segments of a source lie
+// back to back and the segments a spike sends the blocks to are one
+// contiguous region rather than G scattered ones; each item
 // {local target | delay << 16, FP32 weight} (8 bytes) or, with BF16 or FP16
 // weight storage, a tile of at most 1,024 neurons and delays below 64 steps,
 // weight bits << 16 | delay << 10 | local target (4 bytes, the storage
@@ -145,14 +148,18 @@ __device__ __forceinline__ void add_item(typename OwnedItem<kW>::T x, const Owne
   if (IT::valid(x)) ring_add<kFixed>(ring_s, IT::index(x, t, a), IT::weight(x));
 }
 
-// Items of one spike entry (C_s items from b S + off_s), by the whole warp.
+// First item of the segment of tile b of an entry's source.
+__device__ __forceinline__ uint64_t seg_first(uint64_t e, uint64_t b) {
+  return (e & ((1ull << kOffBits) - 1)) * (uint64_t)gridDim.x + b * ((e >> kOffBits) * 4u);
+}
+
+// Items of one spike entry (C_s items from seg_first), by the whole warp.
 template <bool kFixed, int kW>
 __device__ __forceinline__ void deliver_entry_warp(uint64_t e, const OwnedArgs& a, uint64_t tile_base, int64_t t,
                                                    void* ring_s, int lane) {
   using IT = OwnedItem<kW>;
-  const uint64_t off = e & ((1ull << kOffBits) - 1);
   const uint32_t C = (uint32_t)(e >> kOffBits) * 4u;
-  const typename IT::T* it = reinterpret_cast<const typename IT::T*>(a.items) + tile_base + off;
+  const typename IT::T* it = reinterpret_cast<const typename IT::T*>(a.items) + seg_first(e, tile_base);
   uint32_t k = (uint32_t)lane;
   // two chunks of 32 items in flight per pass
   for (; k < C; k += 64) {
@@ -169,9 +176,8 @@ template <int kW>
 __device__ __forceinline__ void load_head(uint64_t e, const OwnedArgs& a, uint64_t tile_base, int lane,
                                           typename OwnedItem<kW>::T& x0, typename OwnedItem<kW>::T& x1) {
   using IT = OwnedItem<kW>;
-  const uint64_t off = e & ((1ull << kOffBits) - 1);
   const uint32_t C = (uint32_t)(e >> kOffBits) * 4u;
-  const typename IT::T* it = reinterpret_cast<const typename IT::T*>(a.items) + tile_base + off;
+  const typename IT::T* it = reinterpret_cast<const typename IT::T*>(a.items) + seg_first(e, tile_base);
   x0 = (uint32_t)lane < C ? __ldg(it + lane) : IT::filler();
   x1 = (uint32_t)lane + 32 < C ? __ldg(it + lane + 32) : IT::filler();
 }
@@ -180,9 +186,8 @@ template <bool kFixed, int kW>
 __device__ __forceinline__ void deliver_entry_tail(uint64_t e, const OwnedArgs& a, uint64_t tile_base, int64_t t,
                                                    void* ring_s, int lane) {
   using IT = OwnedItem<kW>;
-  const uint64_t off = e & ((1ull << kOffBits) - 1);
   const uint32_t C = (uint32_t)(e >> kOffBits) * 4u;
-  const typename IT::T* it = reinterpret_cast<const typename IT::T*>(a.items) + tile_base + off;
+  const typename IT::T* it = reinterpret_cast<const typename IT::T*>(a.items) + seg_first(e, tile_base);
   for (uint32_t k = 64u + (uint32_t)lane; k < C; k += 32) add_item<kFixed, kW>(__ldg(it + k), a, t, ring_s);
 }
 
@@ -191,9 +196,8 @@ template <bool kFixed, int kW>
 __device__ __forceinline__ void deliver_entry_thread(uint64_t e, const OwnedArgs& a, uint64_t tile_base, int64_t t,
                                                      void* ring_s) {
   using IT = OwnedItem<kW>;
-  const uint64_t off = e & ((1ull << kOffBits) - 1);
   const uint32_t C = (uint32_t)(e >> kOffBits) * 4u;
-  const typename IT::T* it = reinterpret_cast<const typename IT::T*>(a.items) + tile_base + off;
+  const typename IT::T* it = reinterpret_cast<const typename IT::T*>(a.items) + seg_first(e, tile_base);
   for (uint32_t k = 0; k < C; ++k) add_item<kFixed, kW>(__ldg(it + k), a, t, ring_s);
 }
 
@@ -219,7 +223,7 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
   constexpr int kWarps = kOwnedBlock / 32;
   const uint32_t T = a.T;
   const int64_t N = a.N;
-  const uint64_t tile_base = (uint64_t)b * a.S;
+  const uint64_t tile_base = (uint64_t)b;  // the block's tile (seg_first)
 
   for (int i = tid; i < a.n_seg; i += kOwnedBlock) s_seg[i] = a.seg[i];
   for (uint32_t i = tid; i < a.n_thr; i += kOwnedBlock) s_thr[i] = a.thr[i];
@@ -634,7 +638,7 @@ __global__ void k_owned_fill(const uint64_t* __restrict__ src_syn, const uint32_
         const uint32_t target = tgt[j] & kTgtMask;
         const uint32_t tile = target % (uint32_t)G, lt = target / (uint32_t)G;
         const uint32_t pos = atomicAdd(cursor + (uint64_t)s * G + tile, 1u);
-        const uint64_t at = (uint64_t)tile * S + off[s] + pos;
+        const uint64_t at = off[s] * (uint64_t)G + (uint64_t)tile * (off[s + 1] - off[s]) + pos;
         if (wfmt == 0) {
           reinterpret_cast<uint2*>(items)[at] = make_uint2(lt | (d << 16), __float_as_uint(weight_at(w, wdtype, j)));
         } else {  // the 16 storage bits of the weight, as stored
