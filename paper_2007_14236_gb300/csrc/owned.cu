@@ -626,7 +626,7 @@ __device__ __forceinline__ float weight_at(const void* w, int wdtype, uint64_t j
 __global__ void k_owned_fill(const uint64_t* __restrict__ src_syn, const uint32_t* __restrict__ src_grp,
                              const uint64_t* __restrict__ grp_start, const uint16_t* __restrict__ grp_delay,
                              const uint32_t* __restrict__ tgt, const void* w, int wdtype, int64_t N, int G,
-                             uint64_t S, const unsigned long long* __restrict__ off, uint32_t* cursor, void* items,
+                             const unsigned long long* __restrict__ off, uint32_t* cursor, void* items,
                              int wfmt) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -708,7 +708,7 @@ cudaError_t owned_build(const Csr& csr, const uint64_t* src_syn, int64_t N, int 
   }
   if (fits && e == cudaSuccess) {
     k_owned_fill<<<grid, 256, 0, st>>>(src_syn, csr.src_grp, csr.grp_start, csr.grp_delay, csr.tgt, csr.w,
-                                       csr.wdtype, N, G, S, off, cnt, out->items, wfmt);
+                                       csr.wdtype, N, G, off, cnt, out->items, wfmt);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
