@@ -153,6 +153,22 @@ __device__ __forceinline__ uint64_t seg_first(uint64_t e, uint64_t b) {
   return (e & ((1ull << kOffBits) - 1)) * (uint64_t)gridDim.x + b * ((e >> kOffBits) * 4u);
 }
 
+// The whole region of an entry's source (its G segments, back to back) into
+// L2 with one bulk prefetch, issued by the block that publishes the spike a
+// step before the blocks load their segments of it.  The region starts on a
+// 16-byte boundary and spans a multiple of 16 bytes (4-item multiples).
+template <int kW>
+__device__ __forceinline__ void prefetch_region(uint64_t e, const OwnedArgs& a) {
+  using IT = OwnedItem<kW>;
+  const char* p = reinterpret_cast<const char*>(reinterpret_cast<const typename IT::T*>(a.items) + seg_first(e, 0));
+  const uint64_t bytes = (uint64_t)gridDim.x * ((e >> kOffBits) * 4u) * sizeof(typename IT::T);
+  constexpr uint64_t kChunkB = 32768;  // bytes per prefetch instruction
+  for (uint64_t o = 0; o < bytes; o += kChunkB) {
+    const uint32_t n = (uint32_t)(bytes - o < kChunkB ? bytes - o : kChunkB);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + o), "r"(n) : "memory");
+  }
+}
+
 // Items of one spike entry (C_s items from seg_first), by the whole warp.
 template <bool kFixed, int kW>
 __device__ __forceinline__ void deliver_entry_warp(uint64_t e, const OwnedArgs& a, uint64_t tile_base, int64_t t,
@@ -371,7 +387,10 @@ __global__ void __launch_bounds__(kOwnedBlock, 1) k_owned(OwnedArgs a) {
       sp[j] = false;
       if (!valid[j]) continue;
       sp[j] = lif_propagate(seg_of(j), y[j], I[j], ref[j], yp[j], rp[j]);
-      if (sp[j] && pub[j] != 0) s_pub[atomicAdd(&s_np[q], 1)] = pub[j];
+      if (sp[j] && pub[j] != 0) {
+        s_pub[atomicAdd(&s_np[q], 1)] = pub[j];
+        prefetch_region<kW>(pub[j], a);
+      }
     }
   };
   auto publish = [&](int64_t r, int np) {
