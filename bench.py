@@ -54,8 +54,9 @@ NCU_TRAFFIC = {("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "gra
                ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "pipelined", "k_deliver"): 3112960,
                ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "pipelined_one_kernel", "k_step_pipe"):
                    6284672,
-               # one launch = one bench step (10,000 simulation steps); mean of four steady-state launches
-               ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "target_owned", "k_owned"): 12544393792}
+               # one launch = one bench step (10,000 simulation steps): the reads of one 1,000-step launch
+               # after 2,000 steps, scaled by the steps, plus the launch's copy-out of ring and state (writes)
+               ("potjans_diesmann_microcircuit_full_scale", "fp32", "ring", "target_owned", "k_owned"): 12764709120}
 SIM_STEPS_PER_BENCH_STEP = 10_000  # 1 s of biological time at dt = 0.1 ms
 # AdEx update (exponential conductances): FP32 and FP64 operations per Runge-Kutta attempt, counted by ncu
 # (FADD + FMUL + 2 FFMA; DADD + DMUL + 2 DFMA) over one launch on the 2e5-neuron network of the same recipe,
