@@ -37,10 +37,14 @@
 //             device record with one atomic when it could overflow, and at
 //             the end of the launch); event count kept per thread
 //   predict   threshold test of step t + 1; entries (off_s, C_s) of the
-//             sources that will fire, collected in shared memory
+//             sources that will fire, collected in shared memory, and each
+//             such source's item region (its G segments) prefetched into L2,
+//             so that the blocks' item loads of step t + 1 find it there
 //   publish   the block's mailbox for step t + 1 (buffer (t + 1) mod 4):
 //             4 stamped words, 3 entries and the count, further entries in
 //             the block's overflow area; then the Poisson counts of t + 1
+//             (with one neuron per thread, the first thresholds of its
+//             segment and the update's constants held in registers)
 //   deliver   the items of step t's spikes added into the shared ring at
 //             slot (t + delay) & (L - 1): FP32 atomics, or int64 fixed point
 //             (units of 2^-32, as the other loops) in deterministic mode
